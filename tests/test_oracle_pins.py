@@ -1,0 +1,305 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check uses a closed form, a structural
+identity the paper proves, an independent dense computation, or a value the paper prints.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ddst_inputs as I
+from oracle import ddst_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _manufactured(dim, n, w, bconv, c0):
+    """Linear ``a``, constant ``b`` and ``c``, quadratic ``u``: the stencil is exact."""
+    X = I.node_coords(dim, n)
+    alpha = [0.5, 0.25, -0.3][:dim]
+    a = 1.0 + sum(alpha[d] * X[d] for d in range(dim))
+    q = [1.0, -0.5, 0.7][:dim]
+    u = sum(q[d] * X[d] ** 2 for d in range(dim)) + 0.3 * X[0] * X[1] + X[0]
+    grad = []
+    for d in range(dim):
+        gd = 2 * q[d] * X[d]
+        if d == 0:
+            gd = gd + 0.3 * X[1] + 1.0
+        if d == 1:
+            gd = gd + 0.3 * X[0]
+        grad.append(gd)
+    # -div(a grad u) = -(grad a . grad u + a lap u)
+    lap = sum(2 * q[d] for d in range(dim))
+    f = -(sum(alpha[d] * grad[d] for d in range(dim)) + a * lap)
+    f = f + sum(bconv[d] * grad[d] for d in range(dim)) + c0 * u
+    inner = tuple(slice(1, n) for _ in range(dim))
+    prob = dict(dim=dim, n=n, w=w, a=a, b=tuple(bconv), c=np.full_like(a, c0), f=f[inner], g=u)
+    return prob, u[inner].ravel()
+
+
+@pytest.mark.parametrize("dim,n,w", [(2, 16, 4), (2, 24, 8), (3, 8, 2)])
+def test_p1_manufactured_quadratic_exact(dim, n, w):
+    """P1: five/seven-point stencil with face means is exact for linear a x quadratic u."""
+    prob, uex = _manufactured(dim, n, w, bconv=[3.0, -2.0, 1.0][:dim], c0=1.5)
+    A, b = O.assemble(prob)
+    us = O.global_solve(A, b)
+    assert np.abs(us - uex).max() <= 1e-12 * np.abs(uex).max()
+    ud, uG, _ = O.dd_solve(prob)
+    assert np.abs(ud - uex).max() <= 1e-12 * np.abs(uex).max()
+
+
+def test_p1_harmonic_boundary_poisson():
+    """P1: Poisson with f = 0 and g = x^2 - y^2 + xy reproduces g at every interior node."""
+    prob = I.make_problem("poisson2d", n=32, w=8)
+    prob["f"] = np.zeros_like(prob["f"])
+    ud, _, _ = O.dd_solve(prob)
+    gex = prob["g"][1:32, 1:32].ravel()
+    assert np.abs(ud - gex).max() <= 1e-13
+
+
+def _schur_route(A, geo):
+    """Interface Schur complement T = A_JJ - A_JI A_II^{-1} A_IJ (Sec. 2.1), densely."""
+    A = A.toarray()
+    J = np.concatenate(geo.G)
+    Ic = np.setdiff1d(np.arange(A.shape[0]), J)
+    T = A[np.ix_(J, J)] - A[np.ix_(J, Ic)] @ np.linalg.solve(A[np.ix_(Ic, Ic)], A[np.ix_(Ic, J)])
+    return T, J, Ic
+
+
+@pytest.mark.parametrize("name,n,w", [("convdiff2d", 16, 4), ("poisson2d", 20, 4)])
+def test_p2_two_route_identity(name, n, w):
+    """P2: local-solve S equals -T_jj^{-1} T_jj' from the global Schur complement (Sec. 2.1)."""
+    prob = I.make_problem(name, n=n, w=w)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(2, n, w)
+    facs = O.factor_local(A, geo)
+    Sp, Sn = O.transfer_blocks(A, geo, facs)
+    fh = O.equivalent_load(b, geo, facs)
+    T, J, Ic = _schur_route(A, geo)
+    m = geo.ngamma
+    Ad = A.toarray()
+    fprime = b[J] - Ad[np.ix_(J, Ic)] @ np.linalg.solve(Ad[np.ix_(Ic, Ic)], b[Ic])
+    for j in range(geo.nds):
+        Tjj = T[j * m:(j + 1) * m, j * m:(j + 1) * m]
+        if Sp[j] is not None:
+            ref = -np.linalg.solve(Tjj, T[j * m:(j + 1) * m, (j - 1) * m:j * m])
+            assert np.abs(Sp[j] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        if Sn[j] is not None:
+            ref = -np.linalg.solve(Tjj, T[j * m:(j + 1) * m, (j + 1) * m:(j + 2) * m])
+            assert np.abs(Sn[j] - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+        fref = np.linalg.solve(Tjj, fprime[j * m:(j + 1) * m])
+        assert np.abs(fh[j] - fref).max() <= 1e-11 * max(1.0, np.abs(fref).max())
+
+
+def test_p3_brute_force_dense():
+    """P3: every route equals a dense LAPACK solve of the global system on a tiny grid."""
+    prob = I.make_problem("convdiff2d", n=16, w=4)
+    A, b = O.assemble(prob)
+    ud_dense = np.linalg.solve(A.toarray(), b)
+    u1, uG1, _ = O.dd_solve(prob)
+    u2, uG2, info = O.dd_solve(prob, use_gmres=True, tol=1e-13)
+    scale = np.abs(ud_dense).max()
+    assert np.abs(u1 - ud_dense).max() <= 1e-12 * scale
+    assert np.abs(u2 - ud_dense).max() <= 1e-10 * scale
+    geo = O.slab_geometry(2, 16, 4)
+    assert np.abs(uG1 - ud_dense[np.concatenate(geo.G)]).max() <= 1e-12 * scale
+
+
+def test_p3_block_thomas_vs_dense_and_reconstruct():
+    prob = I.make_problem("convdiff2d", n=24, w=4)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(2, 24, 4)
+    facs = O.factor_local(A, geo)
+    Sp, Sn = O.transfer_blocks(A, geo, facs)
+    fh = O.equivalent_load(b, geo, facs)
+    M = O.interface_matrix(Sp, Sn, geo.ngamma)
+    ref = np.linalg.solve(M, np.concatenate(fh))
+    uG = O.block_thomas(Sp, Sn, fh)
+    assert np.abs(uG - ref).max() <= 1e-12 * np.abs(ref).max()
+    x = np.random.default_rng(3).standard_normal(M.shape[0])
+    assert np.abs(O.apply_interface(Sp, Sn, x) - M @ x).max() <= 1e-13 * np.abs(M @ x).max()
+    # reconstruction from the exact traces gives the global solution
+    us = O.global_solve(A, b)
+    ur = O.reconstruct(A, b, geo, facs, us[np.concatenate(geo.G)])
+    assert np.abs(ur - us).max() <= 1e-12 * np.abs(us).max()
+
+
+def test_p4_constants_and_maximum_principle():
+    """P4: g = 1, f = 0, c = 0 gives u = 1; S >= 0 entrywise; fhat + S 1 + S 1 = 1."""
+    n, w = 32, 8
+    # b scaled so the cell Peclet number is below 1: A is then an M-matrix
+    prob = I.make_problem("convdiff2d", n=n, w=w, b=(2.0, 1.0))
+    prob["f"] = np.zeros_like(prob["f"])
+    prob["g"] = np.ones_like(prob["g"])
+    A, b = O.assemble(prob)
+    off = A - sp.diags(A.diagonal())
+    assert off.max() <= 0.0
+    ud, uG, _ = O.dd_solve(prob)
+    assert np.abs(ud - 1.0).max() <= 1e-12
+    geo = O.slab_geometry(2, n, w)
+    facs = O.factor_local(A, geo)
+    Sp, Sn = O.transfer_blocks(A, geo, facs)
+    fh = O.equivalent_load(b, geo, facs)
+    one = np.ones(geo.ngamma)
+    for j in range(geo.nds):
+        tot = fh[j].copy()
+        for S in (Sp[j], Sn[j]):
+            if S is not None:
+                assert S.min() >= -1e-15
+                tot += S @ one
+        assert np.abs(tot - 1.0).max() <= 1e-12
+    # rows of [S_{j,j-1} S_{j,j+1}] sum to < 1 for interior slabs (physical boundary leaks)
+    j = geo.nds // 2
+    assert (Sp[j] @ one + Sn[j] @ one).max() < 1.0
+
+
+@pytest.mark.parametrize("name", ["convdiff2d", "poisson2d"])
+def test_p5_spectrum_symmetric_about_one(name):
+    """P5: eigenvalues of I - K pair up as 1 +- mu (two-coloured slab chain, Sec. 4.2)."""
+    n, w = 24, 4
+    prob = I.make_problem(name, n=n, w=w)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(2, n, w)
+    Sp, Sn = O.transfer_blocks(A, geo, O.factor_local(A, geo))
+    M = O.interface_matrix(Sp, Sn, geo.ngamma)
+    ev = np.linalg.eigvals(M) - 1.0
+    # every mu has a partner -mu (nearest-neighbour match of the spectrum with its negation)
+    dist = np.abs(ev[:, None] + ev[None, :]).min(axis=1)
+    assert dist.max() <= 1e-8
+    if name == "poisson2d":
+        # SPD: real spectrum in (0, 2] (red-black bound, Sec. 4.2; Thm. in Sec. 4.3)
+        assert np.abs(ev.imag).max() <= 1e-10
+        lam = ev.real + 1.0
+        assert lam.min() > 0.0 and lam.max() <= 2.0 + 1e-12
+
+
+def test_p6_energy_symmetry():
+    """P6: with D = blkdiag(T_jj), D (I - K) = T is symmetric for an SPD problem (Sec. 4.2)."""
+    n, w = 20, 4
+    prob = I.make_problem("vardiff3d", n=n, w=w, dim=2, b=(0.0, 0.0))
+    A, b = O.assemble(prob)
+    assert abs(A - A.T).max() == 0.0
+    geo = O.slab_geometry(2, n, w)
+    Sp, Sn = O.transfer_blocks(A, geo, O.factor_local(A, geo))
+    M = O.interface_matrix(Sp, Sn, geo.ngamma)
+    T, _, _ = _schur_route(A, geo)
+    m = geo.ngamma
+    D = np.zeros_like(T)
+    for j in range(geo.nds):
+        D[j * m:(j + 1) * m, j * m:(j + 1) * m] = T[j * m:(j + 1) * m, j * m:(j + 1) * m]
+    DS = D @ M
+    assert np.abs(DS - DS.T).max() <= 1e-9 * np.abs(DS).max()
+    assert np.abs(DS - T).max() <= 1e-9 * np.abs(T).max()
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(t) for t in line.split()])
+    return rows
+
+
+def test_p7_printed_poisson_table_first_row():
+    """P7: 3D Poisson, 16^3 grid, 8 slabs: kappa_2(S_H) and GMRES iterations as printed."""
+    N, iters, kappa = _golden("fd_poisson_fixedH.txt")[0]
+    n = round(N ** (1 / 3))
+    prob = I.make_problem("vardiff3d", n=n, w=n // 8, const_a=True)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(3, n, n // 8)
+    Sp, Sn = O.transfer_blocks(A, geo, O.factor_local(A, geo))
+    M = O.interface_matrix(Sp, Sn, geo.ngamma)
+    s = np.linalg.svd(M, compute_uv=False)
+    assert abs(s[0] / s[-1] - kappa) <= 0.01
+    rhs = np.random.default_rng(0).uniform(-1, 1, M.shape[0])
+    _, its, _ = O.gmres(lambda v: M @ v, rhs, tol=1e-8)
+    assert abs(its - iters) <= 0.1 * iters + 1
+
+
+def test_gmres_finite_termination_and_residual():
+    """GMRES on a diagonalizable matrix with k distinct eigenvalues stops after k steps."""
+    rng = np.random.default_rng(1)
+    Q, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    lam = np.repeat([0.5, 1.0, 1.7, 2.5, 3.0], 12)
+    M = Q @ np.diag(lam) @ Q.T
+    rhs = rng.standard_normal(60)
+    x, its, hist = O.gmres(lambda v: M @ v, rhs, tol=1e-12)
+    assert its == 5
+    assert np.linalg.norm(M @ x - rhs) <= 1e-11 * np.linalg.norm(rhs)
+    # nonsymmetric: residual estimate equals the true residual
+    B = np.eye(40) + 0.3 * rng.standard_normal((40, 40)) / np.sqrt(40)
+    rhs = rng.standard_normal(40)
+    x, its, hist = O.gmres(lambda v: B @ v, rhs, tol=1e-10)
+    true = np.linalg.norm(B @ x - rhs) / np.linalg.norm(rhs)
+    assert true <= 2e-10 and abs(true - hist[-1]) <= 1e-12
+
+
+def test_p8_gradients_linear_directions_and_fd_in_a():
+    """P8: adjoint gradients vs central differences (exact in f, g; 1e-5 relative in a)."""
+    n, w = 16, 4
+    prob = I.make_problem("convdiff2d", n=n, w=w)
+    rng = np.random.default_rng(7)
+    u_obs = rng.standard_normal((n - 1) ** 2)
+    L, dLdf, dLdg, dLda, u, lam = O.loss_and_gradients(prob, u_obs)
+
+    def loss(p):
+        A, b = O.assemble(p)
+        r = O.global_solve(A, b) - u_obs
+        return 0.5 * float(r @ r)
+
+    for key, grad in (("f", dLdf), ("g", dLdg), ("a", dLda)):
+        d = rng.standard_normal(prob[key].shape)
+        if key == "g":  # only boundary values of g matter
+            mask = np.ones_like(d); mask[1:n, 1:n] = 0.0; d *= mask
+        eps = 1e-3 if key != "a" else 1e-6
+        pp = dict(prob); pm = dict(prob)
+        pp[key] = prob[key] + eps * d
+        pm[key] = prob[key] - eps * d
+        fd = (loss(pp) - loss(pm)) / (2 * eps)
+        an = float(np.sum(grad * d))
+        assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-12), (key, fd, an)
+
+
+def test_p8_adjoint_dot_product():
+    prob = I.make_problem("convdiff2d", n=16, w=4)
+    A, b = O.assemble(prob)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal(A.shape[0]); y = rng.standard_normal(A.shape[0])
+    lhs = O.global_solve(A, x) @ y
+    rhs = x @ O.adjoint_solve(A, y)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_p9_hodlr_tree_and_exact_limits():
+    """P9: tree partitions the index range; tol -> 0 reproduces S; known low rank found."""
+    for ng in (31, 127, 2047, 1000):
+        for leaf in (16, 64, 128):
+            L = O.hodlr_levels(ng, leaf)
+            spans = [O.hodlr_node(ng, L, t) for t in range(1 << L)]
+            assert spans[0][0] == 0 and spans[-1][1] == ng
+            assert all(spans[i][1] == spans[i + 1][0] for i in range(len(spans) - 1))
+            assert max(hi - lo for lo, hi in spans) <= leaf
+    prob = I.make_problem("convdiff2d", n=64, w=8)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(2, 64, 8)
+    facs = O.factor_local(A, geo)
+    Sp, Sn = O.transfer_blocks(A, geo, facs, slabs=[3])
+    S = Sp[0]
+    H = O.hodlr_compress(S, tol=0.0, leaf=8)
+    assert np.abs(O.hodlr_dense(H) - S).max() <= 1e-13 * np.abs(S).max()
+    # truncation error per block is sigma_{r+1} <= tol ||S||_2 (Eckart-Young), total <= L * that
+    tol = 1e-6
+    H = O.hodlr_compress(S, tol=tol, leaf=8)
+    err = np.linalg.norm(O.hodlr_dense(H) - S, 2) / np.linalg.norm(S, 2)
+    assert err <= 2 * H["L"] * tol
+    x = np.random.default_rng(0).standard_normal(S.shape[0])
+    assert np.abs(O.hodlr_apply(H, x) - O.hodlr_dense(H) @ x).max() <= 1e-12 * np.abs(S @ x).max()
+    # a matrix built from rank-2 off-diagonal pieces: exactly rank <= 2 everywhere
+    ng = 64
+    t = np.linspace(0, 1, ng)
+    K = np.outer(np.cos(t), np.sin(t)) + np.outer(t, t ** 2)
+    H = O.hodlr_compress(K + np.diag(t), tol=1e-12, leaf=8)
+    assert max(U.shape[1] for lev in H["levels"] for (U, V) in lev) <= 2
