@@ -1,0 +1,186 @@
+/*
+ * ddst.h -- C ABI of the GB300 overlapping solution-transfer domain decomposition.
+ *
+ * Method: arXiv 2510.25991, "An overlapping domain decomposition method based on
+ * solution-transfer operators".  The library solves the variable-coefficient elliptic
+ * boundary value problem of Sec. 1, Eq. (basic),
+ *
+ *     -div(a grad u) + b . grad u + c u = f   in the unit square / cube,   u = g on the boundary,
+ *
+ * discretized by the five-point (2D) / seven-point (3D) finite-difference stencil of Sec. 2.1 /
+ * Sec. 5.2 on a uniform grid with n cells per side (h = 1/n).  The domain is cut into slabs of
+ * w cells normal to x; the N_ds = n/w - 1 interior interfaces Gamma_j are coupled by the local
+ * Dirichlet solution-transfer operators S_{j,j-1}, S_{j,j+1} of the overlapping double slabs
+ * Psi_j (Sec. 2.2, Eq. (defS); Alg. 1, Alg. 2).  The equilibrium system (I - K) u_Gamma = fhat
+ * (Sec. 1, Eq. (modelS)) is solved by unrestarted GMRES (Sec. 5), after which the volume is
+ * reconstructed by local solves.  Mixed precision (FP32 local operators, FP64 Krylov and FP64
+ * global residual refinement) is this library's addition; the paper computes in FP64.
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are FP64 and C-contiguous with x the slowest axis.  Nodal arrays (a, c, g and the
+ *    gradient dL/da, dL/dg) have (n+1)^dim entries; interior arrays (f, u, dL/du, dL/df) have
+ *    (n-1)^dim entries.  Interface vectors are N_ds blocks of n_Gamma = (n-1)^(dim-1) values,
+ *    block j holding Gamma_j ordered like the remaining axes (y, then z).
+ *  - An array argument may point to host or to device memory; the library detects which with
+ *    cudaPointerGetAttributes and stages host arrays through its own device buffers.  Arrays
+ *    are owned by the caller and only read/written during the call.
+ *  - Every call is ordered on the CUDA stream given to ddst_setup (NULL = the legacy default
+ *    stream) and returns after the stream has finished the call's work.
+ *  - No entry point aborts, traps or waits without bound.  Errors return a status, record a
+ *    message (ddst_last_error) and leave the context usable.  A call out of order returns
+ *    DDST_ERR_STATE.
+ *  - Device memory of a context is allocated by the library (cudaMalloc) and released by
+ *    ddst_destroy.
+ */
+#ifndef DDST_H
+#define DDST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDST_OK = 0,
+  DDST_ERR_INVALID_ARG = 1,   /* bad size, pointer or option                               */
+  DDST_ERR_OOM = 2,           /* cudaMalloc failed                                         */
+  DDST_ERR_CUDA = 3,          /* any other CUDA runtime error                              */
+  DDST_ERR_SINGULAR = 4,      /* a local pivot block was singular (info.fail_slab/_block)  */
+  DDST_ERR_NOT_CONVERGED = 5, /* GMRES or refinement missed its tolerance                  */
+  DDST_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                             */
+  DDST_ERR_STATE = 7,         /* call out of order (e.g. solve before build_transfer)      */
+  DDST_ERR_NOT_IMPLEMENTED = 8
+} ddst_status;
+
+/* Arithmetic of the local operators, transfer operators and their application. */
+enum {
+  DDST_FP64 = 0,   /* everything FP64                                                      */
+  DDST_MIXED = 1   /* FP32 factors, FP32 transfer operators (FP32 accumulation),
+                      FP64 GMRES vectors, FP64 global residual refinement                  */
+};
+
+typedef struct ddst_ctx ddst_ctx;
+
+/* Uniform grid on the unit square (dim = 2) or cube (dim = 3) with n cells per side. */
+typedef struct {
+  int dim;
+  int64_t n;
+} ddst_grid;
+
+/* PDE coefficients of Sec. 1, Eq. (basic). */
+typedef struct {
+  const double* a;  /* nodal diffusion coefficient, (n+1)^dim values, all > 0 (required)       */
+  double b[3];      /* constant convection vector (unused components ignored)                  */
+  const double* c;  /* nodal reaction coefficient, (n+1)^dim values, or NULL for c = 0         */
+} ddst_coeffs;
+
+typedef struct {
+  int precision;        /* DDST_FP64 or DDST_MIXED                                            */
+  double gmres_tol;     /* relative residual target of each interface GMRES solve             */
+  int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES)                           */
+  double refine_tol;    /* stop when ||correction|| <= refine_tol * ||u|| (FP64 refinement)   */
+  int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
+  int k_max;            /* HODLR rank cap per block                                           */
+  int oversample;       /* extra random samples beyond k_max (sketch width k_max+oversample)  */
+  int leaf_size;        /* HODLR leaf size                                                    */
+  uint64_t seed;        /* seed of the counter-based Gaussian sketch generator                */
+  int check_every;      /* GMRES iterations between host convergence checks                   */
+} ddst_options;
+
+/* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
+typedef struct {
+  int gmres_iters;        /* GMRES iterations summed over refinement steps                    */
+  int gmres_iters_first;  /* iterations of the first interface solve                          */
+  int refine_iters;       /* DD solves performed (1 = no refinement correction needed)        */
+  double rel_residual;    /* final ||b - A u||_2 / ||b||_2 in FP64                            */
+  double est_rel_error;   /* ||last correction||_2 / ||u||_2                                  */
+  double t_factor, t_transfer, t_compress, t_solve;
+  int64_t bytes_factors;  /* device bytes of the local factors                                */
+  int64_t bytes_transfer; /* device bytes of the transfer operators (dense or HODLR)          */
+  int max_rank;           /* largest HODLR rank (0 when dense)                                */
+  int fail_slab;          /* first slab with a singular pivot, else -1                        */
+  int fail_block;         /* its block (y index, 1-based), else -1                            */
+} ddst_info;
+
+/* Fills *opt with defaults: MIXED, gmres_tol 1e-6 (1e-11 for FP64), refine_tol 1e-9,
+ * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234. */
+void ddst_options_default(ddst_options* opt);
+
+/* Builds the local operators A_j(I_j, I_j) of every double slab and factors them
+ * (Sec. 2.5 and Alg. 2: "compute local discretization", "factorize").
+ * grid/coeffs: one problem; slab_width: w cells (n % w == 0, n/w >= 2, 2w-1 <= 127 in 2D,
+ * (2w-1)(n-1) <= 128 in 3D).  opt may be NULL (defaults).  stream: cudaStream_t or NULL.
+ * On success *out receives a new context.  Errors: INVALID_ARG, OOM, CUDA, SINGULAR. */
+ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
+                       const ddst_options* opt, void* stream, ddst_ctx** out);
+
+/* Same for nprob independent problems sharing one context (batched kernels over all slabs of
+ * all problems).  grids, coeffs and slab_widths are arrays of nprob entries. */
+ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                             const int* slab_widths, const ddst_options* opt, void* stream,
+                             ddst_ctx** out);
+
+/* Forms every S_{j,j-1} and S_{j,j+1} explicitly (Sec. 2.2, Eq. (defS)) from one transposed
+ * multi-right-hand-side solve per double slab with the central interface points as sources.
+ * Requires ddst_setup.  Errors: STATE, OOM, CUDA. */
+ddst_status ddst_build_transfer(ddst_ctx* ctx);
+
+/* Compresses every S_{j,j'} into HODLR form (Sec. 2.4: weak admissibility, cluster tree
+ * shared by source and target interface) by randomized sampling with Gaussian sketches; each
+ * off-diagonal block is truncated at sigma_{r+1} <= tol * ||S_{j,j'}||_2 (rank <= k_max).
+ * tol <= 0 keeps the dense operators.  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA. */
+ddst_status ddst_compress(ddst_ctx* ctx, double tol);
+
+/* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.
+ * (equilib1)), GMRES on (I - K) u_Gamma = fhat, volume reconstruction, then FP64 residual
+ * refinement u += DD(b - A u) until ||correction|| <= refine_tol ||u||.
+ * f: interior load; g: nodal Dirichlet data (only boundary nodes are read); u: interior
+ * output.  info may be NULL.  Errors: STATE, INVALID_ARG, NOT_CONVERGED (u still written). */
+ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,
+                       ddst_info* info);
+
+/* Batched form: f, g, u are arrays of nprob pointers (one per problem). */
+ddst_status ddst_solve_batch(ddst_ctx* ctx, const double* const* f, const double* const* g,
+                             double* const* u, ddst_info* info);
+
+/* Discrete adjoint of the last ddst_solve: lambda = A^{-T} dL_du through the transposed DD
+ * (transposed local solves through the same factors, transposed transfer operators, GMRES
+ * on (I - K)^T), refined against the FP64 residual of A^T.  Writes dL_df = lambda (interior),
+ * dL_dg (nodal; boundary nodes only, interior entries set to 0) and dL_da (nodal; may be
+ * NULL to skip).  Any output pointer may be NULL.  Errors: STATE, NOT_CONVERGED. */
+ddst_status ddst_solve_adjoint(ddst_ctx* ctx, const double* dL_du, double* dL_df,
+                               double* dL_dg, double* dL_da, ddst_info* info);
+
+/* Batched adjoint: arrays of nprob pointers. */
+ddst_status ddst_solve_adjoint_batch(ddst_ctx* ctx, const double* const* dL_du,
+                                     double* const* dL_df, double* const* dL_dg,
+                                     double* const* dL_da, ddst_info* info);
+
+/* Interface traces u_Gamma of problem prob from the last solve (N_ds * n_Gamma values). */
+ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG);
+
+/* Copies S_{j,j-1} (side = -1) or S_{j,j+1} (side = +1) of problem prob, slab j (1-based),
+ * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR if compressed). */
+ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* out);
+
+/* y = (I - K) x (transpose = 0) or y = (I - K)^T x (transpose = 1) for problem prob with the
+ * current (dense or HODLR) operators; x and y hold N_ds * n_Gamma values. */
+ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, double* y,
+                                 int transpose);
+
+/* Sizes of problem prob: n_ds, n_gamma and the total interface length (any may be NULL). */
+ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
+                       int* max_rank);
+
+/* Message of the last error on ctx (or of the last failed ddst_setup when ctx is NULL). */
+const char* ddst_last_error(const ddst_ctx* ctx);
+
+/* Releases the context and all its device memory.  NULL is ignored. */
+void ddst_destroy(ddst_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDST_H */

@@ -1,0 +1,898 @@
+// api.cu -- host orchestration behind the C ABI of include/ddst.h.
+//
+// Pipeline (Alg. 2 of the paper, per double slab, batched over all slabs of all problems):
+//   ddst_setup            stencil pack (local discretization) + two-sided block factorization
+//   ddst_build_transfer   explicit S_{j,j-1}, S_{j,j+1} by multi-RHS transposed solves (Alg. 1)
+//   ddst_compress         HODLR compression of every S block (Sec. 2.4)
+//   ddst_solve            fhat (Sec. 2.2, Eq. (equilib1)), GMRES on (I - K) u = fhat (Sec. 5),
+//                         volume reconstruction, FP64 residual refinement
+//   ddst_solve_adjoint    the same chain transposed, then gradient assembly
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ddst.h"
+#include "hodlr.cuh"
+#include "kernels.cuh"
+
+using namespace ddst;
+
+namespace {
+
+std::string g_setup_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ddst_ctx {
+  int nprob = 0;
+  int prec = DDST_MIXED;
+  cudaStream_t stream = nullptr;
+  ddst_options opt{};
+  std::vector<ProbDesc> probs;
+  std::vector<SlabDesc> slabs;
+  std::map<int, std::vector<int>> cls;     // M -> slab ids
+  std::map<int, int*> d_cls;               // M -> device id array
+  std::map<int, int> cls_maxnb;
+  ProbDesc* d_probs = nullptr;
+  SlabDesc* d_slabs = nullptr;
+  DevStatus* d_st = nullptr;
+  int max_nb = 0;
+  int64_t max_ng = 0;
+  int64_t tot_nodes = 0, tot_vol = 0, tot_if = 0, tot_loc = 0, fac_elems = 0, pack_elems = 0,
+          s_elems = 0;
+  size_t esz = 4;  // sizeof working precision
+  // device buffers
+  double *d_a = nullptr, *d_c = nullptr;
+  void *F = nullptr, *B = nullptr, *G = nullptr, *pack = nullptr, *S = nullptr;
+  void *loc_b = nullptr, *loc_bf = nullptr, *loc_bb = nullptr, *loc_x = nullptr;
+  double *d_f = nullptr, *d_g = nullptr, *d_b = nullptr, *d_u = nullptr, *d_r = nullptr,
+         *d_e = nullptr, *d_lam = nullptr, *d_ga = nullptr, *d_gn = nullptr, *d_an = nullptr;
+  double *if_fh = nullptr, *if_u = nullptr, *if_w = nullptr, *if_tmp = nullptr;
+  double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr,
+         *resid = nullptr, *hcol = nullptr, *hpass = nullptr, *part = nullptr, *scal = nullptr,
+         *ysol = nullptr;
+  int ldh = 0;
+  int nchunk = 0;
+  HodlrSet hodlr;  // compressed operators (when compressed)
+  int state = 0;   // 1 factored, 2 transfer formed, 3 compressed
+  bool have_solution = false;
+  std::vector<void*> owned;
+  std::string err;
+  float t_factor = 0.f, t_transfer = 0.f, t_compress = 0.f;
+};
+
+namespace {
+
+ddst_status fail(ddst_ctx* c, ddst_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_setup_error = buf;
+  return s;
+}
+
+ddst_status cuda_fail(ddst_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? DDST_ERR_OOM : DDST_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define CK(expr)                                                 \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr);     \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(ddst_ctx* ctx, P** out, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes < 16 ? 16 : bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }
+  ctx->owned.push_back(p);
+  *out = reinterpret_cast<P*>(p);
+  return cudaSuccess;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copy n doubles from a host or device pointer into device memory dst (stream-ordered).
+cudaError_t stage_in(double* dst, const double* src, size_t n, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, n * sizeof(double),
+                         is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t stage_out(double* dst, const double* src, size_t n, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, n * sizeof(double),
+                         is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+}
+
+ddst_status check_status(ddst_ctx* ctx, ddst_info* info) {
+  DevStatus h;
+  CK(cudaMemcpyAsync(&h, ctx->d_st, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h.code == 0) return DDST_OK;
+  CK(cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), ctx->stream));
+  if (info) {
+    info->fail_slab = h.slab;
+    info->fail_block = h.block;
+  }
+  if (h.code == ST_SINGULAR)
+    return fail(ctx, DDST_ERR_SINGULAR, "singular pivot in slab %d (block %d)", h.slab, h.block);
+  if (h.code == ST_TIMEOUT)
+    return fail(ctx, DDST_ERR_TIMEOUT, "bounded device wait expired (slab %d, block %d)", h.slab,
+                h.block);
+  return fail(ctx, DDST_ERR_CUDA, "device status %d", h.code);
+}
+
+int pad_M(int m) { return m <= 32 ? 32 : (m <= 64 ? 64 : (m <= 128 ? 128 : -1)); }
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  float stop() {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// --------------------------------------------------------------------------------------------
+// Setup
+// --------------------------------------------------------------------------------------------
+ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                       const int* widths, const ddst_options* opt, void* stream, ddst_ctx** out) {
+  if (!out) return fail(nullptr, DDST_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nprob <= 0 || !grids || !coeffs || !widths)
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "bad problem list");
+  ddst_ctx* ctx = new ddst_ctx();
+  ctx->nprob = nprob;
+  ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (opt) ctx->opt = *opt; else ddst_options_default(&ctx->opt);
+  ctx->prec = ctx->opt.precision == DDST_FP64 ? DDST_FP64 : DDST_MIXED;
+  ctx->esz = ctx->prec == DDST_FP64 ? 8 : 4;
+  int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, pack_off = 0, loc_off = 0, s_off = 0;
+  for (int q = 0; q < nprob; ++q) {
+    const ddst_grid& gr = grids[q];
+    const int w = widths[q];
+    if (gr.dim != 2 && gr.dim != 3) { ddst_destroy(ctx); return fail(nullptr, DDST_ERR_INVALID_ARG, "dim must be 2 or 3"); }
+    if (gr.n < 4 || gr.n > (1 << 20) || w < 1 || gr.n % w != 0 || gr.n / w < 2) {
+      ddst_destroy(ctx);
+      return fail(nullptr, DDST_ERR_INVALID_ARG, "problem %d: need n %% w == 0 and n/w >= 2", q);
+    }
+    if (!coeffs[q].a) { ddst_destroy(ctx); return fail(nullptr, DDST_ERR_INVALID_ARG, "problem %d: a is NULL", q); }
+    ProbDesc P{};
+    P.dim = gr.dim;
+    P.n = (int)gr.n;
+    P.w = w;
+    P.nds = P.n / w - 1;
+    P.p = gr.dim == 2 ? 1 : P.n - 1;
+    P.m = (2 * w - 1) * P.p;
+    P.M = pad_M(P.m);
+    if (P.M < 0 || (ctx->prec == DDST_FP64 && P.M > 64)) {
+      ddst_destroy(ctx);
+      return fail(nullptr, DDST_ERR_INVALID_ARG,
+                  "problem %d: block size (2w-1)(n-1)^(dim-2) = %d exceeds %d", q, P.m,
+                  ctx->prec == DDST_FP64 ? 64 : 128);
+    }
+    P.nb = P.n - 1;
+    P.ng = (int64_t)P.nb * P.p;
+    P.nint = 1;
+    P.nnode = 1;
+    for (int d = 0; d < gr.dim; ++d) { P.nint *= (P.n - 1); P.nnode *= (P.n + 1); }
+    P.vol_off = vol_off;
+    P.node_off = node_off;
+    P.if_off = if_off;
+    P.slab0 = (int)ctx->slabs.size();
+    P.has_c = coeffs[q].c != nullptr;
+    P.h = 1.0 / P.n;
+    for (int d = 0; d < 3; ++d) P.b[d] = d < gr.dim ? coeffs[q].b[d] : 0.0;
+    for (int j = 1; j <= P.nds; ++j) {
+      SlabDesc s{};
+      s.prob = q; s.j = j; s.M = P.M; s.m = P.m; s.nb = P.nb; s.p = P.p; s.w = w; s.n = P.n;
+      s.ng = P.ng;
+      s.fac_off = fac_off; fac_off += (int64_t)P.nb * P.M * P.M;
+      s.pack_off = pack_off; pack_off += (int64_t)P.nb * PK_NFIELDS * P.M;
+      s.loc_off = loc_off; loc_off += (int64_t)P.nb * P.M;
+      s.sp_off = -1; s.sn_off = -1;
+      if (j >= 2) { s.sp_off = s_off; s_off += P.ng * P.ng; }
+      if (j <= P.nds - 1) { s.sn_off = s_off; s_off += P.ng * P.ng; }
+      s.vol_off = vol_off; s.node_off = node_off;
+      s.if_off = if_off + (int64_t)(j - 1) * P.ng;
+      ctx->cls[P.M].push_back((int)ctx->slabs.size());
+      ctx->cls_maxnb[P.M] = std::max(ctx->cls_maxnb[P.M], P.nb);
+      ctx->slabs.push_back(s);
+    }
+    ctx->max_nb = std::max(ctx->max_nb, P.nb);
+    ctx->max_ng = std::max(ctx->max_ng, P.ng);
+    node_off += P.nnode;
+    vol_off += P.nint;
+    if_off += (int64_t)P.nds * P.ng;
+    ctx->probs.push_back(P);
+  }
+  ctx->tot_nodes = node_off; ctx->tot_vol = vol_off; ctx->tot_if = if_off;
+  ctx->tot_loc = loc_off; ctx->fac_elems = fac_off; ctx->pack_elems = pack_off; ctx->s_elems = s_off;
+  const int nslab = (int)ctx->slabs.size();
+  const size_t es = ctx->esz;
+  cudaError_t e;
+#define AL(ptr, bytes)                                                        \
+  if ((e = dalloc(ctx, &(ptr), (bytes))) != cudaSuccess) {                    \
+    ddst_status s_ = cuda_fail(nullptr, e, "cudaMalloc " #ptr);               \
+    ddst_destroy(ctx);                                                        \
+    return s_;                                                                \
+  }
+  AL(ctx->d_probs, sizeof(ProbDesc) * nprob);
+  AL(ctx->d_slabs, sizeof(SlabDesc) * nslab);
+  AL(ctx->d_st, sizeof(DevStatus));
+  AL(ctx->d_a, sizeof(double) * ctx->tot_nodes);
+  AL(ctx->d_c, sizeof(double) * ctx->tot_nodes);
+  AL(ctx->pack, es * ctx->pack_elems);
+  AL(ctx->F, es * ctx->fac_elems);
+  AL(ctx->B, es * ctx->fac_elems);
+  AL(ctx->G, es * ctx->fac_elems);
+  AL(ctx->loc_b, es * ctx->tot_loc);
+  AL(ctx->loc_bf, es * ctx->tot_loc);
+  AL(ctx->loc_bb, es * ctx->tot_loc);
+  AL(ctx->loc_x, es * ctx->tot_loc);
+  for (auto& kv : ctx->cls) {
+    int* d = nullptr;
+    AL(d, sizeof(int) * kv.second.size());
+    ctx->d_cls[kv.first] = d;
+  }
+#undef AL
+  cudaStream_t st = ctx->stream;
+  auto bail = [&](cudaError_t err, const char* what) {
+    ddst_status s_ = cuda_fail(nullptr, err, what);
+    ddst_destroy(ctx);
+    return s_;
+  };
+  if ((e = cudaMemcpyAsync(ctx->d_probs, ctx->probs.data(), sizeof(ProbDesc) * nprob,
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(e, "copy probs");
+  if ((e = cudaMemcpyAsync(ctx->d_slabs, ctx->slabs.data(), sizeof(SlabDesc) * nslab,
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(e, "copy slabs");
+  for (auto& kv : ctx->cls)
+    if ((e = cudaMemcpyAsync(ctx->d_cls[kv.first], kv.second.data(), sizeof(int) * kv.second.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(e, "copy ids");
+  cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), st);
+  cudaMemsetAsync(ctx->d_c, 0, sizeof(double) * ctx->tot_nodes, st);
+  for (int q = 0; q < nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    if ((e = stage_in(ctx->d_a + P.node_off, coeffs[q].a, P.nnode, st)) != cudaSuccess) return bail(e, "copy a");
+    if (coeffs[q].c)
+      if ((e = stage_in(ctx->d_c + P.node_off, coeffs[q].c, P.nnode, st)) != cudaSuccess) return bail(e, "copy c");
+  }
+  Timer tm(st);
+  if (ctx->prec == DDST_FP64) {
+    launch_stencil_pack<double>(ctx->d_slabs, nslab, ctx->max_nb, ctx->d_probs, ctx->d_a, ctx->d_c,
+                                (double*)ctx->pack, st);
+    for (auto& kv : ctx->cls)
+      launch_factor<double>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                            ctx->cls_maxnb[kv.first], (double*)ctx->pack, (double*)ctx->F,
+                            (double*)ctx->B, (double*)ctx->G, ctx->d_st, st);
+  } else {
+    launch_stencil_pack<float>(ctx->d_slabs, nslab, ctx->max_nb, ctx->d_probs, ctx->d_a, ctx->d_c,
+                               (float*)ctx->pack, st);
+    for (auto& kv : ctx->cls)
+      launch_factor<float>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                           ctx->cls_maxnb[kv.first], (float*)ctx->pack, (float*)ctx->F,
+                           (float*)ctx->B, (float*)ctx->G, ctx->d_st, st);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "factor launch");
+  ctx->t_factor = tm.stop();
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "factor");
+  ddst_status s = check_status(ctx, nullptr);
+  if (s != DDST_OK) {
+    g_setup_error = ctx->err;
+    ddst_destroy(ctx);
+    return s;
+  }
+  ctx->state = 1;
+  *out = ctx;
+  return DDST_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// Transfer operators
+// --------------------------------------------------------------------------------------------
+template <typename T>
+ddst_status build_transfer_impl(ddst_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  if (!ctx->S) {
+    cudaError_t e = dalloc(ctx, &ctx->S, sizeof(T) * ctx->s_elems);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc S");
+  }
+  Timer tm(st);
+  for (auto& kv : ctx->cls) {
+    const int M = kv.first;
+    const int R = sbuild_tile_cols<T>(M);
+    std::vector<TileDesc> tiles;
+    for (int sid : kv.second) {
+      const SlabDesc& s = ctx->slabs[sid];
+      if (s.sp_off < 0 && s.sn_off < 0) continue;
+      for (int64_t q0 = 0; q0 < s.ng; q0 += R) {
+        const int nq = (int)std::min<int64_t>(R, s.ng - q0);
+        TileDesc up{sid, (int)q0, nq, 0, (int)((q0 + nq - 1) / s.p) + 1, 0};
+        up.len = up.kstart;
+        TileDesc dn{sid, (int)q0, nq, 1, (int)(q0 / s.p) + 1, 0};
+        dn.len = s.nb - dn.kstart + 1;
+        tiles.push_back(up);
+        tiles.push_back(dn);
+      }
+    }
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [](const TileDesc& a, const TileDesc& b) { return a.len > b.len; });
+    if (tiles.empty()) continue;
+    TileDesc* d_tiles = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_tiles, sizeof(TileDesc) * tiles.size(), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocAsync tiles");
+    CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
+                       cudaMemcpyHostToDevice, st));
+    launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
+                     (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
+                     ctx->d_st, st);
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(d_tiles, st));
+  }
+  ctx->t_transfer = tm.stop();
+  CK(cudaStreamSynchronize(st));
+  ddst_status s = check_status(ctx, nullptr);
+  if (s != DDST_OK) return s;
+  ctx->hodlr.clear();
+  ctx->state = 2;
+  return DDST_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// Solve
+// --------------------------------------------------------------------------------------------
+ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
+  if (ctx->d_b) return DDST_OK;
+  const int maxit = std::max(1, ctx->opt.gmres_max_iter);
+  ctx->ldh = maxit + 1;
+  ctx->nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(256, (ctx->tot_if + 4095) / 4096));
+  cudaError_t e;
+#define AL(ptr, bytes) if ((e = dalloc(ctx, &(ptr), (bytes))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc " #ptr);
+  AL(ctx->d_f, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_g, sizeof(double) * ctx->tot_nodes);
+  AL(ctx->d_b, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_u, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_r, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_e, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_lam, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_ga, sizeof(double) * ctx->tot_vol);
+  AL(ctx->d_gn, sizeof(double) * ctx->tot_nodes);
+  AL(ctx->d_an, sizeof(double) * ctx->tot_nodes);
+  AL(ctx->if_fh, sizeof(double) * ctx->tot_if);
+  AL(ctx->if_u, sizeof(double) * ctx->tot_if);
+  AL(ctx->if_w, sizeof(double) * ctx->tot_if);
+  AL(ctx->if_tmp, sizeof(double) * ctx->tot_if);
+  AL(ctx->V, sizeof(double) * ctx->tot_if * (size_t)(maxit + 1));
+  AL(ctx->H, sizeof(double) * (size_t)ctx->ldh * (maxit + 1));
+  AL(ctx->cs, sizeof(double) * (maxit + 1));
+  AL(ctx->sn, sizeof(double) * (maxit + 1));
+  AL(ctx->gv, sizeof(double) * (maxit + 2));
+  AL(ctx->resid, sizeof(double) * (maxit + 1));
+  AL(ctx->hcol, sizeof(double) * (maxit + 1));
+  AL(ctx->hpass, sizeof(double) * (maxit + 1));
+  AL(ctx->part, sizeof(double) * (size_t)(maxit + 1) * std::max(ctx->nchunk, 1024));
+  AL(ctx->scal, sizeof(double) * 16);
+  AL(ctx->ysol, sizeof(double) * (maxit + 1));
+#undef AL
+  return DDST_OK;
+}
+
+template <typename T>
+void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose) {
+  if (ctx->state == 3)
+    hodlr_apply<T>(ctx->hodlr, ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), x, y, transpose,
+                   ctx->stream);
+  else
+    launch_apply_dense<T>(ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), ctx->max_ng,
+                          (const T*)ctx->S, x, y, transpose, ctx->stream);
+}
+
+double host_scalar(ddst_ctx* ctx, const double* d) {
+  double h = 0.0;
+  cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return h;
+}
+
+// GMRES on (I - K) x = rhs (or its transpose), x0 = 0.  Returns iterations; sets *relres.
+template <typename T>
+ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, int transpose,
+                       int* iters, double* relres) {
+  cudaStream_t st = ctx->stream;
+  const int64_t n = ctx->tot_if;
+  const int maxit = std::max(1, ctx->opt.gmres_max_iter);
+  const int check = std::max(1, ctx->opt.check_every);
+  launch_dot(rhs, rhs, n, ctx->part, 256, ctx->scal, st);
+  const double beta = std::sqrt(host_scalar(ctx, ctx->scal));
+  *iters = 0;
+  *relres = 0.0;
+  if (!(beta > 0.0)) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    return DDST_OK;
+  }
+  launch_normalize_start(rhs, ctx->scal, ctx->V, n, st);
+  CK(cudaMemsetAsync(ctx->gv, 0, sizeof(double) * (maxit + 2), st));
+  CK(cudaMemcpyAsync(ctx->gv, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+  std::vector<double> hres(maxit + 1);
+  int kk = -1;
+  int k = 0;
+  for (k = 1; k <= maxit; ++k) {
+    double* vprev = ctx->V + (int64_t)(k - 1) * n;
+    apply_interface_T<T>(ctx, vprev, ctx->if_w, transpose);
+    launch_gs_pass(ctx->V, ctx->if_w, ctx->if_w, n, k, ctx->nchunk, ctx->part, ctx->hpass, ctx->hcol,
+                   0, st);
+    launch_gs_pass(ctx->V, ctx->if_w, ctx->if_w, n, k, ctx->nchunk, ctx->part, ctx->hpass, ctx->hcol,
+                   1, st);
+    launch_dot(ctx->if_w, ctx->if_w, n, ctx->part, 256, ctx->scal + 1, st);
+    launch_givens(ctx->hcol, ctx->scal + 1, k, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, beta,
+                  ctx->resid, ctx->scal + 2, st);
+    launch_scale_to(ctx->if_w, ctx->scal + 2, ctx->V + (int64_t)k * n, n, st);
+    if (k % check == 0 || k == maxit) {
+      CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      CK(cudaGetLastError());
+      for (int i = std::max(0, k - check); i < k; ++i)
+        if (hres[i] <= tol || hres[i] == 0.0) { kk = i + 1; break; }
+      if (kk > 0) break;
+    }
+  }
+  if (kk < 0) kk = maxit;
+  launch_trisolve(ctx->H, ctx->ldh, ctx->gv, kk, ctx->ysol, st);
+  launch_combine_basis(ctx->V, ctx->ysol, kk, n, x, st);
+  CK(cudaGetLastError());
+  *iters = kk;
+  *relres = hres[kk - 1];
+  if (hres[kk - 1] > tol && hres[kk - 1] != 0.0)
+    return fail(ctx, DDST_ERR_NOT_CONVERGED, "GMRES: relative residual %.3e after %d iterations",
+                hres[kk - 1], kk);
+  return DDST_OK;
+}
+
+// One application of the DD solve map (Alg. 2 + GMRES + reconstruction):
+// rhs volume vector r (FP64) -> volume correction e (FP64); traces written into ctx->if_u.
+template <typename T>
+ddst_status dd_apply(ddst_ctx* ctx, const double* r, double* e, int* iters, double* relres,
+                     double tol) {
+  cudaStream_t st = ctx->stream;
+  const int nslab = (int)ctx->slabs.size();
+  T* lb = (T*)ctx->loc_b;
+  // equivalent loads fhat_j = R_C A_j^{-1} r|Psi_j  (Sec. 2.2, Eq. (equilib1))
+  launch_gather<T>(ctx->d_slabs, nslab, r, lb, st);
+  for (auto& kv : ctx->cls)
+    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
+                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          ctx->if_fh, 0, 1, ctx->d_st, st);
+  CK(cudaGetLastError());
+  // interface solve (I - K) u_Gamma = fhat
+  ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 0, iters, relres);
+  if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+  // volume reconstruction: local Dirichlet solves with the traces on Gamma_{j-1}, Gamma_{j+1}
+  launch_add_iface_dirichlet<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, ctx->if_u, lb, st);
+  for (auto& kv : ctx->cls)
+    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
+                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          nullptr, 0, 0, ctx->d_st, st);
+  launch_scatter<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->loc_x, e, 0, st);
+  CK(cudaGetLastError());
+  return s;
+}
+
+double vec_norm(ddst_ctx* ctx, const double* x, int64_t n, int slot) {
+  launch_dot(x, x, n, ctx->part, 256, ctx->scal + slot, ctx->stream);
+  return std::sqrt(host_scalar(ctx, ctx->scal + slot));
+}
+
+template <typename T>
+ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* const* g,
+                       double* const* u, ddst_info* info) {
+  cudaStream_t st = ctx->stream;
+  ddst_status s = ensure_solve_buffers(ctx);
+  if (s != DDST_OK) return s;
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    if (!f[q] || !g[q] || !u[q]) return fail(ctx, DDST_ERR_INVALID_ARG, "NULL array for problem %d", q);
+    CK(stage_in(ctx->d_f + P.vol_off, f[q], P.nint, st));
+    CK(stage_in(ctx->d_g + P.node_off, g[q], P.nnode, st));
+  }
+  Timer tm(st);
+  const int64_t N = ctx->tot_vol;
+  launch_rhs(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_f, ctx->d_g, ctx->d_b, st);
+  CK(cudaMemsetAsync(ctx->d_u, 0, sizeof(double) * N, st));
+  const double bnorm = vec_norm(ctx, ctx->d_b, N, 3);
+  const double tol = ctx->opt.gmres_tol;
+  int total_it = 0, first_it = 0, nref = 0;
+  double est = 0.0, relres = 0.0;
+  ddst_status result = DDST_OK;
+  const int rmax = std::max(0, ctx->opt.refine_max);
+  for (int it = 0; it <= rmax; ++it) {
+    const double* rhs = ctx->d_b;
+    if (it > 0) {
+      launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
+                      nullptr, 512, st);
+      rhs = ctx->d_r;
+    }
+    int its = 0;
+    double rr = 0.0;
+    s = dd_apply<T>(ctx, rhs, ctx->d_e, &its, &rr, tol);
+    if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+    if (it == 0) first_it = its;
+    total_it += its;
+    ++nref;
+    launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
+    const double en = vec_norm(ctx, ctx->d_e, N, 4);
+    const double un = vec_norm(ctx, ctx->d_u, N, 5);
+    est = un > 0.0 ? en / un : 0.0;
+    if (rmax == 0 || est <= ctx->opt.refine_tol) break;
+    if (it == rmax) result = DDST_ERR_NOT_CONVERGED;
+  }
+  launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
+                  nullptr, 512, st);
+  relres = bnorm > 0.0 ? vec_norm(ctx, ctx->d_r, N, 6) / bnorm : 0.0;
+  const float ms = tm.stop();
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    CK(stage_out(u[q], ctx->d_u + P.vol_off, P.nint, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  ddst_status ds = check_status(ctx, info);
+  if (ds != DDST_OK) return ds;
+  ctx->have_solution = true;
+  if (info) {
+    info->gmres_iters = total_it;
+    info->gmres_iters_first = first_it;
+    info->refine_iters = nref;
+    info->rel_residual = relres;
+    info->est_rel_error = est;
+    info->t_factor = ctx->t_factor;
+    info->t_transfer = ctx->t_transfer;
+    info->t_compress = ctx->t_compress;
+    info->t_solve = ms;
+    info->bytes_factors = (int64_t)(3 * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
+    info->bytes_transfer = ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
+    info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+    info->fail_slab = -1;
+    info->fail_block = -1;
+  }
+  if (result != DDST_OK)
+    return fail(ctx, result, "refinement stopped at estimated relative error %.3e", est);
+  return DDST_OK;
+}
+
+
+// Transposed DD map e = M^T r, where M is the forward DD solve map (dd_apply):
+//   M = P A^{-1} G - P A^{-1} D (I - K)^{-1} R A^{-1} G
+//   M^T r = G^T A^{-T} (P^T r + R^T mu),  mu = -(I - K)^{-T} D^T A^{-T} P^T r
+// (G: slab gather, P: owned-plane scatter, R: central rows, D: Dirichlet data of the
+// neighbouring interfaces).  Transposed local solves run through the same factors.
+template <typename T>
+ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, double* relres,
+                       double tol) {
+  cudaStream_t st = ctx->stream;
+  const int nslab = (int)ctx->slabs.size();
+  T* lb = (T*)ctx->loc_b;
+  launch_gather_owned<T>(ctx->d_slabs, ctx->d_probs, nslab, r, lb, st);
+  for (auto& kv : ctx->cls)
+    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
+                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          nullptr, 1, 0, ctx->d_st, st);
+  CK(cudaMemsetAsync(ctx->if_fh, 0, sizeof(double) * ctx->tot_if, st));
+  launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, (T*)ctx->loc_x,
+                              ctx->if_fh, st);
+  CK(cudaGetLastError());
+  ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 1, iters, relres);
+  if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+  launch_inject_center<T>(ctx->d_slabs, nslab, ctx->if_u, lb, st);
+  for (auto& kv : ctx->cls)
+    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
+                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          nullptr, 1, 0, ctx->d_st, st);
+  CK(cudaMemsetAsync(e, 0, sizeof(double) * ctx->tot_vol, st));
+  launch_gather_T<T>(ctx->d_slabs, nslab, (T*)ctx->loc_x, e, st);
+  CK(cudaGetLastError());
+  return s;
+}
+
+template <typename T>
+ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double* const* dLdf,
+                               double* const* dLdg, double* const* dLda, ddst_info* info) {
+  cudaStream_t st = ctx->stream;
+  const int64_t N = ctx->tot_vol;
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    if (!dLdu[q]) return fail(ctx, DDST_ERR_INVALID_ARG, "dL/du is NULL for problem %d", q);
+    CK(stage_in(ctx->d_ga + P.vol_off, dLdu[q], P.nint, st));
+  }
+  Timer tm(st);
+  CK(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double) * N, st));
+  const double gnorm = vec_norm(ctx, ctx->d_ga, N, 3);
+  int total_it = 0, first_it = 0, nref = 0;
+  double est = 0.0;
+  ddst_status result = DDST_OK, s;
+  const int rmax = std::max(0, ctx->opt.refine_max);
+  for (int it = 0; it <= rmax; ++it) {
+    const double* rhs = ctx->d_ga;
+    if (it > 0) {
+      launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_ga, ctx->d_lam,
+                      ctx->d_r, 1, nullptr, 512, st);
+      rhs = ctx->d_r;
+    }
+    int its = 0;
+    double rr = 0.0;
+    s = dd_apply_T<T>(ctx, rhs, ctx->d_e, &its, &rr, ctx->opt.gmres_tol);
+    if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+    if (it == 0) first_it = its;
+    total_it += its;
+    ++nref;
+    launch_axpy(N, 1.0, ctx->d_e, ctx->d_lam, st);
+    const double en = vec_norm(ctx, ctx->d_e, N, 4);
+    const double ln = vec_norm(ctx, ctx->d_lam, N, 5);
+    est = ln > 0.0 ? en / ln : 0.0;
+    if (rmax == 0 || est <= ctx->opt.refine_tol) break;
+    if (it == rmax) result = DDST_ERR_NOT_CONVERGED;
+  }
+  launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_ga, ctx->d_lam, ctx->d_r, 1,
+                  nullptr, 512, st);
+  const double relres = gnorm > 0.0 ? vec_norm(ctx, ctx->d_r, N, 6) / gnorm : 0.0;
+  CK(cudaMemsetAsync(ctx->d_gn, 0, sizeof(double) * ctx->tot_nodes, st));
+  CK(cudaMemsetAsync(ctx->d_an, 0, sizeof(double) * ctx->tot_nodes, st));
+  launch_gradients(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_g, ctx->d_u, ctx->d_lam, ctx->d_gn,
+                   ctx->d_an, st);
+  CK(cudaGetLastError());
+  const float ms = tm.stop();
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    if (dLdf && dLdf[q]) CK(stage_out(dLdf[q], ctx->d_lam + P.vol_off, P.nint, st));
+    if (dLdg && dLdg[q]) CK(stage_out(dLdg[q], ctx->d_gn + P.node_off, P.nnode, st));
+    if (dLda && dLda[q]) CK(stage_out(dLda[q], ctx->d_an + P.node_off, P.nnode, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  ddst_status ds = check_status(ctx, info);
+  if (ds != DDST_OK) return ds;
+  if (info) {
+    info->gmres_iters = total_it;
+    info->gmres_iters_first = first_it;
+    info->refine_iters = nref;
+    info->rel_residual = relres;
+    info->est_rel_error = est;
+    info->t_solve = ms;
+    info->t_factor = ctx->t_factor;
+    info->t_transfer = ctx->t_transfer;
+    info->t_compress = ctx->t_compress;
+    info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+    info->fail_slab = info->fail_block = -1;
+  }
+  if (result != DDST_OK)
+    return fail(ctx, result, "adjoint refinement stopped at estimated relative error %.3e", est);
+  return DDST_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+void ddst_options_default(ddst_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = DDST_MIXED;
+  opt->gmres_tol = 1e-6;
+  opt->gmres_max_iter = 1000;
+  opt->refine_tol = 1e-9;
+  opt->refine_max = 8;
+  opt->k_max = 64;
+  opt->oversample = 10;
+  opt->leaf_size = 128;
+  opt->seed = 1234;
+  opt->check_every = 8;
+}
+
+ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
+                       const ddst_options* opt, void* stream, ddst_ctx** out) {
+  return setup_impl(1, grid, coeffs, &slab_width, opt, stream, out);
+}
+
+ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                             const int* slab_widths, const ddst_options* opt, void* stream,
+                             ddst_ctx** out) {
+  return setup_impl(nprob, grids, coeffs, slab_widths, opt, stream, out);
+}
+
+ddst_status ddst_build_transfer(ddst_ctx* ctx) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 1) return fail(ctx, DDST_ERR_STATE, "ddst_setup has not completed");
+  return ctx->prec == DDST_FP64 ? build_transfer_impl<double>(ctx) : build_transfer_impl<float>(ctx);
+}
+
+ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "ddst_build_transfer has not completed");
+  if (!(tol > 0.0)) {
+    ctx->hodlr.clear();
+    ctx->state = 2;
+    return DDST_OK;
+  }
+  Timer tm(ctx->stream);
+  HodlrParams hp{tol, ctx->opt.k_max, ctx->opt.oversample, ctx->opt.leaf_size, ctx->opt.seed};
+  std::string msg;
+  int rc = ctx->prec == DDST_FP64
+               ? hodlr_build<double>(ctx->hodlr, hp, ctx->slabs, ctx->probs, ctx->d_slabs,
+                                     (const double*)ctx->S, ctx->stream, msg)
+               : hodlr_build<float>(ctx->hodlr, hp, ctx->slabs, ctx->probs, ctx->d_slabs,
+                                    (const float*)ctx->S, ctx->stream, msg);
+  ctx->t_compress = tm.stop();
+  if (rc != 0) return fail(ctx, rc == 2 ? DDST_ERR_OOM : DDST_ERR_CUDA, "compress: %s", msg.c_str());
+  ctx->state = 3;
+  return DDST_OK;
+}
+
+ddst_status ddst_solve_batch(ddst_ctx* ctx, const double* const* f, const double* const* g,
+                             double* const* u, ddst_info* info) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  if (!f || !g || !u) return fail(ctx, DDST_ERR_INVALID_ARG, "NULL pointer array");
+  if (info) { memset(info, 0, sizeof(*info)); info->fail_slab = info->fail_block = -1; }
+  return ctx->prec == DDST_FP64 ? solve_impl<double>(ctx, f, g, u, info)
+                                : solve_impl<float>(ctx, f, g, u, info);
+}
+
+ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,
+                       ddst_info* info) {
+  if (ctx && ctx->nprob != 1) return fail(ctx, DDST_ERR_STATE, "batched context: use ddst_solve_batch");
+  return ddst_solve_batch(ctx, &f, &g, &u, info);
+}
+
+ddst_status ddst_solve_adjoint_batch(ddst_ctx* ctx, const double* const* dL_du,
+                                     double* const* dL_df, double* const* dL_dg,
+                                     double* const* dL_da, ddst_info* info) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->have_solution) return fail(ctx, DDST_ERR_STATE, "ddst_solve has not completed");
+  if (!dL_du) return fail(ctx, DDST_ERR_INVALID_ARG, "dL/du array is NULL");
+  if (info) { memset(info, 0, sizeof(*info)); info->fail_slab = info->fail_block = -1; }
+  return ctx->prec == DDST_FP64 ? solve_adjoint_impl<double>(ctx, dL_du, dL_df, dL_dg, dL_da, info)
+                                : solve_adjoint_impl<float>(ctx, dL_du, dL_df, dL_dg, dL_da, info);
+}
+
+ddst_status ddst_solve_adjoint(ddst_ctx* ctx, const double* dL_du, double* dL_df, double* dL_dg,
+                               double* dL_da, ddst_info* info) {
+  if (ctx && ctx->nprob != 1) return fail(ctx, DDST_ERR_STATE, "batched context: use ddst_solve_adjoint_batch");
+  return ddst_solve_adjoint_batch(ctx, &dL_du, &dL_df, &dL_dg, &dL_da, info);
+}
+
+ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->have_solution) return fail(ctx, DDST_ERR_STATE, "no solution yet");
+  if (prob < 0 || prob >= ctx->nprob || !uG) return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
+  const ProbDesc& P = ctx->probs[prob];
+  // traces of the final solution: read Gamma_j planes of u
+  std::vector<double> hu(P.nint);
+  CK(cudaMemcpyAsync(hu.data(), ctx->d_u + P.vol_off, sizeof(double) * P.nint,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> out((size_t)P.nds * P.ng);
+  const int64_t plane = P.ng;
+  for (int j = 1; j <= P.nds; ++j) {
+    const int i = j * P.w;
+    memcpy(&out[(size_t)(j - 1) * P.ng], &hu[(size_t)(i - 1) * plane], sizeof(double) * P.ng);
+  }
+  CK(cudaMemcpyAsync(uG, out.data(), sizeof(double) * out.size(),
+                     is_device_ptr(uG) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DDST_OK;
+}
+
+ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* out) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  if (prob < 0 || prob >= ctx->nprob || !out || (side != -1 && side != 1))
+    return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
+  const ProbDesc& P = ctx->probs[prob];
+  if (j < 1 || j > P.nds) return fail(ctx, DDST_ERR_INVALID_ARG, "slab index out of range");
+  const SlabDesc& s = ctx->slabs[P.slab0 + j - 1];
+  const int64_t off = side < 0 ? s.sp_off : s.sn_off;
+  if (off < 0) return fail(ctx, DDST_ERR_INVALID_ARG, "slab %d has no neighbour on that side", j);
+  const int64_t ng = P.ng;
+  std::vector<double> cm((size_t)(ng * ng));
+  if (ctx->state == 3) {
+    int rc = hodlr_expand(ctx->hodlr, P.slab0 + j - 1, side, ctx->esz, cm.data(), ctx->stream);
+    if (rc) return fail(ctx, DDST_ERR_CUDA, "expand failed");
+  } else if (ctx->esz == 8) {
+    CK(cudaMemcpyAsync(cm.data(), (double*)ctx->S + off, sizeof(double) * ng * ng,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  } else {
+    std::vector<float> tmp((size_t)(ng * ng));
+    CK(cudaMemcpyAsync(tmp.data(), (float*)ctx->S + off, sizeof(float) * ng * ng,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t e = 0; e < tmp.size(); ++e) cm[e] = tmp[e];
+  }
+  std::vector<double> rm((size_t)(ng * ng));
+  for (int64_t c = 0; c < ng; ++c)
+    for (int64_t r = 0; r < ng; ++r) rm[r * ng + c] = cm[c * ng + r];
+  CK(cudaMemcpyAsync(out, rm.data(), sizeof(double) * rm.size(),
+                     is_device_ptr(out) ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DDST_OK;
+}
+
+ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, double* y,
+                                 int transpose) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  if (prob < 0 || prob >= ctx->nprob || !x || !y) return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
+  ddst_status s = ensure_solve_buffers(ctx);
+  if (s != DDST_OK) return s;
+  const ProbDesc& P = ctx->probs[prob];
+  const int64_t len = (int64_t)P.nds * P.ng;
+  CK(cudaMemsetAsync(ctx->if_tmp, 0, sizeof(double) * ctx->tot_if, ctx->stream));
+  CK(stage_in(ctx->if_tmp + P.if_off, x, len, ctx->stream));
+  if (ctx->prec == DDST_FP64) apply_interface_T<double>(ctx, ctx->if_tmp, ctx->if_w, transpose != 0);
+  else apply_interface_T<float>(ctx, ctx->if_tmp, ctx->if_w, transpose != 0);
+  CK(cudaGetLastError());
+  CK(stage_out(y, ctx->if_w + P.if_off, len, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DDST_OK;
+}
+
+ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma, int* max_rank) {
+  if (!ctx || prob < 0 || prob >= ctx->nprob) return DDST_ERR_INVALID_ARG;
+  const ProbDesc& P = ctx->probs[prob];
+  if (n_ds) *n_ds = P.nds;
+  if (n_gamma) *n_gamma = P.ng;
+  if (max_rank) *max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+  return DDST_OK;
+}
+
+const char* ddst_last_error(const ddst_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_error.c_str();
+}
+
+void ddst_destroy(ddst_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  ctx->hodlr.release();
+  for (void* p : ctx->owned) cudaFree(p);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// hodlr.cuh -- weak-admissibility hierarchical (HODLR) form of the transfer operators.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ddst {
+
+struct HodlrParams {
+  double tol;      // relative truncation tolerance (w.r.t. ||S_{j,j'}||_2)
+  int k_max;       // rank cap
+  int oversample;  // extra samples
+  int leaf;        // leaf size
+  uint64_t seed;   // sketch seed
+};
+
+// One low-rank off-diagonal block (device offsets in elements of the working precision).
+struct HBlock {
+  int sblk;        // S block id: 2 * slab + (side > 0)
+  int level;
+  int64_t row0, nrows, col0, ncols;
+  int rank;
+  int64_t u_off;   // U: nrows x rank, column-major
+  int64_t v_off;   // V: ncols x rank, column-major (block ~ U V^T)
+  int64_t t_off;   // scratch offset for V^T x
+  int64_t in_if, out_if;  // interface offsets of source / target vectors
+};
+
+struct HLeaf {
+  int sblk;
+  int64_t lo, len;
+  int64_t d_off;   // dense leaf, column-major len x len
+  int64_t in_if, out_if;
+};
+
+struct HodlrSet {
+  bool built = false;
+  size_t esz = 4;
+  void* UV = nullptr;      // factors
+  void* D = nullptr;       // dense leaves
+  double* t = nullptr;     // V^T x scratch (FP64)
+  double* acc = nullptr;   // output accumulator (FP64)
+  HBlock* d_blocks = nullptr;
+  HLeaf* d_leaves = nullptr;
+  std::vector<HBlock> blocks;
+  std::vector<HLeaf> leaves;
+  int64_t t_len = 0, acc_len = 0;
+  int64_t bytes = 0;
+  int max_rank = 0;
+  std::vector<int> sblk_L;  // tree depth per S block
+  void clear();
+  void release();
+};
+
+// Compresses every dense S block; returns 0 on success, 1 on CUDA error, 2 on OOM.
+template <typename T>
+int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>& slabs,
+                const std::vector<ProbDesc>& probs, const SlabDesc* d_slabs, const T* S,
+                cudaStream_t st, std::string& msg);
+
+// y = (I - K) x (transpose = 0) or (I - K)^T x with the HODLR blocks.
+template <typename T>
+void hodlr_apply(HodlrSet& H, const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                 const double* x, double* y, int transpose, cudaStream_t st);
+
+// Dense column-major expansion of S block (slab, side) into host memory `out` (ng*ng doubles).
+int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaStream_t st);
+
+}  // namespace ddst

@@ -1,0 +1,97 @@
+// kernels.cuh -- host-side launchers of the device kernels (all stream-ordered, no sync).
+#pragma once
+#include "common.cuh"
+
+namespace ddst {
+
+// One CTA of the multi-right-hand-side sweep that forms S explicitly (sweep.cu).
+struct TileDesc {
+  int slab;    // global slab index
+  int q0;      // first central source point of the tile
+  int nq;      // number of sources in the tile (<= tile width)
+  int dir;     // 0 = upward sweep (blocks kstart..1), 1 = downward (kstart..nb)
+  int kstart;  // first block of the sweep
+  int len;     // number of blocks visited
+};
+
+// stencil.cu
+template <typename T>
+void launch_stencil_pack(const SlabDesc* d_slabs, int nslab, int max_nb, const ProbDesc* d_probs,
+                         const double* a, const double* c, T* pack, cudaStream_t st);
+void launch_rhs(const ProbDesc* d_probs, int nprob, const double* a, const double* f,
+                const double* g, double* b, cudaStream_t st);
+void launch_residual(const ProbDesc* d_probs, int nprob, const double* a, const double* c,
+                     const double* b, const double* u, double* r, int transpose, double* part,
+                     int nblk, cudaStream_t st);
+template <typename T>
+void launch_gather(const SlabDesc* d_slabs, int nslab, const double* vol, T* loc, cudaStream_t st);
+template <typename T>
+void launch_gather_owned(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                         const double* vol, T* loc, cudaStream_t st);
+template <typename T>
+void launch_gather_T(const SlabDesc* d_slabs, int nslab, const T* loc, double* vol,
+                     cudaStream_t st);
+template <typename T>
+void launch_scatter(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab, const T* loc,
+                    double* vol, int mode, cudaStream_t st);
+template <typename T>
+void launch_extract_center(const SlabDesc* d_slabs, int nslab, const T* loc, double* iface,
+                           cudaStream_t st);
+template <typename T>
+void launch_inject_center(const SlabDesc* d_slabs, int nslab, const double* iface, T* loc,
+                          cudaStream_t st);
+template <typename T>
+void launch_add_iface_dirichlet(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                                const T* pack, const double* uG, T* loc, cudaStream_t st);
+template <typename T>
+void launch_iface_dirichlet_T(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                              const T* pack, const T* loc, double* out, cudaStream_t st);
+void launch_dot(const double* x, const double* y, int64_t n, double* part, int nblk, double* out,
+                cudaStream_t st);
+void launch_sum_partials(const double* part, int np, double* out, cudaStream_t st);
+void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
+
+// factor.cu: forward/backward pivot inverses F, B and diagonal inverse blocks G (one size class)
+template <typename T>
+void launch_factor(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                   const T* pack, T* F, T* B, T* G, DevStatus* st, cudaStream_t s);
+
+// sweep.cu: explicit transfer operators
+template <typename T>
+int sbuild_tile_cols(int M);
+template <typename T>
+void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
+                   const T* F, const T* B, const T* G, const T* pack, T* S, DevStatus* st,
+                   cudaStream_t s);
+
+// solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)
+template <typename T>
+void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                        const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
+                        T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
+                        cudaStream_t s);
+
+// krylov.cu
+template <typename T>
+void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                        int64_t max_ng, const T* S, const double* x, double* y, int transpose,
+                        cudaStream_t st);
+void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k, int nchunk,
+                    double* part, double* hpass, double* hcol, int accumulate, cudaStream_t st);
+void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,
+                          cudaStream_t st);
+void launch_givens(const double* hcol, const double* hn2, int k, double* H, int ldh, double* cs,
+                   double* sn, double* gv, double beta, double* resid, double* inv_hn,
+                   cudaStream_t st);
+void launch_scale_to(const double* w, const double* s, double* out, int64_t n, cudaStream_t st);
+void launch_normalize_start(const double* x, const double* nrm2, double* out, int64_t n,
+                            cudaStream_t st);
+void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double* y,
+                     cudaStream_t st);
+
+// grad.cu: dL/dg and dL/da from lambda and u (nodal outputs accumulated; zero them first)
+void launch_gradients(const ProbDesc* d_probs, int nprob, const double* a, const double* g,
+                      const double* u, const double* lam, double* dLdg, double* dLda,
+                      cudaStream_t st);
+
+}  // namespace ddst

@@ -1,0 +1,289 @@
+// krylov.cu -- interface operator application and the GMRES building blocks.
+//
+// The equilibrium system (I - K) u = fhat (Sec. 1, Eq. (modelS); Sec. 2.2, Eq. (equilib2)):
+// block row j reads  u_j - S_{j,j-1} u_{j-1} - S_{j,j+1} u_{j+1}.  It is solved by unrestarted
+// GMRES (Sec. 5): Arnoldi with classical Gram-Schmidt applied twice, Givens rotations, x0 = 0.
+// Krylov vectors are FP64; the operator's blocks are stored in the working precision T and
+// multiplied in T with FP64 accumulation every 32 terms.
+#include "kernels.cuh"
+
+namespace ddst {
+
+// y_j = x_j - S_{j,j-1} x_{j-1} - S_{j,j+1} x_{j+1}; S column-major.  grid = (row tiles of 128,
+// slabs); 256 threads = 128 rows x 2 interleaved halves of the sources.
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict__ slabs,
+                                                     const ProbDesc* __restrict__ probs,
+                                                     const T* __restrict__ S,
+                                                     const double* __restrict__ x,
+                                                     double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SlabDesc s = slabs[blockIdx.y];
+  const ProbDesc P = probs[s.prob];
+  const int64_t ng = s.ng;
+  if ((int64_t)blockIdx.x * 128 >= ng) return;
+  T* xp = reinterpret_cast<T*>(smem_raw);
+  T* xn = xp + ng;
+  __shared__ double red[256];
+  const bool hp = s.j >= 2, hn = s.j <= P.nds - 1;
+  for (int64_t e = threadIdx.x; e < ng; e += blockDim.x) {
+    xp[e] = hp ? static_cast<T>(x[s.if_off - ng + e]) : T(0);
+    xn[e] = hn ? static_cast<T>(x[s.if_off + ng + e]) : T(0);
+  }
+  __syncthreads();
+  const int64_t row = (int64_t)blockIdx.x * 128 + (threadIdx.x & 127);
+  const int half = threadIdx.x >> 7;
+  double acc = 0.0;
+  if (row < ng) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int64_t off = side == 0 ? s.sp_off : s.sn_off;
+      if (off < 0) continue;
+      const T* col = S + off + row;
+      const T* xs = side == 0 ? xp : xn;
+      int64_t src = half;
+      while (src < ng) {
+        T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+        const int64_t stop = min(ng, src + 64);
+        for (; src + 6 < stop; src += 8) {
+          p0 = fma(col[src * ng], xs[src], p0);
+          p1 = fma(col[(src + 2) * ng], xs[src + 2], p1);
+          p2 = fma(col[(src + 4) * ng], xs[src + 4], p2);
+          p3 = fma(col[(src + 6) * ng], xs[src + 6], p3);
+        }
+        for (; src < stop; src += 2) p0 = fma(col[src * ng], xs[src], p0);
+        acc += static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
+               static_cast<double>(p3);
+      }
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (half == 0 && row < ng)
+    y[s.if_off + row] = x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
+}
+
+// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1}: warp per output point, lanes over
+// the (contiguous) rows of the column-major blocks.  grid = (ceil(ng/8), slabs), 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
+                                                       const ProbDesc* __restrict__ probs,
+                                                       const T* __restrict__ S,
+                                                       const double* __restrict__ x,
+                                                       double* __restrict__ y) {
+  const int sidx = blockIdx.y;
+  const SlabDesc s = slabs[sidx];
+  const ProbDesc P = probs[s.prob];
+  const int64_t ng = s.ng;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t src = (int64_t)blockIdx.x * 8 + warp;
+  if (src >= ng) return;
+  double acc = 0.0;
+  if (s.j <= P.nds - 1) {  // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}
+    const SlabDesc t = slabs[sidx + 1];
+    const T* col = S + t.sp_off + src * ng;
+    const double* xv = x + t.if_off;
+    T part = T(0);
+    int cnt = 0;
+    for (int64_t r = lane; r < ng; r += 32) {
+      part = fma(col[r], static_cast<T>(xv[r]), part);
+      if (++cnt == 32) { acc += static_cast<double>(part); part = T(0); cnt = 0; }
+    }
+    acc += static_cast<double>(part);
+  }
+  if (s.j >= 2) {
+    const SlabDesc t = slabs[sidx - 1];
+    const T* col = S + t.sn_off + src * ng;
+    const double* xv = x + t.if_off;
+    T part = T(0);
+    int cnt = 0;
+    for (int64_t r = lane; r < ng; r += 32) {
+      part = fma(col[r], static_cast<T>(xv[r]), part);
+      if (++cnt == 32) { acc += static_cast<double>(part); part = T(0); cnt = 0; }
+    }
+    acc += static_cast<double>(part);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) y[s.if_off + src] = x[s.if_off + src] - acc;
+}
+
+// ---- Arnoldi pieces ------------------------------------------------------------------------
+// part[i * nchunk + chunk] = sum over chunk of V[i] . w      grid = (nchunk, k)
+__global__ void k_gs_dots(const double* __restrict__ V, const double* __restrict__ w, int64_t n,
+                          int64_t chunk, double* __restrict__ part) {
+  const int i = blockIdx.y;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  const double* v = V + (int64_t)i * n;
+  double acc = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += v[e] * w[e];
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// hpass[i] = sum_c part[i][c]; hcol[i] = (accumulate ? hcol[i] : 0) + hpass[i].  warp per i.
+__global__ void k_gs_reduce(const double* __restrict__ part, int nchunk, int k,
+                            double* __restrict__ hpass, double* __restrict__ hcol, int accumulate) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= k) return;
+  double acc = 0.0;
+  for (int c = lane; c < nchunk; c += 32) acc += part[(int64_t)i * nchunk + c];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    hpass[i] = acc;
+    hcol[i] = (accumulate ? hcol[i] : 0.0) + acc;
+  }
+}
+
+// w -= sum_{i<k} h[i] V[i]   (or x = sum_{i<k} h[i] V[i] when assign = 1)
+__global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w,
+                            const double* __restrict__ h, int k, int64_t n, int assign) {
+  extern __shared__ double sh[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = h[i];
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    int i = 0;
+    for (; i + 3 < k; i += 4) {
+      acc += sh[i] * V[(int64_t)i * n + e] + sh[i + 1] * V[(int64_t)(i + 1) * n + e] +
+             sh[i + 2] * V[(int64_t)(i + 2) * n + e] + sh[i + 3] * V[(int64_t)(i + 3) * n + e];
+    }
+    for (; i < k; ++i) acc += sh[i] * V[(int64_t)i * n + e];
+    w[e] = assign ? acc : w[e] - acc;
+  }
+}
+
+// Givens step for column j = k-1 (k basis vectors).  Single thread.
+// H: column-major upper triangle (ld = ldh); gv: rotated rhs; resid[j] = |g_{j+1}| / beta.
+__global__ void k_givens(const double* __restrict__ hcol, const double* __restrict__ hn2, int k,
+                         double* __restrict__ H, int ldh, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ gv, double beta,
+                         double* __restrict__ resid, double* __restrict__ inv_hn) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = k - 1;
+  double* col = H + (int64_t)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+  double sub = sqrt(fmax(hn2[0], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double a = col[j], b = sub;
+  const double den = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (den > 0.0) { c = a / den; s = b / den; }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = den;
+  gv[j + 1] = -s * gv[j];
+  gv[j] = c * gv[j];
+  resid[j] = fabs(gv[j + 1]) / beta;
+  inv_hn[0] = sub > 0.0 ? 1.0 / sub : 0.0;
+}
+
+// V[k] = w * inv_hn
+__global__ void k_scale_to(const double* __restrict__ w, const double* __restrict__ s,
+                           double* __restrict__ out, int64_t n) {
+  const double a = s[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a * w[e];
+}
+
+// out = x / sqrt(nrm2[0]) and gv[0] = sqrt(nrm2[0])  (start of Arnoldi)
+__global__ void k_normalize_start(const double* __restrict__ x, const double* __restrict__ nrm2,
+                                  double* __restrict__ out, int64_t n) {
+  const double nr = sqrt(nrm2[0]);
+  const double a = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a * x[e];
+}
+
+// Back substitution R y = g (R column-major upper triangle, kk x kk).  One CTA.
+__global__ void k_trisolve(const double* __restrict__ H, int ldh, const double* __restrict__ gv,
+                           int kk, double* __restrict__ y) {
+  extern __shared__ double rhs[];
+  for (int i = threadIdx.x; i < kk; i += blockDim.x) rhs[i] = gv[i];
+  __syncthreads();
+  for (int i = kk - 1; i >= 0; --i) {
+    const double* col = H + (int64_t)i * ldh;
+    const double yi = rhs[i] / col[i];
+    __syncthreads();
+    for (int l = threadIdx.x; l < i; l += blockDim.x) rhs[l] -= col[l] * yi;
+    if (threadIdx.x == 0) y[i] = yi;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T>
+void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
+                        int64_t max_ng, const T* S, const double* x, double* y, int transpose,
+                        cudaStream_t st) {
+  if (!transpose) {
+    const size_t smem = 2 * max_ng * sizeof(T);
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+      cudaFuncSetAttribute(k_apply_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = smem;
+    }
+    k_apply_dense<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smem, st>>>(
+        d_slabs, d_probs, S, x, y);
+  } else {
+    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 7) / 8), nslab), 256, 0, st>>>(d_slabs, d_probs,
+                                                                                  S, x, y);
+  }
+}
+
+template void launch_apply_dense<float>(const SlabDesc*, const ProbDesc*, int, int64_t,
+                                        const float*, const double*, double*, int, cudaStream_t);
+template void launch_apply_dense<double>(const SlabDesc*, const ProbDesc*, int, int64_t,
+                                         const double*, const double*, double*, int,
+                                         cudaStream_t);
+
+void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k,
+                    int nchunk, double* part, double* hpass, double* hcol, int accumulate,
+                    cudaStream_t st) {
+  const int64_t chunk = (n + nchunk - 1) / nchunk;
+  k_gs_dots<<<dim3(nchunk, k), 256, 0, st>>>(V, w_in, n, chunk, part);
+  k_gs_reduce<<<(k + 7) / 8, 256, 0, st>>>(part, nchunk, k, hpass, hcol, accumulate);
+  k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, w, hpass, k, n, 0);
+}
+
+void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,
+                          cudaStream_t st) {
+  k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, x, y, k, n, 1);
+}
+
+void launch_givens(const double* hcol, const double* hn2, int k, double* H, int ldh, double* cs,
+                   double* sn, double* gv, double beta, double* resid, double* inv_hn,
+                   cudaStream_t st) {
+  k_givens<<<1, 32, 0, st>>>(hcol, hn2, k, H, ldh, cs, sn, gv, beta, resid, inv_hn);
+}
+
+void launch_scale_to(const double* w, const double* s, double* out, int64_t n, cudaStream_t st) {
+  k_scale_to<<<1024, 256, 0, st>>>(w, s, out, n);
+}
+
+void launch_normalize_start(const double* x, const double* nrm2, double* out, int64_t n,
+                            cudaStream_t st) {
+  k_normalize_start<<<1024, 256, 0, st>>>(x, nrm2, out, n);
+}
+
+void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double* y,
+                     cudaStream_t st) {
+  k_trisolve<<<1, 256, kk * sizeof(double), st>>>(H, ldh, gv, kk, y);
+}
+
+}  // namespace ddst

@@ -1,0 +1,210 @@
+// solve.cu -- single-right-hand-side local solves with the two-sided factorization.
+//
+// Local Dirichlet solves on every double slab are needed for the equivalent loads
+// fhat_j = R_{C_j} A_j^{-1} b (Sec. 2.2, Eq. (equilib1)), for the volume reconstruction from
+// interface traces, and (transposed) for the adjoint.  With forward pivots Sigma_k (inverse F_k),
+// backward pivots Lambda_k (inverse B_k) and G_k = (Sigma_k + Lambda_k - D_k)^{-1}:
+//   top-down   bf_1 = b_1,   bf_k = b_k - L_k F_{k-1} bf_{k-1}
+//   bottom-up  bb_nb = b_nb, bb_k = b_k - U_k B_{k+1} bb_{k+1}
+//   x_k = G_k (bf_k + bb_k - b_k)                       (all k in parallel)
+// For A^T the couplings swap (L_k^T = U_{k-1}-position, diagonal) and every block is transposed:
+//   bf_k = b_k - diag(ups_{k-1}) F_{k-1}^T bf_{k-1},  bb_k = b_k - diag(ell_{k+1}) B_{k+1}^T bb_{k+1},
+//   x_k = G_k^T (bf_k + bb_k - b_k).
+// The two sweeps of a slab run concurrently in two CTAs; each streams its factor blocks
+// through a ring of bulk (TMA) copies.
+#include "kernels.cuh"
+
+namespace ddst {
+
+template <typename T, int M, int NST>
+__global__ void __launch_bounds__(128) k_solve_sweep(const SlabDesc* __restrict__ slabs,
+                                                     const int* __restrict__ ids,
+                                                     const T* __restrict__ F,
+                                                     const T* __restrict__ B,
+                                                     const T* __restrict__ pack,
+                                                     const T* __restrict__ b, T* __restrict__ bf,
+                                                     T* __restrict__ bb, int transpose,
+                                                     DevStatus* st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);   // [NST][M*M]
+  T* sv = sF + NST * M * M;                 // [M] current vector
+  T* sy = sv + M;                           // [M] row results of the warp-per-row product
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sy + M);
+  __shared__ int s_abort;
+  const int sid = ids[blockIdx.x];
+  const SlabDesc s = slabs[sid];
+  const bool down = blockIdx.y == 0;  // top-down sweep uses F, bottom-up uses B
+  const T* Fac = (down ? F : B) + s.fac_off;
+  T* out = (down ? bf : bb) + s.loc_off;
+  const T* rhs = b + s.loc_off;
+  const int nb = s.nb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // coupling field: non-transposed top-down uses ell_k (SOUTH of block k), bottom-up ups_k
+  // (NORTH of block k); transposed top-down ups_{k-1} (NORTH of k-1), bottom-up ell_{k+1}.
+  int issued = 0, consumed = 0;
+  auto blk_of = [&](int step) { return down ? step + 1 : nb - step; };
+  auto issue = [&](int step) {  // step >= 1 needs factor block of the previous block
+    ++issued;
+    const int k = blk_of(step);
+    const int fidx = down ? k - 2 : k;  // F_{k-1} or B_{k+1}
+    const int stage = (step - 1) % NST;
+    mbar_arrive_expect_tx(&bar[stage], M * M * sizeof(T));
+    bulk_g2s(sF + stage * M * M, Fac + (int64_t)fidx * M * M, M * M * sizeof(T), &bar[stage]);
+  };
+  if (tid == 0) {
+    s_abort = 0;
+    for (int q = 0; q < NST; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int q = 1; q <= NST && q < nb; ++q) issue(q);
+  // step 0: bf_1 = b_1 (or bb_nb = b_nb)
+  {
+    const int k = blk_of(0);
+    for (int c = tid; c < M; c += blockDim.x) {
+      const T v = rhs[(int64_t)(k - 1) * M + c];
+      sv[c] = v;
+      out[(int64_t)(k - 1) * M + c] = v;
+    }
+  }
+  __syncthreads();
+  for (int step = 1; step < nb; ++step) {
+    const int k = blk_of(step);
+    const int stage = (step - 1) % NST;
+    if (!mbar_wait(&bar[stage], ((step - 1) / NST) & 1, st, sid, k)) s_abort = 1;
+    consumed = step;
+    const T* A = sF + stage * M * M;
+    int cfield, cblk;
+    if (!transpose) { cfield = down ? PK_SOUTH : PK_NORTH; cblk = k; }
+    else { cfield = down ? PK_NORTH : PK_SOUTH; cblk = down ? k - 1 : k + 1; }
+    const T* cpl = pack + s.pack_off + (int64_t)(cblk - 1) * PK_NFIELDS * M + cfield * M;
+    T y = T(0);
+    int row = -1;
+    if (!transpose) {
+      // y = A v, warp per row, lanes over columns
+      for (int r = warp; r < M; r += 4) {
+        T part = T(0);
+        for (int c = lane; c < M; c += 32) part += A[r * M + c] * sv[c];
+        part = warp_sum(part);
+        if (lane == 0) sy[r] = part;
+      }
+      __syncthreads();
+      if (tid < M) { y = sy[tid]; row = tid; }
+    } else {
+      // y = A^T v, thread per output row: y[r] = sum_c A[c][r] v[c]
+      if (tid < M) {
+        T acc = T(0);
+        for (int c = 0; c < M; ++c) acc += A[c * M + tid] * sv[c];
+        y = acc;
+        row = tid;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (row >= 0) {
+      const T v = rhs[(int64_t)(k - 1) * M + row] - cpl[row] * y;
+      sv[row] = v;
+      out[(int64_t)(k - 1) * M + row] = v;
+    }
+    __syncthreads();
+    if (tid == 0 && step + NST < nb) {
+      fence_proxy_async();
+      issue(step + NST);
+    }
+  }
+  if (tid == 0)
+    for (int q = consumed + 1; q <= issued; ++q)
+      mbar_wait(&bar[(q - 1) % NST], ((q - 1) / NST) & 1, st, sid, -1);
+}
+
+// x_k = G_k (bf_k + bb_k - b_k)  (or G_k^T (...)).  grid = (nb, nslab-of-class).
+// mode 0: full block written to x (slab-local); mode 1: only the central rows, written as FP64
+// into the interface vector iface at the slab's offset.
+template <typename T, int M>
+__global__ void __launch_bounds__(128) k_solve_combine(const SlabDesc* __restrict__ slabs,
+                                                       const int* __restrict__ ids,
+                                                       const T* __restrict__ G,
+                                                       const T* __restrict__ b,
+                                                       const T* __restrict__ bf,
+                                                       const T* __restrict__ bb,
+                                                       T* __restrict__ x, double* __restrict__ iface,
+                                                       int transpose, int mode) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  const int k = blockIdx.x + 1;
+  if (k > s.nb) return;
+  __shared__ T sv[M];
+  const int64_t o = s.loc_off + (int64_t)(k - 1) * M;
+  for (int c = threadIdx.x; c < M; c += blockDim.x) sv[c] = bf[o + c] + bb[o + c] - b[o + c];
+  __syncthreads();
+  const T* Gk = G + s.fac_off + (int64_t)(k - 1) * M * M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (mode == 0) {
+    if (!transpose) {
+      for (int r = warp; r < M; r += 4) {
+        T part = T(0);
+        for (int c = lane; c < M; c += 32) part += Gk[r * M + c] * sv[c];
+        part = warp_sum(part);
+        if (lane == 0) x[o + r] = part;
+      }
+    } else {
+      for (int r = threadIdx.x; r < M; r += blockDim.x) {
+        T acc = T(0);
+        for (int c = 0; c < M; ++c) acc += Gk[c * M + r] * sv[c];
+        x[o + r] = acc;
+      }
+    }
+  } else {
+    // central rows C_t = (w-1)p + t, t = 0..p-1 (non-transposed only)
+    for (int t = warp; t < s.p; t += 4) {
+      const int r = (s.w - 1) * s.p + t;
+      T part = T(0);
+      for (int c = lane; c < M; c += 32) part += Gk[r * M + c] * sv[c];
+      part = warp_sum(part);
+      if (lane == 0) iface[s.if_off + (int64_t)(k - 1) * s.p + t] = static_cast<double>(part);
+    }
+  }
+}
+
+template <typename T, int M, int NST>
+static void run_solve(const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                      const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
+                      T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
+                      cudaStream_t s) {
+  const size_t smem = (size_t)NST * M * M * sizeof(T) + 2 * M * sizeof(T) + NST * 8;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_solve_sweep<T, M, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  k_solve_sweep<T, M, NST><<<dim3(nids, 2), 128, smem, s>>>(d_slabs, d_ids, F, B, pack, b, bf, bb,
+                                                           transpose, st);
+  k_solve_combine<T, M><<<dim3(max_nb, nids), 128, 0, s>>>(d_slabs, d_ids, G, b, bf, bb, x, iface,
+                                                          transpose, mode);
+}
+
+template <typename T>
+void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                        const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
+                        T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
+                        cudaStream_t s) {
+  if (nids == 0) return;
+  switch (M) {
+    case 32: run_solve<T, 32, 4>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    case 64: run_solve<T, 64, 4>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    case 128: run_solve<T, 128, (sizeof(T) == 4 ? 3 : 1)>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    default: break;
+  }
+}
+
+template void launch_local_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
+                                        const float*, const float*, const float*, const float*,
+                                        float*, float*, float*, double*, int, int, DevStatus*,
+                                        cudaStream_t);
+template void launch_local_solve<double>(int, const SlabDesc*, const int*, int, int,
+                                         const double*, const double*, const double*,
+                                         const double*, const double*, double*, double*, double*,
+                                         double*, int, int, DevStatus*, cudaStream_t);
+
+}  // namespace ddst

@@ -1,0 +1,267 @@
+"""Python binding of the C ABI (same names; argument marshalling only).
+
+Arrays may be CUDA ``torch`` tensors (device pointers) or contiguous NumPy / CPU tensors
+(host pointers, staged by the library).  All arithmetic runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
+           "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
+           "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
+           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_last_error",
+           "ddst_destroy", "Solver", "DDSTSolve"]
+
+
+class DDSTError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.name = L.STATUS_NAMES.get(status, str(status))
+
+
+def _ptr(x):
+    """Address of a contiguous FP64 array (torch tensor on any device, or NumPy array)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("arrays must be contiguous float64")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float64")
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _check(lib, ctx, st):
+    if st != L.DDST_OK:
+        msg = lib.ddst_last_error(ctx)
+        raise DDSTError(st, msg.decode() if msg else "")
+
+
+def ddst_options_default(**overrides):
+    lib = L.load()
+    o = L.ddst_options()
+    lib.ddst_options_default(C.byref(o))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = L.DDST_FP64 if v.lower() == "fp64" else L.DDST_MIXED
+        setattr(o, k, v)
+    return o
+
+
+def _coeffs(a, b=(0.0, 0.0, 0.0), c=None):
+    cf = L.ddst_coeffs()
+    cf.a = _ptr(a)
+    bb = list(b) + [0.0] * (3 - len(b))
+    cf.b = (C.c_double * 3)(*bb[:3])
+    cf.c = _ptr(c)
+    return cf
+
+
+def ddst_setup(dim, n, a, slab_width, b=(0.0, 0.0, 0.0), c=None, options=None, stream=None):
+    """Returns an opaque context handle (c_void_p)."""
+    lib = L.load()
+    g = L.ddst_grid(dim, n)
+    cf = _coeffs(a, b, c)
+    out = C.c_void_p()
+    st = lib.ddst_setup(C.byref(g), C.byref(cf), int(slab_width),
+                        C.byref(options) if options is not None else None,
+                        C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(lib, None, st)
+    return out
+
+
+def ddst_setup_batch(problems, options=None, stream=None):
+    """``problems``: list of dicts with ``dim, n, w, a`` and optional ``b, c``."""
+    lib = L.load()
+    k = len(problems)
+    grids = (L.ddst_grid * k)(*[L.ddst_grid(p["dim"], p["n"]) for p in problems])
+    coeffs = (L.ddst_coeffs * k)(*[_coeffs(p["a"], p.get("b") or (0.0,) * 3, p.get("c"))
+                                   for p in problems])
+    widths = (C.c_int * k)(*[int(p["w"]) for p in problems])
+    out = C.c_void_p()
+    st = lib.ddst_setup_batch(k, grids, coeffs, widths,
+                              C.byref(options) if options is not None else None,
+                              C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(lib, None, st)
+    return out
+
+
+def ddst_build_transfer(ctx):
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_build_transfer(ctx))
+
+
+def ddst_compress(ctx, tol):
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_compress(ctx, float(tol)))
+
+
+def ddst_solve(ctx, f, g, u, raise_on_error=True):
+    lib = L.load()
+    info = L.ddst_info()
+    st = lib.ddst_solve(ctx, _ptr(f), _ptr(g), _ptr(u), C.byref(info))
+    if raise_on_error:
+        _check(lib, ctx, st)
+    return st, info.as_dict()
+
+
+def _parr(xs):
+    return (C.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+
+
+def ddst_solve_batch(ctx, fs, gs, us, raise_on_error=True):
+    lib = L.load()
+    info = L.ddst_info()
+    st = lib.ddst_solve_batch(ctx, _parr(fs), _parr(gs), _parr(us), C.byref(info))
+    if raise_on_error:
+        _check(lib, ctx, st)
+    return st, info.as_dict()
+
+
+def ddst_solve_adjoint(ctx, dLdu, dLdf=None, dLdg=None, dLda=None, raise_on_error=True):
+    lib = L.load()
+    info = L.ddst_info()
+    st = lib.ddst_solve_adjoint(ctx, _ptr(dLdu), _ptr(dLdf), _ptr(dLdg), _ptr(dLda), C.byref(info))
+    if raise_on_error:
+        _check(lib, ctx, st)
+    return st, info.as_dict()
+
+
+def ddst_solve_adjoint_batch(ctx, dLdus, dLdfs, dLdgs, dLdas, raise_on_error=True):
+    lib = L.load()
+    info = L.ddst_info()
+    st = lib.ddst_solve_adjoint_batch(ctx, _parr(dLdus), _parr(dLdfs), _parr(dLdgs),
+                                      _parr(dLdas), C.byref(info))
+    if raise_on_error:
+        _check(lib, ctx, st)
+    return st, info.as_dict()
+
+
+def ddst_interface_trace(ctx, prob, out):
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_interface_trace(ctx, prob, _ptr(out)))
+
+
+def ddst_get_transfer(ctx, prob, j, side, out):
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_get_transfer(ctx, prob, j, side, _ptr(out)))
+
+
+def ddst_apply_interface(ctx, prob, x, y, transpose=False):
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_apply_interface(ctx, prob, _ptr(x), _ptr(y), int(bool(transpose))))
+
+
+def ddst_query(ctx, prob=0):
+    lib = L.load()
+    nds, ng, mr = C.c_int(), C.c_int64(), C.c_int()
+    _check(lib, ctx, lib.ddst_query(ctx, prob, C.byref(nds), C.byref(ng), C.byref(mr)))
+    return nds.value, ng.value, mr.value
+
+
+def ddst_last_error(ctx=None):
+    lib = L.load()
+    m = lib.ddst_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ddst_destroy(ctx):
+    if ctx:
+        L.load().ddst_destroy(ctx)
+
+
+class Solver:
+    """Owning wrapper: setup (factor) -> build_transfer -> [compress] -> solve / solve_adjoint."""
+
+    def __init__(self, problems, precision="mixed", stream=None, **opts):
+        if isinstance(problems, dict):
+            problems = [problems]
+        self.problems = problems
+        self.options = ddst_options_default(precision=precision, **opts)
+        self._keep = problems  # keep host arrays alive during setup
+        self.ctx = ddst_setup_batch(problems, self.options, stream)
+
+    def build_transfer(self):
+        ddst_build_transfer(self.ctx)
+        return self
+
+    def compress(self, tol):
+        ddst_compress(self.ctx, tol)
+        return self
+
+    def solve(self, f, g, u, **kw):
+        return ddst_solve(self.ctx, f, g, u, **kw)
+
+    def close(self):
+        if self.ctx:
+            ddst_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_autograd():
+    import torch
+
+    class DDSTSolve(torch.autograd.Function):
+        """``u = A(a)^{-1} b(f, g)`` on the GPU; backward is the hand-written discrete adjoint.
+
+        forward(a, f, g, spec) with ``spec = dict(dim, n, w, b=(..), c=None, precision=..,
+        compress_tol=None)``; the local factors are recomputed for every forward call.
+        """
+
+        @staticmethod
+        def forward(ctx, a, f, g, spec):
+            opts = dict(spec.get("options", {}))
+            sol = Solver(dict(dim=spec["dim"], n=spec["n"], w=spec["w"], a=a.detach().contiguous(),
+                              b=spec.get("b"), c=spec.get("c")),
+                         precision=spec.get("precision", "mixed"), **opts)
+            sol.build_transfer()
+            if spec.get("compress_tol"):
+                sol.compress(spec["compress_tol"])
+            u = torch.empty_like(f)
+            sol.solve(f.detach().contiguous(), g.detach().contiguous(), u)
+            ctx.sol = sol
+            ctx.shapes = (a.shape, f.shape, g.shape)
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            sol = ctx.sol
+            sa, sf, sg = ctx.shapes
+            dev = gu.device
+            da = torch.empty(sa, dtype=torch.float64, device=dev)
+            df = torch.empty(sf, dtype=torch.float64, device=dev)
+            dg = torch.empty(sg, dtype=torch.float64, device=dev)
+            ddst_solve_adjoint(sol.ctx, gu.contiguous(), df, dg, da)
+            sol.close()
+            ctx.sol = None
+            return da, df, dg, None
+
+    return DDSTSolve
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, item):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_autograd()
+        return getattr(_Lazy._cls, item)
+
+
+DDSTSolve = _Lazy()
