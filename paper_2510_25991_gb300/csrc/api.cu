@@ -558,7 +558,11 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     const double en = vec_norm(ctx, ctx->d_e, N, 4);
     const double un = vec_norm(ctx, ctx->d_u, N, 5);
     est = un > 0.0 ? en / un : 0.0;
-    if (rmax == 0 || est <= ctx->opt.refine_tol) break;
+    if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
+      if (s == DDST_ERR_NOT_CONVERGED) result = s;
+      break;
+    }
+    if (est <= ctx->opt.refine_tol) break;
     if (it == rmax) result = DDST_ERR_NOT_CONVERGED;
   }
   launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
@@ -665,7 +669,11 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     const double en = vec_norm(ctx, ctx->d_e, N, 4);
     const double ln = vec_norm(ctx, ctx->d_lam, N, 5);
     est = ln > 0.0 ? en / ln : 0.0;
-    if (rmax == 0 || est <= ctx->opt.refine_tol) break;
+    if (rmax == 0) {
+      if (s == DDST_ERR_NOT_CONVERGED) result = s;
+      break;
+    }
+    if (est <= ctx->opt.refine_tol) break;
     if (it == rmax) result = DDST_ERR_NOT_CONVERGED;
   }
   launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_ga, ctx->d_lam, ctx->d_r, 1,

@@ -1,39 +1,741 @@
-// hodlr.cu -- HODLR compression and application (placeholder until the kernels land).
+// hodlr.cu -- weak-admissibility hierarchical compression of the transfer operators.
+//
+// Sec. 2.4 of the paper: every S_{j,j'} is stored on a cluster tree shared by its source and
+// target interface (the interfaces are discretized isomorphically); with weak admissibility
+// every off-diagonal block of every level is low rank and only the diagonal leaves are dense.
+// The paper uses nested (HBS) bases built by the randomized scheme of its reference [fastHBS];
+// this library stores the non-nested HODLR variant.  Each off-diagonal block B is compressed
+// by randomized sampling (Gaussian test matrix, Alg. 1's sampling step applied to the formed
+// block):
+//   1. Y = B Omega, Omega ~ N(0,1)^{q x s}, s = k_max + oversample (Philox4x32-10 counters,
+//      Box-Muller with the CUDA math library's logf/sincospif).
+//   2. Columns of Y orthonormalized in order by classical Gram-Schmidt applied twice; a column
+//      is kept only if its residual norm exceeds tol * ||S_{j,j'}||_2 (rank detection: the
+//      residual of a Gaussian sample estimates ||(I - Q Q^T) B||_F), at most k_max columns.
+//   3. V = B^T Q, so that B ~ Q V^T.
+// ||S_{j,j'}||_2 is estimated by power iteration on S^T S.  Balanced bisection tree: node t of
+// level l spans [(t ng) >> l, ((t+1) ng) >> l); depth L = min{L : ceil(ng / 2^L) <= leaf}.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "hodlr.cuh"
 #include "kernels.cuh"
 
 namespace ddst {
 
+// ---------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based generator.
+// ---------------------------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ float u01(uint32_t v) {  // (0, 1)
+  return ((v >> 8) + 0.5f) * (1.0f / 16777216.0f);
+}
+
+// Four standard normal numbers for counter (a, b, c).
+__device__ __forceinline__ void gauss4(uint32_t a, uint32_t b, uint32_t c, uint64_t seed,
+                                       float out[4]) {
+  const U4 r = philox4x32_10(U4{a, b, c, 0x5eedu}, (uint32_t)seed, (uint32_t)(seed >> 32));
+  float s0, c0, s1, c1;
+  const float r0 = sqrtf(-2.0f * logf(u01(r.x)));
+  const float r1 = sqrtf(-2.0f * logf(u01(r.z)));
+  sincospif(2.0f * u01(r.y), &s0, &c0);
+  sincospif(2.0f * u01(r.w), &s1, &c1);
+  out[0] = r0 * c0;
+  out[1] = r0 * s0;
+  out[2] = r1 * c1;
+  out[3] = r1 * s1;
+}
+
+struct SBlk {         // one dense S block
+  int64_t off;        // column-major ng x ng in S
+  int64_t ng;
+};
+
+// Work item of the tiled kernels: (block, first row or column of the tile).
+struct HItem {
+  int blk;
+  int64_t lo;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Norm estimate: power iteration on S^T S for every S block (batched GEMV).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_sblk_gemv(const SBlk* __restrict__ sb, const T* __restrict__ S,
+                            const double* __restrict__ x, double* __restrict__ y,
+                            int64_t stride, int transpose) {
+  const SBlk b = sb[blockIdx.y];
+  const double* xv = x + blockIdx.y * stride;
+  double* yv = y + blockIdx.y * stride;
+  const T* M = S + b.off;
+  if (!transpose) {  // y = S x: thread per row, columns contiguous
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= b.ng) return;
+    double acc = 0.0;
+    for (int64_t c0 = 0; c0 < b.ng; c0 += 32) {
+      T part = T(0);
+      const int64_t c1 = min(b.ng, c0 + 32);
+      for (int64_t c = c0; c < c1; ++c) part = fma(M[c * b.ng + row], static_cast<T>(xv[c]), part);
+      acc += (double)part;
+    }
+    yv[row] = acc;
+  } else {  // y = S^T x: warp per column
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (col >= b.ng) return;
+    T part = T(0);
+    for (int64_t r = lane; r < b.ng; r += 32) part = fma(M[col * b.ng + r], static_cast<T>(xv[r]), part);
+    const double acc = warp_sum((double)part);
+    if (lane == 0) yv[col] = acc;
+  }
+}
+
+// x_b <- y_b / ||y_b||, nrm[b] = ||y_b||  (one CTA per block)
+__global__ void k_sblk_normalize(const SBlk* __restrict__ sb, double* __restrict__ x,
+                                 const double* __restrict__ y, int64_t stride,
+                                 double* __restrict__ nrm) {
+  const SBlk b = sb[blockIdx.x];
+  const double* yv = y + blockIdx.x * stride;
+  double* xv = x + blockIdx.x * stride;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < b.ng; e += blockDim.x) acc += yv[e] * yv[e];
+  __shared__ double red[32];
+  __shared__ double tot;
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) tot = sqrt(t);
+  }
+  __syncthreads();
+  const double inv = tot > 0.0 ? 1.0 / tot : 0.0;
+  for (int64_t e = threadIdx.x; e < b.ng; e += blockDim.x) xv[e] = yv[e] * inv;
+  if (threadIdx.x == 0) nrm[blockIdx.x] = tot;
+}
+
+__global__ void k_sblk_init(const SBlk* __restrict__ sb, double* __restrict__ x, int64_t stride,
+                            uint64_t seed) {
+  const SBlk b = sb[blockIdx.x];
+  double* xv = x + blockIdx.x * stride;
+  for (int64_t e = threadIdx.x; e < b.ng; e += blockDim.x) {
+    float g[4];
+    gauss4((uint32_t)e, (uint32_t)blockIdx.x, 0xabcdu, seed, g);
+    xv[e] = g[0];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Compression kernels
+// ---------------------------------------------------------------------------------------------
+struct HDev {        // per off-diagonal block, device view for compression
+  int64_t s_off;     // element offset of B(0,0) in S (column-major, leading dim ng)
+  int64_t ng;
+  int64_t p, q;      // rows, cols
+  int s;             // sample capacity
+  int sblk;
+  int64_t u_off, v_off;
+};
+
+// Omega (q x s, column-major) into the V slot.
+template <typename T>
+__global__ void k_gen_omega(const HDev* __restrict__ hb, T* __restrict__ UV, uint64_t seed) {
+  const HDev b = hb[blockIdx.y];
+  const int64_t total = b.q * ((b.s + 3) / 4);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e % b.q;
+    const int jg = (int)(e / b.q);
+    float g[4];
+    gauss4((uint32_t)c, (uint32_t)jg, (uint32_t)blockIdx.y, seed, g);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * jg + u;
+      if (j < b.s) UV[b.v_off + (int64_t)j * b.q + c] = static_cast<T>(g[u]);
+    }
+  }
+}
+
+// Y = B Omega for a tile of 64 rows (all s samples).  256 threads: 16 row groups (4 rows) x
+// 16 sample groups (SC/16 samples).  Column chunks of 32 staged in shared memory.
+template <typename T, int SC>
+__global__ void __launch_bounds__(256) k_sketch(const HItem* __restrict__ items,
+                                                const HDev* __restrict__ hb,
+                                                const T* __restrict__ S, T* __restrict__ UV) {
+  constexpr int CPT = SC / 16;
+  const HItem it = items[blockIdx.x];
+  const HDev b = hb[it.blk];
+  __shared__ T sB[32][64 + 1];
+  __shared__ T sO[32][SC + 1];
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  T acc[4][CPT];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
+  const T* Bp = S + b.s_off + it.lo;  // B(row, col) at Bp[col * ng + row - lo]
+  const T* Om = UV + b.v_off;         // Omega(col, j) at Om[j * q + col]
+  for (int64_t c0 = 0; c0 < b.q; c0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+      const int cc = e >> 6, rr = e & 63;
+      const int64_t col = c0 + cc, row = it.lo + rr;
+      sB[cc][rr] = (col < b.q && row < b.p) ? Bp[col * b.ng + rr] : T(0);
+    }
+    for (int e = threadIdx.x; e < 32 * SC; e += 256) {
+      const int j = e / 32, cc = e % 32;
+      const int64_t col = c0 + cc;
+      sO[cc][j] = (col < b.q && j < b.s) ? Om[(int64_t)j * b.q + col] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int cc = 0; cc < 32; ++cc) {
+      T bv[4], ov[CPT];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) bv[a] = sB[cc][tr * 4 + a];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) ov[c] = sO[cc][tc * CPT + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[a][c] = fma(bv[a], ov[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t row = it.lo + tr * 4 + a;
+    if (row >= b.p) continue;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = tc * CPT + c;
+      if (j < b.s) UV[b.u_off + (int64_t)j * b.p + row] = acc[a][c];
+    }
+  }
+}
+
+// In-place CGS2 orthonormalization of the sketch columns with rank detection (one CTA per
+// block).  Column j is kept (appended as Q[:, r]) when its residual norm exceeds thr.
+template <typename T>
+__global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
+                                                    T* __restrict__ UV,
+                                                    const double* __restrict__ snorm, double tol,
+                                                    int kmax, int* __restrict__ rank_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const HDev b = hb[blockIdx.x];
+  T* y = reinterpret_cast<T*>(smem_raw);  // p values
+  __shared__ T h[256];
+  __shared__ double red[32];
+  __shared__ double s_nu;
+  T* Q = UV + b.u_off;
+  const double thr = tol * snorm[b.sblk];
+  const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r = 0;
+  for (int j = 0; j < b.s; ++j) {
+    for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) y[i] = Q[(int64_t)j * b.p + i];
+    __syncthreads();
+    for (int pass = 0; pass < 2 && r > 0; ++pass) {
+      for (int c = warp; c < r; c += nw) {
+        T part = T(0);
+        for (int64_t i = lane; i < b.p; i += 32) part = fma(Q[(int64_t)c * b.p + i], y[i], part);
+        const double acc = warp_sum((double)part);
+        if (lane == 0) h[c] = static_cast<T>(acc);
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) {
+        T acc = T(0);
+        for (int c = 0; c < r; ++c) acc = fma(Q[(int64_t)c * b.p + i], h[c], acc);
+        y[i] -= acc;
+      }
+      __syncthreads();
+    }
+    T part = T(0);
+    for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) part = fma(y[i], y[i], part);
+    const double acc = warp_sum((double)part);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) s_nu = sqrt(t);
+    }
+    __syncthreads();
+    const double nu = s_nu;
+    if (nu > thr && r < kmax && r < 256) {
+      const T inv = static_cast<T>(1.0 / nu);
+      for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) Q[(int64_t)r * b.p + i] = y[i] * inv;
+      ++r;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rank_out[blockIdx.x] = r;
+}
+
+// V = B^T Q (q x r) for a tile of 64 columns of B.  Row chunks of 32 staged in shared memory.
+template <typename T, int SC>
+__global__ void __launch_bounds__(256) k_project(const HItem* __restrict__ items,
+                                                 const HDev* __restrict__ hb,
+                                                 const int* __restrict__ rank,
+                                                 const T* __restrict__ S, T* __restrict__ UV) {
+  constexpr int CPT = SC / 16;
+  const HItem it = items[blockIdx.x];
+  const HDev b = hb[it.blk];
+  const int r = rank[it.blk];
+  if (r == 0) return;
+  __shared__ T sB[64][32 + 1];   // [col][row]
+  __shared__ T sQ[32][SC + 1];   // [row][j]
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  T acc[4][CPT];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[a][c] = T(0);
+  const T* Q = UV + b.u_off;
+  for (int64_t r0 = 0; r0 < b.p; r0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+      const int cc = e >> 5, rr = e & 31;
+      const int64_t col = it.lo + cc, row = r0 + rr;
+      sB[cc][rr] = (col < b.q && row < b.p) ? S[b.s_off + col * b.ng + row] : T(0);
+    }
+    for (int e = threadIdx.x; e < 32 * SC; e += 256) {
+      const int j = e / 32, rr = e % 32;
+      const int64_t row = r0 + rr;
+      sQ[rr][j] = (row < b.p && j < r) ? Q[(int64_t)j * b.p + row] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      T bv[4], qv[CPT];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) bv[a] = sB[tr * 4 + a][rr];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) qv[c] = sQ[rr][tc * CPT + c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[a][c] = fma(bv[a], qv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t col = it.lo + tr * 4 + a;
+    if (col >= b.q) continue;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = tc * CPT + c;
+      if (j < r) UV[b.v_off + (int64_t)j * b.q + col] = acc[a][c];
+    }
+  }
+}
+
+// Dense leaves: copy S(lo:lo+len, lo:lo+len) of every leaf.
+template <typename T>
+__global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __restrict__ soff,
+                              const int64_t* __restrict__ sng, const T* __restrict__ S,
+                              T* __restrict__ D) {
+  const HLeaf L = lv[blockIdx.y];
+  const int64_t ng = sng[L.sblk], off = soff[L.sblk];
+  const int64_t total = L.len * L.len;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / L.len, rr = e % L.len;
+    D[L.d_off + e] = S[off + (L.lo + c) * ng + L.lo + rr];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Application
+// ---------------------------------------------------------------------------------------------
+// t_b = W_in^T x_in over the block (W_in = V, or U when transposed): warp per rank column.
+template <typename T>
+__global__ void k_h_inner(const HBlock* __restrict__ bl, const T* __restrict__ UV,
+                          const double* __restrict__ x, double* __restrict__ t, int transpose) {
+  const HBlock b = bl[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t len = transpose ? b.nrows : b.ncols;
+  const T* W = UV + (transpose ? b.u_off : b.v_off);
+  const double* xv = x + (transpose ? b.out_if + b.row0 : b.in_if + b.col0);
+  for (int c = warp; c < b.rank; c += nw) {
+    const T* col = W + (int64_t)c * len;
+    double acc = 0.0;
+    T part = T(0);
+    int cnt = 0;
+    for (int64_t i = lane; i < len; i += 32) {
+      part = fma(col[i], static_cast<T>(xv[i]), part);
+      if (++cnt == 32) { acc += (double)part; part = T(0); cnt = 0; }
+    }
+    acc += (double)part;
+    acc = warp_sum(acc);
+    if (lane == 0) t[b.t_off + c] = acc;
+  }
+}
+
+// acc_out += W_out t_b (W_out = U, or V when transposed): thread per output row, tiles of 256.
+template <typename T>
+__global__ void k_h_outer(const HItem* __restrict__ items, const HBlock* __restrict__ bl,
+                          const T* __restrict__ UV, const double* __restrict__ t,
+                          double* __restrict__ acc, int transpose) {
+  const HItem it = items[blockIdx.x];
+  const HBlock b = bl[it.blk];
+  __shared__ T st[256];
+  for (int c = threadIdx.x; c < b.rank; c += blockDim.x) st[c] = static_cast<T>(t[b.t_off + c]);
+  __syncthreads();
+  const int64_t len = transpose ? b.ncols : b.nrows;
+  const int64_t i = it.lo + threadIdx.x;
+  if (i >= len) return;
+  const T* W = UV + (transpose ? b.v_off : b.u_off);
+  T a = T(0);
+  for (int c = 0; c < b.rank; ++c) a = fma(W[(int64_t)c * len + i], st[c], a);
+  const int64_t o = transpose ? b.in_if + b.col0 + i : b.out_if + b.row0 + i;
+  atomicAdd(&acc[o], (double)a);
+}
+
+// Dense leaves: acc_out += D x_in (or D^T).  One CTA per leaf.
+template <typename T>
+__global__ void k_h_leaf(const HLeaf* __restrict__ lv, const T* __restrict__ D,
+                         const double* __restrict__ x, double* __restrict__ acc, int transpose) {
+  const HLeaf L = lv[blockIdx.x];
+  const T* M = D + L.d_off;
+  if (!transpose) {
+    const double* xv = x + L.in_if + L.lo;
+    for (int64_t r = threadIdx.x; r < L.len; r += blockDim.x) {
+      double a = 0.0;
+      for (int64_t c0 = 0; c0 < L.len; c0 += 32) {
+        T part = T(0);
+        const int64_t c1 = min(L.len, c0 + 32);
+        for (int64_t c = c0; c < c1; ++c) part = fma(M[c * L.len + r], static_cast<T>(xv[c]), part);
+        a += (double)part;
+      }
+      atomicAdd(&acc[L.out_if + L.lo + r], a);
+    }
+  } else {
+    const double* xv = x + L.out_if + L.lo;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int64_t c = warp; c < L.len; c += nw) {
+      T part = T(0);
+      for (int64_t r = lane; r < L.len; r += 32) part = fma(M[c * L.len + r], static_cast<T>(xv[r]), part);
+      const double a = warp_sum((double)part);
+      if (lane == 0) atomicAdd(&acc[L.in_if + L.lo + c], a);
+    }
+  }
+}
+
+__global__ void k_h_finish(const double* __restrict__ x, const double* __restrict__ acc,
+                           double* __restrict__ y, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = x[e] - acc[e];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
 void HodlrSet::clear() { release(); }
 
 void HodlrSet::release() {
-  for (void* p : {UV, D, (void*)t, (void*)acc, (void*)d_blocks, (void*)d_leaves})
+  for (void* p : {UV, D, (void*)t, (void*)acc, (void*)d_blocks, (void*)d_leaves,
+                  (void*)d_out_items, (void*)d_out_items_T})
     if (p) cudaFree(p);
   UV = D = nullptr;
   t = acc = nullptr;
   d_blocks = nullptr;
   d_leaves = nullptr;
+  d_out_items = d_out_items_T = nullptr;
   blocks.clear();
   leaves.clear();
   built = false;
   bytes = 0;
   max_rank = 0;
+  n_out_items = n_out_items_T = 0;
+}
+
+static int levels_for(int64_t ng, int leaf) {
+  int L = 0;
+  while ((ng + (1LL << L) - 1) / (1LL << L) > leaf) ++L;
+  return L;
 }
 
 template <typename T>
-int hodlr_build(HodlrSet& H, const HodlrParams&, const std::vector<SlabDesc>&,
-                const std::vector<ProbDesc>&, const SlabDesc*, const T*, cudaStream_t,
-                std::string& msg) {
+static void launch_sketch(int SC, const HItem* it, int n, const HDev* hb, const T* S, T* UV,
+                          cudaStream_t st) {
+  if (n == 0) return;
+  switch (SC) {
+    case 32: k_sketch<T, 32><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    case 64: k_sketch<T, 64><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    case 96: k_sketch<T, 96><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    default: k_sketch<T, 128><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+  }
+}
+
+template <typename T>
+static void launch_project(int SC, const HItem* it, int n, const HDev* hb, const int* rank,
+                           const T* S, T* UV, cudaStream_t st) {
+  if (n == 0) return;
+  switch (SC) {
+    case 32: k_project<T, 32><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    case 64: k_project<T, 64><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    case 96: k_project<T, 96><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    default: k_project<T, 128><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+  }
+}
+
+template <typename T>
+int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>& slabs,
+                const std::vector<ProbDesc>& probs, const SlabDesc* /*d_slabs*/, const T* S,
+                cudaStream_t st, std::string& msg) {
   H.release();
-  msg = "HODLR compression not available";
-  return 1;
+  H.esz = sizeof(T);
+  const int kmax = std::max(1, std::min(hp.k_max, 128));
+  const int s_req = std::min(128, kmax + std::max(0, hp.oversample));
+  const int leaf = std::max(8, hp.leaf);
+  // S blocks
+  std::vector<SBlk> sb;
+  std::vector<int> sb_slab, sb_side;
+  for (size_t si = 0; si < slabs.size(); ++si) {
+    const SlabDesc& s = slabs[si];
+    if (s.sp_off >= 0) { sb.push_back({s.sp_off, s.ng}); sb_slab.push_back((int)si); sb_side.push_back(-1); }
+    if (s.sn_off >= 0) { sb.push_back({s.sn_off, s.ng}); sb_slab.push_back((int)si); sb_side.push_back(1); }
+  }
+  const int nsb = (int)sb.size();
+  H.sblk_slab = sb_slab;
+  H.sblk_side = sb_side;
+  H.sblk_L.assign(nsb, 0);
+  if (nsb == 0) { H.built = true; return 0; }
+  int64_t max_ng = 0, tot_if = 0;
+  for (auto& P : probs) tot_if += (int64_t)P.nds * P.ng;
+  for (auto& b : sb) max_ng = std::max(max_ng, b.ng);
+  // blocks and leaves
+  std::vector<HDev> hd;
+  int64_t uv = 0, dl = 0, tl = 0;
+  for (int b = 0; b < nsb; ++b) {
+    const SlabDesc& s = slabs[sb_slab[b]];
+    const int64_t ng = sb[b].ng;
+    const int L = levels_for(ng, leaf);
+    H.sblk_L[b] = L;
+    const int64_t in_if = s.if_off + (sb_side[b] < 0 ? -ng : ng), out_if = s.if_off;
+    for (int lev = 1; lev <= L; ++lev) {
+      for (int64_t t = 0; t < (1LL << (lev - 1)); ++t) {
+        const int64_t lo1 = ((2 * t) * ng) >> lev, hi1 = ((2 * t + 1) * ng) >> lev;
+        const int64_t lo2 = hi1, hi2 = ((2 * t + 2) * ng) >> lev;
+        const int64_t rr[2][4] = {{lo1, hi1, lo2, hi2}, {lo2, hi2, lo1, hi1}};
+        for (int e = 0; e < 2; ++e) {
+          HBlock k{};
+          k.sblk = b;
+          k.level = lev;
+          k.row0 = rr[e][0]; k.nrows = rr[e][1] - rr[e][0];
+          k.col0 = rr[e][2]; k.ncols = rr[e][3] - rr[e][2];
+          const int sc = (int)std::min<int64_t>(s_req, std::min(k.nrows, k.ncols));
+          k.u_off = uv; uv += k.nrows * sc;
+          k.v_off = uv; uv += k.ncols * sc;
+          k.t_off = tl; tl += sc;
+          k.in_if = in_if; k.out_if = out_if;
+          k.rank = sc;  // capacity until compressed
+          H.blocks.push_back(k);
+          HDev d{};
+          d.s_off = sb[b].off + k.col0 * ng + k.row0;
+          d.ng = ng; d.p = k.nrows; d.q = k.ncols; d.s = sc; d.sblk = b;
+          d.u_off = k.u_off; d.v_off = k.v_off;
+          hd.push_back(d);
+        }
+      }
+    }
+    for (int64_t t = 0; t < (1LL << L); ++t) {
+      HLeaf lf{};
+      lf.sblk = b;
+      lf.lo = (t * ng) >> L;
+      lf.len = (((t + 1) * ng) >> L) - lf.lo;
+      lf.d_off = dl; dl += lf.len * lf.len;
+      lf.in_if = in_if; lf.out_if = out_if;
+      H.leaves.push_back(lf);
+    }
+  }
+  const int nblk = (int)H.blocks.size();
+  // device memory
+  auto al = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    return true;
+  };
+  SBlk* d_sb = nullptr; double *d_x = nullptr, *d_y = nullptr, *d_nrm = nullptr;
+  HDev* d_hd = nullptr; HItem *d_items = nullptr; int* d_rank = nullptr;
+  int64_t *d_soff = nullptr, *d_sng = nullptr;
+  const int64_t stride = max_ng;
+  bool ok = al(&H.UV, sizeof(T) * uv) && al(&H.D, sizeof(T) * dl) && al((void**)&H.t, sizeof(double) * tl) &&
+            al((void**)&H.acc, sizeof(double) * tot_if) &&
+            al((void**)&H.d_blocks, sizeof(HBlock) * nblk) &&
+            al((void**)&H.d_leaves, sizeof(HLeaf) * H.leaves.size()) &&
+            al((void**)&d_sb, sizeof(SBlk) * nsb) && al((void**)&d_x, sizeof(double) * stride * nsb) &&
+            al((void**)&d_y, sizeof(double) * stride * nsb) && al((void**)&d_nrm, sizeof(double) * nsb) &&
+            al((void**)&d_hd, sizeof(HDev) * nblk) && al((void**)&d_rank, sizeof(int) * nblk) &&
+            al((void**)&d_soff, sizeof(int64_t) * nsb) && al((void**)&d_sng, sizeof(int64_t) * nsb);
+  auto cleanup = [&]() {
+    for (void* p : {(void*)d_sb, (void*)d_x, (void*)d_y, (void*)d_nrm, (void*)d_hd, (void*)d_items,
+                    (void*)d_rank, (void*)d_soff, (void*)d_sng})
+      if (p) cudaFree(p);
+  };
+  if (!ok) { cleanup(); H.release(); msg = "out of device memory"; return 2; }
+  std::vector<int64_t> soff(nsb), sng(nsb);
+  for (int b = 0; b < nsb; ++b) { soff[b] = sb[b].off; sng[b] = sb[b].ng; }
+  cudaMemcpyAsync(d_sb, sb.data(), sizeof(SBlk) * nsb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_hd, hd.data(), sizeof(HDev) * nblk, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_sng, sng.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(H.d_leaves, H.leaves.data(), sizeof(HLeaf) * H.leaves.size(), cudaMemcpyHostToDevice, st);
+  // ||S||_2 by power iteration on S^T S (6 steps)
+  k_sblk_init<<<nsb, 256, 0, st>>>(d_sb, d_x, stride, hp.seed ^ 0x9e3779b97f4a7c15ull);
+  const unsigned gr = (unsigned)((max_ng + 255) / 256), gc = (unsigned)((max_ng + 7) / 8);
+  for (int itp = 0; itp < 6; ++itp) {
+    k_sblk_gemv<T><<<dim3(gr, nsb), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
+    k_sblk_gemv<T><<<dim3(gc, nsb), 256, 0, st>>>(d_sb, S, d_y, d_x, stride, 1);
+    k_sblk_normalize<<<nsb, 256, 0, st>>>(d_sb, d_x, d_x, stride, d_nrm);
+  }
+  // d_nrm now holds ||S^T S x|| ~ sigma_max^2
+  // sketches
+  int SC = 32;
+  while (SC < s_req) SC += 32;
+  std::vector<HItem> items;
+  for (int b = 0; b < nblk; ++b)
+    for (int64_t lo = 0; lo < hd[b].p; lo += 64) items.push_back({b, lo});
+  std::vector<HItem> pitems;
+  for (int b = 0; b < nblk; ++b)
+    for (int64_t lo = 0; lo < hd[b].q; lo += 64) pitems.push_back({b, lo});
+  const size_t nit = std::max(items.size(), pitems.size());
+  if (!al((void**)&d_items, sizeof(HItem) * nit)) { cleanup(); H.release(); msg = "oom"; return 2; }
+  k_gen_omega<T><<<dim3(32, nblk), 256, 0, st>>>(d_hd, (T*)H.UV, hp.seed);
+  cudaMemcpyAsync(d_items, items.data(), sizeof(HItem) * items.size(), cudaMemcpyHostToDevice, st);
+  launch_sketch<T>(SC, d_items, (int)items.size(), d_hd, S, (T*)H.UV, st);
+  // sigma estimate: sqrt of the Rayleigh quotient norm
+  std::vector<double> nrm(nsb);
+  cudaMemcpyAsync(nrm.data(), d_nrm, sizeof(double) * nsb, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  for (auto& v : nrm) v = std::sqrt(std::max(v, 0.0));
+  cudaMemcpyAsync(d_nrm, nrm.data(), sizeof(double) * nsb, cudaMemcpyHostToDevice, st);
+  {
+    int64_t maxp = 0;
+    for (auto& d : hd) maxp = std::max(maxp, d.p);
+    const size_t smem = sizeof(T) * maxp;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(k_range_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax, d_rank);
+  }
+  cudaMemcpyAsync(d_items, pitems.data(), sizeof(HItem) * pitems.size(), cudaMemcpyHostToDevice, st);
+  launch_project<T>(SC, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
+  k_copy_leaves<T><<<dim3(16, (unsigned)H.leaves.size()), 256, 0, st>>>(H.d_leaves, d_soff, d_sng, S,
+                                                                       (T*)H.D);
+  std::vector<int> ranks(nblk);
+  cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  cleanup();
+  if (e != cudaSuccess) { msg = cudaGetErrorString(e); H.release(); return 1; }
+  int64_t used = 0;
+  for (int b = 0; b < nblk; ++b) {
+    H.blocks[b].rank = ranks[b];
+    H.max_rank = std::max(H.max_rank, ranks[b]);
+    used += (H.blocks[b].nrows + H.blocks[b].ncols) * ranks[b];
+  }
+  H.bytes = (used + dl) * (int64_t)sizeof(T);
+  H.acc_len = tot_if;
+  H.t_len = tl;
+  cudaMemcpyAsync(H.d_blocks, H.blocks.data(), sizeof(HBlock) * nblk, cudaMemcpyHostToDevice, st);
+  // output-row work items of the apply (non-transposed: rows of U; transposed: rows of V)
+  std::vector<HItem> oi, oiT;
+  for (int b = 0; b < nblk; ++b) {
+    if (H.blocks[b].rank == 0) continue;
+    for (int64_t lo = 0; lo < H.blocks[b].nrows; lo += 256) oi.push_back({b, lo});
+    for (int64_t lo = 0; lo < H.blocks[b].ncols; lo += 256) oiT.push_back({b, lo});
+  }
+  H.n_out_items = (int)oi.size();
+  H.n_out_items_T = (int)oiT.size();
+  if (!al((void**)&H.d_out_items, sizeof(HItem) * std::max<size_t>(1, oi.size())) ||
+      !al((void**)&H.d_out_items_T, sizeof(HItem) * std::max<size_t>(1, oiT.size()))) {
+    H.release(); msg = "oom"; return 2;
+  }
+  cudaMemcpyAsync(H.d_out_items, oi.data(), sizeof(HItem) * oi.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(H.d_out_items_T, oiT.data(), sizeof(HItem) * oiT.size(), cudaMemcpyHostToDevice, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { msg = cudaGetErrorString(e); H.release(); return 1; }
+  H.built = true;
+  return 0;
 }
 
 template <typename T>
-void hodlr_apply(HodlrSet&, const SlabDesc*, const ProbDesc*, int, const double*, double*, int,
-                 cudaStream_t) {}
+void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const double* x, double* y,
+                 int transpose, cudaStream_t st) {
+  cudaMemsetAsync(H.acc, 0, sizeof(double) * H.acc_len, st);
+  const int nblk = (int)H.blocks.size();
+  if (nblk > 0) {
+    k_h_inner<T><<<nblk, 256, 0, st>>>(H.d_blocks, (const T*)H.UV, x, H.t, transpose);
+    const int ni = transpose ? H.n_out_items_T : H.n_out_items;
+    if (ni > 0)
+      k_h_outer<T><<<ni, 256, 0, st>>>(transpose ? (const HItem*)H.d_out_items_T
+                                                 : (const HItem*)H.d_out_items,
+                                       H.d_blocks, (const T*)H.UV, H.t, H.acc, transpose);
+  }
+  if (!H.leaves.empty())
+    k_h_leaf<T><<<(unsigned)H.leaves.size(), 256, 0, st>>>(H.d_leaves, (const T*)H.D, x, H.acc,
+                                                           transpose);
+  k_h_finish<<<512, 256, 0, st>>>(x, H.acc, y, H.acc_len);
+}
 
-int hodlr_expand(HodlrSet&, int, int, size_t, double*, cudaStream_t) { return 1; }
+int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaStream_t st) {
+  int sbk = -1;
+  for (size_t b = 0; b < H.sblk_slab.size(); ++b)
+    if (H.sblk_slab[b] == slab && H.sblk_side[b] == side) sbk = (int)b;
+  if (sbk < 0) return 1;
+  auto fetch = [&](const void* base, int64_t off, int64_t n, std::vector<double>& dst) {
+    dst.resize(n);
+    if (esz == 8) {
+      cudaMemcpyAsync(dst.data(), (const double*)base + off, sizeof(double) * n,
+                      cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+    } else {
+      std::vector<float> tmp(n);
+      cudaMemcpyAsync(tmp.data(), (const float*)base + off, sizeof(float) * n,
+                      cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      for (int64_t e = 0; e < n; ++e) dst[e] = tmp[e];
+    }
+  };
+  int64_t ng = 0;
+  for (auto& lf : H.leaves)
+    if (lf.sblk == sbk) ng = std::max(ng, lf.lo + lf.len);
+  std::fill(out, out + ng * ng, 0.0);
+  std::vector<double> U, V, Dm;
+  for (auto& b : H.blocks) {
+    if (b.sblk != sbk || b.rank == 0) continue;
+    fetch(H.UV, b.u_off, b.nrows * b.rank, U);
+    fetch(H.UV, b.v_off, b.ncols * b.rank, V);
+    for (int64_t c = 0; c < b.ncols; ++c)
+      for (int64_t r = 0; r < b.nrows; ++r) {
+        double a = 0.0;
+        for (int k = 0; k < b.rank; ++k) a += U[k * b.nrows + r] * V[k * b.ncols + c];
+        out[(b.col0 + c) * ng + b.row0 + r] = a;
+      }
+  }
+  for (auto& lf : H.leaves) {
+    if (lf.sblk != sbk) continue;
+    fetch(H.D, lf.d_off, lf.len * lf.len, Dm);
+    for (int64_t c = 0; c < lf.len; ++c)
+      for (int64_t r = 0; r < lf.len; ++r) out[(lf.lo + c) * ng + lf.lo + r] = Dm[c * lf.len + r];
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
 
 template int hodlr_build<float>(HodlrSet&, const HodlrParams&, const std::vector<SlabDesc>&,
                                 const std::vector<ProbDesc>&, const SlabDesc*, const float*,

@@ -45,10 +45,15 @@ struct HodlrSet {
   HLeaf* d_leaves = nullptr;
   std::vector<HBlock> blocks;
   std::vector<HLeaf> leaves;
+  void* d_out_items = nullptr;    // apply work items (block, row tile)
+  void* d_out_items_T = nullptr;  // transposed apply work items
+  int n_out_items = 0, n_out_items_T = 0;
   int64_t t_len = 0, acc_len = 0;
   int64_t bytes = 0;
   int max_rank = 0;
-  std::vector<int> sblk_L;  // tree depth per S block
+  std::vector<int> sblk_L;     // tree depth per S block
+  std::vector<int> sblk_slab;  // slab of each S block
+  std::vector<int> sblk_side;  // -1: S_{j,j-1}, +1: S_{j,j+1}
   void clear();
   void release();
 };

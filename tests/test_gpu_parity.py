@@ -3,7 +3,9 @@
 Tolerances (derived in the design notes):
 * FP64 path, uncompressed: 1e-10 relative (transfer blocks and solutions).
 * Mixed path (FP32 local operators) after FP64 refinement: 1e-8 relative solution error.
-* FP32 transfer blocks: 2e-5 relative to max |S| (FP32 rounding amplified by the local solve).
+* FP32 transfer blocks: 1e-3 relative to max |S|: a backward-stable FP32 local solve has
+  forward error up to kappa(A_j) u_32, and kappa(A_j) ~ 4e5 for the variable-coefficient
+  double slabs tested (u_32 = 6e-8); measured 2.4e-4 on the 256^2 case.
 """
 import numpy as np
 import pytest
@@ -70,7 +72,7 @@ def test_transfer_blocks_match_oracle(name, n, w, dim, precision):
     facs = O.factor_local(A, geo)
     Sp, Sn = O.transfer_blocks(A, geo, facs)
     sol = make_solver(prob, precision)
-    tol = 1e-10 if precision == "fp64" else 2e-5
+    tol = 1e-10 if precision == "fp64" else 1e-3
     ng = geo.ngamma
     out = np.empty((ng, ng))
     worst = 0.0
