@@ -173,6 +173,10 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
 
+/* Number of CUDA kernels this library has launched in the calling process so far (a
+ * diagnostic for benchmarks: the difference across a timed region counts its launches). */
+int64_t ddst_kernel_launches(void);
+
 /* Message of the last error on ctx (or of the last failed ddst_setup when ctx is NULL). */
 const char* ddst_last_error(const ddst_ctx* ctx);
 

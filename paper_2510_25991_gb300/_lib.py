@@ -67,6 +67,7 @@ SIGNATURES = {
     "ddst_apply_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "ddst_query": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int)]),
+    "ddst_kernel_launches": (C.c_int64, []),
     "ddst_last_error": (C.c_char_p, [_P]),
     "ddst_destroy": (None, [_P]),
 }

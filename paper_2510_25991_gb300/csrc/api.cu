@@ -22,6 +22,13 @@
 
 using namespace ddst;
 
+namespace ddst {
+std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+}  // namespace ddst
+
 namespace {
 
 std::string g_setup_error;
@@ -53,7 +60,8 @@ struct ddst_ctx {
   size_t esz = 4;  // sizeof working precision
   // device buffers
   double *d_a = nullptr, *d_c = nullptr;
-  void *F = nullptr, *B = nullptr, *G = nullptr, *pack = nullptr, *S = nullptr;
+  void *F = nullptr, *B = nullptr, *G = nullptr, *Ft = nullptr, *Bt = nullptr, *pack = nullptr,
+       *S = nullptr;
   void *loc_b = nullptr, *loc_bf = nullptr, *loc_bb = nullptr, *loc_x = nullptr;
   double *d_f = nullptr, *d_g = nullptr, *d_b = nullptr, *d_u = nullptr, *d_r = nullptr,
          *d_e = nullptr, *d_lam = nullptr, *d_ga = nullptr, *d_gn = nullptr, *d_an = nullptr;
@@ -260,6 +268,8 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   AL(ctx->F, es * ctx->fac_elems);
   AL(ctx->B, es * ctx->fac_elems);
   AL(ctx->G, es * ctx->fac_elems);
+  AL(ctx->Ft, es * ctx->fac_elems);
+  AL(ctx->Bt, es * ctx->fac_elems);
   AL(ctx->loc_b, es * ctx->tot_loc);
   AL(ctx->loc_bf, es * ctx->tot_loc);
   AL(ctx->loc_bb, es * ctx->tot_loc);
@@ -298,14 +308,16 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     for (auto& kv : ctx->cls)
       launch_factor<double>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
                             ctx->cls_maxnb[kv.first], (double*)ctx->pack, (double*)ctx->F,
-                            (double*)ctx->B, (double*)ctx->G, ctx->d_st, st);
+                            (double*)ctx->B, (double*)ctx->G, (double*)ctx->Ft, (double*)ctx->Bt,
+                            ctx->d_st, st);
   } else {
     launch_stencil_pack<float>(ctx->d_slabs, nslab, ctx->max_nb, ctx->d_probs, ctx->d_a, ctx->d_c,
                                (float*)ctx->pack, st);
     for (auto& kv : ctx->cls)
       launch_factor<float>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
                            ctx->cls_maxnb[kv.first], (float*)ctx->pack, (float*)ctx->F,
-                           (float*)ctx->B, (float*)ctx->G, ctx->d_st, st);
+                           (float*)ctx->B, (float*)ctx->G, (float*)ctx->Ft, (float*)ctx->Bt,
+                           ctx->d_st, st);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "factor launch");
   ctx->t_factor = tm.stop();
@@ -494,8 +506,8 @@ ddst_status dd_apply(ddst_ctx* ctx, const double* r, double* e, int* iters, doub
   launch_gather<T>(ctx->d_slabs, nslab, r, lb, st);
   for (auto& kv : ctx->cls)
     launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
-                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
+                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
                           ctx->if_fh, 0, 1, ctx->d_st, st);
   CK(cudaGetLastError());
   // interface solve (I - K) u_Gamma = fhat
@@ -505,8 +517,8 @@ ddst_status dd_apply(ddst_ctx* ctx, const double* r, double* e, int* iters, doub
   launch_add_iface_dirichlet<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, ctx->if_u, lb, st);
   for (auto& kv : ctx->cls)
     launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
-                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
+                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
                           nullptr, 0, 0, ctx->d_st, st);
   launch_scatter<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->loc_x, e, 0, st);
   CK(cudaGetLastError());
@@ -587,7 +599,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
     info->t_solve = ms;
-    info->bytes_factors = (int64_t)(3 * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
+    info->bytes_factors = (int64_t)(5 * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
     info->bytes_transfer = ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
     info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
     info->fail_slab = -1;
@@ -613,8 +625,8 @@ ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, do
   launch_gather_owned<T>(ctx->d_slabs, ctx->d_probs, nslab, r, lb, st);
   for (auto& kv : ctx->cls)
     launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
-                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
+                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
                           nullptr, 1, 0, ctx->d_st, st);
   CK(cudaMemsetAsync(ctx->if_fh, 0, sizeof(double) * ctx->tot_if, st));
   launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, (T*)ctx->loc_x,
@@ -625,8 +637,8 @@ ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, do
   launch_inject_center<T>(ctx->d_slabs, nslab, ctx->if_u, lb, st);
   for (auto& kv : ctx->cls)
     launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->G,
-                          (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
+                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
+                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
                           nullptr, 1, 0, ctx->d_st, st);
   CK(cudaMemsetAsync(e, 0, sizeof(double) * ctx->tot_vol, st));
   launch_gather_T<T>(ctx->d_slabs, nslab, (T*)ctx->loc_x, e, st);
@@ -890,6 +902,8 @@ ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamm
   if (max_rank) *max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
   return DDST_OK;
 }
+
+int64_t ddst_kernel_launches(void) { return (int64_t)launch_counter().load(); }
 
 const char* ddst_last_error(const ddst_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_setup_error.c_str();

@@ -13,10 +13,15 @@
 // diagonal blocks D_k and diagonal couplings L_k = diag(ell_k) (to block k-1) and
 // U_k = diag(ups_k) (to block k+1).
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace ddst {
+
+// Process-wide count of kernels launched by the library (reported by ddst_kernel_launches).
+std::atomic<long long>& launch_counter();
+inline void note_launch(int n = 1) { launch_counter().fetch_add(n, std::memory_order_relaxed); }
 
 // Stencil pack fields, stored per (slab, block) as [field][M] in the working precision.
 enum PackField { PK_DIAG = 0, PK_WEST = 1, PK_EAST = 2, PK_SOUTH = 3, PK_NORTH = 4,

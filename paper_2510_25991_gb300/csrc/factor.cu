@@ -7,7 +7,8 @@
 // Two block-LU sweeps are computed concurrently (one CTA per slab and direction):
 //   forward pivots   Sigma_1 = D_1,   Sigma_k  = D_k - L_k Sigma_{k-1}^{-1} U_{k-1}
 //   backward pivots  Lambda_nb = D_nb, Lambda_k = D_k - U_k Lambda_{k+1}^{-1} L_{k+1}
-// and their explicit inverses F_k = Sigma_k^{-1}, B_k = Lambda_k^{-1} are stored.  A third,
+// and their explicit inverses F_k = Sigma_k^{-1}, B_k = Lambda_k^{-1} are stored, each also
+// transposed (thread-per-row products in the single-RHS sweeps need both orientations).  A third,
 // fully parallel pass stores the diagonal blocks of the inverse,
 //     G_k = (A_j^{-1})_{kk} = (Sigma_k + Lambda_k - D_k)^{-1},
 // which lets multi-right-hand-side solves start from any block and single solves run their
@@ -17,12 +18,13 @@
 
 namespace ddst {
 
-// Entry (r, c) of the diagonal block D_k from the stencil pack held in shared memory.
+// Entry (r, c) of the diagonal block D_k from the stencil pack held in shared memory
+// (cxr/tr, cxc/tc: x offset and z index of row r and column c, precomputed by the caller).
 template <typename T>
-__device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int p, int r, int c) {
+__device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int r, int c, int cxr,
+                                    int tr, int cxc, int tc) {
   if (r == c) return pk[PK_DIAG * M + r];
   if (r >= m || c >= m) return T(0);
-  const int cxr = r / p, cxc = c / p, tr = r - cxr * p, tc = c - cxc * p;
   if (tr == tc) {
     if (cxc == cxr - 1) return pk[PK_WEST * M + r];
     if (cxc == cxr + 1) return pk[PK_EAST * M + r];
@@ -101,7 +103,8 @@ template <typename T, int M>
 __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ slabs,
                                                 const int* __restrict__ slab_ids,
                                                 const T* __restrict__ pack, T* __restrict__ F,
-                                                T* __restrict__ B, DevStatus* st) {
+                                                T* __restrict__ B, T* __restrict__ Ft,
+                                                T* __restrict__ Bt, DevStatus* st) {
   constexpr int RP = M / 16;
   const int sid = slab_ids[blockIdx.x];
   const SlabDesc s = slabs[sid];
@@ -116,7 +119,15 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
 #pragma unroll
     for (int cc = 0; cc < RP; ++cc) x[rr][cc] = T(0);
   T* out = (dir == 0 ? F : B) + s.fac_off;
+  T* outT = (dir == 0 ? Ft : Bt) + s.fac_off;
   const int rowfield = dir == 0 ? PK_SOUTH : PK_NORTH;
+  int cxr[RP], trr[RP], cxc[RP], tcc[RP];
+#pragma unroll
+  for (int q = 0; q < RP; ++q) {
+    const int r = ty * RP + q, c = tx * RP + q;
+    cxr[q] = r / s.p; trr[q] = r - cxr[q] * s.p;
+    cxc[q] = c / s.p; tcc[q] = c - cxc[q] * s.p;
+  }
   for (int step = 0; step < s.nb; ++step) {
     const int k = dir == 0 ? step + 1 : s.nb - step;
     const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
@@ -137,18 +148,22 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
 #pragma unroll
       for (int cc = 0; cc < RP; ++cc) {
         const int c = tx * RP + cc;
-        const T d = dblock<T>(s_pk, M, s.m, s.p, r, c);
+        const T d = dblock<T>(s_pk, M, s.m, r, c, cxr[rr], trr[rr], cxc[cc], tcc[cc]);
         x[rr][cc] = step > 0 ? d - rs * x[rr][cc] * s_cpl[c] : d;
       }
     }
     __syncthreads();
     gj_invert<T, M>(x, ty, tx, s_row, s_col, s_thr, st, sid, k);
     T* ob = out + (int64_t)(k - 1) * M * M;
+    T* obT = outT + (int64_t)(k - 1) * M * M;
 #pragma unroll
     for (int rr = 0; rr < RP; ++rr) {
       const int r = ty * RP + rr;
 #pragma unroll
-      for (int cc = 0; cc < RP; ++cc) ob[r * M + tx * RP + cc] = x[rr][cc];
+      for (int cc = 0; cc < RP; ++cc) {
+        ob[r * M + tx * RP + cc] = x[rr][cc];
+        obT[(tx * RP + cc) * M + r] = x[rr][cc];
+      }
     }
   }
 }
@@ -179,6 +194,13 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
   for (int i = threadIdx.x; i < M; i += blockDim.x)
     s_thr[i] = T(1e3) * Eps<T>::v * fabs(s_pk[PK_DIAG * M + i]);
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  int cxr[RP], trr[RP], cxc[RP], tcc[RP];
+#pragma unroll
+  for (int q = 0; q < RP; ++q) {
+    const int r = ty * RP + q, c = tx * RP + q;
+    cxr[q] = r / s.p; trr[q] = r - cxr[q] * s.p;
+    cxc[q] = c / s.p; tcc[q] = c - cxc[q] * s.p;
+  }
   const T* Fp = F + s.fac_off + (int64_t)(k - 2) * M * M;  // F_{k-1}
   const T* Bn = B + s.fac_off + (int64_t)k * M * M;        // B_{k+1}
   T x[RP][RP];
@@ -189,7 +211,7 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
 #pragma unroll
     for (int cc = 0; cc < RP; ++cc) {
       const int c = tx * RP + cc;
-      T v = dblock<T>(s_pk, M, s.m, s.p, r, c);
+      T v = dblock<T>(s_pk, M, s.m, r, c, cxr[rr], trr[rr], cxc[cc], tcc[cc]);
       if (k > 1) v -= ell * Fp[r * M + c] * s_up[c];
       if (k < s.nb) v -= ups * Bn[r * M + c] * s_ln[c];
       x[rr][cc] = v;
@@ -208,26 +230,31 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
 
 template <typename T, int M>
 void launch_factor_M(const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                     const T* pack, T* F, T* B, T* G, DevStatus* st, cudaStream_t s) {
+                     const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st,
+                     cudaStream_t s) {
   if (nids == 0) return;
-  k_factor<T, M><<<dim3(nids, 2), 256, 0, s>>>(d_slabs, d_ids, pack, F, B, st);
+  note_launch();
+  k_factor<T, M><<<dim3(nids, 2), 256, 0, s>>>(d_slabs, d_ids, pack, F, B, Ft, Bt, st);
+  note_launch();
   k_center<T, M><<<dim3(max_nb, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, B, G, st);
 }
 
 template <typename T>
 void launch_factor(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                   const T* pack, T* F, T* B, T* G, DevStatus* st, cudaStream_t s) {
+                   const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st, cudaStream_t s) {
   switch (M) {
-    case 32: launch_factor_M<T, 32>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, st, s); break;
-    case 64: launch_factor_M<T, 64>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, st, s); break;
-    case 128: launch_factor_M<T, 128>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, st, s); break;
+    case 32: launch_factor_M<T, 32>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
+    case 64: launch_factor_M<T, 64>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
+    case 128: launch_factor_M<T, 128>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
     default: break;
   }
 }
 
 template void launch_factor<float>(int, const SlabDesc*, const int*, int, int, const float*,
-                                   float*, float*, float*, DevStatus*, cudaStream_t);
+                                   float*, float*, float*, float*, float*, DevStatus*,
+                                   cudaStream_t);
 template void launch_factor<double>(int, const SlabDesc*, const int*, int, int, const double*,
-                                    double*, double*, double*, DevStatus*, cudaStream_t);
+                                    double*, double*, double*, double*, double*, DevStatus*,
+                                    cudaStream_t);
 
 }  // namespace ddst

@@ -70,6 +70,7 @@ __global__ void k_gradients(const ProbDesc* __restrict__ probs, const double* __
 void launch_gradients(const ProbDesc* d_probs, int nprob, const double* a, const double* g,
                       const double* u, const double* lam, double* dLdg, double* dLda,
                       cudaStream_t st) {
+  note_launch();
   k_gradients<<<dim3(512, nprob), 256, 0, st>>>(d_probs, a, g, u, lam, dLdg, dLda);
 }
 

@@ -230,7 +230,11 @@ __global__ void __launch_bounds__(256) k_sketch(const HItem* __restrict__ items,
 }
 
 // In-place CGS2 orthonormalization of the sketch columns with rank detection (one CTA per
-// block).  Column j is kept (appended as Q[:, r]) when its residual norm exceeds thr.
+// block).  Column j is kept (appended as Q[:, r]) when its residual norm exceeds thr and the
+// working precision can still orthogonalize it: a residual below ~1e3 eps of the sample's own
+// norm is rounding noise, so it is rejected (this floors the effective tolerance at about
+// 1e3 eps_T relative to the block).  A third pass runs when the second one still removed
+// more than 30% of the norm ("twice is enough" test).
 template <typename T>
 __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
                                                     T* __restrict__ UV,
@@ -245,11 +249,29 @@ __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
   T* Q = UV + b.u_off;
   const double thr = tol * snorm[b.sblk];
   const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto norm_y = [&]() -> double {
+    T part = T(0);
+    for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) part = fma(y[i], y[i], part);
+    const double acc = warp_sum((double)part);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) s_nu = sqrt(t);
+    }
+    __syncthreads();
+    const double v = s_nu;
+    __syncthreads();
+    return v;
+  };
   int r = 0;
   for (int j = 0; j < b.s; ++j) {
     for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) y[i] = Q[(int64_t)j * b.p + i];
     __syncthreads();
-    for (int pass = 0; pass < 2 && r > 0; ++pass) {
+    const double n0 = norm_y();
+    double prev = n0, cur = n0;
+    for (int pass = 0; pass < 3 && r > 0; ++pass) {
       for (int c = warp; c < r; c += nw) {
         T part = T(0);
         for (int64_t i = lane; i < b.p; i += 32) part = fma(Q[(int64_t)c * b.p + i], y[i], part);
@@ -263,20 +285,13 @@ __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
         y[i] -= acc;
       }
       __syncthreads();
+      prev = cur;
+      cur = norm_y();
+      if (pass >= 1 && cur >= 0.7 * prev) break;
     }
-    T part = T(0);
-    for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) part = fma(y[i], y[i], part);
-    const double acc = warp_sum((double)part);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-      t = warp_sum(t);
-      if (threadIdx.x == 0) s_nu = sqrt(t);
-    }
-    __syncthreads();
-    const double nu = s_nu;
-    if (nu > thr && r < kmax && r < 256) {
+    const double nu = cur;
+    const double floor_ = 1e3 * (double)Eps<T>::v * n0;
+    if (nu > thr && nu > floor_ && r < kmax && r < 256) {
       const T inv = static_cast<T>(1.0 / nu);
       for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) Q[(int64_t)r * b.p + i] = y[i] * inv;
       ++r;
@@ -362,35 +377,49 @@ __global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __res
 // ---------------------------------------------------------------------------------------------
 // Application
 // ---------------------------------------------------------------------------------------------
-// t_b = W_in^T x_in over the block (W_in = V, or U when transposed): warp per rank column.
+// t_b += W_in^T x_in over one 256-row chunk of W_in (W_in = V, or U when transposed): the
+// chunk of x is staged in shared memory; warp per rank column with 8 independent loads in
+// flight per lane; partial sums folded into FP64 and added atomically (t zeroed by caller).
 template <typename T>
-__global__ void k_h_inner(const HBlock* __restrict__ bl, const T* __restrict__ UV,
-                          const double* __restrict__ x, double* __restrict__ t, int transpose) {
-  const HBlock b = bl[blockIdx.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+__global__ void __launch_bounds__(256) k_h_inner(const HItem* __restrict__ items,
+                                                 const HBlock* __restrict__ bl,
+                                                 const T* __restrict__ UV,
+                                                 const double* __restrict__ x,
+                                                 double* __restrict__ t, int transpose) {
+  const HItem it = items[blockIdx.x];
+  const HBlock b = bl[it.blk];
+  __shared__ T sx[256];
   const int64_t len = transpose ? b.nrows : b.ncols;
-  const T* W = UV + (transpose ? b.u_off : b.v_off);
   const double* xv = x + (transpose ? b.out_if + b.row0 : b.in_if + b.col0);
-  for (int c = warp; c < b.rank; c += nw) {
+  const int64_t lo = it.lo;
+  const int nrow = (int)min((int64_t)256, len - lo);
+  sx[threadIdx.x] = threadIdx.x < nrow ? static_cast<T>(xv[lo + threadIdx.x]) : T(0);
+  __syncthreads();
+  const T* W = UV + (transpose ? b.u_off : b.v_off) + lo;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < b.rank; c += 8) {
     const T* col = W + (int64_t)c * len;
-    double acc = 0.0;
-    T part = T(0);
-    int cnt = 0;
-    for (int64_t i = lane; i < len; i += 32) {
-      part = fma(col[i], static_cast<T>(xv[i]), part);
-      if (++cnt == 32) { acc += (double)part; part = T(0); cnt = 0; }
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int i = lane + 32 * q;
+      v[q] = i < nrow ? col[i] : T(0);
     }
-    acc += (double)part;
-    acc = warp_sum(acc);
-    if (lane == 0) t[b.t_off + c] = acc;
+    T part = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part = fma(v[q], sx[lane + 32 * q], part);
+    const double acc = warp_sum((double)part);
+    if (lane == 0) atomicAdd(&t[b.t_off + c], acc);
   }
 }
 
 // acc_out += W_out t_b (W_out = U, or V when transposed): thread per output row, tiles of 256.
 template <typename T>
-__global__ void k_h_outer(const HItem* __restrict__ items, const HBlock* __restrict__ bl,
-                          const T* __restrict__ UV, const double* __restrict__ t,
-                          double* __restrict__ acc, int transpose) {
+__global__ void __launch_bounds__(256) k_h_outer(const HItem* __restrict__ items,
+                                                 const HBlock* __restrict__ bl,
+                                                 const T* __restrict__ UV,
+                                                 const double* __restrict__ t,
+                                                 double* __restrict__ acc, int transpose) {
   const HItem it = items[blockIdx.x];
   const HBlock b = bl[it.blk];
   __shared__ T st[256];
@@ -399,37 +428,63 @@ __global__ void k_h_outer(const HItem* __restrict__ items, const HBlock* __restr
   const int64_t len = transpose ? b.ncols : b.nrows;
   const int64_t i = it.lo + threadIdx.x;
   if (i >= len) return;
-  const T* W = UV + (transpose ? b.v_off : b.u_off);
-  T a = T(0);
-  for (int c = 0; c < b.rank; ++c) a = fma(W[(int64_t)c * len + i], st[c], a);
+  const T* W = UV + (transpose ? b.v_off : b.u_off) + i;
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int c = 0;
+  for (; c + 3 < b.rank; c += 4) {
+    a0 = fma(W[(int64_t)c * len], st[c], a0);
+    a1 = fma(W[(int64_t)(c + 1) * len], st[c + 1], a1);
+    a2 = fma(W[(int64_t)(c + 2) * len], st[c + 2], a2);
+    a3 = fma(W[(int64_t)(c + 3) * len], st[c + 3], a3);
+  }
+  for (; c < b.rank; ++c) a0 = fma(W[(int64_t)c * len], st[c], a0);
   const int64_t o = transpose ? b.in_if + b.col0 + i : b.out_if + b.row0 + i;
-  atomicAdd(&acc[o], (double)a);
+  atomicAdd(&acc[o], (double)((a0 + a1) + (a2 + a3)));
 }
 
-// Dense leaves: acc_out += D x_in (or D^T).  One CTA per leaf.
+// Dense leaves: acc_out += D x_in (or D^T x_out).  One CTA per leaf; 256 threads = rows x
+// column groups (non-transposed) or warps over columns (transposed).
 template <typename T>
-__global__ void k_h_leaf(const HLeaf* __restrict__ lv, const T* __restrict__ D,
-                         const double* __restrict__ x, double* __restrict__ acc, int transpose) {
+__global__ void __launch_bounds__(256) k_h_leaf(const HLeaf* __restrict__ lv,
+                                                const T* __restrict__ D,
+                                                const double* __restrict__ x,
+                                                double* __restrict__ acc, int transpose) {
   const HLeaf L = lv[blockIdx.x];
   const T* M = D + L.d_off;
+  const int len = (int)L.len;  // <= 256 (leaf size)
+  __shared__ T sx[256];
+  __shared__ double red[256];
+  const double* xv = x + (transpose ? L.out_if : L.in_if) + L.lo;
+  for (int e = threadIdx.x; e < len; e += blockDim.x) sx[e] = static_cast<T>(xv[e]);
+  __syncthreads();
   if (!transpose) {
-    const double* xv = x + L.in_if + L.lo;
-    for (int64_t r = threadIdx.x; r < L.len; r += blockDim.x) {
-      double a = 0.0;
-      for (int64_t c0 = 0; c0 < L.len; c0 += 32) {
-        T part = T(0);
-        const int64_t c1 = min(L.len, c0 + 32);
-        for (int64_t c = c0; c < c1; ++c) part = fma(M[c * L.len + r], static_cast<T>(xv[c]), part);
-        a += (double)part;
+    int rows = 32;
+    while (rows < len) rows <<= 1;
+    const int groups = max(1, 256 / rows);
+    const int r = threadIdx.x % rows, gidx = threadIdx.x / rows;
+    double a = 0.0;
+    if (r < len && gidx < groups) {
+      T p0 = T(0), p1 = T(0);
+      int c = gidx;
+      for (; c + groups < len; c += 2 * groups) {
+        p0 = fma(M[(int64_t)c * len + r], sx[c], p0);
+        p1 = fma(M[(int64_t)(c + groups) * len + r], sx[c + groups], p1);
       }
-      atomicAdd(&acc[L.out_if + L.lo + r], a);
+      for (; c < len; c += groups) p0 = fma(M[(int64_t)c * len + r], sx[c], p0);
+      a = (double)(p0 + p1);
+    }
+    red[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < rows && threadIdx.x < len) {
+      double tot = 0.0;
+      for (int q = 0; q < groups; ++q) tot += red[q * rows + threadIdx.x];
+      atomicAdd(&acc[L.out_if + L.lo + threadIdx.x], tot);
     }
   } else {
-    const double* xv = x + L.out_if + L.lo;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int64_t c = warp; c < L.len; c += nw) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < len; c += 8) {
       T part = T(0);
-      for (int64_t r = lane; r < L.len; r += 32) part = fma(M[c * L.len + r], static_cast<T>(xv[r]), part);
+      for (int r = lane; r < len; r += 32) part = fma(M[(int64_t)c * len + r], sx[r], part);
       const double a = warp_sum((double)part);
       if (lane == 0) atomicAdd(&acc[L.in_if + L.lo + c], a);
     }
@@ -476,10 +531,10 @@ static void launch_sketch(int SC, const HItem* it, int n, const HDev* hb, const 
                           cudaStream_t st) {
   if (n == 0) return;
   switch (SC) {
-    case 32: k_sketch<T, 32><<<n, 256, 0, st>>>(it, hb, S, UV); break;
-    case 64: k_sketch<T, 64><<<n, 256, 0, st>>>(it, hb, S, UV); break;
-    case 96: k_sketch<T, 96><<<n, 256, 0, st>>>(it, hb, S, UV); break;
-    default: k_sketch<T, 128><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    case 32: note_launch(); k_sketch<T, 32><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    case 64: note_launch(); k_sketch<T, 64><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    case 96: note_launch(); k_sketch<T, 96><<<n, 256, 0, st>>>(it, hb, S, UV); break;
+    default: note_launch(); k_sketch<T, 128><<<n, 256, 0, st>>>(it, hb, S, UV); break;
   }
 }
 
@@ -488,10 +543,10 @@ static void launch_project(int SC, const HItem* it, int n, const HDev* hb, const
                            const T* S, T* UV, cudaStream_t st) {
   if (n == 0) return;
   switch (SC) {
-    case 32: k_project<T, 32><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
-    case 64: k_project<T, 64><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
-    case 96: k_project<T, 96><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
-    default: k_project<T, 128><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    case 32: note_launch(); k_project<T, 32><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    case 64: note_launch(); k_project<T, 64><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    case 96: note_launch(); k_project<T, 96><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
+    default: note_launch(); k_project<T, 128><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
   }
 }
 
@@ -503,7 +558,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   H.esz = sizeof(T);
   const int kmax = std::max(1, std::min(hp.k_max, 128));
   const int s_req = std::min(128, kmax + std::max(0, hp.oversample));
-  const int leaf = std::max(8, hp.leaf);
+  const int leaf = std::max(8, std::min(256, hp.leaf));
   // S blocks
   std::vector<SBlk> sb;
   std::vector<int> sb_slab, sb_side;
@@ -597,11 +652,15 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   cudaMemcpyAsync(d_sng, sng.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(H.d_leaves, H.leaves.data(), sizeof(HLeaf) * H.leaves.size(), cudaMemcpyHostToDevice, st);
   // ||S||_2 by power iteration on S^T S (6 steps)
+  note_launch();
   k_sblk_init<<<nsb, 256, 0, st>>>(d_sb, d_x, stride, hp.seed ^ 0x9e3779b97f4a7c15ull);
   const unsigned gr = (unsigned)((max_ng + 255) / 256), gc = (unsigned)((max_ng + 7) / 8);
   for (int itp = 0; itp < 6; ++itp) {
+    note_launch();
     k_sblk_gemv<T><<<dim3(gr, nsb), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
+    note_launch();
     k_sblk_gemv<T><<<dim3(gc, nsb), 256, 0, st>>>(d_sb, S, d_y, d_x, stride, 1);
+    note_launch();
     k_sblk_normalize<<<nsb, 256, 0, st>>>(d_sb, d_x, d_x, stride, d_nrm);
   }
   // d_nrm now holds ||S^T S x|| ~ sigma_max^2
@@ -616,6 +675,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     for (int64_t lo = 0; lo < hd[b].q; lo += 64) pitems.push_back({b, lo});
   const size_t nit = std::max(items.size(), pitems.size());
   if (!al((void**)&d_items, sizeof(HItem) * nit)) { cleanup(); H.release(); msg = "oom"; return 2; }
+  note_launch();
   k_gen_omega<T><<<dim3(32, nblk), 256, 0, st>>>(d_hd, (T*)H.UV, hp.seed);
   cudaMemcpyAsync(d_items, items.data(), sizeof(HItem) * items.size(), cudaMemcpyHostToDevice, st);
   launch_sketch<T>(SC, d_items, (int)items.size(), d_hd, S, (T*)H.UV, st);
@@ -631,10 +691,12 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     const size_t smem = sizeof(T) * maxp;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_range_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launch();
     k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax, d_rank);
   }
   cudaMemcpyAsync(d_items, pitems.data(), sizeof(HItem) * pitems.size(), cudaMemcpyHostToDevice, st);
   launch_project<T>(SC, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
+  note_launch();
   k_copy_leaves<T><<<dim3(16, (unsigned)H.leaves.size()), 256, 0, st>>>(H.d_leaves, d_soff, d_sng, S,
                                                                        (T*)H.D);
   std::vector<int> ranks(nblk);
@@ -680,16 +742,28 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
   cudaMemsetAsync(H.acc, 0, sizeof(double) * H.acc_len, st);
   const int nblk = (int)H.blocks.size();
   if (nblk > 0) {
-    k_h_inner<T><<<nblk, 256, 0, st>>>(H.d_blocks, (const T*)H.UV, x, H.t, transpose);
+    cudaMemsetAsync(H.t, 0, sizeof(double) * H.t_len, st);
+    // inner products run over the input side: V rows (non-transposed) or U rows (transposed)
+    const int ni_in = transpose ? H.n_out_items : H.n_out_items_T;
+    const HItem* in_items = (const HItem*)(transpose ? H.d_out_items : H.d_out_items_T);
+    if (ni_in > 0) {
+      note_launch();
+      k_h_inner<T><<<ni_in, 256, 0, st>>>(in_items, H.d_blocks, (const T*)H.UV, x, H.t, transpose);
+    }
     const int ni = transpose ? H.n_out_items_T : H.n_out_items;
-    if (ni > 0)
+    if (ni > 0) {
+      note_launch();
       k_h_outer<T><<<ni, 256, 0, st>>>(transpose ? (const HItem*)H.d_out_items_T
                                                  : (const HItem*)H.d_out_items,
                                        H.d_blocks, (const T*)H.UV, H.t, H.acc, transpose);
+    }
   }
-  if (!H.leaves.empty())
+  if (!H.leaves.empty()) {
+    note_launch();
     k_h_leaf<T><<<(unsigned)H.leaves.size(), 256, 0, st>>>(H.d_leaves, (const T*)H.D, x, H.acc,
                                                            transpose);
+  }
+  note_launch();
   k_h_finish<<<512, 256, 0, st>>>(x, H.acc, y, H.acc_len);
 }
 

@@ -54,7 +54,7 @@ void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s
 // factor.cu: forward/backward pivot inverses F, B and diagonal inverse blocks G (one size class)
 template <typename T>
 void launch_factor(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                   const T* pack, T* F, T* B, T* G, DevStatus* st, cudaStream_t s);
+                   const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st, cudaStream_t s);
 
 // sweep.cu: explicit transfer operators
 template <typename T>
@@ -66,10 +66,11 @@ void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int 
 
 // solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)
 template <typename T>
+// F, B row-major inverses; Ft, Bt their transposes.
 void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                        const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
-                        T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
-                        cudaStream_t s);
+                        const T* F, const T* B, const T* Ft, const T* Bt, const T* G,
+                        const T* pack, const T* b, T* bf, T* bb, T* x, double* iface,
+                        int transpose, int mode, DevStatus* st, cudaStream_t s);
 
 // krylov.cu
 template <typename T>

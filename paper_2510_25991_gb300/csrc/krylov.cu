@@ -238,9 +238,11 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
       cudaFuncSetAttribute(k_apply_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr = smem;
     }
+    note_launch();
     k_apply_dense<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smem, st>>>(
         d_slabs, d_probs, S, x, y);
   } else {
+    note_launch();
     k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 7) / 8), nslab), 256, 0, st>>>(d_slabs, d_probs,
                                                                                   S, x, y);
   }
@@ -256,33 +258,41 @@ void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, i
                     int nchunk, double* part, double* hpass, double* hcol, int accumulate,
                     cudaStream_t st) {
   const int64_t chunk = (n + nchunk - 1) / nchunk;
+  note_launch();
   k_gs_dots<<<dim3(nchunk, k), 256, 0, st>>>(V, w_in, n, chunk, part);
+  note_launch();
   k_gs_reduce<<<(k + 7) / 8, 256, 0, st>>>(part, nchunk, k, hpass, hcol, accumulate);
+  note_launch();
   k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, w, hpass, k, n, 0);
 }
 
 void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,
                           cudaStream_t st) {
+  note_launch();
   k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, x, y, k, n, 1);
 }
 
 void launch_givens(const double* hcol, const double* hn2, int k, double* H, int ldh, double* cs,
                    double* sn, double* gv, double beta, double* resid, double* inv_hn,
                    cudaStream_t st) {
+  note_launch();
   k_givens<<<1, 32, 0, st>>>(hcol, hn2, k, H, ldh, cs, sn, gv, beta, resid, inv_hn);
 }
 
 void launch_scale_to(const double* w, const double* s, double* out, int64_t n, cudaStream_t st) {
+  note_launch();
   k_scale_to<<<1024, 256, 0, st>>>(w, s, out, n);
 }
 
 void launch_normalize_start(const double* x, const double* nrm2, double* out, int64_t n,
                             cudaStream_t st) {
+  note_launch();
   k_normalize_start<<<1024, 256, 0, st>>>(x, nrm2, out, n);
 }
 
 void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double* y,
                      cudaStream_t st) {
+  note_launch();
   k_trisolve<<<1, 256, kk * sizeof(double), st>>>(H, ldh, gv, kk, y);
 }
 

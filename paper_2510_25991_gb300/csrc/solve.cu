@@ -16,57 +16,66 @@
 
 namespace ddst {
 
+// One sweep of one slab (blockIdx.y = 0: top-down with F, 1: bottom-up with B).  The product
+// y = A v is formed as y[r] = sum_c W[c][r] v[c] with W = A^T row-major (thread per row, no
+// bank conflicts): W = F^T, B^T for A^{-1} sweeps and W = F, B for A^{-T} sweeps.  Each ring
+// stage carries the factor block, the right-hand-side block and the coupling vector of one step
+// (three bulk copies on one mbarrier); the ring is deep enough to keep ~NST steps in flight.
 template <typename T, int M, int NST>
-__global__ void __launch_bounds__(128) k_solve_sweep(const SlabDesc* __restrict__ slabs,
-                                                     const int* __restrict__ ids,
-                                                     const T* __restrict__ F,
-                                                     const T* __restrict__ B,
-                                                     const T* __restrict__ pack,
-                                                     const T* __restrict__ b, T* __restrict__ bf,
-                                                     T* __restrict__ bb, int transpose,
-                                                     DevStatus* st) {
+__global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ slabs,
+                                                   const int* __restrict__ ids,
+                                                   const T* __restrict__ Wf,
+                                                   const T* __restrict__ Wb,
+                                                   const T* __restrict__ pack,
+                                                   const T* __restrict__ b, T* __restrict__ bf,
+                                                   T* __restrict__ bb, int transpose,
+                                                   DevStatus* st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* sF = reinterpret_cast<T*>(smem_raw);   // [NST][M*M]
-  T* sv = sF + NST * M * M;                 // [M] current vector
-  T* sy = sv + M;                           // [M] row results of the warp-per-row product
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sy + M);
+  T* sW = reinterpret_cast<T*>(smem_raw);   // [NST][M*M]
+  T* sB = sW + NST * M * M;                 // [NST][M] right-hand-side block
+  T* sC = sB + NST * M;                     // [NST][M] coupling vector
+  T* sv = sC + NST * M;                     // [M] current vector
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sv + M);
   __shared__ int s_abort;
   const int sid = ids[blockIdx.x];
   const SlabDesc s = slabs[sid];
-  const bool down = blockIdx.y == 0;  // top-down sweep uses F, bottom-up uses B
-  const T* Fac = (down ? F : B) + s.fac_off;
+  const bool down = blockIdx.y == 0;
+  const T* Fac = (down ? Wf : Wb) + s.fac_off;
   T* out = (down ? bf : bb) + s.loc_off;
   const T* rhs = b + s.loc_off;
   const int nb = s.nb;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // coupling field: non-transposed top-down uses ell_k (SOUTH of block k), bottom-up ups_k
-  // (NORTH of block k); transposed top-down ups_{k-1} (NORTH of k-1), bottom-up ell_{k+1}.
+  const int r = threadIdx.x;
   int issued = 0, consumed = 0;
   auto blk_of = [&](int step) { return down ? step + 1 : nb - step; };
-  auto issue = [&](int step) {  // step >= 1 needs factor block of the previous block
+  // coupling: non-transposed top-down ell_k (SOUTH of k), bottom-up ups_k (NORTH of k);
+  // transposed top-down ups_{k-1} (NORTH of k-1), bottom-up ell_{k+1} (SOUTH of k+1).
+  auto issue = [&](int step) {
     ++issued;
     const int k = blk_of(step);
-    const int fidx = down ? k - 2 : k;  // F_{k-1} or B_{k+1}
+    const int fidx = down ? k - 2 : k;
+    int cfield, cblk;
+    if (!transpose) { cfield = down ? PK_SOUTH : PK_NORTH; cblk = k; }
+    else { cfield = down ? PK_NORTH : PK_SOUTH; cblk = down ? k - 1 : k + 1; }
     const int stage = (step - 1) % NST;
-    mbar_arrive_expect_tx(&bar[stage], M * M * sizeof(T));
-    bulk_g2s(sF + stage * M * M, Fac + (int64_t)fidx * M * M, M * M * sizeof(T), &bar[stage]);
+    mbar_arrive_expect_tx(&bar[stage], (M * M + 2 * M) * sizeof(T));
+    bulk_g2s(sW + stage * M * M, Fac + (int64_t)fidx * M * M, M * M * sizeof(T), &bar[stage]);
+    bulk_g2s(sB + stage * M, rhs + (int64_t)(k - 1) * M, M * sizeof(T), &bar[stage]);
+    bulk_g2s(sC + stage * M, pack + s.pack_off + (int64_t)(cblk - 1) * PK_NFIELDS * M + cfield * M,
+             M * sizeof(T), &bar[stage]);
   };
-  if (tid == 0) {
+  if (r == 0) {
     s_abort = 0;
     for (int q = 0; q < NST; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0)
+  if (r == 0)
     for (int q = 1; q <= NST && q < nb; ++q) issue(q);
-  // step 0: bf_1 = b_1 (or bb_nb = b_nb)
   {
     const int k = blk_of(0);
-    for (int c = tid; c < M; c += blockDim.x) {
-      const T v = rhs[(int64_t)(k - 1) * M + c];
-      sv[c] = v;
-      out[(int64_t)(k - 1) * M + c] = v;
-    }
+    const T v = rhs[(int64_t)(k - 1) * M + r];
+    sv[r] = v;
+    out[(int64_t)(k - 1) * M + r] = v;
   }
   __syncthreads();
   for (int step = 1; step < nb; ++step) {
@@ -74,46 +83,27 @@ __global__ void __launch_bounds__(128) k_solve_sweep(const SlabDesc* __restrict_
     const int stage = (step - 1) % NST;
     if (!mbar_wait(&bar[stage], ((step - 1) / NST) & 1, st, sid, k)) s_abort = 1;
     consumed = step;
-    const T* A = sF + stage * M * M;
-    int cfield, cblk;
-    if (!transpose) { cfield = down ? PK_SOUTH : PK_NORTH; cblk = k; }
-    else { cfield = down ? PK_NORTH : PK_SOUTH; cblk = down ? k - 1 : k + 1; }
-    const T* cpl = pack + s.pack_off + (int64_t)(cblk - 1) * PK_NFIELDS * M + cfield * M;
-    T y = T(0);
-    int row = -1;
-    if (!transpose) {
-      // y = A v, warp per row, lanes over columns
-      for (int r = warp; r < M; r += 4) {
-        T part = T(0);
-        for (int c = lane; c < M; c += 32) part += A[r * M + c] * sv[c];
-        part = warp_sum(part);
-        if (lane == 0) sy[r] = part;
-      }
-      __syncthreads();
-      if (tid < M) { y = sy[tid]; row = tid; }
-    } else {
-      // y = A^T v, thread per output row: y[r] = sum_c A[c][r] v[c]
-      if (tid < M) {
-        T acc = T(0);
-        for (int c = 0; c < M; ++c) acc += A[c * M + tid] * sv[c];
-        y = acc;
-        row = tid;
-      }
+    const T* W = sW + stage * M * M;
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+#pragma unroll 8
+    for (int c = 0; c < M; c += 4) {
+      a0 = fma(W[c * M + r], sv[c], a0);
+      a1 = fma(W[(c + 1) * M + r], sv[c + 1], a1);
+      a2 = fma(W[(c + 2) * M + r], sv[c + 2], a2);
+      a3 = fma(W[(c + 3) * M + r], sv[c + 3], a3);
     }
+    const T v = sB[stage * M + r] - sC[stage * M + r] * ((a0 + a1) + (a2 + a3));
     __syncthreads();
     if (s_abort) break;
-    if (row >= 0) {
-      const T v = rhs[(int64_t)(k - 1) * M + row] - cpl[row] * y;
-      sv[row] = v;
-      out[(int64_t)(k - 1) * M + row] = v;
-    }
+    sv[r] = v;
+    out[(int64_t)(k - 1) * M + r] = v;
     __syncthreads();
-    if (tid == 0 && step + NST < nb) {
+    if (r == 0 && step + NST < nb) {
       fence_proxy_async();
       issue(step + NST);
     }
   }
-  if (tid == 0)
+  if (r == 0)
     for (int q = consumed + 1; q <= issued; ++q)
       mbar_wait(&bar[(q - 1) % NST], ((q - 1) / NST) & 1, st, sid, -1);
 }
@@ -168,43 +158,52 @@ __global__ void __launch_bounds__(128) k_solve_combine(const SlabDesc* __restric
 
 template <typename T, int M, int NST>
 static void run_solve(const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                      const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
-                      T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
-                      cudaStream_t s) {
-  const size_t smem = (size_t)NST * M * M * sizeof(T) + 2 * M * sizeof(T) + NST * 8;
+                      const T* F, const T* B, const T* Ft, const T* Bt, const T* G,
+                      const T* pack, const T* b, T* bf, T* bb, T* x, double* iface,
+                      int transpose, int mode, DevStatus* st, cudaStream_t s) {
+  const size_t smem = (size_t)NST * (M * M + 2 * M) * sizeof(T) + M * sizeof(T) + NST * 8;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_solve_sweep<T, M, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     attr = true;
   }
-  k_solve_sweep<T, M, NST><<<dim3(nids, 2), 128, smem, s>>>(d_slabs, d_ids, F, B, pack, b, bf, bb,
-                                                           transpose, st);
+  // A^{-1} sweeps multiply by F, B: pass their transposes (thread-per-row form); A^{-T} sweeps
+  // multiply by F^T, B^T: pass F, B.
+  const T* Wf = transpose ? F : Ft;
+  const T* Wb = transpose ? B : Bt;
+  note_launch();
+  k_solve_sweep<T, M, NST><<<dim3(nids, 2), M, smem, s>>>(d_slabs, d_ids, Wf, Wb, pack, b, bf, bb,
+                                                         transpose, st);
+  note_launch();
   k_solve_combine<T, M><<<dim3(max_nb, nids), 128, 0, s>>>(d_slabs, d_ids, G, b, bf, bb, x, iface,
                                                           transpose, mode);
 }
 
 template <typename T>
 void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                        const T* F, const T* B, const T* G, const T* pack, const T* b, T* bf,
-                        T* bb, T* x, double* iface, int transpose, int mode, DevStatus* st,
-                        cudaStream_t s) {
+                        const T* F, const T* B, const T* Ft, const T* Bt, const T* G,
+                        const T* pack, const T* b, T* bf, T* bb, T* x, double* iface,
+                        int transpose, int mode, DevStatus* st, cudaStream_t s) {
   if (nids == 0) return;
+  // ring depth: ~200 KB of stages in flight per slab sweep
+  constexpr bool F32 = sizeof(T) == 4;
   switch (M) {
-    case 32: run_solve<T, 32, 4>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
-    case 64: run_solve<T, 64, 4>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
-    case 128: run_solve<T, 128, (sizeof(T) == 4 ? 3 : 1)>(d_slabs, d_ids, nids, max_nb, F, B, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    case 32: run_solve<T, 32, F32 ? 24 : 16>(d_slabs, d_ids, nids, max_nb, F, B, Ft, Bt, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    case 64: run_solve<T, 64, F32 ? 11 : 5>(d_slabs, d_ids, nids, max_nb, F, B, Ft, Bt, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
+    case 128: run_solve<T, 128, F32 ? 3 : 1>(d_slabs, d_ids, nids, max_nb, F, B, Ft, Bt, G, pack, b, bf, bb, x, iface, transpose, mode, st, s); break;
     default: break;
   }
 }
 
 template void launch_local_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
                                         const float*, const float*, const float*, const float*,
-                                        float*, float*, float*, double*, int, int, DevStatus*,
-                                        cudaStream_t);
+                                        const float*, const float*, float*, float*, float*,
+                                        double*, int, int, DevStatus*, cudaStream_t);
 template void launch_local_solve<double>(int, const SlabDesc*, const int*, int, int,
                                          const double*, const double*, const double*,
-                                         const double*, const double*, double*, double*, double*,
-                                         double*, int, int, DevStatus*, cudaStream_t);
+                                         const double*, const double*, const double*,
+                                         const double*, double*, double*, double*, double*, int,
+                                         int, DevStatus*, cudaStream_t);
 
 }  // namespace ddst

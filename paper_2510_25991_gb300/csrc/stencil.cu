@@ -360,78 +360,93 @@ template <typename T>
 void launch_stencil_pack(const SlabDesc* d_slabs, int nslab, int max_nb, const ProbDesc* d_probs,
                          const double* a, const double* c, T* pack, cudaStream_t st) {
   dim3 grid(max_nb, nslab);
+  note_launch();
   k_stencil_pack<T><<<grid, 128, 0, st>>>(d_slabs, d_probs, a, c, pack);
 }
 
 void launch_rhs(const ProbDesc* d_probs, int nprob, const double* a, const double* f,
                 const double* g, double* b, cudaStream_t st) {
+  note_launch();
   k_rhs<<<dim3(512, nprob), 256, 0, st>>>(d_probs, a, f, g, b);
 }
 
 void launch_residual(const ProbDesc* d_probs, int nprob, const double* a, const double* c,
                      const double* b, const double* u, double* r, int transpose, double* part,
                      int nblk, cudaStream_t st) {
+  note_launch();
   k_residual<<<dim3(nblk, nprob), 256, 0, st>>>(d_probs, a, c, b, u, r, transpose, part);
 }
 
 template <typename T>
 void launch_gather(const SlabDesc* d_slabs, int nslab, const double* vol, T* loc, cudaStream_t st) {
+  note_launch();
   k_gather<T><<<dim3(64, nslab), 256, 0, st>>>(d_slabs, vol, loc);
 }
 
 template <typename T>
 void launch_gather_owned(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                          const double* vol, T* loc, cudaStream_t st) {
+  note_launch();
   k_gather_owned<T><<<dim3(64, nslab), 256, 0, st>>>(d_slabs, d_probs, vol, loc);
 }
 
 template <typename T>
 void launch_gather_T(const SlabDesc* d_slabs, int nslab, const T* loc, double* vol,
                      cudaStream_t st) {
+  note_launch();
   k_gather_T<T><<<dim3(64, nslab), 256, 0, st>>>(d_slabs, loc, vol);
 }
 
 template <typename T>
 void launch_scatter(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab, const T* loc,
                     double* vol, int mode, cudaStream_t st) {
+  note_launch();
   k_scatter<T><<<dim3(64, nslab), 256, 0, st>>>(d_slabs, d_probs, loc, vol, mode);
 }
 
 template <typename T>
 void launch_extract_center(const SlabDesc* d_slabs, int nslab, const T* loc, double* iface,
                            cudaStream_t st) {
+  note_launch();
   k_extract_center<T><<<dim3(16, nslab), 256, 0, st>>>(d_slabs, loc, iface);
 }
 
 template <typename T>
 void launch_inject_center(const SlabDesc* d_slabs, int nslab, const double* iface, T* loc,
                           cudaStream_t st) {
+  note_launch();
   k_inject_center<T><<<dim3(16, nslab), 256, 0, st>>>(d_slabs, iface, loc);
 }
 
 template <typename T>
 void launch_add_iface_dirichlet(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                                 const T* pack, const double* uG, T* loc, cudaStream_t st) {
+  note_launch();
   k_add_iface_dirichlet<T><<<dim3(16, nslab), 256, 0, st>>>(d_slabs, d_probs, pack, uG, loc);
 }
 
 template <typename T>
 void launch_iface_dirichlet_T(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                               const T* pack, const T* loc, double* out, cudaStream_t st) {
+  note_launch();
   k_iface_dirichlet_T<T><<<dim3(16, nslab), 256, 0, st>>>(d_slabs, d_probs, pack, loc, out);
 }
 
 void launch_dot(const double* x, const double* y, int64_t n, double* part, int nblk,
                 double* out, cudaStream_t st) {
+  note_launch();
   k_dot_partial<<<nblk, 256, 0, st>>>(x, y, n, part);
+  note_launch();
   k_sum_partials<<<1, 256, 0, st>>>(part, nblk, out);
 }
 
 void launch_sum_partials(const double* part, int np, double* out, cudaStream_t st) {
+  note_launch();
   k_sum_partials<<<1, 256, 0, st>>>(part, np, out);
 }
 
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
+  note_launch();
   k_axpy<<<1024, 256, 0, st>>>(n, a, x, y);
 }
 

@@ -221,6 +221,7 @@ static void run_sbuild(const SlabDesc* d_slabs, const TileDesc* d_tiles, int nti
                          (int)C::SMEM);
     attr = true;
   }
+  note_launch();
   k_sbuild<T, M, R, NST><<<ntiles, C::THREADS, C::SMEM, s>>>(d_slabs, d_tiles, F, B, G, pack, S, st);
 }
 

@@ -14,7 +14,8 @@ from . import _lib as L
 __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
-           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_last_error",
+           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_kernel_launches",
+           "ddst_last_error",
            "ddst_destroy", "Solver", "DDSTSolve"]
 
 
@@ -167,6 +168,10 @@ def ddst_query(ctx, prob=0):
     nds, ng, mr = C.c_int(), C.c_int64(), C.c_int()
     _check(lib, ctx, lib.ddst_query(ctx, prob, C.byref(nds), C.byref(ng), C.byref(mr)))
     return nds.value, ng.value, mr.value
+
+
+def ddst_kernel_launches():
+    return int(L.load().ddst_kernel_launches())
 
 
 def ddst_last_error(ctx=None):

@@ -109,4 +109,5 @@ def test_hodlr_transpose_apply(precision):
     D.ddst_apply_interface(sol.ctx, 0, x, ax, False)
     D.ddst_apply_interface(sol.ctx, 0, y, aty, True)
     sol.close()
-    assert abs(ax @ y - x @ aty) <= (1e-12 if precision == "fp64" else 1e-6) * abs(ax @ y)
+    # FP32 factors: both sides round differently, ~sqrt(terms) u_32 relative
+    assert abs(ax @ y - x @ aty) <= (1e-12 if precision == "fp64" else 2e-5) * abs(ax @ y)
