@@ -77,7 +77,9 @@ typedef struct {
 
 typedef struct {
   int precision;        /* DDST_FP64 or DDST_MIXED                                            */
-  double gmres_tol;     /* relative residual target of each interface GMRES solve             */
+  double gmres_tol;     /* relative residual target of each interface GMRES solve; <= 0 picks
+                           1e-2 for DDST_MIXED (inner solve of the refinement) or 1e-10 for
+                           DDST_FP64                                                          */
   int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES)                           */
   double refine_tol;    /* stop when ||correction|| <= refine_tol * ||u|| (FP64 refinement)   */
   int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
@@ -103,7 +105,7 @@ typedef struct {
   int fail_block;         /* its block (y index, 1-based), else -1                            */
 } ddst_info;
 
-/* Fills *opt with defaults: MIXED, gmres_tol 1e-6 (1e-11 for FP64), refine_tol 1e-9,
+/* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
  * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234. */
 void ddst_options_default(ddst_options* opt);
 

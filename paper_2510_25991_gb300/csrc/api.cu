@@ -189,6 +189,10 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   if (opt) ctx->opt = *opt; else ddst_options_default(&ctx->opt);
   ctx->prec = ctx->opt.precision == DDST_FP64 ? DDST_FP64 : DDST_MIXED;
   ctx->esz = ctx->prec == DDST_FP64 ? 8 : 4;
+  // automatic inner tolerance: the FP32 DD solve is only an approximate inverse (refinement
+  // contracts by ~10x per step), so solving its interface system beyond 1e-2 is wasted work;
+  // the FP64 DD solve is accurate, so a tight inner tolerance finishes in one or two steps.
+  if (!(ctx->opt.gmres_tol > 0.0)) ctx->opt.gmres_tol = ctx->prec == DDST_FP64 ? 1e-10 : 1e-2;
   int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, pack_off = 0, loc_off = 0, s_off = 0;
   for (int q = 0; q < nprob; ++q) {
     const ddst_grid& gr = grids[q];
@@ -735,7 +739,7 @@ void ddst_options_default(ddst_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
   opt->precision = DDST_MIXED;
-  opt->gmres_tol = 1e-6;
+  opt->gmres_tol = 0.0;  // automatic: 1e-2 (MIXED) or 1e-10 (FP64)
   opt->gmres_max_iter = 1000;
   opt->refine_tol = 1e-9;
   opt->refine_max = 8;

@@ -36,136 +36,207 @@ __device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int 
   return T(0);
 }
 
-// In-place Gauss-Jordan inversion of an M x M matrix held in registers by 256 threads
-// (16 x 16 thread grid, RP x RP patch each).  One barrier per pivot (double-buffered pivot
-// row/column).  Pivot magnitude check against thr[] (per row, shared memory).
+// ---------------------------------------------------------------------------------------------
+// Blocked Gauss-Jordan inversion in shared memory (block pivots of 16): the 16 x 16 pivot
+// block is inverted by warp 0 (warp-synchronous, no pivoting), then the pivot row panel
+// R = P^{-1} X(q, :), the column panel C = X(:, q) and the trailing update
+// X(i, j) -= C(i, :) R(:, j), X(i, q) = -C(i, :) P^{-1} run on all 256 threads as small GEMMs.
+// Three block barriers per 16 pivots.  X has leading dimension LD = M + 4 (16-byte rows).
+// The trailing update runs over 4 x 4 patches distributed round-robin over the threads.
+// ---------------------------------------------------------------------------------------------
 template <typename T, int M>
-__device__ __forceinline__ void gj_invert(T (&x)[M / 16][M / 16], int ty, int tx,
-                                          T* __restrict__ s_row, T* __restrict__ s_col,
-                                          const T* __restrict__ thr, DevStatus* st, int slab,
-                                          int block) {
-  constexpr int RP = M / 16;
-  for (int p = 0; p < M; ++p) {
-    const int buf = (p & 1) * M;
-    const int owner = p / RP, pi = p - owner * RP;
-    if (ty == owner) {
-#pragma unroll
-      for (int rr = 0; rr < RP; ++rr)
-        if (rr == pi) {
-#pragma unroll
-          for (int cc = 0; cc < RP; ++cc) s_row[buf + tx * RP + cc] = x[rr][cc];
+struct BGJ {
+  static constexpr int LD = M + 4;
+  static constexpr int NB = 16;
+  static constexpr size_t smem_elems = (size_t)M * LD + (size_t)M * (NB + 1) + (size_t)NB * LD;
+};
+
+template <typename T, int M>
+__device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp,
+                                           T* __restrict__ Rp, const T* __restrict__ thr,
+                                           DevStatus* st, int slab, int block) {
+  using G = BGJ<T, M>;
+  constexpr int LD = G::LD, NB = G::NB;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int q0 = 0; q0 < M; q0 += NB) {
+    // (a) warp 0 inverts the pivot block in place; lane owns row lane/2, 8 columns
+    if (warp == 0) {
+      const int r = lane >> 1, c0 = (lane & 1) * 8;
+      T* P = X + q0 * LD + q0;
+      for (int pp = 0; pp < NB; ++pp) {
+        T piv = P[pp * LD + pp];
+        const T lim = thr[q0 + pp];
+        if (!(fabs(piv) > lim)) {
+          if (lane == 0) set_status(st, ST_SINGULAR, slab, block);
+          piv = (piv < T(0)) ? -lim : lim;
+          if (lim == T(0)) piv = T(1);
         }
-    }
-    if (tx == owner) {
+        const T inv = T(1) / piv;
+        const T f = P[r * LD + pp];
+        T prow[8];
 #pragma unroll
-      for (int cc = 0; cc < RP; ++cc)
-        if (cc == pi) {
-#pragma unroll
-          for (int rr = 0; rr < RP; ++rr) s_col[buf + ty * RP + rr] = x[rr][cc];
+        for (int e = 0; e < 8; ++e) {
+          const int c = c0 + e;
+          prow[e] = (c == pp ? T(1) : P[pp * LD + c]) * inv;
         }
-    }
-    __syncthreads();
-    T piv = s_row[buf + p];
-    const T lim = thr[p];
-    if (!(fabs(piv) > lim)) {  // also catches NaN
-      if (threadIdx.x == 0) set_status(st, ST_SINGULAR, slab, block);
-      piv = (piv < T(0)) ? -lim : lim;
-      if (lim == T(0)) piv = T(1);
-    }
-    const T inv = T(1) / piv;
-    T prow[RP], fcol[RP];
+        __syncwarp();
 #pragma unroll
-    for (int cc = 0; cc < RP; ++cc) {
-      const int c = tx * RP + cc;
-      prow[cc] = (c == p ? T(1) : s_row[buf + c]) * inv;
-    }
-#pragma unroll
-    for (int rr = 0; rr < RP; ++rr) fcol[rr] = s_col[buf + ty * RP + rr];
-#pragma unroll
-    for (int rr = 0; rr < RP; ++rr) {
-      const int r = ty * RP + rr;
-#pragma unroll
-      for (int cc = 0; cc < RP; ++cc) {
-        const int c = tx * RP + cc;
-        if (r == p)
-          x[rr][cc] = prow[cc];
-        else
-          x[rr][cc] = (c == p ? T(0) : x[rr][cc]) - fcol[rr] * prow[cc];
+        for (int e = 0; e < 8; ++e) {
+          const int c = c0 + e;
+          const T old = P[r * LD + c];
+          P[r * LD + c] = (r == pp) ? prow[e] : ((c == pp ? T(0) : old) - f * prow[e]);
+        }
+        __syncwarp();
       }
     }
+    __syncthreads();
+    // (b) column panel C = X(:, q) (old values; block rows unused) and row panel R = P^{-1} X(q, :)
+    for (int e = tid; e < M * NB; e += blockDim.x) {
+      const int i = e / NB, t = e - i * NB;
+      Cp[i * (NB + 1) + t] = X[i * LD + q0 + t];
+    }
+    for (int e = tid; e < NB * M; e += blockDim.x) {
+      const int t = e / M, j = e - t * M;
+      T acc = T(0);
+      if (j < q0 || j >= q0 + NB) {
+#pragma unroll
+        for (int s2 = 0; s2 < NB; ++s2) acc = fma(X[(q0 + t) * LD + q0 + s2], X[(q0 + s2) * LD + j], acc);
+      }
+      Rp[t * LD + j] = acc;
+    }
+    __syncthreads();
+    // (c) trailing update on 4 x 4 patches (patch index -> rows 4*pi.., columns 4*pj..)
+    for (int pidx = tid; pidx < (M / 4) * (M / 4); pidx += blockDim.x) {
+      {
+        const int i0 = (pidx / (M / 4)) * 4, j0 = (pidx % (M / 4)) * 4;
+        const bool in_i = (i0 >= q0 && i0 < q0 + NB), in_j = (j0 >= q0 && j0 < q0 + NB);
+        if (in_i && in_j) continue;
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+        if (in_i) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] = Rp[(i0 + a - q0) * LD + j0 + b];
+          continue;
+        }
+        // rows outside the pivot block: need C(i, :) and either R(:, j) or P^{-1}(:, j)
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+          T cv[4], rv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) cv[a] = Cp[(i0 + a) * (NB + 1) + t];
+          const T* src = in_j ? (X + (q0 + t) * LD + j0) : (Rp + t * LD + j0);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) rv[b] = src[b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(cv[a], rv[b], acc[a][b]);
+        }
+        if (in_j) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] = -acc[a][b];
+        } else {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] -= acc[a][b];
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
+}
+
+// Writes X (shared, LD) as a row-major M x M block to `dst` and, if dstT, its transpose.
+template <typename T, int M>
+__device__ __forceinline__ void store_block(const T* __restrict__ X, T* __restrict__ dst,
+                                            T* __restrict__ dstT) {
+  constexpr int LD = BGJ<T, M>::LD;
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int i = e / M, j = e - i * M;
+    dst[e] = X[i * LD + j];
+    if (dstT) dstT[e] = X[j * LD + i];
+  }
 }
 
 // Forward (blockIdx.y == 0) or backward (== 1) pivot sweep of one slab (blockIdx.x indexes
-// slab_ids, the slabs of this block-size class).
+// slab_ids, the slabs of this block-size class).  The stencil pack of the next block is
+// prefetched by a bulk copy while the current block is inverted.
 template <typename T, int M>
 __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ slabs,
                                                 const int* __restrict__ slab_ids,
                                                 const T* __restrict__ pack, T* __restrict__ F,
                                                 T* __restrict__ B, T* __restrict__ Ft,
                                                 T* __restrict__ Bt, DevStatus* st) {
-  constexpr int RP = M / 16;
+  using G = BGJ<T, M>;
+  constexpr int LD = G::LD;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* Cp = X + M * LD;
+  T* Rp = Cp + M * (G::NB + 1);
+  T* pk = Rp + G::NB * LD;              // [3][PK_NFIELDS * M]: ring (previous, current, next)
+  T* thr = pk + 3 * PK_NFIELDS * M;     // [M]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(thr + M);  // [3]
   const int sid = slab_ids[blockIdx.x];
   const SlabDesc s = slabs[sid];
   const int dir = blockIdx.y;
-  __shared__ T s_pk[PK_NFIELDS * M];
-  __shared__ T s_cpl[M];
-  __shared__ T s_row[2 * M], s_col[2 * M], s_thr[M];
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  T x[RP][RP];
-#pragma unroll
-  for (int rr = 0; rr < RP; ++rr)
-#pragma unroll
-    for (int cc = 0; cc < RP; ++cc) x[rr][cc] = T(0);
   T* out = (dir == 0 ? F : B) + s.fac_off;
   T* outT = (dir == 0 ? Ft : Bt) + s.fac_off;
-  const int rowfield = dir == 0 ? PK_SOUTH : PK_NORTH;
-  int cxr[RP], trr[RP], cxc[RP], tcc[RP];
-#pragma unroll
-  for (int q = 0; q < RP; ++q) {
-    const int r = ty * RP + q, c = tx * RP + q;
-    cxr[q] = r / s.p; trr[q] = r - cxr[q] * s.p;
-    cxc[q] = c / s.p; tcc[q] = c - cxc[q] * s.p;
+  const int rowfield = dir == 0 ? PK_SOUTH : PK_NORTH;   // ell_k (fwd) or ups_k (bwd)
+  const int colfield = dir == 0 ? PK_NORTH : PK_SOUTH;   // ups_{k-1} (fwd) or ell_{k+1} (bwd)
+  const uint32_t pbytes = PK_NFIELDS * M * sizeof(T);
+  auto blk = [&](int step) { return dir == 0 ? step + 1 : s.nb - step; };
+  auto issue = [&](int step) {
+    const int k = blk(step);
+    mbar_arrive_expect_tx(&bar[step % 3], pbytes);
+    bulk_g2s(pk + (step % 3) * PK_NFIELDS * M, pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M,
+             pbytes, &bar[step % 3]);
+  };
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 3; ++q) mbar_init(&bar[q], 1);
+    fence_mbar_init();
   }
+  __syncthreads();
+  if (threadIdx.x == 0) issue(0);
+  int waited = 0, issued = 1;
+  bool ok = true;
   for (int step = 0; step < s.nb; ++step) {
-    const int k = dir == 0 ? step + 1 : s.nb - step;
-    const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
-    for (int i = threadIdx.x; i < PK_NFIELDS * M; i += blockDim.x) s_pk[i] = pk[i];
-    if (step > 0) {
-      const int kp = dir == 0 ? k - 1 : k + 1;
-      const T* pp = pack + s.pack_off + (int64_t)(kp - 1) * PK_NFIELDS * M;
-      for (int i = threadIdx.x; i < M; i += blockDim.x)
-        s_cpl[i] = pp[(dir == 0 ? PK_NORTH : PK_SOUTH) * M + i];
+    const int k = blk(step);
+    if (!mbar_wait(&bar[step % 3], (step / 3) & 1, st, sid, k)) ok = false;
+    waited = step + 1;
+    __syncthreads();
+    if (!ok) break;
+    if (threadIdx.x == 0 && step + 1 < s.nb) {
+      fence_proxy_async();
+      issue(step + 1);
+      ++issued;
+    }
+    const T* cur = pk + (step % 3) * PK_NFIELDS * M;
+    const T* prv = pk + ((step + 2) % 3) * PK_NFIELDS * M;   // previous block (step - 1)
+    for (int i = threadIdx.x; i < M; i += blockDim.x) thr[i] = T(1e3) * Eps<T>::v * fabs(cur[PK_DIAG * M + i]);
+    // Sigma_k = D_k - diag(ell_k) F_{k-1} diag(ups_{k-1})   (backward: ups_k, B_{k+1}, ell_{k+1})
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+      const int r = e / M, c = e - r * M;
+      const int cxr = r / s.p, tr = r - cxr * s.p, cxc = c / s.p, tc = c - cxc * s.p;
+      T d = dblock<T>(cur, M, s.m, r, c, cxr, tr, cxc, tc);
+      if (step > 0) d -= cur[rowfield * M + r] * X[r * LD + c] * prv[colfield * M + c];
+      X[r * LD + c] = d;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < M; i += blockDim.x)
-      s_thr[i] = T(1e3) * Eps<T>::v * fabs(s_pk[PK_DIAG * M + i]);
-#pragma unroll
-    for (int rr = 0; rr < RP; ++rr) {
-      const int r = ty * RP + rr;
-      const T rs = s_pk[rowfield * M + r];
-#pragma unroll
-      for (int cc = 0; cc < RP; ++cc) {
-        const int c = tx * RP + cc;
-        const T d = dblock<T>(s_pk, M, s.m, r, c, cxr[rr], trr[rr], cxc[cc], tcc[cc]);
-        x[rr][cc] = step > 0 ? d - rs * x[rr][cc] * s_cpl[c] : d;
-      }
-    }
+    bgj_invert<T, M>(X, Cp, Rp, thr, st, sid, k);
+    store_block<T, M>(X, out + (int64_t)(k - 1) * M * M, outT + (int64_t)(k - 1) * M * M);
     __syncthreads();
-    gj_invert<T, M>(x, ty, tx, s_row, s_col, s_thr, st, sid, k);
-    T* ob = out + (int64_t)(k - 1) * M * M;
-    T* obT = outT + (int64_t)(k - 1) * M * M;
-#pragma unroll
-    for (int rr = 0; rr < RP; ++rr) {
-      const int r = ty * RP + rr;
-#pragma unroll
-      for (int cc = 0; cc < RP; ++cc) {
-        ob[r * M + tx * RP + cc] = x[rr][cc];
-        obT[(tx * RP + cc) * M + r] = x[rr][cc];
-      }
-    }
   }
+  if (threadIdx.x == 0)
+    for (int q = waited; q < issued; ++q) mbar_wait(&bar[q % 3], (q / 3) & 1, st, sid, -1);
 }
 
 // Diagonal blocks of the inverse: G_k = (D_k - L_k F_{k-1} U_{k-1} - U_k B_{k+1} L_{k+1})^{-1}.
@@ -175,57 +246,42 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
                                                 const int* __restrict__ slab_ids,
                                                 const T* __restrict__ pack,
                                                 const T* __restrict__ F, const T* __restrict__ B,
-                                                T* __restrict__ G, DevStatus* st) {
-  constexpr int RP = M / 16;
+                                                T* __restrict__ Gout, DevStatus* st) {
+  using G = BGJ<T, M>;
+  constexpr int LD = G::LD;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);
+  T* Cp = X + M * LD;
+  T* Rp = Cp + M * (G::NB + 1);
+  T* pk = Rp + G::NB * LD;          // [PK_NFIELDS * M]
+  T* thr = pk + PK_NFIELDS * M;     // [M]
+  T* up = thr + M;                  // ups_{k-1}
+  T* ln = up + M;                   // ell_{k+1}
   const int sid = slab_ids[blockIdx.y];
   const SlabDesc s = slabs[sid];
   const int k = blockIdx.x + 1;
   if (k > s.nb) return;
-  __shared__ T s_pk[PK_NFIELDS * M];
-  __shared__ T s_up[M], s_ln[M];  // ups_{k-1} (cols of forward term), ell_{k+1} (backward term)
-  __shared__ T s_row[2 * M], s_col[2 * M], s_thr[M];
-  const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
-  for (int i = threadIdx.x; i < PK_NFIELDS * M; i += blockDim.x) s_pk[i] = pk[i];
+  const T* pkg = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
+  for (int i = threadIdx.x; i < PK_NFIELDS * M; i += blockDim.x) pk[i] = pkg[i];
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    s_up[i] = k > 1 ? pack[s.pack_off + (int64_t)(k - 2) * PK_NFIELDS * M + PK_NORTH * M + i] : T(0);
-    s_ln[i] = k < s.nb ? pack[s.pack_off + (int64_t)k * PK_NFIELDS * M + PK_SOUTH * M + i] : T(0);
+    up[i] = k > 1 ? pack[s.pack_off + (int64_t)(k - 2) * PK_NFIELDS * M + PK_NORTH * M + i] : T(0);
+    ln[i] = k < s.nb ? pack[s.pack_off + (int64_t)k * PK_NFIELDS * M + PK_SOUTH * M + i] : T(0);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < M; i += blockDim.x)
-    s_thr[i] = T(1e3) * Eps<T>::v * fabs(s_pk[PK_DIAG * M + i]);
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  int cxr[RP], trr[RP], cxc[RP], tcc[RP];
-#pragma unroll
-  for (int q = 0; q < RP; ++q) {
-    const int r = ty * RP + q, c = tx * RP + q;
-    cxr[q] = r / s.p; trr[q] = r - cxr[q] * s.p;
-    cxc[q] = c / s.p; tcc[q] = c - cxc[q] * s.p;
-  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) thr[i] = T(1e3) * Eps<T>::v * fabs(pk[PK_DIAG * M + i]);
   const T* Fp = F + s.fac_off + (int64_t)(k - 2) * M * M;  // F_{k-1}
   const T* Bn = B + s.fac_off + (int64_t)k * M * M;        // B_{k+1}
-  T x[RP][RP];
-#pragma unroll
-  for (int rr = 0; rr < RP; ++rr) {
-    const int r = ty * RP + rr;
-    const T ell = s_pk[PK_SOUTH * M + r], ups = s_pk[PK_NORTH * M + r];
-#pragma unroll
-    for (int cc = 0; cc < RP; ++cc) {
-      const int c = tx * RP + cc;
-      T v = dblock<T>(s_pk, M, s.m, r, c, cxr[rr], trr[rr], cxc[cc], tcc[cc]);
-      if (k > 1) v -= ell * Fp[r * M + c] * s_up[c];
-      if (k < s.nb) v -= ups * Bn[r * M + c] * s_ln[c];
-      x[rr][cc] = v;
-    }
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int r = e / M, c = e - r * M;
+    const int cxr = r / s.p, tr = r - cxr * s.p, cxc = c / s.p, tc = c - cxc * s.p;
+    T v = dblock<T>(pk, M, s.m, r, c, cxr, tr, cxc, tc);
+    if (k > 1) v -= pk[PK_SOUTH * M + r] * Fp[e] * up[c];
+    if (k < s.nb) v -= pk[PK_NORTH * M + r] * Bn[e] * ln[c];
+    X[r * LD + c] = v;
   }
   __syncthreads();
-  gj_invert<T, M>(x, ty, tx, s_row, s_col, s_thr, st, sid, k);
-  T* ob = G + s.fac_off + (int64_t)(k - 1) * M * M;
-#pragma unroll
-  for (int rr = 0; rr < RP; ++rr) {
-    const int r = ty * RP + rr;
-#pragma unroll
-    for (int cc = 0; cc < RP; ++cc) ob[r * M + tx * RP + cc] = x[rr][cc];
-  }
+  bgj_invert<T, M>(X, Cp, Rp, thr, st, sid, k);
+  store_block<T, M>(X, Gout + s.fac_off + (int64_t)(k - 1) * M * M, nullptr);
 }
 
 template <typename T, int M>
@@ -233,10 +289,20 @@ void launch_factor_M(const SlabDesc* d_slabs, const int* d_ids, int nids, int ma
                      const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st,
                      cudaStream_t s) {
   if (nids == 0) return;
+  using Gc = BGJ<T, M>;
+  const size_t base = Gc::smem_elems * sizeof(T);
+  const size_t sm_f = base + (3 * PK_NFIELDS * M + M) * sizeof(T) + 24;
+  const size_t sm_c = base + (PK_NFIELDS * M + 3 * M) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_factor<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f);
+    cudaFuncSetAttribute(k_center<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+    attr = true;
+  }
   note_launch();
-  k_factor<T, M><<<dim3(nids, 2), 256, 0, s>>>(d_slabs, d_ids, pack, F, B, Ft, Bt, st);
+  k_factor<T, M><<<dim3(nids, 2), 256, sm_f, s>>>(d_slabs, d_ids, pack, F, B, Ft, Bt, st);
   note_launch();
-  k_center<T, M><<<dim3(max_nb, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, B, G, st);
+  k_center<T, M><<<dim3(max_nb, nids), 256, sm_c, s>>>(d_slabs, d_ids, pack, F, B, G, st);
 }
 
 template <typename T>

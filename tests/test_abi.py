@@ -44,4 +44,4 @@ def test_options_default_without_gpu():
     from paper_2510_25991_gb300 import ddst as D
     o = D.ddst_options_default()
     assert o.precision == 1 and o.k_max == 64 and o.oversample == 10 and o.leaf_size == 128
-    assert 0 < o.gmres_tol < 1e-3 and o.refine_max >= 1
+    assert o.gmres_tol == 0.0 and o.refine_max >= 1  # automatic inner tolerance
