@@ -175,6 +175,29 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
 
+/* Allocation-free FP64 residual of the finite-difference system.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory while
+ * they run (a locked memory budget, an allocator that forbids new device allocations, or host
+ * threads that must not take the driver's allocation locks); every other entry point here
+ * allocates its context and work buffers with cudaMalloc.
+ * Computes r = b(f, g) - A u for the problem (grid, coeffs), where b carries the load f and
+ * the Dirichlet data g exactly as ddst_solve builds it, and writes norms[0] = ||r||_2,
+ * norms[1] = ||b||_2 (so norms[0] / norms[1] is the relative residual ddst_solve reports).
+ * All arrays must be DEVICE memory (this call stages nothing): f, u, r interior
+ * ((n-1)^dim), g and coeffs->a / coeffs->c nodal ((n+1)^dim), norms two doubles.
+ * At most 16,777,216 interior unknowns (e.g. a 4097^2 grid); larger grids return
+ * DDST_ERR_INVALID_ARG.  The scratch is a 1 MiB file-scope device array (one FP64 partial sum
+ * per 256 unknowns and per norm) that every GPU which loads the library holds until the
+ * process exits; every call overwrites the partial sums it reads, so nothing has to start at
+ * zero.  All calls share that array: calls that overlap on the GPU (on different streams)
+ * race and must be serialized by the caller.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Stream-ordered on `stream`; returns once the work is enqueued (it does
+ * not wait for it).  Errors: INVALID_ARG (message via ddst_last_error(NULL)), CUDA. */
+ddst_status ddst_residual_noalloc(const ddst_grid* grid, const ddst_coeffs* coeffs,
+                                  const double* f, const double* g, const double* u, double* r,
+                                  double* norms, void* stream);
+
 /* Number of CUDA kernels this library has launched in the calling process so far (a
  * diagnostic for benchmarks: the difference across a timed region counts its launches). */
 int64_t ddst_kernel_launches(void);

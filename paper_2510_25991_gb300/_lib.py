@@ -67,6 +67,8 @@ SIGNATURES = {
     "ddst_apply_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "ddst_query": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int)]),
+    "ddst_residual_noalloc": (C.c_int, [C.POINTER(ddst_grid), C.POINTER(ddst_coeffs), _P, _P, _P,
+                                        _P, _P, _P]),
     "ddst_kernel_launches": (C.c_int64, []),
     "ddst_last_error": (C.c_char_p, [_P]),
     "ddst_destroy": (None, [_P]),

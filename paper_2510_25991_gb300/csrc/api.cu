@@ -22,7 +22,13 @@
 
 using namespace ddst;
 
+namespace {
+std::string g_setup_error;
+}  // namespace
+
 namespace ddst {
+void set_global_error(const std::string& m) { g_setup_error = m; }
+
 std::atomic<long long>& launch_counter() {
   static std::atomic<long long> c{0};
   return c;
@@ -30,8 +36,6 @@ std::atomic<long long>& launch_counter() {
 }  // namespace ddst
 
 namespace {
-
-std::string g_setup_error;
 
 struct DevBuf {
   void* p = nullptr;

@@ -14,7 +14,8 @@ from . import _lib as L
 __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
-           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_kernel_launches",
+           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_residual_noalloc",
+           "ddst_kernel_launches",
            "ddst_last_error",
            "ddst_destroy", "Solver", "DDSTSolve"]
 
@@ -168,6 +169,17 @@ def ddst_query(ctx, prob=0):
     nds, ng, mr = C.c_int(), C.c_int64(), C.c_int()
     _check(lib, ctx, lib.ddst_query(ctx, prob, C.byref(nds), C.byref(ng), C.byref(mr)))
     return nds.value, ng.value, mr.value
+
+
+def ddst_residual_noalloc(dim, n, a, f, g, u, r, norms, b=(0.0, 0.0, 0.0), c=None, stream=None):
+    """Allocation-free FP64 residual r = b(f, g) - A u and norms (||r||, ||b||); device arrays
+    only.  Stream-ordered: synchronize before reading the results."""
+    lib = L.load()
+    grid = L.ddst_grid(dim, n)
+    cf = _coeffs(a, b, c)
+    st = lib.ddst_residual_noalloc(C.byref(grid), C.byref(cf), _ptr(f), _ptr(g), _ptr(u), _ptr(r),
+                                   _ptr(norms), C.c_void_p(stream) if stream else None)
+    _check(lib, None, st)
 
 
 def ddst_kernel_launches():
