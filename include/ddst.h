@@ -56,8 +56,13 @@ typedef enum {
 /* Arithmetic of the local operators, transfer operators and their application. */
 enum {
   DDST_FP64 = 0,   /* everything FP64                                                      */
-  DDST_MIXED = 1   /* FP32 factors, FP32 transfer operators (FP32 accumulation),
+  DDST_MIXED = 1,  /* FP32 factors, FP32 transfer operators (FP32 accumulation),
                       FP64 GMRES vectors, FP64 global residual refinement                  */
+  DDST_AUTO = 2    /* DDST_MIXED, or DDST_FP64 when an FP32 pivot falls below its floor
+                      (1e3 eps |diag|).  The block elimination does not pivot, so this
+                      happens only for indefinite local operators (Helmholtz slabs wider
+                      than about half a wavelength) whose leading block minors pass near
+                      zero; ddst_get_precision reports which one was used.                */
 };
 
 typedef struct ddst_ctx ddst_ctx;
@@ -76,7 +81,7 @@ typedef struct {
 } ddst_coeffs;
 
 typedef struct {
-  int precision;        /* DDST_FP64 or DDST_MIXED                                            */
+  int precision;        /* DDST_FP64, DDST_MIXED or DDST_AUTO                                 */
   double gmres_tol;     /* relative residual target of each interface GMRES solve; <= 0 picks
                            1e-2 for DDST_MIXED (inner solve of the refinement) or 1e-10 for
                            DDST_FP64                                                          */
@@ -88,6 +93,11 @@ typedef struct {
   int leaf_size;        /* HODLR leaf size                                                    */
   uint64_t seed;        /* seed of the counter-based Gaussian sketch generator                */
   int check_every;      /* GMRES iterations between host convergence checks                   */
+  int factor_chunks;    /* pivot sweeps split along y into warm-started chunks per slab and
+                           direction: 0 automatic, 1 exact sequential sweeps, k > 1 forced     */
+  int factor_warmup;    /* warm-up rows of a chunk (0: 8 w in FP32, 18 w in FP64)              */
+  int tensor_cores;     /* 1: DDST_MIXED transfer build on the tcgen05 tensor cores (3xTF32,
+                           block sizes <= 64); 0: FP32 FMA kernel (kept for validation)       */
 } ddst_options;
 
 /* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
@@ -103,6 +113,9 @@ typedef struct {
   int max_rank;           /* largest HODLR rank (0 when dense)                                */
   int fail_slab;          /* first slab with a singular pivot, else -1                        */
   int fail_block;         /* its block (y index, 1-based), else -1                            */
+  int factor_chunks;      /* chunks per slab sweep actually used (1 = sequential; a failed
+                             warm-up check falls back to 1)                                   */
+  double factor_check;    /* largest relative warm-up check difference (0 when sequential)    */
 } ddst_info;
 
 /* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
@@ -174,6 +187,10 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
 /* Sizes of problem prob: n_ds, n_gamma and the total interface length (any may be NULL). */
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
+
+/* Arithmetic the context was set up with: DDST_FP64 or DDST_MIXED (what DDST_AUTO chose).
+ * Errors: INVALID_ARG for a NULL argument. */
+ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision);
 
 /* Allocation-free FP64 residual of the finite-difference system.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory while

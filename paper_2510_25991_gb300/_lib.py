@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "SINGULAR",
                 5: "NOT_CONVERGED", 6: "TIMEOUT", 7: "STATE", 8: "NOT_IMPLEMENTED"}
 DDST_FP64 = 0
 DDST_MIXED = 1
+DDST_AUTO = 2
 
 
 class ddst_grid(C.Structure):
@@ -31,7 +32,8 @@ class ddst_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("gmres_tol", C.c_double), ("gmres_max_iter", C.c_int),
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("k_max", C.c_int),
                 ("oversample", C.c_int), ("leaf_size", C.c_int), ("seed", C.c_uint64),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("factor_chunks", C.c_int), ("factor_warmup", C.c_int),
+                ("tensor_cores", C.c_int)]
 
 
 class ddst_info(C.Structure):
@@ -40,7 +42,8 @@ class ddst_info(C.Structure):
                 ("est_rel_error", C.c_double), ("t_factor", C.c_double),
                 ("t_transfer", C.c_double), ("t_compress", C.c_double), ("t_solve", C.c_double),
                 ("bytes_factors", C.c_int64), ("bytes_transfer", C.c_int64),
-                ("max_rank", C.c_int), ("fail_slab", C.c_int), ("fail_block", C.c_int)]
+                ("max_rank", C.c_int), ("fail_slab", C.c_int), ("fail_block", C.c_int),
+                ("factor_chunks", C.c_int), ("factor_check", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -67,6 +70,7 @@ SIGNATURES = {
     "ddst_apply_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "ddst_query": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int)]),
+    "ddst_get_precision": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "ddst_residual_noalloc": (C.c_int, [C.POINTER(ddst_grid), C.POINTER(ddst_coeffs), _P, _P, _P,
                                         _P, _P, _P]),
     "ddst_kernel_launches": (C.c_int64, []),

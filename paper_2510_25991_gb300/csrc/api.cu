@@ -81,6 +81,15 @@ struct ddst_ctx {
   std::vector<void*> owned;
   std::string err;
   float t_factor = 0.f, t_transfer = 0.f, t_compress = 0.f;
+  int factor_chunks = 1;
+  double factor_check = 0.0;
+  bool use_tc = false;            // FP32 transfer build on tcgen05
+  cudaStream_t cap_stream = nullptr;     // internal stream for graph capture
+  cudaGraphExec_t arn_graph[2] = {nullptr, nullptr};  // one GMRES step (plain / transposed)
+  int arn_graph_state[2] = {0, 0};       // operator state the graphs were captured for
+  int* d_k = nullptr;                    // device-resident Krylov basis count
+  double *h1 = nullptr, *h2 = nullptr, *d_beta = nullptr;
+  float *Uhi = nullptr, *Ulo = nullptr;  // tensor-core operand copies of F^T | B^T
 };
 
 namespace {
@@ -177,6 +186,118 @@ struct Timer {
     cudaEventDestroy(b);
   }
 };
+
+void drop_graphs(ddst_ctx* ctx) {
+  for (int q = 0; q < 2; ++q) {
+    if (ctx->arn_graph[q]) cudaGraphExecDestroy(ctx->arn_graph[q]);
+    ctx->arn_graph[q] = nullptr;
+    ctx->arn_graph_state[q] = 0;
+  }
+}
+
+// --------------------------------------------------------------------------------------------
+// Factorization: pivot sweeps in warm-started chunks (verified), exact fallback, diagonal blocks
+// --------------------------------------------------------------------------------------------
+template <typename T>
+ddst_status factor_all(ddst_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool f32 = sizeof(T) == 4;
+  const double tol = f32 ? 2e-4 : 1e-11;
+  auto plan = [&](int M, const std::vector<int>& ids, bool exact, std::vector<FacChunk>& out,
+                  int& nslots) {
+    const int conc = factor_ctas_per_sm<T>(M) * nsm;
+    const int per_sd = std::max(1, conc / std::max(1, 2 * (int)ids.size()));
+    for (int sid : ids) {
+      const SlabDesc& s = ctx->slabs[sid];
+      const int W = ctx->opt.factor_warmup > 0 ? ctx->opt.factor_warmup : (f32 ? 8 : 18) * s.w;
+      int nch = 1;
+      if (!exact) {
+        if (ctx->opt.factor_chunks > 1) nch = ctx->opt.factor_chunks;
+        else if (ctx->opt.factor_chunks == 0 && s.nb >= 4 * W) nch = per_sd;
+        nch = std::max(1, std::min(nch, s.nb / 2));
+      }
+      const int C = (s.nb + nch - 1) / nch;
+      for (int dir = 0; dir < 2; ++dir) {
+        for (int c = 0; c < nch; ++c) {
+          FacChunk f{};
+          f.slab = sid;
+          f.dir = dir;
+          if (dir == 0) {
+            f.first = c * C + 1;
+            f.last = std::min(s.nb, (c + 1) * C);
+            f.start = std::max(1, f.first - W);
+            f.chk = f.start == 1 ? -1 : nslots++;
+          } else {
+            f.first = s.nb - c * C;
+            f.last = std::max(1, s.nb - (c + 1) * C + 1);
+            f.start = std::min(s.nb, f.first + W);
+            f.chk = f.start == s.nb ? -1 : nslots++;
+          }
+          if ((f.last - f.first) * (dir == 0 ? 1 : -1) < 0) continue;
+          out.push_back(f);
+        }
+      }
+    }
+    std::stable_sort(out.begin(), out.end(), [](const FacChunk& a, const FacChunk& b) {
+      return std::abs(a.last - a.start) > std::abs(b.last - b.start);
+    });
+  };
+  auto run_sweeps = [&](bool exact, double& worst, int& chunks_used) -> ddst_status {
+    worst = 0.0;
+    chunks_used = 1;
+    for (auto& kv : ctx->cls) {
+      std::vector<FacChunk> ch;
+      int nslots = 0;
+      plan(kv.first, kv.second, exact, ch, nslots);
+      chunks_used = std::max<int>(chunks_used, (int)(ch.size() / (2 * kv.second.size())));
+      FacChunk* d_ch = nullptr;
+      T* d_chk = nullptr;
+      float* d_diff = nullptr;
+      CK(cudaMallocAsync(&d_ch, sizeof(FacChunk) * ch.size(), st));
+      CK(cudaMallocAsync(&d_chk, sizeof(T) * (size_t)std::max(1, nslots) * kv.first * kv.first, st));
+      CK(cudaMallocAsync(&d_diff, sizeof(float) * ch.size(), st));
+      CK(cudaMemcpyAsync(d_ch, ch.data(), sizeof(FacChunk) * ch.size(), cudaMemcpyHostToDevice, st));
+      launch_factor<T>(kv.first, 0, ctx->d_slabs, d_ch, (int)ch.size(), ctx->d_cls[kv.first],
+                       (int)kv.second.size(), ctx->cls_maxnb[kv.first], (T*)ctx->pack, (T*)ctx->F,
+                       (T*)ctx->B, (T*)ctx->G, (T*)ctx->Ft, (T*)ctx->Bt, d_chk, d_diff,
+                       ctx->use_tc ? ctx->Uhi : nullptr, ctx->use_tc ? ctx->Ulo : nullptr,
+                       ctx->fac_elems, ctx->d_st, st);
+      CK(cudaGetLastError());
+      std::vector<float> diff(ch.size());
+      CK(cudaMemcpyAsync(diff.data(), d_diff, sizeof(float) * ch.size(), cudaMemcpyDeviceToHost, st));
+      CK(cudaFreeAsync(d_ch, st));
+      CK(cudaFreeAsync(d_chk, st));
+      CK(cudaFreeAsync(d_diff, st));
+      CK(cudaStreamSynchronize(st));
+      for (float d : diff) worst = (d == d) ? std::max(worst, (double)d) : HUGE_VAL;  // NaN fails
+    }
+    return DDST_OK;
+  };
+  double worst = 0.0;
+  int used = 1;
+  ddst_status s = run_sweeps(ctx->opt.factor_chunks == 1, worst, used);
+  if (s != DDST_OK) return s;
+  if (!(worst <= tol)) {  // a warm-up did not converge (or produced NaN): exact sweeps
+    ctx->factor_check = worst;
+    double w2 = 0.0;
+    s = run_sweeps(true, w2, used);
+    if (s != DDST_OK) return s;
+    used = 1;
+  } else {
+    ctx->factor_check = worst;
+  }
+  ctx->factor_chunks = used;
+  for (auto& kv : ctx->cls)
+    launch_factor<T>(kv.first, 1, ctx->d_slabs, nullptr, 0, ctx->d_cls[kv.first],
+                     (int)kv.second.size(), ctx->cls_maxnb[kv.first], (T*)ctx->pack, (T*)ctx->F,
+                     (T*)ctx->B, (T*)ctx->G, (T*)ctx->Ft, (T*)ctx->Bt, nullptr, nullptr, nullptr,
+                     nullptr, 0, ctx->d_st, st);
+  CK(cudaGetLastError());
+  return DDST_OK;
+}
 
 // --------------------------------------------------------------------------------------------
 // Setup
@@ -287,6 +408,13 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     AL(d, sizeof(int) * kv.second.size());
     ctx->d_cls[kv.first] = d;
   }
+  ctx->use_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
+  for (auto& kv : ctx->cls)
+    if (kv.first > 64) ctx->use_tc = false;
+  if (ctx->use_tc) {
+    AL(ctx->Uhi, sizeof(float) * 2 * ctx->fac_elems);
+    AL(ctx->Ulo, sizeof(float) * 2 * ctx->fac_elems);
+  }
 #undef AL
   cudaStream_t st = ctx->stream;
   auto bail = [&](cudaError_t err, const char* what) {
@@ -310,22 +438,20 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       if ((e = stage_in(ctx->d_c + P.node_off, coeffs[q].c, P.nnode, st)) != cudaSuccess) return bail(e, "copy c");
   }
   Timer tm(st);
+  ddst_status fs;
   if (ctx->prec == DDST_FP64) {
     launch_stencil_pack<double>(ctx->d_slabs, nslab, ctx->max_nb, ctx->d_probs, ctx->d_a, ctx->d_c,
                                 (double*)ctx->pack, st);
-    for (auto& kv : ctx->cls)
-      launch_factor<double>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                            ctx->cls_maxnb[kv.first], (double*)ctx->pack, (double*)ctx->F,
-                            (double*)ctx->B, (double*)ctx->G, (double*)ctx->Ft, (double*)ctx->Bt,
-                            ctx->d_st, st);
+    fs = factor_all<double>(ctx);
   } else {
     launch_stencil_pack<float>(ctx->d_slabs, nslab, ctx->max_nb, ctx->d_probs, ctx->d_a, ctx->d_c,
                                (float*)ctx->pack, st);
-    for (auto& kv : ctx->cls)
-      launch_factor<float>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                           ctx->cls_maxnb[kv.first], (float*)ctx->pack, (float*)ctx->F,
-                           (float*)ctx->B, (float*)ctx->G, (float*)ctx->Ft, (float*)ctx->Bt,
-                           ctx->d_st, st);
+    fs = factor_all<float>(ctx);
+  }
+  if (fs != DDST_OK) {
+    g_setup_error = ctx->err;
+    ddst_destroy(ctx);
+    return fs;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "factor launch");
   ctx->t_factor = tm.stop();
@@ -354,7 +480,8 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   Timer tm(st);
   for (auto& kv : ctx->cls) {
     const int M = kv.first;
-    const int R = sbuild_tile_cols<T>(M);
+    const int R = (sizeof(T) == 4 && ctx->use_tc) ? sbuild_tc_tile_cols(ctx->opt.tensor_cores)
+                                                  : sbuild_tile_cols<T>(M);
     std::vector<TileDesc> tiles;
     for (int sid : kv.second) {
       const SlabDesc& s = ctx->slabs[sid];
@@ -377,9 +504,20 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocAsync tiles");
     CK(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
                        cudaMemcpyHostToDevice, st));
-    launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
-                     (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
-                     ctx->d_st, st);
+    if constexpr (sizeof(T) == 4) {
+      if (ctx->use_tc)
+        launch_sbuild_tc(ctx->opt.tensor_cores, M, ctx->d_slabs, d_tiles, (int)tiles.size(), ctx->Uhi, ctx->Ulo,
+                         ctx->Uhi + ctx->fac_elems, ctx->Ulo + ctx->fac_elems, (const float*)ctx->G,
+                         (const float*)ctx->pack, (float*)ctx->S, ctx->d_st, st);
+      else
+        launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
+                         (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
+                         ctx->d_st, st);
+    } else {
+      launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
+                       (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
+                       ctx->d_st, st);
+    }
     CK(cudaGetLastError());
     CK(cudaFreeAsync(d_tiles, st));
   }
@@ -388,6 +526,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   ddst_status s = check_status(ctx, nullptr);
   if (s != DDST_OK) return s;
   ctx->hodlr.clear();
+  drop_graphs(ctx);
   ctx->state = 2;
   return DDST_OK;
 }
@@ -397,7 +536,8 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
 // --------------------------------------------------------------------------------------------
 ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   if (ctx->d_b) return DDST_OK;
-  const int maxit = std::max(1, ctx->opt.gmres_max_iter);
+  ctx->opt.gmres_max_iter = std::max(1, std::min(ctx->opt.gmres_max_iter, 1000));
+  const int maxit = ctx->opt.gmres_max_iter;
   ctx->ldh = maxit + 1;
   ctx->nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(256, (ctx->tot_if + 4095) / 4096));
   cudaError_t e;
@@ -427,18 +567,61 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   AL(ctx->part, sizeof(double) * (size_t)(maxit + 1) * std::max(ctx->nchunk, 1024));
   AL(ctx->scal, sizeof(double) * 16);
   AL(ctx->ysol, sizeof(double) * (maxit + 1));
+  AL(ctx->d_k, sizeof(int) * 4);
+  AL(ctx->h1, sizeof(double) * (maxit + 1));
+  AL(ctx->h2, sizeof(double) * (maxit + 1));
+  AL(ctx->d_beta, sizeof(double) * 2);
 #undef AL
   return DDST_OK;
 }
 
 template <typename T>
-void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose) {
+void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
+                       cudaStream_t st = nullptr, const int* kdev = nullptr, int64_t kstride = 0) {
+  if (!st) st = ctx->stream;
   if (ctx->state == 3)
     hodlr_apply<T>(ctx->hodlr, ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), x, y, transpose,
-                   ctx->stream);
+                   st, kdev, kstride);
   else
     launch_apply_dense<T>(ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), ctx->max_ng,
-                          (const T*)ctx->S, x, y, transpose, ctx->stream);
+                          (const T*)ctx->S, x, y, transpose, st, kdev, kstride);
+}
+
+// One GMRES step (operator application + Arnoldi CGS2 + Givens + normalization) captured as a
+// CUDA graph on the internal stream; replayed on the context stream.
+template <typename T>
+ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
+  const int key = transpose ? 1 : 0;
+  if (ctx->arn_graph[key] && ctx->arn_graph_state[key] == ctx->state) {
+    *out = ctx->arn_graph[key];
+    return DDST_OK;
+  }
+  if (ctx->arn_graph[key]) {
+    cudaGraphExecDestroy(ctx->arn_graph[key]);
+    ctx->arn_graph[key] = nullptr;
+  }
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  const int64_t n = ctx->tot_if;
+  const int maxit = std::max(1, ctx->opt.gmres_max_iter);
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose, ctx->cap_stream, ctx->d_k, n);
+  launch_arnoldi_step(ctx->V, ctx->if_w, n, ctx->d_k, ctx->h1, ctx->h2, ctx->scal + 1, ctx->H,
+                      ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta, ctx->resid, ctx->scal + 2,
+                      maxit, ctx->cap_stream);
+  const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (ec != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(ctx, ec, "graph capture");
+  }
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_fail(ctx, ei, "graph instantiate");
+  ctx->arn_graph[key] = ex;
+  ctx->arn_graph_state[key] = ctx->state;
+  *out = ex;
+  return DDST_OK;
 }
 
 double host_scalar(ddst_ctx* ctx, const double* d) {
@@ -467,20 +650,21 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   launch_normalize_start(rhs, ctx->scal, ctx->V, n, st);
   CK(cudaMemsetAsync(ctx->gv, 0, sizeof(double) * (maxit + 2), st));
   CK(cudaMemcpyAsync(ctx->gv, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_beta, &beta, sizeof(double), cudaMemcpyHostToDevice, st));
+  const int one = 1;
+  CK(cudaMemcpyAsync(ctx->d_k, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ctx->h1, 0, sizeof(double) * (maxit + 1), st));
+  CK(cudaMemsetAsync(ctx->h2, 0, sizeof(double) * (maxit + 1), st));
+  CK(cudaMemsetAsync(ctx->scal + 1, 0, sizeof(double), st));
+  cudaGraphExec_t graph = nullptr;
+  ddst_status gs = arnoldi_graph<T>(ctx, transpose, &graph);
+  if (gs != DDST_OK) return gs;
   std::vector<double> hres(maxit + 1);
   int kk = -1;
   int k = 0;
   for (k = 1; k <= maxit; ++k) {
-    double* vprev = ctx->V + (int64_t)(k - 1) * n;
-    apply_interface_T<T>(ctx, vprev, ctx->if_w, transpose);
-    launch_gs_pass(ctx->V, ctx->if_w, ctx->if_w, n, k, ctx->nchunk, ctx->part, ctx->hpass, ctx->hcol,
-                   0, st);
-    launch_gs_pass(ctx->V, ctx->if_w, ctx->if_w, n, k, ctx->nchunk, ctx->part, ctx->hpass, ctx->hcol,
-                   1, st);
-    launch_dot(ctx->if_w, ctx->if_w, n, ctx->part, 256, ctx->scal + 1, st);
-    launch_givens(ctx->hcol, ctx->scal + 1, k, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, beta,
-                  ctx->resid, ctx->scal + 2, st);
-    launch_scale_to(ctx->if_w, ctx->scal + 2, ctx->V + (int64_t)k * n, n, st);
+    CK(cudaGraphLaunch(graph, st));
+    note_launch(ctx->state == 3 ? 9 : 6);
     if (k % check == 0 || k == maxit) {
       CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -607,11 +791,13 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
     info->t_solve = ms;
-    info->bytes_factors = (int64_t)(5 * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
+    info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
     info->bytes_transfer = ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
     info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
     info->fail_slab = -1;
     info->fail_block = -1;
+    info->factor_chunks = ctx->factor_chunks;
+    info->factor_check = ctx->factor_check;
   }
   if (result != DDST_OK)
     return fail(ctx, result, "refinement stopped at estimated relative error %.3e", est);
@@ -732,6 +918,32 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
   return DDST_OK;
 }
 
+// DDST_AUTO: the FP32 factorization first; if one of its pivots falls below the FP32 floor
+// (an indefinite local operator whose leading block minors pass near zero), the FP64
+// factorization, whose floor is nine orders of magnitude lower.  Other errors return as they are.
+ddst_status setup_precision(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                            const int* widths, const ddst_options* opt, void* stream,
+                            ddst_ctx** out) {
+  ddst_options o;
+  if (opt) o = *opt; else ddst_options_default(&o);
+  if (o.precision != DDST_FP64 && o.precision != DDST_MIXED && o.precision != DDST_AUTO) {
+    if (out) *out = nullptr;
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "precision must be DDST_FP64, DDST_MIXED or DDST_AUTO");
+  }
+  if (o.precision != DDST_AUTO) return setup_impl(nprob, grids, coeffs, widths, &o, stream, out);
+  o.precision = DDST_MIXED;
+  const ddst_status s = setup_impl(nprob, grids, coeffs, widths, &o, stream, out);
+  if (s != DDST_ERR_SINGULAR) return s;
+  const std::string first = g_setup_error;
+  o.precision = DDST_FP64;
+  const ddst_status s2 = setup_impl(nprob, grids, coeffs, widths, &o, stream, out);
+  if (s2 == DDST_ERR_INVALID_ARG) {  // blocks too large for the FP64 kernels: report the pivot
+    g_setup_error = first;
+    return s;
+  }
+  return s2;
+}
+
 }  // namespace
 
 // ============================================================================================
@@ -752,17 +964,26 @@ void ddst_options_default(ddst_options* opt) {
   opt->leaf_size = 128;
   opt->seed = 1234;
   opt->check_every = 8;
+  opt->factor_chunks = 0;
+  opt->factor_warmup = 0;
+  opt->tensor_cores = 1;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
                        const ddst_options* opt, void* stream, ddst_ctx** out) {
-  return setup_impl(1, grid, coeffs, &slab_width, opt, stream, out);
+  return setup_precision(1, grid, coeffs, &slab_width, opt, stream, out);
 }
 
 ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
                              const int* slab_widths, const ddst_options* opt, void* stream,
                              ddst_ctx** out) {
-  return setup_impl(nprob, grids, coeffs, slab_widths, opt, stream, out);
+  return setup_precision(nprob, grids, coeffs, slab_widths, opt, stream, out);
+}
+
+ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision) {
+  if (!ctx || !precision) return DDST_ERR_INVALID_ARG;
+  *precision = ctx->prec;
+  return DDST_OK;
 }
 
 ddst_status ddst_build_transfer(ddst_ctx* ctx) {
@@ -774,6 +995,7 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx) {
 ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
   if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "ddst_build_transfer has not completed");
+  drop_graphs(ctx);
   if (!(tol > 0.0)) {
     ctx->hodlr.clear();
     ctx->state = 2;
@@ -919,7 +1141,10 @@ const char* ddst_last_error(const ddst_ctx* ctx) {
 
 void ddst_destroy(ddst_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->arn_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->hodlr.release();
   for (void* p : ctx->owned) cudaFree(p);
   delete ctx;

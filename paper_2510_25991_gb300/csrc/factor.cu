@@ -15,6 +15,7 @@
 // two sweeps at the same time.  No pivoting (as in the paper); a pivot below
 // 1e3 * eps * |D_k(p,p)| reports DDST_ERR_SINGULAR with the slab and block.
 #include "kernels.cuh"
+#include "umma.cuh"
 
 namespace ddst {
 
@@ -60,12 +61,24 @@ __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   for (int q0 = 0; q0 < M; q0 += NB) {
-    // (a) warp 0 inverts the pivot block in place; lane owns row lane/2, 8 columns
+    // (a) warp 0 inverts the pivot block in registers: lane owns row lane/2, columns
+    //     8*(lane&1)..+7; pivot rows and entries travel by warp shuffles (no barriers).
     if (warp == 0) {
-      const int r = lane >> 1, c0 = (lane & 1) * 8;
+      const int r = lane >> 1, h = lane & 1;
       T* P = X + q0 * LD + q0;
+      T v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = P[r * LD + 8 * h + e];
       for (int pp = 0; pp < NB; ++pp) {
-        T piv = P[pp * LD + pp];
+        T prow[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) prow[e] = __shfl_sync(0xffffffffu, v[e], 2 * pp + h);
+        const int sel = pp & 7;
+        const T lo4 = (sel & 2) ? ((sel & 1) ? v[3] : v[2]) : ((sel & 1) ? v[1] : v[0]);
+        const T hi4 = (sel & 2) ? ((sel & 1) ? v[7] : v[6]) : ((sel & 1) ? v[5] : v[4]);
+        const T pe = (sel & 4) ? hi4 : lo4;
+        T piv = __shfl_sync(0xffffffffu, pe, 2 * pp + (pp >> 3));
+        const T fv = __shfl_sync(0xffffffffu, pe, 2 * r + (pp >> 3));
         const T lim = thr[q0 + pp];
         if (!(fabs(piv) > lim)) {
           if (lane == 0) set_status(st, ST_SINGULAR, slab, block);
@@ -73,22 +86,15 @@ __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp
           if (lim == T(0)) piv = T(1);
         }
         const T inv = T(1) / piv;
-        const T f = P[r * LD + pp];
-        T prow[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const int c = c0 + e;
-          prow[e] = (c == pp ? T(1) : P[pp * LD + c]) * inv;
+          const int c = 8 * h + e;
+          const T ps = (c == pp ? T(1) : prow[e]) * inv;
+          v[e] = (r == pp) ? ps : ((c == pp ? T(0) : v[e]) - fv * ps);
         }
-        __syncwarp();
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = c0 + e;
-          const T old = P[r * LD + c];
-          P[r * LD + c] = (r == pp) ? prow[e] : ((c == pp ? T(0) : old) - f * prow[e]);
-        }
-        __syncwarp();
       }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) P[r * LD + 8 * h + e] = v[e];
     }
     __syncthreads();
     // (b) column panel C = X(:, q) (old values; block rows unused) and row panel R = P^{-1} X(q, :)
@@ -167,15 +173,23 @@ __device__ __forceinline__ void store_block(const T* __restrict__ X, T* __restri
   }
 }
 
-// Forward (blockIdx.y == 0) or backward (== 1) pivot sweep of one slab (blockIdx.x indexes
-// slab_ids, the slabs of this block-size class).  The stencil pack of the next block is
-// prefetched by a bulk copy while the current block is inverted.
+// One chunk of a forward (dir 0) or backward (dir 1) pivot sweep.  Rows are visited from
+// `start` through `last` (ascending for dir 0, descending for dir 1); inverses are stored for the
+// rows from `first` on.  A chunk whose start is not the slab's end row begins with
+// Sigma_start = D_start (its warm-up rows): the pivot recurrence forgets its initial value
+// exponentially (about exp(-pi/w) per row for slab width w), so after the warm-up the pivots
+// agree with the sequential ones to rounding.  The warm-up's last inverse is written to the
+// check slot `chk` and compared with the previous chunk's stored inverse of the same row by
+// k_factor_verify; the host falls back to the exact sequential sweep if any check fails.  The
+// stencil pack of the next row is prefetched by a bulk copy while the current one is inverted.
 template <typename T, int M>
 __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ slabs,
-                                                const int* __restrict__ slab_ids,
+                                                const FacChunk* __restrict__ chunks,
                                                 const T* __restrict__ pack, T* __restrict__ F,
                                                 T* __restrict__ B, T* __restrict__ Ft,
-                                                T* __restrict__ Bt, DevStatus* st) {
+                                                T* __restrict__ Bt, T* __restrict__ chk,
+                                                float* __restrict__ Uhi, float* __restrict__ Ulo,
+                                                int64_t umma_elems, DevStatus* st) {
   using G = BGJ<T, M>;
   constexpr int LD = G::LD;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -185,15 +199,20 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
   T* pk = Rp + G::NB * LD;              // [3][PK_NFIELDS * M]: ring (previous, current, next)
   T* thr = pk + 3 * PK_NFIELDS * M;     // [M]
   uint64_t* bar = reinterpret_cast<uint64_t*>(thr + M);  // [3]
-  const int sid = slab_ids[blockIdx.x];
+  const FacChunk ch = chunks[blockIdx.x];
+  const int sid = ch.slab;
   const SlabDesc s = slabs[sid];
-  const int dir = blockIdx.y;
+  const int dir = ch.dir;
+  // Uhi/Ulo hold the forward copies in [0, umma_half) and the backward ones behind them
+  const int64_t umma_half = umma_elems;
+  const int sgn = dir == 0 ? 1 : -1;
+  const int len = (ch.last - ch.start) * sgn + 1;
   T* out = (dir == 0 ? F : B) + s.fac_off;
   T* outT = (dir == 0 ? Ft : Bt) + s.fac_off;
   const int rowfield = dir == 0 ? PK_SOUTH : PK_NORTH;   // ell_k (fwd) or ups_k (bwd)
   const int colfield = dir == 0 ? PK_NORTH : PK_SOUTH;   // ups_{k-1} (fwd) or ell_{k+1} (bwd)
   const uint32_t pbytes = PK_NFIELDS * M * sizeof(T);
-  auto blk = [&](int step) { return dir == 0 ? step + 1 : s.nb - step; };
+  auto blk = [&](int step) { return ch.start + sgn * step; };
   auto issue = [&](int step) {
     const int k = blk(step);
     mbar_arrive_expect_tx(&bar[step % 3], pbytes);
@@ -208,19 +227,19 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
   if (threadIdx.x == 0) issue(0);
   int waited = 0, issued = 1;
   bool ok = true;
-  for (int step = 0; step < s.nb; ++step) {
+  for (int step = 0; step < len; ++step) {
     const int k = blk(step);
     if (!mbar_wait(&bar[step % 3], (step / 3) & 1, st, sid, k)) ok = false;
     waited = step + 1;
     __syncthreads();
     if (!ok) break;
-    if (threadIdx.x == 0 && step + 1 < s.nb) {
+    if (threadIdx.x == 0 && step + 1 < len) {
       fence_proxy_async();
       issue(step + 1);
       ++issued;
     }
     const T* cur = pk + (step % 3) * PK_NFIELDS * M;
-    const T* prv = pk + ((step + 2) % 3) * PK_NFIELDS * M;   // previous block (step - 1)
+    const T* prv = pk + ((step + 2) % 3) * PK_NFIELDS * M;   // previous row (step - 1)
     for (int i = threadIdx.x; i < M; i += blockDim.x) thr[i] = T(1e3) * Eps<T>::v * fabs(cur[PK_DIAG * M + i]);
     // Sigma_k = D_k - diag(ell_k) F_{k-1} diag(ups_{k-1})   (backward: ups_k, B_{k+1}, ell_{k+1})
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
@@ -232,11 +251,60 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
     }
     __syncthreads();
     bgj_invert<T, M>(X, Cp, Rp, thr, st, sid, k);
-    store_block<T, M>(X, out + (int64_t)(k - 1) * M * M, outT + (int64_t)(k - 1) * M * M);
+    if ((k - ch.first) * sgn >= 0) {
+      store_block<T, M>(X, out + (int64_t)(k - 1) * M * M, outT + (int64_t)(k - 1) * M * M);
+      if constexpr (sizeof(T) == 4) {
+        if (Uhi)  // tensor-core operand copy (transposed, TF32 hi/lo, K-major layout)
+          store_umma_split_T(reinterpret_cast<const float*>(X), LD, M,
+                             Uhi + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M,
+                             Ulo + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M);
+      }
+    }
+    else if (ch.chk >= 0 && k == ch.first - sgn)
+      store_block<T, M>(X, chk + (int64_t)ch.chk * M * M, nullptr);
     __syncthreads();
   }
   if (threadIdx.x == 0)
     for (int q = waited; q < issued; ++q) mbar_wait(&bar[q % 3], (q / 3) & 1, st, sid, -1);
+}
+
+// Convergence check of the warm-started chunks: relative max difference between a chunk's
+// warm-up inverse and the previous chunk's stored inverse of the same row.  One CTA per chunk.
+template <typename T, int M>
+__global__ void k_factor_verify(const SlabDesc* __restrict__ slabs,
+                                const FacChunk* __restrict__ chunks, const T* __restrict__ F,
+                                const T* __restrict__ B, const T* __restrict__ chk,
+                                float* __restrict__ diff) {
+  const FacChunk ch = chunks[blockIdx.x];
+  if (ch.chk < 0) {
+    if (threadIdx.x == 0) diff[blockIdx.x] = 0.f;
+    return;
+  }
+  const SlabDesc s = slabs[ch.slab];
+  const int row = ch.first - (ch.dir == 0 ? 1 : -1);
+  const T* ref = (ch.dir == 0 ? F : B) + s.fac_off + (int64_t)(row - 1) * M * M;
+  const T* got = chk + (int64_t)ch.chk * M * M;
+  float md = 0.f, mr = 0.f;
+  // live m x m block only: the padded diagonal of an inverse is 1, far above its h^2-sized
+  // entries, and would hide any difference in them
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int r = e / M, c = e - r * M;
+    if (r >= s.m || c >= s.m) continue;
+    md = fmaxf(md, (float)fabs(ref[e] - got[e]));
+    mr = fmaxf(mr, (float)fabs(ref[e]));
+  }
+  __shared__ float sd[256], sr[256];
+  sd[threadIdx.x] = md;
+  sr[threadIdx.x] = mr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sd[threadIdx.x] = fmaxf(sd[threadIdx.x], sd[threadIdx.x + o]);
+      sr[threadIdx.x] = fmaxf(sr[threadIdx.x], sr[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) diff[blockIdx.x] = sr[0] > 0.f ? sd[0] / sr[0] : 0.f;
 }
 
 // Diagonal blocks of the inverse: G_k = (D_k - L_k F_{k-1} U_{k-1} - U_k B_{k+1} L_{k+1})^{-1}.
@@ -285,42 +353,74 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
 }
 
 template <typename T, int M>
-void launch_factor_M(const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                     const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st,
-                     cudaStream_t s) {
-  if (nids == 0) return;
+static size_t factor_smem() {
+  return BGJ<T, M>::smem_elems * sizeof(T) + (3 * PK_NFIELDS * M + M) * sizeof(T) + 24;
+}
+
+template <typename T, int M>
+void launch_factor_M(const SlabDesc* d_slabs, const FacChunk* d_chunks, int nchunks,
+                     const int* d_ids, int nids, int max_nb, const T* pack, T* F, T* B, T* G,
+                     T* Ft, T* Bt, T* chk, float* diff, float* Uhi, float* Ulo,
+                     int64_t umma_elems, int phase, DevStatus* st, cudaStream_t s) {
   using Gc = BGJ<T, M>;
-  const size_t base = Gc::smem_elems * sizeof(T);
-  const size_t sm_f = base + (3 * PK_NFIELDS * M + M) * sizeof(T) + 24;
-  const size_t sm_c = base + (PK_NFIELDS * M + 3 * M) * sizeof(T);
+  const size_t sm_f = factor_smem<T, M>();
+  const size_t sm_c = Gc::smem_elems * sizeof(T) + (PK_NFIELDS * M + 3 * M) * sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_factor<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f);
     cudaFuncSetAttribute(k_center<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
     attr = true;
   }
-  note_launch();
-  k_factor<T, M><<<dim3(nids, 2), 256, sm_f, s>>>(d_slabs, d_ids, pack, F, B, Ft, Bt, st);
-  note_launch();
-  k_center<T, M><<<dim3(max_nb, nids), 256, sm_c, s>>>(d_slabs, d_ids, pack, F, B, G, st);
+  if (phase == 0) {  // pivot sweeps + convergence check of warm-started chunks
+    if (nchunks == 0) return;
+    note_launch();
+    k_factor<T, M><<<nchunks, 256, sm_f, s>>>(d_slabs, d_chunks, pack, F, B, Ft, Bt, chk, Uhi, Ulo,
+                                              umma_elems, st);
+    note_launch();
+    k_factor_verify<T, M><<<nchunks, 256, 0, s>>>(d_slabs, d_chunks, F, B, chk, diff);
+  } else {           // diagonal blocks of the inverse
+    if (nids == 0) return;
+    note_launch();
+    k_center<T, M><<<dim3(max_nb, nids), 256, sm_c, s>>>(d_slabs, d_ids, pack, F, B, G, st);
+  }
 }
 
 template <typename T>
-void launch_factor(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                   const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st, cudaStream_t s) {
+void launch_factor(int M, int phase, const SlabDesc* d_slabs, const FacChunk* d_chunks,
+                   int nchunks, const int* d_ids, int nids, int max_nb, const T* pack, T* F,
+                   T* B, T* G, T* Ft, T* Bt, T* chk, float* diff, float* Uhi, float* Ulo,
+                   int64_t umma_elems, DevStatus* st, cudaStream_t s) {
   switch (M) {
-    case 32: launch_factor_M<T, 32>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
-    case 64: launch_factor_M<T, 64>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
-    case 128: launch_factor_M<T, 128>(d_slabs, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, st, s); break;
+    case 32: launch_factor_M<T, 32>(d_slabs, d_chunks, nchunks, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, chk, diff, Uhi, Ulo, umma_elems, phase, st, s); break;
+    case 64: launch_factor_M<T, 64>(d_slabs, d_chunks, nchunks, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, chk, diff, Uhi, Ulo, umma_elems, phase, st, s); break;
+    case 128: launch_factor_M<T, 128>(d_slabs, d_chunks, nchunks, d_ids, nids, max_nb, pack, F, B, G, Ft, Bt, chk, diff, nullptr, nullptr, 0, phase, st, s); break;
     default: break;
   }
 }
 
-template void launch_factor<float>(int, const SlabDesc*, const int*, int, int, const float*,
-                                   float*, float*, float*, float*, float*, DevStatus*,
+// Resident factor CTAs per SM for block size M (drives the chunk count).
+template <typename T>
+int factor_ctas_per_sm(int M) {
+  int n = 0;
+  switch (M) {
+    case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 32>, 256, factor_smem<T, 32>()); break;
+    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 64>, 256, factor_smem<T, 64>()); break;
+    case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 128>, 256, factor_smem<T, 128>()); break;
+    default: break;
+  }
+  cudaGetLastError();
+  return n > 0 ? n : 1;
+}
+
+template void launch_factor<float>(int, int, const SlabDesc*, const FacChunk*, int, const int*,
+                                   int, int, const float*, float*, float*, float*, float*,
+                                   float*, float*, float*, float*, float*, int64_t, DevStatus*,
                                    cudaStream_t);
-template void launch_factor<double>(int, const SlabDesc*, const int*, int, int, const double*,
-                                    double*, double*, double*, double*, double*, DevStatus*,
+template void launch_factor<double>(int, int, const SlabDesc*, const FacChunk*, int, const int*,
+                                    int, int, const double*, double*, double*, double*, double*,
+                                    double*, double*, float*, float*, float*, int64_t, DevStatus*,
                                     cudaStream_t);
+template int factor_ctas_per_sm<float>(int);
+template int factor_ctas_per_sm<double>(int);
 
 }  // namespace ddst

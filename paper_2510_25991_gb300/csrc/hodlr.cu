@@ -83,21 +83,23 @@ __global__ void k_sblk_gemv(const SBlk* __restrict__ sb, const T* __restrict__ S
   const double* xv = x + blockIdx.y * stride;
   double* yv = y + blockIdx.y * stride;
   const T* M = S + b.off;
-  if (!transpose) {  // y = S x: thread per row, columns contiguous
+  if (!transpose) {  // y += S(:, chunk) x(chunk): thread per row, 128 columns per CTA (y zeroed)
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= b.ng) return;
+    const int64_t c0 = (int64_t)blockIdx.z * 128;
+    if (row >= b.ng || c0 >= b.ng) return;
+    const int64_t c1 = min(b.ng, c0 + 128);
     double acc = 0.0;
-    for (int64_t c0 = 0; c0 < b.ng; c0 += 32) {
+    for (int64_t cb = c0; cb < c1; cb += 32) {
       T part = T(0);
-      const int64_t c1 = min(b.ng, c0 + 32);
-      for (int64_t c = c0; c < c1; ++c) part = fma(M[c * b.ng + row], static_cast<T>(xv[c]), part);
+      const int64_t ce = min(c1, cb + 32);
+      for (int64_t c = cb; c < ce; ++c) part = fma(M[c * b.ng + row], static_cast<T>(xv[c]), part);
       acc += (double)part;
     }
-    yv[row] = acc;
+    atomicAdd(&yv[row], acc);
   } else {  // y = S^T x: warp per column
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (col >= b.ng) return;
+    if (col >= b.ng || blockIdx.z != 0) return;
     T part = T(0);
     for (int64_t r = lane; r < b.ng; r += 32) part = fma(M[col * b.ng + r], static_cast<T>(xv[r]), part);
     const double acc = warp_sum((double)part);
@@ -384,8 +386,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_h_inner(const HItem* __restrict__ items,
                                                  const HBlock* __restrict__ bl,
                                                  const T* __restrict__ UV,
-                                                 const double* __restrict__ x,
-                                                 double* __restrict__ t, int transpose) {
+                                                 const double* __restrict__ x0,
+                                                 double* __restrict__ t, int transpose,
+                                                 const int* kdev, int64_t kstride) {
+  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const HItem it = items[blockIdx.x];
   const HBlock b = bl[it.blk];
   __shared__ T sx[256];
@@ -447,8 +451,10 @@ __global__ void __launch_bounds__(256) k_h_outer(const HItem* __restrict__ items
 template <typename T>
 __global__ void __launch_bounds__(256) k_h_leaf(const HLeaf* __restrict__ lv,
                                                 const T* __restrict__ D,
-                                                const double* __restrict__ x,
-                                                double* __restrict__ acc, int transpose) {
+                                                const double* __restrict__ x0,
+                                                double* __restrict__ acc, int transpose,
+                                                const int* kdev, int64_t kstride) {
+  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const HLeaf L = lv[blockIdx.x];
   const T* M = D + L.d_off;
   const int len = (int)L.len;  // <= 256 (leaf size)
@@ -491,8 +497,9 @@ __global__ void __launch_bounds__(256) k_h_leaf(const HLeaf* __restrict__ lv,
   }
 }
 
-__global__ void k_h_finish(const double* __restrict__ x, const double* __restrict__ acc,
-                           double* __restrict__ y, int64_t n) {
+__global__ void k_h_finish(const double* __restrict__ x0, const double* __restrict__ acc,
+                           double* __restrict__ y, int64_t n, const int* kdev, int64_t kstride) {
+  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
     y[e] = x[e] - acc[e];
@@ -651,16 +658,16 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_sng, sng.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(H.d_leaves, H.leaves.data(), sizeof(HLeaf) * H.leaves.size(), cudaMemcpyHostToDevice, st);
-  // ||S||_2 by power iteration on S^T S (6 steps)
+  // ||S||_2 by power iteration on S^T S (4 steps)
   note_launch();
   k_sblk_init<<<nsb, 256, 0, st>>>(d_sb, d_x, stride, hp.seed ^ 0x9e3779b97f4a7c15ull);
   const unsigned gr = (unsigned)((max_ng + 255) / 256), gc = (unsigned)((max_ng + 7) / 8);
-  for (int itp = 0; itp < 6; ++itp) {
-    note_launch();
-    k_sblk_gemv<T><<<dim3(gr, nsb), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
-    note_launch();
-    k_sblk_gemv<T><<<dim3(gc, nsb), 256, 0, st>>>(d_sb, S, d_y, d_x, stride, 1);
-    note_launch();
+  const unsigned gz = (unsigned)((max_ng + 127) / 128);
+  for (int itp = 0; itp < 4; ++itp) {
+    cudaMemsetAsync(d_y, 0, sizeof(double) * stride * nsb, st);
+    note_launch(3);
+    k_sblk_gemv<T><<<dim3(gr, nsb, gz), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
+    k_sblk_gemv<T><<<dim3(gc, nsb, 1), 256, 0, st>>>(d_sb, S, d_y, d_x, stride, 1);
     k_sblk_normalize<<<nsb, 256, 0, st>>>(d_sb, d_x, d_x, stride, d_nrm);
   }
   // d_nrm now holds ||S^T S x|| ~ sigma_max^2
@@ -738,7 +745,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
 
 template <typename T>
 void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const double* x, double* y,
-                 int transpose, cudaStream_t st) {
+                 int transpose, cudaStream_t st, const int* kdev, int64_t kstride) {
   cudaMemsetAsync(H.acc, 0, sizeof(double) * H.acc_len, st);
   const int nblk = (int)H.blocks.size();
   if (nblk > 0) {
@@ -748,7 +755,8 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
     const HItem* in_items = (const HItem*)(transpose ? H.d_out_items : H.d_out_items_T);
     if (ni_in > 0) {
       note_launch();
-      k_h_inner<T><<<ni_in, 256, 0, st>>>(in_items, H.d_blocks, (const T*)H.UV, x, H.t, transpose);
+      k_h_inner<T><<<ni_in, 256, 0, st>>>(in_items, H.d_blocks, (const T*)H.UV, x, H.t, transpose,
+                                          kdev, kstride);
     }
     const int ni = transpose ? H.n_out_items_T : H.n_out_items;
     if (ni > 0) {
@@ -761,10 +769,10 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
   if (!H.leaves.empty()) {
     note_launch();
     k_h_leaf<T><<<(unsigned)H.leaves.size(), 256, 0, st>>>(H.d_leaves, (const T*)H.D, x, H.acc,
-                                                           transpose);
+                                                           transpose, kdev, kstride);
   }
   note_launch();
-  k_h_finish<<<512, 256, 0, st>>>(x, H.acc, y, H.acc_len);
+  k_h_finish<<<512, 256, 0, st>>>(x, H.acc, y, H.acc_len, kdev, kstride);
 }
 
 int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaStream_t st) {
@@ -818,8 +826,8 @@ template int hodlr_build<double>(HodlrSet&, const HodlrParams&, const std::vecto
                                  const std::vector<ProbDesc>&, const SlabDesc*, const double*,
                                  cudaStream_t, std::string&);
 template void hodlr_apply<float>(HodlrSet&, const SlabDesc*, const ProbDesc*, int, const double*,
-                                 double*, int, cudaStream_t);
+                                 double*, int, cudaStream_t, const int*, int64_t);
 template void hodlr_apply<double>(HodlrSet&, const SlabDesc*, const ProbDesc*, int, const double*,
-                                  double*, int, cudaStream_t);
+                                  double*, int, cudaStream_t, const int*, int64_t);
 
 }  // namespace ddst

@@ -64,10 +64,12 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
                 const std::vector<ProbDesc>& probs, const SlabDesc* d_slabs, const T* S,
                 cudaStream_t st, std::string& msg);
 
-// y = (I - K) x (transpose = 0) or (I - K)^T x with the HODLR blocks.
+// y = (I - K) x (transpose = 0) or (I - K)^T x with the HODLR blocks; when kdev is given the
+// input is x + (*kdev - 1) * kstride (device-resident Krylov index, graph-capturable).
 template <typename T>
 void hodlr_apply(HodlrSet& H, const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
-                 const double* x, double* y, int transpose, cudaStream_t st);
+                 const double* x, double* y, int transpose, cudaStream_t st,
+                 const int* kdev = nullptr, int64_t kstride = 0);
 
 // Dense column-major expansion of S block (slab, side) into host memory `out` (ng*ng doubles).
 int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaStream_t st);

@@ -51,10 +51,28 @@ void launch_dot(const double* x, const double* y, int64_t n, double* part, int n
 void launch_sum_partials(const double* part, int np, double* out, cudaStream_t st);
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
 
-// factor.cu: forward/backward pivot inverses F, B and diagonal inverse blocks G (one size class)
+// One CTA of the pivot sweeps (factor.cu): rows start..last of one slab and direction, inverses
+// stored from `first` on, warm-up inverse of row first-1 (first+1 backward) into check slot chk.
+struct FacChunk {
+  int slab;
+  int dir;     // 0 forward (F), 1 backward (B)
+  int start;   // first row visited (1-based)
+  int first;   // first row whose inverse is stored
+  int last;    // last row visited
+  int chk;     // check slot, -1 when the chunk starts at the slab's end row (exact)
+};
+
+// factor.cu: phase 0 = pivot sweeps F, B (+ transposes) and chunk verification (diff[chunk]);
+// phase 1 = diagonal inverse blocks G.  One block-size class per call.
+// Uhi/Ulo (FP32 only, may be NULL): tensor-core operand copies of F^T (first umma_elems
+// elements) and B^T (next umma_elems), TF32 hi/lo split, K-major operand layout (umma.cuh).
 template <typename T>
-void launch_factor(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
-                   const T* pack, T* F, T* B, T* G, T* Ft, T* Bt, DevStatus* st, cudaStream_t s);
+void launch_factor(int M, int phase, const SlabDesc* d_slabs, const FacChunk* d_chunks,
+                   int nchunks, const int* d_ids, int nids, int max_nb, const T* pack, T* F,
+                   T* B, T* G, T* Ft, T* Bt, T* chk, float* diff, float* Uhi, float* Ulo,
+                   int64_t umma_elems, DevStatus* st, cudaStream_t s);
+template <typename T>
+int factor_ctas_per_sm(int M);
 
 // sweep.cu: explicit transfer operators
 template <typename T>
@@ -63,6 +81,13 @@ template <typename T>
 void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                    const T* F, const T* B, const T* G, const T* pack, T* S, DevStatus* st,
                    cudaStream_t s);
+
+// sweep_tc.cu: explicit transfer operators on tcgen05 (FP32 data, 3xTF32), M in {32, 64}
+void launch_sbuild_tc(int version, int M, const SlabDesc* d_slabs, const TileDesc* d_tiles,
+                      int ntiles, const float* Fhi, const float* Flo, const float* Bhi,
+                      const float* Blo, const float* G, const float* pack, float* S,
+                      DevStatus* st, cudaStream_t s);
+int sbuild_tc_tile_cols(int version);  // sources per CTA of the tensor-core transfer build
 
 // solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)
 template <typename T>
@@ -73,10 +98,16 @@ void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int ni
                         int transpose, int mode, DevStatus* st, cudaStream_t s);
 
 // krylov.cu
+// x may be indexed by a device-resident basis count: x_eff = x + (*kdev - 1) * kstride
 template <typename T>
 void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                         int64_t max_ng, const T* S, const double* x, double* y, int transpose,
-                        cudaStream_t st);
+                        cudaStream_t st, const int* kdev = nullptr, int64_t kstride = 0);
+// One Arnoldi step (CGS2) with device-resident state; graph-capturable (arguments fixed).
+void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
+                         double* h2, double* hn2, double* H, int ldh, double* cs, double* sn,
+                         double* gv, const double* beta, double* resid, double* inv_hn, int kmax,
+                         cudaStream_t st);
 void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k, int nchunk,
                     double* part, double* hpass, double* hcol, int accumulate, cudaStream_t st);
 void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,

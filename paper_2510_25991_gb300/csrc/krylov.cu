@@ -15,9 +15,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict__ slabs,
                                                      const ProbDesc* __restrict__ probs,
                                                      const T* __restrict__ S,
-                                                     const double* __restrict__ x,
-                                                     double* __restrict__ y) {
+                                                     const double* __restrict__ x0,
+                                                     double* __restrict__ y, const int* kdev,
+                                                     int64_t kstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const SlabDesc s = slabs[blockIdx.y];
   const ProbDesc P = probs[s.prob];
   const int64_t ng = s.ng;
@@ -69,8 +71,10 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
                                                        const ProbDesc* __restrict__ probs,
                                                        const T* __restrict__ S,
-                                                       const double* __restrict__ x,
-                                                       double* __restrict__ y) {
+                                                       const double* __restrict__ x0,
+                                                       double* __restrict__ y, const int* kdev,
+                                                       int64_t kstride) {
+  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int sidx = blockIdx.y;
   const SlabDesc s = slabs[sidx];
   const ProbDesc P = probs[s.prob];
@@ -226,11 +230,167 @@ __global__ void k_trisolve(const double* __restrict__ H, int ldh, const double* 
   }
 }
 
+// ---- Fused Arnoldi step with device-resident state (graph-capturable) -----------------------
+// State: st->k basis vectors V[0..k) exist; w = (I - K) V[k-1] has just been formed.
+// h1, h2 (FP64, zeroed) receive the two classical Gram-Schmidt passes by atomics; hn2 the
+// squared norm of the twice-orthogonalized w.  Chunk of ARN_CHUNK elements per CTA.
+constexpr int ARN_T = 256, ARN_E = 4, ARN_CHUNK = ARN_T * ARN_E;
+
+__device__ __forceinline__ void arn_block_dot_accumulate(const double* __restrict__ V, int64_t n,
+                                                         int k, int64_t base, const double (&wv)[ARN_E],
+                                                         double* __restrict__ hout) {
+  __shared__ double part[1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) part[i] = 0.0;
+  __syncthreads();
+  for (int i = 0; i < k; ++i) {
+    const double* v = V + (int64_t)i * n;
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < ARN_E; ++e) {
+      const int64_t idx = base + e * ARN_T + threadIdx.x;
+      if (idx < n) acc = fma(v[idx], wv[e], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) atomicAdd(&part[i], acc);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) atomicAdd(&hout[i], part[i]);
+  (void)warp;
+}
+
+// pass 1 dots: h1[i] += V[i] . w
+__global__ void __launch_bounds__(ARN_T) k_arn_dots(const double* __restrict__ V,
+                                                    const double* __restrict__ w, int64_t n,
+                                                    const int* __restrict__ kdev,
+                                                    double* __restrict__ h1) {
+  const int k = *kdev;
+  const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
+  double wv[ARN_E];
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) {
+    const int64_t idx = base + e * ARN_T + threadIdx.x;
+    wv[e] = idx < n ? w[idx] : 0.0;
+  }
+  arn_block_dot_accumulate(V, n, k, base, wv, h1);
+}
+
+// w -= V h_in (chunk); then either h_out[i] += V[i] . w (dots = 1) or hn2 += |w|^2.
+__global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__ V,
+                                                      double* __restrict__ w, int64_t n,
+                                                      const int* __restrict__ kdev,
+                                                      const double* __restrict__ h_in,
+                                                      double* __restrict__ h_out,
+                                                      double* __restrict__ hn2, int dots) {
+  __shared__ double sh[1024];
+  const int k = *kdev;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = h_in[i];
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
+  double wv[ARN_E];
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) {
+    const int64_t idx = base + e * ARN_T + threadIdx.x;
+    wv[e] = idx < n ? w[idx] : 0.0;
+  }
+  for (int i = 0; i < k; ++i) {
+    const double* v = V + (int64_t)i * n;
+    const double hi = sh[i];
+#pragma unroll
+    for (int e = 0; e < ARN_E; ++e) {
+      const int64_t idx = base + e * ARN_T + threadIdx.x;
+      if (idx < n) wv[e] = fma(-hi, v[idx], wv[e]);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) {
+    const int64_t idx = base + e * ARN_T + threadIdx.x;
+    if (idx < n) w[idx] = wv[e];
+  }
+  if (dots) {
+    arn_block_dot_accumulate(V, n, k, base, wv, h_out);
+  } else {
+    double acc = 0.0;
+#pragma unroll
+    for (int e = 0; e < ARN_E; ++e) acc = fma(wv[e], wv[e], acc);
+    __shared__ double red[ARN_T / 32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double t = threadIdx.x < ARN_T / 32 ? red[threadIdx.x] : 0.0;
+      t = warp_sum(t);
+      if (threadIdx.x == 0) atomicAdd(hn2, t);
+    }
+  }
+}
+
+// Givens step for column j = k-1, then k <- k+1 and the accumulators are cleared for the next
+// step.  Single thread.  inv_hn[0] = 1/||w|| (0 at breakdown).
+__global__ void k_arn_givens(int* __restrict__ kdev, double* __restrict__ h1,
+                             double* __restrict__ h2, double* __restrict__ hn2,
+                             double* __restrict__ H, int ldh, double* __restrict__ cs,
+                             double* __restrict__ sn, double* __restrict__ gv,
+                             const double* __restrict__ beta, double* __restrict__ resid,
+                             double* __restrict__ inv_hn, int kmax) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int k = *kdev;
+  const int j = k - 1;
+  double* col = H + (int64_t)j * ldh;
+  for (int i = 0; i <= j; ++i) {
+    col[i] = h1[i] + h2[i];
+    h1[i] = 0.0;
+    h2[i] = 0.0;
+  }
+  const double sub = sqrt(fmax(hn2[0], 0.0));
+  hn2[0] = 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double a = col[j], b = sub;
+  const double den = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (den > 0.0) { c = a / den; s = b / den; }
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = den;
+  gv[j + 1] = -s * gv[j];
+  gv[j] = c * gv[j];
+  resid[j] = fabs(gv[j + 1]) / beta[0];
+  inv_hn[0] = sub > 0.0 ? 1.0 / sub : 0.0;
+  if (k < kmax) *kdev = k + 1;
+}
+
+// V[k-1] = w * inv_hn with k already advanced by k_arn_givens.
+__global__ void k_arn_scale(const double* __restrict__ w, double* __restrict__ V, int64_t n,
+                            const int* __restrict__ kdev, const double* __restrict__ inv_hn) {
+  const double a = inv_hn[0];
+  double* out = V + (int64_t)(*kdev - 1) * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = a * w[e];
+}
+
+void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
+                         double* h2, double* hn2, double* H, int ldh, double* cs, double* sn,
+                         double* gv, const double* beta, double* resid, double* inv_hn, int kmax,
+                         cudaStream_t st) {
+  const unsigned nb = (unsigned)((n + ARN_CHUNK - 1) / ARN_CHUNK);
+  note_launch(5);
+  k_arn_dots<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h1);
+  k_arn_update<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h1, h2, hn2, 1);
+  k_arn_update<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h2, nullptr, hn2, 0);
+  k_arn_givens<<<1, 32, 0, st>>>(kdev, h1, h2, hn2, H, ldh, cs, sn, gv, beta, resid, inv_hn, kmax);
+  k_arn_scale<<<1024, 256, 0, st>>>(w, V, n, kdev, inv_hn);
+}
+
 // ------------------------------------------------------------------------------------------
 template <typename T>
 void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                         int64_t max_ng, const T* S, const double* x, double* y, int transpose,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* kdev, int64_t kstride) {
   if (!transpose) {
     const size_t smem = 2 * max_ng * sizeof(T);
     static size_t attr = 0;
@@ -240,19 +400,20 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
     }
     note_launch();
     k_apply_dense<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smem, st>>>(
-        d_slabs, d_probs, S, x, y);
+        d_slabs, d_probs, S, x, y, kdev, kstride);
   } else {
     note_launch();
     k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 7) / 8), nslab), 256, 0, st>>>(d_slabs, d_probs,
-                                                                                  S, x, y);
+                                                                                  S, x, y, kdev, kstride);
   }
 }
 
 template void launch_apply_dense<float>(const SlabDesc*, const ProbDesc*, int, int64_t,
-                                        const float*, const double*, double*, int, cudaStream_t);
+                                        const float*, const double*, double*, int, cudaStream_t,
+                                        const int*, int64_t);
 template void launch_apply_dense<double>(const SlabDesc*, const ProbDesc*, int, int64_t,
                                          const double*, const double*, double*, int,
-                                         cudaStream_t);
+                                         cudaStream_t, const int*, int64_t);
 
 void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k,
                     int nchunk, double* part, double* hpass, double* hcol, int accumulate,

@@ -14,7 +14,8 @@ from . import _lib as L
 __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
-           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_residual_noalloc",
+           "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
+           "ddst_residual_noalloc",
            "ddst_kernel_launches",
            "ddst_last_error",
            "ddst_destroy", "Solver", "DDSTSolve"]
@@ -55,7 +56,7 @@ def ddst_options_default(**overrides):
     lib.ddst_options_default(C.byref(o))
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
-            v = L.DDST_FP64 if v.lower() == "fp64" else L.DDST_MIXED
+            v = {"fp64": L.DDST_FP64, "mixed": L.DDST_MIXED, "auto": L.DDST_AUTO}[v.lower()]
         setattr(o, k, v)
     return o
 
@@ -171,6 +172,14 @@ def ddst_query(ctx, prob=0):
     return nds.value, ng.value, mr.value
 
 
+def ddst_get_precision(ctx):
+    """"fp64" or "mixed": the arithmetic the context was set up with (what "auto" chose)."""
+    lib = L.load()
+    p = C.c_int()
+    _check(lib, ctx, lib.ddst_get_precision(ctx, C.byref(p)))
+    return "fp64" if p.value == L.DDST_FP64 else "mixed"
+
+
 def ddst_residual_noalloc(dim, n, a, f, g, u, r, norms, b=(0.0, 0.0, 0.0), c=None, stream=None):
     """Allocation-free FP64 residual r = b(f, g) - A u and norms (||r||, ||b||); device arrays
     only.  Stream-ordered: synchronize before reading the results."""
@@ -207,6 +216,11 @@ class Solver:
         self.options = ddst_options_default(precision=precision, **opts)
         self._keep = problems  # keep host arrays alive during setup
         self.ctx = ddst_setup_batch(problems, self.options, stream)
+
+    @property
+    def precision(self):
+        """"fp64" or "mixed" (the choice of precision="auto")."""
+        return ddst_get_precision(self.ctx)
 
     def build_transfer(self):
         ddst_build_transfer(self.ctx)

@@ -25,7 +25,8 @@ def dev(x):
 def solver(prob, precision, **opts):
     from paper_2510_25991_gb300 import ddst as D
     sol = D.Solver(dict(dim=prob["dim"], n=prob["n"], w=prob["w"], a=dev(prob["a"]),
-                        b=tuple(prob["b"]) + (0.0,) * (3 - len(prob["b"]))),
+                        b=tuple(prob["b"]) + (0.0,) * (3 - len(prob["b"])),
+                        c=dev(prob["c"]) if prob.get("c") is not None else None),
                    precision=precision, **opts)
     sol.build_transfer()
     return sol
@@ -77,6 +78,41 @@ def test_hodlr_error_within_ten_tol_and_ranks_near_optimal(tol):
     sol.close()
     assert worst <= 10 * tol, worst
     # randomized range finder: ranks at most the optimal (truncated SVD) rank + oversampling
+    assert opt_max_rank <= gpu_max_rank <= opt_max_rank + q, (gpu_max_rank, opt_max_rank)
+
+
+@pytest.fixture(scope="module")
+def helmholtz_blocks():
+    """Helmholtz at 512^2, kappa = 100, 2w = 16-cell slabs (positive definite local operators by
+    ~1%, the margin of the 4096^2, kappa = 200, w = 32 workload): every transfer block."""
+    prob = I.make_problem("helmholtz2d", n=512, w=8, kappa=100.0)
+    return (prob,) + oracle_blocks(prob)
+
+
+@pytest.mark.parametrize("tol", [1e-6, 1e-8, 1e-10])
+def test_helmholtz_hodlr_ranks_vs_tol(helmholtz_blocks, tol):
+    """Ranks against the tolerance for the Helmholtz transfer operators: the error stays within
+    10 tol and the ranks between the truncated-SVD optimum and optimum + oversampling."""
+    from paper_2510_25991_gb300 import ddst as D
+    prob, geo, (Sp, Sn) = helmholtz_blocks
+    leaf, q = 32, 10
+    sol = solver(prob, "fp64", leaf_size=leaf, k_max=64, oversample=q)
+    sol.compress(tol)
+    _, _, gpu_max_rank = D.ddst_query(sol.ctx)
+    out = np.empty((geo.ngamma, geo.ngamma))
+    worst, opt_max_rank = 0.0, 0
+    for j in range(geo.nds):
+        for side, ref in ((-1, Sp[j]), (1, Sn[j])):
+            if ref is None:
+                continue
+            nrm = np.linalg.norm(ref, 2)
+            H = O.hodlr_compress(ref, tol, leaf, norm2=nrm)
+            opt_max_rank = max(opt_max_rank, max(U.shape[1] for lev in H["levels"] for U, _ in lev))
+            if j in (1, geo.nds // 2, geo.nds - 2):
+                D.ddst_get_transfer(sol.ctx, 0, j + 1, side, out)
+                worst = max(worst, np.linalg.norm(out - ref, 2) / nrm)
+    sol.close()
+    assert worst <= 10 * tol, worst
     assert opt_max_rank <= gpu_max_rank <= opt_max_rank + q, (gpu_max_rank, opt_max_rank)
 
 
