@@ -128,6 +128,18 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _tc_executed_flops(nds, nb, MB, tile=128, per_cta=256):
+    """MMA flops the tensor-core transfer build issues (2D): a CTA of 256 sources runs len - 1
+    steps of 3 (128 x MB x MB) MMAs per live 128-source tile."""
+    tot = 0
+    for q0 in range(0, nb, per_cta):
+        nq = min(per_cta, nb - q0)
+        live = -(-nq // tile)
+        for length in (q0 + nq, nb - q0):  # upward sweep from block q0 + nq, downward from q0 + 1
+            tot += max(0, length - 1) * live
+    return float(nds * tot * 3 * 2 * tile * MB * MB)
+
+
 def cpu_baseline(n=512):
     import ddst_inputs as I
     from oracle import ddst_oracle as O
@@ -269,27 +281,35 @@ def main():
         fp64 = {"dof_per_s": dof / (f_ms / 1e3), "ms": f_ms, "gmres_iters": finfo["gmres_iters"],
                 "refine_iters": finfo["refine_iters"], "est_rel_error": finfo["est_rel_error"]}
 
-    # roofline of the dominant kernel: the multi-RHS sweep that forms S (k_sbuild), FP32 FMA
+    # roofline of the dominant kernel: the transfer build (k_sbuild_tc), one launch per step,
+    # timed by the CUDA events around ddst_build_transfer on the stream it is launched on.
+    # Algorithmic work: every central source visits every other block once, one (m x m) by
+    # (m x 1) product per visit (2 m^2 flops).  The tensor core executes 3xTF32 on padded blocks
+    # (3 MMAs of 2 MB^2 flops per visit and source), reported as executed_tensor_flops.
     peaks, src = _peaks()
     m = 2 * w - 1
+    MB = 32 if m <= 32 else 64
     nb = n - 1
     nds = n // w - 1
-    flops = nds * nb * (nb - 1) * 2.0 * m * m   # every central source visits every other block once
+    flops = nds * nb * (nb - 1) * 2.0 * m * m
     sb_ms = statistics.mean(sb)
     achieved = flops / (sb_ms / 1e3) / 1e12
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x SM clock
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # dense TF32 : BF16 = 1.1 : 2.25 (nominal)
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "sbuild_traffic.json")) as fh:
-            traffic = json.load(fh).get("bytes_per_launch_fullsize")
+        with open(os.path.join(ROOT, "profiles", "sbuild_tc_traffic.json")) as fh:
+            tj = json.load(fh)
+        if tj.get("n") == n and tj.get("w") == w:
+            traffic = tj.get("bytes_per_launch")
     except Exception:
         pass
-    roof = {"kernel": "k_sbuild (explicit S: multi-RHS transposed sweeps)", "bound": "alu",
-            "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+    roof = {"kernel": "k_sbuild_tc (explicit S: tcgen05 3xTF32 two-sided sweeps)", "bound": "tensor",
+            "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved / tf32_peak,
             "traffic": traffic,
-            "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median SM clock under load)",
-            "algorithmic_flops_per_launch": flops, "avg_launch_ms": sb_ms}
+            "peak_source": f"{src} bf16 burst {peaks['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal TF32:BF16), of {src}",
+            "algorithmic_flops_per_launch": flops,
+            "executed_tensor_flops_per_launch": _tc_executed_flops(nds, nb, MB),
+            "avg_launch_ms": sb_ms}
 
     info = infos[-1]
     line = {"metric": "DOF/s to 1e-8 rel. error, mixed-precision vs FP64 GPU path; s per adjoint gradient",

@@ -88,6 +88,8 @@ struct ddst_ctx {
   cudaGraphExec_t arn_graph[2] = {nullptr, nullptr};  // one GMRES step (plain / transposed)
   int arn_graph_state[2] = {0, 0};       // operator state the graphs were captured for
   int* d_k = nullptr;                    // device-resident Krylov basis count
+  double* arn_part = nullptr;            // Arnoldi partial sums: 2 (maxit+1) + 1 rows of chunks
+  unsigned* arn_ticket = nullptr;        // last-CTA ticket of the Arnoldi finish kernel
   double *h1 = nullptr, *h2 = nullptr, *d_beta = nullptr;
   float *Uhi = nullptr, *Ulo = nullptr;  // tensor-core operand copies of F^T | B^T
 };
@@ -480,7 +482,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   Timer tm(st);
   for (auto& kv : ctx->cls) {
     const int M = kv.first;
-    const int R = (sizeof(T) == 4 && ctx->use_tc) ? sbuild_tc_tile_cols(ctx->opt.tensor_cores)
+    const int R = (sizeof(T) == 4 && ctx->use_tc) ? sbuild_tc_tile_cols()
                                                   : sbuild_tile_cols<T>(M);
     std::vector<TileDesc> tiles;
     for (int sid : kv.second) {
@@ -506,7 +508,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
                        cudaMemcpyHostToDevice, st));
     if constexpr (sizeof(T) == 4) {
       if (ctx->use_tc)
-        launch_sbuild_tc(ctx->opt.tensor_cores, M, ctx->d_slabs, d_tiles, (int)tiles.size(), ctx->Uhi, ctx->Ulo,
+        launch_sbuild_tc(M, ctx->d_slabs, d_tiles, (int)tiles.size(), ctx->Uhi, ctx->Ulo,
                          ctx->Uhi + ctx->fac_elems, ctx->Ulo + ctx->fac_elems, (const float*)ctx->G,
                          (const float*)ctx->pack, (float*)ctx->S, ctx->d_st, st);
       else
@@ -571,6 +573,10 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   AL(ctx->h1, sizeof(double) * (maxit + 1));
   AL(ctx->h2, sizeof(double) * (maxit + 1));
   AL(ctx->d_beta, sizeof(double) * 2);
+  AL(ctx->arn_part, sizeof(double) * (size_t)(2 * (maxit + 1) + 1) * arnoldi_chunks(ctx->tot_if));
+  AL(ctx->arn_ticket, sizeof(unsigned) * 4);
+  if ((e = cudaMemsetAsync(ctx->arn_ticket, 0, sizeof(unsigned) * 4, ctx->stream)) != cudaSuccess)
+    return cuda_fail(ctx, e, "memset ticket");
 #undef AL
   return DDST_OK;
 }
@@ -606,9 +612,9 @@ ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose, ctx->cap_stream, ctx->d_k, n);
-  launch_arnoldi_step(ctx->V, ctx->if_w, n, ctx->d_k, ctx->h1, ctx->h2, ctx->scal + 1, ctx->H,
-                      ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta, ctx->resid, ctx->scal + 2,
-                      maxit, ctx->cap_stream);
+  launch_arnoldi_step(ctx->V, ctx->if_w, n, ctx->d_k, ctx->h1, ctx->h2, ctx->arn_part,
+                      ctx->arn_ticket, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta,
+                      ctx->resid, maxit, ctx->cap_stream);
   const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
   if (ec != cudaSuccess) {
     cudaGetLastError();
@@ -664,7 +670,7 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   int k = 0;
   for (k = 1; k <= maxit; ++k) {
     CK(cudaGraphLaunch(graph, st));
-    note_launch(ctx->state == 3 ? 9 : 6);
+    note_launch(ctx->state == 3 ? 8 : 5);
     if (k % check == 0 || k == maxit) {
       CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));

@@ -254,10 +254,20 @@ __global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ sla
     if ((k - ch.first) * sgn >= 0) {
       store_block<T, M>(X, out + (int64_t)(k - 1) * M * M, outT + (int64_t)(k - 1) * M * M);
       if constexpr (sizeof(T) == 4) {
-        if (Uhi)  // tensor-core operand copy (transposed, TF32 hi/lo, K-major layout)
-          store_umma_split_T(reinterpret_cast<const float*>(X), LD, M,
+        // tensor-core operand copy of the transfer-build step (transposed, TF32 hi/lo, K-major):
+        // forward -diag(ell_{k+1}) F_k, backward -diag(ups_{k-1}) B_k, so that a sweep step of
+        // Alg. 1 is the plain product Y_next^T = Y^T (scaled copy).  The copies of F_nb and B_1
+        // are never used and are written as zeros.
+        if (Uhi) {
+          const int kn = k + sgn;  // the block whose coupling scales this inverse
+          const float* scl = (kn >= 1 && kn <= s.nb)
+                                 ? reinterpret_cast<const float*>(pack) + s.pack_off +
+                                       (int64_t)(kn - 1) * PK_NFIELDS * M + rowfield * M
+                                 : nullptr;
+          store_umma_split_T(reinterpret_cast<const float*>(X), LD, M, scl,
                              Uhi + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M,
                              Ulo + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M);
+        }
       }
     }
     else if (ch.chk >= 0 && k == ch.first - sgn)

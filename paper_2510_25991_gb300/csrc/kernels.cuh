@@ -83,11 +83,11 @@ void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int 
                    cudaStream_t s);
 
 // sweep_tc.cu: explicit transfer operators on tcgen05 (FP32 data, 3xTF32), M in {32, 64}
-void launch_sbuild_tc(int version, int M, const SlabDesc* d_slabs, const TileDesc* d_tiles,
-                      int ntiles, const float* Fhi, const float* Flo, const float* Bhi,
-                      const float* Blo, const float* G, const float* pack, float* S,
-                      DevStatus* st, cudaStream_t s);
-int sbuild_tc_tile_cols(int version);  // sources per CTA of the tensor-core transfer build
+void launch_sbuild_tc(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
+                      const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
+                      const float* G, const float* pack, float* S, DevStatus* st,
+                      cudaStream_t s);
+int sbuild_tc_tile_cols();  // sources per CTA of the tensor-core transfer build
 
 // solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)
 template <typename T>
@@ -104,10 +104,11 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
                         int64_t max_ng, const T* S, const double* x, double* y, int transpose,
                         cudaStream_t st, const int* kdev = nullptr, int64_t kstride = 0);
 // One Arnoldi step (CGS2) with device-resident state; graph-capturable (arguments fixed).
-void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
-                         double* h2, double* hn2, double* H, int ldh, double* cs, double* sn,
-                         double* gv, const double* beta, double* resid, double* inv_hn, int kmax,
+void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1, double* h2,
+                         double* part, unsigned* ticket, double* H, int ldh, double* cs,
+                         double* sn, double* gv, const double* beta, double* resid, int kmax,
                          cudaStream_t st);
+int arnoldi_chunks(int64_t n);  // chunks of the Arnoldi kernels (partial sums per chunk)
 void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k, int nchunk,
                     double* part, double* hpass, double* hcol, int accumulate, cudaStream_t st);
 void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,

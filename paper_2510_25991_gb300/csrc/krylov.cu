@@ -230,85 +230,140 @@ __global__ void k_trisolve(const double* __restrict__ H, int ldh, const double* 
   }
 }
 
-// ---- Fused Arnoldi step with device-resident state (graph-capturable) -----------------------
-// State: st->k basis vectors V[0..k) exist; w = (I - K) V[k-1] has just been formed.
-// h1, h2 (FP64, zeroed) receive the two classical Gram-Schmidt passes by atomics; hn2 the
-// squared norm of the twice-orthogonalized w.  Chunk of ARN_CHUNK elements per CTA.
-constexpr int ARN_T = 256, ARN_E = 4, ARN_CHUNK = ARN_T * ARN_E;
+// ---- Arnoldi step with device-resident state (graph-capturable) ---------------------------
+// State: *kdev = k basis vectors V[0..k) exist; w = (I - K) V[k-1] has just been formed.  One
+// step is classical Gram-Schmidt applied twice (CGS2), the Givens update of the least-squares
+// problem and the normalization V[k] = w / ||w||:
+//   dots   : P1[i][c] = V[i] . w over chunk c
+//   update : h1 = sum_c P1;  w -= V h1;  P2[i][c] = V[i] . w
+//   update : h2 = sum_c P2;  w -= V h2;  Pn[c] = |w|^2 over chunk c
+//   finish : V[k] = w / sqrt(sum_c Pn); the last CTA to finish applies the Givens rotations to
+//            H(:, k-1) = h1 + h2 and advances *kdev.
+// Partial sums are stored per chunk (i-major, coalesced for the readers) and reduced by each
+// consumer CTA: no two CTAs update the same address.
+constexpr int ARN_T = 256, ARN_E = 4, ARN_CHUNK = ARN_T * ARN_E, ARN_G = 8;
 
-__device__ __forceinline__ void arn_block_dot_accumulate(const double* __restrict__ V, int64_t n,
-                                                         int k, int64_t base, const double (&wv)[ARN_E],
-                                                         double* __restrict__ hout) {
-  __shared__ double part[1024];
+// sh[i] = sum_c P[i * nchunk + c] for i < k (every thread of the CTA takes part).
+__device__ __forceinline__ void arn_reduce(const double* __restrict__ P, int nchunk, int k,
+                                           double* __restrict__ sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) part[i] = 0.0;
-  __syncthreads();
-  for (int i = 0; i < k; ++i) {
-    const double* v = V + (int64_t)i * n;
-    double acc = 0.0;
-#pragma unroll
-    for (int e = 0; e < ARN_E; ++e) {
-      const int64_t idx = base + e * ARN_T + threadIdx.x;
-      if (idx < n) acc = fma(v[idx], wv[e], acc);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) atomicAdd(&part[i], acc);
+  for (int i = warp; i < k; i += ARN_T / 32) {
+    const double* row = P + (int64_t)i * nchunk;
+    double a = 0.0;
+    for (int c = lane; c < nchunk; c += 32) a += row[c];
+    a = warp_sum(a);
+    if (lane == 0) sh[i] = a;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < k; i += blockDim.x) atomicAdd(&hout[i], part[i]);
-  (void)warp;
 }
 
-// pass 1 dots: h1[i] += V[i] . w
+// P[i * nchunk + blockIdx.x] = V[i] . wv over this CTA's chunk, for i < k, ARN_G vectors at once.
+__device__ __forceinline__ void arn_chunk_dots(const double* __restrict__ V, int64_t n, int k,
+                                               int64_t base, const double (&wv)[ARN_E],
+                                               double* __restrict__ P, int nchunk) {
+  __shared__ double red[2][ARN_T / 32][ARN_G];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int buf = 0;
+  for (int i0 = 0; i0 < k; i0 += ARN_G, buf ^= 1) {
+    double acc[ARN_G];
+#pragma unroll
+    for (int g = 0; g < ARN_G; ++g) acc[g] = 0.0;
+#pragma unroll
+    for (int g = 0; g < ARN_G; ++g) {
+      if (i0 + g < k) {
+        const double* v = V + (int64_t)(i0 + g) * n;
+#pragma unroll
+        for (int e = 0; e < ARN_E; ++e) {
+          const int64_t idx = base + e * ARN_T + threadIdx.x;
+          if (idx < n) acc[g] = fma(v[idx], wv[e], acc[g]);
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < ARN_G; ++g) {
+      const double t = warp_sum(acc[g]);
+      if (lane == 0) red[buf][warp][g] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < ARN_G && i0 + threadIdx.x < k) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < ARN_T / 32; ++q) t += red[buf][q][threadIdx.x];
+      P[(int64_t)(i0 + threadIdx.x) * nchunk + blockIdx.x] = t;
+    }
+  }
+}
+
+__device__ __forceinline__ void arn_load_chunk(const double* __restrict__ w, int64_t n,
+                                               int64_t base, double (&wv)[ARN_E]) {
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) {
+    const int64_t idx = base + e * ARN_T + threadIdx.x;
+    wv[e] = idx < n ? w[idx] : 0.0;
+  }
+}
+
+// wv -= sum_{i<k} h[i] V[i] over this CTA's chunk, ARN_G vectors at once.
+__device__ __forceinline__ void arn_chunk_update(const double* __restrict__ V, int64_t n, int k,
+                                                 int64_t base, const double* __restrict__ h,
+                                                 double (&wv)[ARN_E]) {
+  for (int i0 = 0; i0 < k; i0 += ARN_G) {
+    double vv[ARN_G][ARN_E];
+#pragma unroll
+    for (int g = 0; g < ARN_G; ++g) {
+      const double* v = V + (int64_t)(i0 + g) * n;
+#pragma unroll
+      for (int e = 0; e < ARN_E; ++e) {
+        const int64_t idx = base + e * ARN_T + threadIdx.x;
+        vv[g][e] = (i0 + g < k && idx < n) ? v[idx] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < ARN_G; ++g) {
+      const double hg = i0 + g < k ? h[i0 + g] : 0.0;
+#pragma unroll
+      for (int e = 0; e < ARN_E; ++e) wv[e] = fma(-hg, vv[g][e], wv[e]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(ARN_T) k_arn_dots(const double* __restrict__ V,
                                                     const double* __restrict__ w, int64_t n,
                                                     const int* __restrict__ kdev,
-                                                    double* __restrict__ h1) {
+                                                    double* __restrict__ P1, int nchunk) {
   const int k = *kdev;
   const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
   double wv[ARN_E];
-#pragma unroll
-  for (int e = 0; e < ARN_E; ++e) {
-    const int64_t idx = base + e * ARN_T + threadIdx.x;
-    wv[e] = idx < n ? w[idx] : 0.0;
-  }
-  arn_block_dot_accumulate(V, n, k, base, wv, h1);
+  arn_load_chunk(w, n, base, wv);
+  arn_chunk_dots(V, n, k, base, wv, P1, nchunk);
 }
 
-// w -= V h_in (chunk); then either h_out[i] += V[i] . w (dots = 1) or hn2 += |w|^2.
+// h = sum_c Pin (CTA 0 also stores it in hout); w -= V h; then P2 = V . w (dots) or
+// Pn[c] = |w|^2 over the chunk.
 __global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__ V,
                                                       double* __restrict__ w, int64_t n,
                                                       const int* __restrict__ kdev,
-                                                      const double* __restrict__ h_in,
-                                                      double* __restrict__ h_out,
-                                                      double* __restrict__ hn2, int dots) {
+                                                      const double* __restrict__ Pin,
+                                                      double* __restrict__ hout,
+                                                      double* __restrict__ Pout,
+                                                      double* __restrict__ Pn, int nchunk,
+                                                      int dots) {
   __shared__ double sh[1024];
   const int k = *kdev;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = h_in[i];
-  __syncthreads();
+  arn_reduce(Pin, nchunk, k, sh);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < k; i += ARN_T) hout[i] = sh[i];
   const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
   double wv[ARN_E];
-#pragma unroll
-  for (int e = 0; e < ARN_E; ++e) {
-    const int64_t idx = base + e * ARN_T + threadIdx.x;
-    wv[e] = idx < n ? w[idx] : 0.0;
-  }
-  for (int i = 0; i < k; ++i) {
-    const double* v = V + (int64_t)i * n;
-    const double hi = sh[i];
-#pragma unroll
-    for (int e = 0; e < ARN_E; ++e) {
-      const int64_t idx = base + e * ARN_T + threadIdx.x;
-      if (idx < n) wv[e] = fma(-hi, v[idx], wv[e]);
-    }
-  }
+  arn_load_chunk(w, n, base, wv);
+  arn_chunk_update(V, n, k, base, sh, wv);
 #pragma unroll
   for (int e = 0; e < ARN_E; ++e) {
     const int64_t idx = base + e * ARN_T + threadIdx.x;
     if (idx < n) w[idx] = wv[e];
   }
   if (dots) {
-    arn_block_dot_accumulate(V, n, k, base, wv, h_out);
+    arn_chunk_dots(V, n, k, base, wv, Pout, nchunk);
   } else {
     double acc = 0.0;
 #pragma unroll
@@ -320,70 +375,99 @@ __global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__
     if (threadIdx.x < 32) {
       double t = threadIdx.x < ARN_T / 32 ? red[threadIdx.x] : 0.0;
       t = warp_sum(t);
-      if (threadIdx.x == 0) atomicAdd(hn2, t);
+      if (threadIdx.x == 0) Pn[blockIdx.x] = t;
     }
   }
 }
 
-// Givens step for column j = k-1, then k <- k+1 and the accumulators are cleared for the next
-// step.  Single thread.  inv_hn[0] = 1/||w|| (0 at breakdown).
-__global__ void k_arn_givens(int* __restrict__ kdev, double* __restrict__ h1,
-                             double* __restrict__ h2, double* __restrict__ hn2,
-                             double* __restrict__ H, int ldh, double* __restrict__ cs,
-                             double* __restrict__ sn, double* __restrict__ gv,
-                             const double* __restrict__ beta, double* __restrict__ resid,
-                             double* __restrict__ inv_hn, int kmax) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// V[k] = w / ||w|| over this CTA's chunk (0 at breakdown).  The last CTA to get here (atomic
+// ticket after a fence; nothing waits) applies the previous Givens rotations to
+// H(:, k-1) = h1 + h2, forms the new one, records the residual estimate and advances *kdev.
+__global__ void __launch_bounds__(ARN_T) k_arn_finish(double* __restrict__ V,
+                                                      const double* __restrict__ w, int64_t n,
+                                                      int* __restrict__ kdev,
+                                                      const double* __restrict__ Pn, int nchunk,
+                                                      const double* __restrict__ h1,
+                                                      const double* __restrict__ h2,
+                                                      double* __restrict__ H, int ldh,
+                                                      double* __restrict__ cs,
+                                                      double* __restrict__ sn,
+                                                      double* __restrict__ gv,
+                                                      const double* __restrict__ beta,
+                                                      double* __restrict__ resid, int kmax,
+                                                      unsigned* __restrict__ ticket) {
+  __shared__ double s_hn2;
+  __shared__ bool s_last;
   const int k = *kdev;
+  if (threadIdx.x < 32) {
+    double a = 0.0;
+    for (int c = threadIdx.x; c < nchunk; c += 32) a += Pn[c];
+    a = warp_sum(a);
+    if (threadIdx.x == 0) s_hn2 = a;
+  }
+  __syncthreads();
+  const double sub = sqrt(fmax(s_hn2, 0.0));
+  const double inv = sub > 0.0 ? 1.0 / sub : 0.0;
+  const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
+  double* out = V + (int64_t)k * n;
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) {
+    const int64_t idx = base + e * ARN_T + threadIdx.x;
+    if (idx < n) out[idx] = inv * w[idx];
+  }
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  // Givens update of column j = k - 1 (single CTA)
+  __shared__ double col[1024], c_s[1024], s_s[1024];
   const int j = k - 1;
-  double* col = H + (int64_t)j * ldh;
-  for (int i = 0; i <= j; ++i) {
-    col[i] = h1[i] + h2[i];
-    h1[i] = 0.0;
-    h2[i] = 0.0;
+  for (int i = threadIdx.x; i <= j; i += ARN_T) col[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i < j; i += ARN_T) {
+    c_s[i] = cs[i];
+    s_s[i] = sn[i];
   }
-  const double sub = sqrt(fmax(hn2[0], 0.0));
-  hn2[0] = 0.0;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < j; ++i) {
+      const double t = c_s[i] * col[i] + s_s[i] * col[i + 1];
+      col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
+      col[i] = t;
+    }
+    const double a = col[j], b = sub;
+    const double den = hypot(a, b);
+    double c = 1.0, s = 0.0;
+    if (den > 0.0) { c = a / den; s = b / den; }
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = den;
+    gv[j + 1] = -s * gv[j];
+    gv[j] = c * gv[j];
+    resid[j] = fabs(gv[j + 1]) / beta[0];
+    if (k < kmax) *kdev = k + 1;
+    *ticket = 0u;
   }
-  const double a = col[j], b = sub;
-  const double den = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (den > 0.0) { c = a / den; s = b / den; }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = den;
-  gv[j + 1] = -s * gv[j];
-  gv[j] = c * gv[j];
-  resid[j] = fabs(gv[j + 1]) / beta[0];
-  inv_hn[0] = sub > 0.0 ? 1.0 / sub : 0.0;
-  if (k < kmax) *kdev = k + 1;
+  __syncthreads();
+  double* hc = H + (int64_t)j * ldh;
+  for (int i = threadIdx.x; i <= j; i += ARN_T) hc[i] = col[i];
 }
 
-// V[k-1] = w * inv_hn with k already advanced by k_arn_givens.
-__global__ void k_arn_scale(const double* __restrict__ w, double* __restrict__ V, int64_t n,
-                            const int* __restrict__ kdev, const double* __restrict__ inv_hn) {
-  const double a = inv_hn[0];
-  double* out = V + (int64_t)(*kdev - 1) * n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = a * w[e];
-}
+int arnoldi_chunks(int64_t n) { return (int)((n + ARN_CHUNK - 1) / ARN_CHUNK); }
 
-void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
-                         double* h2, double* hn2, double* H, int ldh, double* cs, double* sn,
-                         double* gv, const double* beta, double* resid, double* inv_hn, int kmax,
+void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1, double* h2,
+                         double* part, unsigned* ticket, double* H, int ldh, double* cs,
+                         double* sn, double* gv, const double* beta, double* resid, int kmax,
                          cudaStream_t st) {
-  const unsigned nb = (unsigned)((n + ARN_CHUNK - 1) / ARN_CHUNK);
-  note_launch(5);
-  k_arn_dots<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h1);
-  k_arn_update<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h1, h2, hn2, 1);
-  k_arn_update<<<nb, ARN_T, 0, st>>>(V, w, n, kdev, h2, nullptr, hn2, 0);
-  k_arn_givens<<<1, 32, 0, st>>>(kdev, h1, h2, hn2, H, ldh, cs, sn, gv, beta, resid, inv_hn, kmax);
-  k_arn_scale<<<1024, 256, 0, st>>>(w, V, n, kdev, inv_hn);
+  const int nchunk = arnoldi_chunks(n);
+  double* P1 = part;
+  double* P2 = part + (int64_t)(kmax + 1) * nchunk;
+  double* Pn = part + 2 * (int64_t)(kmax + 1) * nchunk;
+  note_launch(4);
+  k_arn_dots<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, nchunk);
+  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, h1, P2, nullptr, nchunk, 1);
+  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P2, h2, nullptr, Pn, nchunk, 0);
+  k_arn_finish<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, Pn, nchunk, h1, h2, H, ldh, cs, sn, gv,
+                                         beta, resid, kmax, ticket);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -21,14 +21,16 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// Writes the TF32 hi/lo split of X^T in the K-major operand layout (operand row r, K index c
-// holds X(c, r)); X is M x M row-major in shared memory with leading dimension ld.
+// Writes the TF32 hi/lo split of (-diag(scale) X)^T in the K-major operand layout: operand row
+// r, K index c holds -scale[c] * X(c, r); X is M x M row-major in shared memory with leading
+// dimension ld, scale a global vector of M values (NULL: the copy is zero).
 __device__ __forceinline__ void store_umma_split_T(const float* __restrict__ X, int ld, int M,
+                                                   const float* __restrict__ scale,
                                                    float* __restrict__ hi,
                                                    float* __restrict__ lo) {
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
     const int r = e / M, c = e - r * M;
-    const float v = X[c * ld + r];
+    const float v = scale ? -scale[c] * X[c * ld + r] : 0.f;
     const float h = tf32_rna(v);
     const uint32_t o = umma_off(r, c, M) >> 2;
     hi[o] = h;
