@@ -361,18 +361,18 @@ __global__ void __launch_bounds__(256) k_project(const HItem* __restrict__ items
   }
 }
 
-// Dense leaves: copy S(lo:lo+len, lo:lo+len) of every leaf.
+// Dense leaves: copy S(lo:lo+len, lo:lo+len) of every leaf (rows len..ld of each column zero).
 template <typename T>
 __global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __restrict__ soff,
                               const int64_t* __restrict__ sng, const T* __restrict__ S,
                               T* __restrict__ D) {
   const HLeaf L = lv[blockIdx.y];
   const int64_t ng = sng[L.sblk], off = soff[L.sblk];
-  const int64_t total = L.len * L.len;
+  const int64_t total = L.ld * L.len;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = e / L.len, rr = e % L.len;
-    D[L.d_off + e] = S[off + (L.lo + c) * ng + L.lo + rr];
+    const int64_t c = e / L.ld, rr = e % L.ld;
+    D[L.d_off + e] = rr < L.len ? S[off + (L.lo + c) * ng + L.lo + rr] : T(0);
   }
 }
 
@@ -446,53 +446,94 @@ __global__ void __launch_bounds__(256) k_h_outer(const HItem* __restrict__ items
   atomicAdd(&acc[o], (double)((a0 + a1) + (a2 + a3)));
 }
 
-// Dense leaves: acc_out += D x_in (or D^T x_out).  One CTA per leaf; 256 threads = rows x
-// column groups (non-transposed) or warps over columns (transposed).
+// Dense leaves: acc_out += D x_in (or D^T x_out).  One CTA per leaf (len <= 256, column stride
+// ld a multiple of 4, so columns start on 16-byte boundaries).
+//   non-transposed: thread = (vector of VEC rows, column group); VEC = 16 bytes of T; four
+//                   columns in flight per thread; column groups reduced in shared memory;
+//   transposed:     warp per column, 16-byte vectors along the column, warp reduction.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vec_fma(const typename Vec16<T>::type& m, T x, T* a);
+template <>
+__device__ __forceinline__ void vec_fma<float>(const float4& m, float x, float* a) {
+  a[0] = fma(m.x, x, a[0]); a[1] = fma(m.y, x, a[1]); a[2] = fma(m.z, x, a[2]); a[3] = fma(m.w, x, a[3]);
+}
+template <>
+__device__ __forceinline__ void vec_fma<double>(const double2& m, double x, double* a) {
+  a[0] = fma(m.x, x, a[0]); a[1] = fma(m.y, x, a[1]);
+}
+template <typename T>
+__device__ __forceinline__ T vec_dot(const typename Vec16<T>::type& m, const T* x);
+template <>
+__device__ __forceinline__ float vec_dot<float>(const float4& m, const float* x) {
+  return m.x * x[0] + m.y * x[1] + m.z * x[2] + m.w * x[3];
+}
+template <>
+__device__ __forceinline__ double vec_dot<double>(const double2& m, const double* x) {
+  return m.x * x[0] + m.y * x[1];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_h_leaf(const HLeaf* __restrict__ lv,
                                                 const T* __restrict__ D,
                                                 const double* __restrict__ x0,
                                                 double* __restrict__ acc, int transpose,
                                                 const int* kdev, int64_t kstride) {
+  using V = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const HLeaf L = lv[blockIdx.x];
   const T* M = D + L.d_off;
-  const int len = (int)L.len;  // <= 256 (leaf size)
-  __shared__ T sx[256];
-  __shared__ double red[256];
+  const int len = (int)L.len, ld = (int)L.ld;  // len <= 256, ld = len rounded up to 4
+  __shared__ __align__(16) T sx[256];
+  __shared__ T red[256 * 4];
   const double* xv = x + (transpose ? L.out_if : L.in_if) + L.lo;
-  for (int e = threadIdx.x; e < len; e += blockDim.x) sx[e] = static_cast<T>(xv[e]);
+  for (int e = threadIdx.x; e < ld; e += blockDim.x) sx[e] = e < len ? static_cast<T>(xv[e]) : T(0);
   __syncthreads();
   if (!transpose) {
-    int rows = 32;
-    while (rows < len) rows <<= 1;
-    const int groups = max(1, 256 / rows);
-    const int r = threadIdx.x % rows, gidx = threadIdx.x / rows;
-    double a = 0.0;
-    if (r < len && gidx < groups) {
-      T p0 = T(0), p1 = T(0);
-      int c = gidx;
-      for (; c + groups < len; c += 2 * groups) {
-        p0 = fma(M[(int64_t)c * len + r], sx[c], p0);
-        p1 = fma(M[(int64_t)(c + groups) * len + r], sx[c + groups], p1);
+    const int nvr = ld / VEC;                       // row vectors
+    const int rv = nvr <= 32 ? 32 : (nvr <= 64 ? 64 : 128);
+    const int groups = 256 / rv;
+    const int r = threadIdx.x % rv, g = threadIdx.x / rv;
+    T a[VEC];
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a[q] = T(0);
+    if (r < nvr) {
+      const V* col = reinterpret_cast<const V*>(M) + r;
+      const int ldv = ld / VEC;
+      int c = g;
+      for (; c + 3 * groups < len; c += 4 * groups) {
+        const V m0 = col[(int64_t)c * ldv];
+        const V m1 = col[(int64_t)(c + groups) * ldv];
+        const V m2 = col[(int64_t)(c + 2 * groups) * ldv];
+        const V m3 = col[(int64_t)(c + 3 * groups) * ldv];
+        vec_fma<T>(m0, sx[c], a);
+        vec_fma<T>(m1, sx[c + groups], a);
+        vec_fma<T>(m2, sx[c + 2 * groups], a);
+        vec_fma<T>(m3, sx[c + 3 * groups], a);
       }
-      for (; c < len; c += groups) p0 = fma(M[(int64_t)c * len + r], sx[c], p0);
-      a = (double)(p0 + p1);
+      for (; c < len; c += groups) vec_fma<T>(col[(int64_t)c * ldv], sx[c], a);
     }
-    red[threadIdx.x] = a;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) red[g * (rv * VEC) + r * VEC + q] = a[q];
     __syncthreads();
-    if (threadIdx.x < rows && threadIdx.x < len) {
+    for (int row = threadIdx.x; row < len; row += blockDim.x) {
       double tot = 0.0;
-      for (int q = 0; q < groups; ++q) tot += red[q * rows + threadIdx.x];
-      atomicAdd(&acc[L.out_if + L.lo + threadIdx.x], tot);
+      for (int q = 0; q < groups; ++q) tot += (double)red[q * (rv * VEC) + row];
+      atomicAdd(&acc[L.out_if + L.lo + row], tot);
     }
   } else {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvr = ld / VEC;
     for (int c = warp; c < len; c += 8) {
+      const V* col = reinterpret_cast<const V*>(M + (int64_t)c * ld);
       T part = T(0);
-      for (int r = lane; r < len; r += 32) part = fma(M[(int64_t)c * len + r], sx[r], part);
-      const double a = warp_sum((double)part);
-      if (lane == 0) atomicAdd(&acc[L.in_if + L.lo + c], a);
+      for (int v = lane; v < nvr; v += 32) part += vec_dot<T>(col[v], sx + v * VEC);
+      const double s = warp_sum((double)part);
+      if (lane == 0) atomicAdd(&acc[L.in_if + L.lo + c], s);
     }
   }
 }
@@ -622,7 +663,8 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
       lf.sblk = b;
       lf.lo = (t * ng) >> L;
       lf.len = (((t + 1) * ng) >> L) - lf.lo;
-      lf.d_off = dl; dl += lf.len * lf.len;
+      lf.ld = (lf.len + 3) / 4 * 4;
+      lf.d_off = dl; dl += lf.ld * lf.len;
       lf.in_if = in_if; lf.out_if = out_if;
       H.leaves.push_back(lf);
     }
@@ -812,9 +854,9 @@ int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaS
   }
   for (auto& lf : H.leaves) {
     if (lf.sblk != sbk) continue;
-    fetch(H.D, lf.d_off, lf.len * lf.len, Dm);
+    fetch(H.D, lf.d_off, lf.ld * lf.len, Dm);
     for (int64_t c = 0; c < lf.len; ++c)
-      for (int64_t r = 0; r < lf.len; ++r) out[(lf.lo + c) * ng + lf.lo + r] = Dm[c * lf.len + r];
+      for (int64_t r = 0; r < lf.len; ++r) out[(lf.lo + c) * ng + lf.lo + r] = Dm[c * lf.ld + r];
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }

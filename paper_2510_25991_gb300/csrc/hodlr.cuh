@@ -30,7 +30,8 @@ struct HBlock {
 struct HLeaf {
   int sblk;
   int64_t lo, len;
-  int64_t d_off;   // dense leaf, column-major len x len
+  int64_t ld;      // leading dimension: len rounded up to a multiple of 4 (zero rows below len)
+  int64_t d_off;   // dense leaf, column-major ld x len
   int64_t in_if, out_if;
 };
 
