@@ -95,7 +95,7 @@ typedef struct {
   int check_every;      /* GMRES iterations between host convergence checks                   */
   int factor_chunks;    /* pivot sweeps split along y into warm-started chunks per slab and
                            direction: 0 automatic, 1 exact sequential sweeps, k > 1 forced     */
-  int factor_warmup;    /* warm-up rows of a chunk (0: 8 w in FP32, 18 w in FP64)              */
+  int factor_warmup;    /* warm-up rows of a chunk (0: 4 w in FP32, 10 w in FP64)              */
   int tensor_cores;     /* 1: DDST_MIXED transfer build on the tcgen05 tensor cores (3xTF32,
                            block sizes <= 64); 0: FP32 FMA kernel (kept for validation)       */
 } ddst_options;

@@ -207,14 +207,14 @@ ddst_status factor_all(ddst_ctx* ctx) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const bool f32 = sizeof(T) == 4;
-  const double tol = f32 ? 2e-4 : 1e-11;
+  const double tol = f32 ? 1e-5 : 1e-11;
   auto plan = [&](int M, const std::vector<int>& ids, bool exact, std::vector<FacChunk>& out,
                   int& nslots) {
     const int conc = factor_ctas_per_sm<T>(M) * nsm;
     const int per_sd = std::max(1, conc / std::max(1, 2 * (int)ids.size()));
     for (int sid : ids) {
       const SlabDesc& s = ctx->slabs[sid];
-      const int W = ctx->opt.factor_warmup > 0 ? ctx->opt.factor_warmup : (f32 ? 8 : 18) * s.w;
+      const int W = ctx->opt.factor_warmup > 0 ? ctx->opt.factor_warmup : (f32 ? 4 : 10) * s.w;
       int nch = 1;
       if (!exact) {
         if (ctx->opt.factor_chunks > 1) nch = ctx->opt.factor_chunks;

@@ -182,8 +182,13 @@ __device__ __forceinline__ void store_block(const T* __restrict__ X, T* __restri
 // check slot `chk` and compared with the previous chunk's stored inverse of the same row by
 // k_factor_verify; the host falls back to the exact sequential sweep if any check fails.  The
 // stencil pack of the next row is prefetched by a bulk copy while the current one is inverted.
+// Each chunk's recurrence is latency-bound (one block row at a time), so throughput comes from
+// concurrent chunks: the FP32 kernel is bounded to 64 registers for 4 resident CTAs per SM.
+template <typename T> struct FactorOcc { static constexpr int min_blocks = 1; };
+template <> struct FactorOcc<float> { static constexpr int min_blocks = 4; };
+
 template <typename T, int M>
-__global__ void __launch_bounds__(256) k_factor(const SlabDesc* __restrict__ slabs,
+__global__ void __launch_bounds__(256, FactorOcc<T>::min_blocks) k_factor(const SlabDesc* __restrict__ slabs,
                                                 const FacChunk* __restrict__ chunks,
                                                 const T* __restrict__ pack, T* __restrict__ F,
                                                 T* __restrict__ B, T* __restrict__ Ft,

@@ -277,7 +277,7 @@ def test_chunked_pivot_sweeps_fall_back_when_warmup_is_too_short():
     sol = make_solver(prob, "mixed", factor_chunks=4, factor_warmup=2)
     u, info, st = solve(sol, prob)
     sol.close()
-    assert info["factor_chunks"] == 1 and info["factor_check"] > 2e-4, info
+    assert info["factor_chunks"] == 1 and info["factor_check"] > 1e-5, info
     assert relerr(u, O.global_solve(A, b)) <= 1e-8
 
 
