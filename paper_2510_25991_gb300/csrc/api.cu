@@ -670,7 +670,7 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   int k = 0;
   for (k = 1; k <= maxit; ++k) {
     CK(cudaGraphLaunch(graph, st));
-    note_launch(ctx->state == 3 ? 8 : 5);
+    note_launch(ctx->state == 3 ? 6 : 5);
     if (k % check == 0 || k == maxit) {
       CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <map>
+
 #include "hodlr.cuh"
 #include "kernels.cuh"
 
@@ -377,80 +379,45 @@ __global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __res
 }
 
 // ---------------------------------------------------------------------------------------------
-// Application
+// Application: y = x - K x (or x - K^T x) in two kernels.
+//   k_h_inner : t_b = W_in^T x for every low-rank block b (W_in = V; U when transposed);
+//   k_h_owner : one CTA per output-owner item (interface, leaf row range): the dense leaves and
+//               the low-rank blocks (W_out t_b, W_out = U; V when transposed) of the S blocks
+//               that write these rows, then y = x - sum, written once (no accumulator, no
+//               atomics).
 // ---------------------------------------------------------------------------------------------
-// t_b += W_in^T x_in over one 256-row chunk of W_in (W_in = V, or U when transposed): the
-// chunk of x is staged in shared memory; warp per rank column with 8 independent loads in
-// flight per lane; partial sums folded into FP64 and added atomically (t zeroed by caller).
+// One warp per (low-rank block, rank column) item: t_b[c] = W_in(:, c) . x_in, four loads in
+// flight per lane and a single warp reduction.
 template <typename T>
-__global__ void __launch_bounds__(256) k_h_inner(const HItem* __restrict__ items,
+__global__ void __launch_bounds__(256) k_h_inner(const HItem* __restrict__ items, int nitems,
                                                  const HBlock* __restrict__ bl,
                                                  const T* __restrict__ UV,
                                                  const double* __restrict__ x0,
                                                  double* __restrict__ t, int transpose,
                                                  const int* kdev, int64_t kstride) {
+  const int wi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (wi >= nitems) return;
+  const HItem it = items[wi];
+  const HBlock& b = bl[it.blk];
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
-  const HItem it = items[blockIdx.x];
-  const HBlock b = bl[it.blk];
-  __shared__ T sx[256];
-  const int64_t len = transpose ? b.nrows : b.ncols;
+  const int len = (int)(transpose ? b.nrows : b.ncols);
   const double* xv = x + (transpose ? b.out_if + b.row0 : b.in_if + b.col0);
-  const int64_t lo = it.lo;
-  const int nrow = (int)min((int64_t)256, len - lo);
-  sx[threadIdx.x] = threadIdx.x < nrow ? static_cast<T>(xv[lo + threadIdx.x]) : T(0);
-  __syncthreads();
-  const T* W = UV + (transpose ? b.u_off : b.v_off) + lo;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < b.rank; c += 8) {
-    const T* col = W + (int64_t)c * len;
-    T v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int i = lane + 32 * q;
-      v[q] = i < nrow ? col[i] : T(0);
-    }
-    T part = T(0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) part = fma(v[q], sx[lane + 32 * q], part);
-    const double acc = warp_sum((double)part);
-    if (lane == 0) atomicAdd(&t[b.t_off + c], acc);
-  }
-}
-
-// acc_out += W_out t_b (W_out = U, or V when transposed): thread per output row, tiles of 256.
-template <typename T>
-__global__ void __launch_bounds__(256) k_h_outer(const HItem* __restrict__ items,
-                                                 const HBlock* __restrict__ bl,
-                                                 const T* __restrict__ UV,
-                                                 const double* __restrict__ t,
-                                                 double* __restrict__ acc, int transpose) {
-  const HItem it = items[blockIdx.x];
-  const HBlock b = bl[it.blk];
-  __shared__ T st[256];
-  for (int c = threadIdx.x; c < b.rank; c += blockDim.x) st[c] = static_cast<T>(t[b.t_off + c]);
-  __syncthreads();
-  const int64_t len = transpose ? b.ncols : b.nrows;
-  const int64_t i = it.lo + threadIdx.x;
-  if (i >= len) return;
-  const T* W = UV + (transpose ? b.v_off : b.u_off) + i;
+  const T* w = UV + (transpose ? b.u_off : b.v_off) + it.lo * (int64_t)len;
   T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-  int c = 0;
-  for (; c + 3 < b.rank; c += 4) {
-    a0 = fma(W[(int64_t)c * len], st[c], a0);
-    a1 = fma(W[(int64_t)(c + 1) * len], st[c + 1], a1);
-    a2 = fma(W[(int64_t)(c + 2) * len], st[c + 2], a2);
-    a3 = fma(W[(int64_t)(c + 3) * len], st[c + 3], a3);
+  int r = lane;
+  for (; r + 96 < len; r += 128) {
+    a0 = fma(w[r], static_cast<T>(xv[r]), a0);
+    a1 = fma(w[r + 32], static_cast<T>(xv[r + 32]), a1);
+    a2 = fma(w[r + 64], static_cast<T>(xv[r + 64]), a2);
+    a3 = fma(w[r + 96], static_cast<T>(xv[r + 96]), a3);
   }
-  for (; c < b.rank; ++c) a0 = fma(W[(int64_t)c * len], st[c], a0);
-  const int64_t o = transpose ? b.in_if + b.col0 + i : b.out_if + b.row0 + i;
-  atomicAdd(&acc[o], (double)((a0 + a1) + (a2 + a3)));
+  for (; r < len; r += 32) a0 = fma(w[r], static_cast<T>(xv[r]), a0);
+  const double v = warp_sum((double)((a0 + a1) + (a2 + a3)));
+  if (lane == 0) t[b.t_off + it.lo] = v;
 }
 
-// Dense leaves: acc_out += D x_in (or D^T x_out).  One CTA per leaf (len <= 256, column stride
-// ld a multiple of 4, so columns start on 16-byte boundaries).
-//   non-transposed: thread = (vector of VEC rows, column group); VEC = 16 bytes of T; four
-//                   columns in flight per thread; column groups reduced in shared memory;
-//   transposed:     warp per column, 16-byte vectors along the column, warp reduction.
+// Dense leaves are column-major with a leading dimension that is a multiple of 4, so every
+// column starts on a 16-byte boundary and is read with 16-byte vectors.
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
@@ -477,73 +444,151 @@ __device__ __forceinline__ double vec_dot<double>(const double2& m, const double
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_h_leaf(const HLeaf* __restrict__ lv,
-                                                const T* __restrict__ D,
-                                                const double* __restrict__ x0,
-                                                double* __restrict__ acc, int transpose,
-                                                const int* kdev, int64_t kstride) {
+__global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
+                                                 const HBlock* __restrict__ bl,
+                                                 const HLeaf* __restrict__ lv,
+                                                 const T* __restrict__ UV,
+                                                 const T* __restrict__ D,
+                                                 const double* __restrict__ t,
+                                                 const double* __restrict__ x0,
+                                                 double* __restrict__ y, int transpose,
+                                                 const int* kdev, int64_t kstride) {
   using V = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
-  const HLeaf L = lv[blockIdx.x];
-  const T* M = D + L.d_off;
-  const int len = (int)L.len, ld = (int)L.ld;  // len <= 256, ld = len rounded up to 4
-  __shared__ __align__(16) T sx[256];
+  const HOwn* it = items + blockIdx.x;
+  const int len = it->len, nsrc = it->nsrc;  // len <= 256
+  __shared__ __align__(16) T sx[2 * 256];
   __shared__ T red[256 * 4];
-  const double* xv = x + (transpose ? L.out_if : L.in_if) + L.lo;
-  for (int e = threadIdx.x; e < ld; e += blockDim.x) sx[e] = e < len ? static_cast<T>(xv[e]) : T(0);
-  __syncthreads();
-  if (!transpose) {
-    const int nvr = ld / VEC;                       // row vectors
-    const int rv = nvr <= 32 ? 32 : (nvr <= 64 ? 64 : 128);
-    const int groups = 256 / rv;
-    const int r = threadIdx.x % rv, g = threadIdx.x / rv;
-    T a[VEC];
-#pragma unroll
-    for (int q = 0; q < VEC; ++q) a[q] = T(0);
-    if (r < nvr) {
-      const V* col = reinterpret_cast<const V*>(M) + r;
-      const int ldv = ld / VEC;
-      int c = g;
-      for (; c + 3 * groups < len; c += 4 * groups) {
-        const V m0 = col[(int64_t)c * ldv];
-        const V m1 = col[(int64_t)(c + groups) * ldv];
-        const V m2 = col[(int64_t)(c + 2 * groups) * ldv];
-        const V m3 = col[(int64_t)(c + 3 * groups) * ldv];
-        vec_fma<T>(m0, sx[c], a);
-        vec_fma<T>(m1, sx[c + groups], a);
-        vec_fma<T>(m2, sx[c + 2 * groups], a);
-        vec_fma<T>(m3, sx[c + 3 * groups], a);
-      }
-      for (; c < len; c += groups) vec_fma<T>(col[(int64_t)c * ldv], sx[c], a);
-    }
-#pragma unroll
-    for (int q = 0; q < VEC; ++q) red[g * (rv * VEC) + r * VEC + q] = a[q];
-    __syncthreads();
-    for (int row = threadIdx.x; row < len; row += blockDim.x) {
-      double tot = 0.0;
-      for (int q = 0; q < groups; ++q) tot += (double)red[q * (rv * VEC) + row];
-      atomicAdd(&acc[L.out_if + L.lo + row], tot);
-    }
-  } else {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nvr = ld / VEC;
-    for (int c = warp; c < len; c += 8) {
-      const V* col = reinterpret_cast<const V*>(M + (int64_t)c * ld);
-      T part = T(0);
-      for (int v = lane; v < nvr; v += 32) part += vec_dot<T>(col[v], sx + v * VEC);
-      const double s = warp_sum((double)part);
-      if (lane == 0) atomicAdd(&acc[L.in_if + L.lo + c], s);
+  __shared__ double outv[256];
+  // low-rank blocks over these rows, per (source, level): W_out offset of row lo, its leading
+  // dimension, rank, and t_b (first HOWN_TCAP entries) staged once
+  constexpr int NSL = 2 * HOWN_MAXL;
+  __shared__ int64_t s_woff[NSL], s_nr[NSL];
+  __shared__ int s_rank[NSL];
+  __shared__ T s_t[NSL * HOWN_TCAP];
+  for (int r = threadIdx.x; r < len; r += blockDim.x) outv[r] = 0.0;
+  for (int q = threadIdx.x; q < NSL; q += blockDim.x) {
+    const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;
+    const int hb = s < nsrc ? it->hb[s][l] : -1;
+    s_rank[q] = 0;
+    if (hb >= 0) {
+      const HBlock& B = bl[hb];
+      s_rank[q] = B.rank;
+      s_nr[q] = transpose ? B.ncols : B.nrows;
+      s_woff[q] = (transpose ? B.v_off : B.u_off) + it->lo - (transpose ? B.col0 : B.row0);
     }
   }
-}
-
-__global__ void k_h_finish(const double* __restrict__ x0, const double* __restrict__ acc,
-                           double* __restrict__ y, int64_t n, const int* kdev, int64_t kstride) {
-  const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = x[e] - acc[e];
+  for (int e = threadIdx.x; e < NSL * HOWN_TCAP; e += blockDim.x) {
+    const int q = e / HOWN_TCAP, c = e % HOWN_TCAP;
+    const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;
+    const int hb = s < nsrc ? it->hb[s][l] : -1;
+    if (hb >= 0 && c < bl[hb].rank) s_t[e] = static_cast<T>(t[bl[hb].t_off + c]);
+  }
+  // dense leaves of both sources over these rows (same tree, so same ld), one pass
+  const int ld = nsrc > 0 ? (int)lv[it->leaf[0]].ld : 0;
+  const T* M0 = nsrc > 0 ? D + lv[it->leaf[0]].d_off : nullptr;
+  const T* M1 = nsrc > 1 ? D + lv[it->leaf[1]].d_off : nullptr;
+  for (int q = 0; q < nsrc; ++q) {
+    const HLeaf L = lv[it->leaf[q]];
+    const double* xv = x + (transpose ? L.out_if : L.in_if) + L.lo;
+    for (int e = threadIdx.x; e < ld; e += blockDim.x)
+      sx[q * 256 + e] = e < len ? static_cast<T>(xv[e]) : T(0);
+  }
+  __syncthreads();
+  if (nsrc > 0) {
+    if (!transpose) {  // D x: thread = (vector of VEC rows, column group)
+      const int nvr = ld / VEC;
+      const int rv = nvr <= 32 ? 32 : (nvr <= 64 ? 64 : 128);
+      const int groups = 256 / rv;
+      const int r = threadIdx.x % rv, g = threadIdx.x / rv;
+      T a[VEC];
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) a[q] = T(0);
+      if (r < nvr) {
+        const int ldv = ld / VEC;
+        const V* c0p = reinterpret_cast<const V*>(M0) + r;
+        const V* c1p = reinterpret_cast<const V*>(M1 ? M1 : M0) + r;
+        const T* sx1 = sx + (M1 ? 256 : 0);
+        const T f1 = M1 ? T(1) : T(0);
+        int c = g;
+        for (; c + 3 * groups < len; c += 4 * groups) {  // eight 16-byte loads in flight
+          V m[8];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            m[u] = c0p[(int64_t)(c + u * groups) * ldv];
+            m[4 + u] = c1p[(int64_t)(c + u * groups) * ldv];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            vec_fma<T>(m[u], sx[c + u * groups], a);
+            vec_fma<T>(m[4 + u], f1 * sx1[c + u * groups], a);
+          }
+        }
+        for (; c < len; c += groups) {
+          vec_fma<T>(c0p[(int64_t)c * ldv], sx[c], a);
+          vec_fma<T>(c1p[(int64_t)c * ldv], f1 * sx1[c], a);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) red[g * (rv * VEC) + r * VEC + q] = a[q];
+      __syncthreads();
+      for (int row = threadIdx.x; row < len; row += blockDim.x) {
+        double tot = 0.0;
+        for (int q = 0; q < groups; ++q) tot += (double)red[q * (rv * VEC) + row];
+        outv[row] += tot;
+      }
+    } else {  // D^T x: warp per column, both leaves
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int nvr = ld / VEC;
+      for (int c = warp; c < len; c += 8) {
+        const V* col0 = reinterpret_cast<const V*>(M0 + (int64_t)c * ld);
+        T part = T(0);
+        for (int v = lane; v < nvr; v += 32) part += vec_dot<T>(col0[v], sx + v * VEC);
+        if (M1) {
+          const V* col1 = reinterpret_cast<const V*>(M1 + (int64_t)c * ld);
+          for (int v = lane; v < nvr; v += 32) part += vec_dot<T>(col1[v], sx + 256 + v * VEC);
+        }
+        const double sm = warp_sum((double)part);
+        if (lane == 0) outv[c] += sm;
+      }
+    }
+  }
+  __syncthreads();
+  // W_out(rows, :) t_b of every low-rank block, one row per thread, four columns in flight
+  for (int r = threadIdx.x; r < len; r += blockDim.x) {
+    double a = 0.0;
+    for (int q = 0; q < NSL; ++q) {
+      const int rank = s_rank[q];
+      if (rank == 0) continue;
+      const T* W = UV + s_woff[q] + r;
+      const int64_t nr = s_nr[q];
+      const T* tq = s_t + q * HOWN_TCAP;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int c = 0;
+      for (; c + 3 < rank && c + 3 < HOWN_TCAP; c += 4) {
+        a0 = fma(W[(int64_t)c * nr], tq[c], a0);
+        a1 = fma(W[(int64_t)(c + 1) * nr], tq[c + 1], a1);
+        a2 = fma(W[(int64_t)(c + 2) * nr], tq[c + 2], a2);
+        a3 = fma(W[(int64_t)(c + 3) * nr], tq[c + 3], a3);
+      }
+      for (; c < rank; ++c) {
+        T tc;
+        if (c < HOWN_TCAP) {
+          tc = tq[c];
+        } else {
+          const int hb = it->hb[q / HOWN_MAXL][q % HOWN_MAXL];
+          tc = static_cast<T>(t[bl[hb].t_off + c]);
+        }
+        a0 = fma(W[(int64_t)c * nr], tc, a0);
+      }
+      a += (double)((a0 + a1) + (a2 + a3));
+    }
+    outv[r] += a;
+  }
+  __syncthreads();
+  const int64_t o = it->out + it->lo;
+  for (int r = threadIdx.x; r < len; r += blockDim.x) y[o + r] = x[o + r] - outv[r];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -552,20 +597,22 @@ __global__ void k_h_finish(const double* __restrict__ x0, const double* __restri
 void HodlrSet::clear() { release(); }
 
 void HodlrSet::release() {
-  for (void* p : {UV, D, (void*)t, (void*)acc, (void*)d_blocks, (void*)d_leaves,
-                  (void*)d_out_items, (void*)d_out_items_T})
+  for (void* p : {UV, D, (void*)t, (void*)d_blocks, (void*)d_leaves, (void*)d_own,
+                  (void*)d_own_T, d_inner})
     if (p) cudaFree(p);
   UV = D = nullptr;
-  t = acc = nullptr;
+  t = nullptr;
   d_blocks = nullptr;
   d_leaves = nullptr;
-  d_out_items = d_out_items_T = nullptr;
+  d_own = d_own_T = nullptr;
+  d_inner = nullptr;
+  n_inner = 0;
   blocks.clear();
   leaves.clear();
   built = false;
   bytes = 0;
   max_rank = 0;
-  n_out_items = n_out_items_T = 0;
+  n_own = n_own_T = 0;
 }
 
 static int levels_for(int64_t ng, int leaf) {
@@ -620,17 +667,20 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   H.sblk_side = sb_side;
   H.sblk_L.assign(nsb, 0);
   if (nsb == 0) { H.built = true; return 0; }
-  int64_t max_ng = 0, tot_if = 0;
-  for (auto& P : probs) tot_if += (int64_t)P.nds * P.ng;
+  int64_t max_ng = 0;
   for (auto& b : sb) max_ng = std::max(max_ng, b.ng);
   // blocks and leaves
   std::vector<HDev> hd;
+  std::vector<int> sb_fb(nsb + 1), sb_fl(nsb);  // first block / first leaf of every S block
   int64_t uv = 0, dl = 0, tl = 0;
   for (int b = 0; b < nsb; ++b) {
     const SlabDesc& s = slabs[sb_slab[b]];
     const int64_t ng = sb[b].ng;
     const int L = levels_for(ng, leaf);
+    if (L > HOWN_MAXL) { msg = "cluster tree deeper than 12 levels (raise leaf_size)"; return 1; }
     H.sblk_L[b] = L;
+    sb_fb[b] = (int)H.blocks.size();
+    sb_fl[b] = (int)H.leaves.size();
     const int64_t in_if = s.if_off + (sb_side[b] < 0 ? -ng : ng), out_if = s.if_off;
     for (int lev = 1; lev <= L; ++lev) {
       for (int64_t t = 0; t < (1LL << (lev - 1)); ++t) {
@@ -670,6 +720,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     }
   }
   const int nblk = (int)H.blocks.size();
+  sb_fb[nsb] = nblk;
   // device memory
   auto al = [&](void** p, size_t bytes) -> bool {
     if (cudaMalloc(p, bytes < 16 ? 16 : bytes) != cudaSuccess) { cudaGetLastError(); return false; }
@@ -680,7 +731,6 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   int64_t *d_soff = nullptr, *d_sng = nullptr;
   const int64_t stride = max_ng;
   bool ok = al(&H.UV, sizeof(T) * uv) && al(&H.D, sizeof(T) * dl) && al((void**)&H.t, sizeof(double) * tl) &&
-            al((void**)&H.acc, sizeof(double) * tot_if) &&
             al((void**)&H.d_blocks, sizeof(HBlock) * nblk) &&
             al((void**)&H.d_leaves, sizeof(HLeaf) * H.leaves.size()) &&
             al((void**)&d_sb, sizeof(SBlk) * nsb) && al((void**)&d_x, sizeof(double) * stride * nsb) &&
@@ -761,24 +811,62 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     used += (H.blocks[b].nrows + H.blocks[b].ncols) * ranks[b];
   }
   H.bytes = (used + dl) * (int64_t)sizeof(T);
-  H.acc_len = tot_if;
   H.t_len = tl;
   cudaMemcpyAsync(H.d_blocks, H.blocks.data(), sizeof(HBlock) * nblk, cudaMemcpyHostToDevice, st);
-  // output-row work items of the apply (non-transposed: rows of U; transposed: rows of V)
-  std::vector<HItem> oi, oiT;
-  for (int b = 0; b < nblk; ++b) {
-    if (H.blocks[b].rank == 0) continue;
-    for (int64_t lo = 0; lo < H.blocks[b].nrows; lo += 256) oi.push_back({b, lo});
-    for (int64_t lo = 0; lo < H.blocks[b].ncols; lo += 256) oiT.push_back({b, lo});
+  // output-owner items: one per (interface, leaf row range), for the plain and transposed apply
+  std::vector<HOwn> own[2];
+  {
+    std::map<int64_t, std::vector<int>> by_if[2];  // S blocks writing an interface: out_if / in_if
+    for (int b = 0; b < nsb; ++b) {
+      by_if[0][H.leaves[sb_fl[b]].out_if].push_back(b);
+      by_if[1][H.leaves[sb_fl[b]].in_if].push_back(b);
+    }
+    const std::vector<int> none;
+    for (const ProbDesc& P : probs) {
+      const int L = levels_for(P.ng, leaf);
+      for (int j = 0; j < P.nds; ++j) {
+        const int64_t iface = P.if_off + (int64_t)j * P.ng;
+        for (int tr = 0; tr < 2; ++tr) {
+          const auto f = by_if[tr].find(iface);
+          const std::vector<int>& src = f == by_if[tr].end() ? none : f->second;
+          if (src.size() > 2) { msg = "more than two S blocks write one interface"; H.release(); return 1; }
+          for (int64_t tt = 0; tt < (1LL << L); ++tt) {
+            HOwn o{};
+            o.out = iface;
+            o.lo = (tt * P.ng) >> L;
+            o.len = (int)((((tt + 1) * P.ng) >> L) - o.lo);
+            o.nsrc = (int)src.size();
+            for (int q = 0; q < o.nsrc; ++q) {
+              const int b = src[q];
+              o.leaf[q] = sb_fl[b] + (int)tt;
+              for (int l = 0; l < HOWN_MAXL; ++l) o.hb[q][l] = -1;
+              for (int bi = sb_fb[b]; bi < sb_fb[b + 1]; ++bi) {
+                const HBlock& B = H.blocks[bi];
+                const int64_t a0 = tr ? B.col0 : B.row0, an = tr ? B.ncols : B.nrows;
+                if (B.rank > 0 && o.lo >= a0 && o.lo < a0 + an) o.hb[q][B.level - 1] = bi;
+              }
+            }
+            own[tr].push_back(o);
+          }
+        }
+      }
+    }
   }
-  H.n_out_items = (int)oi.size();
-  H.n_out_items_T = (int)oiT.size();
-  if (!al((void**)&H.d_out_items, sizeof(HItem) * std::max<size_t>(1, oi.size())) ||
-      !al((void**)&H.d_out_items_T, sizeof(HItem) * std::max<size_t>(1, oiT.size()))) {
+  // inner-product items: one per (low-rank block, rank column)
+  std::vector<HItem> inner;
+  for (int b = 0; b < nblk; ++b)
+    for (int c = 0; c < H.blocks[b].rank; ++c) inner.push_back({b, (int64_t)c});
+  H.n_inner = (int)inner.size();
+  H.n_own = (int)own[0].size();
+  H.n_own_T = (int)own[1].size();
+  if (!al(&H.d_inner, sizeof(HItem) * std::max<size_t>(1, inner.size())) ||
+      !al((void**)&H.d_own, sizeof(HOwn) * std::max<size_t>(1, own[0].size())) ||
+      !al((void**)&H.d_own_T, sizeof(HOwn) * std::max<size_t>(1, own[1].size()))) {
     H.release(); msg = "oom"; return 2;
   }
-  cudaMemcpyAsync(H.d_out_items, oi.data(), sizeof(HItem) * oi.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(H.d_out_items_T, oiT.data(), sizeof(HItem) * oiT.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(H.d_inner, inner.data(), sizeof(HItem) * inner.size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(H.d_own, own[0].data(), sizeof(HOwn) * own[0].size(), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(H.d_own_T, own[1].data(), sizeof(HOwn) * own[1].size(), cudaMemcpyHostToDevice, st);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { msg = cudaGetErrorString(e); H.release(); return 1; }
   H.built = true;
@@ -788,33 +876,19 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
 template <typename T>
 void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const double* x, double* y,
                  int transpose, cudaStream_t st, const int* kdev, int64_t kstride) {
-  cudaMemsetAsync(H.acc, 0, sizeof(double) * H.acc_len, st);
-  const int nblk = (int)H.blocks.size();
-  if (nblk > 0) {
-    cudaMemsetAsync(H.t, 0, sizeof(double) * H.t_len, st);
-    // inner products run over the input side: V rows (non-transposed) or U rows (transposed)
-    const int ni_in = transpose ? H.n_out_items : H.n_out_items_T;
-    const HItem* in_items = (const HItem*)(transpose ? H.d_out_items : H.d_out_items_T);
-    if (ni_in > 0) {
-      note_launch();
-      k_h_inner<T><<<ni_in, 256, 0, st>>>(in_items, H.d_blocks, (const T*)H.UV, x, H.t, transpose,
-                                          kdev, kstride);
-    }
-    const int ni = transpose ? H.n_out_items_T : H.n_out_items;
-    if (ni > 0) {
-      note_launch();
-      k_h_outer<T><<<ni, 256, 0, st>>>(transpose ? (const HItem*)H.d_out_items_T
-                                                 : (const HItem*)H.d_out_items,
-                                       H.d_blocks, (const T*)H.UV, H.t, H.acc, transpose);
-    }
-  }
-  if (!H.leaves.empty()) {
+  if (H.n_inner > 0) {
     note_launch();
-    k_h_leaf<T><<<(unsigned)H.leaves.size(), 256, 0, st>>>(H.d_leaves, (const T*)H.D, x, H.acc,
-                                                           transpose, kdev, kstride);
+    k_h_inner<T><<<(H.n_inner + 7) / 8, 256, 0, st>>>((const HItem*)H.d_inner, H.n_inner,
+                                                     H.d_blocks, (const T*)H.UV, x, H.t,
+                                                     transpose, kdev, kstride);
   }
-  note_launch();
-  k_h_finish<<<512, 256, 0, st>>>(x, H.acc, y, H.acc_len, kdev, kstride);
+  const int no = transpose ? H.n_own_T : H.n_own;
+  if (no > 0) {
+    note_launch();
+    k_h_owner<T><<<no, 256, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_leaves,
+                                     (const T*)H.UV, (const T*)H.D, H.t, x, y, transpose, kdev,
+                                     kstride);
+  }
 }
 
 int hodlr_expand(HodlrSet& H, int slab, int side, size_t esz, double* out, cudaStream_t st) {

@@ -35,21 +35,37 @@ struct HLeaf {
   int64_t in_if, out_if;
 };
 
+// Output-owner work item of the apply: rows [lo, lo + len) of one interface (a leaf range of
+// the shared cluster tree).  Up to two S blocks write there (S_{j,j-1} and S_{j,j+1} onto
+// Gamma_j; transposed: S_{j+1,j}^T and S_{j-1,j}^T); for each, its dense leaf over these rows
+// and, per tree level, the low-rank block whose output range holds them (-1: none / rank 0).
+constexpr int HOWN_MAXL = 12;
+constexpr int HOWN_TCAP = 16;  // t_b entries per block staged in shared memory by the apply
+struct HOwn {
+  int64_t out;                 // interface offset of the output rows
+  int64_t lo;                  // first row within the interface
+  int len;                     // number of rows (<= 256)
+  int nsrc;                    // contributing S blocks (0..2)
+  int leaf[2];
+  int hb[2][HOWN_MAXL];
+};
+
 struct HodlrSet {
   bool built = false;
   size_t esz = 4;
   void* UV = nullptr;      // factors
   void* D = nullptr;       // dense leaves
-  double* t = nullptr;     // V^T x scratch (FP64)
-  double* acc = nullptr;   // output accumulator (FP64)
+  double* t = nullptr;     // V^T x (U^T x when transposed) per low-rank block (FP64)
   HBlock* d_blocks = nullptr;
   HLeaf* d_leaves = nullptr;
   std::vector<HBlock> blocks;
   std::vector<HLeaf> leaves;
-  void* d_out_items = nullptr;    // apply work items (block, row tile)
-  void* d_out_items_T = nullptr;  // transposed apply work items
-  int n_out_items = 0, n_out_items_T = 0;
-  int64_t t_len = 0, acc_len = 0;
+  HOwn* d_own = nullptr;      // output-owner items of the apply
+  HOwn* d_own_T = nullptr;    // ... of the transposed apply
+  int n_own = 0, n_own_T = 0;
+  void* d_inner = nullptr;    // inner-product items (low-rank block, rank column)
+  int n_inner = 0;
+  int64_t t_len = 0;
   int64_t bytes = 0;
   int max_rank = 0;
   std::vector<int> sblk_L;     // tree depth per S block
