@@ -184,6 +184,14 @@ ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* 
 ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, double* y,
                                  int transpose);
 
+/* Diagnostic timing of the interface operator, the matrix-vector product of every GMRES
+ * iteration (Eq. (modelS)): runs `reps` applications of (I - K) (or its transpose) to the
+ * context's own interface work vectors, back to back on the context stream, and returns the
+ * mean device time per application in *ms (CUDA events on that stream).  The work vectors'
+ * contents are overwritten.  Errors: INVALID_ARG (NULL or reps < 1), STATE (operators not
+ * built), CUDA. */
+ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms);
+
 /* Sizes of problem prob: n_ds, n_gamma and the total interface length (any may be NULL). */
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);

@@ -68,6 +68,7 @@ SIGNATURES = {
     "ddst_interface_trace": (C.c_int, [_P, C.c_int, _P]),
     "ddst_get_transfer": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "ddst_apply_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    "ddst_time_apply": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_float)]),
     "ddst_query": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int)]),
     "ddst_get_precision": (C.c_int, [_P, C.POINTER(C.c_int)]),

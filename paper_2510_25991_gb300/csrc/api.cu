@@ -611,7 +611,8 @@ ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-  apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose, ctx->cap_stream, ctx->d_k, n);
+  // Arnoldi on K (bit 1 of the mode): same Krylov space as I - K, see launch_arnoldi_step
+  apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose | 2, ctx->cap_stream, ctx->d_k, n);
   launch_arnoldi_step(ctx->V, ctx->if_w, n, ctx->d_k, ctx->h1, ctx->h2, ctx->arn_part,
                       ctx->arn_ticket, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta,
                       ctx->resid, maxit, ctx->cap_stream);
@@ -1127,6 +1128,34 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
   CK(cudaGetLastError());
   CK(stage_out(y, ctx->if_w + P.if_off, len, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return DDST_OK;
+}
+
+ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms) {
+  if (!ctx || !ms || reps < 1) return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  ddst_status s = ensure_solve_buffers(ctx);
+  if (s != DDST_OK) return s;
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(ctx->if_tmp, 0, sizeof(double) * ctx->tot_if, st));
+  auto one = [&]() {
+    if (ctx->prec == DDST_FP64) apply_interface_T<double>(ctx, ctx->if_tmp, ctx->if_w, transpose != 0, st);
+    else apply_interface_T<float>(ctx, ctx->if_tmp, ctx->if_w, transpose != 0, st);
+  };
+  one();  // warm
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; ++r) one();
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  *ms = t / reps;
   return DDST_OK;
 }
 

@@ -384,7 +384,7 @@ __global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __res
 //   k_h_owner : one CTA per output-owner item (interface, leaf row range): the dense leaves and
 //               the low-rank blocks (W_out t_b, W_out = U; V when transposed) of the S blocks
 //               that write these rows, then y = x - sum, written once (no accumulator, no
-//               atomics).
+//               atomics), or y = sum alone (K x) when asked.
 // ---------------------------------------------------------------------------------------------
 // One warp per (low-rank block, rank column) item: t_b[c] = W_in(:, c) . x_in, four loads in
 // flight per lane and a single warp reduction.
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
                                                  const double* __restrict__ t,
                                                  const double* __restrict__ x0,
                                                  double* __restrict__ y, int transpose,
-                                                 const int* kdev, int64_t kstride) {
+                                                 int konly, const int* kdev, int64_t kstride) {
   using V = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
   }
   __syncthreads();
   const int64_t o = it->out + it->lo;
-  for (int r = threadIdx.x; r < len; r += blockDim.x) y[o + r] = x[o + r] - outv[r];
+  for (int r = threadIdx.x; r < len; r += blockDim.x) y[o + r] = konly ? outv[r] : x[o + r] - outv[r];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -876,6 +876,8 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
 template <typename T>
 void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const double* x, double* y,
                  int transpose, cudaStream_t st, const int* kdev, int64_t kstride) {
+  const int konly = transpose >> 1;  // bit 1: y = K x (or K^T x) instead of (I - K) x
+  transpose &= 1;
   if (H.n_inner > 0) {
     note_launch();
     k_h_inner<T><<<(H.n_inner + 7) / 8, 256, 0, st>>>((const HItem*)H.d_inner, H.n_inner,
@@ -886,8 +888,8 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
   if (no > 0) {
     note_launch();
     k_h_owner<T><<<no, 256, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_leaves,
-                                     (const T*)H.UV, (const T*)H.D, H.t, x, y, transpose, kdev,
-                                     kstride);
+                                     (const T*)H.UV, (const T*)H.D, H.t, x, y, transpose, konly,
+                                     kdev, kstride);
   }
 }
 

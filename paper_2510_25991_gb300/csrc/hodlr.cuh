@@ -81,8 +81,9 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
                 const std::vector<ProbDesc>& probs, const SlabDesc* d_slabs, const T* S,
                 cudaStream_t st, std::string& msg);
 
-// y = (I - K) x (transpose = 0) or (I - K)^T x with the HODLR blocks; when kdev is given the
-// input is x + (*kdev - 1) * kstride (device-resident Krylov index, graph-capturable).
+// y = (I - K) x (transpose bit 0 clear) or (I - K)^T x with the HODLR blocks; with bit 1 set,
+// y = K x (or K^T x).  When kdev is given the input is x + (*kdev - 1) * kstride
+// (device-resident Krylov index, graph-capturable).
 template <typename T>
 void hodlr_apply(HodlrSet& H, const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                  const double* x, double* y, int transpose, cudaStream_t st,

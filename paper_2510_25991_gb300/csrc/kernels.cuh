@@ -98,7 +98,8 @@ void launch_local_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int ni
                         int transpose, int mode, DevStatus* st, cudaStream_t s);
 
 // krylov.cu
-// x may be indexed by a device-resident basis count: x_eff = x + (*kdev - 1) * kstride
+// x may be indexed by a device-resident basis count: x_eff = x + (*kdev - 1) * kstride.
+// transpose: bit 0 = transposed operator, bit 1 = y = K x instead of (I - K) x.
 template <typename T>
 void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                         int64_t max_ng, const T* S, const double* x, double* y, int transpose,

@@ -9,15 +9,16 @@
 
 namespace ddst {
 
-// y_j = x_j - S_{j,j-1} x_{j-1} - S_{j,j+1} x_{j+1}; S column-major.  grid = (row tiles of 128,
-// slabs); 256 threads = 128 rows x 2 interleaved halves of the sources.
+// y_j = x_j - S_{j,j-1} x_{j-1} - S_{j,j+1} x_{j+1} (konly: y_j = S_{j,j-1} x_{j-1} + S_{j,j+1}
+// x_{j+1}, i.e. y = K x); S column-major.  grid = (row tiles of 128, slabs); 256 threads = 128
+// rows x 2 interleaved halves of the sources.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict__ slabs,
                                                      const ProbDesc* __restrict__ probs,
                                                      const T* __restrict__ S,
                                                      const double* __restrict__ x0,
                                                      double* __restrict__ y, const int* kdev,
-                                                     int64_t kstride) {
+                                                     int64_t kstride, int konly) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const SlabDesc s = slabs[blockIdx.y];
@@ -62,18 +63,20 @@ __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict_
   red[threadIdx.x] = acc;
   __syncthreads();
   if (half == 0 && row < ng)
-    y[s.if_off + row] = x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
+    y[s.if_off + row] = konly ? red[threadIdx.x] + red[threadIdx.x + 128]
+                              : x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
 }
 
-// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1}: warp per output point, lanes over
-// the (contiguous) rows of the column-major blocks.  grid = (ceil(ng/8), slabs), 256 threads.
+// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): warp per output
+// point, lanes over the (contiguous) rows of the column-major blocks.  grid = (ceil(ng/8),
+// slabs), 256 threads.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
                                                        const ProbDesc* __restrict__ probs,
                                                        const T* __restrict__ S,
                                                        const double* __restrict__ x0,
                                                        double* __restrict__ y, const int* kdev,
-                                                       int64_t kstride) {
+                                                       int64_t kstride, int konly) {
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int sidx = blockIdx.y;
   const SlabDesc s = slabs[sidx];
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
     acc += static_cast<double>(part);
   }
   acc = warp_sum(acc);
-  if (lane == 0) y[s.if_off + src] = x[s.if_off + src] - acc;
+  if (lane == 0) y[s.if_off + src] = konly ? acc : x[s.if_off + src] - acc;
 }
 
 // ---- Arnoldi pieces ------------------------------------------------------------------------
@@ -232,13 +235,20 @@ __global__ void k_trisolve(const double* __restrict__ H, int ldh, const double* 
 
 // ---- Arnoldi step with device-resident state (graph-capturable) ---------------------------
 // State: *kdev = k basis vectors V[0..k) exist; w = (I - K) V[k-1] has just been formed.  One
-// step is classical Gram-Schmidt applied twice (CGS2), the Givens update of the least-squares
-// problem and the normalization V[k] = w / ||w||:
-//   dots   : P1[i][c] = V[i] . w over chunk c
-//   update : h1 = sum_c P1;  w -= V h1;  P2[i][c] = V[i] . w
-//   update : h2 = sum_c P2;  w -= V h2;  Pn[c] = |w|^2 over chunk c
+// step is classical Gram-Schmidt with selective reorthogonalization (a second pass only when the
+// first one cancels more than half of ||w||^2: Kahan-Parlett, "twice is enough"), the Givens
+// update of the least-squares problem and the normalization V[k] = w / ||w||:
+//   dots   : P1[i][c] = V[i] . w over chunk c (i < k), P1[k][c] = |w|^2 over chunk c
+//   update : h1 = sum_c P1;  w -= V h1;  second pass needed iff |w|^2 - |h1|^2 < |w|^2 / 2
+//            (flag kdev[1]); then P2[i][c] = V[i] . w, or Pn[c] = |w|^2 if no second pass
+//   update : if the flag is set, h2 = sum_c P2;  w -= V h2;  Pn[c] = |w|^2; else h2 = 0
 //   finish : V[k] = w / sqrt(sum_c Pn); the last CTA to finish applies the Givens rotations to
-//            H(:, k-1) = h1 + h2 and advances *kdev.
+//            the new column of the Hessenberg matrix of (I - K) and advances *kdev.
+// The Arnoldi process runs on K itself (w = K V[k-1]): K and I - K span the same Krylov spaces,
+// and (I - K) V_k = V_{k+1} (I~ - Hbar_K) with I~ the identity padded by a zero row, so column
+// k-1 of the (I - K) matrix is e_{k-1} - (h1 + h2) with subdiagonal -||w||.  On K the first
+// Gram-Schmidt pass rarely cancels half of ||w|| (on I - K it always would, through the
+// V[k-1] component), so the second pass is mostly skipped.
 // Partial sums are stored per chunk (i-major, coalesced for the readers) and reduced by each
 // consumer CTA: no two CTAs update the same address.
 constexpr int ARN_T = 256, ARN_E = 4, ARN_CHUNK = ARN_T * ARN_E, ARN_G = 8;
@@ -336,21 +346,47 @@ __global__ void __launch_bounds__(ARN_T) k_arn_dots(const double* __restrict__ V
   double wv[ARN_E];
   arn_load_chunk(w, n, base, wv);
   arn_chunk_dots(V, n, k, base, wv, P1, nchunk);
+  double acc = 0.0;  // |w|^2 over the chunk, row k of P1
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) acc = fma(wv[e], wv[e], acc);
+  __shared__ double red[ARN_T / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < ARN_T / 32 ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) P1[(int64_t)k * nchunk + blockIdx.x] = t;
+  }
 }
 
-// h = sum_c Pin (CTA 0 also stores it in hout); w -= V h; then P2 = V . w (dots) or
-// Pn[c] = |w|^2 over the chunk.
+// h = sum_c Pin (CTA 0 also stores it in hout); w -= V h; then P2 = V . w or Pn[c] = |w|^2 over
+// the chunk.  first = 1: the first pass, which also decides (identically in every CTA) whether
+// a second pass is needed and publishes that in kdev[1]; first = 0: the second pass, skipped
+// (h = 0) when kdev[1] is clear.
 __global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__ V,
                                                       double* __restrict__ w, int64_t n,
-                                                      const int* __restrict__ kdev,
+                                                      int* __restrict__ kdev,
                                                       const double* __restrict__ Pin,
                                                       double* __restrict__ hout,
                                                       double* __restrict__ Pout,
                                                       double* __restrict__ Pn, int nchunk,
-                                                      int dots) {
-  __shared__ double sh[1024];
+                                                      int first) {
+  __shared__ double sh[1024 + 1];
   const int k = *kdev;
-  arn_reduce(Pin, nchunk, k, sh);
+  if (!first && kdev[1] == 0) {  // no second pass: h2 = 0, Pn already holds |w|^2
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < k; i += ARN_T) hout[i] = 0.0;
+    return;
+  }
+  arn_reduce(Pin, nchunk, first ? k + 1 : k, sh);
+  bool dots = false;
+  if (first) {
+    double hn = 0.0;
+    for (int i = 0; i < k; ++i) hn = fma(sh[i], sh[i], hn);
+    dots = sh[k] - hn < 0.5 * sh[k];  // lost more than half of |w|^2: reorthogonalize
+    if (blockIdx.x == 0 && threadIdx.x == 0) kdev[1] = dots ? 1 : 0;
+  }
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < k; i += ARN_T) hout[i] = sh[i];
   const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
@@ -381,8 +417,9 @@ __global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__
 }
 
 // V[k] = w / ||w|| over this CTA's chunk (0 at breakdown).  The last CTA to get here (atomic
-// ticket after a fence; nothing waits) applies the previous Givens rotations to
-// H(:, k-1) = h1 + h2, forms the new one, records the residual estimate and advances *kdev.
+// ticket after a fence; nothing waits) applies the previous Givens rotations to the new column
+// e_{k-1} - (h1 + h2) (subdiagonal -||w||), forms the new one, records the residual estimate
+// and advances *kdev.
 __global__ void __launch_bounds__(ARN_T) k_arn_finish(double* __restrict__ V,
                                                       const double* __restrict__ w, int64_t n,
                                                       int* __restrict__ kdev,
@@ -422,7 +459,7 @@ __global__ void __launch_bounds__(ARN_T) k_arn_finish(double* __restrict__ V,
   // Givens update of column j = k - 1 (single CTA)
   __shared__ double col[1024], c_s[1024], s_s[1024];
   const int j = k - 1;
-  for (int i = threadIdx.x; i <= j; i += ARN_T) col[i] = h1[i] + h2[i];
+  for (int i = threadIdx.x; i <= j; i += ARN_T) col[i] = (i == j ? 1.0 : 0.0) - (h1[i] + h2[i]);
   for (int i = threadIdx.x; i < j; i += ARN_T) {
     c_s[i] = cs[i];
     s_s[i] = sn[i];
@@ -434,7 +471,7 @@ __global__ void __launch_bounds__(ARN_T) k_arn_finish(double* __restrict__ V,
       col[i + 1] = -s_s[i] * col[i] + c_s[i] * col[i + 1];
       col[i] = t;
     }
-    const double a = col[j], b = sub;
+    const double a = col[j], b = -sub;
     const double den = hypot(a, b);
     double c = 1.0, s = 0.0;
     if (den > 0.0) { c = a / den; s = b / den; }
@@ -464,7 +501,7 @@ void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
   double* Pn = part + 2 * (int64_t)(kmax + 1) * nchunk;
   note_launch(4);
   k_arn_dots<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, nchunk);
-  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, h1, P2, nullptr, nchunk, 1);
+  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, h1, P2, Pn, nchunk, 1);
   k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P2, h2, nullptr, Pn, nchunk, 0);
   k_arn_finish<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, Pn, nchunk, h1, h2, H, ldh, cs, sn, gv,
                                          beta, resid, kmax, ticket);
@@ -475,6 +512,8 @@ template <typename T>
 void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab,
                         int64_t max_ng, const T* S, const double* x, double* y, int transpose,
                         cudaStream_t st, const int* kdev, int64_t kstride) {
+  const int konly = transpose >> 1;  // bit 1: y = K x (or K^T x) instead of (I - K) x
+  transpose &= 1;
   if (!transpose) {
     const size_t smem = 2 * max_ng * sizeof(T);
     static size_t attr = 0;
@@ -484,11 +523,12 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
     }
     note_launch();
     k_apply_dense<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smem, st>>>(
-        d_slabs, d_probs, S, x, y, kdev, kstride);
+        d_slabs, d_probs, S, x, y, kdev, kstride, konly);
   } else {
     note_launch();
     k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 7) / 8), nslab), 256, 0, st>>>(d_slabs, d_probs,
-                                                                                  S, x, y, kdev, kstride);
+                                                                                  S, x, y, kdev, kstride,
+                                                                                  konly);
   }
 }
 

@@ -15,6 +15,7 @@ __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch"
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
+           "ddst_time_apply",
            "ddst_residual_noalloc",
            "ddst_kernel_launches",
            "ddst_last_error",
@@ -163,6 +164,14 @@ def ddst_get_transfer(ctx, prob, j, side, out):
 def ddst_apply_interface(ctx, prob, x, y, transpose=False):
     lib = L.load()
     _check(lib, ctx, lib.ddst_apply_interface(ctx, prob, _ptr(x), _ptr(y), int(bool(transpose))))
+
+
+def ddst_time_apply(ctx, transpose=False, reps=50):
+    """Mean device milliseconds of one interface-operator application (diagnostic)."""
+    lib = L.load()
+    ms = C.c_float()
+    _check(lib, ctx, lib.ddst_time_apply(ctx, int(bool(transpose)), int(reps), C.byref(ms)))
+    return ms.value
 
 
 def ddst_query(ctx, prob=0):
