@@ -128,6 +128,22 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _traffic_table():
+    """DRAM bytes per launch, (kernel, n, w) -> bytes, from the ncu summary table (text lines
+    "kernel n=<n> w=<w> bytes=<b>"); empty if absent."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as fh:
+            for line in fh:
+                f = line.split()
+                if len(f) == 4 and not line.startswith("#"):
+                    kv = dict(t.split("=", 1) for t in f[1:])
+                    out[(f[0], int(kv["n"]), int(kv["w"]))] = float(kv["bytes"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return out
+
+
 def _tc_executed_flops(nds, nb, MB, tile=128, per_cta=256):
     """MMA flops the tensor-core transfer build issues (2D): a CTA of 256 sources runs len - 1
     steps of 3 (128 x MB x MB) MMAs per live 128-source tile."""
@@ -204,8 +220,11 @@ def main():
         opts["gmres_tol"] = args.gmres_tol
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(precision="mixed", host=None):
-        """Returns (forward ms, adjoint ms, info, sbuild ms)."""
+    kept = []
+
+    def step(precision="mixed", host=None, keep=False):
+        """Returns (forward ms, adjoint ms, info, sbuild ms); keep: leave the solver open (in
+        kept) for the kernel timings after the timed region."""
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1, e2, e3, e4 = ev(), ev(), ev(), ev(), ev()
@@ -234,7 +253,10 @@ def main():
             torch.cuda.synchronize()
             adj_ms = ea.elapsed_time(eb)
         torch.cuda.synchronize()
-        sol.close()
+        if keep:
+            kept.append(sol)
+        else:
+            sol.close()
         return e0.elapsed_time(e3), adj_ms, info, e1.elapsed_time(e2)
 
     for _ in range(args.warmup):
@@ -248,8 +270,8 @@ def main():
     l0 = D.ddst_kernel_launches()
     t_start = time.perf_counter()
     fw, adj, sb, infos = [], [], [], []
-    for _ in range(args.steps):
-        a_ms, b_ms, info, s_ms = step()
+    for k_ in range(args.steps):
+        a_ms, b_ms, info, s_ms = step(keep=k_ == args.steps - 1)
         fw.append(a_ms); adj.append(b_ms); sb.append(s_ms); infos.append(info)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_start
@@ -281,35 +303,48 @@ def main():
         fp64 = {"dof_per_s": dof / (f_ms / 1e3), "ms": f_ms, "gmres_iters": finfo["gmres_iters"],
                 "refine_iters": finfo["refine_iters"], "est_rel_error": finfo["est_rel_error"]}
 
-    # roofline of the dominant kernel: the transfer build (k_sbuild_tc), one launch per step,
-    # timed by the CUDA events around ddst_build_transfer on the stream it is launched on.
-    # Algorithmic work: every central source visits every other block once, one (m x m) by
-    # (m x 1) product per visit (2 m^2 flops).  The tensor core executes 3xTF32 on padded blocks
-    # (3 MMAs of 2 MB^2 flops per visit and source), reported as executed_tensor_flops.
+    # Rooflines of the two operations that dominate a step's device time, both measured live
+    # with CUDA events on the stream their kernels are launched on; "roofline" is the one with
+    # the larger device time per step.
     peaks, src = _peaks()
+    traffic = _traffic_table()
+    info = infos[-1]
     m = 2 * w - 1
     MB = 32 if m <= 32 else 64
     nb = n - 1
     nds = n // w - 1
+    # (1) transfer build, k_sbuild_tc, one launch per step (events around ddst_build_transfer).
+    # Algorithmic work: every central source visits every other block once, one (m x m) by
+    # (m x 1) product per visit (2 m^2 flops); the tensor core executes 3xTF32 on padded blocks.
     flops = nds * nb * (nb - 1) * 2.0 * m * m
     sb_ms = statistics.mean(sb)
-    achieved = flops / (sb_ms / 1e3) / 1e12
     tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # dense TF32 : BF16 = 1.1 : 2.25 (nominal)
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "sbuild_tc_traffic.json")) as fh:
-            tj = json.load(fh)
-        if tj.get("n") == n and tj.get("w") == w:
-            traffic = tj.get("bytes_per_launch")
-    except Exception:
-        pass
-    roof = {"kernel": "k_sbuild_tc (explicit S: tcgen05 3xTF32 two-sided sweeps)", "bound": "tensor",
-            "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved / tf32_peak,
-            "traffic": traffic,
-            "peak_source": f"{src} bf16 burst {peaks['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal TF32:BF16), of {src}",
-            "algorithmic_flops_per_launch": flops,
-            "executed_tensor_flops_per_launch": _tc_executed_flops(nds, nb, MB),
-            "avg_launch_ms": sb_ms}
+    roof_tc = {"kernel": "k_sbuild_tc (explicit S: tcgen05 3xTF32 two-sided sweeps)", "bound": "tensor",
+               "achieved": flops / (sb_ms / 1e3) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+               "frac": flops / (sb_ms / 1e3) / 1e12 / tf32_peak,
+               "traffic": traffic.get(("k_sbuild_tc", n, w)),
+               "peak_source": f"bf16 burst {peaks['bf16_tflops']} TFLOP/s x 1.1/2.25 (nominal TF32:BF16), of {src}",
+               "algorithmic_flops_per_launch": flops,
+               "executed_tensor_flops_per_launch": _tc_executed_flops(nds, nb, MB),
+               "avg_launch_ms": sb_ms, "launches_per_step": 1, "ms_per_step": sb_ms}
+    # (2) interface operator (k_h_inner + k_h_owner), once per GMRES iteration, timed by
+    # ddst_time_apply.  Algorithmic bytes: every stored HODLR entry once (dense leaves and the
+    # U, V columns up to the rank, FP32) plus x read twice and y written once (FP64).
+    sol = kept.pop()  # the last timed step's operators
+    ap_ms = D.ddst_time_apply(sol.ctx, False, 50)
+    sol.close()
+    n_if = nds * nb
+    ap_bytes = float(info["bytes_transfer"]) + 3.0 * 8.0 * n_if
+    hbm = peaks["hbm_gbs"]
+    roof_ap = {"kernel": "HODLR interface apply (k_h_inner + k_h_owner)", "bound": "hbm",
+               "achieved": ap_bytes / (ap_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+               "frac": ap_bytes / (ap_ms / 1e3) / 1e9 / hbm,
+               "traffic": traffic.get(("hodlr_apply", n, w)),
+               "peak_source": f"hbm copy {hbm} GB/s, of {src}",
+               "algorithmic_bytes_per_launch": ap_bytes, "avg_launch_ms": ap_ms,
+               "launches_per_step": info["gmres_iters"],
+               "ms_per_step": ap_ms * info["gmres_iters"]}
+    roof = max((roof_tc, roof_ap), key=lambda r: r["ms_per_step"])
 
     info = infos[-1]
     line = {"metric": "DOF/s to 1e-8 rel. error, mixed-precision vs FP64 GPU path; s per adjoint gradient",
@@ -326,7 +361,8 @@ def main():
             "solve_info": {"gmres_iters": info["gmres_iters"], "refine_iters": info["refine_iters"],
                            "est_rel_error": info["est_rel_error"], "rel_residual": info["rel_residual"],
                            "max_rank": info["max_rank"], "bytes_transfer": info["bytes_transfer"]},
-            "fp64_path": fp64, "e2e": e2e, "roofline": roof, "clocks": clk,
+            "fp64_path": fp64, "e2e": e2e, "roofline": roof,
+            "rooflines": {"transfer_build": roof_tc, "interface_apply": roof_ap}, "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.ref_n)

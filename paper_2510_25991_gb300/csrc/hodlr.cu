@@ -238,12 +238,14 @@ __global__ void __launch_bounds__(256) k_sketch(const HItem* __restrict__ items,
 // working precision can still orthogonalize it: a residual below ~1e3 eps of the sample's own
 // norm is rounding noise, so it is rejected (this floors the effective tolerance at about
 // 1e3 eps_T relative to the block).  A third pass runs when the second one still removed
-// more than 30% of the norm ("twice is enough" test).
+// more than 30% of the norm ("twice is enough" test).  The scan stops after `run` consecutive
+// rejected samples: the stopping rule of the adaptive randomized range finder (Halko, Martinsson
+// & Tropp 2011, Sec. 4.4), with the oversampling as the run length.
 template <typename T>
 __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
                                                     T* __restrict__ UV,
                                                     const double* __restrict__ snorm, double tol,
-                                                    int kmax, int* __restrict__ rank_out) {
+                                                    int kmax, int run, int* __restrict__ rank_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const HDev b = hb[blockIdx.x];
   T* y = reinterpret_cast<T*>(smem_raw);  // p values
@@ -269,8 +271,8 @@ __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
     __syncthreads();
     return v;
   };
-  int r = 0;
-  for (int j = 0; j < b.s; ++j) {
+  int r = 0, rejected = 0;
+  for (int j = 0; j < b.s && rejected < run; ++j) {
     for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) y[i] = Q[(int64_t)j * b.p + i];
     __syncthreads();
     const double n0 = norm_y();
@@ -299,6 +301,9 @@ __global__ void __launch_bounds__(512) k_range_cgs2(const HDev* __restrict__ hb,
       const T inv = static_cast<T>(1.0 / nu);
       for (int64_t i = threadIdx.x; i < b.p; i += blockDim.x) Q[(int64_t)r * b.p + i] = y[i] * inv;
       ++r;
+      rejected = 0;
+    } else {
+      ++rejected;
     }
     __syncthreads();
   }
@@ -386,34 +391,54 @@ __global__ void k_copy_leaves(const HLeaf* __restrict__ lv, const int64_t* __res
 //               that write these rows, then y = x - sum, written once (no accumulator, no
 //               atomics), or y = sum alone (K x) when asked.
 // ---------------------------------------------------------------------------------------------
-// One warp per (low-rank block, rank column) item: t_b[c] = W_in(:, c) . x_in, four loads in
-// flight per lane and a single warp reduction.
+// One warp per low-rank block: t_b = W_in^T x_in over all rank columns, eight columns at a time,
+// rows unrolled by four (32 loads in flight per lane), one warp reduction per column.  All
+// blocks fit in one wave, so the time is that of the longest (top-level) block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_h_inner(const HItem* __restrict__ items, int nitems,
-                                                 const HBlock* __restrict__ bl,
+__global__ void __launch_bounds__(256) k_h_inner(const HBlock* __restrict__ bl, int nblk,
                                                  const T* __restrict__ UV,
                                                  const double* __restrict__ x0,
                                                  double* __restrict__ t, int transpose,
                                                  const int* kdev, int64_t kstride) {
   const int wi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (wi >= nitems) return;
-  const HItem it = items[wi];
-  const HBlock& b = bl[it.blk];
+  if (wi >= nblk) return;
+  const HBlock& b = bl[wi];
+  const int rank = b.rank;
+  if (rank == 0) return;
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int len = (int)(transpose ? b.nrows : b.ncols);
   const double* xv = x + (transpose ? b.out_if + b.row0 : b.in_if + b.col0);
-  const T* w = UV + (transpose ? b.u_off : b.v_off) + it.lo * (int64_t)len;
-  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-  int r = lane;
-  for (; r + 96 < len; r += 128) {
-    a0 = fma(w[r], static_cast<T>(xv[r]), a0);
-    a1 = fma(w[r + 32], static_cast<T>(xv[r + 32]), a1);
-    a2 = fma(w[r + 64], static_cast<T>(xv[r + 64]), a2);
-    a3 = fma(w[r + 96], static_cast<T>(xv[r + 96]), a3);
+  const T* W = UV + (transpose ? b.u_off : b.v_off);
+  for (int c0 = 0; c0 < rank; c0 += 8) {
+    const int nc = min(8, rank - c0);
+    const T* Wc = W + (int64_t)c0 * len;
+    T acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) acc[g] = T(0);
+    int r = lane;
+    for (; r + 96 < len; r += 128) {
+      T xr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xr[u] = static_cast<T>(xv[r + 32 * u]);
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (g < nc) {
+          const T* wg = Wc + (int64_t)g * len + r;
+          acc[g] = fma(wg[0], xr[0], fma(wg[32], xr[1], fma(wg[64], xr[2], fma(wg[96], xr[3], acc[g]))));
+        }
+    }
+    for (; r < len; r += 32) {
+      const T xr = static_cast<T>(xv[r]);
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (g < nc) acc[g] = fma(Wc[(int64_t)g * len + r], xr, acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const double v = warp_sum((double)acc[g]);
+      if (lane == 0 && g < nc) t[b.t_off + c0 + g] = v;
+    }
   }
-  for (; r < len; r += 32) a0 = fma(w[r], static_cast<T>(xv[r]), a0);
-  const double v = warp_sum((double)((a0 + a1) + (a2 + a3)));
-  if (lane == 0) t[b.t_off + it.lo] = v;
 }
 
 // Dense leaves are column-major with a leading dimension that is a multiple of 4, so every
@@ -555,7 +580,8 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
     }
   }
   __syncthreads();
-  // W_out(rows, :) t_b of every low-rank block, one row per thread, four columns in flight
+  // W_out(rows, :) t_b of every low-rank block, one row per thread: the first eight columns of
+  // a block are loaded together (one latency round per block), further columns in a tail loop
   for (int r = threadIdx.x; r < len; r += blockDim.x) {
     double a = 0.0;
     for (int q = 0; q < NSL; ++q) {
@@ -564,15 +590,13 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
       const T* W = UV + s_woff[q] + r;
       const int64_t nr = s_nr[q];
       const T* tq = s_t + q * HOWN_TCAP;
-      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-      int c = 0;
-      for (; c + 3 < rank && c + 3 < HOWN_TCAP; c += 4) {
-        a0 = fma(W[(int64_t)c * nr], tq[c], a0);
-        a1 = fma(W[(int64_t)(c + 1) * nr], tq[c + 1], a1);
-        a2 = fma(W[(int64_t)(c + 2) * nr], tq[c + 2], a2);
-        a3 = fma(W[(int64_t)(c + 3) * nr], tq[c + 3], a3);
-      }
-      for (; c < rank; ++c) {
+      T wv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) wv[c] = c < rank ? W[(int64_t)c * nr] : T(0);
+      T acc = T(0);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc = fma(wv[c], c < rank ? tq[c] : T(0), acc);
+      for (int c = 8; c < rank; ++c) {
         T tc;
         if (c < HOWN_TCAP) {
           tc = tq[c];
@@ -580,9 +604,9 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
           const int hb = it->hb[q / HOWN_MAXL][q % HOWN_MAXL];
           tc = static_cast<T>(t[bl[hb].t_off + c]);
         }
-        a0 = fma(W[(int64_t)c * nr], tc, a0);
+        acc = fma(W[(int64_t)c * nr], tc, acc);
       }
-      a += (double)((a0 + a1) + (a2 + a3));
+      a += (double)acc;
     }
     outv[r] += a;
   }
@@ -598,15 +622,13 @@ void HodlrSet::clear() { release(); }
 
 void HodlrSet::release() {
   for (void* p : {UV, D, (void*)t, (void*)d_blocks, (void*)d_leaves, (void*)d_own,
-                  (void*)d_own_T, d_inner})
+                  (void*)d_own_T})
     if (p) cudaFree(p);
   UV = D = nullptr;
   t = nullptr;
   d_blocks = nullptr;
   d_leaves = nullptr;
   d_own = d_own_T = nullptr;
-  d_inner = nullptr;
-  n_inner = 0;
   blocks.clear();
   leaves.clear();
   built = false;
@@ -746,7 +768,8 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   std::vector<int64_t> soff(nsb), sng(nsb);
   for (int b = 0; b < nsb; ++b) { soff[b] = sb[b].off; sng[b] = sb[b].ng; }
   cudaMemcpyAsync(d_sb, sb.data(), sizeof(SBlk) * nsb, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(d_hd, hd.data(), sizeof(HDev) * nblk, cudaMemcpyHostToDevice, st);
+  // a tree without low-rank levels (n_Gamma <= leaf) has only dense leaves: no sketch below
+  if (nblk > 0) cudaMemcpyAsync(d_hd, hd.data(), sizeof(HDev) * nblk, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_sng, sng.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(H.d_leaves, H.leaves.data(), sizeof(HLeaf) * H.leaves.size(), cudaMemcpyHostToDevice, st);
@@ -774,32 +797,37 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     for (int64_t lo = 0; lo < hd[b].q; lo += 64) pitems.push_back({b, lo});
   const size_t nit = std::max(items.size(), pitems.size());
   if (!al((void**)&d_items, sizeof(HItem) * nit)) { cleanup(); H.release(); msg = "oom"; return 2; }
-  note_launch();
-  k_gen_omega<T><<<dim3(32, nblk), 256, 0, st>>>(d_hd, (T*)H.UV, hp.seed);
-  cudaMemcpyAsync(d_items, items.data(), sizeof(HItem) * items.size(), cudaMemcpyHostToDevice, st);
-  launch_sketch<T>(SC, d_items, (int)items.size(), d_hd, S, (T*)H.UV, st);
+  if (nblk > 0) {
+    note_launch();
+    k_gen_omega<T><<<dim3(32, nblk), 256, 0, st>>>(d_hd, (T*)H.UV, hp.seed);
+    cudaMemcpyAsync(d_items, items.data(), sizeof(HItem) * items.size(), cudaMemcpyHostToDevice, st);
+    launch_sketch<T>(SC, d_items, (int)items.size(), d_hd, S, (T*)H.UV, st);
+  }
   // sigma estimate: sqrt of the Rayleigh quotient norm
   std::vector<double> nrm(nsb);
   cudaMemcpyAsync(nrm.data(), d_nrm, sizeof(double) * nsb, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   for (auto& v : nrm) v = std::sqrt(std::max(v, 0.0));
   cudaMemcpyAsync(d_nrm, nrm.data(), sizeof(double) * nsb, cudaMemcpyHostToDevice, st);
-  {
+  if (nblk > 0) {
     int64_t maxp = 0;
     for (auto& d : hd) maxp = std::max(maxp, d.p);
     const size_t smem = sizeof(T) * maxp;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(k_range_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     note_launch();
-    k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax, d_rank);
+    k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax,
+                                             std::max(1, hp.oversample), d_rank);
   }
-  cudaMemcpyAsync(d_items, pitems.data(), sizeof(HItem) * pitems.size(), cudaMemcpyHostToDevice, st);
-  launch_project<T>(SC, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
+  if (nblk > 0) {
+    cudaMemcpyAsync(d_items, pitems.data(), sizeof(HItem) * pitems.size(), cudaMemcpyHostToDevice, st);
+    launch_project<T>(SC, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
+  }
   note_launch();
   k_copy_leaves<T><<<dim3(16, (unsigned)H.leaves.size()), 256, 0, st>>>(H.d_leaves, d_soff, d_sng, S,
                                                                        (T*)H.D);
   std::vector<int> ranks(nblk);
-  cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
+  if (nblk > 0) cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cleanup();
@@ -812,7 +840,8 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   }
   H.bytes = (used + dl) * (int64_t)sizeof(T);
   H.t_len = tl;
-  cudaMemcpyAsync(H.d_blocks, H.blocks.data(), sizeof(HBlock) * nblk, cudaMemcpyHostToDevice, st);
+  if (nblk > 0)
+    cudaMemcpyAsync(H.d_blocks, H.blocks.data(), sizeof(HBlock) * nblk, cudaMemcpyHostToDevice, st);
   // output-owner items: one per (interface, leaf row range), for the plain and transposed apply
   std::vector<HOwn> own[2];
   {
@@ -852,21 +881,16 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
       }
     }
   }
-  // inner-product items: one per (low-rank block, rank column)
-  std::vector<HItem> inner;
-  for (int b = 0; b < nblk; ++b)
-    for (int c = 0; c < H.blocks[b].rank; ++c) inner.push_back({b, (int64_t)c});
-  H.n_inner = (int)inner.size();
   H.n_own = (int)own[0].size();
   H.n_own_T = (int)own[1].size();
-  if (!al(&H.d_inner, sizeof(HItem) * std::max<size_t>(1, inner.size())) ||
-      !al((void**)&H.d_own, sizeof(HOwn) * std::max<size_t>(1, own[0].size())) ||
+  if (!al((void**)&H.d_own, sizeof(HOwn) * std::max<size_t>(1, own[0].size())) ||
       !al((void**)&H.d_own_T, sizeof(HOwn) * std::max<size_t>(1, own[1].size()))) {
     H.release(); msg = "oom"; return 2;
   }
-  cudaMemcpyAsync(H.d_inner, inner.data(), sizeof(HItem) * inner.size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(H.d_own, own[0].data(), sizeof(HOwn) * own[0].size(), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(H.d_own_T, own[1].data(), sizeof(HOwn) * own[1].size(), cudaMemcpyHostToDevice, st);
+  for (int tr = 0; tr < 2; ++tr)
+    if (!own[tr].empty())
+      cudaMemcpyAsync(tr ? H.d_own_T : H.d_own, own[tr].data(), sizeof(HOwn) * own[tr].size(),
+                      cudaMemcpyHostToDevice, st);
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { msg = cudaGetErrorString(e); H.release(); return 1; }
   H.built = true;
@@ -878,11 +902,11 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
                  int transpose, cudaStream_t st, const int* kdev, int64_t kstride) {
   const int konly = transpose >> 1;  // bit 1: y = K x (or K^T x) instead of (I - K) x
   transpose &= 1;
-  if (H.n_inner > 0) {
+  if (!H.blocks.empty()) {
     note_launch();
-    k_h_inner<T><<<(H.n_inner + 7) / 8, 256, 0, st>>>((const HItem*)H.d_inner, H.n_inner,
-                                                     H.d_blocks, (const T*)H.UV, x, H.t,
-                                                     transpose, kdev, kstride);
+    const int nblk = (int)H.blocks.size();
+    k_h_inner<T><<<(nblk + 7) / 8, 256, 0, st>>>(H.d_blocks, nblk, (const T*)H.UV, x, H.t,
+                                                 transpose, kdev, kstride);
   }
   const int no = transpose ? H.n_own_T : H.n_own;
   if (no > 0) {

@@ -63,8 +63,6 @@ struct HodlrSet {
   HOwn* d_own = nullptr;      // output-owner items of the apply
   HOwn* d_own_T = nullptr;    // ... of the transposed apply
   int n_own = 0, n_own_T = 0;
-  void* d_inner = nullptr;    // inner-product items (low-rank block, rank column)
-  int n_inner = 0;
   int64_t t_len = 0;
   int64_t bytes = 0;
   int max_rank = 0;

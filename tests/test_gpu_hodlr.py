@@ -54,6 +54,41 @@ def test_hodlr_exact_when_tolerance_vanishes():
     sol.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_compress_with_leaf_covering_the_whole_block(precision):
+    """n_Gamma = 63 <= leaf size: the cluster tree has no low-rank level, every S block is one
+    dense leaf; compression, both applies and the solve still work."""
+    from paper_2510_25991_gb300 import ddst as D
+    prob = I.make_problem("convdiff2d", n=64, w=16)
+    A, b = O.assemble(prob)
+    uref = O.global_solve(A, b)
+    geo, (Sp, Sn) = oracle_blocks(prob)
+    sol = solver(prob, precision, gmres_tol=1e-12 if precision == "fp64" else 0.0)
+    sol.compress(1e-8)
+    _, _, rank = D.ddst_query(sol.ctx)
+    assert rank == 0
+    u = torch.empty((63, 63), dtype=torch.float64, device="cuda")
+    st, info = sol.solve(dev(prob["f"]), dev(prob["g"]), u)
+    assert np.linalg.norm(u.cpu().numpy().ravel() - uref) / np.linalg.norm(uref) <= 1e-8, info
+    rng = np.random.default_rng(5)
+    nif = geo.nds * geo.ngamma
+    x = rng.standard_normal(nif)
+    K = np.zeros((nif, nif))
+    for j in range(geo.nds):
+        rows = slice(j * geo.ngamma, (j + 1) * geo.ngamma)
+        if Sp[j] is not None:
+            K[rows, (j - 1) * geo.ngamma:j * geo.ngamma] = Sp[j]
+        if Sn[j] is not None:
+            K[rows, (j + 1) * geo.ngamma:(j + 2) * geo.ngamma] = Sn[j]
+    tol = 1e-12 if precision == "fp64" else 1e-3  # FP32 transfer operators (as for S itself)
+    for tr, Kop in ((0, K), (1, K.T)):
+        y = np.empty(nif)
+        D.ddst_apply_interface(sol.ctx, 0, x, y, tr)
+        ref = x - Kop @ x
+        assert np.abs(y - ref).max() <= tol * np.abs(ref).max()
+    sol.close()
+
+
 @pytest.mark.parametrize("tol", [1e-6, 1e-8])
 def test_hodlr_error_within_ten_tol_and_ranks_near_optimal(tol):
     from paper_2510_25991_gb300 import ddst as D
