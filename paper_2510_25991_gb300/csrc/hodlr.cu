@@ -468,8 +468,10 @@ __device__ __forceinline__ double vec_dot<double>(const double2& m, const double
   return m.x * x[0] + m.y * x[1];
 }
 
+constexpr int OWN_T = 128;  // threads of an owner CTA: 9 resident per SM, one wave at 2048^2
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
+__global__ void __launch_bounds__(OWN_T) k_h_owner(const HOwn* __restrict__ items,
                                                  const HBlock* __restrict__ bl,
                                                  const HLeaf* __restrict__ lv,
                                                  const T* __restrict__ UV,
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
     if (!transpose) {  // D x: thread = (vector of VEC rows, column group)
       const int nvr = ld / VEC;
       const int rv = nvr <= 32 ? 32 : (nvr <= 64 ? 64 : 128);
-      const int groups = 256 / rv;
+      const int groups = OWN_T / rv;  // >= 1 (nvr <= 128 for len <= 256)
       const int r = threadIdx.x % rv, g = threadIdx.x / rv;
       T a[VEC];
 #pragma unroll
@@ -566,7 +568,7 @@ __global__ void __launch_bounds__(256) k_h_owner(const HOwn* __restrict__ items,
     } else {  // D^T x: warp per column, both leaves
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
       const int nvr = ld / VEC;
-      for (int c = warp; c < len; c += 8) {
+      for (int c = warp; c < len; c += OWN_T / 32) {
         const V* col0 = reinterpret_cast<const V*>(M0 + (int64_t)c * ld);
         T part = T(0);
         for (int v = lane; v < nvr; v += 32) part += vec_dot<T>(col0[v], sx + v * VEC);
@@ -773,12 +775,13 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_sng, sng.data(), sizeof(int64_t) * nsb, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(H.d_leaves, H.leaves.data(), sizeof(HLeaf) * H.leaves.size(), cudaMemcpyHostToDevice, st);
-  // ||S||_2 by power iteration on S^T S (4 steps)
+  // ||S||_2 by power iteration on S^T S (2 steps; an underestimate only lowers the truncation
+  // threshold, i.e. errs towards higher ranks)
   note_launch();
   k_sblk_init<<<nsb, 256, 0, st>>>(d_sb, d_x, stride, hp.seed ^ 0x9e3779b97f4a7c15ull);
   const unsigned gr = (unsigned)((max_ng + 255) / 256), gc = (unsigned)((max_ng + 7) / 8);
   const unsigned gz = (unsigned)((max_ng + 127) / 128);
-  for (int itp = 0; itp < 4; ++itp) {
+  for (int itp = 0; itp < 2; ++itp) {
     cudaMemsetAsync(d_y, 0, sizeof(double) * stride * nsb, st);
     note_launch(3);
     k_sblk_gemv<T><<<dim3(gr, nsb, gz), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
@@ -911,7 +914,7 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
   const int no = transpose ? H.n_own_T : H.n_own;
   if (no > 0) {
     note_launch();
-    k_h_owner<T><<<no, 256, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_leaves,
+    k_h_owner<T><<<no, OWN_T, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_leaves,
                                      (const T*)H.UV, (const T*)H.D, H.t, x, y, transpose, konly,
                                      kdev, kstride);
   }
