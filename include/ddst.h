@@ -86,7 +86,9 @@ typedef struct {
                            1e-2 for DDST_MIXED (inner solve of the refinement) or 1e-10 for
                            DDST_FP64                                                          */
   int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES)                           */
-  double refine_tol;    /* stop when ||correction|| <= refine_tol * ||u|| (FP64 refinement)   */
+  double refine_tol;    /* FP64 refinement stops when its error estimate, rho / (1 - rho) times
+                           the last correction (rho: observed contraction, capped at 1/2),
+                           is <= refine_tol * ||u||                                         */
   int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
   int k_max;            /* HODLR rank cap per block                                           */
   int oversample;       /* extra random samples beyond k_max (sketch width k_max+oversample)  */
@@ -106,7 +108,7 @@ typedef struct {
   int gmres_iters_first;  /* iterations of the first interface solve                          */
   int refine_iters;       /* DD solves performed (1 = no refinement correction needed)        */
   double rel_residual;    /* final ||b - A u||_2 / ||b||_2 in FP64                            */
-  double est_rel_error;   /* ||last correction||_2 / ||u||_2                                  */
+  double est_rel_error;   /* refinement error bound rho/(1-rho) ||last correction|| / ||u||    */
   double t_factor, t_transfer, t_compress, t_solve;
   int64_t bytes_factors;  /* device bytes of the local factors                                */
   int64_t bytes_transfer; /* device bytes of the transfer operators (dense or HODLR)          */

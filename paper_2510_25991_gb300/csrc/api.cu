@@ -693,6 +693,23 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   return DDST_OK;
 }
 
+// A-posteriori error of a contracting fixed-point iteration: if every step reduces the error by
+// a factor rho < 1, the error after applying the correction delta_k is at most
+// rho / (1 - rho) ||delta_k||.  rho is estimated by the larger of the last two ratios
+// ||delta_k|| / ||delta_{k-1}|| (only the first ratio after one step) and used up to 1/2; the
+// first correction (from zero) has no estimate and counts in full.  Returns the bound relative
+// to ||x|| given the correction norms so far (hist) and ||x||.
+double refine_error_estimate(const std::vector<double>& hist, double xn) {
+  const size_t k = hist.size();
+  if (k == 0 || !(xn > 0.0)) return 0.0;
+  double rel = hist[k - 1] / xn;
+  if (k < 2) return rel;
+  double rho = hist[k - 2] > 0.0 ? hist[k - 1] / hist[k - 2] : 1.0;
+  if (k >= 3 && hist[k - 3] > 0.0) rho = std::max(rho, hist[k - 2] / hist[k - 3]);
+  rho = std::min(rho, 0.5);
+  return rel * rho / (1.0 - rho);
+}
+
 // One application of the DD solve map (Alg. 2 + GMRES + reconstruction):
 // rhs volume vector r (FP64) -> volume correction e (FP64); traces written into ctx->if_u.
 template <typename T>
@@ -749,6 +766,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
   const double tol = ctx->opt.gmres_tol;
   int total_it = 0, first_it = 0, nref = 0;
   double est = 0.0, relres = 0.0;
+  std::vector<double> dnorm;
   ddst_status result = DDST_OK;
   const int rmax = std::max(0, ctx->opt.refine_max);
   for (int it = 0; it <= rmax; ++it) {
@@ -766,9 +784,8 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
-    const double en = vec_norm(ctx, ctx->d_e, N, 4);
-    const double un = vec_norm(ctx, ctx->d_u, N, 5);
-    est = un > 0.0 ? en / un : 0.0;
+    dnorm.push_back(vec_norm(ctx, ctx->d_e, N, 4));
+    est = refine_error_estimate(dnorm, vec_norm(ctx, ctx->d_u, N, 5));
     if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;
@@ -862,6 +879,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
   const double gnorm = vec_norm(ctx, ctx->d_ga, N, 3);
   int total_it = 0, first_it = 0, nref = 0;
   double est = 0.0;
+  std::vector<double> dnorm;
   ddst_status result = DDST_OK, s;
   const int rmax = std::max(0, ctx->opt.refine_max);
   for (int it = 0; it <= rmax; ++it) {
@@ -879,9 +897,8 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_lam, st);
-    const double en = vec_norm(ctx, ctx->d_e, N, 4);
-    const double ln = vec_norm(ctx, ctx->d_lam, N, 5);
-    est = ln > 0.0 ? en / ln : 0.0;
+    dnorm.push_back(vec_norm(ctx, ctx->d_e, N, 4));
+    est = refine_error_estimate(dnorm, vec_norm(ctx, ctx->d_lam, N, 5));
     if (rmax == 0) {
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;
