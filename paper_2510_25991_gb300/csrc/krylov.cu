@@ -253,16 +253,34 @@ __global__ void k_trisolve(const double* __restrict__ H, int ldh, const double* 
 // consumer CTA: no two CTAs update the same address.
 constexpr int ARN_T = 256, ARN_E = 4, ARN_CHUNK = ARN_T * ARN_E, ARN_G = 8;
 
-// sh[i] = sum_c P[i * nchunk + c] for i < k (every thread of the CTA takes part).
+// sh[i] = sum_c P[i * nchunk + c] for i < k (every thread of the CTA takes part).  A warp sums
+// two rows per round; each lane issues its loads of a 128-chunk window together (predicated,
+// independent), so a round costs one L2 latency for up to 128 chunks.
 __device__ __forceinline__ void arn_reduce(const double* __restrict__ P, int nchunk, int k,
                                            double* __restrict__ sh) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i < k; i += ARN_T / 32) {
-    const double* row = P + (int64_t)i * nchunk;
-    double a = 0.0;
-    for (int c = lane; c < nchunk; c += 32) a += row[c];
-    a = warp_sum(a);
-    if (lane == 0) sh[i] = a;
+  constexpr int W = ARN_T / 32;
+  for (int i = warp; i < k; i += 2 * W) {
+    const int i2 = i + W;
+    const double* r1 = P + (int64_t)i * nchunk;
+    const double* r2 = P + (int64_t)(i2 < k ? i2 : i) * nchunk;
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = 0.0;
+    for (int c0 = 0; c0 < nchunk; c0 += 128) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = c0 + q * 32 + lane;
+        a[q] += c < nchunk ? r1[c] : 0.0;
+        a[4 + q] += c < nchunk ? r2[c] : 0.0;
+      }
+    }
+    const double s1 = warp_sum((a[0] + a[1]) + (a[2] + a[3]));
+    const double s2 = warp_sum((a[4] + a[5]) + (a[6] + a[7]));
+    if (lane == 0) {
+      sh[i] = s1;
+      if (i2 < k) sh[i2] = s2;
+    }
   }
   __syncthreads();
 }
@@ -337,15 +355,38 @@ __device__ __forceinline__ void arn_chunk_update(const double* __restrict__ V, i
   }
 }
 
+// First-pass dots: the chunk of w is staged in shared memory and each warp takes whole basis
+// vectors (warp q: vectors q, q + 8, ...), 32 loads in flight per lane and one warp reduction
+// per vector, no block barrier inside the loop.
 __global__ void __launch_bounds__(ARN_T) k_arn_dots(const double* __restrict__ V,
                                                     const double* __restrict__ w, int64_t n,
                                                     const int* __restrict__ kdev,
                                                     double* __restrict__ P1, int nchunk) {
+  __shared__ double sw[ARN_CHUNK];
   const int k = *kdev;
   const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
   double wv[ARN_E];
   arn_load_chunk(w, n, base, wv);
-  arn_chunk_dots(V, n, k, base, wv, P1, nchunk);
+#pragma unroll
+  for (int e = 0; e < ARN_E; ++e) sw[e * ARN_T + threadIdx.x] = wv[e];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t len = n - base < ARN_CHUNK ? n - base : ARN_CHUNK;
+  for (int i = warp; i < k; i += ARN_T / 32) {
+    const double* v = V + (int64_t)i * n + base;
+    double acc = 0.0;
+    if (len == ARN_CHUNK) {
+      double a4[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int e = 0; e < ARN_CHUNK / 32; ++e)
+        a4[e & 3] = fma(v[e * 32 + lane], sw[e * 32 + lane], a4[e & 3]);
+      acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
+    } else {
+      for (int64_t e = lane; e < len; e += 32) acc = fma(v[e], sw[e], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) P1[(int64_t)i * nchunk + blockIdx.x] = acc;
+  }
   double acc = 0.0;  // |w|^2 over the chunk, row k of P1
 #pragma unroll
   for (int e = 0; e < ARN_E; ++e) acc = fma(wv[e], wv[e], acc);
