@@ -21,8 +21,11 @@ namespace ddst {
 // bank conflicts): W = F^T, B^T for A^{-1} sweeps and W = F, B for A^{-T} sweeps.  Each ring
 // stage carries the factor block, the right-hand-side block and the coupling vector of one step
 // (three bulk copies on one mbarrier); the ring is deep enough to keep ~NST steps in flight.
+// 4 M threads: thread t handles row t % M over the column quarter t / M (a warp shares one
+// quarter, so the shared-memory reads of W are conflict-free); the quarters' partial sums are
+// combined in shared memory before the row update.
 template <typename T, int M, int NST>
-__global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ slabs,
+__global__ void __launch_bounds__(4 * M) k_solve_sweep(const SlabDesc* __restrict__ slabs,
                                                    const int* __restrict__ ids,
                                                    const T* __restrict__ Wf,
                                                    const T* __restrict__ Wb,
@@ -35,7 +38,8 @@ __global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ 
   T* sB = sW + NST * M * M;                 // [NST][M] right-hand-side block
   T* sC = sB + NST * M;                     // [NST][M] coupling vector
   T* sv = sC + NST * M;                     // [M] current vector
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sv + M);
+  T* red = sv + M;                          // [4][M] partial sums of the column quarters
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 4 * M);
   __shared__ int s_abort;
   const int sid = ids[blockIdx.x];
   const SlabDesc s = slabs[sid];
@@ -44,7 +48,7 @@ __global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ 
   T* out = (down ? bf : bb) + s.loc_off;
   const T* rhs = b + s.loc_off;
   const int nb = s.nb;
-  const int r = threadIdx.x;
+  const int r = threadIdx.x % M, part = threadIdx.x / M;
   int issued = 0, consumed = 0;
   auto blk_of = [&](int step) { return down ? step + 1 : nb - step; };
   // coupling: non-transposed top-down ell_k (SOUTH of k), bottom-up ups_k (NORTH of k);
@@ -63,15 +67,15 @@ __global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ 
     bulk_g2s(sC + stage * M, pack + s.pack_off + (int64_t)(cblk - 1) * PK_NFIELDS * M + cfield * M,
              M * sizeof(T), &bar[stage]);
   };
-  if (r == 0) {
+  if (threadIdx.x == 0) {
     s_abort = 0;
     for (int q = 0; q < NST; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (r == 0)
+  if (threadIdx.x == 0)
     for (int q = 1; q <= NST && q < nb; ++q) issue(q);
-  {
+  if (part == 0) {
     const int k = blk_of(0);
     const T v = rhs[(int64_t)(k - 1) * M + r];
     sv[r] = v;
@@ -85,25 +89,30 @@ __global__ void __launch_bounds__(M) k_solve_sweep(const SlabDesc* __restrict__ 
     consumed = step;
     const T* W = sW + stage * M * M;
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-#pragma unroll 8
-    for (int c = 0; c < M; c += 4) {
+    const int c0 = part * (M / 4);
+#pragma unroll
+    for (int c = c0; c < c0 + M / 4; c += 4) {
       a0 = fma(W[c * M + r], sv[c], a0);
       a1 = fma(W[(c + 1) * M + r], sv[c + 1], a1);
       a2 = fma(W[(c + 2) * M + r], sv[c + 2], a2);
       a3 = fma(W[(c + 3) * M + r], sv[c + 3], a3);
     }
-    const T v = sB[stage * M + r] - sC[stage * M + r] * ((a0 + a1) + (a2 + a3));
+    red[part * M + r] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (s_abort) break;
-    sv[r] = v;
-    out[(int64_t)(k - 1) * M + r] = v;
+    if (part == 0) {
+      const T v = sB[stage * M + r] -
+                  sC[stage * M + r] * ((red[r] + red[M + r]) + (red[2 * M + r] + red[3 * M + r]));
+      sv[r] = v;
+      out[(int64_t)(k - 1) * M + r] = v;
+    }
     __syncthreads();
-    if (r == 0 && step + NST < nb) {
+    if (threadIdx.x == 0 && step + NST < nb) {
       fence_proxy_async();
       issue(step + NST);
     }
   }
-  if (r == 0)
+  if (threadIdx.x == 0)
     for (int q = consumed + 1; q <= issued; ++q)
       mbar_wait(&bar[(q - 1) % NST], ((q - 1) / NST) & 1, st, sid, -1);
 }
@@ -161,7 +170,7 @@ static void run_solve(const SlabDesc* d_slabs, const int* d_ids, int nids, int m
                       const T* F, const T* B, const T* Ft, const T* Bt, const T* G,
                       const T* pack, const T* b, T* bf, T* bb, T* x, double* iface,
                       int transpose, int mode, DevStatus* st, cudaStream_t s) {
-  const size_t smem = (size_t)NST * (M * M + 2 * M) * sizeof(T) + M * sizeof(T) + NST * 8;
+  const size_t smem = (size_t)NST * (M * M + 2 * M) * sizeof(T) + 5 * M * sizeof(T) + NST * 8;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_solve_sweep<T, M, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -173,7 +182,7 @@ static void run_solve(const SlabDesc* d_slabs, const int* d_ids, int nids, int m
   const T* Wf = transpose ? F : Ft;
   const T* Wb = transpose ? B : Bt;
   note_launch();
-  k_solve_sweep<T, M, NST><<<dim3(nids, 2), M, smem, s>>>(d_slabs, d_ids, Wf, Wb, pack, b, bf, bb,
+  k_solve_sweep<T, M, NST><<<dim3(nids, 2), 4 * M, smem, s>>>(d_slabs, d_ids, Wf, Wb, pack, b, bf, bb,
                                                          transpose, st);
   note_launch();
   k_solve_combine<T, M><<<dim3(max_nb, nids), 128, 0, s>>>(d_slabs, d_ids, G, b, bf, bb, x, iface,
