@@ -41,7 +41,7 @@ __device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int 
 // Blocked Gauss-Jordan inversion in shared memory (block pivots of 16): the 16 x 16 pivot
 // block is inverted by warp 0 (warp-synchronous, no pivoting), then the pivot row panel
 // R = P^{-1} X(q, :), the column panel C = X(:, q) and the trailing update
-// X(i, j) -= C(i, :) R(:, j), X(i, q) = -C(i, :) P^{-1} run on all 256 threads as small GEMMs.
+// X(i, j) -= C(i, :) R(:, j), X(i, q) = -C(i, :) P^{-1} run on all threads as small GEMMs.
 // Three block barriers per 16 pivots.  X has leading dimension LD = M + 4 (16-byte rows).
 // The trailing update runs over 4 x 4 patches distributed round-robin over the threads.
 // ---------------------------------------------------------------------------------------------
@@ -183,12 +183,16 @@ __device__ __forceinline__ void store_block(const T* __restrict__ X, T* __restri
 // k_factor_verify; the host falls back to the exact sequential sweep if any check fails.  The
 // stencil pack of the next row is prefetched by a bulk copy while the current one is inverted.
 // Each chunk's recurrence is latency-bound (one block row at a time), so throughput comes from
-// concurrent chunks: the FP32 kernel is bounded to 64 registers for 4 resident CTAs per SM.
-template <typename T> struct FactorOcc { static constexpr int min_blocks = 1; };
-template <> struct FactorOcc<float> { static constexpr int min_blocks = 4; };
+// concurrent chunks: the FP32 kernel runs 128-thread CTAs, 6 resident per SM (shared memory).
+template <typename T> struct FactorOcc {
+  static constexpr int threads = 256, min_blocks = 1;
+};
+template <> struct FactorOcc<float> {
+  static constexpr int threads = 128, min_blocks = 6;
+};
 
 template <typename T, int M>
-__global__ void __launch_bounds__(256, FactorOcc<T>::min_blocks) k_factor(const SlabDesc* __restrict__ slabs,
+__global__ void __launch_bounds__(FactorOcc<T>::threads, FactorOcc<T>::min_blocks) k_factor(const SlabDesc* __restrict__ slabs,
                                                 const FacChunk* __restrict__ chunks,
                                                 const T* __restrict__ pack, T* __restrict__ F,
                                                 T* __restrict__ B, T* __restrict__ Ft,
@@ -389,7 +393,7 @@ void launch_factor_M(const SlabDesc* d_slabs, const FacChunk* d_chunks, int nchu
   if (phase == 0) {  // pivot sweeps + convergence check of warm-started chunks
     if (nchunks == 0) return;
     note_launch();
-    k_factor<T, M><<<nchunks, 256, sm_f, s>>>(d_slabs, d_chunks, pack, F, B, Ft, Bt, chk, Uhi, Ulo,
+    k_factor<T, M><<<nchunks, FactorOcc<T>::threads, sm_f, s>>>(d_slabs, d_chunks, pack, F, B, Ft, Bt, chk, Uhi, Ulo,
                                               umma_elems, st);
     note_launch();
     k_factor_verify<T, M><<<nchunks, 256, 0, s>>>(d_slabs, d_chunks, F, B, chk, diff);
@@ -418,9 +422,9 @@ template <typename T>
 int factor_ctas_per_sm(int M) {
   int n = 0;
   switch (M) {
-    case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 32>, 256, factor_smem<T, 32>()); break;
-    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 64>, 256, factor_smem<T, 64>()); break;
-    case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 128>, 256, factor_smem<T, 128>()); break;
+    case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 32>, FactorOcc<T>::threads, factor_smem<T, 32>()); break;
+    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 64>, FactorOcc<T>::threads, factor_smem<T, 64>()); break;
+    case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_factor<T, 128>, FactorOcc<T>::threads, factor_smem<T, 128>()); break;
     default: break;
   }
   cudaGetLastError();
