@@ -8,7 +8,10 @@ two-sided block factorization, explicit transfer operators, HODLR compression, e
 loads, interface GMRES, reconstruction and FP64 refinement until the estimated relative error
 is below 1e-8 (the forward part, which the headline DOF/s measures), followed by one adjoint
 gradient (timed separately).  Inputs are resident on the device when the timed region starts;
-the working set (factors ~6 GB) is far larger than L2 and L2 is also flushed between steps.
+the working set (factors and their tensor-core copies, ~20 GB) is far larger than L2, and L2 is
+also flushed between steps.  After the timed region the two operations that dominate a step,
+the transfer build and the interface-operator apply, are timed with CUDA events on their launch
+stream for the roofline entries.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on a bounded sample of
 the same workload family.  Under torchrun every rank solves its own instance (weak scaling,
