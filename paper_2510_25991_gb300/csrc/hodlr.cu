@@ -662,6 +662,7 @@ static void launch_project(int SC, const HItem* it, int n, const HDev* hb, const
                            const T* S, T* UV, cudaStream_t st) {
   if (n == 0) return;
   switch (SC) {
+    case 16: note_launch(); k_project<T, 16><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
     case 32: note_launch(); k_project<T, 32><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
     case 64: note_launch(); k_project<T, 64><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
     case 96: note_launch(); k_project<T, 96><<<n, 256, 0, st>>>(it, hb, rank, S, UV); break;
@@ -822,15 +823,20 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax,
                                              std::max(1, hp.oversample), d_rank);
   }
+  // the projection is instantiated for the largest detected rank, not the sample capacity
+  std::vector<int> ranks(nblk);
   if (nblk > 0) {
+    cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    int maxr = 0;
+    for (int v : ranks) maxr = std::max(maxr, v);
+    const int SCp = maxr <= 16 ? 16 : (maxr <= 32 ? 32 : (maxr <= 64 ? 64 : (maxr <= 96 ? 96 : 128)));
     cudaMemcpyAsync(d_items, pitems.data(), sizeof(HItem) * pitems.size(), cudaMemcpyHostToDevice, st);
-    launch_project<T>(SC, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
+    if (maxr > 0) launch_project<T>(SCp, d_items, (int)pitems.size(), d_hd, d_rank, S, (T*)H.UV, st);
   }
   note_launch();
   k_copy_leaves<T><<<dim3(16, (unsigned)H.leaves.size()), 256, 0, st>>>(H.d_leaves, d_soff, d_sng, S,
                                                                        (T*)H.D);
-  std::vector<int> ranks(nblk);
-  if (nblk > 0) cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cleanup();
