@@ -91,20 +91,36 @@ __global__ void k_sblk_gemv(const SBlk* __restrict__ sb, const T* __restrict__ S
     if (row >= b.ng || c0 >= b.ng) return;
     const int64_t c1 = min(b.ng, c0 + 128);
     double acc = 0.0;
-    for (int64_t cb = c0; cb < c1; cb += 32) {
-      T part = T(0);
+    for (int64_t cb = c0; cb < c1; cb += 32) {  // four independent chains per 32 columns
+      T p[4] = {T(0), T(0), T(0), T(0)};
       const int64_t ce = min(c1, cb + 32);
-      for (int64_t c = cb; c < ce; ++c) part = fma(M[c * b.ng + row], static_cast<T>(xv[c]), part);
-      acc += (double)part;
+      int64_t c = cb;
+      for (; c + 3 < ce; c += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = fma(M[(c + u) * b.ng + row], static_cast<T>(xv[c + u]), p[u]);
+      }
+      for (; c < ce; ++c) p[0] = fma(M[c * b.ng + row], static_cast<T>(xv[c]), p[0]);
+      acc += (double)((p[0] + p[1]) + (p[2] + p[3]));
     }
     atomicAdd(&yv[row], acc);
   } else {  // y = S^T x: warp per column
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (col >= b.ng || blockIdx.z != 0) return;
-    T part = T(0);
-    for (int64_t r = lane; r < b.ng; r += 32) part = fma(M[col * b.ng + r], static_cast<T>(xv[r]), part);
-    const double acc = warp_sum((double)part);
+    const T* mc = M + col * b.ng;
+    double acc = 0.0;
+    for (int64_t r0 = 0; r0 < b.ng; r0 += 1024) {  // four independent chains, 32 rows each
+      T p[4] = {T(0), T(0), T(0), T(0)};
+      const int64_t re = min(b.ng, r0 + 1024);
+      int64_t r = r0 + lane;
+      for (; r + 96 < re; r += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] = fma(mc[r + 32 * u], static_cast<T>(xv[r + 32 * u]), p[u]);
+      }
+      for (; r < re; r += 32) p[0] = fma(mc[r], static_cast<T>(xv[r]), p[0]);
+      acc += (double)((p[0] + p[1]) + (p[2] + p[3]));
+    }
+    acc = warp_sum(acc);
     if (lane == 0) yv[col] = acc;
   }
 }
