@@ -71,7 +71,7 @@ struct ddst_ctx {
          *d_e = nullptr, *d_lam = nullptr, *d_ga = nullptr, *d_gn = nullptr, *d_an = nullptr;
   double *if_fh = nullptr, *if_u = nullptr, *if_w = nullptr, *if_tmp = nullptr;
   double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr,
-         *resid = nullptr, *hcol = nullptr, *hpass = nullptr, *part = nullptr, *scal = nullptr,
+         *resid = nullptr, *part = nullptr, *scal = nullptr,
          *ysol = nullptr;
   int ldh = 0;
   int nchunk = 0;
@@ -564,8 +564,6 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   AL(ctx->sn, sizeof(double) * (maxit + 1));
   AL(ctx->gv, sizeof(double) * (maxit + 2));
   AL(ctx->resid, sizeof(double) * (maxit + 1));
-  AL(ctx->hcol, sizeof(double) * (maxit + 1));
-  AL(ctx->hpass, sizeof(double) * (maxit + 1));
   AL(ctx->part, sizeof(double) * (size_t)(maxit + 1) * std::max(ctx->nchunk, 1024));
   AL(ctx->scal, sizeof(double) * 16);
   AL(ctx->ysol, sizeof(double) * (maxit + 1));

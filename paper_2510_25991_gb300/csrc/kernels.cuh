@@ -110,14 +110,8 @@ void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
                          double* sn, double* gv, const double* beta, double* resid, int kmax,
                          cudaStream_t st);
 int arnoldi_chunks(int64_t n);  // chunks of the Arnoldi kernels (partial sums per chunk)
-void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k, int nchunk,
-                    double* part, double* hpass, double* hcol, int accumulate, cudaStream_t st);
 void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,
                           cudaStream_t st);
-void launch_givens(const double* hcol, const double* hn2, int k, double* H, int ldh, double* cs,
-                   double* sn, double* gv, double beta, double* resid, double* inv_hn,
-                   cudaStream_t st);
-void launch_scale_to(const double* w, const double* s, double* out, int64_t n, cudaStream_t st);
 void launch_normalize_start(const double* x, const double* nrm2, double* out, int64_t n,
                             cudaStream_t st);
 void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double* y,

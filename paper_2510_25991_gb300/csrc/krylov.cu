@@ -114,45 +114,9 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
   if (lane == 0) y[s.if_off + src] = konly ? acc : x[s.if_off + src] - acc;
 }
 
-// ---- Arnoldi pieces ------------------------------------------------------------------------
-// part[i * nchunk + chunk] = sum over chunk of V[i] . w      grid = (nchunk, k)
-__global__ void k_gs_dots(const double* __restrict__ V, const double* __restrict__ w, int64_t n,
-                          int64_t chunk, double* __restrict__ part) {
-  const int i = blockIdx.y;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
-  const int64_t hi = min(n, lo + chunk);
-  const double* v = V + (int64_t)i * n;
-  double acc = 0.0;
-  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) acc += v[e] * w[e];
-  __shared__ double red[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    t = warp_sum(t);
-    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = t;
-  }
-}
-
-// hpass[i] = sum_c part[i][c]; hcol[i] = (accumulate ? hcol[i] : 0) + hpass[i].  warp per i.
-__global__ void k_gs_reduce(const double* __restrict__ part, int nchunk, int k,
-                            double* __restrict__ hpass, double* __restrict__ hcol, int accumulate) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= k) return;
-  double acc = 0.0;
-  for (int c = lane; c < nchunk; c += 32) acc += part[(int64_t)i * nchunk + c];
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    hpass[i] = acc;
-    hcol[i] = (accumulate ? hcol[i] : 0.0) + acc;
-  }
-}
-
-// w -= sum_{i<k} h[i] V[i]   (or x = sum_{i<k} h[i] V[i] when assign = 1)
-__global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w,
-                            const double* __restrict__ h, int k, int64_t n, int assign) {
+// GMRES solution from the Krylov basis: x = sum_{i<k} y[i] V[i]
+__global__ void k_combine_basis(const double* __restrict__ V, double* __restrict__ x,
+                                const double* __restrict__ h, int k, int64_t n) {
   extern __shared__ double sh[];
   for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = h[i];
   __syncthreads();
@@ -165,46 +129,8 @@ __global__ void k_gs_update(const double* __restrict__ V, double* __restrict__ w
              sh[i + 2] * V[(int64_t)(i + 2) * n + e] + sh[i + 3] * V[(int64_t)(i + 3) * n + e];
     }
     for (; i < k; ++i) acc += sh[i] * V[(int64_t)i * n + e];
-    w[e] = assign ? acc : w[e] - acc;
+    x[e] = acc;
   }
-}
-
-// Givens step for column j = k-1 (k basis vectors).  Single thread.
-// H: column-major upper triangle (ld = ldh); gv: rotated rhs; resid[j] = |g_{j+1}| / beta.
-__global__ void k_givens(const double* __restrict__ hcol, const double* __restrict__ hn2, int k,
-                         double* __restrict__ H, int ldh, double* __restrict__ cs,
-                         double* __restrict__ sn, double* __restrict__ gv, double beta,
-                         double* __restrict__ resid, double* __restrict__ inv_hn) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int j = k - 1;
-  double* col = H + (int64_t)j * ldh;
-  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
-  double sub = sqrt(fmax(hn2[0], 0.0));
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double a = col[j], b = sub;
-  const double den = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (den > 0.0) { c = a / den; s = b / den; }
-  cs[j] = c;
-  sn[j] = s;
-  col[j] = den;
-  gv[j + 1] = -s * gv[j];
-  gv[j] = c * gv[j];
-  resid[j] = fabs(gv[j + 1]) / beta;
-  inv_hn[0] = sub > 0.0 ? 1.0 / sub : 0.0;
-}
-
-// V[k] = w * inv_hn
-__global__ void k_scale_to(const double* __restrict__ w, const double* __restrict__ s,
-                           double* __restrict__ out, int64_t n) {
-  const double a = s[0];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = a * w[e];
 }
 
 // out = x / sqrt(nrm2[0]) and gv[0] = sqrt(nrm2[0])  (start of Arnoldi)
@@ -580,34 +506,10 @@ template void launch_apply_dense<double>(const SlabDesc*, const ProbDesc*, int, 
                                          const double*, const double*, double*, int,
                                          cudaStream_t, const int*, int64_t);
 
-void launch_gs_pass(const double* V, const double* w_in, double* w, int64_t n, int k,
-                    int nchunk, double* part, double* hpass, double* hcol, int accumulate,
-                    cudaStream_t st) {
-  const int64_t chunk = (n + nchunk - 1) / nchunk;
-  note_launch();
-  k_gs_dots<<<dim3(nchunk, k), 256, 0, st>>>(V, w_in, n, chunk, part);
-  note_launch();
-  k_gs_reduce<<<(k + 7) / 8, 256, 0, st>>>(part, nchunk, k, hpass, hcol, accumulate);
-  note_launch();
-  k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, w, hpass, k, n, 0);
-}
-
 void launch_combine_basis(const double* V, const double* y, int k, int64_t n, double* x,
                           cudaStream_t st) {
   note_launch();
-  k_gs_update<<<1024, 256, k * sizeof(double), st>>>(V, x, y, k, n, 1);
-}
-
-void launch_givens(const double* hcol, const double* hn2, int k, double* H, int ldh, double* cs,
-                   double* sn, double* gv, double beta, double* resid, double* inv_hn,
-                   cudaStream_t st) {
-  note_launch();
-  k_givens<<<1, 32, 0, st>>>(hcol, hn2, k, H, ldh, cs, sn, gv, beta, resid, inv_hn);
-}
-
-void launch_scale_to(const double* w, const double* s, double* out, int64_t n, cudaStream_t st) {
-  note_launch();
-  k_scale_to<<<1024, 256, 0, st>>>(w, s, out, n);
+  k_combine_basis<<<1024, 256, k * sizeof(double), st>>>(V, x, y, k, n);
 }
 
 void launch_normalize_start(const double* x, const double* nrm2, double* out, int64_t n,
