@@ -48,7 +48,6 @@ void launch_iface_dirichlet_T(const SlabDesc* d_slabs, const ProbDesc* d_probs, 
                               const T* pack, const T* loc, double* out, cudaStream_t st);
 void launch_dot(const double* x, const double* y, int64_t n, double* part, int nblk, double* out,
                 cudaStream_t st);
-void launch_sum_partials(const double* part, int np, double* out, cudaStream_t st);
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
 
 // One CTA of the pivot sweeps (factor.cu): rows start..last of one slab and direction, inverses

@@ -440,11 +440,6 @@ void launch_dot(const double* x, const double* y, int64_t n, double* part, int n
   k_sum_partials<<<1, 256, 0, st>>>(part, nblk, out);
 }
 
-void launch_sum_partials(const double* part, int np, double* out, cudaStream_t st) {
-  note_launch();
-  k_sum_partials<<<1, 256, 0, st>>>(part, np, out);
-}
-
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {
   note_launch();
   k_axpy<<<1024, 256, 0, st>>>(n, a, x, y);
