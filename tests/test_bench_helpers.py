@@ -1,0 +1,33 @@
+"""Host-side helpers of bench.py: the DRAM-traffic table it reads from the profiles folder, and
+the count of MMA flops the tensor-core transfer build issues."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_table_has_the_benchmarked_kernels():
+    t = _bench()._traffic_table()
+    assert t[("k_sbuild_tc", 2048, 32)] > 0
+    # the interface apply reads every stored HODLR entry about once: ~0.17 GB per launch
+    assert 0.1e9 < t[("hodlr_apply", 2048, 32)] < 0.3e9
+
+
+def test_tensor_core_flop_count():
+    f = _bench()._tc_executed_flops
+    # a single CTA with one partly filled tile: 64 sources on 64 blocks (n = 65), MB = 32
+    nb, MB = 64, 32
+    up = nb - 1      # upward sweep from block 64: 63 steps
+    down = nb - 1    # downward sweep from block 1: 63 steps
+    assert f(1, nb, MB) == (up + down) * 3 * 2 * 128 * MB * MB
+    # every source visits every other block once: the executed work covers the algorithmic
+    # (m x m) x (m x 1) products at least three times over (3xTF32), on padded blocks
+    nds, nb, m = 63, 2047, 63
+    assert f(nds, nb, 64) >= 3 * nds * nb * (nb - 1) * 2.0 * m * m
