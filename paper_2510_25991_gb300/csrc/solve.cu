@@ -139,12 +139,20 @@ __global__ void __launch_bounds__(128) k_solve_combine(const SlabDesc* __restric
   const T* Gk = G + s.fac_off + (int64_t)(k - 1) * M * M;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (mode == 0) {
-    if (!transpose) {
-      for (int r = warp; r < M; r += 4) {
-        T part = T(0);
-        for (int c = lane; c < M; c += 32) part += Gk[r * M + c] * sv[c];
-        part = warp_sum(part);
-        if (lane == 0) x[o + r] = part;
+    if (!transpose) {  // a warp takes 4 consecutive rows per round (M/8 loads in flight per lane)
+      for (int r0 = warp * 4; r0 < M; r0 += 16) {
+        T p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          p[u] = T(0);
+#pragma unroll
+          for (int c = lane; c < M; c += 32) p[u] += Gk[(r0 + u) * M + c] * sv[c];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T v = warp_sum(p[u]);
+          if (lane == 0) x[o + r0 + u] = v;
+        }
       }
     } else {
       for (int r = threadIdx.x; r < M; r += blockDim.x) {
