@@ -151,7 +151,8 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 
 /* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.
  * (equilib1)), GMRES on (I - K) u_Gamma = fhat, volume reconstruction, then FP64 residual
- * refinement u += DD(b - A u) until ||correction|| <= refine_tol ||u||.
+ * refinement u += DD(b - A u) until the error bound rho/(1-rho) ||correction|| (rho: observed
+ * contraction, capped at 1/2) is <= refine_tol ||u||; the bound is info->est_rel_error.
  * f: interior load; g: nodal Dirichlet data (only boundary nodes are read); u: interior
  * output.  info may be NULL.  Errors: STATE, INVALID_ARG, NOT_CONVERGED (u still written). */
 ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,
@@ -174,15 +175,20 @@ ddst_status ddst_solve_adjoint_batch(ddst_ctx* ctx, const double* const* dL_du,
                                      double* const* dL_df, double* const* dL_dg,
                                      double* const* dL_da, ddst_info* info);
 
-/* Interface traces u_Gamma of problem prob from the last solve (N_ds * n_Gamma values). */
+/* Interface traces u_Gamma of problem prob from the last solve (N_ds * n_Gamma values, host or
+ * device array).  Errors: INVALID_ARG (bad prob or NULL), STATE (no solve yet), CUDA. */
 ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG);
 
 /* Copies S_{j,j-1} (side = -1) or S_{j,j+1} (side = +1) of problem prob, slab j (1-based),
- * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR if compressed). */
+ * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR if compressed) into
+ * a host or device array.  Errors: INVALID_ARG (bad prob, j or side; no such block at the
+ * ends), STATE (transfer operators not built), CUDA. */
 ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* out);
 
 /* y = (I - K) x (transpose = 0) or y = (I - K)^T x (transpose = 1) for problem prob with the
- * current (dense or HODLR) operators; x and y hold N_ds * n_Gamma values. */
+ * current (dense or HODLR) operators (Sec. 2.2, Eq. (modelS)); x and y hold N_ds * n_Gamma
+ * values, host or device arrays; returns after y is written (synchronizes the context stream).
+ * Errors: INVALID_ARG, STATE (transfer operators not built), CUDA. */
 ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, double* y,
                                  int transpose);
 
@@ -194,7 +200,9 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
  * built), CUDA. */
 ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms);
 
-/* Sizes of problem prob: n_ds, n_gamma and the total interface length (any may be NULL). */
+/* Sizes of problem prob: number of double slabs n_ds, interface length n_gamma, and the
+ * largest HODLR rank of the context (0 while dense).  Any output may be NULL.
+ * Errors: INVALID_ARG (NULL ctx or bad prob). */
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
 
