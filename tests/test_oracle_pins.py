@@ -219,6 +219,91 @@ def test_p7_printed_poisson_table_first_row():
     assert abs(its - iters) <= 0.1 * iters + 1
 
 
+def _separable_poisson(dim, n, w):
+    """Closed form of I - K for constant-coefficient Poisson, by separation of variables.
+
+    The discrete sine modes of the interface directions diagonalize every S_{j,j+-1} at once.
+    Mode k has the 1D Dirichlet eigenvalue mu_k = 4 sin^2(pi k / 2n) per direction, and the
+    x-direction recurrence -u_{i-1} + (2 + mu) u_i - u_{i+1} = 0 on the 2w - 1 interior
+    columns of a double slab.  Its solution, 1 on one outer column and 0 on the other, is
+    sinh((2w - i) theta) / sinh(2 w theta) with cosh theta = 1 + mu / 2.  At the central
+    column this is s = 1 / (2 cosh(w theta)).  Per mode, I - K is therefore tridiag(-s, 1, -s)
+    over the N_ds interfaces, with eigenvalues 1 - 2 s cos(pi l / (N_ds + 1)).
+    Returns (s per mode, N_ds).
+    """
+    k = np.arange(1, n)
+    mu1 = 4.0 * np.sin(np.pi * k / (2 * n)) ** 2
+    mu = mu1 if dim == 2 else (mu1[:, None] + mu1[None, :]).ravel()
+    theta = np.arccosh(1.0 + mu / 2.0)
+    return 1.0 / (2.0 * np.cosh(w * theta)), n // w - 1
+
+
+def _separable_eigs(dim, n, w):
+    s, nds = _separable_poisson(dim, n, w)
+    c = np.cos(np.pi * np.arange(1, nds + 1) / (nds + 1))
+    return np.sort((1.0 - 2.0 * s[:, None] * c[None, :]).ravel())
+
+
+@pytest.mark.parametrize("dim,n,w", [(2, 24, 4), (2, 30, 5), (3, 8, 2), (3, 12, 3), (3, 12, 2)])
+def test_p5_constant_coefficient_spectrum_closed_form(dim, n, w):
+    """P5: the oracle's I - K for Poisson has exactly the separable closed-form spectrum."""
+    name = "poisson2d" if dim == 2 else "vardiff3d"
+    prob = I.make_problem(name, n=n, w=w, **({} if dim == 2 else dict(const_a=True)))
+    prob["b"] = (0.0,) * dim
+    A, _ = O.assemble(prob)
+    geo = O.slab_geometry(dim, n, w)
+    Sp, Sn = O.transfer_blocks(A, geo, O.factor_local(A, geo))
+    M = O.interface_matrix(Sp, Sn, geo.ngamma)
+    assert M.shape[0] == (n // w - 1) * (n - 1) ** (dim - 1)
+    ev = np.linalg.eigvals(M)
+    assert np.abs(ev.imag).max() <= 1e-12
+    assert np.abs(np.sort(ev.real) - _separable_eigs(dim, n, w)).max() <= 1e-12
+
+
+def _separable_gmres_iterations(n, w, seed):
+    """Oracle GMRES on the mode-diagonalized I - K (unitarily similar to the full operator).
+
+    Applying the orthonormal sine transform on every interface is a unitary similarity, so
+    GMRES from x0 = 0 takes the same steps on the transformed system; a Gaussian right-hand
+    side stays Gaussian under it.
+    """
+    s, nds = _separable_poisson(3, n, w)
+
+    def matvec(v):
+        V = v.reshape(nds, s.size)
+        Y = V.copy()
+        Y[1:] -= s * V[:-1]
+        Y[:-1] -= s * V[1:]
+        return Y.ravel()
+
+    rhs = np.random.default_rng(seed).standard_normal(nds * s.size)
+    _, its, hist = O.gmres(matvec, rhs, tol=1e-8, maxit=100)
+    assert hist[-1] <= 1e-8
+    return its
+
+
+@pytest.mark.parametrize("table,col_n", [("fd_poisson_fixedH.txt", "N"),
+                                         ("fd_shrinkingH.txt", "invH")])
+def test_p7_printed_poisson_tables_closed_form(table, col_n):
+    """P7: both printed 3D Poisson tables of Sec. 5.2 at their own grid sizes.
+
+    kappa_2(S_H) from the closed form (pinned to the oracle above) within 0.01 of each printed
+    value, and oracle GMRES iterations within 10% + 1 of the printed S_H counts.
+    """
+    for row in _golden(table):
+        if col_n == "N":
+            n = round(row[0] ** (1 / 3))
+            w = n // 8
+        else:
+            n = 64
+            w = n // round(row[0])
+        iters, kappa = row[1], row[2]
+        ev = _separable_eigs(3, n, w)
+        assert abs(ev.max() / ev.min() - kappa) <= 0.01, (n, w)
+        its = _separable_gmres_iterations(n, w, seed=n + w)
+        assert abs(its - iters) <= 0.1 * iters + 1, (n, w, its)
+
+
 def test_gmres_finite_termination_and_residual():
     """GMRES on a diagonalizable matrix with k distinct eigenvalues stops after k steps."""
     rng = np.random.default_rng(1)
