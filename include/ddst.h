@@ -202,12 +202,13 @@ ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms);
 
 /* Sizes of problem prob: number of double slabs n_ds, interface length n_gamma, and the
  * largest HODLR rank of the context (0 while dense).  Any output may be NULL.
- * Errors: INVALID_ARG (NULL ctx or bad prob). */
+ * Errors: INVALID_ARG (NULL ctx or bad prob; message via ddst_last_error(NULL), since ctx is
+ * const). */
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
 
 /* Arithmetic the context was set up with: DDST_FP64 or DDST_MIXED (what DDST_AUTO chose).
- * Errors: INVALID_ARG for a NULL argument. */
+ * Errors: INVALID_ARG for a NULL argument (message via ddst_last_error(NULL)). */
 ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision);
 
 /* Allocation-free FP64 residual of the finite-difference system.  The paper has no

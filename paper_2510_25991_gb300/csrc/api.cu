@@ -1003,7 +1003,7 @@ ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeff
 }
 
 ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision) {
-  if (!ctx || !precision) return DDST_ERR_INVALID_ARG;
+  if (!ctx || !precision) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx or precision is NULL");
   *precision = ctx->prec;
   return DDST_OK;
 }
@@ -1175,7 +1175,9 @@ ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms) {
 }
 
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma, int* max_rank) {
-  if (!ctx || prob < 0 || prob >= ctx->nprob) return DDST_ERR_INVALID_ARG;
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (prob < 0 || prob >= ctx->nprob)
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "prob %d outside [0, %d)", prob, ctx->nprob);
   const ProbDesc& P = ctx->probs[prob];
   if (n_ds) *n_ds = P.nds;
   if (n_gamma) *n_gamma = P.ng;

@@ -177,7 +177,8 @@ def ddst_time_apply(ctx, transpose=False, reps=50):
 def ddst_query(ctx, prob=0):
     lib = L.load()
     nds, ng, mr = C.c_int(), C.c_int64(), C.c_int()
-    _check(lib, ctx, lib.ddst_query(ctx, prob, C.byref(nds), C.byref(ng), C.byref(mr)))
+    # the context is const here: its errors are reported in the process-wide message
+    _check(lib, None, lib.ddst_query(ctx, prob, C.byref(nds), C.byref(ng), C.byref(mr)))
     return nds.value, ng.value, mr.value
 
 
@@ -185,7 +186,7 @@ def ddst_get_precision(ctx):
     """"fp64" or "mixed": the arithmetic the context was set up with (what "auto" chose)."""
     lib = L.load()
     p = C.c_int()
-    _check(lib, ctx, lib.ddst_get_precision(ctx, C.byref(p)))
+    _check(lib, None, lib.ddst_get_precision(ctx, C.byref(p)))
     return "fp64" if p.value == L.DDST_FP64 else "mixed"
 
 

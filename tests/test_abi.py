@@ -45,3 +45,56 @@ def test_options_default_without_gpu():
     o = D.ddst_options_default()
     assert o.precision == 1 and o.k_max == 64 and o.oversample == 10 and o.leaf_size == 128
     assert o.gmres_tol == 0.0 and o.refine_max >= 1  # automatic inner tolerance
+
+
+def _square(n):
+    import numpy as np
+    return np.ones((n + 1, n + 1))
+
+
+@pytest.mark.parametrize("problem,message", [
+    (dict(dim=2, n=10, w=3), "n % w == 0"),          # slab width does not divide n
+    (dict(dim=2, n=10, w=10), "n/w >= 2"),           # a single slab has no interface
+    (dict(dim=4, n=10, w=5), "dim must be 2 or 3"),
+    (dict(dim=2, n=2048, w=128), "exceeds 128"),     # block 2w - 1 = 255 above the FP32 limit
+])
+def test_setup_rejects_bad_problems_without_gpu(problem, message):
+    """Argument checks run on the host before any device work and leave a message."""
+    from paper_2510_25991_gb300 import ddst as D
+    problem = dict(problem, a=_square(problem["n"]))
+    with pytest.raises(D.DDSTError) as e:
+        D.ddst_setup_batch([problem])
+    assert e.value.name == "INVALID_ARG" and message in str(e.value)
+
+
+def test_setup_rejects_bad_options_and_lists_without_gpu():
+    from paper_2510_25991_gb300 import ddst as D
+    ok = dict(dim=2, n=16, w=4, a=_square(16))
+    with pytest.raises(D.DDSTError, match="precision must be"):
+        D.ddst_setup_batch([ok], D.ddst_options_default(precision=7))
+    with pytest.raises(D.DDSTError, match="block size"):  # FP64 kernels stop at 64-row blocks
+        D.ddst_setup_batch([dict(dim=2, n=80, w=40, a=_square(80))],
+                           D.ddst_options_default(precision=0))
+    with pytest.raises(D.DDSTError, match="a is NULL"):
+        D.ddst_setup_batch([dict(ok, a=None)])
+    with pytest.raises(D.DDSTError, match="bad problem list"):
+        D.ddst_setup_batch([])
+
+
+def test_null_context_errors_without_gpu():
+    """Every entry point answers a NULL context with INVALID_ARG and a message."""
+    import numpy as np
+
+    from paper_2510_25991_gb300 import ddst as D
+    x = np.zeros(4)
+    calls = [lambda: D.ddst_build_transfer(None), lambda: D.ddst_compress(None, 1e-8),
+             lambda: D.ddst_solve(None, x, x, x), lambda: D.ddst_solve_adjoint(None, x),
+             lambda: D.ddst_interface_trace(None, 0, x), lambda: D.ddst_query(None),
+             lambda: D.ddst_get_precision(None)]
+    for call in calls:
+        # leave a different message first, so a stale one cannot pass
+        with pytest.raises(D.DDSTError, match="dim must be 2 or 3"):
+            D.ddst_setup_batch([dict(dim=4, n=8, w=4, a=_square(8))])
+        with pytest.raises(D.DDSTError) as e:
+            call()
+        assert e.value.name == "INVALID_ARG" and "NULL" in str(e.value)
