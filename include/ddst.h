@@ -238,7 +238,10 @@ ddst_status ddst_residual_noalloc(const ddst_grid* grid, const ddst_coeffs* coef
  * diagnostic for benchmarks: the difference across a timed region counts its launches). */
 int64_t ddst_kernel_launches(void);
 
-/* Message of the last error on ctx (or of the last failed ddst_setup when ctx is NULL). */
+/* Message of the last error on ctx.  With ctx NULL: the last error the calling thread got
+ * without a context (a failed ddst_setup, a NULL context, ddst_query, ddst_get_precision,
+ * ddst_residual_noalloc); the message is kept per thread.  The string stays valid until the
+ * next error on the same context (or thread) or ddst_destroy. */
 const char* ddst_last_error(const ddst_ctx* ctx);
 
 /* Releases the context and all its device memory.  NULL is ignored. */

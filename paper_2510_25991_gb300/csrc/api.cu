@@ -23,7 +23,9 @@
 using namespace ddst;
 
 namespace {
-std::string g_setup_error;
+// Message of the last error raised without a context (ddst_last_error(NULL)); one per thread,
+// so concurrent setups on different threads do not overwrite each other's message.
+thread_local std::string g_setup_error;
 }  // namespace
 
 namespace ddst {

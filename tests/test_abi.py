@@ -98,3 +98,26 @@ def test_null_context_errors_without_gpu():
         with pytest.raises(D.DDSTError) as e:
             call()
         assert e.value.name == "INVALID_ARG" and "NULL" in str(e.value)
+
+
+def test_context_free_error_message_is_per_thread():
+    """ddst_last_error(NULL) holds the calling thread's own last message."""
+    import threading
+
+    from paper_2510_25991_gb300 import ddst as D
+    from paper_2510_25991_gb300 import _lib as L
+    lib = L.load()
+    with pytest.raises(D.DDSTError, match="dim must be 2 or 3"):
+        D.ddst_setup_batch([dict(dim=4, n=8, w=4, a=_square(8))])
+    seen = {}
+
+    def other():
+        with pytest.raises(D.DDSTError):
+            D.ddst_setup_batch([dict(dim=2, n=10, w=3, a=_square(10))])
+        seen["other"] = lib.ddst_last_error(None).decode()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert "n % w == 0" in seen["other"]
+    assert "dim must be 2 or 3" in lib.ddst_last_error(None).decode()
