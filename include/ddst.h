@@ -31,6 +31,10 @@
  *    DDST_ERR_STATE.
  *  - Device memory of a context is allocated by the library (cudaMalloc) and released by
  *    ddst_destroy.
+ *  - Threads and devices: the library holds process-wide launch settings (kernel shared-memory
+ *    limits, set on first use), so calls from different threads must be serialized by the
+ *    caller, contexts included.  A process drives one GPU: a context runs on the device that
+ *    is current at ddst_setup, and several GPUs are used with one process per GPU.
  */
 #ifndef DDST_H
 #define DDST_H
