@@ -31,10 +31,13 @@
  *    DDST_ERR_STATE.
  *  - Device memory of a context is allocated by the library (cudaMalloc) and released by
  *    ddst_destroy.
- *  - Threads and devices: the library holds process-wide launch settings (kernel shared-memory
- *    limits, set on first use), so calls from different threads must be serialized by the
- *    caller, contexts included.  A process drives one GPU: a context runs on the device that
- *    is current at ddst_setup, and several GPUs are used with one process per GPU.
+ *  - Threads: calls on one context must not overlap; different contexts may be used from
+ *    different threads at the same time (kernel shared-memory limits are raised under a lock,
+ *    the context-free error message is per thread).  ddst_residual_noalloc calls share one
+ *    scratch array and must be serialized by the caller.
+ *  - Devices: a context belongs to the device that is current at ddst_setup, and that device
+ *    must be current for every later call on it.  Several GPUs are driven with one process
+ *    per GPU.
  */
 #ifndef DDST_H
 #define DDST_H

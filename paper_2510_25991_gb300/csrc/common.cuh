@@ -22,6 +22,11 @@ namespace ddst {
 // Process-wide count of kernels launched by the library (reported by ddst_kernel_launches).
 std::atomic<long long>& launch_counter();
 inline void note_launch(int n = 1) { launch_counter().fetch_add(n, std::memory_order_relaxed); }
+// Raises the dynamic shared-memory limit of kernel `func` on the current device to at least
+// `bytes` (never lowers it; nothing to do up to the 48 KiB default).  Thread-safe: one limit
+// per (device, kernel), kept under a lock, so a smaller request on another thread cannot undo
+// a larger one.  Returns the error of the attribute call (cudaSuccess when none was needed).
+cudaError_t raise_smem_limit(const void* func, size_t bytes);
 
 // Stencil pack fields, stored per (slab, block) as [field][M] in the working precision.
 enum PackField { PK_DIAG = 0, PK_WEST = 1, PK_EAST = 2, PK_SOUTH = 3, PK_NORTH = 4,

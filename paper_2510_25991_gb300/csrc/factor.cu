@@ -384,12 +384,8 @@ void launch_factor_M(const SlabDesc* d_slabs, const FacChunk* d_chunks, int nchu
   using Gc = BGJ<T, M>;
   const size_t sm_f = factor_smem<T, M>();
   const size_t sm_c = Gc::smem_elems * sizeof(T) + (PK_NFIELDS * M + 3 * M) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_factor<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_f);
-    cudaFuncSetAttribute(k_center<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
-    attr = true;
-  }
+  raise_smem_limit(reinterpret_cast<const void*>(&k_factor<T, M>), sm_f);
+  raise_smem_limit(reinterpret_cast<const void*>(&k_center<T, M>), sm_c);
   if (phase == 0) {  // pivot sweeps + convergence check of warm-started chunks
     if (nchunks == 0) return;
     note_launch();

@@ -833,8 +833,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     int64_t maxp = 0;
     for (auto& d : hd) maxp = std::max(maxp, d.p);
     const size_t smem = sizeof(T) * maxp;
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(k_range_cgs2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit(reinterpret_cast<const void*>(&k_range_cgs2<T>), smem);
     note_launch();
     k_range_cgs2<T><<<nblk, 512, smem, st>>>(d_hd, (T*)H.UV, d_nrm, hp.tol, kmax,
                                              std::max(1, hp.oversample), d_rank);

@@ -483,11 +483,7 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
   transpose &= 1;
   if (!transpose) {
     const size_t smem = 2 * max_ng * sizeof(T);
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-      cudaFuncSetAttribute(k_apply_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = smem;
-    }
+    raise_smem_limit(reinterpret_cast<const void*>(&k_apply_dense<T>), smem);
     note_launch();
     k_apply_dense<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smem, st>>>(
         d_slabs, d_probs, S, x, y, kdev, kstride, konly);

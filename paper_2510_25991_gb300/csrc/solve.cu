@@ -179,12 +179,7 @@ static void run_solve(const SlabDesc* d_slabs, const int* d_ids, int nids, int m
                       const T* pack, const T* b, T* bf, T* bb, T* x, double* iface,
                       int transpose, int mode, DevStatus* st, cudaStream_t s) {
   const size_t smem = (size_t)NST * (M * M + 2 * M) * sizeof(T) + 5 * M * sizeof(T) + NST * 8;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_solve_sweep<T, M, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
+  raise_smem_limit(reinterpret_cast<const void*>(&k_solve_sweep<T, M, NST>), smem);
   // A^{-1} sweeps multiply by F, B: pass their transposes (thread-per-row form); A^{-T} sweeps
   // multiply by F^T, B^T: pass F, B.
   const T* Wf = transpose ? F : Ft;

@@ -215,12 +215,7 @@ static void run_sbuild(const SlabDesc* d_slabs, const TileDesc* d_tiles, int nti
                        const T* B, const T* G, const T* pack, T* S, DevStatus* st,
                        cudaStream_t s) {
   using C = SweepCfg<T, M, R, NST>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_sbuild<T, M, R, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)C::SMEM);
-    attr = true;
-  }
+  raise_smem_limit(reinterpret_cast<const void*>(&k_sbuild<T, M, R, NST>), C::SMEM);
   note_launch();
   k_sbuild<T, M, R, NST><<<ntiles, C::THREADS, C::SMEM, s>>>(d_slabs, d_tiles, F, B, G, pack, S, st);
 }

@@ -386,11 +386,7 @@ static void run_tc(const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                    const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                    const float* G, const float* pack, float* S, DevStatus* st, cudaStream_t s) {
   using C = TcCfg<MB>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_sbuild_tc<MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    attr = true;
-  }
+  raise_smem_limit(reinterpret_cast<const void*>(&k_sbuild_tc<MB>), C::SMEM);
   note_launch();
   k_sbuild_tc<MB><<<ntiles, C::THREADS, C::SMEM, s>>>(d_slabs, d_tiles, Fhi, Flo, Bhi, Blo, G,
                                                       pack, S, st);
