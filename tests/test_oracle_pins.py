@@ -16,7 +16,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def _manufactured(dim, n, w, bconv, c0):
-    """Linear ``a``, constant ``b`` and ``c``, quadratic ``u``: the stencil is exact."""
+    """Linear ``a``, constant ``b``, variable ``c`` and quadratic ``u``: the stencil is exact."""
     X = I.node_coords(dim, n)
     alpha = [0.5, 0.25, -0.3][:dim]
     a = 1.0 + sum(alpha[d] * X[d] for d in range(dim))
@@ -33,9 +33,12 @@ def _manufactured(dim, n, w, bconv, c0):
     # -div(a grad u) = -(grad a . grad u + a lap u)
     lap = sum(2 * q[d] for d in range(dim))
     f = -(sum(alpha[d] * grad[d] for d in range(dim)) + a * lap)
-    f = f + sum(bconv[d] * grad[d] for d in range(dim)) + c0 * u
+    # reaction varies along every axis, so a misplaced node index of c changes the answer
+    beta = [0.5, -0.25, 0.4][:dim]
+    c = c0 * (1.0 + sum(beta[d] * X[d] for d in range(dim)) + 0.3 * X[0] * X[1])
+    f = f + sum(bconv[d] * grad[d] for d in range(dim)) + c * u
     inner = tuple(slice(1, n) for _ in range(dim))
-    prob = dict(dim=dim, n=n, w=w, a=a, b=tuple(bconv), c=np.full_like(a, c0), f=f[inner], g=u)
+    prob = dict(dim=dim, n=n, w=w, a=a, b=tuple(bconv), c=c, f=f[inner], g=u)
     return prob, u[inner].ravel()
 
 
