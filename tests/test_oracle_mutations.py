@@ -1,0 +1,75 @@
+"""Planted mistakes in the oracle: every one must make at least one pin fail.
+
+Each case replaces one line of ``oracle/ddst_oracle.py`` (in a copy, on the CPU) by a
+plausible error -- a dropped term, a wrong sign, index or scale, a transposed or swapped
+operand -- and runs ``tests/test_oracle_pins.py`` against the copy.  The run must fail.
+
+One variant is left out on purpose: recording only the first Gram-Schmidt pass's
+coefficients in the Hessenberg column while still orthogonalizing twice.  The second-pass
+coefficients are of the order of rounding, so that variant gives the same iterates to
+rounding and no pin can tell it apart; skipping the second pass altogether is included.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle", "ddst_oracle.py")
+
+MUTATIONS = [
+ ("O1 face mean dropped (a_p instead of (a_p+a_q)/2)", "af = 0.5 * (ap + aq)\n            coef", "af = ap\n            coef"),
+ ("O1 convection sign", "coef = -af / h ** 2 + s * bconv[d]", "coef = -af / h ** 2 - s * bconv[d]"),
+ ("O1 convection scale 1/h instead of 1/(2h)", "s * bconv[d] / (2.0 * h)", "s * bconv[d] / h"),
+ ("O1 boundary data sign", "rhs[P[bnd]] -= coef[bnd]", "rhs[P[bnd]] += coef[bnd]"),
+ ("O1 reaction dropped", "diag += c[_interior(dim, n)].ravel()", "diag += 0.0"),
+ ("O1 diagonal from a_p instead of face mean", "diag += af / h ** 2", "diag += ap / h ** 2"),
+ ("geometry: central plane off by one", "geo.C.append((j * w - lo) * rest", "geo.C.append((j * w - lo + 1) * rest"),
+ ("geometry: previous interface plane off by one", "plane((j - 1) * w) if j >= 2", "plane((j - 1) * w + 1) if j >= 2"),
+ ("geometry: double slab one plane short", "lo, hi = (j - 1) * w + 1, (j + 1) * w - 1", "lo, hi = (j - 1) * w + 1, (j + 1) * w - 2"),
+ ("O3 sign of S", "out.append(-lu.solve(rhs)[C, :])", "out.append(lu.solve(rhs)[C, :])"),
+ ("O3 S_{j,j-1} and S_{j,j+1} swapped", "Sp.append(out[0]); Sn.append(out[1])", "Sp.append(out[1]); Sn.append(out[0])"),
+ ("O3 S transposed", "out.append(-lu.solve(rhs)[C, :])", "out.append(-lu.solve(rhs)[C, :].T)"),
+ ("O3 fhat from the neighbouring slab's factor", "return [facs[j].solve(np.asarray(b)[geo.I[j]])[geo.C[j]]", "return [facs[max(j - 1, 0)].solve(np.asarray(b)[geo.I[j]])[geo.C[j]]"),
+ ("O4 interface matrix sign", "M[j * m:(j + 1) * m, (j - 1) * m:j * m] = -Sp[j]", "M[j * m:(j + 1) * m, (j - 1) * m:j * m] = Sp[j]"),
+ ("O4 interface matrix block transposed", "M[j * m:(j + 1) * m, (j + 1) * m:(j + 2) * m] = -Sn[j]", "M[j * m:(j + 1) * m, (j + 1) * m:(j + 2) * m] = -Sn[j].T"),
+ ("O4 apply with transposed S", "Y[j] -= Sp[j] @ X[j - 1]", "Y[j] -= Sp[j].T @ X[j - 1]"),
+ ("O4 block Thomas back-substitution sign", "u[j] = sla.solve(Dm[j], r[j] + Sn[j] @ u[j + 1])", "u[j] = sla.solve(Dm[j], r[j] - Sn[j] @ u[j + 1])"),
+ ("O4 GMRES single classical Gram-Schmidt pass", "        h2 = V[:k] @ wv\n        wv = wv - V[:k].T @ h2\n        hcol = h1 + h2\n", "        hcol = h1\n"),
+ ("O4 GMRES Givens sign", "gvec[k] = -sn[k - 1] * gvec[k - 1]", "gvec[k] = sn[k - 1] * gvec[k - 1]"),
+ ("O4 GMRES rotation of new column sign", "H[i + 1, k - 1] = -sn[i] * H[i, k - 1] + cs[i] * H[i + 1, k - 1]", "H[i + 1, k - 1] = sn[i] * H[i, k - 1] + cs[i] * H[i + 1, k - 1]"),
+ ("O5 Dirichlet data sign in reconstruction", "rhs -= A[I][:, geo.Jprev[j]] @ U[j - 1]", "rhs += A[I][:, geo.Jprev[j]] @ U[j - 1]"),
+ ("O5 kept planes off by one", "keep = w * rest if j < nds - 1", "keep = (w - 1) * rest if j < nds - 1"),
+ ("O6 rank one short", "r = int(np.sum(s > thr))", "r = max(int(np.sum(s > thr)) - 1, 0)"),
+ ("O6 lower block taken from the upper one", "for (r0, r1, c0, c1) in ((lo1, hi1, lo2, hi2), (lo2, hi2, lo1, hi1)):", "for (r0, r1, c0, c1) in ((lo1, hi1, lo2, hi2), (lo1, hi1, lo2, hi2)):"),
+ ("O6 tree node boundary off by one", "return (t * ng) >> level, ((t + 1) * ng) >> level", "return (t * ng + 1) >> level, ((t + 1) * ng + 1) >> level"),
+ ("O6 apply reads the wrong half of x", "y[lo1:hi1] += U @ (V.T @ x[lo2:hi2])", "y[lo1:hi1] += U @ (V.T @ x[lo1:hi1])"),
+ ("O6 threshold relative to max|S| instead of ||S||_2", "norm2 = np.linalg.norm(S, 2)", "norm2 = np.abs(S).max()"),
+ ("O7 adjoint without transpose", "lu = spla.splu(sp.csc_matrix(sp.csr_matrix(A).T))", "lu = spla.splu(sp.csc_matrix(sp.csr_matrix(A)))"),
+ ("O7 dL/da face sign", "dface = -(lam_full[lo] - lam_full[hi])", "dface = (lam_full[lo] - lam_full[hi])"),
+ ("O7 dL/da face not split between nodes", "dLda[lo] += 0.5 * dface", "dLda[lo] += dface"),
+ ("O7 dL/dg convection sign (upper boundary)", "lam_full[lo] * (af / h ** 2 - bconv[d] / (2 * h))", "lam_full[lo] * (af / h ** 2 + bconv[d] / (2 * h))"),
+ ("O7 dL/dg convection sign (lower boundary)", "lam_full[hi] * (af / h ** 2 + bconv[d] / (2 * h))", "lam_full[hi] * (af / h ** 2 - bconv[d] / (2 * h))"),
+ ("O7 dL/da boundary u_q from 0 instead of g", "u_full = np.array(g, dtype=np.float64).copy()", "u_full = np.zeros_like(np.array(g, dtype=np.float64))"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.timeout(600)
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_oracle_mistake_fails_a_pin(tmp_path, name, old, new):
+    src = open(ORACLE).read()
+    assert src.count(old) == 1, f"mutation site not found: {name}"
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests")
+    shutil.copytree(os.path.join(ROOT, "ddst_inputs"), tmp_path / "ddst_inputs",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    (tmp_path / "oracle").mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), tmp_path / "oracle" / "__init__.py")
+    (tmp_path / "oracle" / "ddst_oracle.py").write_text(src.replace(old, new))
+    env = dict(os.environ, OMP_NUM_THREADS="4", OPENBLAS_NUM_THREADS="4", MKL_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True,
+                       timeout=600, env=env)
+    assert r.returncode == 1, f"{name}: no pin failed\n{r.stdout[-2000:]}"

@@ -325,6 +325,51 @@ def test_gmres_finite_termination_and_residual():
     assert true <= 2e-10 and abs(true - hist[-1]) <= 1e-12
 
 
+def test_gmres_orthogonal_basis_keeps_finite_termination():
+    """GMRES ends by step n on an n x n matrix when the Krylov basis stays orthogonal.
+
+    A normal matrix with 200 eigenvalues graded from 1 to 1e-6: in exact arithmetic GMRES
+    terminates by step 200.  Gram-Schmidt applied twice keeps the basis orthogonal to
+    rounding, so the computed run reaches 1e-10 by then with the true residual at the
+    estimate; a single classical pass loses orthogonality here and stalls near 1e-9.
+    """
+    rng = np.random.default_rng(0)
+    n = 200
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    M = Q @ np.diag(np.logspace(0, -6, n)) @ Q.T
+    rhs = rng.standard_normal(n)
+    x, its, hist = O.gmres(lambda v: M @ v, rhs, tol=1e-10, maxit=n)
+    assert its <= n and hist[-1] <= 1e-10
+    assert np.linalg.norm(M @ x - rhs) <= 1e-9 * np.linalg.norm(rhs)
+
+
+def test_p9_hodlr_ranks_exact_on_cs_decomposition():
+    """P9: level-1 ranks equal #{sigma_i > tol ||S||_2} where the sigma_i are known exactly.
+
+    Q = diag(U1, U2) [[C, -S], [S, C]] diag(V1, V2)^T with C = diag(cos theta), S = diag(sin
+    theta) and U1, U2, V1, V2 orthogonal is orthogonal, so ||Q||_2 = 1, and its off-diagonal
+    halves -U1 S V2^T and U2 S V1^T have singular values sin theta_i exactly (the CS
+    decomposition).
+    """
+    rng = np.random.default_rng(7)
+    h = 32
+    orth = [np.linalg.qr(rng.standard_normal((h, h)))[0] for _ in range(4)]
+    U1, U2, V1, V2 = orth
+    sig = 10.0 ** (-0.4 * np.arange(h) - 0.1)   # never within a factor 10^0.1 of a power of 10
+    cth = np.sqrt(1.0 - sig ** 2)
+    Z = np.zeros((h, h))
+    Q = (np.block([[U1, Z], [Z, U2]]) @ np.block([[np.diag(cth), -np.diag(sig)],
+                                                  [np.diag(sig), np.diag(cth)]])
+         @ np.block([[V1, Z], [Z, V2]]).T)
+    assert np.abs(Q @ Q.T - np.eye(2 * h)).max() <= 1e-13
+    for tol in (1e-2, 1e-5, 1e-8, 1e-11):
+        want = int(np.sum(sig > tol))
+        H = O.hodlr_compress(Q, tol=tol, leaf=8)
+        assert [U.shape[1] for (U, V) in H["levels"][0]] == [want, want]
+        H = O.hodlr_compress(Q, tol=tol, leaf=8, kmax=3)
+        assert [U.shape[1] for (U, V) in H["levels"][0]] == [min(want, 3)] * 2
+
+
 def test_p8_gradients_linear_directions_and_fd_in_a():
     """P8: adjoint gradients vs central differences (exact in f, g; 1e-5 relative in a)."""
     n, w = 16, 4
