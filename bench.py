@@ -78,9 +78,16 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        with open(self.path) as fh:
+            return self.summarize(fh)
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, maximum SM clock and the throttle reasons seen in the samples
+        (lines of the query above, CSV without header or units)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [t.strip() for t in line.split(",")]
             if len(f) < 9:
                 continue
@@ -115,7 +122,9 @@ def run_reference(args, ws, rank):
 
     for _ in range(args.warmup):
         step()
+    c0 = time.process_time()  # CPU time of all the process's threads
     ts = [step() for _ in range(args.steps)]
+    busy = (time.process_time() - c0) / sum(ts)
     v = dof * len(ts) / sum(ts)
     cores = os.cpu_count()
     sample = (f"oracle dd_solve (sparse LU per double slab, dense S, block-Thomas interface "
@@ -126,7 +135,8 @@ def run_reference(args, ws, rank):
             "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"convdiff2d n={n} w={w} (bounded CPU sample of the 2048^2 workload)"},
-            "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "DOF/s", "cores": cores, "threads_busy": round(busy, 1),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -164,10 +174,12 @@ def cpu_baseline(n=512):
     from oracle import ddst_oracle as O
     prob = I.make_problem("convdiff2d", n=n, w=32)
     O.dd_solve(prob)  # warm caches / imports
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     O.dd_solve(prob)
     dt = time.perf_counter() - t0
-    return {"value": (n - 1) ** 2 / dt, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+    busy = (time.process_time() - c0) / dt  # average threads busy (BLAS threads included)
+    return {"value": (n - 1) ** 2 / dt, "unit": "DOF/s", "cores": os.cpu_count(),
+            "threads_busy": round(busy, 1), "kind": "oracle",
             "sample": f"oracle dd_solve on the {n}x{n} instance of the workload (FP64, {dt:.1f} s)"}
 
 

@@ -31,3 +31,26 @@ def test_tensor_core_flop_count():
     # (m x m) x (m x 1) products at least three times over (3xTF32), on padded blocks
     nds, nb, m = 63, 2047, 63
     assert f(nds, nb, 64) >= 3 * nds * nb * (nb - 1) * 2.0 * m * m
+
+
+def test_clock_log_summary():
+    """Median and maximum SM clock and the throttle reasons of an nvidia-smi sample log."""
+    S = _bench().ClockSampler.summarize
+    q = "0, {sm}, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, {cap}"
+    lines = [q.format(sm=sm, cap=cap) for sm, cap in
+             [(2070, "Not Active"), (1980, "Active"), (2055, "Not Active")]]
+    lines.append("0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active")
+    lines.append("garbled")
+    r = S(lines)
+    assert r == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    hot = "0, 1500, 2070, 1400, 0x8, Active, Not Active, Active, Not Active"
+    assert S([hot])["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert S([])["sm_mhz"] is None and S([])["samples"] == 0
+
+
+def test_cpu_baseline_reports_busy_threads():
+    """The oracle baseline reports its rate, the host's cores and the threads it kept busy."""
+    r = _bench().cpu_baseline(n=64)
+    assert r["kind"] == "oracle" and r["unit"] == "DOF/s" and r["value"] > 0
+    assert r["cores"] == os.cpu_count()
+    assert 0.0 < r["threads_busy"] <= r["cores"] + 0.5

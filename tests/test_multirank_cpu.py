@@ -23,4 +23,4 @@ def test_bench_reference_arm_two_ranks_gloo():
     assert len(lines) == 1  # rank 0 alone prints
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
-    assert d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["threads_busy"] > 0
