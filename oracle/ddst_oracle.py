@@ -34,6 +34,11 @@ Conventions: grid and array layout as documented in ``ddst_inputs``; slabs are n
 x axis; interface ``Gamma_j`` (``j = 1..N_ds``, ``N_ds = n/w - 1``) is the node plane
 ``x = j w h``; double slab ``Psi_j`` holds the interior x-planes ``(j-1)w+1 .. (j+1)w-1``.
 Interface values are ordered like the remaining axes in C order.
+
+Every function above is pinned by ``tests/test_oracle_pins.py`` to facts the paper and the
+mathematics fix (closed forms, exact identities, printed values, brute force), and
+``tests/test_oracle_mutations.py`` checks that one-line mistakes planted in a copy of this
+module make a pin fail.
 """
 from __future__ import annotations
 
