@@ -104,6 +104,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _ref_size(steps, warmup, ref_n=None):
+    """Grid of the oracle's bounded sample: 512^2 (about 16 s per solve on 16 host cores) while
+    steps + warmup <= 10 keeps the run within about three minutes, else 256^2 (a few seconds
+    per solve); an explicit size wins."""
+    if ref_n:
+        return int(ref_n)
+    return 512 if steps + warmup <= 10 else 256
+
+
 def run_reference(args, ws, rank):
     """FP64 CPU oracle, as it stands, on a bounded sample of the workload family."""
     if rank != 0:
@@ -111,7 +120,7 @@ def run_reference(args, ws, rank):
     import numpy as np
     import ddst_inputs as I
     from oracle import ddst_oracle as O
-    n, w = args.ref_n, 32
+    n, w = _ref_size(args.steps, args.warmup, args.ref_n), 32
     prob = I.make_problem("convdiff2d", n=n, w=w)
     dof = (n - 1) ** 2
 
@@ -193,7 +202,8 @@ def main():
     ap.add_argument("--w", type=int, default=32)
     ap.add_argument("--tol", type=float, default=1e-8, help="HODLR truncation tolerance")
     ap.add_argument("--gmres-tol", type=float, default=None)
-    ap.add_argument("--ref-n", type=int, default=512)
+    ap.add_argument("--ref-n", type=int, default=None,
+                    help="grid of the oracle sample (default: by steps + warmup, see _ref_size)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -380,7 +390,7 @@ def main():
             "rooflines": {"transfer_build": roof_tc, "interface_apply": roof_ap}, "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.ref_n)
+        line["cpu_baseline"] = cpu_baseline(args.ref_n or 512)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -54,3 +54,10 @@ def test_cpu_baseline_reports_busy_threads():
     assert r["kind"] == "oracle" and r["unit"] == "DOF/s" and r["value"] > 0
     assert r["cores"] == os.cpu_count()
     assert 0.0 < r["threads_busy"] <= r["cores"] + 0.5
+
+
+def test_reference_sample_size_is_bounded_by_the_step_count():
+    size = _bench()._ref_size
+    assert size(5, 3) == 512 and size(7, 3) == 512     # default run: about two minutes
+    assert size(20, 3) == 256                          # longer runs take the smaller sample
+    assert size(20, 3, 128) == 128                     # an explicit size wins
