@@ -97,9 +97,10 @@ typedef struct {
                            the last correction (rho: observed contraction, capped at 1/2),
                            is <= refine_tol * ||u||                                         */
   int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
-  int k_max;            /* HODLR rank cap per block                                           */
-  int oversample;       /* extra random samples beyond k_max (sketch width k_max+oversample)  */
-  int leaf_size;        /* HODLR leaf size                                                    */
+  int k_max;            /* HODLR rank cap per block (used clamped to 1..128)                  */
+  int oversample;       /* extra random samples beyond k_max; the sketch width k_max +
+                           oversample is capped at 128                                        */
+  int leaf_size;        /* HODLR leaf size (used clamped to 8..256)                          */
   uint64_t seed;        /* seed of the counter-based Gaussian sketch generator                */
   int check_every;      /* GMRES iterations between host convergence checks                   */
   int factor_chunks;    /* pivot sweeps split along y into warm-started chunks per slab and
@@ -153,7 +154,8 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx);
 /* Compresses every S_{j,j'} into HODLR form (Sec. 2.4: weak admissibility, cluster tree
  * shared by source and target interface) by randomized sampling with Gaussian sketches; each
  * off-diagonal block is truncated at sigma_{r+1} <= tol * ||S_{j,j'}||_2 (rank <= k_max).
- * tol <= 0 keeps the dense operators.  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA. */
+ * tol <= 0 keeps the dense operators.  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA,
+ * INVALID_ARG (cluster tree deeper than 12 levels: raise leaf_size). */
 ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 
 /* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.

@@ -1050,7 +1050,9 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
                : hodlr_build<float>(ctx->hodlr, hp, ctx->slabs, ctx->probs, ctx->d_slabs,
                                     (const float*)ctx->S, ctx->stream, msg);
   ctx->t_compress = tm.stop();
-  if (rc != 0) return fail(ctx, rc == 2 ? DDST_ERR_OOM : DDST_ERR_CUDA, "compress: %s", msg.c_str());
+  if (rc != 0)
+    return fail(ctx, rc == 2 ? DDST_ERR_OOM : rc == 3 ? DDST_ERR_INVALID_ARG : DDST_ERR_CUDA,
+                "compress: %s", msg.c_str());
   ctx->state = 3;
   return DDST_OK;
 }

@@ -718,7 +718,7 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
     const SlabDesc& s = slabs[sb_slab[b]];
     const int64_t ng = sb[b].ng;
     const int L = levels_for(ng, leaf);
-    if (L > HOWN_MAXL) { msg = "cluster tree deeper than 12 levels (raise leaf_size)"; return 1; }
+    if (L > HOWN_MAXL) { msg = "cluster tree deeper than 12 levels (raise leaf_size)"; return 3; }
     H.sblk_L[b] = L;
     sb_fb[b] = (int)H.blocks.size();
     sb_fl[b] = (int)H.leaves.size();

@@ -73,7 +73,8 @@ struct HodlrSet {
   void release();
 };
 
-// Compresses every dense S block; returns 0 on success, 1 on CUDA error, 2 on OOM.
+// Compresses every dense S block; returns 0 on success, 1 on CUDA error, 2 on OOM, 3 when the
+// cluster tree would be deeper than HOWN_MAXL levels (an argument error).
 template <typename T>
 int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>& slabs,
                 const std::vector<ProbDesc>& probs, const SlabDesc* d_slabs, const T* S,
