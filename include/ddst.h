@@ -228,7 +228,8 @@ ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision);
  * Computes r = b(f, g) - A u for the problem (grid, coeffs), where b carries the load f and
  * the Dirichlet data g exactly as ddst_solve builds it, and writes norms[0] = ||r||_2,
  * norms[1] = ||b||_2 (so norms[0] / norms[1] is the relative residual ddst_solve reports).
- * All arrays must be DEVICE memory (this call stages nothing): f, u, r interior
+ * All arrays must be DEVICE memory of the current device, or managed memory (this call
+ * stages nothing; another GPU's memory is refused): f, u, r interior
  * ((n-1)^dim), g and coeffs->a / coeffs->c nodal ((n+1)^dim), norms two doubles.
  * At most 16,777,216 interior unknowns (e.g. a 4097^2 grid); larger grids return
  * DDST_ERR_INVALID_ARG.  The scratch is a 1 MiB file-scope device array (one FP64 partial sum

@@ -125,14 +125,17 @@ namespace {
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_partials, per device
 
-bool on_device(const void* p) {
+// Memory the kernels may read on device dev: device memory of dev itself, or managed memory.
+// Device memory of another GPU is refused (without peer access a load from it would fault).
+bool on_device(const void* p, int dev) {
   if (!p) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice && at.device == dev) ||
+         at.type == cudaMemoryTypeManaged;
 }
 }  // namespace
 
@@ -159,15 +162,17 @@ extern "C" ddst_status ddst_residual_noalloc(const ddst_grid* grid, const ddst_c
                                          std::to_string(kNoallocMaxBlocks * kNoallocThreads) +
                                          " interior unknowns; this grid has " +
                                          std::to_string(nint));
-  if (!on_device(coeffs->a) || !on_device(f) || !on_device(g) || !on_device(u) ||
-      !on_device(r) || !on_device(norms) || (coeffs->c && !on_device(coeffs->c)))
-    return bad(DDST_ERR_INVALID_ARG,
-               "ddst_residual_noalloc takes device arrays only (it stages nothing)");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return bad(DDST_ERR_CUDA, "cudaGetDevice failed");
   }
+  if (!on_device(coeffs->a, dev) || !on_device(f, dev) || !on_device(g, dev) ||
+      !on_device(u, dev) || !on_device(r, dev) || !on_device(norms, dev) ||
+      (coeffs->c && !on_device(coeffs->c, dev)))
+    return bad(DDST_ERR_INVALID_ARG,
+               "ddst_residual_noalloc takes device arrays of the current device only (it stages "
+               "nothing)");
   if (!g_noalloc_ptr[dev]) {
     // host code may not use the array's name as an address: ask the runtime for it, once per
     // device, with that device current
