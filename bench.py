@@ -383,6 +383,8 @@ def main():
             "s_per_adjoint_gradient": statistics.mean(adj) / 1e3,
             "phases_ms": {"factor": info["t_factor"], "transfer": info["t_transfer"],
                           "compress": info["t_compress"], "solve": info["t_solve"]},
+            # setup reused (the method's multi-right-hand-side use): solve phase alone
+            "solve_only_dof_per_s": dof / (info["t_solve"] / 1e3) if info["t_solve"] > 0 else None,
             "solve_info": {"gmres_iters": info["gmres_iters"], "refine_iters": info["refine_iters"],
                            "est_rel_error": info["est_rel_error"], "rel_residual": info["rel_residual"],
                            "max_rank": info["max_rank"], "bytes_transfer": info["bytes_transfer"]},
