@@ -5,6 +5,7 @@ a misspelt name in the benchmark's timed region or in the binding cannot surface
 GPU machine.  Uses only the standard library's symbol tables.
 """
 import builtins
+import glob
 import os
 import symtable
 
@@ -13,7 +14,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FILES = ["bench.py", "__graft_entry__.py", "paper_2510_25991_gb300/ddst.py",
          "paper_2510_25991_gb300/_lib.py", "paper_2510_25991_gb300/build.py",
-         "oracle/ddst_oracle.py", "ddst_inputs/__init__.py"]
+         "oracle/ddst_oracle.py", "ddst_inputs/__init__.py"] + sorted(
+    os.path.relpath(f, ROOT) for f in glob.glob(os.path.join(ROOT, "tests", "test_*.py")))
 
 
 def _undefined_globals(path):
