@@ -92,7 +92,7 @@ typedef struct {
   double gmres_tol;     /* relative residual target of each interface GMRES solve; <= 0 picks
                            1e-2 for DDST_MIXED (inner solve of the refinement) or 1e-10 for
                            DDST_FP64                                                          */
-  int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES)                           */
+  int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES; used clamped to 1..1000)  */
   double refine_tol;    /* FP64 refinement stops when its error estimate, rho / (1 - rho) times
                            the last correction (rho: observed contraction, capped at 1/2),
                            is <= refine_tol * ||u||                                         */
