@@ -51,13 +51,24 @@ def _check(lib, ctx, st):
         raise DDSTError(st, msg.decode() if msg else "")
 
 
+_PRECISIONS = {"fp64": L.DDST_FP64, "mixed": L.DDST_MIXED, "auto": L.DDST_AUTO}
+
+
 def ddst_options_default(**overrides):
+    """The library's default options with ``overrides`` applied; ``precision`` may be given as
+    "fp64", "mixed" or "auto".  Unknown option names raise TypeError (a ctypes structure would
+    otherwise take them silently as plain attributes)."""
     lib = L.load()
     o = L.ddst_options()
     lib.ddst_options_default(C.byref(o))
+    fields = {f[0] for f in L.ddst_options._fields_}
     for k, v in overrides.items():
+        if k not in fields:
+            raise TypeError(f"unknown option {k!r}; options are {', '.join(sorted(fields))}")
         if k == "precision" and isinstance(v, str):
-            v = {"fp64": L.DDST_FP64, "mixed": L.DDST_MIXED, "auto": L.DDST_AUTO}[v.lower()]
+            if v.lower() not in _PRECISIONS:
+                raise ValueError(f"precision must be one of {', '.join(_PRECISIONS)}, not {v!r}")
+            v = _PRECISIONS[v.lower()]
         setattr(o, k, v)
     return o
 

@@ -121,3 +121,13 @@ def test_context_free_error_message_is_per_thread():
     t.join()
     assert "n % w == 0" in seen["other"]
     assert "dim must be 2 or 3" in lib.ddst_last_error(None).decode()
+
+
+def test_options_reject_unknown_names_and_precisions():
+    from paper_2510_25991_gb300 import ddst as D
+    assert D.ddst_options_default(precision="auto").precision == 2
+    assert D.ddst_options_default(precision="FP64", leaf_size=64).leaf_size == 64
+    with pytest.raises(TypeError, match="unknown option 'leafsize'"):
+        D.ddst_options_default(leafsize=64)
+    with pytest.raises(ValueError, match="precision must be"):
+        D.ddst_options_default(precision="half")
