@@ -45,6 +45,20 @@ def _ptr(x):
     raise TypeError(type(x))
 
 
+def _check_sizes(prob, **arrays):
+    """Element counts of interior (f, u, dL/du, dL/df) and nodal (g, a, dL/dg, dL/da) arrays of
+    one problem: the library takes plain pointers and cannot check them itself."""
+    d, n = prob["dim"], prob["n"]
+    nodal = {"g", "a", "dLdg", "dLda"}
+    for name, x in arrays.items():
+        if x is None:
+            continue
+        k = x.numel() if hasattr(x, "data_ptr") else np.asarray(x).size
+        want = (n + 1) ** d if name in nodal else (n - 1) ** d
+        if k != want:
+            raise ValueError(f"{name} has {k} entries; a {d}D problem with n = {n} needs {want}")
+
+
 def _check(lib, ctx, st):
     if st != L.DDST_OK:
         msg = lib.ddst_last_error(ctx)
@@ -252,6 +266,8 @@ class Solver:
         return self
 
     def solve(self, f, g, u, **kw):
+        if len(self.problems) == 1:
+            _check_sizes(self.problems[0], f=f, g=g, u=u)
         return ddst_solve(self.ctx, f, g, u, **kw)
 
     def close(self):

@@ -131,3 +131,16 @@ def test_options_reject_unknown_names_and_precisions():
         D.ddst_options_default(leafsize=64)
     with pytest.raises(ValueError, match="precision must be"):
         D.ddst_options_default(precision="half")
+
+
+def test_array_sizes_checked_before_the_library_is_called():
+    import numpy as np
+
+    from paper_2510_25991_gb300 import ddst as D
+    prob = dict(dim=2, n=16)
+    D._check_sizes(prob, f=np.zeros((15, 15)), g=np.zeros((17, 17)), u=np.zeros(225), a=None)
+    with pytest.raises(ValueError, match="g has 225 entries"):
+        D._check_sizes(prob, f=np.zeros((15, 15)), g=np.zeros((15, 15)))
+    with pytest.raises(ValueError, match="u has 289 entries"):
+        D._check_sizes(dict(dim=2, n=16), u=np.zeros((17, 17)))
+    D._check_sizes(dict(dim=3, n=8), f=np.zeros(343), dLdg=np.zeros(729))
