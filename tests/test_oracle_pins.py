@@ -325,6 +325,33 @@ def test_gmres_finite_termination_and_residual():
     assert true <= 2e-10 and abs(true - hist[-1]) <= 1e-12
 
 
+def test_helmholtz_local_operators_definite_by_a_small_margin():
+    """Helmholtz reading: c = -kappa^2 (1 - 0.5 exp(-25 |x - x_c|^2)) >= -kappa^2, so by Weyl
+    lambda_min(-Lap_h) - kappa^2 <= lambda_min(A_j) <= lambda_min(-Lap_h) - kappa^2 (1 - bump/2),
+    bump = the largest exp(-25 |x - x_c|^2) over the slab, with the closed form
+    lambda_min(-Lap_h) = (4/h^2)(sin^2(pi/4w) + sin^2(pi/2n)) of the (2w-1) x (n-1) slab.
+    At 4096^2, w = 32, kappa = 200 the margin is about 1%; the 512^2, kappa = 100, w = 8 case
+    keeps it (0.8%), and every local operator the oracle assembles lies in its bracket."""
+    import scipy.sparse.linalg as spla
+    lap = lambda n, w: 4.0 * n * n * (np.sin(np.pi / (4 * w)) ** 2 + np.sin(np.pi / (2 * n)) ** 2)
+    assert 0.01 <= lap(4096, 32) / 200.0 ** 2 - 1.0 <= 0.012
+    n, w, kappa = 512, 8, 100.0
+    assert 0.005 <= lap(n, w) / kappa ** 2 - 1.0 <= 0.01
+    prob = I.make_problem("helmholtz2d", n=n, w=w, kappa=kappa)
+    A, _ = O.assemble(prob)
+    geo = O.slab_geometry(2, n, w)
+    X = I.node_coords(2, n)
+    bump = np.exp(-25.0 * ((X[0] - 0.5) ** 2 + (X[1] - 0.5) ** 2))
+    for j in (0, 1, geo.nds // 2, geo.nds - 1):
+        Aj = sp.csc_matrix(A[geo.I[j]][:, geo.I[j]])
+        lam = spla.eigsh(Aj, k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+        xs = slice(j * w + 1, (j + 2) * w)            # interior x-nodes of double slab j
+        top = bump[xs, 1:n].max()
+        lo, hi = lap(n, w) - kappa ** 2, lap(n, w) - kappa ** 2 * (1.0 - 0.5 * top)
+        assert lo * (1 - 1e-9) <= lam <= hi * (1 + 1e-9), (j, lam, lo, hi)
+        assert lam > 0.0
+
+
 def test_gmres_orthogonal_basis_keeps_finite_termination():
     """GMRES ends by step n on an n x n matrix when the Krylov basis stays orthogonal.
 
