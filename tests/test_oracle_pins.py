@@ -325,6 +325,24 @@ def test_gmres_finite_termination_and_residual():
     assert true <= 2e-10 and abs(true - hist[-1]) <= 1e-12
 
 
+def test_benchmark_convection_needs_no_upwinding():
+    """Central convection keeps the nonsymmetric workload an M-matrix: every face coefficient
+    a_face / h^2 exceeds |b_d| / (2h), i.e. the cell Peclet number |b_d| h / (2 a_face) < 1.
+    Checked on the full 2048^2 coefficient field, and on the oracle's assembled operator at
+    512^2 (off-diagonals <= 0, rows weakly diagonally dominant)."""
+    prob = I.make_problem("convdiff2d")
+    a, n = prob["a"], prob["n"]
+    h = 1.0 / n
+    fx, fy = 0.5 * (a[1:, :] + a[:-1, :]), 0.5 * (a[:, 1:] + a[:, :-1])
+    bx, by = abs(prob["b"][0]), abs(prob["b"][1])
+    assert max(bx * h / (2 * fx.min()), by * h / (2 * fy.min())) < 0.05
+    small = I.make_problem("convdiff2d", n=512, w=32)
+    A, _ = O.assemble(small)
+    off = A - sp.diags(A.diagonal())
+    assert off.max() <= 0.0
+    assert (np.asarray(A.sum(axis=1)).ravel() >= -1e-9 * A.diagonal().max()).all()
+
+
 def test_helmholtz_local_operators_definite_by_a_small_margin():
     """Helmholtz reading: c = -kappa^2 (1 - 0.5 exp(-25 |x - x_c|^2)) >= -kappa^2, so by Weyl
     lambda_min(-Lap_h) - kappa^2 <= lambda_min(A_j) <= lambda_min(-Lap_h) - kappa^2 (1 - bump/2),
