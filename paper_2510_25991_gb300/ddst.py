@@ -49,7 +49,7 @@ def _check_sizes(prob, **arrays):
     """Element counts of interior (f, u, dL/du, dL/df) and nodal (g, a, dL/dg, dL/da) arrays of
     one problem: the library takes plain pointers and cannot check them itself."""
     d, n = prob["dim"], prob["n"]
-    nodal = {"g", "a", "dLdg", "dLda"}
+    nodal = {"g", "a", "c", "dLdg", "dLda"}
     for name, x in arrays.items():
         if x is None:
             continue
@@ -217,7 +217,17 @@ def ddst_get_precision(ctx):
 
 def ddst_residual_noalloc(dim, n, a, f, g, u, r, norms, b=(0.0, 0.0, 0.0), c=None, stream=None):
     """Allocation-free FP64 residual r = b(f, g) - A u and norms (||r||, ||b||); device arrays
-    only.  Stream-ordered: synchronize before reading the results."""
+    only.  The library receives plain pointers and cannot see array sizes, so they are checked
+    here before anything is launched (ValueError).  ``stream`` defaults to torch's current CUDA
+    stream when the arrays are torch tensors (else the legacy default stream).  The call returns
+    once the work is enqueued: synchronize that stream before reading r or norms."""
+    _check_sizes(dict(dim=dim, n=n), f=f, g=g, u=u, r=r, a=a, c=c)
+    k = norms.numel() if hasattr(norms, "data_ptr") else np.asarray(norms).size
+    if k < 2:
+        raise ValueError(f"norms has {k} entries; it needs 2")
+    if stream is None and hasattr(u, "data_ptr") and getattr(u, "is_cuda", False):
+        import torch
+        stream = torch.cuda.current_stream(u.device).cuda_stream
     lib = L.load()
     grid = L.ddst_grid(dim, n)
     cf = _coeffs(a, b, c)
