@@ -13,6 +13,13 @@ follows ("the paper" below):
   face values ``a_pq = (a_p + a_q)/2``; convection by central differences; Dirichlet
   neighbours moved to the right-hand side.
 * O2 ``global_solve``: sparse direct solve of the global system (SuperLU).
+* O2b ``poisson_dst_solve``: the same global solution for the constant-coefficient Poisson
+  operator (``a = 1``, ``b = 0``, ``c = 0``; the Poisson experiments of Sec. 5.2, Table
+  fd_poisson_fixedH) by the sine transform that diagonalizes it (separation of variables); exact
+  to rounding and fast at any size.
+* O2c ``diffusion_error_bound``: a rigorous a-posteriori bound on ``||u - u*|| / ||u*||`` for a
+  pure-diffusion operator (``b = 0``, ``c >= 0``) from the FP64 residual of O1 and the closed-form
+  smallest eigenvalue of the constant-coefficient Laplacian, used where O2 is too large to run.
 * O3 ``transfer_blocks`` / ``equivalent_load``: the local solution-transfer operators
   ``S_{j,j'} = -R_{C_j} A_j(I_j,I_j)^{-1} A_j(I_j,J_{j,j'})`` (Sec. 2.2, Eq. (defS); Sec. 2.5)
   and the equivalent loads ``fhat_j`` (Sec. 2.2, Eq. (equilib1), Fig. genBC: local solve with the global load and physical data,
@@ -46,12 +53,14 @@ import math
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.fft as sfft
 import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 __all__ = [
-    "assemble", "global_solve", "SlabGeometry", "slab_geometry", "factor_local",
+    "assemble", "global_solve", "poisson_dst_solve", "laplacian_lambda_min",
+    "diffusion_error_bound", "SlabGeometry", "slab_geometry", "factor_local",
     "transfer_blocks", "equivalent_load", "interface_matrix", "apply_interface",
     "block_thomas", "gmres", "reconstruct", "dd_solve", "hodlr_levels", "hodlr_node",
     "hodlr_compress", "hodlr_dense", "hodlr_apply", "adjoint_solve", "gradients",
@@ -123,6 +132,63 @@ def global_solve(A, b):
     """``u* = A^{-1} b`` by SuperLU (FP64)."""
     lu = spla.splu(sp.csc_matrix(A))
     return lu.solve(np.asarray(b, dtype=np.float64))
+
+
+def poisson_dst_solve(prob: dict):
+    """O2b: ``u* = A^{-1} b`` for ``a = 1``, ``b = 0``, ``c = 0`` by the discrete sine transform.
+
+    The five/seven-point Dirichlet Laplacian on the interior nodes is the Kronecker sum of the
+    1D operators ``tridiag(-1, 2, -1)/h^2``, whose eigenvectors are ``sin(pi i k / n)``
+    (``k = 1..n-1``) with eigenvalues ``(4/h^2) sin^2(pi k / (2n))``.  The type-1 DST applies
+    that eigenbasis (up to a scale its inverse removes), so the solve is: transform ``b``,
+    divide by the eigenvalue sums, transform back.  ``b`` is O1's right-hand side (load plus
+    boundary data).
+    """
+    dim, n = prob["dim"], prob["n"]
+    if not (np.all(np.asarray(prob["a"]) == 1.0) and prob.get("c") is None
+            and not any(prob.get("b") or ())):
+        raise ValueError("poisson_dst_solve needs a = 1, b = 0 and no reaction term")
+    _, b = assemble(prob)
+    k = np.arange(1, n)
+    lam1 = 4.0 * n * n * np.sin(np.pi * k / (2.0 * n)) ** 2
+    lam = np.zeros((n - 1,) * dim)
+    for d in range(dim):
+        shape = [1] * dim
+        shape[d] = n - 1
+        lam = lam + lam1.reshape(shape)
+    bh = sfft.dstn(b.reshape((n - 1,) * dim), type=1)
+    return sfft.idstn(bh / lam, type=1).ravel()
+
+
+def laplacian_lambda_min(dim: int, n: int) -> float:
+    """Smallest eigenvalue of the constant-coefficient Dirichlet Laplacian (O2b's basis):
+    ``dim (4/h^2) sin^2(pi h / 2)``."""
+    return dim * 4.0 * n * n * math.sin(math.pi / (2.0 * n)) ** 2
+
+
+def diffusion_error_bound(prob: dict, u):
+    """O2c: rigorous bound on ``||u - u*||_2 / ||u*||_2`` for ``-div(a grad u) + c u = f`` with
+    ``c >= 0`` and no convection.
+
+    O1's matrix is ``A = sum_faces a_pq (e_p - e_q)(e_p - e_q)^T / h^2`` (boundary faces keep only
+    ``e_p e_p^T``) plus ``diag(c)``; every term is positive semidefinite and ``a_pq`` is at least
+    ``a_min`` (the smallest nodal value), so ``A - a_min L`` is positive semidefinite and
+    ``lambda_min(A) >= a_min lambda_min(L)``.  Hence ``||u - u*|| = ||A^{-1} r|| <= ||r|| /
+    (a_min lambda_min(L))``, with ``r = b - A u`` evaluated in FP64 and enlarged by the
+    rounding bound of that evaluation (at most 8 terms per row: ``gamma_8 (|b| + |A| |u|)``).
+    """
+    if any(prob.get("b") or ()) or (prob.get("c") is not None and np.min(prob["c"]) < 0):
+        raise ValueError("the bound needs b = 0 and c >= 0")
+    A, b = assemble(prob)
+    u = np.asarray(u, dtype=np.float64).ravel()
+    r = b - A @ u
+    eps = np.finfo(np.float64).eps
+    gam = 8 * eps / (1 - 8 * eps)
+    rnorm = np.linalg.norm(r) + gam * np.linalg.norm(np.abs(b) + abs(A) @ np.abs(u))
+    lam = float(np.min(prob["a"])) * laplacian_lambda_min(prob["dim"], prob["n"])
+    err = rnorm / lam
+    un = np.linalg.norm(u)
+    return err / (un - err) if un > err else math.inf
 
 
 # ---------------------------------------------------------------------------------------

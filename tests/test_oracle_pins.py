@@ -481,3 +481,48 @@ def test_p9_hodlr_tree_and_exact_limits():
     K = np.outer(np.cos(t), np.sin(t)) + np.outer(t, t ** 2)
     H = O.hodlr_compress(K + np.diag(t), tol=1e-12, leaf=8)
     assert max(U.shape[1] for lev in H["levels"] for (U, V) in lev) <= 2
+
+
+@pytest.mark.parametrize("dim,n", [(2, 32), (3, 12), (3, 10)])
+def test_o2b_sine_transform_poisson_matches_sparse_direct(dim, n):
+    """O2b against O2 (SuperLU) on the same constant-coefficient Poisson system, and against the
+    exact manufactured solution: with f = 0 and harmonic quadratic boundary data the discrete
+    solution is the quadratic itself (the stencil is exact on quadratics)."""
+    prob = I.make_problem("poisson2d" if dim == 2 else "vardiff3d", n=n, w=2, const_a=True)
+    A, b = O.assemble(prob)
+    u = O.global_solve(A, b)
+    assert np.abs(O.poisson_dst_solve(prob) - u).max() <= 1e-12 * np.abs(u).max()
+    harm = dict(prob, f=np.zeros_like(prob["f"]))
+    inner = tuple(slice(1, n) for _ in range(dim))
+    exact = prob["g"][inner].ravel()
+    assert np.abs(O.poisson_dst_solve(harm) - exact).max() <= 1e-12 * np.abs(exact).max()
+    with pytest.raises(ValueError):
+        O.poisson_dst_solve(I.make_problem("vardiff3d", n=8, w=2))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 24), (3, 10)])
+def test_o2c_error_bound_holds_and_is_tight_on_the_lowest_mode(dim, n):
+    """O2c is an upper bound for a variable-coefficient operator and random perturbations of the
+    exact solution, and it is attained (to 1%) when the error is the lowest Laplacian mode of a
+    constant-coefficient operator: then A e = a lambda_min e exactly."""
+    rng = np.random.default_rng(3)
+    prob = I.make_problem("poisson2d" if dim == 2 else "vardiff3d", n=n, w=2)
+    if dim == 2:
+        prob["a"] = I.fourier_log_field(2, n, 77)
+    A, b = O.assemble(prob)
+    us = O.global_solve(A, b)
+    for scale in (1e-3, 1e-8):
+        u = us + scale * np.abs(us).max() * rng.standard_normal(us.size)
+        true = np.linalg.norm(u - us) / np.linalg.norm(us)
+        assert O.diffusion_error_bound(prob, u) >= true
+    # a = 0.5 everywhere: lambda_min(A) = 0.5 lambda_min(L)
+    pc = dict(prob, a=np.full_like(prob["a"], 0.5))
+    A, b = O.assemble(pc)
+    us = O.global_solve(A, b)
+    grids = np.meshgrid(*([np.arange(1, n)] * dim), indexing="ij")
+    mode = np.prod([np.sin(np.pi * gd / n) for gd in grids], axis=0).ravel()
+    e = 1e-6 * np.linalg.norm(us) * mode / np.linalg.norm(mode)
+    true = np.linalg.norm(e) / np.linalg.norm(us)
+    bound = O.diffusion_error_bound(pc, us + e)
+    assert true <= bound <= 1.01 * true
+    assert abs(O.laplacian_lambda_min(dim, n) * 0.5 - (A @ mode)[0] / mode[0]) <= 1e-9 * n * n
