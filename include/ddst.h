@@ -106,8 +106,14 @@ typedef struct {
   int factor_chunks;    /* pivot sweeps split along y into warm-started chunks per slab and
                            direction: 0 automatic, 1 exact sequential sweeps, k > 1 forced     */
   int factor_warmup;    /* warm-up rows of a chunk (0: 4 w in FP32, 10 w in FP64)              */
-  int tensor_cores;     /* 1: DDST_MIXED transfer build on the tcgen05 tensor cores (3xTF32,
-                           block sizes <= 64); 0: FP32 FMA kernel (kept for validation)       */
+  int tensor_cores;     /* 1: DDST_MIXED transfer build (block sizes <= 64) and large-block
+                           factorization on the tcgen05 tensor cores (3xTF32); 0: FP32 FMA
+                           kernels (kept for validation)                                      */
+  int explicit_S;       /* transfer operators: 1 formed explicitly (Alg. 1 with the identity as
+                           test matrix; required by ddst_compress), 0 applied matrix-free through
+                           two sweeps of local solves per GMRES iteration (no S stored), -1
+                           automatic: matrix-free when some block is larger than 128 (or 64 in
+                           FP64), explicit otherwise                                          */
 } ddst_options;
 
 /* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
@@ -129,14 +135,20 @@ typedef struct {
 } ddst_info;
 
 /* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
- * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234. */
+ * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234,
+ * tensor_cores 1, explicit_S -1. */
 void ddst_options_default(ddst_options* opt);
 
 /* Builds the local operators A_j(I_j, I_j) of every double slab and factors them
  * (Sec. 2.5 and Alg. 2: "compute local discretization", "factorize").
- * grid/coeffs: one problem; slab_width: w cells (n % w == 0, n/w >= 2, 2w-1 <= 127 in 2D,
- * (2w-1)(n-1) <= 128 in 3D).  opt may be NULL (defaults).  stream: cudaStream_t or NULL.
- * On success *out receives a new context.  Errors: INVALID_ARG, OOM, CUDA, SINGULAR. */
+ * grid/coeffs: one problem; slab_width: w cells (n % w == 0, n/w >= 2, block size
+ * m = (2w-1)(n-1)^(dim-2) <= 8192).  Blocks up to 128 (64 in FP64) are factored by one CTA per
+ * slab and sweep direction (two-sided block LU, explicit inverses F, B and diagonal blocks G of
+ * A_j^{-1}); larger blocks, padded to a multiple of 128, by a one-sided block LU whose dense
+ * inverses are formed by 128-wide Gauss-Jordan panels on the tensor cores (FP32) or FMA (FP64),
+ * all slabs of a block size advancing together.  opt may be NULL (defaults).  stream:
+ * cudaStream_t or NULL.  On success *out receives a new context.  Errors: INVALID_ARG, OOM,
+ * CUDA, SINGULAR. */
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
                        const ddst_options* opt, void* stream, ddst_ctx** out);
 
@@ -148,6 +160,9 @@ ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeff
 
 /* Forms every S_{j,j-1} and S_{j,j+1} explicitly (Sec. 2.2, Eq. (defS)) from one transposed
  * multi-right-hand-side solve per double slab with the central interface points as sources.
+ * In a matrix-free context (options.explicit_S) nothing is formed: S is applied through the
+ * local factors (two sweeps of local solves per application; Sec. 2.5, the LU column of the
+ * comparison in Sec. 5.1), and this call only marks the operators ready.
  * Requires ddst_setup.  Errors: STATE, OOM, CUDA. */
 ddst_status ddst_build_transfer(ddst_ctx* ctx);
 
@@ -155,7 +170,8 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx);
  * shared by source and target interface) by randomized sampling with Gaussian sketches; each
  * off-diagonal block is truncated at sigma_{r+1} <= tol * ||S_{j,j'}||_2 (rank <= k_max).
  * tol <= 0 keeps the dense operators.  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA,
- * INVALID_ARG (cluster tree deeper than 12 levels: raise leaf_size). */
+ * INVALID_ARG (cluster tree deeper than 12 levels: raise leaf_size), NOT_IMPLEMENTED (tol > 0 on a
+ * matrix-free context: compression samples the explicit operators). */
 ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 
 /* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.
@@ -191,7 +207,7 @@ ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG);
 /* Copies S_{j,j-1} (side = -1) or S_{j,j+1} (side = +1) of problem prob, slab j (1-based),
  * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR if compressed) into
  * a host or device array.  Errors: INVALID_ARG (bad prob, j or side; no such block at the
- * ends), STATE (transfer operators not built), CUDA. */
+ * ends), STATE (transfer operators not built), NOT_IMPLEMENTED (matrix-free context), CUDA. */
 ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* out);
 
 /* y = (I - K) x (transpose = 0) or y = (I - K)^T x (transpose = 1) for problem prob with the

@@ -110,6 +110,19 @@ struct ddst_ctx {
   unsigned* arn_ticket = nullptr;        // last-CTA ticket of the Arnoldi finish kernel
   double *h1 = nullptr, *h2 = nullptr, *d_beta = nullptr;
   float *Uhi = nullptr, *Ulo = nullptr;  // tensor-core operand copies of F^T | B^T
+  // large-block classes (M > 128, or > 64 in FP64): one-sided factors in Fbig, work buffers
+  std::map<int, bool> big;               // M -> factored by the large-block kernels
+  int64_t fac_big_elems = 0;
+  void* Fbig = nullptr;
+  struct BigWork { void *C = nullptr, *XqT = nullptr, *RT = nullptr, *Pinv = nullptr; };
+  std::map<int, BigWork> bigw;
+  bool big_tc = false;                   // large-block Gauss-Jordan updates on tcgen05
+  // matrix-free interface operator (no explicit S): its own slab-local buffers, so that an
+  // application inside GMRES leaves the DD solve's vectors untouched
+  bool matfree = false;
+  void *mf_b = nullptr, *mf_z = nullptr, *mf_z2 = nullptr, *mf_x = nullptr;
+  double* if_kx = nullptr;
+  long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
 };
 
 namespace {
@@ -184,7 +197,14 @@ ddst_status check_status(ddst_ctx* ctx, ddst_info* info) {
   return fail(ctx, DDST_ERR_CUDA, "device status %d", h.code);
 }
 
-int pad_M(int m) { return m <= 32 ? 32 : (m <= 64 ? 64 : (m <= 128 ? 128 : -1)); }
+// Padded block size: 32, 64 or 128 for the single-CTA kernels, else a multiple of 128 (at most
+// 8192) for the large-block kernels.
+int pad_M(int m) {
+  if (m <= 32) return 32;
+  if (m <= 64) return 64;
+  if (m <= 128) return 128;
+  return m <= 8192 ? ((m + 127) / 128) * 128 : -1;
+}
 
 struct Timer {
   cudaEvent_t a, b;
@@ -269,6 +289,7 @@ ddst_status factor_all(ddst_ctx* ctx) {
     worst = 0.0;
     chunks_used = 1;
     for (auto& kv : ctx->cls) {
+      if (ctx->big[kv.first]) continue;
       std::vector<FacChunk> ch;
       int nslots = 0;
       plan(kv.first, kv.second, exact, ch, nslots);
@@ -310,12 +331,25 @@ ddst_status factor_all(ddst_ctx* ctx) {
     ctx->factor_check = worst;
   }
   ctx->factor_chunks = used;
-  for (auto& kv : ctx->cls)
+  for (auto& kv : ctx->cls) {
+    if (ctx->big[kv.first]) continue;
     launch_factor<T>(kv.first, 1, ctx->d_slabs, nullptr, 0, ctx->d_cls[kv.first],
                      (int)kv.second.size(), ctx->cls_maxnb[kv.first], (T*)ctx->pack, (T*)ctx->F,
                      (T*)ctx->B, (T*)ctx->G, (T*)ctx->Ft, (T*)ctx->Bt, nullptr, nullptr, nullptr,
                      nullptr, 0, ctx->d_st, st);
+  }
   CK(cudaGetLastError());
+  // large blocks: one-sided block LU, every slab of a class one block row at a time
+  for (auto& kv : ctx->cls) {
+    if (!ctx->big[kv.first]) continue;
+    ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
+    for (int k = 1; k <= ctx->cls_maxnb[kv.first]; ++k) {
+      launch_big_factor_step<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
+                                (const T*)ctx->pack, (T*)ctx->Fbig, k, (T*)bw.C, (T*)bw.XqT,
+                                (T*)bw.RT, (T*)bw.Pinv, ctx->big_tc, ctx->d_st, st);
+      CK(cudaGetLastError());
+    }
+  }
   return DDST_OK;
 }
 
@@ -338,7 +372,8 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   // contracts by ~10x per step), so solving its interface system beyond 1e-2 is wasted work;
   // the FP64 DD solve is accurate, so a tight inner tolerance finishes in one or two steps.
   if (!(ctx->opt.gmres_tol > 0.0)) ctx->opt.gmres_tol = ctx->prec == DDST_FP64 ? 1e-10 : 1e-2;
-  int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, pack_off = 0, loc_off = 0, s_off = 0;
+  int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, fac_big_off = 0, pack_off = 0,
+          loc_off = 0, s_off = 0;
   for (int q = 0; q < nprob; ++q) {
     const ddst_grid& gr = grids[q];
     const int w = widths[q];
@@ -356,12 +391,16 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     P.p = gr.dim == 2 ? 1 : P.n - 1;
     P.m = (2 * w - 1) * P.p;
     P.M = pad_M(P.m);
-    if (P.M < 0 || (ctx->prec == DDST_FP64 && P.M > 64)) {
+    if (P.M < 0) {
       ddst_destroy(ctx);
       return fail(nullptr, DDST_ERR_INVALID_ARG,
-                  "problem %d: block size (2w-1)(n-1)^(dim-2) = %d exceeds %d", q, P.m,
-                  ctx->prec == DDST_FP64 ? 64 : 128);
+                  "problem %d: block size (2w-1)(n-1)^(dim-2) = %d exceeds 8192", q, P.m);
     }
+    // blocks above the single-CTA kernels' reach (128 in FP32, 64 in FP64) go to the
+    // large-block kernels, padded to a multiple of 128
+    const bool isbig = P.M > 128 || (ctx->prec == DDST_FP64 && P.M > 64);
+    if (isbig) P.M = ((P.m + 127) / 128) * 128;
+    ctx->big[P.M] = isbig;
     P.nb = P.n - 1;
     P.ng = (int64_t)P.nb * P.p;
     P.nint = 1;
@@ -378,7 +417,8 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       SlabDesc s{};
       s.prob = q; s.j = j; s.M = P.M; s.m = P.m; s.nb = P.nb; s.p = P.p; s.w = w; s.n = P.n;
       s.ng = P.ng;
-      s.fac_off = fac_off; fac_off += (int64_t)P.nb * P.M * P.M;
+      if (isbig) { s.fac_off = fac_big_off; fac_big_off += (int64_t)P.nb * P.M * P.M; }
+      else { s.fac_off = fac_off; fac_off += (int64_t)P.nb * P.M * P.M; }
       s.pack_off = pack_off; pack_off += (int64_t)P.nb * PK_NFIELDS * P.M;
       s.loc_off = loc_off; loc_off += (int64_t)P.nb * P.M;
       s.sp_off = -1; s.sn_off = -1;
@@ -399,6 +439,17 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   }
   ctx->tot_nodes = node_off; ctx->tot_vol = vol_off; ctx->tot_if = if_off;
   ctx->tot_loc = loc_off; ctx->fac_elems = fac_off; ctx->pack_elems = pack_off; ctx->s_elems = s_off;
+  ctx->fac_big_elems = fac_big_off;
+  bool any_big = false;
+  for (auto& kv : ctx->big) any_big = any_big || kv.second;
+  if (ctx->opt.explicit_S == 1 && any_big) {
+    ddst_destroy(ctx);
+    return fail(nullptr, DDST_ERR_INVALID_ARG,
+                "explicit transfer operators need blocks of at most 128 (64 in FP64) unknowns; "
+                "use explicit_S = 0 or -1 (matrix-free) for larger blocks");
+  }
+  ctx->matfree = ctx->opt.explicit_S == 0 || (ctx->opt.explicit_S < 0 && any_big);
+  ctx->big_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
   const int nslab = (int)ctx->slabs.size();
   const size_t es = ctx->esz;
   cudaError_t e;
@@ -423,12 +474,28 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   AL(ctx->loc_bf, es * ctx->tot_loc);
   AL(ctx->loc_bb, es * ctx->tot_loc);
   AL(ctx->loc_x, es * ctx->tot_loc);
+  if (ctx->fac_big_elems > 0) AL(ctx->Fbig, es * ctx->fac_big_elems);
   for (auto& kv : ctx->cls) {
     int* d = nullptr;
     AL(d, sizeof(int) * kv.second.size());
     ctx->d_cls[kv.first] = d;
+    if (ctx->big[kv.first]) {
+      ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
+      const size_t panel = es * kv.second.size() * (size_t)kv.first * 128;
+      AL(bw.C, panel);
+      AL(bw.XqT, panel);
+      AL(bw.RT, panel);
+      AL(bw.Pinv, es * kv.second.size() * 128 * 128);
+    }
   }
-  ctx->use_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
+  if (ctx->matfree) {
+    AL(ctx->mf_b, es * ctx->tot_loc);
+    AL(ctx->mf_z, es * ctx->tot_loc);
+    AL(ctx->mf_z2, es * ctx->tot_loc);
+    AL(ctx->mf_x, es * ctx->tot_loc);
+    AL(ctx->if_kx, sizeof(double) * ctx->tot_if);
+  }
+  ctx->use_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0 && !ctx->matfree;
   for (auto& kv : ctx->cls)
     if (kv.first > 64) ctx->use_tc = false;
   if (ctx->use_tc) {
@@ -493,6 +560,13 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
 template <typename T>
 ddst_status build_transfer_impl(ddst_ctx* ctx) {
   cudaStream_t st = ctx->stream;
+  if (ctx->matfree) {  // S is applied through the local factors: nothing to form
+    ctx->t_transfer = 0.f;
+    ctx->hodlr.clear();
+    drop_graphs(ctx);
+    ctx->state = 2;
+    return DDST_OK;
+  }
   if (!ctx->S) {
     cudaError_t e = dalloc(ctx, &ctx->S, sizeof(T) * ctx->s_elems);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc S");
@@ -597,11 +671,55 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   return DDST_OK;
 }
 
+// Local Dirichlet solves of every double slab, all block-size classes: x = A_j^{-1} b
+// (transpose: A_j^{-T} b).  mode 0 writes x slab-locally; mode 1 (not transposed) writes the
+// central rows, R_C x, into the FP64 interface vector iface.  z1, z2: slab-local temporaries.
+template <typename T>
+void local_solves(ddst_ctx* ctx, const T* b, T* z1, T* z2, T* x, double* iface, int transpose,
+                  int mode, cudaStream_t st) {
+  for (auto& kv : ctx->cls) {
+    const int M = kv.first, nids = (int)kv.second.size();
+    if (ctx->big[M]) {
+      launch_big_solve<T>(M, ctx->d_slabs, ctx->d_cls[M], nids, ctx->cls_maxnb[M],
+                          (const T*)ctx->Fbig, (const T*)ctx->pack, b, z1, x, transpose, st);
+      if (mode == 1) launch_big_extract<T>(ctx->d_slabs, ctx->d_cls[M], nids, x, iface, st);
+    } else {
+      launch_local_solve<T>(M, ctx->d_slabs, ctx->d_cls[M], nids, ctx->cls_maxnb[M], (T*)ctx->F,
+                            (T*)ctx->B, (T*)ctx->Ft, (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, b, z1,
+                            z2, x, iface, transpose, mode, ctx->d_st, st);
+    }
+  }
+}
+
+// y = (I - K) x, or K x (bit 1 of mode), or the transposes (bit 0), with K applied through local
+// solves (Sec. 2.2, Eq. (defS)): K x = R_C A_j^{-1} (-A(I_j, J) x_J) per double slab;
+// K^T x = -A(J, I_j) A_j^{-T} R_C^T x_j.  Uses the matrix-free buffers only.
+template <typename T>
+void apply_matfree(ddst_ctx* ctx, const double* x, double* y, int mode, cudaStream_t st,
+                   const int* kdev, int64_t kstride) {
+  const int nslab = (int)ctx->slabs.size();
+  T* b = (T*)ctx->mf_b;
+  cudaMemsetAsync(b, 0, ctx->esz * ctx->tot_loc, st);
+  if (!(mode & 1)) {
+    launch_mf_rhs<T>(ctx->d_slabs, ctx->d_probs, nslab, (const T*)ctx->pack, x, kdev, kstride, b, st);
+    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, ctx->if_kx, 0, 1, st);
+  } else {
+    launch_mf_inject<T>(ctx->d_slabs, nslab, x, kdev, kstride, b, st);
+    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, nullptr, 1, 0, st);
+    cudaMemsetAsync(ctx->if_kx, 0, sizeof(double) * ctx->tot_if, st);
+    launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (const T*)ctx->pack,
+                                (const T*)ctx->mf_x, ctx->if_kx, st);
+  }
+  launch_mf_combine(ctx->tot_if, x, kdev, kstride, ctx->if_kx, y, (mode & 2) ? 1 : 0, st);
+}
+
 template <typename T>
 void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
                        cudaStream_t st = nullptr, const int* kdev = nullptr, int64_t kstride = 0) {
   if (!st) st = ctx->stream;
-  if (ctx->state == 3)
+  if (ctx->matfree)
+    apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
+  else if (ctx->state == 3)
     hodlr_apply<T>(ctx->hodlr, ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), x, y, transpose,
                    st, kdev, kstride);
   else
@@ -626,6 +744,7 @@ ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
   const int64_t n = ctx->tot_if;
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
   cudaGraph_t g = nullptr;
+  const long long l0 = launch_counter().load();
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
   // Arnoldi on K (bit 1 of the mode): same Krylov space as I - K, see launch_arnoldi_step
   apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose | 2, ctx->cap_stream, ctx->d_k, n);
@@ -633,6 +752,9 @@ ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
                       ctx->arn_ticket, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta,
                       ctx->resid, maxit, ctx->cap_stream);
   const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+  // launches recorded during capture run only when the graph is replayed: count them there
+  ctx->arn_graph_launches[key] = launch_counter().load() - l0;
+  launch_counter().fetch_sub(ctx->arn_graph_launches[key]);
   if (ec != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(ctx, ec, "graph capture");
@@ -687,7 +809,7 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   int k = 0;
   for (k = 1; k <= maxit; ++k) {
     CK(cudaGraphLaunch(graph, st));
-    note_launch(ctx->state == 3 ? 6 : 5);
+    note_launch((int)ctx->arn_graph_launches[transpose ? 1 : 0]);
     if (k % check == 0 || k == maxit) {
       CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -736,22 +858,14 @@ ddst_status dd_apply(ddst_ctx* ctx, const double* r, double* e, int* iters, doub
   T* lb = (T*)ctx->loc_b;
   // equivalent loads fhat_j = R_C A_j^{-1} r|Psi_j  (Sec. 2.2, Eq. (equilib1))
   launch_gather<T>(ctx->d_slabs, nslab, r, lb, st);
-  for (auto& kv : ctx->cls)
-    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
-                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
-                          ctx->if_fh, 0, 1, ctx->d_st, st);
+  local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, ctx->if_fh, 0, 1, st);
   CK(cudaGetLastError());
   // interface solve (I - K) u_Gamma = fhat
   ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 0, iters, relres);
   if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
   // volume reconstruction: local Dirichlet solves with the traces on Gamma_{j-1}, Gamma_{j+1}
   launch_add_iface_dirichlet<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, ctx->if_u, lb, st);
-  for (auto& kv : ctx->cls)
-    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
-                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
-                          nullptr, 0, 0, ctx->d_st, st);
+  local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, nullptr, 0, 0, st);
   launch_scatter<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->loc_x, e, 0, st);
   CK(cudaGetLastError());
   return s;
@@ -831,8 +945,10 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
     info->t_solve = ms;
-    info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems + ctx->pack_elems) * (int64_t)ctx->esz;
-    info->bytes_transfer = ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
+    info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems +
+                                    ctx->fac_big_elems + ctx->pack_elems) * (int64_t)ctx->esz;
+    info->bytes_transfer = ctx->matfree ? 0
+                           : ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
     info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
     info->fail_slab = -1;
     info->fail_block = -1;
@@ -857,11 +973,7 @@ ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, do
   const int nslab = (int)ctx->slabs.size();
   T* lb = (T*)ctx->loc_b;
   launch_gather_owned<T>(ctx->d_slabs, ctx->d_probs, nslab, r, lb, st);
-  for (auto& kv : ctx->cls)
-    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
-                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
-                          nullptr, 1, 0, ctx->d_st, st);
+  local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, nullptr, 1, 0, st);
   CK(cudaMemsetAsync(ctx->if_fh, 0, sizeof(double) * ctx->tot_if, st));
   launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, (T*)ctx->loc_x,
                               ctx->if_fh, st);
@@ -869,11 +981,7 @@ ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, do
   ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 1, iters, relres);
   if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
   launch_inject_center<T>(ctx->d_slabs, nslab, ctx->if_u, lb, st);
-  for (auto& kv : ctx->cls)
-    launch_local_solve<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                          ctx->cls_maxnb[kv.first], (T*)ctx->F, (T*)ctx->B, (T*)ctx->Ft,
-                          (T*)ctx->Bt, (T*)ctx->G, (T*)ctx->pack, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x,
-                          nullptr, 1, 0, ctx->d_st, st);
+  local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, nullptr, 1, 0, st);
   CK(cudaMemsetAsync(e, 0, sizeof(double) * ctx->tot_vol, st));
   launch_gather_T<T>(ctx->d_slabs, nslab, (T*)ctx->loc_x, e, st);
   CK(cudaGetLastError());
@@ -1007,6 +1115,7 @@ void ddst_options_default(ddst_options* opt) {
   opt->factor_chunks = 0;
   opt->factor_warmup = 0;
   opt->tensor_cores = 1;
+  opt->explicit_S = -1;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
@@ -1035,6 +1144,10 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx) {
 ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
   if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "ddst_build_transfer has not completed");
+  if (ctx->matfree && tol > 0.0)
+    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED,
+                "compression samples the explicit transfer operators; this context applies them "
+                "matrix-free (explicit_S = 0, or blocks larger than 128)");
   drop_graphs(ctx);
   if (!(tol > 0.0)) {
     ctx->hodlr.clear();
@@ -1117,6 +1230,8 @@ ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* 
   if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
   if (prob < 0 || prob >= ctx->nprob || !out || (side != -1 && side != 1))
     return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
+  if (ctx->matfree)
+    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED, "matrix-free context: no explicit transfer operators");
   const ProbDesc& P = ctx->probs[prob];
   if (j < 1 || j > P.nds) return fail(ctx, DDST_ERR_INVALID_ARG, "slab index out of range");
   const SlabDesc& s = ctx->slabs[P.slab0 + j - 1];

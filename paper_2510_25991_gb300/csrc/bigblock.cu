@@ -1,0 +1,670 @@
+// bigblock.cu -- factorization and local solves of double slabs whose dense blocks are large
+// (m > 128: every 3D double slab of a fine grid, and 2D slabs wider than 64 cells).
+//
+// Alg. 2 of the paper factors each local operator A_j(I_j, I_j) once (Sec. 2.5).  Ordered along y,
+// A_j is block tridiagonal with dense diagonal blocks D_k of size m = (2w-1)(n-1)^(dim-2) and
+// diagonal couplings L_k = diag(ell_k), U_k = diag(ups_k).  Here the one-sided block LU
+//     Sigma_1 = D_1,   Sigma_k = D_k - L_k Sigma_{k-1}^{-1} U_{k-1},   F_k = Sigma_k^{-1}
+// is computed with all slabs of a block-size class advancing together, one block row k at a time.
+// Each F_k is formed in place: Sigma_k is written into the slot of F_k and inverted there by a
+// blocked Gauss-Jordan elimination with 128-wide panels (no pivoting, as in the paper).  Per panel
+// q (rows/columns Q = 128q .. 128q+127):
+//   pivot    P = X(Q,Q), P^{-1} by the shared-memory Gauss-Jordan kernel; copies C = X(:,Q) and
+//            X(Q,:)^T are kept for the next two steps
+//   row      R = P^{-1} X(Q,:)  (stored transposed, R^T, and written back into X(Q,:));  R(:,Q) =
+//            P^{-1}, so that the update below also produces the column panel
+//   update   X(I,J) = X(I,J) - C(I,:) R(:,J) for I != Q, J != Q;  X(I,Q) = -C(I,:) P^{-1}
+// The row and update steps are dense products with K = 128: tcgen05 tensor-core kernels in the
+// FP32 path (3xTF32 with FP32 accumulation in tensor memory), FMA kernels in FP64 (and as an FP32
+// reference).  The local solves of a slab stream its F_k (forward and backward block sweeps,
+// one batched matrix-vector product per block row); A_j^{-T} uses the same factors transposed.
+#include "bgj.cuh"
+#include "kernels.cuh"
+#include "umma.cuh"
+
+namespace ddst {
+
+constexpr int BT = 128;  // panel width and output tile edge
+
+// ---------------------------------------------------------------------------------------------
+// Sigma_k = D_k - diag(ell_k) F_{k-1} diag(ups_{k-1}), written into the slot of F_k.
+// grid = (chunks, slabs of the class).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_sigma(const SlabDesc* __restrict__ slabs,
+                                                   const int* __restrict__ ids,
+                                                   const T* __restrict__ pack, T* __restrict__ F,
+                                                   int k) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  if (k > s.nb) return;
+  const int M = s.M;
+  T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
+  const T* Xp = F + s.fac_off + (int64_t)(k - 2) * M * M;  // used only for k > 1
+  const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
+  const T* pkp = pack + s.pack_off + (int64_t)(k - 2) * PK_NFIELDS * M;
+  const int64_t total = (int64_t)M * M;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / M), c = (int)(e - (int64_t)r * M);
+    T v = T(0);
+    if (r == c) {
+      v = pk[PK_DIAG * M + r];
+    } else if (r < s.m && c < s.m) {
+      // x neighbours sit p entries away (same z), z neighbours one entry away (same x column)
+      if (c == r - s.p) v = pk[PK_WEST * M + r];
+      else if (c == r + s.p) v = pk[PK_EAST * M + r];
+      else if (s.p > 1 && c == r - 1 && r % s.p != 0) v = pk[PK_ZLO * M + r];
+      else if (s.p > 1 && c == r + 1 && r % s.p != s.p - 1) v = pk[PK_ZHI * M + r];
+    }
+    if (k > 1) v -= pk[PK_SOUTH * M + r] * Xp[e] * pkp[PK_NORTH * M + c];
+    X[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pivot step of panel q.  grid = (M/128, slabs).  CTA q inverts P = X(Q,Q) in shared memory
+// (singular-pivot check against 1e3 eps |D_k|), writes X(Q,Q) = P^{-1}, Pinv = P^{-1},
+// RT(Q rows) = P^{-T} and C(Q rows) = P; every other CTA b copies its tiles C(B rows) = X(B,Q)
+// and XqT(B rows) = X(Q,B)^T.  Work buffers are per slab of the class: C, XqT, RT are M x 128,
+// Pinv is 128 x 128, all row-major.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_pivot(const SlabDesc* __restrict__ slabs,
+                                                   const int* __restrict__ ids,
+                                                   const T* __restrict__ pack, T* __restrict__ F,
+                                                   int k, int q, T* __restrict__ Cb,
+                                                   T* __restrict__ XqT, T* __restrict__ RT,
+                                                   T* __restrict__ Pinv, DevStatus* st) {
+  using G = BGJ<T, BT>;
+  constexpr int LD = G::LD;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* Xs = reinterpret_cast<T*>(smem_raw);
+  const int sid = ids[blockIdx.y];
+  const SlabDesc s = slabs[sid];
+  if (k > s.nb) return;
+  const int M = s.M;
+  T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
+  const int64_t wo = (int64_t)blockIdx.y * M * BT;
+  T* C = Cb + wo;
+  T* Xt = XqT + wo;
+  T* R = RT + wo;
+  T* Pi = Pinv + (int64_t)blockIdx.y * BT * BT;
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int64_t Q0 = (int64_t)q * BT, B0 = (int64_t)b * BT;
+  if (b != q) {
+    // C(B rows) = X(B, Q): straight row-segment copy
+    for (int e = tid; e < BT * BT; e += blockDim.x) {
+      const int i = e / BT, t = e - i * BT;
+      C[(B0 + i) * BT + t] = X[(B0 + i) * M + Q0 + t];
+    }
+    // XqT(B rows) = X(Q, B)^T through a padded shared tile
+    for (int e = tid; e < BT * BT; e += blockDim.x) {
+      const int t = e / BT, j = e - t * BT;
+      Xs[t * (BT + 1) + j] = X[(Q0 + t) * M + B0 + j];
+    }
+    __syncthreads();
+    for (int e = tid; e < BT * BT; e += blockDim.x) {
+      const int j = e / BT, t = e - j * BT;
+      Xt[(B0 + j) * BT + t] = Xs[t * (BT + 1) + j];
+    }
+    return;
+  }
+  T* Cp = Xs + BT * LD;
+  T* Rp = Cp + BT * (G::NB + 1);
+  T* thr = Rp + G::NB * LD;
+  const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
+  for (int e = tid; e < BT * BT; e += blockDim.x) {
+    const int i = e / BT, t = e - i * BT;
+    const T v = X[(Q0 + i) * M + Q0 + t];
+    Xs[i * LD + t] = v;
+    C[(Q0 + i) * BT + t] = v;
+  }
+  for (int i = tid; i < BT; i += blockDim.x) thr[i] = T(1e3) * Eps<T>::v * fabs(pk[PK_DIAG * M + Q0 + i]);
+  __syncthreads();
+  bgj_invert<T, BT>(Xs, Cp, Rp, thr, st, sid, k);
+  for (int e = tid; e < BT * BT; e += blockDim.x) {
+    const int i = e / BT, t = e - i * BT;
+    const T v = Xs[i * LD + t];
+    X[(Q0 + i) * M + Q0 + t] = v;
+    Pi[e] = v;
+    R[(Q0 + t) * BT + i] = v;  // RT rows of panel Q hold P^{-T}
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row and update steps as FMA products (FP64 path; FP32 reference for the tensor-core kernel).
+// Tile (I, J) of 128 x 128 with K = 128: acc(i, j) = sum_t A(i, t) Bt(j, t), A and Bt row-major
+// 128-wide panels.
+//   ROW    (grid = (M/128, 1, slabs), J != q): A = XqT(J rows), Bt = Pinv;  RT(J rows) = acc,
+//          X(Q, J) = acc^T
+//   UPDATE (grid = (M/128, M/128, slabs), I != q): A = C(I rows), Bt = RT(J rows);
+//          X(I, J) = [J != q] X(I, J) - acc
+// 256 threads, 8 x 8 outputs each, K staged through shared memory 16 at a time.
+// ---------------------------------------------------------------------------------------------
+enum { GJ_ROW = 0, GJ_UPDATE = 1 };
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_big_gemm_fma(const SlabDesc* __restrict__ slabs,
+                                                      const int* __restrict__ ids,
+                                                      T* __restrict__ F, int k, int q,
+                                                      const T* __restrict__ Cb,
+                                                      const T* __restrict__ XqT,
+                                                      T* __restrict__ RT,
+                                                      const T* __restrict__ Pinv) {
+  constexpr int KC = 16;
+  __shared__ T As[KC][BT + 4];
+  __shared__ T Bs[KC][BT + 4];
+  const SlabDesc s = slabs[ids[blockIdx.z]];
+  if (k > s.nb) return;
+  const int M = s.M;
+  const int J = blockIdx.x, I = MODE == GJ_ROW ? J : (int)blockIdx.y;
+  if (MODE == GJ_ROW ? (J == q) : (I == q)) return;
+  T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
+  const int64_t wo = (int64_t)blockIdx.z * M * BT;
+  const T* A = MODE == GJ_ROW ? XqT + wo + (int64_t)J * BT * BT : Cb + wo + (int64_t)I * BT * BT;
+  const T* Bt = MODE == GJ_ROW ? Pinv + (int64_t)blockIdx.z * BT * BT : RT + wo + (int64_t)J * BT * BT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[a][c] = T(0);
+  for (int t0 = 0; t0 < BT; t0 += KC) {
+    for (int e = tid; e < BT * KC; e += 256) {
+      const int r = e / KC, t = e - r * KC;
+      As[t][r] = A[r * BT + t0 + t];
+      Bs[t][r] = Bt[r * BT + t0 + t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < KC; ++t) {
+      T av[8], bv[8];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) av[a] = As[t][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bv[c] = Bs[t][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = ty + 16 * a;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = tx + 16 * c;
+      if (MODE == GJ_ROW) {
+        RT[wo + (J0 + i) * BT + j] = acc[a][c];
+        X[(Q0 + j) * M + J0 + i] = acc[a][c];
+      } else {
+        T* dst = X + (I0 + i) * M + J0 + j;
+        *dst = (J == q ? T(0) : *dst) - acc[a][c];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same two steps on the tensor cores (FP32 data, 3xTF32, FP32 accumulation in TMEM).
+// One 128 x 128 output tile per CTA, K = 128 in 8 stages of 16 through a 3-deep ring.
+// Roles: warps 0-3 load A and Bt rows (thread = row), split every value into TF32 hi/lo parts
+// (hi = rna(x), lo = rna(x - hi)) and store them in the canonical K-major layout; after the last
+// stage they become the epilogue (thread = TMEM lane = output row), staging 32 x 32 blocks
+// through shared memory so that every global access is a coalesced row segment.  Warp 4
+// allocates tensor memory and issues the MMAs: D += A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// Barriers: full[s] (128 producer arrivals after fence.proxy.async), empty[s] (MMA commit),
+// dready (last commit).  Every wait is bounded and also ends when another role raised the abort
+// flag; the tensor memory is freed on every path.
+// ---------------------------------------------------------------------------------------------
+struct GjTc {
+  static constexpr int KC = 16;
+  static constexpr int NST = 3;
+  static constexpr uint32_t PART = BT * KC * 4;       // one operand part (hi or lo) of a stage
+  static constexpr uint32_t STAGE = 4 * PART;         // A hi, A lo, B hi, B lo
+  static constexpr size_t RING = (size_t)NST * STAGE; // 96 KB
+  static constexpr size_t SMEM = RING + 8 * (2 * NST + 2) + 1024;
+  static constexpr int THREADS = 160;
+  static constexpr uint32_t TCOLS = 128;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(GjTc::THREADS, 2)
+    k_big_gemm_tc(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                  float* __restrict__ F, int k, int q, const float* __restrict__ Cb,
+                  const float* __restrict__ XqT, float* __restrict__ RT,
+                  const float* __restrict__ Pinv, DevStatus* st) {
+  using C = GjTc;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* ring = smem_raw;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + C::RING);
+  uint64_t* empty = full + C::NST;
+  uint64_t* dready = empty + C::NST;
+  uint64_t* done = dready + 1;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  volatile int* abort = &s_abort;
+
+  const int sid = ids[blockIdx.z];
+  const SlabDesc s = slabs[sid];
+  if (k > s.nb) return;
+  const int M = s.M;
+  const int J = blockIdx.x, I = MODE == GJ_ROW ? J : (int)blockIdx.y;
+  if (MODE == GJ_ROW ? (J == q) : (I == q)) return;
+  float* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
+  const int64_t wo = (int64_t)blockIdx.z * M * BT;
+  const float* A = MODE == GJ_ROW ? XqT + wo + (int64_t)J * BT * BT : Cb + wo + (int64_t)I * BT * BT;
+  const float* Bt = MODE == GJ_ROW ? Pinv + (int64_t)blockIdx.z * BT * BT : RT + wo + (int64_t)J * BT * BT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(C::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    for (int b = 0; b < C::NST; ++b) {
+      mbar_init(&full[b], BT);
+      mbar_init(&empty[b], 1);
+    }
+    mbar_init(dready, 1);
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  constexpr int NCH = BT / C::KC;
+
+  if (warp < 4) {
+    // ---------------------------------------------------------------- producer (thread = row)
+    const int r = tid;
+    bool ok = true;
+    for (int c = 0; c < NCH && ok; ++c) {
+      const int stage = c % C::NST;
+      if (c >= C::NST && !mbar_wait_ab(&empty[stage], ((c / C::NST) - 1) & 1, abort, st, sid, k)) {
+        ok = false;
+        break;
+      }
+      unsigned char* sb = ring + stage * C::STAGE;
+      const float4* ar = reinterpret_cast<const float4*>(A + (int64_t)r * BT + c * C::KC);
+      const float4* br = reinterpret_cast<const float4*>(Bt + (int64_t)r * BT + c * C::KC);
+      float4 va[C::KC / 4], vb[C::KC / 4];
+#pragma unroll
+      for (int u = 0; u < C::KC / 4; ++u) {
+        va[u] = ar[u];
+        vb[u] = br[u];
+      }
+#pragma unroll
+      for (int u = 0; u < C::KC / 4; ++u) {
+        const uint32_t o = umma_off(r, 4 * u, C::KC);
+        float4 h, l;
+        h.x = tf32_rna(va[u].x); l.x = tf32_rna(va[u].x - h.x);
+        h.y = tf32_rna(va[u].y); l.y = tf32_rna(va[u].y - h.y);
+        h.z = tf32_rna(va[u].z); l.z = tf32_rna(va[u].z - h.z);
+        h.w = tf32_rna(va[u].w); l.w = tf32_rna(va[u].w - h.w);
+        *reinterpret_cast<float4*>(sb + o) = h;
+        *reinterpret_cast<float4*>(sb + C::PART + o) = l;
+        h.x = tf32_rna(vb[u].x); l.x = tf32_rna(vb[u].x - h.x);
+        h.y = tf32_rna(vb[u].y); l.y = tf32_rna(vb[u].y - h.y);
+        h.z = tf32_rna(vb[u].z); l.z = tf32_rna(vb[u].z - h.z);
+        h.w = tf32_rna(vb[u].w); l.w = tf32_rna(vb[u].w - h.w);
+        *reinterpret_cast<float4*>(sb + 2 * C::PART + o) = h;
+        *reinterpret_cast<float4*>(sb + 3 * C::PART + o) = l;
+      }
+      fence_proxy_async();
+      mbar_arrive1(&full[stage]);
+    }
+    // ---------------------------------------------------------------- epilogue (thread = row)
+    bool go = ok && mbar_wait_ab(dready, 0, abort, st, sid, k);
+    go = __all_sync(0xffffffffu, go);  // tcgen05.ld is warp-collective
+    if (go) {
+      tc_fence_after();
+      // the ring is idle once the last MMA completed: reuse it for the 32 x 33 staging blocks
+      float* E = reinterpret_cast<float*>(ring) + warp * 32 * 33;
+      const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
+      for (int cc = 0; cc < BT / 32; ++cc) {
+        uint32_t v[32];
+        tmem_ld32_wait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) E[lane * 33 + e] = __uint_as_float(v[e]);
+        __syncwarp();
+        // E(rr, cl): output row warp*32 + rr, output column cc*32 + cl
+        if (MODE == GJ_ROW) {
+          for (int rr = 0; rr < 32; ++rr)
+            RT[wo + (J0 + warp * 32 + rr) * BT + cc * 32 + lane] = E[rr * 33 + lane];
+          for (int cl = 0; cl < 32; ++cl)
+            X[(Q0 + cc * 32 + cl) * M + J0 + warp * 32 + lane] = E[lane * 33 + cl];
+        } else {
+          for (int rr = 0; rr < 32; ++rr) {
+            float* dst = X + (I0 + warp * 32 + rr) * M + J0 + cc * 32 + lane;
+            *dst = (J == q ? 0.f : *dst) - E[rr * 33 + lane];
+          }
+        }
+        __syncwarp();
+      }
+    }
+  } else if (lane == 0) {
+    // ---------------------------------------------------------------- MMA issue (warp 4)
+    constexpr uint32_t IDESC = idesc_tf32(BT, BT);
+    for (int c = 0; c < NCH; ++c) {
+      const int stage = c % C::NST;
+      if (!mbar_wait_ab(&full[stage], (c / C::NST) & 1, abort, st, sid, k)) break;
+      tc_fence_after();
+      const uint32_t sa = smem_u32(ring + stage * C::STAGE);
+#pragma unroll
+      for (int ks = 0; ks < C::KC / 8; ++ks) {
+        const uint64_t ah = umma_desc(sa + ks * 256, 128, C::KC * 32);
+        const uint64_t al = umma_desc(sa + C::PART + ks * 256, 128, C::KC * 32);
+        const uint64_t bh = umma_desc(sa + 2 * C::PART + ks * 256, 128, C::KC * 32);
+        const uint64_t bl = umma_desc(sa + 3 * C::PART + ks * 256, 128, C::KC * 32);
+        mma_tf32_ss(tmem, ah, bh, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32_ss(tmem, ah, bl, IDESC, 1u);
+        mma_tf32_ss(tmem, al, bh, IDESC, 1u);
+      }
+      mma_commit(&empty[stage]);
+      if (c == NCH - 1) mma_commit(dready);
+    }
+    // every MMA issued has completed before the accumulator is released
+    mma_commit(done);
+    mbar_wait(done, 0, st, sid, -1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Local solves through the stored inverses F_k = Sigma_k^{-1}:
+//   A^{-1} b:  z_1 = b_1,  z_k = b_k - ell_k o (F_{k-1} z_{k-1});
+//              x_nb = F_nb z_nb,  x_k = F_k (z_k - ups_k o x_{k+1})
+//   A^{-T} b:  w_1 = F_1^T b_1,  w_k = F_k^T (b_k - ups_{k-1} o w_{k-1});
+//              x_nb = w_nb,  x_{k-1} = w_{k-1} - F_{k-1}^T (ell_k o x_k)
+// (o: elementwise product with the diagonal coupling).  One launch per block row and direction,
+// over all slabs of the class; step i of a backward sweep handles block nb - i of each slab.
+// ---------------------------------------------------------------------------------------------
+enum { SV_NFWD = 0, SV_NBWD = 1, SV_TFWD = 2, SV_TBWD = 3 };
+
+template <typename T>
+struct SolveStep {
+  int kf;                 // factor block applied (1-based; 0: nothing to do for this slab)
+  const T* P; const T* Q; const T* phi; T vs;   // v = P + vs phi o Q   (P, Q, phi may be NULL)
+  T* out; const T* R; const T* psi; T os;       // out = R + os psi o y (R, psi may be NULL)
+};
+
+template <typename T>
+__device__ __forceinline__ SolveStep<T> solve_step(const SlabDesc& s, const T* pack, const T* b,
+                                                   T* z, T* x, int mode, int i) {
+  SolveStep<T> d{};
+  const int M = s.M, nb = s.nb;
+  auto vec = [&](const T* base, int blk) { return base + s.loc_off + (int64_t)(blk - 1) * M; };
+  auto fld = [&](int blk, int f) { return pack + s.pack_off + (int64_t)(blk - 1) * PK_NFIELDS * M + f * M; };
+  if (mode == SV_NFWD) {                      // i = block k (2..nb)
+    const int kk = i;
+    if (kk < 2 || kk > nb) return d;
+    d.kf = kk - 1;
+    d.P = vec(kk == 2 ? b : z, kk - 1);
+    d.out = z + s.loc_off + (int64_t)(kk - 1) * M;
+    d.R = vec(b, kk); d.psi = fld(kk, PK_SOUTH); d.os = T(-1);
+  } else if (mode == SV_NBWD) {               // block k = nb - i
+    const int kk = nb - i;
+    if (kk < 1) return d;
+    d.kf = kk;
+    d.P = vec(kk == 1 ? b : z, kk);
+    if (kk < nb) { d.Q = vec(x, kk + 1); d.phi = fld(kk, PK_NORTH); d.vs = T(-1); }
+    d.out = x + s.loc_off + (int64_t)(kk - 1) * M;
+    d.os = T(1);
+  } else if (mode == SV_TFWD) {               // i = block k (1..nb)
+    const int kk = i;
+    if (kk < 1 || kk > nb) return d;
+    d.kf = kk;
+    d.P = vec(b, kk);
+    if (kk > 1) { d.Q = vec(z, kk - 1); d.phi = fld(kk - 1, PK_NORTH); d.vs = T(-1); }
+    d.out = z + s.loc_off + (int64_t)(kk - 1) * M;
+    d.os = T(1);
+  } else {                                    // SV_TBWD: block k = nb - i (>= 2) -> x_{k-1}
+    const int kk = nb - i;
+    if (kk < 2) return d;
+    d.kf = kk - 1;
+    d.Q = vec(i == 0 ? z : x, kk); d.phi = fld(kk, PK_SOUTH); d.vs = T(1);
+    d.out = x + s.loc_off + (int64_t)(kk - 2) * M;
+    d.R = vec(z, kk - 1); d.os = T(-1);
+  }
+  return d;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_v(const SolveStep<T>& d, int M, T* v) {
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    T a = d.P ? d.P[c] : T(0);
+    if (d.Q) a += d.vs * (d.phi ? d.phi[c] : T(1)) * d.Q[c];
+    v[c] = a;
+  }
+}
+
+// y = F v (row-major F): a warp takes 4 rows, lanes stride the columns with 16-byte loads.
+// grid = (M / 32, slabs of the class), 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_gemv_n(const SlabDesc* __restrict__ slabs,
+                                                    const int* __restrict__ ids,
+                                                    const T* __restrict__ F,
+                                                    const T* __restrict__ pack,
+                                                    const T* __restrict__ b, T* __restrict__ z,
+                                                    T* __restrict__ x, int mode, int i) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* v = reinterpret_cast<T*>(smem_raw);
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  const SolveStep<T> d = solve_step<T>(s, pack, b, z, x, mode, i);
+  if (d.kf == 0) return;
+  const int M = s.M;
+  load_v(d, M, v);
+  __syncthreads();
+  const T* Fk = F + s.fac_off + (int64_t)(d.kf - 1) * M * M;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = blockIdx.x * 32 + warp * 4;
+  constexpr int VW = 16 / sizeof(T);  // elements per 16-byte load
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int c = lane * VW; c < M; c += 32 * VW) {
+    T vv[VW];
+#pragma unroll
+    for (int e = 0; e < VW; ++e) vv[e] = v[c + e];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const V f = *reinterpret_cast<const V*>(Fk + (int64_t)(r0 + u) * M + c);
+      const T* fe = reinterpret_cast<const T*>(&f);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) acc[u] = fma(fe[e], vv[e], acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const T y = warp_sum(acc[u]);
+    if (lane == 0) {
+      const int r = r0 + u;
+      d.out[r] = (d.R ? d.R[r] : T(0)) + d.os * (d.psi ? d.psi[r] : T(1)) * y;
+    }
+  }
+}
+
+// y = F^T v: a CTA owns 64 columns (lanes hold two adjacent columns), its 8 warps split the rows
+// and combine their partial sums in shared memory.  grid = (M / 64, slabs of the class).
+template <typename T>
+__global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__ slabs,
+                                                    const int* __restrict__ ids,
+                                                    const T* __restrict__ F,
+                                                    const T* __restrict__ pack,
+                                                    const T* __restrict__ b, T* __restrict__ z,
+                                                    T* __restrict__ x, int mode, int i) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  const int M = s.M;
+  T* v = reinterpret_cast<T*>(smem_raw);
+  T* red = v + M;  // [8][64]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = blockIdx.x * 64 + 2 * lane;
+  if (mode == SV_TBWD && i == 0 && s.nb >= 1) {  // x_nb = w_nb (this CTA's columns)
+    T* xn = x + s.loc_off + (int64_t)(s.nb - 1) * M;
+    const T* wn = z + s.loc_off + (int64_t)(s.nb - 1) * M;
+    if (warp == 0) { xn[c0] = wn[c0]; xn[c0 + 1] = wn[c0 + 1]; }
+  }
+  const SolveStep<T> d = solve_step<T>(s, pack, b, z, x, mode, i);
+  if (d.kf == 0) return;
+  load_v(d, M, v);
+  __syncthreads();
+  const T* Fk = F + s.fac_off + (int64_t)(d.kf - 1) * M * M;
+  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+  int r = warp;
+  for (; r + 8 < M; r += 16) {
+    const T* p0 = Fk + (int64_t)r * M + c0;
+    const T* p1 = Fk + (int64_t)(r + 8) * M + c0;
+    const T f00 = p0[0], f01 = p0[1], f10 = p1[0], f11 = p1[1];
+    a0 = fma(f00, v[r], a0); a1 = fma(f01, v[r], a1);
+    b0 = fma(f10, v[r + 8], b0); b1 = fma(f11, v[r + 8], b1);
+  }
+  for (; r < M; r += 8) {
+    const T* p0 = Fk + (int64_t)r * M + c0;
+    a0 = fma(p0[0], v[r], a0); a1 = fma(p0[1], v[r], a1);
+  }
+  red[warp * 64 + 2 * lane] = a0 + b0;
+  red[warp * 64 + 2 * lane + 1] = a1 + b1;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    T y = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) y += red[w * 64 + threadIdx.x];
+    const int c = blockIdx.x * 64 + threadIdx.x;
+    d.out[c] = (d.R ? d.R[c] : T(0)) + d.os * (d.psi ? d.psi[c] : T(1)) * y;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static size_t pivot_smem() {
+  return BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
+}
+
+template <typename T>
+void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
+                            const T* pack, T* F, int k, T* Cb, T* XqT, T* RT, T* Pinv,
+                            bool tensor_cores, DevStatus* st, cudaStream_t s) {
+  const int nP = M / BT;
+  note_launch();
+  k_big_sigma<T><<<dim3(512, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, k);
+  const size_t psm = pivot_smem<T>();
+  raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T>), psm);
+  bool tc = false;
+  if constexpr (sizeof(T) == 4) {
+    tc = tensor_cores;
+    if (tc) {
+      raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_ROW>), GjTc::SMEM);
+      raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_UPDATE>), GjTc::SMEM);
+    }
+  }
+  for (int q = 0; q < nP; ++q) {
+    note_launch();
+    k_big_pivot<T><<<dim3(nP, nids), 256, psm, s>>>(d_slabs, d_ids, pack, F, k, q, Cb, XqT, RT,
+                                                    Pinv, st);
+    if (nP == 1) continue;
+    if constexpr (sizeof(T) == 4) {
+      if (tc) {
+        note_launch(2);
+        k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
+            d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
+        k_big_gemm_tc<GJ_UPDATE><<<dim3(nP, nP, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
+            d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
+        continue;
+      }
+    }
+    note_launch(2);
+    k_big_gemm_fma<T, GJ_ROW><<<dim3(nP, 1, nids), 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb, XqT,
+                                                                RT, Pinv);
+    k_big_gemm_fma<T, GJ_UPDATE><<<dim3(nP, nP, nids), 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb,
+                                                                    XqT, RT, Pinv);
+  }
+}
+
+template <typename T>
+void launch_big_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                      const T* F, const T* pack, const T* b, T* z, T* x, int transpose,
+                      cudaStream_t s) {
+  const size_t vsm = (size_t)M * sizeof(T);
+  const size_t tsm = (size_t)(M + 8 * 64) * sizeof(T);
+  raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemv_n<T>), vsm);
+  raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemv_t<T>), tsm);
+  if (!transpose) {
+    for (int k = 2; k <= max_nb; ++k) {
+      note_launch();
+      k_big_gemv_n<T><<<dim3(M / 32, nids), 256, vsm, s>>>(d_slabs, d_ids, F, pack, b, z, x,
+                                                           SV_NFWD, k);
+    }
+    for (int i = 0; i < max_nb; ++i) {
+      note_launch();
+      k_big_gemv_n<T><<<dim3(M / 32, nids), 256, vsm, s>>>(d_slabs, d_ids, F, pack, b, z, x,
+                                                           SV_NBWD, i);
+    }
+  } else {
+    for (int k = 1; k <= max_nb; ++k) {
+      note_launch();
+      k_big_gemv_t<T><<<dim3(M / 64, nids), 256, tsm, s>>>(d_slabs, d_ids, F, pack, b, z, x,
+                                                           SV_TFWD, k);
+    }
+    for (int i = 0; i < max_nb; ++i) {
+      note_launch();
+      k_big_gemv_t<T><<<dim3(M / 64, nids), 256, tsm, s>>>(d_slabs, d_ids, F, pack, b, z, x,
+                                                           SV_TBWD, i);
+    }
+  }
+}
+
+// Central rows of slab-local vectors of the listed slabs into the FP64 interface vector.
+template <typename T>
+__global__ void k_big_extract(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                              const T* __restrict__ loc, double* __restrict__ iface) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.ng;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / s.p) + 1, t = (int)(e % s.p);
+    iface[s.if_off + e] =
+        static_cast<double>(loc[s.loc_off + (int64_t)(k - 1) * s.M + (s.w - 1) * s.p + t]);
+  }
+}
+
+template <typename T>
+void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, const T* loc,
+                        double* iface, cudaStream_t s) {
+  note_launch();
+  k_big_extract<T><<<dim3(32, nids), 256, 0, s>>>(d_slabs, d_ids, loc, iface);
+}
+
+template void launch_big_factor_step<float>(int, const SlabDesc*, const int*, int, const float*,
+                                            float*, int, float*, float*, float*, float*, bool,
+                                            DevStatus*, cudaStream_t);
+template void launch_big_factor_step<double>(int, const SlabDesc*, const int*, int,
+                                             const double*, double*, int, double*, double*,
+                                             double*, double*, bool, DevStatus*, cudaStream_t);
+template void launch_big_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
+                                      const float*, const float*, float*, float*, int,
+                                      cudaStream_t);
+template void launch_big_solve<double>(int, const SlabDesc*, const int*, int, int, const double*,
+                                       const double*, const double*, double*, double*, int,
+                                       cudaStream_t);
+template void launch_big_extract<float>(const SlabDesc*, const int*, int, const float*, double*,
+                                        cudaStream_t);
+template void launch_big_extract<double>(const SlabDesc*, const int*, int, const double*, double*,
+                                         cudaStream_t);
+
+}  // namespace ddst

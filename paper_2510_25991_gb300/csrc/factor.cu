@@ -14,6 +14,7 @@
 // which lets multi-right-hand-side solves start from any block and single solves run their
 // two sweeps at the same time.  No pivoting (as in the paper); a pivot below
 // 1e3 * eps * |D_k(p,p)| reports DDST_ERR_SINGULAR with the slab and block.
+#include "bgj.cuh"
 #include "kernels.cuh"
 #include "umma.cuh"
 
@@ -35,130 +36,6 @@ __device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int 
     if (tc == tr + 1) return pk[PK_ZHI * M + r];
   }
   return T(0);
-}
-
-// ---------------------------------------------------------------------------------------------
-// Blocked Gauss-Jordan inversion in shared memory (block pivots of 16): the 16 x 16 pivot
-// block is inverted by warp 0 (warp-synchronous, no pivoting), then the pivot row panel
-// R = P^{-1} X(q, :), the column panel C = X(:, q) and the trailing update
-// X(i, j) -= C(i, :) R(:, j), X(i, q) = -C(i, :) P^{-1} run on all threads as small GEMMs.
-// Three block barriers per 16 pivots.  X has leading dimension LD = M + 4 (16-byte rows).
-// The trailing update runs over 4 x 4 patches distributed round-robin over the threads.
-// ---------------------------------------------------------------------------------------------
-template <typename T, int M>
-struct BGJ {
-  static constexpr int LD = M + 4;
-  static constexpr int NB = 16;
-  static constexpr size_t smem_elems = (size_t)M * LD + (size_t)M * (NB + 1) + (size_t)NB * LD;
-};
-
-template <typename T, int M>
-__device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp,
-                                           T* __restrict__ Rp, const T* __restrict__ thr,
-                                           DevStatus* st, int slab, int block) {
-  using G = BGJ<T, M>;
-  constexpr int LD = G::LD, NB = G::NB;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
-  for (int q0 = 0; q0 < M; q0 += NB) {
-    // (a) warp 0 inverts the pivot block in registers: lane owns row lane/2, columns
-    //     8*(lane&1)..+7; pivot rows and entries travel by warp shuffles (no barriers).
-    if (warp == 0) {
-      const int r = lane >> 1, h = lane & 1;
-      T* P = X + q0 * LD + q0;
-      T v[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = P[r * LD + 8 * h + e];
-      for (int pp = 0; pp < NB; ++pp) {
-        T prow[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) prow[e] = __shfl_sync(0xffffffffu, v[e], 2 * pp + h);
-        const int sel = pp & 7;
-        const T lo4 = (sel & 2) ? ((sel & 1) ? v[3] : v[2]) : ((sel & 1) ? v[1] : v[0]);
-        const T hi4 = (sel & 2) ? ((sel & 1) ? v[7] : v[6]) : ((sel & 1) ? v[5] : v[4]);
-        const T pe = (sel & 4) ? hi4 : lo4;
-        T piv = __shfl_sync(0xffffffffu, pe, 2 * pp + (pp >> 3));
-        const T fv = __shfl_sync(0xffffffffu, pe, 2 * r + (pp >> 3));
-        const T lim = thr[q0 + pp];
-        if (!(fabs(piv) > lim)) {
-          if (lane == 0) set_status(st, ST_SINGULAR, slab, block);
-          piv = (piv < T(0)) ? -lim : lim;
-          if (lim == T(0)) piv = T(1);
-        }
-        const T inv = T(1) / piv;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int c = 8 * h + e;
-          const T ps = (c == pp ? T(1) : prow[e]) * inv;
-          v[e] = (r == pp) ? ps : ((c == pp ? T(0) : v[e]) - fv * ps);
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) P[r * LD + 8 * h + e] = v[e];
-    }
-    __syncthreads();
-    // (b) column panel C = X(:, q) (old values; block rows unused) and row panel R = P^{-1} X(q, :)
-    for (int e = tid; e < M * NB; e += blockDim.x) {
-      const int i = e / NB, t = e - i * NB;
-      Cp[i * (NB + 1) + t] = X[i * LD + q0 + t];
-    }
-    for (int e = tid; e < NB * M; e += blockDim.x) {
-      const int t = e / M, j = e - t * M;
-      T acc = T(0);
-      if (j < q0 || j >= q0 + NB) {
-#pragma unroll
-        for (int s2 = 0; s2 < NB; ++s2) acc = fma(X[(q0 + t) * LD + q0 + s2], X[(q0 + s2) * LD + j], acc);
-      }
-      Rp[t * LD + j] = acc;
-    }
-    __syncthreads();
-    // (c) trailing update on 4 x 4 patches (patch index -> rows 4*pi.., columns 4*pj..)
-    for (int pidx = tid; pidx < (M / 4) * (M / 4); pidx += blockDim.x) {
-      {
-        const int i0 = (pidx / (M / 4)) * 4, j0 = (pidx % (M / 4)) * 4;
-        const bool in_i = (i0 >= q0 && i0 < q0 + NB), in_j = (j0 >= q0 && j0 < q0 + NB);
-        if (in_i && in_j) continue;
-        T acc[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-        if (in_i) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] = Rp[(i0 + a - q0) * LD + j0 + b];
-          continue;
-        }
-        // rows outside the pivot block: need C(i, :) and either R(:, j) or P^{-1}(:, j)
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {
-          T cv[4], rv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) cv[a] = Cp[(i0 + a) * (NB + 1) + t];
-          const T* src = in_j ? (X + (q0 + t) * LD + j0) : (Rp + t * LD + j0);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) rv[b] = src[b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(cv[a], rv[b], acc[a][b]);
-        }
-        if (in_j) {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] = -acc[a][b];
-        } else {
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) X[(i0 + a) * LD + j0 + b] -= acc[a][b];
-        }
-      }
-    }
-    __syncthreads();
-  }
 }
 
 // Writes X (shared, LD) as a row-major M x M block to `dst` and, if dstT, its transpose.

@@ -116,6 +116,33 @@ void launch_normalize_start(const double* x, const double* nrm2, double* out, in
 void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double* y,
                      cudaStream_t st);
 
+// bigblock.cu: large dense blocks (M a multiple of 128).  One block row k of the one-sided block
+// LU of every slab in the class (Sigma_k formed in the slot of F_k, inverted there by 128-wide
+// Gauss-Jordan panels); work buffers Cb, XqT, RT (nids x M x 128) and Pinv (nids x 128 x 128).
+template <typename T>
+void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
+                            const T* pack, T* F, int k, T* Cb, T* XqT, T* RT, T* Pinv,
+                            bool tensor_cores, DevStatus* st, cudaStream_t s);
+// Local solve x = A^{-1} b (transpose 0) or A^{-T} b (transpose 1) of every slab of the class;
+// z is a slab-local temporary.
+template <typename T>
+void launch_big_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids, int max_nb,
+                      const T* F, const T* pack, const T* b, T* z, T* x, int transpose,
+                      cudaStream_t s);
+template <typename T>
+void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, const T* loc,
+                        double* iface, cudaStream_t s);
+
+// matfree.cu: the interface operator through local solves (x indexed by kdev as above)
+template <typename T>
+void launch_mf_rhs(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab, const T* pack,
+                   const double* x, const int* kdev, int64_t kstride, T* loc, cudaStream_t st);
+template <typename T>
+void launch_mf_inject(const SlabDesc* d_slabs, int nslab, const double* x, const int* kdev,
+                      int64_t kstride, T* loc, cudaStream_t st);
+void launch_mf_combine(int64_t n, const double* x, const int* kdev, int64_t kstride,
+                       const double* kx, double* y, int konly, cudaStream_t st);
+
 // grad.cu: dL/dg and dL/da from lambda and u (nodal outputs accumulated; zero them first)
 void launch_gradients(const ProbDesc* d_probs, int nprob, const double* a, const double* g,
                       const double* u, const double* lam, double* dLdg, double* dLda,

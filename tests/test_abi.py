@@ -56,7 +56,7 @@ def _square(n):
     (dict(dim=2, n=10, w=3), "n % w == 0"),          # slab width does not divide n
     (dict(dim=2, n=10, w=10), "n/w >= 2"),           # a single slab has no interface
     (dict(dim=4, n=10, w=5), "dim must be 2 or 3"),
-    (dict(dim=2, n=2048, w=128), "exceeds 128"),     # block 2w - 1 = 255 above the FP32 limit
+    (dict(dim=3, n=256, w=32), "exceeds 8192"),      # block 63 * 255 above the large-block limit
 ])
 def test_setup_rejects_bad_problems_without_gpu(problem, message):
     """Argument checks run on the host before any device work and leave a message."""
@@ -72,9 +72,13 @@ def test_setup_rejects_bad_options_and_lists_without_gpu():
     ok = dict(dim=2, n=16, w=4, a=_square(16))
     with pytest.raises(D.DDSTError, match="precision must be"):
         D.ddst_setup_batch([ok], D.ddst_options_default(precision=7))
-    with pytest.raises(D.DDSTError, match="block size"):  # FP64 kernels stop at 64-row blocks
-        D.ddst_setup_batch([dict(dim=2, n=80, w=40, a=_square(80))],
-                           D.ddst_options_default(precision=0))
+    # explicit transfer operators are formed only for blocks the single-CTA kernels take
+    with pytest.raises(D.DDSTError, match="explicit transfer operators need"):
+        D.ddst_setup_batch([dict(dim=2, n=512, w=128, a=_square(512))],
+                           D.ddst_options_default(explicit_S=1))
+    with pytest.raises(D.DDSTError, match="explicit transfer operators need"):
+        D.ddst_setup_batch([dict(dim=2, n=160, w=40, a=_square(160))],
+                           D.ddst_options_default(precision=0, explicit_S=1))
     with pytest.raises(D.DDSTError, match="a is NULL"):
         D.ddst_setup_batch([dict(ok, a=None)])
     with pytest.raises(D.DDSTError, match="bad problem list"):
