@@ -480,12 +480,14 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     AL(d, sizeof(int) * kv.second.size());
     ctx->d_cls[kv.first] = d;
     if (ctx->big[kv.first]) {
+      // panels of 128 columns per slab: plain (FMA path) or split into TF32 hi/lo parts
+      // (tensor-core path), hence twice the plain size
       ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
-      const size_t panel = es * kv.second.size() * (size_t)kv.first * 128;
+      const size_t panel = 2 * es * kv.second.size() * (size_t)kv.first * 128;
       AL(bw.C, panel);
       AL(bw.XqT, panel);
       AL(bw.RT, panel);
-      AL(bw.Pinv, es * kv.second.size() * 128 * 128);
+      AL(bw.Pinv, 2 * es * kv.second.size() * 128 * 128);
     }
   }
   if (ctx->matfree) {

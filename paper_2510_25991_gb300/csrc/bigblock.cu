@@ -62,14 +62,49 @@ __global__ void __launch_bounds__(256) k_big_sigma(const SlabDesc* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------------------------
-// Pivot step of panel q.  grid = (M/128, slabs).  CTA q inverts P = X(Q,Q) in shared memory
-// (singular-pivot check against 1e3 eps |D_k|), writes X(Q,Q) = P^{-1}, Pinv = P^{-1},
-// RT(Q rows) = P^{-T} and C(Q rows) = P; every other CTA b copies its tiles C(B rows) = X(B,Q)
-// and XqT(B rows) = X(Q,B)^T.  Work buffers are per slab of the class: C, XqT, RT are M x 128,
-// Pinv is 128 x 128, all row-major.
+// Operand tiles of the tensor-core steps are stored once, already split into TF32 parts
+// (hi = rna(x), lo = rna(x - hi)) in the canonical K-major layout, chunk-major: element (r, k) of
+// a 128 x 128 tile (r: output row, k: contraction index) sits at float offset
+//     (k / 16) * 2048 + umma_off(r, k % 16, 16) / 4
+// of the hi part, and 16384 floats further in the lo part.  One 16-wide K chunk of one part is a
+// contiguous 8 KB block, so the MMA kernels load their operands with plain bulk copies.
 // ---------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_big_pivot(const SlabDesc* __restrict__ slabs,
+constexpr int SPLIT_TILE = 2 * BT * BT;  // floats of one split tile (hi + lo)
+
+__device__ __forceinline__ int split_off(int r, int k) {
+  return (k >> 4) * 2048 + (int)(umma_off(r, k & 15, 16) >> 2);
+}
+
+// Element (r, k) read from shared memory at src[r * ldr + k * ldk].
+__device__ __forceinline__ void store_split_tile(const float* __restrict__ src, int ldr, int ldk,
+                                                 float* __restrict__ dst) {
+  for (int e = threadIdx.x; e < BT * (BT / 4); e += blockDim.x) {
+    const int r = e % BT, k = 4 * (e / BT);
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = src[r * ldr + (k + u) * ldk];
+    float4 h, l;
+    h.x = tf32_rna(x[0]); l.x = tf32_rna(x[0] - h.x);
+    h.y = tf32_rna(x[1]); l.y = tf32_rna(x[1] - h.y);
+    h.z = tf32_rna(x[2]); l.z = tf32_rna(x[2] - h.z);
+    h.w = tf32_rna(x[3]); l.w = tf32_rna(x[3] - h.w);
+    const int o = split_off(r, k);
+    *reinterpret_cast<float4*>(dst + o) = h;
+    *reinterpret_cast<float4*>(dst + BT * BT + o) = l;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pivot step of panel q.  grid = (M/128, slabs).  CTA q inverts P = X(Q,Q) in shared memory
+// (singular-pivot check against 1e3 eps |D_k|) and writes X(Q,Q) = P^{-1}; every other CTA b
+// copies the tiles X(B,Q) and X(Q,B) of the column and row panels.  Work buffers are per slab of
+// the class.  FMA path (plain row-major): C = X(:,Q) (M x 128), XqT = X(Q,:)^T (M x 128),
+// Pinv = P^{-1} (128 x 128), RT(Q rows) = P^{-T}.  Tensor-core path (SPLIT, split tiles): the
+// same operands as split tiles, C tile b = X(B,Q), XqT tile b = X(Q,B)^T, Pinv = P^{-1} and RT
+// tile q = P^{-T}, and C tile q = P.
+// ---------------------------------------------------------------------------------------------
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(512) k_big_pivot(const SlabDesc* __restrict__ slabs,
                                                    const int* __restrict__ ids,
                                                    const T* __restrict__ pack, T* __restrict__ F,
                                                    int k, int q, T* __restrict__ Cb,
@@ -77,36 +112,46 @@ __global__ void __launch_bounds__(256) k_big_pivot(const SlabDesc* __restrict__ 
                                                    T* __restrict__ Pinv, DevStatus* st) {
   using G = BGJ<T, BT>;
   constexpr int LD = G::LD;
+  constexpr int LS = BT + 1;  // staging tiles: conflict-free row and column reads
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* Xs = reinterpret_cast<T*>(smem_raw);
   const int sid = ids[blockIdx.y];
   const SlabDesc s = slabs[sid];
   if (k > s.nb) return;
-  const int M = s.M;
+  const int M = s.M, nP = M / BT;
   T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
-  const int64_t wo = (int64_t)blockIdx.y * M * BT;
-  T* C = Cb + wo;
-  T* Xt = XqT + wo;
-  T* R = RT + wo;
-  T* Pi = Pinv + (int64_t)blockIdx.y * BT * BT;
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t Q0 = (int64_t)q * BT, B0 = (int64_t)b * BT;
+  // per-slab work buffers: plain M x 128 panels, or nP split tiles
+  const int64_t wo = SPLIT ? (int64_t)blockIdx.y * nP * SPLIT_TILE : (int64_t)blockIdx.y * M * BT;
+  T* C = Cb + wo;
+  T* Xt = XqT + wo;
+  T* R = RT + wo;
+  T* Pi = Pinv + (int64_t)blockIdx.y * (SPLIT ? SPLIT_TILE : BT * BT);
   if (b != q) {
-    // C(B rows) = X(B, Q): straight row-segment copy
-    for (int e = tid; e < BT * BT; e += blockDim.x) {
-      const int i = e / BT, t = e - i * BT;
-      C[(B0 + i) * BT + t] = X[(B0 + i) * M + Q0 + t];
-    }
-    // XqT(B rows) = X(Q, B)^T through a padded shared tile
-    for (int e = tid; e < BT * BT; e += blockDim.x) {
-      const int t = e / BT, j = e - t * BT;
-      Xs[t * (BT + 1) + j] = X[(Q0 + t) * M + B0 + j];
-    }
-    __syncthreads();
-    for (int e = tid; e < BT * BT; e += blockDim.x) {
-      const int j = e / BT, t = e - j * BT;
-      Xt[(B0 + j) * BT + t] = Xs[t * (BT + 1) + j];
+    if constexpr (SPLIT) {
+      float* S1 = reinterpret_cast<float*>(Xs);  // X(B, Q): (r = i, k = t)
+      float* S2 = S1 + BT * LS;                  // X(Q, B): (t, j)
+      for (int e = tid; e < BT * BT; e += blockDim.x) {
+        const int i = e / BT, t = e - i * BT;
+        S1[i * LS + t] = X[(B0 + i) * M + Q0 + t];
+        S2[i * LS + t] = X[(Q0 + i) * M + B0 + t];
+      }
+      __syncthreads();
+      store_split_tile(S1, LS, 1, C + (int64_t)b * SPLIT_TILE);
+      store_split_tile(S2, 1, LS, Xt + (int64_t)b * SPLIT_TILE);  // (r = j, k = t) = X(Q0+t, B0+j)
+    } else {
+      for (int e = tid; e < BT * BT; e += blockDim.x) {
+        const int i = e / BT, t = e - i * BT;
+        C[(B0 + i) * BT + t] = X[(B0 + i) * M + Q0 + t];
+        Xs[i * LS + t] = X[(Q0 + i) * M + B0 + t];
+      }
+      __syncthreads();
+      for (int e = tid; e < BT * BT; e += blockDim.x) {
+        const int j = e / BT, t = e - j * BT;
+        Xt[(B0 + j) * BT + t] = Xs[t * LS + j];
+      }
     }
     return;
   }
@@ -116,19 +161,30 @@ __global__ void __launch_bounds__(256) k_big_pivot(const SlabDesc* __restrict__ 
   const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
   for (int e = tid; e < BT * BT; e += blockDim.x) {
     const int i = e / BT, t = e - i * BT;
-    const T v = X[(Q0 + i) * M + Q0 + t];
-    Xs[i * LD + t] = v;
-    C[(Q0 + i) * BT + t] = v;
+    Xs[i * LD + t] = X[(Q0 + i) * M + Q0 + t];
   }
   for (int i = tid; i < BT; i += blockDim.x) thr[i] = T(1e3) * Eps<T>::v * fabs(pk[PK_DIAG * M + Q0 + i]);
+  __syncthreads();
+  if constexpr (SPLIT) {
+    store_split_tile(reinterpret_cast<const float*>(Xs), LD, 1, C + (int64_t)q * SPLIT_TILE);
+  } else {
+    for (int e = tid; e < BT * BT; e += blockDim.x) C[(Q0 + e / BT) * BT + e % BT] = Xs[(e / BT) * LD + e % BT];
+  }
   __syncthreads();
   bgj_invert<T, BT>(Xs, Cp, Rp, thr, st, sid, k);
   for (int e = tid; e < BT * BT; e += blockDim.x) {
     const int i = e / BT, t = e - i * BT;
-    const T v = Xs[i * LD + t];
-    X[(Q0 + i) * M + Q0 + t] = v;
-    Pi[e] = v;
-    R[(Q0 + t) * BT + i] = v;  // RT rows of panel Q hold P^{-T}
+    X[(Q0 + i) * M + Q0 + t] = Xs[i * LD + t];
+  }
+  if constexpr (SPLIT) {
+    store_split_tile(reinterpret_cast<const float*>(Xs), LD, 1, Pi);                          // P^{-1}
+    store_split_tile(reinterpret_cast<const float*>(Xs), 1, LD, R + (int64_t)q * SPLIT_TILE);  // P^{-T}
+  } else {
+    for (int e = tid; e < BT * BT; e += blockDim.x) {
+      const int i = e / BT, t = e - i * BT;
+      Pi[e] = Xs[i * LD + t];
+      R[(Q0 + i) * BT + t] = Xs[t * LD + i];  // RT rows of panel Q hold P^{-T}
+    }
   }
 }
 
@@ -192,6 +248,17 @@ __global__ void __launch_bounds__(256) k_big_gemm_fma(const SlabDesc* __restrict
     __syncthreads();
   }
   const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
+  if (MODE == GJ_UPDATE && J != q) {  // old values first: 64 independent loads in flight
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[a][c] = X[(I0 + ty + 16 * a) * M + J0 + tx + 16 * c] - acc[a][c];
+  } else if (MODE == GJ_UPDATE) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[a][c] = -acc[a][c];
+  }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int i = ty + 16 * a;
@@ -202,42 +269,44 @@ __global__ void __launch_bounds__(256) k_big_gemm_fma(const SlabDesc* __restrict
         RT[wo + (J0 + i) * BT + j] = acc[a][c];
         X[(Q0 + j) * M + J0 + i] = acc[a][c];
       } else {
-        T* dst = X + (I0 + i) * M + J0 + j;
-        *dst = (J == q ? T(0) : *dst) - acc[a][c];
+        X[(I0 + i) * M + J0 + j] = acc[a][c];
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// The same two steps on the tensor cores (FP32 data, 3xTF32, FP32 accumulation in TMEM).
-// One 128 x 128 output tile per CTA, K = 128 in 8 stages of 16 through a 3-deep ring.
-// Roles: warps 0-3 load A and Bt rows (thread = row), split every value into TF32 hi/lo parts
-// (hi = rna(x), lo = rna(x - hi)) and store them in the canonical K-major layout; after the last
-// stage they become the epilogue (thread = TMEM lane = output row), staging 32 x 32 blocks
-// through shared memory so that every global access is a coalesced row segment.  Warp 4
-// allocates tensor memory and issues the MMAs: D += A_hi B_hi + A_hi B_lo + A_lo B_hi.
-// Barriers: full[s] (128 producer arrivals after fence.proxy.async), empty[s] (MMA commit),
-// dready (last commit).  Every wait is bounded and also ends when another role raised the abort
-// flag; the tensor memory is freed on every path.
+// The same two steps on the tensor cores (FP32 data, 3xTF32, FP32 accumulation in TMEM), with
+// the operands as split tiles (see above).  One 128 x 128 output tile per CTA, K = 128 in 8
+// chunks of 16 through a 3-deep ring of bulk copies (A hi, A lo, B hi, B lo: 32 KB a chunk).
+//   ROW    A = XqT tile J, B = Pinv:  RT tile J (split) = acc, X(Q, J) = acc^T
+//   UPDATE A = C tile I,  B = RT tile J:  X(I, J) = [J != q] X(I, J) - acc
+// Roles: warp 4 lane 0 issues the bulk copies, warp 5 allocates tensor memory and issues the
+// MMAs, D += A_hi B_hi + A_hi B_lo + A_lo B_hi; warps 0-3 are the epilogue (thread = TMEM lane =
+// output row): they load the old values of their rows before the accumulator is ready and stage
+// 32 x 32 blocks through shared memory so that every global row access is coalesced.
+// Barriers: full[s] (copies landed), empty[s] (MMA commit), dready (last commit).  Every wait is
+// bounded and also ends when another role raised the abort flag; copies in flight are drained
+// and the tensor memory is freed on every path.
 // ---------------------------------------------------------------------------------------------
 struct GjTc {
   static constexpr int KC = 16;
+  static constexpr int NCH = BT / KC;
   static constexpr int NST = 3;
-  static constexpr uint32_t PART = BT * KC * 4;       // one operand part (hi or lo) of a stage
+  static constexpr uint32_t PART = BT * KC * 4;       // one operand part (hi or lo) of a chunk
   static constexpr uint32_t STAGE = 4 * PART;         // A hi, A lo, B hi, B lo
   static constexpr size_t RING = (size_t)NST * STAGE; // 96 KB
   static constexpr size_t SMEM = RING + 8 * (2 * NST + 2) + 1024;
-  static constexpr int THREADS = 160;
+  static constexpr int THREADS = 192;
   static constexpr uint32_t TCOLS = 128;
 };
 
 template <int MODE>
 __global__ void __launch_bounds__(GjTc::THREADS, 2)
     k_big_gemm_tc(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
-                  float* __restrict__ F, int k, int q, const float* __restrict__ Cb,
-                  const float* __restrict__ XqT, float* __restrict__ RT,
-                  const float* __restrict__ Pinv, DevStatus* st) {
+                  float* __restrict__ F, int k, int q, const float* __restrict__ Cs,
+                  const float* __restrict__ XqTs, float* __restrict__ RTs,
+                  const float* __restrict__ Pis, DevStatus* st) {
   using C = GjTc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = smem_raw;
@@ -252,16 +321,16 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   const int sid = ids[blockIdx.z];
   const SlabDesc s = slabs[sid];
   if (k > s.nb) return;
-  const int M = s.M;
+  const int M = s.M, nP = M / BT;
   const int J = blockIdx.x, I = MODE == GJ_ROW ? J : (int)blockIdx.y;
   if (MODE == GJ_ROW ? (J == q) : (I == q)) return;
   float* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
-  const int64_t wo = (int64_t)blockIdx.z * M * BT;
-  const float* A = MODE == GJ_ROW ? XqT + wo + (int64_t)J * BT * BT : Cb + wo + (int64_t)I * BT * BT;
-  const float* Bt = MODE == GJ_ROW ? Pinv + (int64_t)blockIdx.z * BT * BT : RT + wo + (int64_t)J * BT * BT;
+  const int64_t wo = (int64_t)blockIdx.z * nP * SPLIT_TILE;
+  const float* A = MODE == GJ_ROW ? XqTs + wo + (int64_t)J * SPLIT_TILE : Cs + wo + (int64_t)I * SPLIT_TILE;
+  const float* B = MODE == GJ_ROW ? Pis + (int64_t)blockIdx.z * SPLIT_TILE : RTs + wo + (int64_t)J * SPLIT_TILE;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 4) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&s_tmem)),
                  "r"(C::TCOLS)
@@ -271,7 +340,7 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   if (tid == 0) {
     s_abort = 0;
     for (int b = 0; b < C::NST; ++b) {
-      mbar_init(&full[b], BT);
+      mbar_init(&full[b], 1);
       mbar_init(&empty[b], 1);
     }
     mbar_init(dready, 1);
@@ -282,80 +351,96 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  constexpr int NCH = BT / C::KC;
 
   if (warp < 4) {
-    // ---------------------------------------------------------------- producer (thread = row)
-    const int r = tid;
-    bool ok = true;
-    for (int c = 0; c < NCH && ok; ++c) {
-      const int stage = c % C::NST;
-      if (c >= C::NST && !mbar_wait_ab(&empty[stage], ((c / C::NST) - 1) & 1, abort, st, sid, k)) {
-        ok = false;
-        break;
-      }
-      unsigned char* sb = ring + stage * C::STAGE;
-      const float4* ar = reinterpret_cast<const float4*>(A + (int64_t)r * BT + c * C::KC);
-      const float4* br = reinterpret_cast<const float4*>(Bt + (int64_t)r * BT + c * C::KC);
-      float4 va[C::KC / 4], vb[C::KC / 4];
-#pragma unroll
-      for (int u = 0; u < C::KC / 4; ++u) {
-        va[u] = ar[u];
-        vb[u] = br[u];
-      }
-#pragma unroll
-      for (int u = 0; u < C::KC / 4; ++u) {
-        const uint32_t o = umma_off(r, 4 * u, C::KC);
-        float4 h, l;
-        h.x = tf32_rna(va[u].x); l.x = tf32_rna(va[u].x - h.x);
-        h.y = tf32_rna(va[u].y); l.y = tf32_rna(va[u].y - h.y);
-        h.z = tf32_rna(va[u].z); l.z = tf32_rna(va[u].z - h.z);
-        h.w = tf32_rna(va[u].w); l.w = tf32_rna(va[u].w - h.w);
-        *reinterpret_cast<float4*>(sb + o) = h;
-        *reinterpret_cast<float4*>(sb + C::PART + o) = l;
-        h.x = tf32_rna(vb[u].x); l.x = tf32_rna(vb[u].x - h.x);
-        h.y = tf32_rna(vb[u].y); l.y = tf32_rna(vb[u].y - h.y);
-        h.z = tf32_rna(vb[u].z); l.z = tf32_rna(vb[u].z - h.z);
-        h.w = tf32_rna(vb[u].w); l.w = tf32_rna(vb[u].w - h.w);
-        *reinterpret_cast<float4*>(sb + 2 * C::PART + o) = h;
-        *reinterpret_cast<float4*>(sb + 3 * C::PART + o) = l;
-      }
-      fence_proxy_async();
-      mbar_arrive1(&full[stage]);
-    }
     // ---------------------------------------------------------------- epilogue (thread = row)
-    bool go = ok && mbar_wait_ab(dready, 0, abort, st, sid, k);
+    const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
+    // UPDATE: the old values of this warp's 32 rows, one 32-column block at a time, loaded
+    // ahead (the first block while the MMAs run), 32 independent loads in flight per lane
+    float old[32];
+    const bool keep = MODE == GJ_UPDATE && J != q;
+    float* xrow = X + (I0 + warp * 32) * M + J0 + lane;  // row warp*32 + rr at + rr * M
+    if (keep) {
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) old[rr] = xrow[(int64_t)rr * M];
+    }
+    bool go = mbar_wait_ab(dready, 0, abort, st, sid, k);
     go = __all_sync(0xffffffffu, go);  // tcgen05.ld is warp-collective
     if (go) {
       tc_fence_after();
       // the ring is idle once the last MMA completed: reuse it for the 32 x 33 staging blocks
       float* E = reinterpret_cast<float*>(ring) + warp * 32 * 33;
-      const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
+#pragma unroll 1
       for (int cc = 0; cc < BT / 32; ++cc) {
         uint32_t v[32];
         tmem_ld32_wait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+        if (MODE == GJ_ROW) {
+          // RT tile J (split): row i = warp*32 + lane, contraction index cc*32 + e
+          float* rt = RTs + wo + (int64_t)J * SPLIT_TILE;
+          const int i = warp * 32 + lane;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            float4 h, l;
+            const float x0 = __uint_as_float(v[4 * g]), x1 = __uint_as_float(v[4 * g + 1]);
+            const float x2 = __uint_as_float(v[4 * g + 2]), x3 = __uint_as_float(v[4 * g + 3]);
+            h.x = tf32_rna(x0); l.x = tf32_rna(x0 - h.x);
+            h.y = tf32_rna(x1); l.y = tf32_rna(x1 - h.y);
+            h.z = tf32_rna(x2); l.z = tf32_rna(x2 - h.z);
+            h.w = tf32_rna(x3); l.w = tf32_rna(x3 - h.w);
+            const int o = split_off(i, cc * 32 + 4 * g);
+            *reinterpret_cast<float4*>(rt + o) = h;
+            *reinterpret_cast<float4*>(rt + BT * BT + o) = l;
+          }
+        }
 #pragma unroll
         for (int e = 0; e < 32; ++e) E[lane * 33 + e] = __uint_as_float(v[e]);
         __syncwarp();
         // E(rr, cl): output row warp*32 + rr, output column cc*32 + cl
         if (MODE == GJ_ROW) {
-          for (int rr = 0; rr < 32; ++rr)
-            RT[wo + (J0 + warp * 32 + rr) * BT + cc * 32 + lane] = E[rr * 33 + lane];
+#pragma unroll 8
           for (int cl = 0; cl < 32; ++cl)
             X[(Q0 + cc * 32 + cl) * M + J0 + warp * 32 + lane] = E[lane * 33 + cl];
         } else {
-          for (int rr = 0; rr < 32; ++rr) {
-            float* dst = X + (I0 + warp * 32 + rr) * M + J0 + cc * 32 + lane;
-            *dst = (J == q ? 0.f : *dst) - E[rr * 33 + lane];
+          float nxt[32];
+          if (keep && cc + 1 < BT / 32) {
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) nxt[rr] = xrow[(int64_t)rr * M + (cc + 1) * 32];
+          }
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr)
+            xrow[(int64_t)rr * M + cc * 32] = (keep ? old[rr] : 0.f) - E[rr * 33 + lane];
+          if (keep && cc + 1 < BT / 32) {
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) old[rr] = nxt[rr];
           }
         }
         __syncwarp();
       }
     }
+  } else if (warp == 4) {
+    // ---------------------------------------------------------------- bulk-copy producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int c = 0; c < C::NCH; ++c) {
+        const int stage = c % C::NST;
+        if (c >= C::NST && !mbar_wait_ab(&empty[stage], ((c / C::NST) - 1) & 1, abort, st, sid, k))
+          break;
+        unsigned char* sb = ring + stage * C::STAGE;
+        mbar_arrive_expect_tx(&full[stage], C::STAGE);
+        bulk_g2s(sb, A + c * 2048, C::PART, &full[stage]);
+        bulk_g2s(sb + C::PART, A + BT * BT + c * 2048, C::PART, &full[stage]);
+        bulk_g2s(sb + 2 * C::PART, B + c * 2048, C::PART, &full[stage]);
+        bulk_g2s(sb + 3 * C::PART, B + BT * BT + c * 2048, C::PART, &full[stage]);
+        ++issued;
+      }
+      // no copy may still target this CTA's shared memory when it exits
+      for (int c = issued > C::NST ? issued - C::NST : 0; c < issued; ++c)
+        mbar_wait(&full[c % C::NST], (c / C::NST) & 1, st, sid, -1);
+    }
   } else if (lane == 0) {
-    // ---------------------------------------------------------------- MMA issue (warp 4)
+    // ---------------------------------------------------------------- MMA issue (warp 5)
     constexpr uint32_t IDESC = idesc_tf32(BT, BT);
-    for (int c = 0; c < NCH; ++c) {
+    for (int c = 0; c < C::NCH; ++c) {
       const int stage = c % C::NST;
       if (!mbar_wait_ab(&full[stage], (c / C::NST) & 1, abort, st, sid, k)) break;
       tc_fence_after();
@@ -371,7 +456,7 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
         mma_tf32_ss(tmem, al, bh, IDESC, 1u);
       }
       mma_commit(&empty[stage]);
-      if (c == NCH - 1) mma_commit(dready);
+      if (c == C::NCH - 1) mma_commit(dready);
     }
     // every MMA issued has completed before the accumulator is released
     mma_commit(done);
@@ -380,7 +465,7 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4)
+  if (warp == 5)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS)
                  : "memory");
 }
@@ -554,7 +639,9 @@ __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 static size_t pivot_smem() {
-  return BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
+  const size_t gj = BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
+  const size_t stage = (size_t)2 * BT * (BT + 1) * sizeof(T);  // two staging tiles
+  return gj > stage ? gj : stage;
 }
 
 template <typename T>
@@ -565,30 +652,33 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
   note_launch();
   k_big_sigma<T><<<dim3(512, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, k);
   const size_t psm = pivot_smem<T>();
-  raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T>), psm);
   bool tc = false;
-  if constexpr (sizeof(T) == 4) {
-    tc = tensor_cores;
-    if (tc) {
+  if constexpr (sizeof(T) == 4) tc = tensor_cores;
+  if (tc) {
+    if constexpr (sizeof(T) == 4) {
+      raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<float, true>), psm);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_ROW>), GjTc::SMEM);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_UPDATE>), GjTc::SMEM);
-    }
-  }
-  for (int q = 0; q < nP; ++q) {
-    note_launch();
-    k_big_pivot<T><<<dim3(nP, nids), 256, psm, s>>>(d_slabs, d_ids, pack, F, k, q, Cb, XqT, RT,
-                                                    Pinv, st);
-    if (nP == 1) continue;
-    if constexpr (sizeof(T) == 4) {
-      if (tc) {
+      for (int q = 0; q < nP; ++q) {
+        note_launch();
+        k_big_pivot<float, true><<<dim3(nP, nids), 512, psm, s>>>(d_slabs, d_ids, pack, F, k, q,
+                                                                  Cb, XqT, RT, Pinv, st);
+        if (nP == 1) continue;
         note_launch(2);
         k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
             d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
         k_big_gemm_tc<GJ_UPDATE><<<dim3(nP, nP, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
             d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
-        continue;
       }
     }
+    return;
+  }
+  raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T, false>), psm);
+  for (int q = 0; q < nP; ++q) {
+    note_launch();
+    k_big_pivot<T, false><<<dim3(nP, nids), 512, psm, s>>>(d_slabs, d_ids, pack, F, k, q, Cb, XqT,
+                                                           RT, Pinv, st);
+    if (nP == 1) continue;
     note_launch(2);
     k_big_gemm_fma<T, GJ_ROW><<<dim3(nP, 1, nids), 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb, XqT,
                                                                 RT, Pinv);
