@@ -25,6 +25,10 @@ follows ("the paper" below):
   and the equivalent loads ``fhat_j`` (Sec. 2.2, Eq. (equilib1), Fig. genBC: local solve with the global load and physical data,
   zero Dirichlet data on the neighbouring interfaces, restricted to ``Gamma_j``), computed by
   local sparse LU solves on each double slab ``Psi_j``.
+* O3b ``poisson_transfer_apply``: ``S_{j,j'} x`` for the constant-coefficient Poisson operator
+  in closed form: in the transverse sine basis every transfer operator is diagonal, with the
+  separable solution of the double slab as multiplier (used to probe the transfer operators
+  where forming O3 is too large).
 * O4 ``interface_matrix`` / ``block_thomas`` / ``gmres``: the equilibrium system
   ``(I - K) u = fhat`` of Sec. 1, Eq. (modelS) / Sec. 2.2, Eq. (modelScond) solved exactly by block Gaussian elimination, and by
   unrestarted GMRES (Sec. 5 and Sec. 5.2, x0 = 0, classical Gram-Schmidt applied twice, Givens rotations).
@@ -61,7 +65,7 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "assemble", "global_solve", "poisson_dst_solve", "laplacian_lambda_min",
     "diffusion_error_bound", "SlabGeometry", "slab_geometry", "factor_local",
-    "transfer_blocks", "equivalent_load", "interface_matrix", "apply_interface",
+    "transfer_blocks", "poisson_transfer_apply", "equivalent_load", "interface_matrix", "apply_interface",
     "block_thomas", "gmres", "reconstruct", "dd_solve", "hodlr_levels", "hodlr_node",
     "hodlr_compress", "hodlr_dense", "hodlr_apply", "adjoint_solve", "gradients",
     "loss_and_gradients",
@@ -261,6 +265,29 @@ def transfer_blocks(A, geo: SlabGeometry, facs, slabs=None):
             out.append(-lu.solve(rhs)[C, :])
         Sp.append(out[0]); Sn.append(out[1])
     return Sp, Sn
+
+
+def poisson_transfer_apply(dim: int, n: int, w: int, x):
+    """O3b: ``S_{j,j+1} x`` (equal to ``S_{j,j-1} x``) for ``a = 1``, ``b = 0``, ``c = 0``.
+
+    Expand the Dirichlet data on the neighbouring interface in the transverse sine modes
+    (``dim - 1`` axes, O2b's basis) with eigenvalue sums ``mu`` (in units of ``1/h^2``).  Across
+    the double slab (x = 0 .. 2w with zero data on the far interface) each mode solves the
+    three-term recurrence ``u_{i-1} - (2 + mu) u_i + u_{i+1} = 0``, i.e. ``u_i = sinh(i theta) /
+    sinh(2 w theta)`` with ``cosh theta = 1 + mu / 2``; its value at the central plane ``i = w`` is
+    ``1 / (2 cosh(w theta))``.  ``x`` holds ``n_Gamma = (n-1)^(dim-1)`` values in interface order.
+    """
+    k = np.arange(1, n)
+    mu1 = 4.0 * np.sin(np.pi * k / (2.0 * n)) ** 2
+    mu = np.zeros((n - 1,) * (dim - 1))
+    for d in range(dim - 1):
+        shape = [1] * (dim - 1)
+        shape[d] = n - 1
+        mu = mu + mu1.reshape(shape)
+    theta = np.arccosh(1.0 + mu / 2.0)
+    s = 1.0 / (2.0 * np.cosh(w * theta))
+    xh = sfft.dstn(np.asarray(x, dtype=np.float64).reshape((n - 1,) * (dim - 1)), type=1)
+    return sfft.idstn(s * xh, type=1).ravel()
 
 
 def equivalent_load(b, geo: SlabGeometry, facs):

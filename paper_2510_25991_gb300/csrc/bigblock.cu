@@ -637,10 +637,12 @@ __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------------------------
-template <typename T>
+// Shared memory of the pivot kernel: the Gauss-Jordan block of CTA q, or the staging tiles of
+// the copying CTAs (two in the split path, one in the plain path).
+template <typename T, bool SPLIT>
 static size_t pivot_smem() {
   const size_t gj = BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
-  const size_t stage = (size_t)2 * BT * (BT + 1) * sizeof(T);  // two staging tiles
+  const size_t stage = (size_t)(SPLIT ? 2 : 1) * BT * (BT + 1) * sizeof(T);
   return gj > stage ? gj : stage;
 }
 
@@ -651,11 +653,11 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
   const int nP = M / BT;
   note_launch();
   k_big_sigma<T><<<dim3(512, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, k);
-  const size_t psm = pivot_smem<T>();
   bool tc = false;
   if constexpr (sizeof(T) == 4) tc = tensor_cores;
   if (tc) {
     if constexpr (sizeof(T) == 4) {
+      const size_t psm = pivot_smem<float, true>();
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<float, true>), psm);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_ROW>), GjTc::SMEM);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_UPDATE>), GjTc::SMEM);
@@ -673,6 +675,7 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
     }
     return;
   }
+  const size_t psm = pivot_smem<T, false>();
   raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T, false>), psm);
   for (int q = 0; q < nP; ++q) {
     note_launch();

@@ -56,6 +56,7 @@ MUTATIONS = [
  ("O2b DST of type 2 instead of 1", "bh = sfft.dstn(b.reshape((n - 1,) * dim), type=1)", "bh = sfft.dstn(b.reshape((n - 1,) * dim), type=2)"),
  ("O2c lambda_min without the dimension factor", "return dim * 4.0 * n * n * math.sin", "return 4.0 * n * n * math.sin"),
  ("O2c a_min dropped from the eigenvalue bound", "lam = float(np.min(prob[\"a\"])) * laplacian_lambda_min", "lam = 1.0 * laplacian_lambda_min"),
+ ("O3b closed-form multiplier at the slab edge instead of the centre", "s = 1.0 / (2.0 * np.cosh(w * theta))", "s = 1.0 / (2.0 * np.cosh(2 * w * theta))"),
  ("O7 dL/da boundary u_q from 0 instead of g", "u_full = np.array(g, dtype=np.float64).copy()", "u_full = np.zeros_like(np.array(g, dtype=np.float64))"),
 ]
 

@@ -526,3 +526,21 @@ def test_o2c_error_bound_holds_and_is_tight_on_the_lowest_mode(dim, n):
     bound = O.diffusion_error_bound(pc, us + e)
     assert true <= bound <= 1.01 * true
     assert abs(O.laplacian_lambda_min(dim, n) * 0.5 - (A @ mode)[0] / mode[0]) <= 1e-9 * n * n
+
+
+@pytest.mark.parametrize("dim,n,w", [(2, 24, 4), (3, 12, 3), (3, 10, 5)])
+def test_o3b_poisson_transfer_closed_form_matches_local_solves(dim, n, w):
+    """O3b against O3: the closed-form transfer operator of constant-coefficient Poisson equals
+    both S_{j,j-1} and S_{j,j+1} formed by sparse LU local solves, on every slab."""
+    prob = I.make_problem("poisson2d" if dim == 2 else "vardiff3d", n=n, w=w, const_a=True)
+    prob["b"] = (0.0,) * dim
+    A, _ = O.assemble(prob)
+    geo = O.slab_geometry(dim, n, w)
+    Sp, Sn = O.transfer_blocks(A, geo, O.factor_local(A, geo))
+    rng = np.random.default_rng(21)
+    for j in range(geo.nds):
+        x = rng.standard_normal(geo.ngamma)
+        ref = O.poisson_transfer_apply(dim, n, w, x)
+        for S in (Sp[j], Sn[j]):
+            if S is not None:
+                assert np.abs(S @ x - ref).max() <= 1e-12 * np.abs(ref).max()
