@@ -94,8 +94,8 @@ typedef struct {
                            DDST_FP64                                                          */
   int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES; used clamped to 1..1000)  */
   double refine_tol;    /* FP64 refinement stops when its error estimate, rho / (1 - rho) times
-                           the last correction (rho: observed contraction, capped at 1/2),
-                           is <= refine_tol * ||u||                                         */
+                           the last correction (rho: observed contraction; no estimate while
+                           rho >= 1), is <= refine_tol * ||u||                              */
   int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
   int k_max;            /* HODLR rank cap per block (used clamped to 1..128)                  */
   int oversample;       /* extra random samples beyond k_max; the sketch width k_max +
@@ -177,7 +177,8 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 /* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.
  * (equilib1)), GMRES on (I - K) u_Gamma = fhat, volume reconstruction, then FP64 residual
  * refinement u += DD(b - A u) until the error bound rho/(1-rho) ||correction|| (rho: observed
- * contraction, capped at 1/2) is <= refine_tol ||u||; the bound is info->est_rel_error.
+ * contraction ratio of the corrections, no bound while it is >= 1) is <= refine_tol ||u||; the
+ * bound is info->est_rel_error.
  * f: interior load; g: nodal Dirichlet data (only boundary nodes are read); u: interior
  * output.  info may be NULL.  Errors: STATE, INVALID_ARG, NOT_CONVERGED (u still written). */
 ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,

@@ -836,17 +836,22 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
 // A-posteriori error of a contracting fixed-point iteration: if every step reduces the error by
 // a factor rho < 1, the error after applying the correction delta_k is at most
 // rho / (1 - rho) ||delta_k||.  rho is estimated by the larger of the last two ratios
-// ||delta_k|| / ||delta_{k-1}|| (only the first ratio after one step) and used up to 1/2; the
-// first correction (from zero) has no estimate and counts in full.  Returns the bound relative
-// to ||x|| given the correction norms so far (hist) and ||x||.
+// ||delta_k|| / ||delta_{k-1}|| (only the first ratio after two steps) and used as observed: a
+// slow contraction (rho near 1) enlarges the bound accordingly, and rho >= 1 (no contraction seen)
+// gives no bound at all (infinity), unless the correction itself is at the FP64 rounding level of
+// the residual (relative size below 1e-14), where the corrections are rounding noise and their
+// size is the only error measure left.  The first correction (from zero) has no estimate and
+// counts in full.  Returns the bound relative to ||x|| given the correction norms so far (hist)
+// and ||x||.
 double refine_error_estimate(const std::vector<double>& hist, double xn) {
   const size_t k = hist.size();
   if (k == 0 || !(xn > 0.0)) return 0.0;
-  double rel = hist[k - 1] / xn;
+  const double rel = hist[k - 1] / xn;
   if (k < 2) return rel;
   double rho = hist[k - 2] > 0.0 ? hist[k - 1] / hist[k - 2] : 1.0;
   if (k >= 3 && hist[k - 3] > 0.0) rho = std::max(rho, hist[k - 2] / hist[k - 3]);
-  rho = std::min(rho, 0.5);
+  if (rel <= 1e-14) return rel;
+  if (!(rho < 1.0)) return HUGE_VAL;
   return rel * rho / (1.0 - rho);
 }
 
