@@ -102,7 +102,8 @@ typedef struct {
                            oversample is capped at 128                                        */
   int leaf_size;        /* HODLR leaf size (used clamped to 8..256)                          */
   uint64_t seed;        /* seed of the counter-based Gaussian sketch generator                */
-  int check_every;      /* GMRES iterations between host convergence checks                   */
+  int check_every;      /* GMRES iterations between host convergence checks; 0 = automatic:
+                           every iteration for matrix-free operators, every 8 otherwise       */
   int factor_chunks;    /* pivot sweeps split along y into warm-started chunks per slab and
                            direction: 0 automatic, 1 exact sequential sweeps, k > 1 forced     */
   int factor_warmup;    /* warm-up rows of a chunk (0: 4 w in FP32, 10 w in FP64)              */
@@ -136,7 +137,15 @@ typedef struct {
 
 /* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
  * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234,
- * tensor_cores 1, explicit_S -1. */
+ * check_every 0 (automatic), tensor_cores 1, explicit_S -1.
+ * Testing hooks (environment variables, read at each use; they exercise the error paths without
+ * a device fault):
+ *  - DDST_FAIL_ALLOC=k: the k-th device allocation of the library after the variable was set
+ *    fails as out of memory (DDST_ERR_OOM) without calling cudaMalloc.
+ *  - DDST_WAIT_CYCLES=c: the pipeline waits of the tensor-core transfer build give up after c
+ *    clock cycles instead of about 4e9 (2 s); a short budget makes a wait expire on purpose and
+ *    ddst_build_transfer returns DDST_ERR_TIMEOUT.  Waits for copies or MMAs already issued keep
+ *    the full budget, so nothing is in flight when the kernel exits. */
 void ddst_options_default(ddst_options* opt);
 
 /* Builds the local operators A_j(I_j, I_j) of every double slab and factors them

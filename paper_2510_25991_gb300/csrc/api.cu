@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -123,6 +124,7 @@ struct ddst_ctx {
   void *mf_b = nullptr, *mf_z = nullptr, *mf_z2 = nullptr, *mf_x = nullptr;
   double* if_kx = nullptr;
   long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
+  bool solve_bufs_ready = false;
 };
 
 namespace {
@@ -148,8 +150,38 @@ ddst_status cuda_fail(ddst_ctx* c, cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr);     \
   } while (0)
 
+// Allocation-failure injection for tests of the out-of-memory path: with the environment
+// variable DDST_FAIL_ALLOC=k, the k-th device allocation of the library made after the variable
+// was set (or changed) fails as cudaErrorMemoryAllocation without calling cudaMalloc.
+bool inject_alloc_failure() {
+  static std::mutex mu;
+  static std::string last;
+  static long count = 0;
+  const char* v = getenv("DDST_FAIL_ALLOC");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!v || !*v) {
+    last.clear();
+    count = 0;
+    return false;
+  }
+  if (last != v) {
+    last = v;
+    count = 0;
+  }
+  return ++count == atol(v);
+}
+
+// Bounded-wait budget of the pipelined tensor-core kernels' role waits, in clock cycles: 4e9
+// (about 2 s), or DDST_WAIT_CYCLES when set (a testing hook that makes a wait expire).
+long long pipeline_wait_budget() {
+  const char* v = getenv("DDST_WAIT_CYCLES");
+  const long long c = v ? atoll(v) : 0;
+  return c > 0 ? c : 4000000000LL;
+}
+
 template <typename P>
 cudaError_t dalloc(ddst_ctx* ctx, P** out, size_t bytes) {
+  if (inject_alloc_failure()) return cudaErrorMemoryAllocation;
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes < 16 ? 16 : bytes);
   if (e != cudaSuccess) { cudaGetLastError(); return e; }
@@ -604,7 +636,8 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
       if (ctx->use_tc)
         launch_sbuild_tc(M, ctx->d_slabs, d_tiles, (int)tiles.size(), ctx->Uhi, ctx->Ulo,
                          ctx->Uhi + ctx->fac_elems, ctx->Ulo + ctx->fac_elems, (const float*)ctx->G,
-                         (const float*)ctx->pack, (float*)ctx->S, ctx->d_st, st);
+                         (const float*)ctx->pack, (float*)ctx->S, ctx->d_st,
+                         pipeline_wait_budget(), st);
       else
         launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
                          (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
@@ -631,7 +664,8 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
 // Solve
 // --------------------------------------------------------------------------------------------
 ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
-  if (ctx->d_b) return DDST_OK;
+  // set only once every buffer exists: a failed allocation leaves the context able to retry
+  if (ctx->solve_bufs_ready) return DDST_OK;
   ctx->opt.gmres_max_iter = std::max(1, std::min(ctx->opt.gmres_max_iter, 1000));
   const int maxit = ctx->opt.gmres_max_iter;
   ctx->ldh = maxit + 1;
@@ -670,6 +704,7 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   if ((e = cudaMemsetAsync(ctx->arn_ticket, 0, sizeof(unsigned) * 4, ctx->stream)) != cudaSuccess)
     return cuda_fail(ctx, e, "memset ticket");
 #undef AL
+  ctx->solve_bufs_ready = true;
   return DDST_OK;
 }
 
@@ -785,7 +820,9 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   cudaStream_t st = ctx->stream;
   const int64_t n = ctx->tot_if;
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
-  const int check = std::max(1, ctx->opt.check_every);
+  // host convergence checks: every iteration when a matrix-free application (local solves on
+  // every slab) costs far more than the check's synchronization, else every 8
+  const int check = ctx->opt.check_every > 0 ? ctx->opt.check_every : (ctx->matfree ? 1 : 8);
   launch_dot(rhs, rhs, n, ctx->part, 256, ctx->scal, st);
   const double beta = std::sqrt(host_scalar(ctx, ctx->scal));
   *iters = 0;
@@ -1118,7 +1155,7 @@ void ddst_options_default(ddst_options* opt) {
   opt->oversample = 10;
   opt->leaf_size = 128;
   opt->seed = 1234;
-  opt->check_every = 8;
+  opt->check_every = 0;
   opt->factor_chunks = 0;
   opt->factor_warmup = 0;
   opt->tensor_cores = 1;

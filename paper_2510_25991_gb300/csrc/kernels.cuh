@@ -81,11 +81,12 @@ void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int 
                    const T* F, const T* B, const T* G, const T* pack, T* S, DevStatus* st,
                    cudaStream_t s);
 
-// sweep_tc.cu: explicit transfer operators on tcgen05 (FP32 data, 3xTF32), M in {32, 64}
+// sweep_tc.cu: explicit transfer operators on tcgen05 (FP32 data, 3xTF32), M in {32, 64};
+// budget: clock cycles before a pipeline wait of a role gives up (ST_TIMEOUT)
 void launch_sbuild_tc(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                       const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                       const float* G, const float* pack, float* S, DevStatus* st,
-                      cudaStream_t s);
+                      long long budget, cudaStream_t s);
 int sbuild_tc_tile_cols();  // sources per CTA of the tensor-core transfer build
 
 // solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)

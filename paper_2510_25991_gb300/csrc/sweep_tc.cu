@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
                 const float* __restrict__ Fhi, const float* __restrict__ Flo,
                 const float* __restrict__ Bhi, const float* __restrict__ Blo,
                 const float* __restrict__ G, const float* __restrict__ pack,
-                float* __restrict__ S, DevStatus* st) {
+                float* __restrict__ S, DevStatus* st, long long budget) {
   using C = TcCfg<MB>;
   constexpr int NST = C::NST, NT = C::NT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
       int issued = 0;
       for (int stp = 0; stp < len; ++stp) {
         const int stage = stp % NST;
-        if (stp >= NST && !mbar_wait_ab(&empty[stage], ((stp / NST) - 1) & 1, abort, st, td.slab, blk(stp)))
+        if (stp >= NST && !mbar_wait_ab(&empty[stage], ((stp / NST) - 1) & 1, abort, st, td.slab, blk(stp), budget))
           break;
         const int i = blk(stp);
         const bool has_f = stp < len - 1;
@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
       for (int stp = 0; stp < len - 1; ++stp) {
         const int stage = stp % NST;
         const int i = blk(stp);
-        if (!mbar_wait_ab(&full[stage], (stp / NST) & 1, abort, st, td.slab, i)) break;
+        if (!mbar_wait_ab(&full[stage], (stp / NST) & 1, abort, st, td.slab, i, budget)) break;
         const unsigned char* fb = ring + stage * C::STAGE;
         const uint32_t b_hi = smem_u32(fb), b_lo = smem_u32(fb + C::FBLK);
         bool ok = true;
         for (int u = 0; u < nlive; ++u) {
-          if (!mbar_wait_ab(&aready[u], stp & 1, abort, st, td.slab, i)) { ok = false; break; }
+          if (!mbar_wait_ab(&aready[u], stp & 1, abort, st, td.slab, i, budget)) { ok = false; break; }
           tc_fence_after();
           const uint32_t base = tmem + (uint32_t)(u * 3 * MB);
           const uint32_t a_hi = base + (uint32_t)((stp & 1) * MB);
@@ -195,9 +195,9 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
     for (int stp = 0; stp < len; ++stp) {
       const int stage = stp % NST;
       const int i = blk(stp);
-      if (!mbar_wait_ab(&full[stage], (stp / NST) & 1, abort, st, td.slab, i)) break;
+      if (!mbar_wait_ab(&full[stage], (stp / NST) & 1, abort, st, td.slab, i, budget)) break;
       if (stp > 0) {
-        if (!mbar_wait_ab(&dready[u], (stp - 1) & 1, abort, st, td.slab, i)) break;
+        if (!mbar_wait_ab(&dready[u], (stp - 1) & 1, abort, st, td.slab, i, budget)) break;
         tc_fence_after();
       }
       const uint32_t dcur = base + (uint32_t)((stp & 1) * MB);
@@ -271,22 +271,23 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
 template <int MB>
 static void run_tc(const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                    const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
-                   const float* G, const float* pack, float* S, DevStatus* st, cudaStream_t s) {
+                   const float* G, const float* pack, float* S, DevStatus* st, long long budget,
+                   cudaStream_t s) {
   using C = TcCfg<MB>;
   raise_smem_limit(reinterpret_cast<const void*>(&k_sbuild_tc<MB>), C::SMEM);
   note_launch();
   k_sbuild_tc<MB><<<ntiles, C::THREADS, C::SMEM, s>>>(d_slabs, d_tiles, Fhi, Flo, Bhi, Blo, G,
-                                                      pack, S, st);
+                                                      pack, S, st, budget);
 }
 
 void launch_sbuild_tc(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                       const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                       const float* G, const float* pack, float* S, DevStatus* st,
-                      cudaStream_t s) {
+                      long long budget, cudaStream_t s) {
   if (ntiles == 0) return;
   switch (M) {
-    case 32: run_tc<32>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, s); break;
-    case 64: run_tc<64>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, s); break;
+    case 32: run_tc<32>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, s); break;
+    case 64: run_tc<64>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, s); break;
     default: break;
   }
 }

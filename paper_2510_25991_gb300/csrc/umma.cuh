@@ -76,15 +76,17 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait that also returns (false) once *abort is set by another role.
+// Bounded wait that also returns (false) once *abort is set by another role.  budget: clock
+// cycles before the wait gives up (records ST_TIMEOUT and raises *abort); 4e9 is about 2 s.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                             DevStatus* st, int slab, int block) {
+                                             DevStatus* st, int slab, int block,
+                                             long long budget = 4000000000LL) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (clock64() - t0 > 4000000000LL) {
+    if (clock64() - t0 > budget) {
       set_status(st, ST_TIMEOUT, slab, block);
       *abort = 1;
       return false;
