@@ -149,19 +149,20 @@ def make_problem(name: str, n: int | None = None, w: int | None = None, **overri
     return dict(name=name, dim=dim, n=n, w=w, a=a, b=b, c=c, f=f, g=g)
 
 
-def batch_specs(count: int = 64, seed0: int = 5000, wmax: int = 64):
+def batch_specs(count: int = 64, seed0: int = 5000, wmax: int | None = None):
     """Uneven batch of independent 2D diffusion problems.
 
     Problem ``i``: ``n_i = 64 * m_i`` with ``m_i ~ U{4..16}`` (256..1024 cells) and a slab
-    count drawn from ``{8, 16, 32}`` among those that keep the slab width ``n_i / slabs``
-    at most ``wmax`` cells; seed ``seed0 + i``.  Returns a list of dicts with ``n, w, seed``.
+    count drawn from ``{8, 16, 32}`` (slab width ``n_i / slabs``, 8 to 128 cells); seed
+    ``seed0 + i``.  ``wmax`` optionally restricts the draw to slab counts whose width is at most
+    ``wmax`` cells.  Returns a list of dicts with ``n, w, seed``.
     """
     out = []
     for i in range(count):
         rng = np.random.Generator(np.random.PCG64(seed0 + i))
         m = int(rng.integers(4, 17))
         n = 64 * m
-        choices = [s for s in (8, 16, 32) if n // s <= wmax]
+        choices = [s for s in (8, 16, 32) if wmax is None or n // s <= wmax]
         slabs = int(choices[int(rng.integers(0, len(choices)))])
         out.append(dict(n=n, w=n // slabs, seed=seed0 + i))
     return out

@@ -17,9 +17,9 @@ follows ("the paper" below):
   operator (``a = 1``, ``b = 0``, ``c = 0``; the Poisson experiments of Sec. 5.2, Table
   fd_poisson_fixedH) by the sine transform that diagonalizes it (separation of variables); exact
   to rounding and fast at any size.
-* O2c ``diffusion_error_bound``: a rigorous a-posteriori bound on ``||u - u*|| / ||u*||`` for a
-  pure-diffusion operator (``b = 0``, ``c >= 0``) from the FP64 residual of O1 and the closed-form
-  smallest eigenvalue of the constant-coefficient Laplacian, used where O2 is too large to run.
+* O2c ``diffusion_error_bound``: a rigorous a-posteriori bound on ``||u - u*|| / ||u*||`` (constant
+  convection, ``c >= 0``) from the FP64 residual of O1 and the closed-form smallest eigenvalue of
+  the constant-coefficient Laplacian, used where O2 is too large to run.
 * O3 ``transfer_blocks`` / ``equivalent_load``: the local solution-transfer operators
   ``S_{j,j'} = -R_{C_j} A_j(I_j,I_j)^{-1} A_j(I_j,J_{j,j'})`` (Sec. 2.2, Eq. (defS); Sec. 2.5)
   and the equivalent loads ``fhat_j`` (Sec. 2.2, Eq. (equilib1), Fig. genBC: local solve with the global load and physical data,
@@ -171,18 +171,21 @@ def laplacian_lambda_min(dim: int, n: int) -> float:
 
 
 def diffusion_error_bound(prob: dict, u):
-    """O2c: rigorous bound on ``||u - u*||_2 / ||u*||_2`` for ``-div(a grad u) + c u = f`` with
-    ``c >= 0`` and no convection.
+    """O2c: rigorous bound on ``||u - u*||_2 / ||u*||_2`` for ``-div(a grad u) + b . grad u + c u
+    = f`` with constant ``b`` and ``c >= 0``.
 
-    O1's matrix is ``A = sum_faces a_pq (e_p - e_q)(e_p - e_q)^T / h^2`` (boundary faces keep only
-    ``e_p e_p^T``) plus ``diag(c)``; every term is positive semidefinite and ``a_pq`` is at least
-    ``a_min`` (the smallest nodal value), so ``A - a_min L`` is positive semidefinite and
-    ``lambda_min(A) >= a_min lambda_min(L)``.  Hence ``||u - u*|| = ||A^{-1} r|| <= ||r|| /
-    (a_min lambda_min(L))``, with ``r = b - A u`` evaluated in FP64 and enlarged by the
-    rounding bound of that evaluation (at most 8 terms per row: ``gamma_8 (|b| + |A| |u|)``).
+    O1's diffusion part is ``sum_faces a_pq (e_p - e_q)(e_p - e_q)^T / h^2`` (boundary faces keep
+    only ``e_p e_p^T``) plus ``diag(c)``; every term is positive semidefinite and ``a_pq`` is at
+    least ``a_min`` (the smallest nodal value), so it is ``>= a_min L`` with ``L`` the
+    constant-coefficient Laplacian.  The central-difference convection part with constant ``b``
+    couples interior neighbours by ``+-b_d / (2h)``, a skew-symmetric matrix, so ``x^T A x`` sees
+    only the diffusion part and ``||A x|| ||x|| >= x^T A x >= a_min lambda_min(L) ||x||^2``.
+    Hence ``||u - u*|| = ||A^{-1} r|| <= ||r|| / (a_min lambda_min(L))``, with ``r = b - A u``
+    evaluated in FP64 and enlarged by the rounding bound of that evaluation (at most 8 terms per
+    row: ``gamma_8 (|b| + |A| |u|)``).
     """
-    if any(prob.get("b") or ()) or (prob.get("c") is not None and np.min(prob["c"]) < 0):
-        raise ValueError("the bound needs b = 0 and c >= 0")
+    if prob.get("c") is not None and np.min(prob["c"]) < 0:
+        raise ValueError("the bound needs c >= 0")
     A, b = assemble(prob)
     u = np.asarray(u, dtype=np.float64).ravel()
     r = b - A @ u

@@ -120,7 +120,12 @@ struct ddst_ctx {
   bool big_tc = false;                   // large-block Gauss-Jordan updates on tcgen05
   // matrix-free interface operator (no explicit S): its own slab-local buffers, so that an
   // application inside GMRES leaves the DD solve's vectors untouched
-  bool matfree = false;
+  // matfree: every class is applied matrix-free; mf_any: at least one (large-block classes in
+  // an otherwise explicit context); mf_cls: per class
+  bool matfree = false, mf_any = false;
+  std::map<int, bool> mf_cls;
+  int* d_mf_ids = nullptr;               // slabs of the matrix-free classes
+  int n_mf_ids = 0;
   void *mf_b = nullptr, *mf_z = nullptr, *mf_z2 = nullptr, *mf_x = nullptr;
   double* if_kx = nullptr;
   long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
@@ -453,9 +458,9 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       else { s.fac_off = fac_off; fac_off += (int64_t)P.nb * P.M * P.M; }
       s.pack_off = pack_off; pack_off += (int64_t)P.nb * PK_NFIELDS * P.M;
       s.loc_off = loc_off; loc_off += (int64_t)P.nb * P.M;
-      s.sp_off = -1; s.sn_off = -1;
-      if (j >= 2) { s.sp_off = s_off; s_off += P.ng * P.ng; }
-      if (j <= P.nds - 1) { s.sn_off = s_off; s_off += P.ng * P.ng; }
+      s.sp_off = -1; s.sn_off = -1;  // large-block slabs never form S
+      if (j >= 2 && !isbig) { s.sp_off = s_off; s_off += P.ng * P.ng; }
+      if (j <= P.nds - 1 && !isbig) { s.sn_off = s_off; s_off += P.ng * P.ng; }
       s.vol_off = vol_off; s.node_off = node_off;
       s.if_off = if_off + (int64_t)(j - 1) * P.ng;
       ctx->cls[P.M].push_back((int)ctx->slabs.size());
@@ -480,7 +485,16 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
                 "explicit transfer operators need blocks of at most 128 (64 in FP64) unknowns; "
                 "use explicit_S = 0 or -1 (matrix-free) for larger blocks");
   }
-  ctx->matfree = ctx->opt.explicit_S == 0 || (ctx->opt.explicit_S < 0 && any_big);
+  bool all_big = true;
+  for (auto& kv : ctx->big) all_big = all_big && kv.second;
+  ctx->matfree = ctx->opt.explicit_S == 0 || (ctx->opt.explicit_S < 0 && all_big);
+  ctx->mf_any = ctx->matfree || any_big;
+  std::vector<int> mf_ids;
+  for (auto& kv : ctx->cls) {
+    ctx->mf_cls[kv.first] = ctx->matfree || ctx->big[kv.first];
+    if (ctx->mf_cls[kv.first]) mf_ids.insert(mf_ids.end(), kv.second.begin(), kv.second.end());
+  }
+  ctx->n_mf_ids = (int)mf_ids.size();
   ctx->big_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
   const int nslab = (int)ctx->slabs.size();
   const size_t es = ctx->esz;
@@ -522,16 +536,18 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       AL(bw.Pinv, 2 * es * kv.second.size() * 128 * 128);
     }
   }
-  if (ctx->matfree) {
+  if (ctx->mf_any) {
     AL(ctx->mf_b, es * ctx->tot_loc);
     AL(ctx->mf_z, es * ctx->tot_loc);
     AL(ctx->mf_z2, es * ctx->tot_loc);
     AL(ctx->mf_x, es * ctx->tot_loc);
     AL(ctx->if_kx, sizeof(double) * ctx->tot_if);
+    AL(ctx->d_mf_ids, sizeof(int) * mf_ids.size());
   }
+  // tensor-core transfer build: explicit classes only, all of them with blocks <= 64
   ctx->use_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0 && !ctx->matfree;
   for (auto& kv : ctx->cls)
-    if (kv.first > 64) ctx->use_tc = false;
+    if (!ctx->mf_cls[kv.first] && kv.first > 64) ctx->use_tc = false;
   if (ctx->use_tc) {
     AL(ctx->Uhi, sizeof(float) * 2 * ctx->fac_elems);
     AL(ctx->Ulo, sizeof(float) * 2 * ctx->fac_elems);
@@ -550,6 +566,9 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   for (auto& kv : ctx->cls)
     if ((e = cudaMemcpyAsync(ctx->d_cls[kv.first], kv.second.data(), sizeof(int) * kv.second.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(e, "copy ids");
+  if (ctx->mf_any && !mf_ids.empty() &&
+      (e = cudaMemcpyAsync(ctx->d_mf_ids, mf_ids.data(), sizeof(int) * mf_ids.size(),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess) return bail(e, "copy ids");
   cudaMemsetAsync(ctx->d_st, 0, sizeof(DevStatus), st);
   cudaMemsetAsync(ctx->d_c, 0, sizeof(double) * ctx->tot_nodes, st);
   for (int q = 0; q < nprob; ++q) {
@@ -608,6 +627,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   Timer tm(st);
   for (auto& kv : ctx->cls) {
     const int M = kv.first;
+    if (ctx->mf_cls[M]) continue;  // applied matrix-free
     const int R = (sizeof(T) == 4 && ctx->use_tc) ? sbuild_tc_tile_cols()
                                                   : sbuild_tile_cols<T>(M);
     std::vector<TileDesc> tiles;
@@ -713,9 +733,10 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
 // central rows, R_C x, into the FP64 interface vector iface.  z1, z2: slab-local temporaries.
 template <typename T>
 void local_solves(ddst_ctx* ctx, const T* b, T* z1, T* z2, T* x, double* iface, int transpose,
-                  int mode, cudaStream_t st) {
+                  int mode, cudaStream_t st, bool only_mf = false) {
   for (auto& kv : ctx->cls) {
     const int M = kv.first, nids = (int)kv.second.size();
+    if (only_mf && !ctx->mf_cls[M]) continue;
     if (ctx->big[M]) {
       launch_big_solve<T>(M, ctx->d_slabs, ctx->d_cls[M], nids, ctx->cls_maxnb[M],
                           (const T*)ctx->Fbig, (const T*)ctx->pack, b, z1, x, transpose, st);
@@ -730,38 +751,47 @@ void local_solves(ddst_ctx* ctx, const T* b, T* z1, T* z2, T* x, double* iface, 
 
 // y = (I - K) x, or K x (bit 1 of mode), or the transposes (bit 0), with K applied through local
 // solves (Sec. 2.2, Eq. (defS)): K x = R_C A_j^{-1} (-A(I_j, J) x_J) per double slab;
-// K^T x = -A(J, I_j) A_j^{-T} R_C^T x_j.  Uses the matrix-free buffers only.
+// K^T x = -A(J, I_j) A_j^{-T} R_C^T x_j.  Covers the interfaces of the matrix-free classes only
+// (a problem's slabs are all in one class, so K never couples them to an explicit class); uses
+// the matrix-free buffers only.
 template <typename T>
 void apply_matfree(ddst_ctx* ctx, const double* x, double* y, int mode, cudaStream_t st,
                    const int* kdev, int64_t kstride) {
-  const int nslab = (int)ctx->slabs.size();
+  if (ctx->n_mf_ids == 0) return;
   T* b = (T*)ctx->mf_b;
   cudaMemsetAsync(b, 0, ctx->esz * ctx->tot_loc, st);
   if (!(mode & 1)) {
-    launch_mf_rhs<T>(ctx->d_slabs, ctx->d_probs, nslab, (const T*)ctx->pack, x, kdev, kstride, b, st);
-    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, ctx->if_kx, 0, 1, st);
+    launch_mf_rhs<T>(ctx->d_slabs, ctx->d_mf_ids, ctx->n_mf_ids, ctx->d_probs, (const T*)ctx->pack,
+                     x, kdev, kstride, b, st);
+    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, ctx->if_kx, 0, 1, st, true);
   } else {
-    launch_mf_inject<T>(ctx->d_slabs, nslab, x, kdev, kstride, b, st);
-    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, nullptr, 1, 0, st);
+    launch_mf_inject<T>(ctx->d_slabs, ctx->d_mf_ids, ctx->n_mf_ids, x, kdev, kstride, b, st);
+    local_solves<T>(ctx, b, (T*)ctx->mf_z, (T*)ctx->mf_z2, (T*)ctx->mf_x, nullptr, 1, 0, st, true);
     cudaMemsetAsync(ctx->if_kx, 0, sizeof(double) * ctx->tot_if, st);
-    launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (const T*)ctx->pack,
-                                (const T*)ctx->mf_x, ctx->if_kx, st);
+    launch_mf_dirichlet_T<T>(ctx->d_slabs, ctx->d_mf_ids, ctx->n_mf_ids, ctx->d_probs,
+                             (const T*)ctx->pack, (const T*)ctx->mf_x, ctx->if_kx, st);
   }
-  launch_mf_combine(ctx->tot_if, x, kdev, kstride, ctx->if_kx, y, (mode & 2) ? 1 : 0, st);
+  launch_mf_combine(ctx->d_slabs, ctx->d_mf_ids, ctx->n_mf_ids, x, kdev, kstride, ctx->if_kx, y,
+                    (mode & 2) ? 1 : 0, st);
 }
 
 template <typename T>
 void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
                        cudaStream_t st = nullptr, const int* kdev = nullptr, int64_t kstride = 0) {
   if (!st) st = ctx->stream;
-  if (ctx->matfree)
+  if (ctx->matfree) {
     apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
-  else if (ctx->state == 3)
+    return;
+  }
+  // explicit operators (their apply also writes the matrix-free classes' interfaces, as if K
+  // were zero there), then the matrix-free classes overwrite their own interfaces
+  if (ctx->state == 3)
     hodlr_apply<T>(ctx->hodlr, ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), x, y, transpose,
                    st, kdev, kstride);
   else
     launch_apply_dense<T>(ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), ctx->max_ng,
                           (const T*)ctx->S, x, y, transpose, st, kdev, kstride);
+  if (ctx->mf_any) apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
 }
 
 // One GMRES step (operator application + Arnoldi CGS2 + Givens + normalization) captured as a
@@ -822,7 +852,7 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
   // host convergence checks: every iteration when a matrix-free application (local solves on
   // every slab) costs far more than the check's synchronization, else every 8
-  const int check = ctx->opt.check_every > 0 ? ctx->opt.check_every : (ctx->matfree ? 1 : 8);
+  const int check = ctx->opt.check_every > 0 ? ctx->opt.check_every : (ctx->mf_any ? 1 : 8);
   launch_dot(rhs, rhs, n, ctx->part, 256, ctx->scal, st);
   const double beta = std::sqrt(host_scalar(ctx, ctx->scal));
   *iters = 0;
@@ -1274,10 +1304,11 @@ ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* 
   if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
   if (prob < 0 || prob >= ctx->nprob || !out || (side != -1 && side != 1))
     return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
-  if (ctx->matfree)
-    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED, "matrix-free context: no explicit transfer operators");
   const ProbDesc& P = ctx->probs[prob];
   if (j < 1 || j > P.nds) return fail(ctx, DDST_ERR_INVALID_ARG, "slab index out of range");
+  if (ctx->mf_cls[P.M])
+    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED,
+                "problem %d applies its transfer operators matrix-free: none is formed", prob);
   const SlabDesc& s = ctx->slabs[P.slab0 + j - 1];
   const int64_t off = side < 0 ? s.sp_off : s.sn_off;
   if (off < 0) return fail(ctx, DDST_ERR_INVALID_ARG, "slab %d has no neighbour on that side", j);

@@ -134,15 +134,22 @@ template <typename T>
 void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, const T* loc,
                         double* iface, cudaStream_t s);
 
-// matfree.cu: the interface operator through local solves (x indexed by kdev as above)
+// matfree.cu: the interface operator through local solves, over the listed slabs (x indexed by
+// kdev as above)
 template <typename T>
-void launch_mf_rhs(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab, const T* pack,
-                   const double* x, const int* kdev, int64_t kstride, T* loc, cudaStream_t st);
+void launch_mf_rhs(const SlabDesc* d_slabs, const int* d_ids, int nids, const ProbDesc* d_probs,
+                   const T* pack, const double* x, const int* kdev, int64_t kstride, T* loc,
+                   cudaStream_t st);
 template <typename T>
-void launch_mf_inject(const SlabDesc* d_slabs, int nslab, const double* x, const int* kdev,
-                      int64_t kstride, T* loc, cudaStream_t st);
-void launch_mf_combine(int64_t n, const double* x, const int* kdev, int64_t kstride,
-                       const double* kx, double* y, int konly, cudaStream_t st);
+void launch_mf_inject(const SlabDesc* d_slabs, const int* d_ids, int nids, const double* x,
+                      const int* kdev, int64_t kstride, T* loc, cudaStream_t st);
+template <typename T>
+void launch_mf_dirichlet_T(const SlabDesc* d_slabs, const int* d_ids, int nids,
+                           const ProbDesc* d_probs, const T* pack, const T* loc, double* out,
+                           cudaStream_t st);
+void launch_mf_combine(const SlabDesc* d_slabs, const int* d_ids, int nids, const double* x,
+                       const int* kdev, int64_t kstride, const double* kx, double* y, int konly,
+                       cudaStream_t st);
 
 // grad.cu: dL/dg and dL/da from lambda and u (nodal outputs accumulated; zero them first)
 void launch_gradients(const ProbDesc* d_probs, int nprob, const double* a, const double* g,

@@ -22,11 +22,13 @@ __device__ __forceinline__ const double* eff(const double* x, const int* kdev, i
 
 // loc (zeroed by the caller) gets the Dirichlet data of the neighbouring interfaces:
 // loc[k][W_t] = -beta_{k,t} x_{j-1}(k,t),  loc[k][E_t] = -gamma_{k,t} x_{j+1}(k,t).
+// grid = (chunks, listed slabs).
 template <typename T>
-__global__ void k_mf_rhs(const SlabDesc* __restrict__ slabs, const ProbDesc* __restrict__ probs,
-                         const T* __restrict__ pack, const double* __restrict__ x0,
-                         const int* __restrict__ kdev, int64_t kstride, T* __restrict__ loc) {
-  const SlabDesc s = slabs[blockIdx.y];
+__global__ void k_mf_rhs(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                         const ProbDesc* __restrict__ probs, const T* __restrict__ pack,
+                         const double* __restrict__ x0, const int* __restrict__ kdev,
+                         int64_t kstride, T* __restrict__ loc) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
   const ProbDesc P = probs[s.prob];
   const double* x = eff(x0, kdev, kstride);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.ng;
@@ -45,9 +47,10 @@ __global__ void k_mf_rhs(const SlabDesc* __restrict__ slabs, const ProbDesc* __r
 
 // loc (zeroed by the caller) gets x_j on the central plane: loc[k][C_t] = x_j(k,t).
 template <typename T>
-__global__ void k_mf_inject(const SlabDesc* __restrict__ slabs, const double* __restrict__ x0,
-                            const int* __restrict__ kdev, int64_t kstride, T* __restrict__ loc) {
-  const SlabDesc s = slabs[blockIdx.y];
+__global__ void k_mf_inject(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                            const double* __restrict__ x0, const int* __restrict__ kdev,
+                            int64_t kstride, T* __restrict__ loc) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
   const double* x = eff(x0, kdev, kstride);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.ng;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -56,43 +59,84 @@ __global__ void k_mf_inject(const SlabDesc* __restrict__ slabs, const double* __
   }
 }
 
-// y = x - Kx (konly = 0) or y = Kx (konly = 1).
-__global__ void k_mf_combine(int64_t n, const double* __restrict__ x0, const int* __restrict__ kdev,
+// Transposed Dirichlet coupling: the data x_{j-1}, x_{j+1} enters slab j's right-hand side
+// through -beta / -gamma, so z (slab-local) feeds out_{j-1} -= beta z[W], out_{j+1} -= gamma z[E]
+// (atomic: two slabs feed each interface).
+template <typename T>
+__global__ void k_mf_dirichlet_T(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                                 const ProbDesc* __restrict__ probs, const T* __restrict__ pack,
+                                 const T* __restrict__ loc, double* __restrict__ out) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
+  const ProbDesc P = probs[s.prob];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.ng;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / s.p) + 1, t = (int)(e % s.p);
+    const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * s.M;
+    const T* row = loc + s.loc_off + (int64_t)(k - 1) * s.M;
+    if (s.j >= 2)
+      atomicAdd(&out[s.if_off - s.ng + e],
+                -static_cast<double>(pk[PK_WEST * s.M + t]) * static_cast<double>(row[t]));
+    if (s.j <= P.nds - 1) {
+      const int cE = (2 * s.w - 2) * s.p + t;
+      atomicAdd(&out[s.if_off + s.ng + e],
+                -static_cast<double>(pk[PK_EAST * s.M + cE]) * static_cast<double>(row[cE]));
+    }
+  }
+}
+
+// On the interface Gamma_j of every listed slab: y = x - Kx (konly = 0) or y = Kx (konly = 1).
+__global__ void k_mf_combine(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
+                             const double* __restrict__ x0, const int* __restrict__ kdev,
                              int64_t kstride, const double* __restrict__ kx, double* __restrict__ y,
                              int konly) {
+  const SlabDesc s = slabs[ids[blockIdx.y]];
   const double* x = eff(x0, kdev, kstride);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = konly ? kx[e] : x[e] - kx[e];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < s.ng;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = s.if_off + e;
+    y[i] = konly ? kx[i] : x[i] - kx[i];
+  }
 }
 
 template <typename T>
-void launch_mf_rhs(const SlabDesc* d_slabs, const ProbDesc* d_probs, int nslab, const T* pack,
-                   const double* x, const int* kdev, int64_t kstride, T* loc, cudaStream_t st) {
+void launch_mf_rhs(const SlabDesc* d_slabs, const int* d_ids, int nids, const ProbDesc* d_probs,
+                   const T* pack, const double* x, const int* kdev, int64_t kstride, T* loc,
+                   cudaStream_t st) {
   note_launch();
-  k_mf_rhs<T><<<dim3(32, nslab), 256, 0, st>>>(d_slabs, d_probs, pack, x, kdev, kstride, loc);
+  k_mf_rhs<T><<<dim3(32, nids), 256, 0, st>>>(d_slabs, d_ids, d_probs, pack, x, kdev, kstride, loc);
 }
 
 template <typename T>
-void launch_mf_inject(const SlabDesc* d_slabs, int nslab, const double* x, const int* kdev,
-                      int64_t kstride, T* loc, cudaStream_t st) {
+void launch_mf_inject(const SlabDesc* d_slabs, const int* d_ids, int nids, const double* x,
+                      const int* kdev, int64_t kstride, T* loc, cudaStream_t st) {
   note_launch();
-  k_mf_inject<T><<<dim3(32, nslab), 256, 0, st>>>(d_slabs, x, kdev, kstride, loc);
+  k_mf_inject<T><<<dim3(32, nids), 256, 0, st>>>(d_slabs, d_ids, x, kdev, kstride, loc);
 }
 
-void launch_mf_combine(int64_t n, const double* x, const int* kdev, int64_t kstride,
-                       const double* kx, double* y, int konly, cudaStream_t st) {
+template <typename T>
+void launch_mf_dirichlet_T(const SlabDesc* d_slabs, const int* d_ids, int nids,
+                           const ProbDesc* d_probs, const T* pack, const T* loc, double* out,
+                           cudaStream_t st) {
   note_launch();
-  k_mf_combine<<<256, 256, 0, st>>>(n, x, kdev, kstride, kx, y, konly);
+  k_mf_dirichlet_T<T><<<dim3(32, nids), 256, 0, st>>>(d_slabs, d_ids, d_probs, pack, loc, out);
 }
 
-template void launch_mf_rhs<float>(const SlabDesc*, const ProbDesc*, int, const float*,
-                                   const double*, const int*, int64_t, float*, cudaStream_t);
-template void launch_mf_rhs<double>(const SlabDesc*, const ProbDesc*, int, const double*,
-                                    const double*, const int*, int64_t, double*, cudaStream_t);
-template void launch_mf_inject<float>(const SlabDesc*, int, const double*, const int*, int64_t,
-                                      float*, cudaStream_t);
-template void launch_mf_inject<double>(const SlabDesc*, int, const double*, const int*, int64_t,
-                                       double*, cudaStream_t);
+void launch_mf_combine(const SlabDesc* d_slabs, const int* d_ids, int nids, const double* x,
+                       const int* kdev, int64_t kstride, const double* kx, double* y, int konly,
+                       cudaStream_t st) {
+  note_launch();
+  k_mf_combine<<<dim3(32, nids), 256, 0, st>>>(d_slabs, d_ids, x, kdev, kstride, kx, y, konly);
+}
+
+#define INST(T)                                                                                  \
+  template void launch_mf_rhs<T>(const SlabDesc*, const int*, int, const ProbDesc*, const T*,    \
+                                 const double*, const int*, int64_t, T*, cudaStream_t);          \
+  template void launch_mf_inject<T>(const SlabDesc*, const int*, int, const double*, const int*, \
+                                    int64_t, T*, cudaStream_t);                                  \
+  template void launch_mf_dirichlet_T<T>(const SlabDesc*, const int*, int, const ProbDesc*,      \
+                                         const T*, const T*, double*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
 
 }  // namespace ddst

@@ -2,13 +2,13 @@
 
 * Helmholtz, 4096^2 grid, kappa = 200, 127 double slabs of 64 cells (the ranks-vs-tolerance
   configuration): sampled transfer-operator rows against oracle transposed local solves, and
-  HODLR compression at tol 1e-6 / 1e-8 against the dense operator (ranks non-decreasing, error
-  within 10 tol or the FP32 floor of the mixed path).  The interface GMRES of this strongly indefinite global problem is not part
+  HODLR compression at tol 1e-6 against the dense operator (error within 10 tol; ranks at a 1e-8
+  request non-decreasing).  The interface GMRES of this strongly indefinite global problem is not part
   of the check: with 127 slabs at 32 wavelengths it does not converge in the iteration cap
   (the reduced-size Helmholtz tests cover the solve).
 * The uneven batch of 64 independent diffusion problems (256^2 .. 1024^2 grids, 8-32 slabs):
-  one batched setup, solve and adjoint; loss and gradients of three sampled problems (smallest,
-  median, largest) against the oracle.
+  one batched setup, solve and adjoint; every problem's solution, loss and gradients against the
+  oracle.
 """
 import numpy as np
 import pytest
@@ -74,48 +74,50 @@ def test_helmholtz_4096_transfer_rows_and_hodlr_tolerances():
         ref = -(Acsr[I_][:, J].T @ Y).T
         assert np.abs(dense[side][rows] - ref).max() <= 1e-3 * np.abs(ref).max()
     del A, Acsr, lu
-    # HODLR at two tolerances against the dense (FP32) operator.  In FP32 the range finder rejects
-    # samples below 1e3 eps_32 of their own norm as rounding noise, which floors the compression
-    # error there (the FP64 refinement of the solve removes it); the FP64 compression at these
-    # tolerances and at 1e-10 is checked at reduced size.
-    floor = 1e3 * float(np.finfo(np.float32).eps)
-    ranks = []
-    for tol in (1e-6, 1e-8):
-        sol.compress(tol)
-        ranks.append(D.ddst_query(sol.ctx)[2])
-        for side in (-1, 1):
-            out = np.empty((ng, ng))
-            D.ddst_get_transfer(sol.ctx, 0, j + 1, side, out)
-            err = _norm2(out - dense[side]) / _norm2(dense[side])
-            assert err <= max(10 * tol, floor), (tol, side, err)
-    assert 0 < ranks[0] <= ranks[1] <= 64, ranks
+    # HODLR against the dense (FP32) operator at tol 1e-6, the smallest tolerance the mixed path's
+    # FP32 range finder meets; at a 1e-8 request only the ranks are recorded (they may not
+    # decrease).  Compression at 1e-8 and 1e-10 within 10 tol is checked in FP64 at reduced size.
+    sol.compress(1e-6)
+    r6 = D.ddst_query(sol.ctx)[2]
+    for side in (-1, 1):
+        out = np.empty((ng, ng))
+        D.ddst_get_transfer(sol.ctx, 0, j + 1, side, out)
+        err = _norm2(out - dense[side]) / _norm2(dense[side])
+        assert err <= 10 * 1e-6, (side, err)
+    sol.compress(1e-8)
+    r8 = D.ddst_query(sol.ctx)[2]
+    assert 0 < r6 <= r8 <= 64, (r6, r8)
     sol.close()
 
 
 def test_adjoint_batch_of_64_uneven_problems():
+    """The uneven adjoint batch as specified: 64 problems with 8, 16 or 32 slabs (slab widths up to
+    128 cells, so blocks of up to 255 unknowns: those problems take the large-block kernels and a
+    matrix-free interface operator, the others explicit ones), one batched setup, solve and
+    adjoint.  Every problem's solution, loss, dL/df and dL/da against O7, the oracle runs in a
+    spawn process pool on the host cores."""
+    import multiprocessing as mp
+    import os
     from paper_2510_25991_gb300 import ddst as D
+    from _batch_oracle import check_problem
     specs = I.batch_specs(64)
+    assert max(s["w"] for s in specs) > 64
     probs = [I.batch_problem(s) for s in specs]
     sol = D.Solver([dict(dim=2, n=p["n"], w=p["w"], a=_dev(p["a"]), b=(0.0, 0.0, 0.0)) for p in probs],
                    precision="mixed")
     sol.build_transfer()
     us = [torch.empty((p["n"] - 1, p["n"] - 1), dtype=torch.float64, device="cuda") for p in probs]
     D.ddst_solve_batch(sol.ctx, [_dev(p["f"]) for p in probs], [_dev(p["g"]) for p in probs], us)
-    rng = np.random.default_rng(11)
-    obs = [rng.standard_normal((p["n"] - 1) ** 2) for p in probs]
+    obs = [np.random.default_rng(100 + i).standard_normal((p["n"] - 1) ** 2) for i, p in enumerate(probs)]
     dLdu = [_dev((u.cpu().numpy().ravel() - o).reshape(u.shape)) for u, o in zip(us, obs)]
     dfs = [torch.empty_like(u) for u in us]
     dgs = [torch.empty((p["n"] + 1, p["n"] + 1), dtype=torch.float64, device="cuda") for p in probs]
     das = [torch.empty_like(x) for x in dgs]
     D.ddst_solve_adjoint_batch(sol.ctx, dLdu, dfs, dgs, das)
     sol.close()
-    order = np.argsort([p["n"] for p in probs], kind="stable")
-    for i in (order[0], order[len(order) // 2], order[-1]):
-        p = probs[i]
-        L, dLdf, dLdg, dLda, uref, lam = O.loss_and_gradients(p, obs[i])
-        u = us[i].cpu().numpy().ravel()
-        assert np.linalg.norm(u - uref) / np.linalg.norm(uref) <= 1e-8
-        assert abs(0.5 * np.sum((u - obs[i]) ** 2) - L) <= 1e-7 * L
-        dLdf, dLda = np.ravel(dLdf), np.ravel(dLda)
-        assert np.linalg.norm(dfs[i].cpu().numpy().ravel() - dLdf) <= 1e-8 * np.linalg.norm(dLdf)
-        assert np.linalg.norm(das[i].cpu().numpy().ravel() - dLda) <= 1e-7 * np.linalg.norm(dLda)
+    work = [(specs[i], 100 + i, us[i].cpu().numpy().ravel(), dfs[i].cpu().numpy().ravel(),
+             das[i].cpu().numpy().ravel()) for i in range(len(probs))]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        errs = pool.map(check_problem, work)
+    for i, (eu, eL, ef, ea) in enumerate(errs):
+        assert eu <= 1e-8 and eL <= 1e-7 and ef <= 1e-8 and ea <= 1e-7, (i, specs[i], eu, eL, ef, ea)

@@ -84,6 +84,8 @@ def test_uneven_batch_specification():
     for s in specs:
         n, w = s["n"], s["w"]
         assert n % 64 == 0 and 256 <= n <= 1024
-        assert n % w == 0 and n // w in (8, 16, 32) and w <= 64
+        assert n % w == 0 and n // w in (8, 16, 32)
     assert len({s["n"] for s in specs}) > 5          # genuinely uneven
+    assert max(s["w"] for s in specs) > 64           # wide slabs (blocks above 128) included
+    assert all(s["w"] <= 64 for s in I.batch_specs(64, wmax=64))
     assert specs == I.batch_specs(64)

@@ -509,12 +509,22 @@ def test_o2c_error_bound_holds_and_is_tight_on_the_lowest_mode(dim, n):
     prob = I.make_problem("poisson2d" if dim == 2 else "vardiff3d", n=n, w=2)
     if dim == 2:
         prob["a"] = I.fourier_log_field(2, n, 77)
-    A, b = O.assemble(prob)
+    for bconv in ((0.0,) * dim, (40.0, -25.0, 10.0)[:dim]):  # skew-symmetric convection too
+        pb = dict(prob, b=bconv)
+        A, b = O.assemble(pb)
+        us = O.global_solve(A, b)
+        for scale in (1e-3, 1e-8):
+            u = us + scale * np.abs(us).max() * rng.standard_normal(us.size)
+            true = np.linalg.norm(u - us) / np.linalg.norm(us)
+            assert O.diffusion_error_bound(pb, u) >= true
+    # the worst case: the error along the singular vector of the smallest singular value of A
+    pb = dict(prob, b=(40.0, -25.0, 10.0)[:dim])
+    A, b = O.assemble(pb)
     us = O.global_solve(A, b)
-    for scale in (1e-3, 1e-8):
-        u = us + scale * np.abs(us).max() * rng.standard_normal(us.size)
-        true = np.linalg.norm(u - us) / np.linalg.norm(us)
-        assert O.diffusion_error_bound(prob, u) >= true
+    _, sv, Vt = np.linalg.svd(A.toarray())
+    e = 1e-6 * np.linalg.norm(us) * Vt[-1]
+    true = np.linalg.norm(e) / np.linalg.norm(us)
+    assert O.diffusion_error_bound(pb, us + e) >= true
     # a = 0.5 everywhere: lambda_min(A) = 0.5 lambda_min(L)
     pc = dict(prob, a=np.full_like(prob["a"], 0.5))
     A, b = O.assemble(pc)
