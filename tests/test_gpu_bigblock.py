@@ -165,3 +165,35 @@ def test_large_block_batch_with_uneven_slab_counts():
     for p, u in zip(probs, us):
         A, b = O.assemble(p)
         assert relerr(u.cpu().numpy().ravel(), O.global_solve(A, b)) <= 1e-8, p["name"]
+
+
+def test_mixed_context_hodlr_plus_matrix_free_with_adjoint():
+    """One context with explicit classes (HODLR-compressed) and a large-block class (matrix-free):
+    the compressed apply covers the explicit problems, the matrix-free apply then writes the
+    large-block problem's interfaces.  Forward solutions and dL/df of every problem against
+    O2 / O7."""
+    from paper_2510_25991_gb300 import ddst as D
+    probs = [I.make_problem("convdiff2d", n=128, w=16), I.make_problem("convdiff2d", n=256, w=128),
+             I.make_problem("poisson2d", n=128, w=32)]
+    spec = [dict(dim=2, n=p["n"], w=p["w"], a=dev(p["a"]), b=tuple(p["b"]) + (0.0,) * (3 - len(p["b"])))
+            for p in probs]
+    sol = D.Solver(spec, precision="mixed", leaf_size=32)
+    sol.build_transfer()
+    sol.compress(1e-8)
+    assert D.ddst_query(sol.ctx, 0)[2] > 0
+    us = [torch.empty((p["n"] - 1,) * 2, dtype=torch.float64, device="cuda") for p in probs]
+    D.ddst_solve_batch(sol.ctx, [dev(p["f"]) for p in probs], [dev(p["g"]) for p in probs], us)
+    rng = np.random.default_rng(4)
+    obs = [rng.standard_normal((p["n"] - 1) ** 2) for p in probs]
+    dLdu = [dev((u.cpu().numpy().ravel() - o).reshape(u.shape)) for u, o in zip(us, obs)]
+    dfs = [torch.empty_like(u) for u in us]
+    D.ddst_solve_adjoint_batch(sol.ctx, dLdu, dfs, [None] * 3, [None] * 3)
+    with pytest.raises(D.DDSTError) as e:
+        D.ddst_get_transfer(sol.ctx, 1, 1, 1, np.empty((255, 255)))
+    assert e.value.name == "NOT_IMPLEMENTED"
+    sol.close()
+    for p, u, df, o in zip(probs, us, dfs, obs):
+        A, b = O.assemble(p)
+        uh = u.cpu().numpy().ravel()
+        assert relerr(uh, O.global_solve(A, b)) <= 1e-8, p["name"]
+        assert relerr(df.cpu().numpy().ravel(), O.adjoint_solve(A, uh - o)) <= 1e-8, p["name"]
