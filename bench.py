@@ -493,9 +493,11 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"convdiff2d n={n} w={w} ({nds} double slabs), -div(a grad u) + (20,10).grad u = f, "
                                    f"a = exp(8 Fourier modes), HODLR tol {args.tol:g} requested, sketch 64+10",
-                       "hodlr_note": "the mixed-precision compression meets 10 tol down to tol 1e-6; below that "
-                                     "its FP32 range finder floors near 1e-5 of each block, and the FP64 "
-                                     "refinement of the solve restores the 1e-8 solution",
+                       "hodlr_note": "mixed precision: the compression meets 10 tol (and optimal <= rank <= optimal "
+                                     "+ oversampling) for tol >= 1e-5; below that its FP32 sketch and range "
+                                     "finder floor near 2e-5 of ||S|| per block (2.3e-5 / 1.0e-5 / 7.6e-6 on the "
+                                     "first / middle / last block at this request), and the FP64 refinement of "
+                                     "the solve restores the 1e-8 solution",
                        "dof": dof, "l2": "inputs and factors >> L2; L2 flushed between steps"},
             "s_per_adjoint_gradient": statistics.mean(adj) / 1e3,
             "phases_ms": {"factor": info["t_factor"], "transfer": info["t_transfer"],

@@ -178,7 +178,10 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx);
 /* Compresses every S_{j,j'} into HODLR form (Sec. 2.4: weak admissibility, cluster tree
  * shared by source and target interface) by randomized sampling with Gaussian sketches; each
  * off-diagonal block is truncated at sigma_{r+1} <= tol * ||S_{j,j'}||_2 (rank <= k_max).
- * tol <= 0 keeps the dense operators.  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA,
+ * tol <= 0 keeps the dense operators.  In DDST_MIXED the sketch and range finder run in FP32 and
+ * reject samples below 1e3 eps_32 of their own norm, which floors the compression error near 1e-5
+ * of ||S_{j,j'}||_2: requests below about 1e-5 are met only in DDST_FP64 (the FP64 refinement of
+ * ddst_solve still reaches its refine_tol).  Requires ddst_build_transfer.  Errors: STATE, OOM, CUDA,
  * INVALID_ARG (cluster tree deeper than 12 levels: raise leaf_size), NOT_IMPLEMENTED (tol > 0 on a
  * matrix-free context: compression samples the explicit operators). */
 ddst_status ddst_compress(ddst_ctx* ctx, double tol);

@@ -62,16 +62,17 @@ def test_sampled_transfer_rows_match_oracle(full):
 
 def test_mixed_hodlr_against_dense_operator_and_optimal_ranks(full):
     """Mixed-precision compression of this workload's transfer operators on the first, middle and
-    last double slab, at tol 1e-6.  That is the smallest tolerance the mixed path meets: its FP32
-    range finder rejects samples below 1e3 eps_32 of their own norm, so a request of 1e-8 (the
-    benchmark's) is compressed to about 1e-5 and the FP64 refinement of the solve restores the
-    1e-8 solution.  Checked: error against the dense FP32 operator it compresses <= 10 tol (2-norm),
-    and the largest rank between the truncated-SVD optimum of O6 on the oracle's operator (O3) and
-    that optimum plus the oversampling."""
+    last double slab, at tol 1e-5.  That is the smallest tolerance the mixed path meets: its FP32
+    sketch and range finder (samples below 1e3 eps_32 of their own norm are rejected as rounding
+    noise) floor the error near 2e-5 of ||S|| (measured 2.3e-5, 1.0e-5 and 7.6e-6 on these three
+    blocks for any request below 1e-5, the benchmark's 1e-8 included), and the FP64 refinement of
+    the solve restores the 1e-8 solution.  Checked: error against the dense FP32 operator it
+    compresses <= 10 tol (2-norm), and the largest rank between the truncated-SVD optimum of O6 on
+    the oracle's operator (O3) and that optimum plus the oversampling."""
     from paper_2510_25991_gb300 import ddst as D
     prob, sol, u, dev = full
     n, w = prob["n"], prob["w"]
-    tol, leaf, q = 1e-6, 128, 10
+    tol, leaf, q = 1e-5, 128, 10
     geo = O.slab_geometry(2, n, w)
     ng = geo.ngamma
     picks = ((0, 1), (geo.nds // 2, 1), (geo.nds - 1, -1))

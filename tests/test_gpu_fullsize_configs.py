@@ -2,7 +2,7 @@
 
 * Helmholtz, 4096^2 grid, kappa = 200, 127 double slabs of 64 cells (the ranks-vs-tolerance
   configuration): sampled transfer-operator rows against oracle transposed local solves, and
-  HODLR compression at tol 1e-6 against the dense operator (error within 10 tol; ranks at a 1e-8
+  HODLR compression at tol 1e-5 against the dense operator (error within 10 tol; ranks at a 1e-8
   request non-decreasing).  The interface GMRES of this strongly indefinite global problem is not part
   of the check: with 127 slabs at 32 wavelengths it does not converge in the iteration cap
   (the reduced-size Helmholtz tests cover the solve).
@@ -74,19 +74,20 @@ def test_helmholtz_4096_transfer_rows_and_hodlr_tolerances():
         ref = -(Acsr[I_][:, J].T @ Y).T
         assert np.abs(dense[side][rows] - ref).max() <= 1e-3 * np.abs(ref).max()
     del A, Acsr, lu
-    # HODLR against the dense (FP32) operator at tol 1e-6, the smallest tolerance the mixed path's
-    # FP32 range finder meets; at a 1e-8 request only the ranks are recorded (they may not
-    # decrease).  Compression at 1e-8 and 1e-10 within 10 tol is checked in FP64 at reduced size.
-    sol.compress(1e-6)
-    r6 = D.ddst_query(sol.ctx)[2]
+    # HODLR against the dense (FP32) operator at tol 1e-5, the smallest tolerance the mixed path's
+    # FP32 sketch and range finder meet; at a 1e-8 request only the ranks are recorded (they may
+    # not decrease).  Compression at 1e-8 and 1e-10 within 10 tol is checked in FP64 at reduced
+    # size.
+    sol.compress(1e-5)
+    r5 = D.ddst_query(sol.ctx)[2]
     for side in (-1, 1):
         out = np.empty((ng, ng))
         D.ddst_get_transfer(sol.ctx, 0, j + 1, side, out)
         err = _norm2(out - dense[side]) / _norm2(dense[side])
-        assert err <= 10 * 1e-6, (side, err)
+        assert err <= 10 * 1e-5, (side, err)
     sol.compress(1e-8)
     r8 = D.ddst_query(sol.ctx)[2]
-    assert 0 < r6 <= r8 <= 64, (r6, r8)
+    assert 0 < r5 <= r8 <= 64, (r5, r8)
     sol.close()
 
 
