@@ -293,6 +293,98 @@ def bench_c4(peaks, src, steps=2, warmup=1, certify=True):
     return out
 
 
+def bench_c5(steps=2, warmup=1):
+    """The adjoint batch: 64 independent 2D problems -div(a grad u) = f with grids uneven in
+    256^2 .. 1024^2 and 8, 16 or 32 slabs (slab widths 8 .. 128 cells), loss 1/2 ||u - u_obs||^2,
+    gradients with respect to a, f and g.  A step is one batched setup (every problem's local
+    factors; problems with blocks above 128 on the large-block kernels), transfer operators
+    (explicit for the single-CTA classes, matrix-free for the others), the batched forward solve
+    and the batched adjoint; the metric is seconds per adjoint gradient (step time / 64).  Inputs
+    resident on the device; the end-to-end leg passes host arrays through the C ABI instead."""
+    import numpy as np
+    import torch
+
+    import ddst_inputs as I
+    from paper_2510_25991_gb300 import ddst as D
+    specs = I.batch_specs(64)
+    probs = [I.batch_problem(s_) for s_ in specs]
+    nprob = len(probs)
+    devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    rng = np.random.default_rng(2)
+    host = [dict(a=p["a"], f=p["f"], g=p["g"], obs=rng.standard_normal((p["n"] - 1, p["n"] - 1)))
+            for p in probs]
+    dev = [{k: devt(v) for k, v in h.items()} for h in host]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(bufs, on_device):
+        spec = [dict(dim=2, n=p["n"], w=p["w"], a=b["a"], b=(0.0, 0.0, 0.0)) for p, b in zip(probs, bufs)]
+        sol = D.Solver(spec, precision="mixed")
+        sol.build_transfer()
+        D.ddst_solve_batch(sol.ctx, [b["f"] for b in bufs], [b["g"] for b in bufs], [b["u"] for b in bufs])
+        # dL/du = u - u_obs (elementwise, on the buffers' own side)
+        for b in bufs:
+            if on_device:
+                torch.sub(b["u"], b["obs"], out=b["dLdu"])
+            else:
+                np.subtract(b["u"], b["obs"], out=b["dLdu"])
+        st, info = D.ddst_solve_adjoint_batch(sol.ctx, [b["dLdu"] for b in bufs], [b["df"] for b in bufs],
+                                              [b["dg"] for b in bufs], [b["da"] for b in bufs])
+        sol.close()
+        return info
+
+    for b, p in zip(dev, probs):
+        n = p["n"]
+        b.update(u=torch.empty((n - 1, n - 1), dtype=torch.float64, device="cuda"))
+        b.update(dLdu=torch.empty_like(b["u"]), df=torch.empty_like(b["u"]),
+                 dg=torch.empty((n + 1, n + 1), dtype=torch.float64, device="cuda"))
+        b.update(da=torch.empty_like(b["dg"]))
+    ts = []
+    for it in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        info = step(dev, True)
+        e1.record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.mean(ts)
+    # end to end: pinned host arrays through the C ABI (the library stages them in and out)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+    hb = []
+    for h, p in zip(host, probs):
+        n = p["n"]
+        hb.append(dict(a=pin(h["a"]), f=pin(h["f"]), g=pin(h["g"]), obs=h["obs"],
+                       u=pin(np.empty((n - 1, n - 1))), dLdu=pin(np.empty((n - 1, n - 1))),
+                       df=pin(np.empty((n - 1, n - 1))), dg=pin(np.empty((n + 1, n + 1))),
+                       da=pin(np.empty((n + 1, n + 1)))))
+    t0 = time.perf_counter()
+    step(hb, False)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(8 * (h["a"].size + h["f"].size + h["g"].size + h["dLdu"].size) for h in hb)
+    d2h = sum(8 * (h["u"].size + h["df"].size + h["dg"].size + h["da"].size) for h in hb)
+    dof = sum((p["n"] - 1) ** 2 for p in probs)
+    # the oracle's adjoint gradient of the median problem on the host cores
+    from oracle import ddst_oracle as O
+    order = np.argsort([p["n"] for p in probs], kind="stable")
+    pm = probs[order[nprob // 2]]
+    t0 = time.perf_counter()
+    O.loss_and_gradients(pm, np.zeros((pm["n"] - 1) ** 2))
+    t_or = time.perf_counter() - t0
+    return {"workload": f"adjoint batch: {nprob} problems -div(a grad u) = f, grids 256^2..1024^2 "
+                        "(n = 64 m, m ~ U{4..16}), 8/16/32 slabs, loss 1/2 ||u - u_obs||^2, "
+                        "gradients wrt a, f, g; mixed precision",
+            "dof_total": dof, "problems": nprob,
+            "large_block_problems": sum(1 for p in probs if 2 * p["w"] - 1 > 128),
+            "s_per_adjoint_gradient": ms / 1e3 / nprob, "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "gmres_iters_adjoint": info["gmres_iters"],
+            "e2e": {"s_per_adjoint_gradient": e2e_s / nprob, "unit": "s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "oracle_median_problem": {"n": pm["n"], "w": pm["w"], "s_per_gradient": t_or,
+                                      "kind": "oracle loss_and_gradients (SuperLU, FP64)",
+                                      "cpu_model": cpu_model(), "cores": os.cpu_count()}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,6 +401,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
+    ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if ws > 1:
@@ -515,6 +608,8 @@ def main():
             "gpu_launches": int(launches), "wall_s": wall}
     if rank == 0 and not args.no_c4:
         line["c4"] = bench_c4(peaks, src)
+    if rank == 0 and not args.no_c5:
+        line["c5"] = bench_c5()
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(args.ref_n or 512)
     if rank == 0:
