@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
   const int64_t src = (int64_t)blockIdx.x * 8 + warp;
   if (src >= ng) return;
   double acc = 0.0;
-  if (s.j <= P.nds - 1) {  // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}
+  // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}; a neighbour without explicit
+  // blocks (a class applied matrix-free, offset -1) contributes nothing here
+  if (s.j <= P.nds - 1 && slabs[sidx + 1].sp_off >= 0) {
     const SlabDesc t = slabs[sidx + 1];
     const T* col = S + t.sp_off + src * ng;
     const double* xv = x + t.if_off;
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
     }
     acc += static_cast<double>(part);
   }
-  if (s.j >= 2) {
+  if (s.j >= 2 && slabs[sidx - 1].sn_off >= 0) {
     const SlabDesc t = slabs[sidx - 1];
     const T* col = S + t.sn_off + src * ng;
     const double* xv = x + t.if_off;
