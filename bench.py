@@ -214,7 +214,7 @@ def _certify(prob, u):
     return O.diffusion_error_bound(prob, u)
 
 
-def bench_c4(peaks, src, steps=2, warmup=1, certify=True):
+def bench_c4(peaks, src, steps=2, warmup=1, certify=True, n=128, w=16):
     """The 3D variable-coefficient workload: 128^3 cells (2,048,383 unknowns), 8 slabs of 16
     cells, a = exp(8 Fourier modes in 3D), mixed precision to 1e-8 (estimated).  7 double slabs
     with dense blocks of 31 * 127 = 3937 unknowns (padded to 3968): one-sided block LU on the
@@ -228,7 +228,6 @@ def bench_c4(peaks, src, steps=2, warmup=1, certify=True):
 
     import ddst_inputs as I
     from paper_2510_25991_gb300 import ddst as D
-    n, w = 128, 16
     prob = I.make_problem("vardiff3d", n=n, w=w)
     dof = (n - 1) ** 3
     devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -402,6 +401,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
     ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
+    ap.add_argument("--only-c4", action="store_true",
+                    help="run only the 3D section and print it alone (for profiling smaller cases)")
+    ap.add_argument("--c4-n", type=int, default=128)
+    ap.add_argument("--c4-w", type=int, default=16)
+    ap.add_argument("--c4-steps", type=int, default=2)
+    ap.add_argument("--c4-warmup", type=int, default=1)
     args = ap.parse_args()
     ws, rank, local = _dist()
     if ws > 1:
@@ -423,6 +428,11 @@ def main():
 
     torch.cuda.set_device(local)
     B.build()
+    if args.only_c4:
+        peaks, src = _peaks()
+        print(json.dumps(bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
+                                  certify=False, n=args.c4_n, w=args.c4_w)), flush=True)
+        return
     n, w = args.n, args.w
     prob = I.make_problem("convdiff2d", n=n, w=w)
     dof = (n - 1) ** 2
@@ -607,7 +617,8 @@ def main():
             "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
     if rank == 0 and not args.no_c4:
-        line["c4"] = bench_c4(peaks, src)
+        line["c4"] = bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
+                              n=args.c4_n, w=args.c4_w)
     if rank == 0 and not args.no_c5:
         line["c5"] = bench_c5()
     if rank == 0 and ws == 1 and not args.no_cpu:

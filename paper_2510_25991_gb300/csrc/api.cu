@@ -115,9 +115,13 @@ struct ddst_ctx {
   std::map<int, bool> big;               // M -> factored by the large-block kernels
   int64_t fac_big_elems = 0;
   void* Fbig = nullptr;
-  struct BigWork { void *C = nullptr, *XqT = nullptr, *RT = nullptr, *Pinv = nullptr; };
+  struct BigWork { void *C[2] = {}, *XqT[2] = {}, *RT[2] = {}, *Pinv[2] = {}; };  // two sets
   std::map<int, BigWork> bigw;
   bool big_tc = false;                   // large-block Gauss-Jordan updates on tcgen05
+  // look-ahead of the large-block factorization: panel steps on a high-priority stream, the bulk
+  // updates on a second one
+  cudaStream_t s_hi = nullptr, s_lo = nullptr;
+  cudaEvent_t big_ev[5] = {};
   // matrix-free interface operator (no explicit S): its own slab-local buffers, so that an
   // application inside GMRES leaves the DD solve's vectors untouched
   // matfree: every class is applied matrix-free; mf_any: at least one (large-block classes in
@@ -376,16 +380,28 @@ ddst_status factor_all(ddst_ctx* ctx) {
                      nullptr, 0, ctx->d_st, st);
   }
   CK(cudaGetLastError());
-  // large blocks: one-sided block LU, every slab of a class one block row at a time
-  for (auto& kv : ctx->cls) {
-    if (!ctx->big[kv.first]) continue;
-    ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
-    for (int k = 1; k <= ctx->cls_maxnb[kv.first]; ++k) {
-      launch_big_factor_step<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first], (int)kv.second.size(),
-                                (const T*)ctx->pack, (T*)ctx->Fbig, k, (T*)bw.C, (T*)bw.XqT,
-                                (T*)bw.RT, (T*)bw.Pinv, ctx->big_tc, ctx->d_st, st);
-      CK(cudaGetLastError());
+  // large blocks: one-sided block LU, every slab of a class one block row at a time, on the
+  // look-ahead streams, joined back into the context stream at the end
+  if (ctx->s_hi) {
+    CK(cudaEventRecord(ctx->big_ev[3], st));
+    CK(cudaStreamWaitEvent(ctx->s_hi, ctx->big_ev[3], 0));
+    for (auto& kv : ctx->cls) {
+      if (!ctx->big[kv.first]) continue;
+      ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
+      T* C[2] = {(T*)bw.C[0], (T*)bw.C[1]};
+      T* XqT[2] = {(T*)bw.XqT[0], (T*)bw.XqT[1]};
+      T* RT[2] = {(T*)bw.RT[0], (T*)bw.RT[1]};
+      T* Pinv[2] = {(T*)bw.Pinv[0], (T*)bw.Pinv[1]};
+      for (int k = 1; k <= ctx->cls_maxnb[kv.first]; ++k) {
+        launch_big_factor_step<T>(kv.first, ctx->d_slabs, ctx->d_cls[kv.first],
+                                  (int)kv.second.size(), (const T*)ctx->pack, (T*)ctx->Fbig, k, C,
+                                  XqT, RT, Pinv, ctx->big_tc, ctx->d_st, ctx->s_hi, ctx->s_lo,
+                                  ctx->big_ev);
+        CK(cudaGetLastError());
+      }
     }
+    CK(cudaEventRecord(ctx->big_ev[4], ctx->s_hi));
+    CK(cudaStreamWaitEvent(st, ctx->big_ev[4], 0));
   }
   return DDST_OK;
 }
@@ -530,11 +546,29 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       // (tensor-core path), hence twice the plain size
       ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
       const size_t panel = 2 * es * kv.second.size() * (size_t)kv.first * 128;
-      AL(bw.C, panel);
-      AL(bw.XqT, panel);
-      AL(bw.RT, panel);
-      AL(bw.Pinv, 2 * es * kv.second.size() * 128 * 128);
+      for (int b = 0; b < 2; ++b) {
+        AL(bw.C[b], panel);
+        AL(bw.XqT[b], panel);
+        AL(bw.RT[b], panel);
+        AL(bw.Pinv[b], 2 * es * kv.second.size() * 128 * 128);
+      }
     }
+  }
+  if (any_big) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if ((e = cudaStreamCreateWithPriority(&ctx->s_hi, cudaStreamNonBlocking, hi)) != cudaSuccess ||
+        (e = cudaStreamCreateWithPriority(&ctx->s_lo, cudaStreamNonBlocking, lo)) != cudaSuccess) {
+      ddst_status s_ = cuda_fail(nullptr, e, "stream create");
+      ddst_destroy(ctx);
+      return s_;
+    }
+    for (cudaEvent_t& ev : ctx->big_ev)
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+        ddst_status s_ = cuda_fail(nullptr, e, "event create");
+        ddst_destroy(ctx);
+        return s_;
+      }
   }
   if (ctx->mf_any) {
     AL(ctx->mf_b, es * ctx->tot_loc);
@@ -1407,6 +1441,10 @@ void ddst_destroy(ddst_ctx* ctx) {
   for (auto& g : ctx->arn_graph)
     if (g) cudaGraphExecDestroy(g);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->s_hi) { cudaStreamSynchronize(ctx->s_hi); cudaStreamDestroy(ctx->s_hi); }
+  if (ctx->s_lo) { cudaStreamSynchronize(ctx->s_lo); cudaStreamDestroy(ctx->s_lo); }
+  for (cudaEvent_t ev : ctx->big_ev)
+    if (ev) cudaEventDestroy(ev);
   ctx->hodlr.release();
   for (void* p : ctx->owned) cudaFree(p);
   delete ctx;

@@ -200,6 +200,38 @@ __global__ void __launch_bounds__(512) k_big_pivot(const SlabDesc* __restrict__ 
 // ---------------------------------------------------------------------------------------------
 enum { GJ_ROW = 0, GJ_UPDATE = 1 };
 
+// Tiles of the update of panel q (I != q), split for the look-ahead: set 0 all of them
+// ((nP-1) nP tiles), set 1 the row block q+1 and the column block q+1 (2 nP - 2), which the
+// next panel's pivot and row steps read, set 2 the rest ((nP-2)(nP-1)).
+enum { GJ_ALL = 0, GJ_NEXT = 1, GJ_REST = 2 };
+__host__ __device__ __forceinline__ int gj_count(int tset, int nP) {
+  return tset == GJ_ALL ? (nP - 1) * nP : tset == GJ_NEXT ? 2 * nP - 2 : (nP - 2) * (nP - 1);
+}
+__device__ __forceinline__ void gj_tile(int tset, int nP, int q, int t, int& I, int& J) {
+  if (tset == GJ_ALL) {
+    I = t / nP;
+    J = t - I * nP;
+    if (I >= q) ++I;
+    return;
+  }
+  if (tset == GJ_NEXT) {
+    if (t < nP) {
+      I = q + 1;
+      J = t;
+      return;
+    }
+    I = t - nP;          // column q+1, rows other than q and q+1
+    if (I >= q) I += 2;
+    J = q + 1;
+    return;
+  }
+  const int c = nP - 1;  // rows other than q and q+1, columns other than q+1
+  I = t / c;
+  J = t - I * c;
+  if (I >= q) I += 2;
+  if (J >= q + 1) ++J;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_big_gemm_fma(const SlabDesc* __restrict__ slabs,
                                                       const int* __restrict__ ids,
@@ -207,15 +239,20 @@ __global__ void __launch_bounds__(256) k_big_gemm_fma(const SlabDesc* __restrict
                                                       const T* __restrict__ Cb,
                                                       const T* __restrict__ XqT,
                                                       T* __restrict__ RT,
-                                                      const T* __restrict__ Pinv) {
+                                                      const T* __restrict__ Pinv, int tset) {
   constexpr int KC = 16;
   __shared__ T As[KC][BT + 4];
   __shared__ T Bs[KC][BT + 4];
   const SlabDesc s = slabs[ids[blockIdx.z]];
   if (k > s.nb) return;
   const int M = s.M;
-  const int J = blockIdx.x, I = MODE == GJ_ROW ? J : (int)blockIdx.y;
-  if (MODE == GJ_ROW ? (J == q) : (I == q)) return;
+  int I, J;
+  if (MODE == GJ_ROW) {
+    J = I = blockIdx.x;
+    if (J == q) return;
+  } else {
+    gj_tile(tset, M / BT, q, blockIdx.x, I, J);
+  }
   T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
   const int64_t wo = (int64_t)blockIdx.z * M * BT;
   const T* A = MODE == GJ_ROW ? XqT + wo + (int64_t)J * BT * BT : Cb + wo + (int64_t)I * BT * BT;
@@ -306,7 +343,7 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
     k_big_gemm_tc(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
                   float* __restrict__ F, int k, int q, const float* __restrict__ Cs,
                   const float* __restrict__ XqTs, float* __restrict__ RTs,
-                  const float* __restrict__ Pis, DevStatus* st) {
+                  const float* __restrict__ Pis, DevStatus* st, int tset) {
   using C = GjTc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = smem_raw;
@@ -322,8 +359,13 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   const SlabDesc s = slabs[sid];
   if (k > s.nb) return;
   const int M = s.M, nP = M / BT;
-  const int J = blockIdx.x, I = MODE == GJ_ROW ? J : (int)blockIdx.y;
-  if (MODE == GJ_ROW ? (J == q) : (I == q)) return;
+  int I, J;
+  if (MODE == GJ_ROW) {
+    J = I = blockIdx.x;
+    if (J == q) return;
+  } else {
+    gj_tile(tset, nP, q, blockIdx.x, I, J);
+  }
   float* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
   const int64_t wo = (int64_t)blockIdx.z * nP * SPLIT_TILE;
   const float* A = MODE == GJ_ROW ? XqTs + wo + (int64_t)J * SPLIT_TILE : Cs + wo + (int64_t)I * SPLIT_TILE;
@@ -646,48 +688,91 @@ static size_t pivot_smem() {
   return gj > stage ? gj : stage;
 }
 
+// One block row k of the large-block factorization with look-ahead.  Stream sh (high priority)
+// runs the Sigma_k formation and, per panel q, the update of the next panel's row and column
+// blocks followed by that panel's pivot and row steps; stream sl runs the rest of panel q's
+// update at the same time.  The work buffers alternate between two sets by panel parity, so the
+// next panel's pivot step never overwrites operands the current update still reads.  ev: three
+// events owned by the caller.  On return both streams' work is ordered before later work on sh.
 template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
-                            const T* pack, T* F, int k, T* Cb, T* XqT, T* RT, T* Pinv,
-                            bool tensor_cores, DevStatus* st, cudaStream_t s) {
+                            const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
+                            T* const RT[2], T* const Pinv[2], bool tensor_cores, DevStatus* st,
+                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev) {
   const int nP = M / BT;
-  note_launch();
-  k_big_sigma<T><<<dim3(512, nids), 256, 0, s>>>(d_slabs, d_ids, pack, F, k);
   bool tc = false;
   if constexpr (sizeof(T) == 4) tc = tensor_cores;
+  const size_t psm = tc ? pivot_smem<T, true>() : pivot_smem<T, false>();
+  auto pivot = [&](int q) {
+    const int b = q & 1;
+    note_launch();
+    if constexpr (sizeof(T) == 4) {
+      if (tc) {
+        k_big_pivot<float, true><<<dim3(nP, nids), 512, psm, sh>>>(d_slabs, d_ids, pack, F, k, q,
+                                                                   Cb[b], XqT[b], RT[b], Pinv[b], st);
+        return;
+      }
+    }
+    k_big_pivot<T, false><<<dim3(nP, nids), 512, psm, sh>>>(d_slabs, d_ids, pack, F, k, q, Cb[b],
+                                                            XqT[b], RT[b], Pinv[b], st);
+  };
+  auto row = [&](int q) {
+    const int b = q & 1;
+    note_launch();
+    if constexpr (sizeof(T) == 4) {
+      if (tc) {
+        k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, sh>>>(
+            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, GJ_ALL);
+        return;
+      }
+    }
+    k_big_gemm_fma<T, GJ_ROW><<<dim3(nP, 1, nids), 256, 0, sh>>>(d_slabs, d_ids, F, k, q, Cb[b],
+                                                                 XqT[b], RT[b], Pinv[b], GJ_ALL);
+  };
+  auto update = [&](int q, int tset, cudaStream_t s) {
+    const int b = q & 1;
+    note_launch();
+    const dim3 grid(gj_count(tset, nP), 1, nids);
+    if constexpr (sizeof(T) == 4) {
+      if (tc) {
+        k_big_gemm_tc<GJ_UPDATE><<<grid, GjTc::THREADS, GjTc::SMEM, s>>>(
+            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, tset);
+        return;
+      }
+    }
+    k_big_gemm_fma<T, GJ_UPDATE><<<grid, 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb[b], XqT[b],
+                                                      RT[b], Pinv[b], tset);
+  };
   if (tc) {
     if constexpr (sizeof(T) == 4) {
-      const size_t psm = pivot_smem<float, true>();
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<float, true>), psm);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_ROW>), GjTc::SMEM);
       raise_smem_limit(reinterpret_cast<const void*>(&k_big_gemm_tc<GJ_UPDATE>), GjTc::SMEM);
-      for (int q = 0; q < nP; ++q) {
-        note_launch();
-        k_big_pivot<float, true><<<dim3(nP, nids), 512, psm, s>>>(d_slabs, d_ids, pack, F, k, q,
-                                                                  Cb, XqT, RT, Pinv, st);
-        if (nP == 1) continue;
-        note_launch(2);
-        k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
-            d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
-        k_big_gemm_tc<GJ_UPDATE><<<dim3(nP, nP, nids), GjTc::THREADS, GjTc::SMEM, s>>>(
-            d_slabs, d_ids, F, k, q, Cb, XqT, RT, Pinv, st);
-      }
     }
-    return;
+  } else {
+    raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T, false>), psm);
   }
-  const size_t psm = pivot_smem<T, false>();
-  raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T, false>), psm);
+  cudaEvent_t evA = ev[0], evB[2] = {ev[1], ev[2]};
+  note_launch();
+  k_big_sigma<T><<<dim3(512, nids), 256, 0, sh>>>(d_slabs, d_ids, pack, F, k);
+  pivot(0);
+  if (nP == 1) return;
+  row(0);
+  cudaEventRecord(evA, sh);
   for (int q = 0; q < nP; ++q) {
-    note_launch();
-    k_big_pivot<T, false><<<dim3(nP, nids), 512, psm, s>>>(d_slabs, d_ids, pack, F, k, q, Cb, XqT,
-                                                           RT, Pinv, st);
-    if (nP == 1) continue;
-    note_launch(2);
-    k_big_gemm_fma<T, GJ_ROW><<<dim3(nP, 1, nids), 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb, XqT,
-                                                                RT, Pinv);
-    k_big_gemm_fma<T, GJ_UPDATE><<<dim3(nP, nP, nids), 256, 0, s>>>(d_slabs, d_ids, F, k, q, Cb,
-                                                                    XqT, RT, Pinv);
+    const bool ahead = q + 1 < nP;
+    cudaStreamWaitEvent(sl, evA, 0);
+    update(q, ahead ? GJ_REST : GJ_ALL, sl);
+    cudaEventRecord(evB[q & 1], sl);
+    if (ahead) {
+      if (q >= 1) cudaStreamWaitEvent(sh, evB[(q - 1) & 1], 0);  // rest of panel q-1 done
+      update(q, GJ_NEXT, sh);
+      pivot(q + 1);
+      row(q + 1);
+      cudaEventRecord(evA, sh);
+    }
   }
+  cudaStreamWaitEvent(sh, evB[(nP - 1) & 1], 0);
 }
 
 template <typename T>
@@ -744,11 +829,14 @@ void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, con
 }
 
 template void launch_big_factor_step<float>(int, const SlabDesc*, const int*, int, const float*,
-                                            float*, int, float*, float*, float*, float*, bool,
-                                            DevStatus*, cudaStream_t);
+                                            float*, int, float* const[2], float* const[2],
+                                            float* const[2], float* const[2], bool, DevStatus*,
+                                            cudaStream_t, cudaStream_t, cudaEvent_t*);
 template void launch_big_factor_step<double>(int, const SlabDesc*, const int*, int,
-                                             const double*, double*, int, double*, double*,
-                                             double*, double*, bool, DevStatus*, cudaStream_t);
+                                             const double*, double*, int, double* const[2],
+                                             double* const[2], double* const[2],
+                                             double* const[2], bool, DevStatus*, cudaStream_t,
+                                             cudaStream_t, cudaEvent_t*);
 template void launch_big_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
                                       const float*, const float*, float*, float*, int,
                                       cudaStream_t);

@@ -119,11 +119,15 @@ void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double*
 
 // bigblock.cu: large dense blocks (M a multiple of 128).  One block row k of the one-sided block
 // LU of every slab in the class (Sigma_k formed in the slot of F_k, inverted there by 128-wide
-// Gauss-Jordan panels); work buffers Cb, XqT, RT (nids x M x 128) and Pinv (nids x 128 x 128).
+// Gauss-Jordan panels with look-ahead on two streams: sh high priority, sl the bulk updates; ev
+// three events).  Two sets of work buffers (alternating by panel parity), each Cb, XqT, RT
+// (nids x M x 128, twice that when split for the tensor cores) and Pinv (nids x 128 x 128, or
+// twice).  All work is ordered before later work on sh.
 template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
-                            const T* pack, T* F, int k, T* Cb, T* XqT, T* RT, T* Pinv,
-                            bool tensor_cores, DevStatus* st, cudaStream_t s);
+                            const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
+                            T* const RT[2], T* const Pinv[2], bool tensor_cores, DevStatus* st,
+                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev);
 // Local solve x = A^{-1} b (transpose 0) or A^{-T} b (transpose 1) of every slab of the class;
 // z is a slab-local temporary.
 template <typename T>
