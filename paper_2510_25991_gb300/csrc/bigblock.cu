@@ -731,6 +731,7 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
   };
   auto update = [&](int q, int tset, cudaStream_t s) {
     const int b = q & 1;
+    if (gj_count(tset, nP) == 0) return;  // two panels: panel 0 has no tiles besides the next
     note_launch();
     const dim3 grid(gj_count(tset, nP), 1, nids);
     if constexpr (sizeof(T) == 4) {
