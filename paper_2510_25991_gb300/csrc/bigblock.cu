@@ -97,7 +97,9 @@ __device__ __forceinline__ void store_split_tile(const float* __restrict__ src, 
 // ---------------------------------------------------------------------------------------------
 // Pivot step of panel q.  grid = (M/128, slabs).  CTA q inverts P = X(Q,Q) in shared memory
 // (singular-pivot check against 1e3 eps |D_k|) and writes X(Q,Q) = P^{-1}; every other CTA b
-// copies the tiles X(B,Q) and X(Q,B) of the column and row panels.  Work buffers are per slab of
+// copies the tiles X(B,Q) and X(Q,B) of the column and row panels (on the tensor-core path only
+// for the first panel of a block row: later panels' tiles are written split by the update and row
+// steps of the panel before, and the launch has one CTA per slab).  Work buffers are per slab of
 // the class.  FMA path (plain row-major): C = X(:,Q) (M x 128), XqT = X(Q,:)^T (M x 128),
 // Pinv = P^{-1} (128 x 128), RT(Q rows) = P^{-T}.  Tensor-core path (SPLIT, split tiles): the
 // same operands as split tiles, C tile b = X(B,Q), XqT tile b = X(Q,B)^T, Pinv = P^{-1} and RT
@@ -120,7 +122,9 @@ __global__ void __launch_bounds__(512) k_big_pivot(const SlabDesc* __restrict__ 
   if (k > s.nb) return;
   const int M = s.M, nP = M / BT;
   T* X = F + s.fac_off + (int64_t)(k - 1) * M * M;
-  const int b = blockIdx.x;
+  // a grid of one CTA per slab launches only the pivot CTA (the copies were written by the
+  // previous panel's update and row steps)
+  const int b = gridDim.x == 1 ? q : (int)blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t Q0 = (int64_t)q * BT, B0 = (int64_t)b * BT;
   // per-slab work buffers: plain M x 128 panels, or nP split tiles
@@ -343,7 +347,8 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
     k_big_gemm_tc(const SlabDesc* __restrict__ slabs, const int* __restrict__ ids,
                   float* __restrict__ F, int k, int q, const float* __restrict__ Cs,
                   const float* __restrict__ XqTs, float* __restrict__ RTs,
-                  const float* __restrict__ Pis, DevStatus* st, int tset) {
+                  const float* __restrict__ Pis, DevStatus* st, int tset,
+                  float* __restrict__ Cn, float* __restrict__ XqTn) {
   using C = GjTc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = smem_raw;
@@ -412,6 +417,15 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
       tc_fence_after();
       // the ring is idle once the last MMA completed: reuse it for the 32 x 33 staging blocks
       float* E = reinterpret_cast<float*>(ring) + warp * 32 * 33;
+      // the next panel's operand tiles, written split here so its pivot launch need not copy:
+      // the update of the next panel's row and column blocks writes C_{q+1}(I) (column block
+      // q+1) and XqT_{q+1}(J) (row block q+1); the row step writes C_{q+1}(q) (tile (q, q+1))
+      const int qn = q + 1;
+      // C_{q+1} tile I = new X(I, q+1) (update: I != q+1; the row step's tile is (q, q+1))
+      const bool wr_c = Cn != nullptr && J == qn && (MODE == GJ_ROW || I != qn);
+      const bool wr_x = Cn != nullptr && MODE == GJ_UPDATE && I == qn && J != qn;  // XqT_{q+1}(J)
+      float* cn = wr_c ? Cn + wo + (int64_t)(MODE == GJ_ROW ? q : I) * SPLIT_TILE : nullptr;
+      float* xn = wr_x ? XqTn + wo + (int64_t)J * SPLIT_TILE : nullptr;
 #pragma unroll 1
       for (int cc = 0; cc < BT / 32; ++cc) {
         uint32_t v[32];
@@ -442,6 +456,14 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
 #pragma unroll 8
           for (int cl = 0; cl < 32; ++cl)
             X[(Q0 + cc * 32 + cl) * M + J0 + warp * 32 + lane] = E[lane * 33 + cl];
+          if (cn) {  // tile (q, q+1) of X is acc^T: element (r = cc*32 + cl, k = warp*32 + lane)
+            for (int cl = 0; cl < 32; ++cl) {
+              const float x = E[lane * 33 + cl], h = tf32_rna(x);
+              const int o = split_off(cc * 32 + cl, warp * 32 + lane);
+              cn[o] = h;
+              cn[BT * BT + o] = tf32_rna(x - h);
+            }
+          }
         } else {
           float nxt[32];
           if (keep && cc + 1 < BT / 32) {
@@ -449,8 +471,36 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
             for (int rr = 0; rr < 32; ++rr) nxt[rr] = xrow[(int64_t)rr * M + (cc + 1) * 32];
           }
 #pragma unroll
-          for (int rr = 0; rr < 32; ++rr)
-            xrow[(int64_t)rr * M + cc * 32] = (keep ? old[rr] : 0.f) - E[rr * 33 + lane];
+          for (int rr = 0; rr < 32; ++rr) {
+            const float x = (keep ? old[rr] : 0.f) - E[rr * 33 + lane];
+            xrow[(int64_t)rr * M + cc * 32] = x;
+            if (cn || xn) E[rr * 33 + lane] = x;  // keep the new values for the copies below
+          }
+          __syncwarp();
+          if (cn) {  // C_{q+1}(I): element (r = warp*32 + lane, k = cc*32 + e), this thread's row
+            const int r = warp * 32 + lane;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              float4 h, l;
+              const float x0 = E[lane * 33 + 4 * g], x1 = E[lane * 33 + 4 * g + 1];
+              const float x2 = E[lane * 33 + 4 * g + 2], x3 = E[lane * 33 + 4 * g + 3];
+              h.x = tf32_rna(x0); l.x = tf32_rna(x0 - h.x);
+              h.y = tf32_rna(x1); l.y = tf32_rna(x1 - h.y);
+              h.z = tf32_rna(x2); l.z = tf32_rna(x2 - h.z);
+              h.w = tf32_rna(x3); l.w = tf32_rna(x3 - h.w);
+              const int o = split_off(r, cc * 32 + 4 * g);
+              *reinterpret_cast<float4*>(cn + o) = h;
+              *reinterpret_cast<float4*>(cn + BT * BT + o) = l;
+            }
+          }
+          if (xn) {  // XqT_{q+1}(J): element (r = cc*32 + e, k = warp*32 + lane) = X(q+1 row, J col)
+            for (int e = 0; e < 32; ++e) {
+              const float x = E[lane * 33 + e], h = tf32_rna(x);
+              const int o = split_off(cc * 32 + e, warp * 32 + lane);
+              xn[o] = h;
+              xn[BT * BT + o] = tf32_rna(x - h);
+            }
+          }
           if (keep && cc + 1 < BT / 32) {
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr) old[rr] = nxt[rr];
@@ -681,6 +731,11 @@ __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__
 // ---------------------------------------------------------------------------------------------
 // Shared memory of the pivot kernel: the Gauss-Jordan block of CTA q, or the staging tiles of
 // the copying CTAs (two in the split path, one in the plain path).
+template <typename T>
+static size_t pivot_smem_gj() {  // the pivot CTA alone: its Gauss-Jordan block
+  return BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
+}
+
 template <typename T, bool SPLIT>
 static size_t pivot_smem() {
   const size_t gj = BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
@@ -708,8 +763,10 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
     note_launch();
     if constexpr (sizeof(T) == 4) {
       if (tc) {
-        k_big_pivot<float, true><<<dim3(nP, nids), 512, psm, sh>>>(d_slabs, d_ids, pack, F, k, q,
-                                                                   Cb[b], XqT[b], RT[b], Pinv[b], st);
+        // from the second panel on, the copies come from the previous panel's update and row
+        k_big_pivot<float, true><<<dim3(q == 0 ? nP : 1, nids), 512, q == 0 ? psm : pivot_smem_gj<float>(),
+                                   sh>>>(d_slabs, d_ids, pack, F, k, q, Cb[b], XqT[b], RT[b],
+                                         Pinv[b], st);
         return;
       }
     }
@@ -722,7 +779,8 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
     if constexpr (sizeof(T) == 4) {
       if (tc) {
         k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, sh>>>(
-            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, GJ_ALL);
+            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, GJ_ALL,
+            q + 1 < nP ? Cb[b ^ 1] : nullptr, q + 1 < nP ? XqT[b ^ 1] : nullptr);
         return;
       }
     }
@@ -736,8 +794,10 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
     const dim3 grid(gj_count(tset, nP), 1, nids);
     if constexpr (sizeof(T) == 4) {
       if (tc) {
+        const bool nx = tset == GJ_NEXT;
         k_big_gemm_tc<GJ_UPDATE><<<grid, GjTc::THREADS, GjTc::SMEM, s>>>(
-            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, tset);
+            d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, tset,
+            nx ? Cb[b ^ 1] : nullptr, nx ? XqT[b ^ 1] : nullptr);
         return;
       }
     }
