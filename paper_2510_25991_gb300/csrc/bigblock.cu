@@ -402,10 +402,15 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
   if (warp < 4) {
     // ---------------------------------------------------------------- epilogue (thread = row)
     const int64_t I0 = (int64_t)I * BT, J0 = (int64_t)J * BT, Q0 = (int64_t)q * BT;
-    // UPDATE: the old values of this warp's 32 rows, one 32-column block at a time, loaded
-    // ahead (the first block while the MMAs run), 32 independent loads in flight per lane
+    // Bulk path (the update outside the next panel's row and column blocks): -acc is staged row
+    // by row in the idle ring and added to X (stored, for column block q) by bulk copies, so the
+    // memory system performs the read-modify-write and the SM never waits for old values.
+    const bool bulk = MODE == GJ_UPDATE && tset != GJ_NEXT;
+    // Otherwise (the next panel's tiles, whose new values are also copied split, and the row
+    // step): the old values of this warp's 32 rows, one 32-column block at a time, loaded ahead
+    // (the first block while the MMAs run), 32 independent loads in flight per lane.
     float old[32];
-    const bool keep = MODE == GJ_UPDATE && J != q;
+    const bool keep = !bulk && MODE == GJ_UPDATE && J != q;
     float* xrow = X + (I0 + warp * 32) * M + J0 + lane;  // row warp*32 + rr at + rr * M
     if (keep) {
 #pragma unroll
@@ -413,7 +418,32 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
     }
     bool go = mbar_wait_ab(dready, 0, abort, st, sid, k);
     go = __all_sync(0xffffffffu, go);  // tcgen05.ld is warp-collective
-    if (go) {
+    if (go && bulk) {
+      tc_fence_after();
+      // row pitch 132 floats (528 B): 16-byte aligned rows and conflict-free 16-byte stores
+      constexpr int LP = BT + 4;
+      float* rowbuf = reinterpret_cast<float*>(ring) + (warp * 32 + lane) * LP;
+#pragma unroll 1
+      for (int cc = 0; cc < BT / 32; ++cc) {
+        uint32_t v[32];
+        tmem_ld32_wait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          float4 o;
+          o.x = -__uint_as_float(v[4 * g]);
+          o.y = -__uint_as_float(v[4 * g + 1]);
+          o.z = -__uint_as_float(v[4 * g + 2]);
+          o.w = -__uint_as_float(v[4 * g + 3]);
+          *reinterpret_cast<float4*>(rowbuf + cc * 32 + 4 * g) = o;
+        }
+      }
+      fence_proxy_async();  // this thread's row is visible to its bulk copy
+      float* dst = X + (I0 + warp * 32 + lane) * M + J0;
+      if (J == q) bulk_s2g(dst, rowbuf, BT * 4);
+      else bulk_s2g_add(dst, rowbuf, BT * 4);
+      bulk_commit();
+      bulk_wait_all();  // performed before the CTA exits (and before its ring is released)
+    } else if (go) {
       tc_fence_after();
       // the ring is idle once the last MMA completed: reuse it for the 32 x 33 staging blocks
       float* E = reinterpret_cast<float*>(ring) + warp * 32 * 33;

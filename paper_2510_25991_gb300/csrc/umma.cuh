@@ -170,4 +170,27 @@ __device__ __forceinline__ void mma_tf32_ss(uint32_t tmem_d, uint64_t a, uint64_
       : "memory");
 }
 
+// Bulk shared -> global copies of the async proxy: plain store or element-wise FP32 add at the
+// destination (performed by the memory system, so the issuing thread never reads the old
+// values).  Both addresses 16-byte aligned, bytes a multiple of 16; the shared-memory source
+// must be made visible to the async proxy first (fence.proxy.async).
+__device__ __forceinline__ void bulk_s2g(float* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g_add(float* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
+                   dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until every committed bulk group of this thread has completed (its writes performed).
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 }  // namespace ddst
