@@ -90,8 +90,9 @@ typedef struct {
 typedef struct {
   int precision;        /* DDST_FP64, DDST_MIXED or DDST_AUTO                                 */
   double gmres_tol;     /* relative residual target of each interface GMRES solve; <= 0 picks
-                           1e-2 for DDST_MIXED (inner solve of the refinement) or 1e-10 for
-                           DDST_FP64                                                          */
+                           1e-10 for DDST_FP64 and, for DDST_MIXED (inner solve of the
+                           refinement), 1e-3 with explicit transfer operators or 1e-2 when some
+                           are applied matrix-free                                            */
   int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES; used clamped to 1..1000)  */
   double refine_tol;    /* FP64 refinement stops when its error estimate, rho / (1 - rho) times
                            the last correction (rho: observed contraction; no estimate while
@@ -115,6 +116,10 @@ typedef struct {
                            two sweeps of local solves per GMRES iteration (no S stored), -1
                            automatic: matrix-free when some block is larger than 128 (or 64 in
                            FP64), explicit otherwise                                          */
+  int recompute_factors; /* 1: release the local factors once the transfer operators exist and
+                           recompute them at the start of every solve, adjoint or matrix-free
+                           application (the HBM they take is free in between, at the cost of
+                           one factorization per call); 0: keep them                          */
 } ddst_options;
 
 /* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
@@ -125,7 +130,8 @@ typedef struct {
   double rel_residual;    /* final ||b - A u||_2 / ||b||_2 in FP64                            */
   double est_rel_error;   /* refinement error bound rho/(1-rho) ||last correction|| / ||u||    */
   double t_factor, t_transfer, t_compress, t_solve;
-  int64_t bytes_factors;  /* device bytes of the local factors                                */
+  int64_t bytes_factors;  /* device bytes of the local factors (held only during setup and each
+                             call when recompute_factors is set)                              */
   int64_t bytes_transfer; /* device bytes of the transfer operators (dense or HODLR)          */
   int max_rank;           /* largest HODLR rank (0 when dense)                                */
   int fail_slab;          /* first slab with a singular pivot, else -1                        */
@@ -137,7 +143,7 @@ typedef struct {
 
 /* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
  * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234,
- * check_every 0 (automatic), tensor_cores 1, explicit_S -1.
+ * check_every 0 (automatic), tensor_cores 1, explicit_S -1, recompute_factors 0.
  * Testing hooks (environment variables, read at each use; they exercise the error paths without
  * a device fault):
  *  - DDST_FAIL_ALLOC=k: the k-th device allocation of the library after the variable was set

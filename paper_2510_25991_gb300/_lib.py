@@ -33,7 +33,8 @@ class ddst_options(C.Structure):
                 ("refine_tol", C.c_double), ("refine_max", C.c_int), ("k_max", C.c_int),
                 ("oversample", C.c_int), ("leaf_size", C.c_int), ("seed", C.c_uint64),
                 ("check_every", C.c_int), ("factor_chunks", C.c_int), ("factor_warmup", C.c_int),
-                ("tensor_cores", C.c_int), ("explicit_S", C.c_int)]
+                ("tensor_cores", C.c_int), ("explicit_S", C.c_int),
+                ("recompute_factors", C.c_int)]
 
 
 class ddst_info(C.Structure):

@@ -134,6 +134,7 @@ struct ddst_ctx {
   double* if_kx = nullptr;
   long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
   bool solve_bufs_ready = false;
+  bool factors_valid = false;            // local factors present (recompute_factors releases them)
 };
 
 namespace {
@@ -407,6 +408,65 @@ ddst_status factor_all(ddst_ctx* ctx) {
 }
 
 // --------------------------------------------------------------------------------------------
+// Factor storage: allocated at setup, and (recompute_factors) released once the transfer
+// operators exist and recomputed for every solve
+// --------------------------------------------------------------------------------------------
+void dfree(ddst_ctx* ctx, void*& p) {
+  if (!p) return;
+  auto it = std::find(ctx->owned.begin(), ctx->owned.end(), p);
+  if (it != ctx->owned.end()) ctx->owned.erase(it);
+  cudaFree(p);
+  p = nullptr;
+}
+
+cudaError_t alloc_factors(ddst_ctx* ctx) {
+  const size_t es = ctx->esz;
+  cudaError_t e;
+#define AF(ptr, bytes) if ((e = dalloc(ctx, &(ptr), (bytes))) != cudaSuccess) return e;
+  AF(ctx->F, es * ctx->fac_elems);
+  AF(ctx->B, es * ctx->fac_elems);
+  AF(ctx->G, es * ctx->fac_elems);
+  AF(ctx->Ft, es * ctx->fac_elems);
+  AF(ctx->Bt, es * ctx->fac_elems);
+  if (ctx->use_tc) {
+    AF(ctx->Uhi, sizeof(float) * 2 * ctx->fac_elems);
+    AF(ctx->Ulo, sizeof(float) * 2 * ctx->fac_elems);
+  }
+  if (ctx->fac_big_elems > 0) AF(ctx->Fbig, es * ctx->fac_big_elems);
+  for (auto& kv : ctx->cls) {
+    if (!ctx->big[kv.first]) continue;
+    // panels of 128 columns per slab: plain (FMA path) or split into TF32 hi/lo parts
+    // (tensor-core path), hence twice the plain size
+    ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
+    const size_t panel = 2 * es * kv.second.size() * (size_t)kv.first * 128;
+    for (int b = 0; b < 2; ++b) {
+      AF(bw.C[b], panel);
+      AF(bw.XqT[b], panel);
+      AF(bw.RT[b], panel);
+      AF(bw.Pinv[b], 2 * es * kv.second.size() * 128 * 128);
+    }
+  }
+#undef AF
+  ctx->factors_valid = false;
+  return cudaSuccess;
+}
+
+void release_factors(ddst_ctx* ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  void** arrays[] = {&ctx->F, &ctx->B, &ctx->G, &ctx->Ft, &ctx->Bt, &ctx->Fbig,
+                     reinterpret_cast<void**>(&ctx->Uhi), reinterpret_cast<void**>(&ctx->Ulo)};
+  for (void** a : arrays) dfree(ctx, *a);
+  for (auto& kv : ctx->bigw)
+    for (int b = 0; b < 2; ++b) {
+      dfree(ctx, kv.second.C[b]);
+      dfree(ctx, kv.second.XqT[b]);
+      dfree(ctx, kv.second.RT[b]);
+      dfree(ctx, kv.second.Pinv[b]);
+    }
+  ctx->factors_valid = false;
+}
+
+// --------------------------------------------------------------------------------------------
 // Setup
 // --------------------------------------------------------------------------------------------
 ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
@@ -421,10 +481,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   if (opt) ctx->opt = *opt; else ddst_options_default(&ctx->opt);
   ctx->prec = ctx->opt.precision == DDST_FP64 ? DDST_FP64 : DDST_MIXED;
   ctx->esz = ctx->prec == DDST_FP64 ? 8 : 4;
-  // automatic inner tolerance: the FP32 DD solve is only an approximate inverse (refinement
-  // contracts by ~10x per step), so solving its interface system beyond 1e-2 is wasted work;
-  // the FP64 DD solve is accurate, so a tight inner tolerance finishes in one or two steps.
-  if (!(ctx->opt.gmres_tol > 0.0)) ctx->opt.gmres_tol = ctx->prec == DDST_FP64 ? 1e-10 : 1e-2;
+  const bool auto_tol = !(ctx->opt.gmres_tol > 0.0);  // picked once the operator kind is known
   int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, fac_big_off = 0, pack_off = 0,
           loc_off = 0, s_off = 0;
   for (int q = 0; q < nprob; ++q) {
@@ -511,6 +568,13 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     if (ctx->mf_cls[kv.first]) mf_ids.insert(mf_ids.end(), kv.second.begin(), kv.second.end());
   }
   ctx->n_mf_ids = (int)mf_ids.size();
+  // automatic inner tolerance: the FP64 DD solve is accurate, so a tight inner tolerance
+  // finishes in one or two refinement steps.  The FP32 DD solve is only an approximate inverse
+  // inside the FP64 refinement: with explicit operators (a 120 us iteration against a few ms of
+  // local solves per refinement step) 1e-3 balances iterations against steps; with matrix-free
+  // operators every iteration is itself a local solve, and 1e-2 is cheaper (both measured on
+  // the 2048^2 and 127^3 workloads).
+  if (auto_tol) ctx->opt.gmres_tol = ctx->prec == DDST_FP64 ? 1e-10 : (ctx->mf_any ? 1e-2 : 1e-3);
   ctx->big_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
   const int nslab = (int)ctx->slabs.size();
   const size_t es = ctx->esz;
@@ -527,32 +591,14 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   AL(ctx->d_a, sizeof(double) * ctx->tot_nodes);
   AL(ctx->d_c, sizeof(double) * ctx->tot_nodes);
   AL(ctx->pack, es * ctx->pack_elems);
-  AL(ctx->F, es * ctx->fac_elems);
-  AL(ctx->B, es * ctx->fac_elems);
-  AL(ctx->G, es * ctx->fac_elems);
-  AL(ctx->Ft, es * ctx->fac_elems);
-  AL(ctx->Bt, es * ctx->fac_elems);
   AL(ctx->loc_b, es * ctx->tot_loc);
   AL(ctx->loc_bf, es * ctx->tot_loc);
   AL(ctx->loc_bb, es * ctx->tot_loc);
   AL(ctx->loc_x, es * ctx->tot_loc);
-  if (ctx->fac_big_elems > 0) AL(ctx->Fbig, es * ctx->fac_big_elems);
   for (auto& kv : ctx->cls) {
     int* d = nullptr;
     AL(d, sizeof(int) * kv.second.size());
     ctx->d_cls[kv.first] = d;
-    if (ctx->big[kv.first]) {
-      // panels of 128 columns per slab: plain (FMA path) or split into TF32 hi/lo parts
-      // (tensor-core path), hence twice the plain size
-      ddst_ctx::BigWork& bw = ctx->bigw[kv.first];
-      const size_t panel = 2 * es * kv.second.size() * (size_t)kv.first * 128;
-      for (int b = 0; b < 2; ++b) {
-        AL(bw.C[b], panel);
-        AL(bw.XqT[b], panel);
-        AL(bw.RT[b], panel);
-        AL(bw.Pinv[b], 2 * es * kv.second.size() * 128 * 128);
-      }
-    }
   }
   if (any_big) {
     int lo = 0, hi = 0;
@@ -582,11 +628,12 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   ctx->use_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0 && !ctx->matfree;
   for (auto& kv : ctx->cls)
     if (!ctx->mf_cls[kv.first] && kv.first > 64) ctx->use_tc = false;
-  if (ctx->use_tc) {
-    AL(ctx->Uhi, sizeof(float) * 2 * ctx->fac_elems);
-    AL(ctx->Ulo, sizeof(float) * 2 * ctx->fac_elems);
-  }
 #undef AL
+  if ((e = alloc_factors(ctx)) != cudaSuccess) {
+    ddst_status s_ = cuda_fail(nullptr, e, "cudaMalloc factors");
+    ddst_destroy(ctx);
+    return s_;
+  }
   cudaStream_t st = ctx->stream;
   auto bail = [&](cudaError_t err, const char* what) {
     ddst_status s_ = cuda_fail(nullptr, err, what);
@@ -636,9 +683,33 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     ddst_destroy(ctx);
     return s;
   }
+  ctx->factors_valid = true;
   ctx->state = 1;
   *out = ctx;
   return DDST_OK;
+}
+
+// Local factors for a solve: recomputed (allocated and factored again) when recompute_factors
+// released them; the factorization time counts towards the solve.
+template <typename T>
+ddst_status ensure_factors(ddst_ctx* ctx) {
+  if (ctx->factors_valid) return DDST_OK;
+  cudaError_t e = alloc_factors(ctx);
+  if (e != cudaSuccess) {
+    release_factors(ctx);
+    return cuda_fail(ctx, e, "cudaMalloc factors (recompute_factors)");
+  }
+  ddst_status fs = factor_all<T>(ctx);
+  if (fs != DDST_OK) return fs;
+  CK(cudaStreamSynchronize(ctx->stream));
+  fs = check_status(ctx, nullptr);
+  if (fs != DDST_OK) return fs;
+  ctx->factors_valid = true;
+  return DDST_OK;
+}
+
+void maybe_release_factors(ddst_ctx* ctx) {
+  if (ctx->opt.recompute_factors == 1 && ctx->state >= 2) release_factors(ctx);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -990,6 +1061,10 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
   cudaStream_t st = ctx->stream;
   ddst_status s = ensure_solve_buffers(ctx);
   if (s != DDST_OK) return s;
+  Timer tfac(st);
+  s = ensure_factors<T>(ctx);
+  if (s != DDST_OK) return s;
+  const float recompute_ms = tfac.stop();
   for (int q = 0; q < ctx->nprob; ++q) {
     const ProbDesc& P = ctx->probs[q];
     if (!f[q] || !g[q] || !u[q]) return fail(ctx, DDST_ERR_INVALID_ARG, "NULL array for problem %d", q);
@@ -1052,7 +1127,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
-    info->t_solve = ms;
+    info->t_solve = ms + recompute_ms;
     info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems +
                                     ctx->fac_big_elems + ctx->pack_elems) * (int64_t)ctx->esz;
     info->bytes_transfer = ctx->matfree ? 0
@@ -1063,6 +1138,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->factor_chunks = ctx->factor_chunks;
     info->factor_check = ctx->factor_check;
   }
+  maybe_release_factors(ctx);
   if (result != DDST_OK)
     return fail(ctx, result, "refinement stopped at estimated relative error %.3e", est);
   return DDST_OK;
@@ -1101,6 +1177,10 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
                                double* const* dLdg, double* const* dLda, ddst_info* info) {
   cudaStream_t st = ctx->stream;
   const int64_t N = ctx->tot_vol;
+  Timer tfac(st);
+  ddst_status sf = ensure_factors<T>(ctx);
+  if (sf != DDST_OK) return sf;
+  const float recompute_ms = tfac.stop();
   for (int q = 0; q < ctx->nprob; ++q) {
     const ProbDesc& P = ctx->probs[q];
     if (!dLdu[q]) return fail(ctx, DDST_ERR_INVALID_ARG, "dL/du is NULL for problem %d", q);
@@ -1169,6 +1249,8 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
     info->fail_slab = info->fail_block = -1;
   }
+  if (info) info->t_solve += recompute_ms;
+  maybe_release_factors(ctx);
   if (result != DDST_OK)
     return fail(ctx, result, "adjoint refinement stopped at estimated relative error %.3e", est);
   return DDST_OK;
@@ -1211,7 +1293,7 @@ void ddst_options_default(ddst_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof(*opt));
   opt->precision = DDST_MIXED;
-  opt->gmres_tol = 0.0;  // automatic: 1e-2 (MIXED) or 1e-10 (FP64)
+  opt->gmres_tol = 0.0;  // automatic (see the header)
   opt->gmres_max_iter = 1000;
   opt->refine_tol = 1e-9;
   opt->refine_max = 8;
@@ -1224,6 +1306,7 @@ void ddst_options_default(ddst_options* opt) {
   opt->factor_warmup = 0;
   opt->tensor_cores = 1;
   opt->explicit_S = -1;
+  opt->recompute_factors = 0;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
@@ -1246,7 +1329,11 @@ ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision) {
 ddst_status ddst_build_transfer(ddst_ctx* ctx) {
   if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
   if (ctx->state < 1) return fail(ctx, DDST_ERR_STATE, "ddst_setup has not completed");
-  return ctx->prec == DDST_FP64 ? build_transfer_impl<double>(ctx) : build_transfer_impl<float>(ctx);
+  ddst_status s = ctx->prec == DDST_FP64 ? ensure_factors<double>(ctx) : ensure_factors<float>(ctx);
+  if (s != DDST_OK) return s;
+  s = ctx->prec == DDST_FP64 ? build_transfer_impl<double>(ctx) : build_transfer_impl<float>(ctx);
+  if (s == DDST_OK) maybe_release_factors(ctx);
+  return s;
 }
 
 ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
@@ -1378,6 +1465,10 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
   if (prob < 0 || prob >= ctx->nprob || !x || !y) return fail(ctx, DDST_ERR_INVALID_ARG, "bad argument");
   ddst_status s = ensure_solve_buffers(ctx);
   if (s != DDST_OK) return s;
+  if (ctx->mf_any) {  // matrix-free operators apply through the local factors
+    s = ctx->prec == DDST_FP64 ? ensure_factors<double>(ctx) : ensure_factors<float>(ctx);
+    if (s != DDST_OK) return s;
+  }
   const ProbDesc& P = ctx->probs[prob];
   const int64_t len = (int64_t)P.nds * P.ng;
   CK(cudaMemsetAsync(ctx->if_tmp, 0, sizeof(double) * ctx->tot_if, ctx->stream));
@@ -1395,6 +1486,10 @@ ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms) {
   if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
   ddst_status s = ensure_solve_buffers(ctx);
   if (s != DDST_OK) return s;
+  if (ctx->mf_any) {
+    s = ctx->prec == DDST_FP64 ? ensure_factors<double>(ctx) : ensure_factors<float>(ctx);
+    if (s != DDST_OK) return s;
+  }
   cudaStream_t st = ctx->stream;
   CK(cudaMemsetAsync(ctx->if_tmp, 0, sizeof(double) * ctx->tot_if, st));
   auto one = [&]() {
