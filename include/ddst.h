@@ -63,8 +63,13 @@ typedef enum {
 /* Arithmetic of the local operators, transfer operators and their application. */
 enum {
   DDST_FP64 = 0,   /* everything FP64                                                      */
-  DDST_MIXED = 1,  /* FP32 factors, FP32 transfer operators (FP32 accumulation),
-                      FP64 GMRES vectors, FP64 global residual refinement                  */
+  DDST_MIXED = 1,  /* FP32 factors, FP32 transfer operators (FP32 accumulation; the
+                      tensor-core products as 3xTF32, accurate to FP32), FP64 GMRES
+                      vectors, FP64 global residual refinement                             */
+  DDST_MIXED_TF32 = 3, /* DDST_MIXED with one TF32 product (not 3xTF32) per tensor-core step
+                      of the transfer build and the large-block factorization: about a third
+                      of their tensor work, TF32-accurate operators (relative error ~1e-3),
+                      more FP64 refinement steps for the same final accuracy            */
   DDST_AUTO = 2    /* DDST_MIXED, or DDST_FP64 when an FP32 pivot falls below its floor
                       (1e3 eps |diag|).  The block elimination does not pivot, so this
                       happens only for indefinite local operators (Helmholtz slabs wider
@@ -88,7 +93,7 @@ typedef struct {
 } ddst_coeffs;
 
 typedef struct {
-  int precision;        /* DDST_FP64, DDST_MIXED or DDST_AUTO                                 */
+  int precision;        /* DDST_FP64, DDST_MIXED, DDST_MIXED_TF32 or DDST_AUTO                */
   double gmres_tol;     /* relative residual target of each interface GMRES solve; <= 0 picks
                            1e-10 for DDST_FP64 and, for DDST_MIXED (inner solve of the
                            refinement), 1e-3 with explicit transfer operators or 1e-2 when some
@@ -251,7 +256,8 @@ ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms);
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,
                        int* max_rank);
 
-/* Arithmetic the context was set up with: DDST_FP64 or DDST_MIXED (what DDST_AUTO chose).
+/* Arithmetic the context was set up with: DDST_FP64, DDST_MIXED or DDST_MIXED_TF32 (what
+ * DDST_AUTO chose).
  * Errors: INVALID_ARG for a NULL argument (message via ddst_last_error(NULL)). */
 ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision);
 

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "SINGULAR",
 DDST_FP64 = 0
 DDST_MIXED = 1
 DDST_AUTO = 2
+DDST_MIXED_TF32 = 3
 
 
 class ddst_grid(C.Structure):

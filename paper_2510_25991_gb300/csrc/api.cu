@@ -117,7 +117,8 @@ struct ddst_ctx {
   void* Fbig = nullptr;
   struct BigWork { void *C[2] = {}, *XqT[2] = {}, *RT[2] = {}, *Pinv[2] = {}; };  // two sets
   std::map<int, BigWork> bigw;
-  bool big_tc = false;                   // large-block Gauss-Jordan updates on tcgen05
+  int big_tc = 0;                        // large-block updates: 0 FMA, 1 tcgen05 3xTF32, 2 TF32
+  bool tf32 = false;                     // DDST_MIXED_TF32: one TF32 product per tensor-core step
   // look-ahead of the large-block factorization: panel steps on a high-priority stream, the bulk
   // updates on a second one
   cudaStream_t s_hi = nullptr, s_lo = nullptr;
@@ -480,6 +481,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   if (opt) ctx->opt = *opt; else ddst_options_default(&ctx->opt);
   ctx->prec = ctx->opt.precision == DDST_FP64 ? DDST_FP64 : DDST_MIXED;
+  ctx->tf32 = ctx->opt.precision == DDST_MIXED_TF32;
   ctx->esz = ctx->prec == DDST_FP64 ? 8 : 4;
   const bool auto_tol = !(ctx->opt.gmres_tol > 0.0);  // picked once the operator kind is known
   int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, fac_big_off = 0, pack_off = 0,
@@ -575,7 +577,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   // operators every iteration is itself a local solve, and 1e-2 is cheaper (both measured on
   // the 2048^2 and 127^3 workloads).
   if (auto_tol) ctx->opt.gmres_tol = ctx->prec == DDST_FP64 ? 1e-10 : (ctx->mf_any ? 1e-2 : 1e-3);
-  ctx->big_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0;
+  ctx->big_tc = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0 ? (ctx->tf32 ? 2 : 1) : 0;
   const int nslab = (int)ctx->slabs.size();
   const size_t es = ctx->esz;
   cudaError_t e;
@@ -762,7 +764,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
         launch_sbuild_tc(M, ctx->d_slabs, d_tiles, (int)tiles.size(), ctx->Uhi, ctx->Ulo,
                          ctx->Uhi + ctx->fac_elems, ctx->Ulo + ctx->fac_elems, (const float*)ctx->G,
                          (const float*)ctx->pack, (float*)ctx->S, ctx->d_st,
-                         pipeline_wait_budget(), st);
+                         pipeline_wait_budget(), ctx->tf32 ? 0 : 1, st);
       else
         launch_sbuild<T>(M, ctx->d_slabs, d_tiles, (int)tiles.size(), (const T*)ctx->F,
                          (const T*)ctx->B, (const T*)ctx->G, (const T*)ctx->pack, (T*)ctx->S,
@@ -1264,9 +1266,11 @@ ddst_status setup_precision(int nprob, const ddst_grid* grids, const ddst_coeffs
                             ddst_ctx** out) {
   ddst_options o;
   if (opt) o = *opt; else ddst_options_default(&o);
-  if (o.precision != DDST_FP64 && o.precision != DDST_MIXED && o.precision != DDST_AUTO) {
+  if (o.precision != DDST_FP64 && o.precision != DDST_MIXED && o.precision != DDST_AUTO &&
+      o.precision != DDST_MIXED_TF32) {
     if (out) *out = nullptr;
-    return fail(nullptr, DDST_ERR_INVALID_ARG, "precision must be DDST_FP64, DDST_MIXED or DDST_AUTO");
+    return fail(nullptr, DDST_ERR_INVALID_ARG,
+                "precision must be DDST_FP64, DDST_MIXED, DDST_MIXED_TF32 or DDST_AUTO");
   }
   if (o.precision != DDST_AUTO) return setup_impl(nprob, grids, coeffs, widths, &o, stream, out);
   o.precision = DDST_MIXED;
@@ -1322,7 +1326,7 @@ ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeff
 
 ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision) {
   if (!ctx || !precision) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx or precision is NULL");
-  *precision = ctx->prec;
+  *precision = ctx->tf32 ? DDST_MIXED_TF32 : ctx->prec;
   return DDST_OK;
 }
 

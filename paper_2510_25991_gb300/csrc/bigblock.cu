@@ -15,8 +15,8 @@
 //            P^{-1}, so that the update below also produces the column panel
 //   update   X(I,J) = X(I,J) - C(I,:) R(:,J) for I != Q, J != Q;  X(I,Q) = -C(I,:) P^{-1}
 // The row and update steps are dense products with K = 128: tcgen05 tensor-core kernels in the
-// FP32 path (3xTF32 with FP32 accumulation in tensor memory), FMA kernels in FP64 (and as an FP32
-// reference).  The local solves of a slab stream its F_k (forward and backward block sweeps,
+// FP32 path (3xTF32 with FP32 accumulation in tensor memory, or plain TF32 in the TF32 mode), FMA
+// kernels in FP64 (and as an FP32 reference).  The local solves of a slab stream its F_k (forward and backward block sweeps,
 // one batched matrix-vector product per block row); A_j^{-T} uses the same factors transposed.
 #include "bgj.cuh"
 #include "kernels.cuh"
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
                   float* __restrict__ F, int k, int q, const float* __restrict__ Cs,
                   const float* __restrict__ XqTs, float* __restrict__ RTs,
                   const float* __restrict__ Pis, DevStatus* st, int tset,
-                  float* __restrict__ Cn, float* __restrict__ XqTn) {
+                  float* __restrict__ Cn, float* __restrict__ XqTn, int three) {
   using C = GjTc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* ring = smem_raw;
@@ -548,11 +548,12 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
         if (c >= C::NST && !mbar_wait_ab(&empty[stage], ((c / C::NST) - 1) & 1, abort, st, sid, k))
           break;
         unsigned char* sb = ring + stage * C::STAGE;
-        mbar_arrive_expect_tx(&full[stage], C::STAGE);
+        // the TF32 mode (three == 0) uses only the hi parts
+        mbar_arrive_expect_tx(&full[stage], three ? C::STAGE : 2 * C::PART);
         bulk_g2s(sb, A + c * 2048, C::PART, &full[stage]);
-        bulk_g2s(sb + C::PART, A + BT * BT + c * 2048, C::PART, &full[stage]);
+        if (three) bulk_g2s(sb + C::PART, A + BT * BT + c * 2048, C::PART, &full[stage]);
         bulk_g2s(sb + 2 * C::PART, B + c * 2048, C::PART, &full[stage]);
-        bulk_g2s(sb + 3 * C::PART, B + BT * BT + c * 2048, C::PART, &full[stage]);
+        if (three) bulk_g2s(sb + 3 * C::PART, B + BT * BT + c * 2048, C::PART, &full[stage]);
         ++issued;
       }
       // no copy may still target this CTA's shared memory when it exits
@@ -574,8 +575,10 @@ __global__ void __launch_bounds__(GjTc::THREADS, 2)
         const uint64_t bh = umma_desc(sa + 2 * C::PART + ks * 256, 128, C::KC * 32);
         const uint64_t bl = umma_desc(sa + 3 * C::PART + ks * 256, 128, C::KC * 32);
         mma_tf32_ss(tmem, ah, bh, IDESC, (c > 0 || ks > 0) ? 1u : 0u);
-        mma_tf32_ss(tmem, ah, bl, IDESC, 1u);
-        mma_tf32_ss(tmem, al, bh, IDESC, 1u);
+        if (three) {
+          mma_tf32_ss(tmem, ah, bl, IDESC, 1u);
+          mma_tf32_ss(tmem, al, bh, IDESC, 1u);
+        }
       }
       mma_commit(&empty[stage]);
       if (c == C::NCH - 1) mma_commit(dready);
@@ -782,11 +785,12 @@ static size_t pivot_smem() {
 template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
                             const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
-                            T* const RT[2], T* const Pinv[2], bool tensor_cores, DevStatus* st,
+                            T* const RT[2], T* const Pinv[2], int tensor_cores, DevStatus* st,
                             cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev) {
   const int nP = M / BT;
   bool tc = false;
-  if constexpr (sizeof(T) == 4) tc = tensor_cores;
+  if constexpr (sizeof(T) == 4) tc = tensor_cores != 0;
+  const int three = tensor_cores == 1 ? 1 : 0;  // 1: 3xTF32, 2: TF32
   const size_t psm = tc ? pivot_smem<T, true>() : pivot_smem<T, false>();
   auto pivot = [&](int q) {
     const int b = q & 1;
@@ -810,7 +814,7 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
       if (tc) {
         k_big_gemm_tc<GJ_ROW><<<dim3(nP, 1, nids), GjTc::THREADS, GjTc::SMEM, sh>>>(
             d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, GJ_ALL,
-            q + 1 < nP ? Cb[b ^ 1] : nullptr, q + 1 < nP ? XqT[b ^ 1] : nullptr);
+            q + 1 < nP ? Cb[b ^ 1] : nullptr, q + 1 < nP ? XqT[b ^ 1] : nullptr, three);
         return;
       }
     }
@@ -827,7 +831,7 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
         const bool nx = tset == GJ_NEXT;
         k_big_gemm_tc<GJ_UPDATE><<<grid, GjTc::THREADS, GjTc::SMEM, s>>>(
             d_slabs, d_ids, F, k, q, Cb[b], XqT[b], RT[b], Pinv[b], st, tset,
-            nx ? Cb[b ^ 1] : nullptr, nx ? XqT[b ^ 1] : nullptr);
+            nx ? Cb[b ^ 1] : nullptr, nx ? XqT[b ^ 1] : nullptr, three);
         return;
       }
     }
@@ -921,12 +925,12 @@ void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, con
 
 template void launch_big_factor_step<float>(int, const SlabDesc*, const int*, int, const float*,
                                             float*, int, float* const[2], float* const[2],
-                                            float* const[2], float* const[2], bool, DevStatus*,
+                                            float* const[2], float* const[2], int, DevStatus*,
                                             cudaStream_t, cudaStream_t, cudaEvent_t*);
 template void launch_big_factor_step<double>(int, const SlabDesc*, const int*, int,
                                              const double*, double*, int, double* const[2],
                                              double* const[2], double* const[2],
-                                             double* const[2], bool, DevStatus*, cudaStream_t,
+                                             double* const[2], int, DevStatus*, cudaStream_t,
                                              cudaStream_t, cudaEvent_t*);
 template void launch_big_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
                                       const float*, const float*, float*, float*, int,

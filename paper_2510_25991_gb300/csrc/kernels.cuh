@@ -82,11 +82,12 @@ void launch_sbuild(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int 
                    cudaStream_t s);
 
 // sweep_tc.cu: explicit transfer operators on tcgen05 (FP32 data, 3xTF32), M in {32, 64};
-// budget: clock cycles before a pipeline wait of a role gives up (ST_TIMEOUT)
+// budget: clock cycles before a pipeline wait of a role gives up (ST_TIMEOUT); three: 3xTF32 (1)
+// or TF32 (0)
 void launch_sbuild_tc(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                       const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                       const float* G, const float* pack, float* S, DevStatus* st,
-                      long long budget, cudaStream_t s);
+                      long long budget, int three, cudaStream_t s);
 int sbuild_tc_tile_cols();  // sources per CTA of the tensor-core transfer build
 
 // solve.cu: single-RHS local solves (mode 0: full block into x; mode 1: central rows -> iface)
@@ -122,11 +123,12 @@ void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double*
 // Gauss-Jordan panels with look-ahead on two streams: sh high priority, sl the bulk updates; ev
 // three events).  Two sets of work buffers (alternating by panel parity), each Cb, XqT, RT
 // (nids x M x 128, twice that when split for the tensor cores) and Pinv (nids x 128 x 128, or
-// twice).  All work is ordered before later work on sh.
+// twice).  tensor_cores: 0 FMA, 1 tcgen05 3xTF32, 2 tcgen05 TF32.  All work is ordered before
+// later work on sh.
 template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
                             const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
-                            T* const RT[2], T* const Pinv[2], bool tensor_cores, DevStatus* st,
+                            T* const RT[2], T* const Pinv[2], int tensor_cores, DevStatus* st,
                             cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev);
 // Local solve x = A^{-1} b (transpose 0) or A^{-T} b (transpose 1) of every slab of the class;
 // z is a slab-local temporary.

@@ -15,7 +15,8 @@
 // stores the two S entries the block contributes, and splits Y^T in place into TF32 parts:
 // hi = rna(y) back into D[s % 2], lo = rna(y - hi) into the lo block.  The MMAs of step s read
 // A_hi from D[s % 2] and A_lo from the lo block and write D[(s + 1) % 2]:
-//     D_next = A_hi B_hi + A_hi B_lo + A_lo B_hi   (3xTF32, Ootomo & Yokota 2022).
+//     D_next = A_hi B_hi + A_hi B_lo + A_lo B_hi   (3xTF32, Ootomo & Yokota 2022),
+// or D_next = A_hi B_hi alone in the TF32 mode (its lo copies are then not loaded).
 //
 // A CTA holds two tiles that visit the same blocks in lockstep, so one factor stream feeds both,
 // and the tensor core works on one tile while the other tile's epilogue runs.  Roles:
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
                 const float* __restrict__ Fhi, const float* __restrict__ Flo,
                 const float* __restrict__ Bhi, const float* __restrict__ Blo,
                 const float* __restrict__ G, const float* __restrict__ pack,
-                float* __restrict__ S, DevStatus* st, long long budget) {
+                float* __restrict__ S, DevStatus* st, long long budget, int three) {
   using C = TcCfg<MB>;
   constexpr int NST = C::NST, NT = C::NT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -129,13 +130,15 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
         const bool has_g = g_in_ring && qa < td.q0 + td.nq && qb > td.q0;
         const uint32_t gbytes = (uint32_t)s.p * MB * 4;
         unsigned char* sb = ring + stage * C::STAGE;
-        mbar_arrive_expect_tx(&full[stage], C::PKB + (has_f ? 2 * C::FBLK : 0u) + (has_g ? gbytes : 0u));
+        // 1xTF32 (three == 0) reads only the hi part of the factor copy
+        mbar_arrive_expect_tx(&full[stage], C::PKB + (has_f ? (three ? 2 : 1) * C::FBLK : 0u) +
+                                                (has_g ? gbytes : 0u));
         bulk_g2s(sb + 2 * C::FBLK, pack + s.pack_off + (int64_t)(i - 1) * PK_NFIELDS * MB, C::PKB,
                  &full[stage]);
         if (has_f) {
           const int fidx = up ? i - 2 : i;
           bulk_g2s(sb, Fh + (int64_t)fidx * MB * MB, C::FBLK, &full[stage]);
-          bulk_g2s(sb + C::FBLK, Fl + (int64_t)fidx * MB * MB, C::FBLK, &full[stage]);
+          if (three) bulk_g2s(sb + C::FBLK, Fl + (int64_t)fidx * MB * MB, C::FBLK, &full[stage]);
         }
         if (has_g)
           bulk_g2s(sb + 2 * C::FBLK + C::PKB,
@@ -170,8 +173,10 @@ __global__ void __launch_bounds__(TcCfg<MB>::THREADS, 1)
             const uint64_t dbh = umma_desc(b_hi + ks * 256, 128, MB * 32);
             const uint64_t dbl = umma_desc(b_lo + ks * 256, 128, MB * 32);
             mma_tf32_tmem_a(d, a_hi + ks * 8, dbh, IDESC, ks > 0 ? 1u : 0u);
-            mma_tf32_tmem_a(d, a_hi + ks * 8, dbl, IDESC, 1u);
-            mma_tf32_tmem_a(d, a_lo + ks * 8, dbh, IDESC, 1u);
+            if (three) {
+              mma_tf32_tmem_a(d, a_hi + ks * 8, dbl, IDESC, 1u);
+              mma_tf32_tmem_a(d, a_lo + ks * 8, dbh, IDESC, 1u);
+            }
           }
           mma_commit(&dready[u]);
         }
@@ -272,22 +277,22 @@ template <int MB>
 static void run_tc(const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                    const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                    const float* G, const float* pack, float* S, DevStatus* st, long long budget,
-                   cudaStream_t s) {
+                   int three, cudaStream_t s) {
   using C = TcCfg<MB>;
   raise_smem_limit(reinterpret_cast<const void*>(&k_sbuild_tc<MB>), C::SMEM);
   note_launch();
   k_sbuild_tc<MB><<<ntiles, C::THREADS, C::SMEM, s>>>(d_slabs, d_tiles, Fhi, Flo, Bhi, Blo, G,
-                                                      pack, S, st, budget);
+                                                      pack, S, st, budget, three);
 }
 
 void launch_sbuild_tc(int M, const SlabDesc* d_slabs, const TileDesc* d_tiles, int ntiles,
                       const float* Fhi, const float* Flo, const float* Bhi, const float* Blo,
                       const float* G, const float* pack, float* S, DevStatus* st,
-                      long long budget, cudaStream_t s) {
+                      long long budget, int three, cudaStream_t s) {
   if (ntiles == 0) return;
   switch (M) {
-    case 32: run_tc<32>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, s); break;
-    case 64: run_tc<64>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, s); break;
+    case 32: run_tc<32>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, three, s); break;
+    case 64: run_tc<64>(d_slabs, d_tiles, ntiles, Fhi, Flo, Bhi, Blo, G, pack, S, st, budget, three, s); break;
     default: break;
   }
 }

@@ -65,12 +65,13 @@ def _check(lib, ctx, st):
         raise DDSTError(st, msg.decode() if msg else "")
 
 
-_PRECISIONS = {"fp64": L.DDST_FP64, "mixed": L.DDST_MIXED, "auto": L.DDST_AUTO}
+_PRECISIONS = {"fp64": L.DDST_FP64, "mixed": L.DDST_MIXED, "mixed_tf32": L.DDST_MIXED_TF32,
+               "auto": L.DDST_AUTO}
 
 
 def ddst_options_default(**overrides):
     """The library's default options with ``overrides`` applied; ``precision`` may be given as
-    "fp64", "mixed" or "auto".  Unknown option names raise TypeError (a ctypes structure would
+    "fp64", "mixed", "mixed_tf32" or "auto".  Unknown option names raise TypeError (a ctypes structure would
     otherwise take them silently as plain attributes)."""
     lib = L.load()
     o = L.ddst_options()
@@ -208,11 +209,12 @@ def ddst_query(ctx, prob=0):
 
 
 def ddst_get_precision(ctx):
-    """"fp64" or "mixed": the arithmetic the context was set up with (what "auto" chose)."""
+    """"fp64", "mixed" or "mixed_tf32": the arithmetic the context was set up with (what "auto"
+    chose)."""
     lib = L.load()
     p = C.c_int()
     _check(lib, None, lib.ddst_get_precision(ctx, C.byref(p)))
-    return "fp64" if p.value == L.DDST_FP64 else "mixed"
+    return {L.DDST_FP64: "fp64", L.DDST_MIXED_TF32: "mixed_tf32"}.get(p.value, "mixed")
 
 
 def ddst_residual_noalloc(dim, n, a, f, g, u, r, norms, b=(0.0, 0.0, 0.0), c=None, stream=None):

@@ -60,3 +60,27 @@ def test_recompute_factors_gives_the_same_solutions_and_gradients(name, n, w, co
     tol = 2e-5 if compress is None else 1e-3
     assert np.abs(y.cpu().numpy() - ref).max() <= tol * np.abs(ref).max()
     sol.close()
+
+
+@pytest.mark.parametrize("name,n,w", [("convdiff2d", 256, 32), ("vardiff3d", 32, 8)])
+def test_tf32_mode_reaches_the_target_after_refinement(name, n, w):
+    """DDST_MIXED_TF32: one TF32 product per tensor-core step (2D: the transfer build; 3D: the
+    large-block factorization) instead of 3xTF32.  The operators are TF32-accurate, and the FP64
+    refinement still reaches 1e-8 against O2, with at least as many refinement steps."""
+    from paper_2510_25991_gb300 import ddst as D
+    prob = I.make_problem(name, n=n, w=w)
+    dim = prob["dim"]
+    A, b = O.assemble(prob)
+    uref = O.global_solve(A, b)
+    steps = {}
+    for prec in ("mixed", "mixed_tf32"):
+        sol = D.Solver(dict(dim=dim, n=n, w=w, a=dev(prob["a"]), b=tuple(prob["b"]) + (0.0,) * (3 - dim)),
+                       precision=prec)
+        assert sol.precision == prec
+        sol.build_transfer()
+        u = torch.empty((n - 1,) * dim, dtype=torch.float64, device="cuda")
+        st, info = sol.solve(dev(prob["f"]), dev(prob["g"]), u)
+        sol.close()
+        assert relerr(u.cpu().numpy().ravel(), uref) <= 1e-8, (prec, info)
+        steps[prec] = info["refine_iters"]
+    assert steps["mixed_tf32"] >= steps["mixed"], steps
