@@ -133,7 +133,8 @@ typedef struct {
   int gmres_iters_first;  /* iterations of the first interface solve                          */
   int refine_iters;       /* DD solves performed (1 = no refinement correction needed)        */
   double rel_residual;    /* final ||b - A u||_2 / ||b||_2 in FP64                            */
-  double est_rel_error;   /* refinement error bound rho/(1-rho) ||last correction|| / ||u||    */
+  double est_rel_error;   /* refinement error bound rho/(1-rho) ||last correction|| / ||u||,   */
+                          /* per problem; a batch reports its largest problem's bound          */
   double t_factor, t_transfer, t_compress, t_solve;
   int64_t bytes_factors;  /* device bytes of the local factors (held only during setup and each
                              call when recompute_factors is set)                              */
@@ -201,7 +202,8 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol);
  * (equilib1)), GMRES on (I - K) u_Gamma = fhat, volume reconstruction, then FP64 residual
  * refinement u += DD(b - A u) until the error bound rho/(1-rho) ||correction|| (rho: observed
  * contraction ratio of the corrections, no bound while it is >= 1) is <= refine_tol ||u||; the
- * bound is info->est_rel_error.
+ * bound is info->est_rel_error.  In a batch the test holds for every problem on its own (its own
+ * corrections and its own ||u||), not for the concatenated vector.
  * f: interior load; g: nodal Dirichlet data (only boundary nodes are read); u: interior
  * output.  info may be NULL.  Errors: STATE, INVALID_ARG, NOT_CONVERGED (u still written). */
 ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,

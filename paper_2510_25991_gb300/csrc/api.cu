@@ -61,6 +61,8 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+constexpr int kNormBlocks = 32;  // CTAs per problem in the refinement's per-problem norms
+
 }  // namespace
 
 struct ddst_ctx {
@@ -92,6 +94,7 @@ struct ddst_ctx {
   double *V = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr,
          *resid = nullptr, *part = nullptr, *scal = nullptr,
          *ysol = nullptr;
+  double *pn_part = nullptr, *pn = nullptr;  // per-problem norms of the refinement (2 nprob each)
   int ldh = 0;
   int nchunk = 0;
   HodlrSet hodlr;  // compressed operators (when compressed)
@@ -821,6 +824,8 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   AL(ctx->resid, sizeof(double) * (maxit + 1));
   AL(ctx->part, sizeof(double) * (size_t)(maxit + 1) * std::max(ctx->nchunk, 1024));
   AL(ctx->scal, sizeof(double) * 16);
+  AL(ctx->pn_part, sizeof(double) * 2 * (size_t)ctx->nprob * kNormBlocks);
+  AL(ctx->pn, sizeof(double) * 2 * (size_t)ctx->nprob);
   AL(ctx->ysol, sizeof(double) * (maxit + 1));
   AL(ctx->d_k, sizeof(int) * 4);
   AL(ctx->h1, sizeof(double) * (maxit + 1));
@@ -1029,6 +1034,30 @@ double refine_error_estimate(const std::vector<double>& hist, double xn) {
   return rel * rho / (1.0 - rho);
 }
 
+// One refinement step's bookkeeping for a batch: appends each problem's correction norm
+// ||e_q|| to hist[q] and returns the largest of the problems' bounds, each relative to its own
+// ||x_q||.  A bound over the concatenated batch would let a problem with a small solution hide
+// behind one with a large solution (the interface GMRES also stops on the batch's residual), so
+// the stopping test holds problem by problem.  One host synchronisation.
+double refine_batch_estimate(ddst_ctx* ctx, const double* e, const double* x,
+                             std::vector<std::vector<double>>& hist) {
+  const int np = ctx->nprob;
+  cudaStream_t st = ctx->stream;
+  launch_prob_sqnorms(ctx->d_probs, np, e, ctx->pn_part, kNormBlocks, ctx->pn, st);
+  launch_prob_sqnorms(ctx->d_probs, np, x, ctx->pn_part + (size_t)np * kNormBlocks, kNormBlocks,
+                      ctx->pn + np, st);
+  std::vector<double> h(2 * (size_t)np);
+  cudaMemcpyAsync(h.data(), ctx->pn, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  hist.resize(np);
+  double est = 0.0;
+  for (int q = 0; q < np; ++q) {
+    hist[q].push_back(std::sqrt(h[q]));
+    est = std::max(est, refine_error_estimate(hist[q], std::sqrt(h[np + q])));
+  }
+  return est;
+}
+
 // One application of the DD solve map (Alg. 2 + GMRES + reconstruction):
 // rhs volume vector r (FP64) -> volume correction e (FP64); traces written into ctx->if_u.
 template <typename T>
@@ -1081,7 +1110,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
   const double tol = ctx->opt.gmres_tol;
   int total_it = 0, first_it = 0, nref = 0;
   double est = 0.0, relres = 0.0;
-  std::vector<double> dnorm;
+  std::vector<std::vector<double>> dnorm;
   ddst_status result = DDST_OK;
   const int rmax = std::max(0, ctx->opt.refine_max);
   for (int it = 0; it <= rmax; ++it) {
@@ -1099,8 +1128,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
-    dnorm.push_back(vec_norm(ctx, ctx->d_e, N, 4));
-    est = refine_error_estimate(dnorm, vec_norm(ctx, ctx->d_u, N, 5));
+    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_u, dnorm);
     if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;
@@ -1193,7 +1221,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
   const double gnorm = vec_norm(ctx, ctx->d_ga, N, 3);
   int total_it = 0, first_it = 0, nref = 0;
   double est = 0.0;
-  std::vector<double> dnorm;
+  std::vector<std::vector<double>> dnorm;
   ddst_status result = DDST_OK, s;
   const int rmax = std::max(0, ctx->opt.refine_max);
   for (int it = 0; it <= rmax; ++it) {
@@ -1211,8 +1239,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_lam, st);
-    dnorm.push_back(vec_norm(ctx, ctx->d_e, N, 4));
-    est = refine_error_estimate(dnorm, vec_norm(ctx, ctx->d_lam, N, 5));
+    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_lam, dnorm);
     if (rmax == 0) {
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;

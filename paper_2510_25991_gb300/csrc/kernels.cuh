@@ -48,6 +48,9 @@ void launch_iface_dirichlet_T(const SlabDesc* d_slabs, const ProbDesc* d_probs, 
                               const T* pack, const T* loc, double* out, cudaStream_t st);
 void launch_dot(const double* x, const double* y, int64_t n, double* part, int nblk, double* out,
                 cudaStream_t st);
+// out[q] = sum of squares of x over problem q's interior unknowns (part: nprob * nblk doubles).
+void launch_prob_sqnorms(const ProbDesc* d_probs, int nprob, const double* x, double* part,
+                         int nblk, double* out, cudaStream_t st);
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
 
 // One CTA of the pivot sweeps (factor.cu): rows start..last of one slab and direction, inverses

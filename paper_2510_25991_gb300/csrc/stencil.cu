@@ -331,8 +331,29 @@ __global__ void k_dot_partial(const double* __restrict__ x, const double* __rest
   }
 }
 
-// Sum of np partials into out[0] (one CTA).
+// Per-problem sums of squares, first stage: part[q * gridDim.x + b] for problem q = blockIdx.y
+// over its interior unknowns x[vol_off, vol_off + nint).
+__global__ void k_prob_sqnorm_partial(const ProbDesc* __restrict__ probs, const double* __restrict__ x,
+                                      double* __restrict__ part) {
+  const int64_t off = probs[blockIdx.y].vol_off, n = probs[blockIdx.y].nint;
+  double v = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    v += x[off + e] * x[off + e];
+  __shared__ double red[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Sum of np partials into out[0]; with several CTAs, CTA c sums part[c np, (c + 1) np) into out[c].
 __global__ void k_sum_partials(const double* __restrict__ part, int np, double* __restrict__ out) {
+  part += (int64_t)blockIdx.x * np;
   double v = 0.0;
   for (int e = threadIdx.x; e < np; e += blockDim.x) v += part[e];
   __shared__ double red[32];
@@ -342,7 +363,7 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
   if (threadIdx.x < 32) {
     double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     t = warp_sum(t);
-    if (threadIdx.x == 0) out[0] = t;
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
   }
 }
 
@@ -438,6 +459,14 @@ void launch_dot(const double* x, const double* y, int64_t n, double* part, int n
   k_dot_partial<<<nblk, 256, 0, st>>>(x, y, n, part);
   note_launch();
   k_sum_partials<<<1, 256, 0, st>>>(part, nblk, out);
+}
+
+void launch_prob_sqnorms(const ProbDesc* d_probs, int nprob, const double* x, double* part,
+                         int nblk, double* out, cudaStream_t st) {
+  note_launch();
+  k_prob_sqnorm_partial<<<dim3(nblk, nprob), 256, 0, st>>>(d_probs, x, part);
+  note_launch();
+  k_sum_partials<<<nprob, 256, 0, st>>>(part, nblk, out);
 }
 
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {

@@ -52,7 +52,8 @@ MUTATIONS = [
  ("O7 dL/da face not split between nodes", "dLda[lo] += 0.5 * dface", "dLda[lo] += dface"),
  ("O7 dL/dg convection sign (upper boundary)", "lam_full[lo] * (af / h ** 2 - bconv[d] / (2 * h))", "lam_full[lo] * (af / h ** 2 + bconv[d] / (2 * h))"),
  ("O7 dL/dg convection sign (lower boundary)", "lam_full[hi] * (af / h ** 2 + bconv[d] / (2 * h))", "lam_full[hi] * (af / h ** 2 - bconv[d] / (2 * h))"),
- ("O2b sine-transform eigenvalue pi k / n instead of pi k / (2n)", "np.sin(np.pi * k / (2.0 * n)) ** 2", "np.sin(np.pi * k / n) ** 2"),
+ ("O2b sine-transform eigenvalue pi k / n instead of pi k / (2n)", "lam1 = 4.0 * n * n * np.sin(np.pi * k / (2.0 * n)) ** 2", "lam1 = 4.0 * n * n * np.sin(np.pi * k / n) ** 2"),
+ ("O3b transverse eigenvalue pi k / n instead of pi k / (2n)", "mu1 = 4.0 * np.sin(np.pi * k / (2.0 * n)) ** 2", "mu1 = 4.0 * np.sin(np.pi * k / n) ** 2"),
  ("O2b DST of type 2 instead of 1", "bh = sfft.dstn(b.reshape((n - 1,) * dim), type=1)", "bh = sfft.dstn(b.reshape((n - 1,) * dim), type=2)"),
  ("O2c lambda_min without the dimension factor", "return dim * 4.0 * n * n * math.sin", "return 4.0 * n * n * math.sin"),
  ("O2c a_min dropped from the eigenvalue bound", "lam = float(np.min(prob[\"a\"])) * laplacian_lambda_min", "lam = 1.0 * laplacian_lambda_min"),
