@@ -100,8 +100,9 @@ typedef struct {
                            are applied matrix-free                                            */
   int gmres_max_iter;   /* Krylov dimension cap (unrestarted GMRES; used clamped to 1..1000)  */
   double refine_tol;    /* FP64 refinement stops when its error estimate, rho / (1 - rho) times
-                           the last correction (rho: observed contraction; no estimate while
-                           rho >= 1), is <= refine_tol * ||u||                              */
+                           the last correction (rho: observed contraction, the larger of the
+                           last two ratios; taken as >= 1/2 while only one ratio is known; no
+                           estimate while rho >= 1), is <= refine_tol * ||u||               */
   int refine_max;       /* maximum number of refinement steps (0 = plain DD solve)            */
   int k_max;            /* HODLR rank cap per block (used clamped to 1..128)                  */
   int oversample;       /* extra random samples beyond k_max; the sketch width k_max +

@@ -1015,13 +1015,16 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
 // A-posteriori error of a contracting fixed-point iteration: if every step reduces the error by
 // a factor rho < 1, the error after applying the correction delta_k is at most
 // rho / (1 - rho) ||delta_k||.  rho is estimated by the larger of the last two ratios
-// ||delta_k|| / ||delta_{k-1}|| (only the first ratio after two steps) and used as observed: a
-// slow contraction (rho near 1) enlarges the bound accordingly, and rho >= 1 (no contraction seen)
-// gives no bound at all (infinity), unless the correction itself is at the FP64 rounding level of
-// the residual (relative size below 1e-14), where the corrections are rounding noise and their
-// size is the only error measure left.  The first correction (from zero) has no estimate and
-// counts in full.  Returns the bound relative to ||x|| given the correction norms so far (hist)
-// and ||x||.
+// ||delta_k|| / ||delta_{k-1}|| and used as observed: a slow contraction (rho near 1) enlarges
+// the bound accordingly, and rho >= 1 (no contraction seen) gives no bound at all (infinity),
+// unless the correction itself is at the FP64 rounding level of the residual (relative size below
+// 1e-14), where the corrections are rounding noise and their size is the only error measure left.
+// The first correction (from zero) has no estimate and counts in full.  After two corrections the
+// one ratio seen is that of the first DD solve on the whole right-hand side, which resolves it
+// better than later solves resolve the residual (that residual lies where the inner GMRES and the
+// low-precision factors are weakest), so it underestimates the later contraction: the bound is
+// then the last correction itself (rho taken as at least 1/2).  Returns the bound relative to
+// ||x|| given the correction norms so far (hist) and ||x||.
 double refine_error_estimate(const std::vector<double>& hist, double xn) {
   const size_t k = hist.size();
   if (k == 0 || !(xn > 0.0)) return 0.0;
@@ -1031,6 +1034,7 @@ double refine_error_estimate(const std::vector<double>& hist, double xn) {
   if (k >= 3 && hist[k - 3] > 0.0) rho = std::max(rho, hist[k - 2] / hist[k - 3]);
   if (rel <= 1e-14) return rel;
   if (!(rho < 1.0)) return HUGE_VAL;
+  if (k == 2) rho = std::max(rho, 0.5);
   return rel * rho / (1.0 - rho);
 }
 
