@@ -208,21 +208,48 @@ def cpu_baseline(n=512):
             "sample": f"oracle dd_solve on the {n}x{n} instance of the workload (FP64, {dt:.1f} s)"}
 
 
-def _certify(prob, u):
-    """Rigorous bound on the relative error of u (the oracle's residual bound, host cores)."""
+def cpu_leg(c2_prob, c2_u, verify=True, c4=None, c5_prob=None, ref_n=512):
+    """The cpu_baseline leg: every use of the oracle in the GPU arm, on the host cores, after
+    all GPU timing (rank 0, one GPU).
+    * the oracle's FP64 DD solve timed on a bounded sample (``cpu_baseline``);
+    * the error of the timed run's own 2D solution against the oracle's global sparse solve
+      (O2, about two minutes on the host) and the oracle's rigorous residual bound (O2c);
+    * the O2c bound on the 3D solution (O2 does not finish at 127^3);
+    * the oracle's adjoint gradient of the adjoint batch's median problem, timed."""
+    import numpy as np
     from oracle import ddst_oracle as O
-    return O.diffusion_error_bound(prob, u)
+    out = {"cpu_baseline": cpu_baseline(ref_n)}
+    ver = {"certified_rel_error_bound": O.diffusion_error_bound(c2_prob, c2_u)}
+    if verify:
+        t0 = time.perf_counter()
+        A, b = O.assemble(c2_prob)
+        ustar = O.global_solve(A, b)
+        ver["rel_error_vs_oracle"] = float(np.linalg.norm(c2_u - ustar) / np.linalg.norm(ustar))
+        ver["max_abs_error_vs_oracle"] = float(np.abs(c2_u - ustar).max() / np.abs(ustar).max())
+        ver["oracle"] = f"global sparse solve O2 (SuperLU, FP64) of this instance, {time.perf_counter() - t0:.0f} s"
+    out["verify"] = ver
+    if c4 is not None:
+        prob4, u4 = c4
+        out["c4_certified_rel_error_bound"] = O.diffusion_error_bound(prob4, u4)
+    if c5_prob is not None:
+        t0 = time.perf_counter()
+        O.loss_and_gradients(c5_prob, np.zeros((c5_prob["n"] - 1) ** 2))
+        out["c5_oracle_median_problem"] = {
+            "n": c5_prob["n"], "w": c5_prob["w"], "s_per_gradient": time.perf_counter() - t0,
+            "kind": "oracle loss_and_gradients (SuperLU, FP64)", "cpu_model": cpu_model(),
+            "cores": os.cpu_count()}
+    return out
 
 
-def bench_c4(peaks, src, steps=2, warmup=1, certify=True, n=128, w=16):
+def bench_c4(peaks, src, steps=2, warmup=1, n=128, w=16):
     """The 3D variable-coefficient workload: 128^3 cells (2,048,383 unknowns), 8 slabs of 16
     cells, a = exp(8 Fourier modes in 3D), mixed precision to 1e-8 (estimated).  7 double slabs
     with dense blocks of 31 * 127 = 3937 unknowns (padded to 3968): one-sided block LU on the
     tensor cores, transfer operators applied matrix-free (two sweeps of local solves per GMRES
     iteration).  A step is setup (factorization) + solve, inputs resident on the device; the
     factors (56 GB) are far larger than L2.  After the timed steps: the factorization's
-    tensor-core rate, the local-solve bandwidth, and the oracle's rigorous error bound (O2c) on
-    the last solution."""
+    tensor-core rate and the local-solve bandwidth.  Returns the section and (problem, last
+    solution) for the oracle's bound in the cpu_baseline leg."""
     import numpy as np
     import torch
 
@@ -286,10 +313,7 @@ def bench_c4(peaks, src, steps=2, warmup=1, certify=True, n=128, w=16):
            "paper": {"hardware": "24-core Xeon Gold 6248R 3 GHz, unparallelized (Sec. 5.1)",
                      "table": "lu_vs_hbs, N = 128^3, H = 1/16",
                      "lu_path_s": 12.73 + 50.50, "hbs_path_s": 12.73 + 61.48 + 30.99 + 1.91}}
-    if certify:
-        from oracle import ddst_oracle as O
-        out["certified_rel_error_bound"] = O.diffusion_error_bound(prob, u.cpu().numpy().ravel())
-    return out
+    return out, (prob, u.cpu().numpy().ravel())
 
 
 def bench_c5(steps=2, warmup=1):
@@ -363,13 +387,9 @@ def bench_c5(steps=2, warmup=1):
     h2d = sum(8 * (h["a"].size + h["f"].size + h["g"].size + h["dLdu"].size) for h in hb)
     d2h = sum(8 * (h["u"].size + h["df"].size + h["dg"].size + h["da"].size) for h in hb)
     dof = sum((p["n"] - 1) ** 2 for p in probs)
-    # the oracle's adjoint gradient of the median problem on the host cores
-    from oracle import ddst_oracle as O
+    # the median problem, whose oracle gradient the cpu_baseline leg times on the host cores
     order = np.argsort([p["n"] for p in probs], kind="stable")
     pm = probs[order[nprob // 2]]
-    t0 = time.perf_counter()
-    O.loss_and_gradients(pm, np.zeros((pm["n"] - 1) ** 2))
-    t_or = time.perf_counter() - t0
     return {"workload": f"adjoint batch: {nprob} problems -div(a grad u) = f, grids 256^2..1024^2 "
                         "(n = 64 m, m ~ U{4..16}), 8/16/32 slabs, loss 1/2 ||u - u_obs||^2, "
                         "gradients wrt a, f, g; mixed precision",
@@ -378,10 +398,7 @@ def bench_c5(steps=2, warmup=1):
             "s_per_adjoint_gradient": ms / 1e3 / nprob, "ms_per_step": ms, "steps": steps,
             "warmup": warmup, "gmres_iters_adjoint": info["gmres_iters"],
             "e2e": {"s_per_adjoint_gradient": e2e_s / nprob, "unit": "s",
-                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "oracle_median_problem": {"n": pm["n"], "w": pm["w"], "s_per_gradient": t_or,
-                                      "kind": "oracle loss_and_gradients (SuperLU, FP64)",
-                                      "cpu_model": cpu_model(), "cores": os.cpu_count()}}
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}, pm
 
 
 def main():
@@ -398,7 +415,10 @@ def main():
                     help="grid of the oracle sample (default: by steps + warmup, see _ref_size)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the cpu_baseline leg (every oracle computation of this arm)")
+    ap.add_argument("--no-verify", action="store_true",
+                    help="skip the oracle's global solve of the 2D instance in the cpu_baseline leg")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
     ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
     ap.add_argument("--only-c4", action="store_true",
@@ -431,7 +451,7 @@ def main():
     if args.only_c4:
         peaks, src = _peaks()
         print(json.dumps(bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
-                                  certify=False, n=args.c4_n, w=args.c4_w)), flush=True)
+                                  n=args.c4_n, w=args.c4_w)[0]), flush=True)
         return
     n, w = args.n, args.w
     prob = I.make_problem("convdiff2d", n=n, w=w)
@@ -610,19 +630,25 @@ def main():
             "solve_info": {"gmres_iters": info["gmres_iters"], "refine_iters": info["refine_iters"],
                            "est_rel_error": info["est_rel_error"], "rel_residual": info["rel_residual"],
                            "max_rank": info["max_rank"], "bytes_transfer": info["bytes_transfer"]},
-            # the oracle's rigorous bound on ||u - u*|| / ||u*|| for this run's own solution
-            "certified_rel_error_bound": _certify(prob, u_mixed),
             "fp64_path": fp64, "e2e": e2e, "roofline": roof,
             "rooflines": {"transfer_build": roof_tc, "interface_apply": roof_ap, "factor": roof_fac},
             "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
+    c4_sol = c5_prob = None
     if rank == 0 and not args.no_c4:
-        line["c4"] = bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
-                              n=args.c4_n, w=args.c4_w)
+        line["c4"], c4_sol = bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
+                                      n=args.c4_n, w=args.c4_w)
     if rank == 0 and not args.no_c5:
-        line["c5"] = bench_c5()
+        line["c5"], c5_prob = bench_c5()
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.ref_n or 512)
+        leg = cpu_leg(prob, u_mixed, verify=not args.no_verify, c4=c4_sol, c5_prob=c5_prob,
+                      ref_n=args.ref_n or 512)
+        line["cpu_baseline"] = leg["cpu_baseline"]
+        line["verify"] = leg["verify"]
+        if "c4_certified_rel_error_bound" in leg:
+            line["c4"]["certified_rel_error_bound"] = leg["c4_certified_rel_error_bound"]
+        if "c5_oracle_median_problem" in leg:
+            line["c5"]["oracle_median_problem"] = leg["c5_oracle_median_problem"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
