@@ -116,7 +116,8 @@ typedef struct {
   int factor_warmup;    /* warm-up rows of a chunk (0: 4 w in FP32, 10 w in FP64)              */
   int tensor_cores;     /* 1: DDST_MIXED transfer build (block sizes <= 64) and large-block
                            factorization on the tcgen05 tensor cores (3xTF32); 0: FP32 FMA
-                           kernels (kept for validation)                                      */
+                           kernels (kept for validation); -1 automatic: 1 unless a tuned
+                           cache entry (autotune_cache) says otherwise                        */
   int explicit_S;       /* transfer operators: 1 formed explicitly (Alg. 1 with the identity as
                            test matrix; required by ddst_compress), 0 applied matrix-free through
                            two sweeps of local solves per GMRES iteration (no S stored), -1
@@ -126,6 +127,13 @@ typedef struct {
                            recompute them at the start of every solve, adjoint or matrix-free
                            application (the HBM they take is free in between, at the cost of
                            one factorization per call); 0: keep them                          */
+  const char* autotune_cache; /* path of the autotuner's cache file (text, one line per
+                           device and set of problem shapes), or NULL.  At setup, an entry for
+                           this device and these shapes replaces the knobs left automatic:
+                           precision (only DDST_AUTO), tensor_cores (-1), explicit_S (-1),
+                           gmres_tol (<= 0), check_every (0) and factor_chunks (0).
+                           ddst_autotune writes the entry.  The string is read during the
+                           call only.                                                         */
 } ddst_options;
 
 /* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
@@ -146,11 +154,15 @@ typedef struct {
   int factor_chunks;      /* chunks per slab sweep actually used (1 = sequential; a failed
                              warm-up check falls back to 1)                                   */
   double factor_check;    /* largest relative warm-up check difference (0 when sequential)    */
+  double refine_rho;      /* slowest refinement contraction observed: the largest ratio
+                             ||correction_k|| / ||correction_{k-1}|| over the problems (corrections
+                             at the FP64 rounding level excluded); 0 with one DD solve          */
 } ddst_info;
 
 /* Fills *opt with defaults: MIXED, gmres_tol automatic (see above), refine_tol 1e-9,
  * refine_max 8, gmres_max_iter 1000, k_max 64, oversample 10, leaf_size 128, seed 1234,
- * check_every 0 (automatic), tensor_cores 1, explicit_S -1, recompute_factors 0.
+ * check_every 0 (automatic), tensor_cores -1 (automatic), explicit_S -1, recompute_factors 0,
+ * autotune_cache NULL.
  * Testing hooks (environment variables, read at each use; they exercise the error paths without
  * a device fault):
  *  - DDST_FAIL_ALLOC=k: the k-th device allocation of the library after the variable was set
@@ -291,6 +303,55 @@ ddst_status ddst_residual_noalloc(const ddst_grid* grid, const ddst_coeffs* coef
 /* Number of CUDA kernels this library has launched in the calling process so far (a
  * diagnostic for benchmarks: the difference across a timed region counts its launches). */
 int64_t ddst_kernel_launches(void);
+
+/* ---- Autotuner --------------------------------------------------------------------------
+ * The method leaves its schedule to the implementation: how the pivot sweeps are split, the
+ * tensor-core precision, whether S is formed or applied through local solves, and how the
+ * inner GMRES tolerance is balanced against refinement steps.  ddst_autotune times these knobs
+ * on the caller's own problems (one coordinate at a time, starting from the automatic
+ * choices): each candidate is a full setup, transfer build, compression (compress_tol > 0) and
+ * two solves, and its cost is factor + transfer + compression time plus the faster solve, all
+ * CUDA-event times.  A candidate is rejected unless it solves to refine_tol with a refinement
+ * contraction (ddst_info.refine_rho) of at most 0.1, so a cheaper but less accurate operator
+ * wins only if the FP64 refinement still converges fast on it.  Only knobs left automatic in
+ * *base are tuned.  The chosen options go to rep->chosen and, when base->autotune_cache is set,
+ * into that file under the key of this device and these problem shapes (ddst_autotune_key),
+ * replacing an older entry.  f, g: nprob right-hand sides as for ddst_solve_batch.
+ * Errors: INVALID_ARG; the status of the untuned configuration when even that fails. */
+typedef struct {
+  ddst_options chosen;  /* base with the tuned knobs set (autotune_cache copied from base)     */
+  int candidates;       /* configurations run, the untuned one included                       */
+  int rejected;         /* candidates that failed or contracted slower than 0.1              */
+  double default_ms;    /* cost of the untuned configuration                                  */
+  double best_ms;       /* cost of the chosen configuration                                   */
+  double best_rho;      /* refinement contraction observed with the chosen configuration     */
+  int cache_written;    /* 1 when the entry was stored in base->autotune_cache                */
+} ddst_tune_report;
+
+ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                          const int* slab_widths, const double* const* f,
+                          const double* const* g, double compress_tol, const ddst_options* base,
+                          void* stream, ddst_tune_report* rep);
+
+/* The cache key of a set of problems on the current device: the device name, compute
+ * capability and SM count ("nodevice" without a GPU), the requested precision, and per problem
+ * its dimension, n, slab width and whether it has a reaction term.  Writes a NUL-terminated
+ * string of at most len bytes.  Errors: INVALID_ARG (NULL argument, or len too small). */
+ddst_status ddst_autotune_key(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
+                              const int* slab_widths, int precision, char* buf, size_t len);
+
+/* Cache file access (host only; no GPU needed).  ddst_autotune_lookup sets *found and, when the
+ * key is present, replaces the automatic knobs of *opt as ddst_setup does; lines that do not
+ * parse are ignored.  ddst_autotune_store writes opt's knobs under key, replacing an existing
+ * entry (the file is rewritten through a temporary file and renamed).  Errors: INVALID_ARG
+ * (NULL argument, or a file that cannot be written). */
+ddst_status ddst_autotune_lookup(const char* path, const char* key, ddst_options* opt, int* found);
+ddst_status ddst_autotune_store(const char* path, const char* key, const ddst_options* opt);
+
+/* The options a context runs with, automatic choices resolved (gmres_tol, check_every,
+ * tensor_cores, precision after a DDST_AUTO fallback) and tuned knobs applied.
+ * Errors: INVALID_ARG for a NULL argument. */
+ddst_status ddst_get_options(const ddst_ctx* ctx, ddst_options* opt);
 
 /* Message of the last error on ctx.  With ctx NULL: the last error the calling thread got
  * without a context (a failed ddst_setup, a NULL context, ddst_query, ddst_get_precision,

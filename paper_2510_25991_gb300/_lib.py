@@ -35,7 +35,7 @@ class ddst_options(C.Structure):
                 ("oversample", C.c_int), ("leaf_size", C.c_int), ("seed", C.c_uint64),
                 ("check_every", C.c_int), ("factor_chunks", C.c_int), ("factor_warmup", C.c_int),
                 ("tensor_cores", C.c_int), ("explicit_S", C.c_int),
-                ("recompute_factors", C.c_int)]
+                ("recompute_factors", C.c_int), ("autotune_cache", C.c_char_p)]
 
 
 class ddst_info(C.Structure):
@@ -45,10 +45,17 @@ class ddst_info(C.Structure):
                 ("t_transfer", C.c_double), ("t_compress", C.c_double), ("t_solve", C.c_double),
                 ("bytes_factors", C.c_int64), ("bytes_transfer", C.c_int64),
                 ("max_rank", C.c_int), ("fail_slab", C.c_int), ("fail_block", C.c_int),
-                ("factor_chunks", C.c_int), ("factor_check", C.c_double)]
+                ("factor_chunks", C.c_int), ("factor_check", C.c_double),
+                ("refine_rho", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ddst_tune_report(C.Structure):
+    _fields_ = [("chosen", ddst_options), ("candidates", C.c_int), ("rejected", C.c_int),
+                ("default_ms", C.c_double), ("best_ms", C.c_double), ("best_rho", C.c_double),
+                ("cache_written", C.c_int)]
 
 
 _P = C.c_void_p
@@ -77,6 +84,15 @@ SIGNATURES = {
     "ddst_residual_noalloc": (C.c_int, [C.POINTER(ddst_grid), C.POINTER(ddst_coeffs), _P, _P, _P,
                                         _P, _P, _P]),
     "ddst_kernel_launches": (C.c_int64, []),
+    "ddst_autotune": (C.c_int, [C.c_int, C.POINTER(ddst_grid), C.POINTER(ddst_coeffs),
+                                C.POINTER(C.c_int), _PP, _PP, C.c_double, C.POINTER(ddst_options),
+                                _P, C.POINTER(ddst_tune_report)]),
+    "ddst_autotune_key": (C.c_int, [C.c_int, C.POINTER(ddst_grid), C.POINTER(ddst_coeffs),
+                                    C.POINTER(C.c_int), C.c_int, C.c_char_p, C.c_size_t]),
+    "ddst_autotune_lookup": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(ddst_options),
+                                       C.POINTER(C.c_int)]),
+    "ddst_autotune_store": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(ddst_options)]),
+    "ddst_get_options": (C.c_int, [_P, C.POINTER(ddst_options)]),
     "ddst_last_error": (C.c_char_p, [_P]),
     "ddst_destroy": (None, [_P]),
 }

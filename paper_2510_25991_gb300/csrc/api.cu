@@ -483,6 +483,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   ctx->nprob = nprob;
   ctx->stream = reinterpret_cast<cudaStream_t>(stream);
   if (opt) ctx->opt = *opt; else ddst_options_default(&ctx->opt);
+  ctx->opt.autotune_cache = nullptr;  // read by the setup wrapper only; not kept
   ctx->prec = ctx->opt.precision == DDST_FP64 ? DDST_FP64 : DDST_MIXED;
   ctx->tf32 = ctx->opt.precision == DDST_MIXED_TF32;
   ctx->esz = ctx->prec == DDST_FP64 ? 8 : 4;
@@ -1044,7 +1045,7 @@ double refine_error_estimate(const std::vector<double>& hist, double xn) {
 // behind one with a large solution (the interface GMRES also stops on the batch's residual), so
 // the stopping test holds problem by problem.  One host synchronisation.
 double refine_batch_estimate(ddst_ctx* ctx, const double* e, const double* x,
-                             std::vector<std::vector<double>>& hist) {
+                             std::vector<std::vector<double>>& hist, double* rho) {
   const int np = ctx->nprob;
   cudaStream_t st = ctx->stream;
   launch_prob_sqnorms(ctx->d_probs, np, e, ctx->pn_part, kNormBlocks, ctx->pn, st);
@@ -1057,7 +1058,11 @@ double refine_batch_estimate(ddst_ctx* ctx, const double* e, const double* x,
   double est = 0.0;
   for (int q = 0; q < np; ++q) {
     hist[q].push_back(std::sqrt(h[q]));
-    est = std::max(est, refine_error_estimate(hist[q], std::sqrt(h[np + q])));
+    const double xn = std::sqrt(h[np + q]);
+    est = std::max(est, refine_error_estimate(hist[q], xn));
+    const size_t k = hist[q].size();  // observed contraction, rounding-level corrections aside
+    if (k >= 2 && hist[q][k - 2] > 0.0 && xn > 0.0 && hist[q][k - 1] > 1e-14 * xn)
+      *rho = std::max(*rho, hist[q][k - 1] / hist[q][k - 2]);
   }
   return est;
 }
@@ -1113,7 +1118,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
   const double bnorm = vec_norm(ctx, ctx->d_b, N, 3);
   const double tol = ctx->opt.gmres_tol;
   int total_it = 0, first_it = 0, nref = 0;
-  double est = 0.0, relres = 0.0;
+  double est = 0.0, relres = 0.0, rho = 0.0;
   std::vector<std::vector<double>> dnorm;
   ddst_status result = DDST_OK;
   const int rmax = std::max(0, ctx->opt.refine_max);
@@ -1132,7 +1137,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
-    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_u, dnorm);
+    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_u, dnorm, &rho);
     if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;
@@ -1158,6 +1163,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->refine_iters = nref;
     info->rel_residual = relres;
     info->est_rel_error = est;
+    info->refine_rho = rho;
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
@@ -1224,7 +1230,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
   CK(cudaMemsetAsync(ctx->d_lam, 0, sizeof(double) * N, st));
   const double gnorm = vec_norm(ctx, ctx->d_ga, N, 3);
   int total_it = 0, first_it = 0, nref = 0;
-  double est = 0.0;
+  double est = 0.0, rho = 0.0;
   std::vector<std::vector<double>> dnorm;
   ddst_status result = DDST_OK, s;
   const int rmax = std::max(0, ctx->opt.refine_max);
@@ -1243,7 +1249,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     total_it += its;
     ++nref;
     launch_axpy(N, 1.0, ctx->d_e, ctx->d_lam, st);
-    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_lam, dnorm);
+    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_lam, dnorm, &rho);
     if (rmax == 0) {
       if (s == DDST_ERR_NOT_CONVERGED) result = s;
       break;
@@ -1275,6 +1281,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     info->refine_iters = nref;
     info->rel_residual = relres;
     info->est_rel_error = est;
+    info->refine_rho = rho;
     info->t_solve = ms;
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
@@ -1302,6 +1309,12 @@ ddst_status setup_precision(int nprob, const ddst_grid* grids, const ddst_coeffs
     if (out) *out = nullptr;
     return fail(nullptr, DDST_ERR_INVALID_ARG,
                 "precision must be DDST_FP64, DDST_MIXED, DDST_MIXED_TF32 or DDST_AUTO");
+  }
+  if (o.autotune_cache && *o.autotune_cache) {  // tuned knobs for this device and these shapes
+    char key[8192];
+    int found = 0;
+    if (ddst_autotune_key(nprob, grids, coeffs, widths, o.precision, key, sizeof(key)) == DDST_OK)
+      ddst_autotune_lookup(o.autotune_cache, key, &o, &found);
   }
   if (o.precision != DDST_AUTO) return setup_impl(nprob, grids, coeffs, widths, &o, stream, out);
   o.precision = DDST_MIXED;
@@ -1339,9 +1352,10 @@ void ddst_options_default(ddst_options* opt) {
   opt->check_every = 0;
   opt->factor_chunks = 0;
   opt->factor_warmup = 0;
-  opt->tensor_cores = 1;
+  opt->tensor_cores = -1;
   opt->explicit_S = -1;
   opt->recompute_factors = 0;
+  opt->autotune_cache = nullptr;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
@@ -1358,6 +1372,16 @@ ddst_status ddst_setup_batch(int nprob, const ddst_grid* grids, const ddst_coeff
 ddst_status ddst_get_precision(const ddst_ctx* ctx, int* precision) {
   if (!ctx || !precision) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx or precision is NULL");
   *precision = ctx->tf32 ? DDST_MIXED_TF32 : ctx->prec;
+  return DDST_OK;
+}
+
+ddst_status ddst_get_options(const ddst_ctx* ctx, ddst_options* opt) {
+  if (!ctx || !opt) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx or opt is NULL");
+  *opt = ctx->opt;
+  opt->precision = ctx->tf32 ? DDST_MIXED_TF32 : ctx->prec;
+  if (opt->tensor_cores < 0) opt->tensor_cores = 1;
+  if (opt->check_every == 0) opt->check_every = ctx->mf_any ? 1 : 8;
+  opt->autotune_cache = nullptr;  // read during setup only
   return DDST_OK;
 }
 

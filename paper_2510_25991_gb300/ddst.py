@@ -6,6 +6,7 @@ Arrays may be CUDA ``torch`` tensors (device pointers) or contiguous NumPy / CPU
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -15,7 +16,8 @@ __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch"
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
-           "ddst_time_apply",
+           "ddst_time_apply", "ddst_get_options",
+           "ddst_autotune", "ddst_autotune_key", "ddst_autotune_lookup", "ddst_autotune_store",
            "ddst_residual_noalloc",
            "ddst_kernel_launches",
            "ddst_last_error",
@@ -84,8 +86,19 @@ def ddst_options_default(**overrides):
             if v.lower() not in _PRECISIONS:
                 raise ValueError(f"precision must be one of {', '.join(_PRECISIONS)}, not {v!r}")
             v = _PRECISIONS[v.lower()]
+        if k == "autotune_cache" and v is not None:
+            v = os.fsencode(v)  # the structure keeps the bytes object alive
         setattr(o, k, v)
     return o
+
+
+def _options_dict(o):
+    d = {k: getattr(o, k) for k, _ in L.ddst_options._fields_}
+    d["precision"] = {L.DDST_FP64: "fp64", L.DDST_MIXED: "mixed", L.DDST_MIXED_TF32: "mixed_tf32",
+                      L.DDST_AUTO: "auto"}.get(d["precision"], d["precision"])
+    if d["autotune_cache"] is not None:
+        d["autotune_cache"] = os.fsdecode(d["autotune_cache"])
+    return d
 
 
 def _coeffs(a, b=(0.0, 0.0, 0.0), c=None):
@@ -113,11 +126,7 @@ def ddst_setup(dim, n, a, slab_width, b=(0.0, 0.0, 0.0), c=None, options=None, s
 def ddst_setup_batch(problems, options=None, stream=None):
     """``problems``: list of dicts with ``dim, n, w, a`` and optional ``b, c``."""
     lib = L.load()
-    k = len(problems)
-    grids = (L.ddst_grid * k)(*[L.ddst_grid(p["dim"], p["n"]) for p in problems])
-    coeffs = (L.ddst_coeffs * k)(*[_coeffs(p["a"], p.get("b") or (0.0,) * 3, p.get("c"))
-                                   for p in problems])
-    widths = (C.c_int * k)(*[int(p["w"]) for p in problems])
+    k, grids, coeffs, widths = _problem_arrays(problems)
     out = C.c_void_p()
     st = lib.ddst_setup_batch(k, grids, coeffs, widths,
                               C.byref(options) if options is not None else None,
@@ -236,6 +245,70 @@ def ddst_residual_noalloc(dim, n, a, f, g, u, r, norms, b=(0.0, 0.0, 0.0), c=Non
     st = lib.ddst_residual_noalloc(C.byref(grid), C.byref(cf), _ptr(f), _ptr(g), _ptr(u), _ptr(r),
                                    _ptr(norms), C.c_void_p(stream) if stream else None)
     _check(lib, None, st)
+
+
+def ddst_get_options(ctx):
+    """The options the context runs with (automatic choices resolved, tuned knobs applied)."""
+    lib = L.load()
+    o = L.ddst_options()
+    _check(lib, None, lib.ddst_get_options(ctx, C.byref(o)))
+    return _options_dict(o)
+
+
+def _problem_arrays(problems):
+    k = len(problems)
+    grids = (L.ddst_grid * k)(*[L.ddst_grid(p["dim"], p["n"]) for p in problems])
+    coeffs = (L.ddst_coeffs * k)(*[_coeffs(p["a"], p.get("b") or (0.0,) * 3, p.get("c"))
+                                   for p in problems])
+    widths = (C.c_int * k)(*[int(p["w"]) for p in problems])
+    return k, grids, coeffs, widths
+
+
+def ddst_autotune(problems, fs, gs, compress_tol=0.0, stream=None, **opts):
+    """Times the schedule knobs left automatic in ``opts`` on these problems and right-hand
+    sides; returns the report as a dict (``chosen`` is an options dict).  With
+    ``autotune_cache=path`` the choice is stored there for later setups."""
+    if isinstance(problems, dict):
+        problems, fs, gs = [problems], [fs], [gs]
+    for p, f, g in zip(problems, fs, gs):
+        _check_sizes(p, f=f, g=g, a=p["a"], c=p.get("c"))
+    lib = L.load()
+    k, grids, coeffs, widths = _problem_arrays(problems)
+    o = ddst_options_default(**opts)
+    rep = L.ddst_tune_report()
+    st = lib.ddst_autotune(k, grids, coeffs, widths, _parr(fs), _parr(gs), float(compress_tol),
+                           C.byref(o), C.c_void_p(stream) if stream else None, C.byref(rep))
+    _check(lib, None, st)
+    d = {k2: getattr(rep, k2) for k2, _ in L.ddst_tune_report._fields_ if k2 != "chosen"}
+    d["chosen"] = _options_dict(rep.chosen)
+    return d
+
+
+def ddst_autotune_key(problems, precision="mixed"):
+    if isinstance(problems, dict):
+        problems = [problems]
+    lib = L.load()
+    k, grids, coeffs, widths = _problem_arrays(problems)
+    buf = C.create_string_buffer(8192)
+    prec = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib, None, lib.ddst_autotune_key(k, grids, coeffs, widths, prec, buf, len(buf)))
+    return buf.value.decode()
+
+
+def ddst_autotune_lookup(path, key, **opts):
+    """(found, options dict): the cached knobs applied to ``opts``' automatic fields."""
+    lib = L.load()
+    o = ddst_options_default(**opts)
+    found = C.c_int()
+    _check(lib, None, lib.ddst_autotune_lookup(os.fsencode(path), key.encode(), C.byref(o),
+                                               C.byref(found)))
+    return bool(found.value), _options_dict(o)
+
+
+def ddst_autotune_store(path, key, **opts):
+    lib = L.load()
+    o = ddst_options_default(**opts)
+    _check(lib, None, lib.ddst_autotune_store(os.fsencode(path), key.encode(), C.byref(o)))
 
 
 def ddst_kernel_launches():
