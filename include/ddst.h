@@ -134,6 +134,16 @@ typedef struct {
                            gmres_tol (<= 0), check_every (0) and factor_chunks (0).
                            ddst_autotune writes the entry.  The string is read during the
                            call only.                                                         */
+  int interface_solver; /* 0: GMRES on (I - K) u_Gamma = fhat (the paper's solver); 1: direct,
+                           by block cyclic reduction of the block-tridiagonal system (the
+                           direct solvers of Sec. 4), factored from the explicit S at the first
+                           solve after ddst_build_transfer (dense blocks, also after
+                           ddst_compress) and reused by every later solve and adjoint.  Needs
+                           explicit transfer operators and n_Gamma <= 8192 (else
+                           NOT_IMPLEMENTED at the solve).  Cost: per level, the inversion of
+                           half the remaining diagonal blocks and about three products of
+                           n_Gamma^3 per block; memory about 5 N_ds n_Gamma^2 elements plus
+                           packed scratch during the factorization                            */
 } ddst_options;
 
 /* Per-call report.  Times are milliseconds measured with CUDA events on the context stream. */
@@ -154,6 +164,7 @@ typedef struct {
   int factor_chunks;      /* chunks per slab sweep actually used (1 = sequential; a failed
                              warm-up check falls back to 1)                                   */
   double factor_check;    /* largest relative warm-up check difference (0 when sequential)    */
+  double t_direct;        /* milliseconds of the direct interface factorization (0 if none)  */
   double refine_rho;      /* slowest refinement contraction observed: the largest ratio
                              ||correction_k|| / ||correction_{k-1}|| over the problems (corrections
                              at the FP64 rounding level excluded); 0 with one DD solve          */
@@ -303,6 +314,17 @@ ddst_status ddst_residual_noalloc(const ddst_grid* grid, const ddst_coeffs* coef
 /* Number of CUDA kernels this library has launched in the calling process so far (a
  * diagnostic for benchmarks: the difference across a timed region counts its launches). */
 int64_t ddst_kernel_launches(void);
+
+/* The direct interface solve alone (interface_solver = 1 machinery, whatever the option):
+ * x = (I - K)^{-1} rhs (transpose 0) or (I - K)^{-T} rhs (transpose 1) for problem prob, rhs and
+ * x of N_ds n_Gamma values in the interface order above, by block cyclic reduction of the
+ * explicit transfer operators (factored at the first call, kept until ddst_build_transfer runs
+ * again).  Sec. 1, Eq. (modelS); Sec. 4, direct solvers.  Errors: INVALID_ARG, STATE (no
+ * transfer operators), NOT_IMPLEMENTED (matrix-free operators, n_Gamma > 8192), SINGULAR (a
+ * diagonal block of the reduction fell below 1e3 eps; fail_slab names the interface block),
+ * OOM. */
+ddst_status ddst_solve_interface(ddst_ctx* ctx, int prob, const double* rhs, double* x,
+                                 int transpose);
 
 /* ---- Autotuner --------------------------------------------------------------------------
  * The method leaves its schedule to the implementation: how the pivot sweeps are split, the

@@ -35,7 +35,8 @@ class ddst_options(C.Structure):
                 ("oversample", C.c_int), ("leaf_size", C.c_int), ("seed", C.c_uint64),
                 ("check_every", C.c_int), ("factor_chunks", C.c_int), ("factor_warmup", C.c_int),
                 ("tensor_cores", C.c_int), ("explicit_S", C.c_int),
-                ("recompute_factors", C.c_int), ("autotune_cache", C.c_char_p)]
+                ("recompute_factors", C.c_int), ("autotune_cache", C.c_char_p),
+                ("interface_solver", C.c_int)]
 
 
 class ddst_info(C.Structure):
@@ -46,7 +47,7 @@ class ddst_info(C.Structure):
                 ("bytes_factors", C.c_int64), ("bytes_transfer", C.c_int64),
                 ("max_rank", C.c_int), ("fail_slab", C.c_int), ("fail_block", C.c_int),
                 ("factor_chunks", C.c_int), ("factor_check", C.c_double),
-                ("refine_rho", C.c_double)]
+                ("t_direct", C.c_double), ("refine_rho", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +79,7 @@ SIGNATURES = {
     "ddst_get_transfer": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P]),
     "ddst_apply_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "ddst_time_apply": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_float)]),
+    "ddst_solve_interface": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
     "ddst_query": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64),
                              C.POINTER(C.c_int)]),
     "ddst_get_precision": (C.c_int, [_P, C.POINTER(C.c_int)]),

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/ddst.h"
+#include "bcr.cuh"
 #include "hodlr.cuh"
 #include "kernels.cuh"
 
@@ -138,6 +139,11 @@ struct ddst_ctx {
   double* if_kx = nullptr;
   long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
   bool solve_bufs_ready = false;
+  // direct interface solver (interface_solver = 1): block cyclic reduction of every problem's
+  // equilibrium system, formed from the explicit S at the first solve after build_transfer
+  std::vector<BcrSystem> bcr;
+  bool bcr_ready = false;
+  float t_bcr = 0.f;
   bool factors_valid = false;            // local factors present (recompute_factors releases them)
 };
 
@@ -721,9 +727,12 @@ void maybe_release_factors(ddst_ctx* ctx) {
 // --------------------------------------------------------------------------------------------
 // Transfer operators
 // --------------------------------------------------------------------------------------------
+void drop_bcr(ddst_ctx* ctx);
+
 template <typename T>
 ddst_status build_transfer_impl(ddst_ctx* ctx) {
   cudaStream_t st = ctx->stream;
+  drop_bcr(ctx);  // formed again from the new operators when next needed
   if (ctx->matfree) {  // S is applied through the local factors: nothing to form
     ctx->t_transfer = 0.f;
     ctx->hodlr.clear();
@@ -956,6 +965,105 @@ double host_scalar(ddst_ctx* ctx, const double* d) {
   return h;
 }
 
+// --------------------------------------------------------------------------------------------
+// Direct interface solver: block cyclic reduction of (I - K) from the explicit S (bcr.cu)
+// --------------------------------------------------------------------------------------------
+BcrEnv bcr_env(ddst_ctx* ctx) {
+  BcrEnv env;
+  env.alloc = [ctx](void** p, size_t b) { return dalloc(ctx, p, b); };
+  env.release = [ctx](void*& p) { dfree(ctx, p); };
+  env.st = ctx->stream;
+  env.sh = ctx->s_hi;
+  env.sl = ctx->s_lo;
+  env.ev = ctx->big_ev;
+  env.d_st = ctx->d_st;
+  env.tensor_cores = ctx->prec == DDST_MIXED && ctx->opt.tensor_cores != 0 ? (ctx->tf32 ? 2 : 1) : 0;
+  return env;
+}
+
+void drop_bcr(ddst_ctx* ctx) {
+  if (ctx->bcr.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  const BcrEnv env = bcr_env(ctx);
+  for (BcrSystem& b : ctx->bcr) bcr_free(b, env);
+  ctx->bcr.clear();
+  ctx->bcr_ready = false;
+}
+
+// The panel look-ahead streams and events (created at setup when a class has large blocks).
+cudaError_t ensure_side_streams(ddst_ctx* ctx) {
+  cudaError_t e;
+  if (!ctx->s_hi) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if ((e = cudaStreamCreateWithPriority(&ctx->s_hi, cudaStreamNonBlocking, hi)) != cudaSuccess) return e;
+    if ((e = cudaStreamCreateWithPriority(&ctx->s_lo, cudaStreamNonBlocking, lo)) != cudaSuccess) return e;
+  }
+  for (cudaEvent_t& ev : ctx->big_ev)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+ddst_status ensure_bcr(ddst_ctx* ctx) {
+  if (ctx->bcr_ready) return DDST_OK;
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "ddst_build_transfer has not completed");
+  if (ctx->mf_any)
+    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED,
+                "the direct interface solve eliminates the explicit transfer operators; this "
+                "context applies some matrix-free (explicit_S = 0, or blocks larger than 128)");
+  for (const ProbDesc& P : ctx->probs)
+    if (P.ng > 8192)
+      return fail(ctx, DDST_ERR_NOT_IMPLEMENTED,
+                  "direct interface solve: interfaces of %lld points exceed 8192",
+                  (long long)P.ng);
+  cudaError_t e = ensure_side_streams(ctx);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream create");
+  drop_bcr(ctx);
+  Timer tm(ctx->stream);
+  const BcrEnv env = bcr_env(ctx);
+  ctx->bcr.resize(ctx->nprob);
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    std::vector<int64_t> sp(P.nds), sn(P.nds);
+    for (int j = 0; j < P.nds; ++j) {
+      sp[j] = ctx->slabs[P.slab0 + j].sp_off;
+      sn[j] = ctx->slabs[P.slab0 + j].sn_off;
+    }
+    e = bcr_factor<T>(ctx->bcr[q], (const T*)ctx->S, sp, sn, P.nds, P.ng, env);
+    if (e != cudaSuccess) {
+      drop_bcr(ctx);
+      return e == cudaErrorMemoryAllocation ? cuda_fail(ctx, e, "cudaMalloc (direct interface solver)")
+                                            : cuda_fail(ctx, e, "direct interface factorization");
+    }
+  }
+  ctx->t_bcr = tm.stop();
+  ddst_status s = check_status(ctx, nullptr);
+  if (s != DDST_OK) {
+    drop_bcr(ctx);
+    const std::string m = ctx->err;
+    return fail(ctx, s, "direct interface factorization: %s (slab = interface block, 0-based)",
+                m.c_str());
+  }
+  ctx->bcr_ready = true;
+  return DDST_OK;
+}
+
+// x = (I - K)^{-1} rhs (or ^{-T}) for every problem through the factored systems.
+template <typename T>
+ddst_status direct_interface_solve(ddst_ctx* ctx, const double* rhs, double* x, int transpose) {
+  ddst_status s = ensure_bcr<T>(ctx);
+  if (s != DDST_OK) return s;
+  const BcrEnv env = bcr_env(ctx);
+  if (rhs != x) CK(cudaMemcpyAsync(x, rhs, sizeof(double) * ctx->tot_if, cudaMemcpyDeviceToDevice, ctx->stream));
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    const cudaError_t e = bcr_solve<T>(ctx->bcr[q], x + P.if_off, ctx->if_tmp + P.if_off, transpose, env);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "direct interface solve");
+  }
+  return DDST_OK;
+}
+
 // GMRES on (I - K) x = rhs (or its transpose), x0 = 0.  Returns iterations; sets *relres.
 template <typename T>
 ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, int transpose,
@@ -1079,8 +1187,15 @@ ddst_status dd_apply(ddst_ctx* ctx, const double* r, double* e, int* iters, doub
   launch_gather<T>(ctx->d_slabs, nslab, r, lb, st);
   local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, ctx->if_fh, 0, 1, st);
   CK(cudaGetLastError());
-  // interface solve (I - K) u_Gamma = fhat
-  ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 0, iters, relres);
+  // interface solve (I - K) u_Gamma = fhat: GMRES, or the block cyclic reduction
+  ddst_status s;
+  if (ctx->opt.interface_solver == 1) {
+    s = direct_interface_solve<T>(ctx, ctx->if_fh, ctx->if_u, 0);
+    *iters = 0;
+    *relres = 0.0;
+  } else {
+    s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 0, iters, relres);
+  }
   if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
   // volume reconstruction: local Dirichlet solves with the traces on Gamma_{j-1}, Gamma_{j+1}
   launch_add_iface_dirichlet<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, ctx->if_u, lb, st);
@@ -1164,6 +1279,7 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     info->rel_residual = relres;
     info->est_rel_error = est;
     info->refine_rho = rho;
+    info->t_direct = ctx->t_bcr;
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
@@ -1202,7 +1318,14 @@ ddst_status dd_apply_T(ddst_ctx* ctx, const double* r, double* e, int* iters, do
   launch_iface_dirichlet_T<T>(ctx->d_slabs, ctx->d_probs, nslab, (T*)ctx->pack, (T*)ctx->loc_x,
                               ctx->if_fh, st);
   CK(cudaGetLastError());
-  ddst_status s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 1, iters, relres);
+  ddst_status s;
+  if (ctx->opt.interface_solver == 1) {
+    s = direct_interface_solve<T>(ctx, ctx->if_fh, ctx->if_u, 1);
+    *iters = 0;
+    *relres = 0.0;
+  } else {
+    s = gmres_impl<T>(ctx, ctx->if_fh, ctx->if_u, tol, 1, iters, relres);
+  }
   if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
   launch_inject_center<T>(ctx->d_slabs, nslab, ctx->if_u, lb, st);
   local_solves<T>(ctx, lb, (T*)ctx->loc_bf, (T*)ctx->loc_bb, (T*)ctx->loc_x, nullptr, 1, 0, st);
@@ -1282,6 +1405,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     info->rel_residual = relres;
     info->est_rel_error = est;
     info->refine_rho = rho;
+    info->t_direct = ctx->t_bcr;
     info->t_solve = ms;
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
@@ -1356,6 +1480,7 @@ void ddst_options_default(ddst_options* opt) {
   opt->explicit_S = -1;
   opt->recompute_factors = 0;
   opt->autotune_cache = nullptr;
+  opt->interface_solver = 0;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
@@ -1538,6 +1663,26 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
   CK(stage_out(y, ctx->if_w + P.if_off, len, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return DDST_OK;
+}
+
+ddst_status ddst_solve_interface(ddst_ctx* ctx, int prob, const double* rhs, double* x,
+                                 int transpose) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (prob < 0 || prob >= ctx->nprob) return fail(ctx, DDST_ERR_INVALID_ARG, "bad problem index");
+  if (!rhs || !x) return fail(ctx, DDST_ERR_INVALID_ARG, "rhs or x is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  ddst_status s = ensure_solve_buffers(ctx);
+  if (s != DDST_OK) return s;
+  const ProbDesc& P = ctx->probs[prob];
+  const size_t len = (size_t)P.nds * P.ng;
+  CK(cudaMemsetAsync(ctx->if_u, 0, sizeof(double) * ctx->tot_if, ctx->stream));
+  CK(stage_in(ctx->if_u + P.if_off, rhs, len, ctx->stream));
+  s = ctx->prec == DDST_FP64 ? direct_interface_solve<double>(ctx, ctx->if_u, ctx->if_u, transpose != 0)
+                             : direct_interface_solve<float>(ctx, ctx->if_u, ctx->if_u, transpose != 0);
+  if (s != DDST_OK) return s;
+  CK(stage_out(x, ctx->if_u + P.if_off, len, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_status(ctx, nullptr);
 }
 
 ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms) {

@@ -20,11 +20,10 @@
 // one batched matrix-vector product per block row); A_j^{-T} uses the same factors transposed.
 #include "bgj.cuh"
 #include "kernels.cuh"
+#include "splittile.cuh"
 #include "umma.cuh"
 
 namespace ddst {
-
-constexpr int BT = 128;  // panel width and output tile edge
 
 // ---------------------------------------------------------------------------------------------
 // Sigma_k = D_k - diag(ell_k) F_{k-1} diag(ups_{k-1}), written into the slot of F_k.
@@ -58,39 +57,6 @@ __global__ void __launch_bounds__(256) k_big_sigma(const SlabDesc* __restrict__ 
     }
     if (k > 1) v -= pk[PK_SOUTH * M + r] * Xp[e] * pkp[PK_NORTH * M + c];
     X[e] = v;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Operand tiles of the tensor-core steps are stored once, already split into TF32 parts
-// (hi = rna(x), lo = rna(x - hi)) in the canonical K-major layout, chunk-major: element (r, k) of
-// a 128 x 128 tile (r: output row, k: contraction index) sits at float offset
-//     (k / 16) * 2048 + umma_off(r, k % 16, 16) / 4
-// of the hi part, and 16384 floats further in the lo part.  One 16-wide K chunk of one part is a
-// contiguous 8 KB block, so the MMA kernels load their operands with plain bulk copies.
-// ---------------------------------------------------------------------------------------------
-constexpr int SPLIT_TILE = 2 * BT * BT;  // floats of one split tile (hi + lo)
-
-__device__ __forceinline__ int split_off(int r, int k) {
-  return (k >> 4) * 2048 + (int)(umma_off(r, k & 15, 16) >> 2);
-}
-
-// Element (r, k) read from shared memory at src[r * ldr + k * ldk].
-__device__ __forceinline__ void store_split_tile(const float* __restrict__ src, int ldr, int ldk,
-                                                 float* __restrict__ dst) {
-  for (int e = threadIdx.x; e < BT * (BT / 4); e += blockDim.x) {
-    const int r = e % BT, k = 4 * (e / BT);
-    float x[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) x[u] = src[r * ldr + (k + u) * ldk];
-    float4 h, l;
-    h.x = tf32_rna(x[0]); l.x = tf32_rna(x[0] - h.x);
-    h.y = tf32_rna(x[1]); l.y = tf32_rna(x[1] - h.y);
-    h.z = tf32_rna(x[2]); l.z = tf32_rna(x[2] - h.z);
-    h.w = tf32_rna(x[3]); l.w = tf32_rna(x[3] - h.w);
-    const int o = split_off(r, k);
-    *reinterpret_cast<float4*>(dst + o) = h;
-    *reinterpret_cast<float4*>(dst + BT * BT + o) = l;
   }
 }
 
@@ -786,7 +752,7 @@ template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
                             const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
                             T* const RT[2], T* const Pinv[2], int tensor_cores, DevStatus* st,
-                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev) {
+                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev, int form_sigma) {
   const int nP = M / BT;
   bool tc = false;
   if constexpr (sizeof(T) == 4) tc = tensor_cores != 0;
@@ -848,8 +814,10 @@ void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, in
     raise_smem_limit(reinterpret_cast<const void*>(&k_big_pivot<T, false>), psm);
   }
   cudaEvent_t evA = ev[0], evB[2] = {ev[1], ev[2]};
-  note_launch();
-  k_big_sigma<T><<<dim3(512, nids), 256, 0, sh>>>(d_slabs, d_ids, pack, F, k);
+  if (form_sigma) {
+    note_launch();
+    k_big_sigma<T><<<dim3(512, nids), 256, 0, sh>>>(d_slabs, d_ids, pack, F, k);
+  }
   pivot(0);
   if (nP == 1) return;
   row(0);
@@ -926,12 +894,12 @@ void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, con
 template void launch_big_factor_step<float>(int, const SlabDesc*, const int*, int, const float*,
                                             float*, int, float* const[2], float* const[2],
                                             float* const[2], float* const[2], int, DevStatus*,
-                                            cudaStream_t, cudaStream_t, cudaEvent_t*);
+                                            cudaStream_t, cudaStream_t, cudaEvent_t*, int);
 template void launch_big_factor_step<double>(int, const SlabDesc*, const int*, int,
                                              const double*, double*, int, double* const[2],
                                              double* const[2], double* const[2],
                                              double* const[2], int, DevStatus*, cudaStream_t,
-                                             cudaStream_t, cudaEvent_t*);
+                                             cudaStream_t, cudaEvent_t*, int);
 template void launch_big_solve<float>(int, const SlabDesc*, const int*, int, int, const float*,
                                       const float*, const float*, float*, float*, int,
                                       cudaStream_t);

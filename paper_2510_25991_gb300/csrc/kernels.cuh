@@ -126,13 +126,14 @@ void launch_trisolve(const double* H, int ldh, const double* gv, int kk, double*
 // Gauss-Jordan panels with look-ahead on two streams: sh high priority, sl the bulk updates; ev
 // three events).  Two sets of work buffers (alternating by panel parity), each Cb, XqT, RT
 // (nids x M x 128, twice that when split for the tensor cores) and Pinv (nids x 128 x 128, or
-// twice).  tensor_cores: 0 FMA, 1 tcgen05 3xTF32, 2 tcgen05 TF32.  All work is ordered before
-// later work on sh.
+// twice).  tensor_cores: 0 FMA, 1 tcgen05 3xTF32, 2 tcgen05 TF32.  form_sigma = 0 skips the
+// Schur complement and inverts the block already in the slot of F_k (the pivot floor is then
+// 1e3 eps |pack diagonal|).  All work is ordered before later work on sh.
 template <typename T>
 void launch_big_factor_step(int M, const SlabDesc* d_slabs, const int* d_ids, int nids,
                             const T* pack, T* F, int k, T* const Cb[2], T* const XqT[2],
                             T* const RT[2], T* const Pinv[2], int tensor_cores, DevStatus* st,
-                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev);
+                            cudaStream_t sh, cudaStream_t sl, cudaEvent_t* ev, int form_sigma = 1);
 // Local solve x = A^{-1} b (transpose 0) or A^{-T} b (transpose 1) of every slab of the class;
 // z is a slab-local temporary.
 template <typename T>
@@ -142,6 +143,52 @@ void launch_big_solve(int M, const SlabDesc* d_slabs, const int* d_ids, int nids
 template <typename T>
 void launch_big_extract(const SlabDesc* d_slabs, const int* d_ids, int nids, const T* loc,
                         double* iface, cudaStream_t s);
+
+// gemm_tc.cu: batched products of square blocks of edge 128 nT (row-major, leading dimension
+// 128 nT).  Packing writes pre-split TF32 tiles: trans 0 for an A operand, 1 for a B operand
+// (packed as B^T); a packed block takes 2 (128 nT)^2 floats.
+struct PackTask {
+  const float* src;
+  float* dst;
+  int trans;
+};
+struct GemmTask {  // C = alpha A B (+ C when accumulate), A and B packed
+  const float* A;
+  const float* B;
+  float* C;
+  float alpha;
+  int accumulate;
+};
+template <typename T>
+struct GemmTaskT {  // the same on plain row-major blocks (FMA kernel)
+  const T* A;
+  const T* B;
+  T* C;
+  T alpha;
+  int accumulate;
+};
+void launch_pack_split(const PackTask* d_tasks, int ntasks, int nT, cudaStream_t st);
+// three: 1 3xTF32, 0 TF32.  Timeouts of the bounded waits are recorded in *dst.
+void launch_gemm_tc(const GemmTask* d_tasks, int ntasks, int nT, int three, DevStatus* dst,
+                    cudaStream_t st);
+template <typename T>
+void launch_gemm_fma(const GemmTaskT<T>* d_tasks, int ntasks, int nT, cudaStream_t st);
+
+// bcr.cu: products of interface blocks with FP64 vectors for the direct interface solve.
+// Task: y = x0 + coef sum over its terms of op(M_t) v_t (op = transpose or not, M_t blocks of
+// leading dimension ldm, vectors of length n; NULL terms and a NULL x0 count as zero).  x0 may
+// alias y; the v_t may not.
+template <typename T>
+struct BlockMv {
+  double* y;
+  const double* x0;
+  double coef;
+  const T* M[2];
+  const double* v[2];
+};
+template <typename T>
+void launch_block_mv(const BlockMv<T>* d_tasks, int ntasks, int n, int ldm, int transpose,
+                     cudaStream_t st);
 
 // matfree.cu: the interface operator through local solves, over the listed slabs (x indexed by
 // kdev as above)

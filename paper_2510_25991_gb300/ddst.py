@@ -16,7 +16,7 @@ __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch"
            "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
-           "ddst_time_apply", "ddst_get_options",
+           "ddst_time_apply", "ddst_get_options", "ddst_solve_interface",
            "ddst_autotune", "ddst_autotune_key", "ddst_autotune_lookup", "ddst_autotune_store",
            "ddst_residual_noalloc",
            "ddst_kernel_launches",
@@ -199,6 +199,13 @@ def ddst_get_transfer(ctx, prob, j, side, out):
 def ddst_apply_interface(ctx, prob, x, y, transpose=False):
     lib = L.load()
     _check(lib, ctx, lib.ddst_apply_interface(ctx, prob, _ptr(x), _ptr(y), int(bool(transpose))))
+
+
+def ddst_solve_interface(ctx, prob, rhs, x, transpose=False):
+    """x = (I - K)^{-1} rhs (or ^{-T}) for one problem by the direct (block cyclic reduction)
+    interface solver."""
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_solve_interface(ctx, prob, _ptr(rhs), _ptr(x), int(bool(transpose))))
 
 
 def ddst_time_apply(ctx, transpose=False, reps=50):
