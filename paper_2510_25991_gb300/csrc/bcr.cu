@@ -23,20 +23,27 @@
 namespace ddst {
 
 // ---------------------------------------------------------------------------------------------
-// Initial blocks: dst (NG x NG, padded) = sign * src (n x n, row-major) on the top-left, zero
-// elsewhere; identity when src is NULL (the diagonal blocks, padding included).
+// Initial blocks: dst (NG x NG, row-major, padded) = sign * src on the top-left n x n, zero
+// elsewhere, where src holds the transfer block column by column (the transfer build writes one
+// source point's column at a time); identity when src is NULL (the diagonal blocks, padding
+// included).  32 x 32 tiles transposed through shared memory, grid = (NG/32, NG/32), 32 x 8.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void k_bcr_init(const T* __restrict__ src, int64_t n, T* __restrict__ dst, int NG,
-                           T sign) {
-  const int64_t tot = (int64_t)NG * NG;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / NG, c = e - r * NG;
-    T v;
-    if (!src) v = r == c ? T(1) : T(0);
-    else v = (r < n && c < n) ? sign * src[r * n + c] : T(0);
-    dst[e] = v;
+__global__ void __launch_bounds__(256) k_bcr_init(const T* __restrict__ src, int64_t n,
+                                                  T* __restrict__ dst, int NG, T sign) {
+  __shared__ T tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (src) {
+    for (int k = ty; k < 32; k += 8) {  // src column c0 + k, rows r0 + tx (coalesced)
+      const int64_t c = c0 + k, r = r0 + tx;
+      tile[k][tx] = (r < n && c < n) ? src[c * n + r] : T(0);
+    }
+    __syncthreads();
+  }
+  for (int k = ty; k < 32; k += 8) {  // dst row r0 + k, columns c0 + tx (coalesced)
+    const int64_t r = r0 + k, c = c0 + tx;
+    dst[r * NG + c] = src ? sign * tile[tx][k] : (r == c ? T(1) : T(0));
   }
 }
 
@@ -196,15 +203,16 @@ cudaError_t bcr_factor(BcrSystem& B, const T* S, const std::vector<int64_t>& sp_
   T* U = (T*)B.U;
   T* PQ = (T*)B.PQ;
   auto blkp = [&](T* base, int j) { return base + (size_t)j * blk; };
+  const dim3 ig(NG / 32, NG / 32), ib(32, 8);
   for (int j = 0; j < nds; ++j) {
     note_launch();
-    k_bcr_init<T><<<1024, 256, 0, st>>>(nullptr, ng, blkp(D, j), NG, T(1));
+    k_bcr_init<T><<<ig, ib, 0, st>>>(nullptr, ng, blkp(D, j), NG, T(1));
     note_launch();
-    k_bcr_init<T><<<1024, 256, 0, st>>>(sp_off[j] >= 0 ? S + sp_off[j] : nullptr, ng, blkp(L, j),
-                                        NG, T(-1));
+    k_bcr_init<T><<<ig, ib, 0, st>>>(sp_off[j] >= 0 ? S + sp_off[j] : nullptr, ng, blkp(L, j),
+                                     NG, T(-1));
     note_launch();
-    k_bcr_init<T><<<1024, 256, 0, st>>>(sn_off[j] >= 0 ? S + sn_off[j] : nullptr, ng, blkp(U, j),
-                                        NG, T(-1));
+    k_bcr_init<T><<<ig, ib, 0, st>>>(sn_off[j] >= 0 ? S + sn_off[j] : nullptr, ng, blkp(U, j),
+                                     NG, T(-1));
   }
   // a block without a neighbour on one side has no coupling there: zero it (not identity)
   if (sp_off[0] < 0 && (e = cudaMemsetAsync(blkp(L, 0), 0, sizeof(T) * blk, st)) != cudaSuccess) return e;
