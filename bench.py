@@ -316,6 +316,75 @@ def bench_c4(peaks, src, steps=2, warmup=1, n=128, w=16):
     return out, (prob, u.cpu().numpy().ravel())
 
 
+def bcr_flops(nds, m):
+    """Products and inversions of the block cyclic reduction of N_ds blocks of edge m (the level
+    structure of the library's direct interface solver): 2 m^3 flops per block product and per
+    inversion."""
+    cur = list(range(nds))
+    prods = invs = 0
+    while len(cur) > 1:
+        k = len(cur)
+        odd = [p for p in range(k) if p & 1]
+        invs += len(odd)
+        for p in range(0, k, 2):
+            if p >= 1:
+                prods += 3  # P = L D^-1, D -= P U, L' = -P L
+            if p + 1 < k:
+                prods += 2 + (1 if p + 2 < k else 0)  # Q = U D^-1, D -= Q L, U' = -Q U
+        cur = [cur[p] for p in range(0, k, 2)]
+    invs += 1
+    return prods * 2.0 * m ** 3, invs * 2.0 * m ** 3
+
+
+def bench_direct(a, f, g, n, w, tol, peaks, src, solves=5):
+    """The direct interface solver on the headline workload (same problem, HODLR-compressed
+    operators for the GMRES reference): the block cyclic reduction of (I - K) is factored once
+    from the explicit S at the first solve and reused by every later one.  Reports the
+    factorization time and its tensor-core rate, and the per-solve time of both interface
+    solvers (median of `solves` solves after the first)."""
+    import torch
+
+    from paper_2510_25991_gb300 import ddst as D
+    u = torch.empty((n - 1, n - 1), dtype=torch.float64, device="cuda")
+    res = {}
+    for isol in (0, 1):
+        sol = D.Solver(dict(dim=2, n=n, w=w, a=a, b=(20.0, 10.0, 0.0)), precision="mixed",
+                       k_max=64, oversample=10, interface_solver=isol)
+        sol.build_transfer()
+        if tol > 0:
+            sol.compress(tol)
+        st, first = sol.solve(f, g, u)
+        ts, info = [], first
+        for _ in range(solves):
+            st, info = sol.solve(f, g, u)
+            ts.append(info["t_solve"])
+        sol.close()
+        res[isol] = (first, info, statistics.median(ts))
+    dof = (n - 1) ** 2
+    nds, ng = n // w - 1, n - 1
+    NG = (ng + 127) // 128 * 128
+    prod_alg, inv_alg = bcr_flops(nds, ng)
+    prod_pad, inv_pad = bcr_flops(nds, NG)
+    fac_ms = res[1][1]["t_direct"]
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
+    return {"workload": f"convdiff2d n={n} w={w}: block cyclic reduction of (I - K), {nds} interface "
+                        f"blocks of {ng} (padded to {NG}), mixed precision (3xTF32 tensor-core products)",
+            "factor_ms": fac_ms,
+            "factor_roofline": {"bound": "tensor", "algorithmic_flops": prod_alg + inv_alg,
+                                "achieved": (prod_alg + inv_alg) / (fac_ms / 1e3) / 1e12,
+                                "peak": tf32_peak, "unit": "TFLOP/s",
+                                "frac": (prod_alg + inv_alg) / (fac_ms / 1e3) / 1e12 / tf32_peak,
+                                "executed_tensor_flops": 3 * (prod_pad + inv_pad),
+                                "peak_source": f"bf16 burst {peaks['bf16_tflops']} TFLOP/s x 1.1/2.25 "
+                                               f"(nominal TF32:BF16), of {src}"},
+            "solve_ms": {"direct": res[1][2], "gmres": res[0][2]},
+            "solve_only_dof_per_s": {"direct": dof / (res[1][2] / 1e3), "gmres": dof / (res[0][2] / 1e3)},
+            "first_solve_ms_direct": res[1][0]["t_solve"],
+            "refine_iters": {"direct": res[1][1]["refine_iters"], "gmres": res[0][1]["refine_iters"]},
+            "gmres_iters": res[0][1]["gmres_iters"],
+            "est_rel_error": {"direct": res[1][1]["est_rel_error"], "gmres": res[0][1]["est_rel_error"]}}
+
+
 def bench_c5(steps=2, warmup=1):
     """The adjoint batch: 64 independent 2D problems -div(a grad u) = f with grids uneven in
     256^2 .. 1024^2 and 8, 16 or 32 slabs (slab widths 8 .. 128 cells), loss 1/2 ||u - u_obs||^2,
@@ -419,6 +488,8 @@ def main():
                     help="skip the cpu_baseline leg (every oracle computation of this arm)")
     ap.add_argument("--no-verify", action="store_true",
                     help="skip the oracle's global solve of the 2D instance in the cpu_baseline leg")
+    ap.add_argument("--no-direct", action="store_true",
+                    help="skip the direct interface solver section")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
     ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
     ap.add_argument("--only-c4", action="store_true",
@@ -634,6 +705,8 @@ def main():
             "rooflines": {"transfer_build": roof_tc, "interface_apply": roof_ap, "factor": roof_fac},
             "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
+    if rank == 0 and not args.no_direct:
+        line["direct"] = bench_direct(a, f, g, n, w, args.tol, peaks, src)
     c4_sol = c5_prob = None
     if rank == 0 and not args.no_c4:
         line["c4"], c4_sol = bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,

@@ -131,10 +131,12 @@ typedef struct {
                            device and set of problem shapes), or NULL.  At setup, an entry for
                            this device and these shapes replaces the knobs left automatic:
                            precision (only DDST_AUTO), tensor_cores (-1), explicit_S (-1),
-                           gmres_tol (<= 0), check_every (0) and factor_chunks (0).
+                           gmres_tol (<= 0), check_every (0), factor_chunks (0) and
+                           interface_solver (-1).
                            ddst_autotune writes the entry.  The string is read during the
                            call only.                                                         */
-  int interface_solver; /* 0: GMRES on (I - K) u_Gamma = fhat (the paper's solver); 1: direct,
+  int interface_solver; /* 0: GMRES on (I - K) u_Gamma = fhat (the paper's solver); -1
+                           automatic: GMRES unless a tuned cache entry says 1; 1: direct,
                            by block cyclic reduction of the block-tridiagonal system (the
                            direct solvers of Sec. 4), factored from the explicit S at the first
                            solve after ddst_build_transfer (dense blocks, also after
@@ -339,6 +341,10 @@ ddst_status ddst_solve_interface(ddst_ctx* ctx, int prob, const double* rhs, dou
  * *base are tuned.  The chosen options go to rep->chosen and, when base->autotune_cache is set,
  * into that file under the key of this device and these problem shapes (ddst_autotune_key),
  * replacing an older entry.  f, g: nprob right-hand sides as for ddst_solve_batch.
+ * solves_per_setup (>= 1) weighs the solve against the one-time work in the cost: setup
+ * phases + direct interface factorization + solves_per_setup x one solve (the second of the two,
+ * without one-time work); the interface solver is tuned too (GMRES or block cyclic reduction).
+ * The cache key does not include solves_per_setup: the last tuning of a shape is the one kept.
  * Errors: INVALID_ARG; the status of the untuned configuration when even that fails. */
 typedef struct {
   ddst_options chosen;  /* base with the tuned knobs set (autotune_cache copied from base)     */
@@ -352,8 +358,8 @@ typedef struct {
 
 ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
                           const int* slab_widths, const double* const* f,
-                          const double* const* g, double compress_tol, const ddst_options* base,
-                          void* stream, ddst_tune_report* rep);
+                          const double* const* g, double compress_tol, int solves_per_setup,
+                          const ddst_options* base, void* stream, ddst_tune_report* rep);
 
 /* The cache key of a set of problems on the current device: the device name, compute
  * capability and SM count ("nodevice" without a GPU), the requested precision, and per problem

@@ -87,8 +87,8 @@ SIGNATURES = {
                                         _P, _P, _P]),
     "ddst_kernel_launches": (C.c_int64, []),
     "ddst_autotune": (C.c_int, [C.c_int, C.POINTER(ddst_grid), C.POINTER(ddst_coeffs),
-                                C.POINTER(C.c_int), _PP, _PP, C.c_double, C.POINTER(ddst_options),
-                                _P, C.POINTER(ddst_tune_report)]),
+                                C.POINTER(C.c_int), _PP, _PP, C.c_double, C.c_int,
+                                C.POINTER(ddst_options), _P, C.POINTER(ddst_tune_report)]),
     "ddst_autotune_key": (C.c_int, [C.c_int, C.POINTER(ddst_grid), C.POINTER(ddst_coeffs),
                                     C.POINTER(C.c_int), C.c_int, C.c_char_p, C.c_size_t]),
     "ddst_autotune_lookup": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(ddst_options),

@@ -1480,7 +1480,7 @@ void ddst_options_default(ddst_options* opt) {
   opt->explicit_S = -1;
   opt->recompute_factors = 0;
   opt->autotune_cache = nullptr;
-  opt->interface_solver = 0;
+  opt->interface_solver = -1;
 }
 
 ddst_status ddst_setup(const ddst_grid* grid, const ddst_coeffs* coeffs, int slab_width,
@@ -1506,6 +1506,7 @@ ddst_status ddst_get_options(const ddst_ctx* ctx, ddst_options* opt) {
   opt->precision = ctx->tf32 ? DDST_MIXED_TF32 : ctx->prec;
   if (opt->tensor_cores < 0) opt->tensor_cores = 1;
   if (opt->check_every == 0) opt->check_every = ctx->mf_any ? 1 : 8;
+  if (opt->interface_solver < 0) opt->interface_solver = 0;
   opt->autotune_cache = nullptr;  // read during setup only
   return DDST_OK;
 }

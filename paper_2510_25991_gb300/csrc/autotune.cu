@@ -65,15 +65,15 @@ std::string format_knobs(const ddst_options& o) {
   char buf[256];
   snprintf(buf, sizeof(buf),
            "precision=%d tensor_cores=%d explicit_S=%d gmres_tol=%.17g check_every=%d "
-           "factor_chunks=%d",
+           "factor_chunks=%d interface_solver=%d",
            o.precision, o.tensor_cores, o.explicit_S, o.gmres_tol, o.check_every,
-           o.factor_chunks);
+           o.factor_chunks, o.interface_solver);
   return buf;
 }
 
 struct Knobs {
   int precision = DDST_MIXED, tensor_cores = 1, explicit_S = -1, check_every = 0,
-      factor_chunks = 0;
+      factor_chunks = 0, interface_solver = 0;
   double gmres_tol = 0.0;
 };
 
@@ -96,12 +96,13 @@ bool parse_knobs(const std::string& s, Knobs* k) {
       else if (name == "explicit_S") k->explicit_S = (int)v;
       else if (name == "check_every") k->check_every = (int)v;
       else if (name == "factor_chunks") k->factor_chunks = (int)v;
+      else if (name == "interface_solver") k->interface_solver = (int)v;
       else continue;  // a knob of a later version: ignored
     }
     if (!end || *end != '\0') return false;
     ++seen;
   }
-  return seen == 6 && (k->precision == DDST_FP64 || k->precision == DDST_MIXED ||
+  return seen == 7 && (k->precision == DDST_FP64 || k->precision == DDST_MIXED ||
                        k->precision == DDST_MIXED_TF32);
 }
 
@@ -113,6 +114,7 @@ void apply_knobs(const Knobs& k, ddst_options* o) {
   if (!(o->gmres_tol > 0.0)) o->gmres_tol = k.gmres_tol;
   if (o->check_every == 0) o->check_every = k.check_every;
   if (o->factor_chunks == 0) o->factor_chunks = k.factor_chunks;
+  if (o->interface_solver < 0) o->interface_solver = k.interface_solver;
 }
 
 bool read_lines(const char* path, std::vector<std::string>* lines) {
@@ -130,10 +132,12 @@ struct Eval {
   bool matfree_only = false;
 };
 
-// One candidate: setup, transfer build, compression, two solves; cost in event milliseconds.
+// One candidate: setup, transfer build, compression, two solves.  Cost in event milliseconds:
+// the setup phases, the direct interface factorization (once), and `solves` times the second
+// solve (the first also pays one-time work: graph capture, the direct factorization).
 Eval evaluate(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs, const int* widths,
               const double* const* f, const double* const* g, double* const* u,
-              double compress_tol, const ddst_options& o, void* stream) {
+              double compress_tol, int solves, const ddst_options& o, void* stream) {
   Eval r;
   ddst_ctx* ctx = nullptr;
   r.st = ddst_setup_batch(nprob, grids, coeffs, widths, &o, stream, &ctx);
@@ -144,7 +148,7 @@ Eval evaluate(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs, cons
   if (r.st == DDST_OK) r.st = ddst_solve_batch(ctx, f, g, u, &i1);
   if (r.st == DDST_OK) r.st = ddst_solve_batch(ctx, f, g, u, &i2);
   if (r.st == DDST_OK) {
-    r.ms = i2.t_factor + i2.t_transfer + i2.t_compress + std::min(i1.t_solve, i2.t_solve);
+    r.ms = i2.t_factor + i2.t_transfer + i2.t_compress + i2.t_direct + solves * i2.t_solve;
     r.rho = std::max(i1.refine_rho, i2.refine_rho);
     r.chunks = i2.factor_chunks;
   }
@@ -212,10 +216,11 @@ ddst_status ddst_autotune_store(const char* path, const char* key, const ddst_op
 
 ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
                           const int* slab_widths, const double* const* f,
-                          const double* const* g, double compress_tol, const ddst_options* base,
-                          void* stream, ddst_tune_report* rep) {
+                          const double* const* g, double compress_tol, int solves_per_setup,
+                          const ddst_options* base, void* stream, ddst_tune_report* rep) {
   if (nprob <= 0 || !grids || !coeffs || !slab_widths || !f || !g || !rep)
     return arg_error("ddst_autotune: bad problem list or NULL argument");
+  const int solves = std::max(1, solves_per_setup);
   for (int q = 0; q < nprob; ++q)
     if (!f[q] || !g[q]) return arg_error("ddst_autotune: NULL right-hand side");
   ddst_options b;
@@ -242,9 +247,11 @@ ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* 
   ddst_options cur = b;
   if (cur.precision == DDST_AUTO) cur.precision = DDST_MIXED;
   if (cur.tensor_cores < 0) cur.tensor_cores = 1;
+  if (cur.interface_solver < 0) cur.interface_solver = 0;
   auto run = [&](const ddst_options& o) {
     ++rep->candidates;
-    Eval e = evaluate(nprob, grids, coeffs, slab_widths, f, g, u.data(), compress_tol, o, stream);
+    Eval e = evaluate(nprob, grids, coeffs, slab_widths, f, g, u.data(), compress_tol, solves, o,
+                      stream);
     if (e.st != DDST_OK || !(e.rho <= kTuneRhoMax)) ++rep->rejected;
     return e;
   };
@@ -274,7 +281,13 @@ ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* 
     c.explicit_S = 0;
     consider(c);
   }
-  // 2. tensor-core precision of the local operators
+  // 2. interface solver: GMRES or the block cyclic reduction (explicit operators only)
+  if (b.interface_solver < 0 && cur.explicit_S != 0) {
+    ddst_options c = cur;
+    c.interface_solver = 1;
+    consider(c);
+  }
+  // 3. tensor-core precision of the local operators
   if (mixed) {
     if (b.tensor_cores < 0) {
       ddst_options c = cur;
@@ -289,8 +302,8 @@ ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* 
       consider(c);
     }
   }
-  // 3. inner GMRES tolerance against refinement steps
-  if (!(b.gmres_tol > 0.0)) {
+  // 4. inner GMRES tolerance against refinement steps
+  if (!(b.gmres_tol > 0.0) && cur.interface_solver != 1) {
     const std::vector<double> tols = mixed ? std::vector<double>{1e-2, 1e-3, 1e-4}
                                            : std::vector<double>{1e-8, 1e-10};
     for (double t : tols) {
@@ -299,14 +312,14 @@ ddst_status ddst_autotune(int nprob, const ddst_grid* grids, const ddst_coeffs* 
       consider(c);
     }
   }
-  // 4. host convergence checks of GMRES
-  if (b.check_every == 0)
+  // 5. host convergence checks of GMRES
+  if (b.check_every == 0 && cur.interface_solver != 1)
     for (int ce : {1, 4, 16}) {
       ddst_options c = cur;
       c.check_every = ce;
       consider(c);
     }
-  // 5. warm-started chunks of the pivot sweeps (around the automatic count)
+  // 6. warm-started chunks of the pivot sweeps (around the automatic count)
   if (b.factor_chunks == 0 && best.chunks > 1) {
     const int used = best.chunks;
     for (int k : {1, std::max(2, used / 2), used * 2}) {

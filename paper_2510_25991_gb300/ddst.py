@@ -271,7 +271,7 @@ def _problem_arrays(problems):
     return k, grids, coeffs, widths
 
 
-def ddst_autotune(problems, fs, gs, compress_tol=0.0, stream=None, **opts):
+def ddst_autotune(problems, fs, gs, compress_tol=0.0, solves_per_setup=1, stream=None, **opts):
     """Times the schedule knobs left automatic in ``opts`` on these problems and right-hand
     sides; returns the report as a dict (``chosen`` is an options dict).  With
     ``autotune_cache=path`` the choice is stored there for later setups."""
@@ -284,7 +284,8 @@ def ddst_autotune(problems, fs, gs, compress_tol=0.0, stream=None, **opts):
     o = ddst_options_default(**opts)
     rep = L.ddst_tune_report()
     st = lib.ddst_autotune(k, grids, coeffs, widths, _parr(fs), _parr(gs), float(compress_tol),
-                           C.byref(o), C.c_void_p(stream) if stream else None, C.byref(rep))
+                           int(solves_per_setup), C.byref(o), C.c_void_p(stream) if stream else None,
+                           C.byref(rep))
     _check(lib, None, st)
     d = {k2: getattr(rep, k2) for k2, _ in L.ddst_tune_report._fields_ if k2 != "chosen"}
     d["chosen"] = _options_dict(rep.chosen)

@@ -28,17 +28,18 @@ def test_store_then_lookup_applies_only_automatic_knobs(tmp_path):
     path = str(tmp_path / "tune.txt")
     key = D.ddst_autotune_key(_prob(), "auto")
     D.ddst_autotune_store(path, key, precision="mixed_tf32", tensor_cores=1, explicit_S=0,
-                          gmres_tol=1e-4, check_every=4, factor_chunks=3)
+                          gmres_tol=1e-4, check_every=4, factor_chunks=3, interface_solver=1)
     found, o = D.ddst_autotune_lookup(path, key, precision="auto")
     assert found
     assert (o["precision"], o["tensor_cores"], o["explicit_S"], o["gmres_tol"], o["check_every"],
-            o["factor_chunks"]) == ("mixed_tf32", 1, 0, 1e-4, 4, 3)
+            o["factor_chunks"], o["interface_solver"]) == ("mixed_tf32", 1, 0, 1e-4, 4, 3, 1)
     # knobs the caller set keep the caller's values
     found, o = D.ddst_autotune_lookup(path, key, precision="mixed", tensor_cores=0, explicit_S=1,
-                                      gmres_tol=1e-6, check_every=2, factor_chunks=1)
+                                      gmres_tol=1e-6, check_every=2, factor_chunks=1,
+                                      interface_solver=0)
     assert found
     assert (o["precision"], o["tensor_cores"], o["explicit_S"], o["gmres_tol"], o["check_every"],
-            o["factor_chunks"]) == ("mixed", 0, 1, 1e-6, 2, 1)
+            o["factor_chunks"], o["interface_solver"]) == ("mixed", 0, 1, 1e-6, 2, 1, 0)
 
 
 def test_store_replaces_its_own_line_and_keeps_others(tmp_path):
@@ -59,8 +60,10 @@ def test_missing_file_and_malformed_lines_are_not_entries(tmp_path):
     key = D.ddst_autotune_key(_prob(), "mixed")
     assert D.ddst_autotune_lookup(path, key) == (False, D.ddst_autotune_lookup(path, key)[1])
     with open(path, "w") as fh:
-        fh.write(key + "\tprecision=1 tensor_cores=x explicit_S=-1 gmres_tol=1e-3 check_every=8 factor_chunks=0\n")
-        fh.write(key + "\tprecision=9 tensor_cores=1 explicit_S=-1 gmres_tol=1e-3 check_every=8 factor_chunks=0\n")
+        fh.write(key + "\tprecision=1 tensor_cores=x explicit_S=-1 gmres_tol=1e-3 check_every=8 "
+                 "factor_chunks=0 interface_solver=0\n")
+        fh.write(key + "\tprecision=9 tensor_cores=1 explicit_S=-1 gmres_tol=1e-3 check_every=8 "
+                 "factor_chunks=0 interface_solver=0\n")
         fh.write(key + "\tgmres_tol=1e-3\n")
         fh.write("no tab here\n")
     found, o = D.ddst_autotune_lookup(path, key)

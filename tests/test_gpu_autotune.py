@@ -41,16 +41,16 @@ def test_autotune_writes_a_cache_entry_that_setup_applies(tmp_path):
     spec = _spec(p)
     rep = D.ddst_autotune(spec, dev(p["f"]), dev(p["g"]), precision="auto", autotune_cache=path)
     ch = rep["chosen"]
-    # untuned run (twice), operator kind, FMA vs tensor cores, TF32, three inner tolerances,
-    # three check intervals, up to three chunk counts
-    assert rep["candidates"] >= 11 and rep["cache_written"] == 1
+    # untuned run (twice), operator kind, direct interface solver, FMA vs tensor cores, TF32, and
+    # (GMRES kept) three inner tolerances, three check intervals; up to three chunk counts
+    assert rep["candidates"] >= 6 and rep["cache_written"] == 1
     assert 0 < rep["best_ms"] <= rep["default_ms"] and rep["best_rho"] <= 0.1
     assert ch["precision"] in ("mixed", "mixed_tf32")
     key = D.ddst_autotune_key(spec, "auto")
     assert open(path).read().startswith(key + "\t")
     sol = D.Solver(spec, precision="auto", autotune_cache=path)
     eff = D.ddst_get_options(sol.ctx)
-    for k in ("precision", "explicit_S", "check_every"):
+    for k in ("precision", "explicit_S", "check_every", "interface_solver"):
         assert eff[k] == ch[k], k
     if ch["gmres_tol"] > 0:
         assert eff["gmres_tol"] == ch["gmres_tol"]
@@ -64,12 +64,14 @@ def test_autotune_writes_a_cache_entry_that_setup_applies(tmp_path):
 
 def test_autotune_with_compression_keeps_explicit_operators_and_set_knobs():
     """compress_tol > 0 needs the explicit operators, so explicit_S is not tuned; knobs the
-    caller set (gmres_tol here) are not tuned either."""
+    caller set (gmres_tol and the interface solver here) are not tuned either."""
     from paper_2510_25991_gb300 import ddst as D
     p = I.make_problem("convdiff2d", n=128, w=16)
-    rep = D.ddst_autotune(_spec(p), dev(p["f"]), dev(p["g"]), compress_tol=1e-6, gmres_tol=1e-4)
+    rep = D.ddst_autotune(_spec(p), dev(p["f"]), dev(p["g"]), compress_tol=1e-6, gmres_tol=1e-4,
+                          interface_solver=0)
     ch = rep["chosen"]
     assert ch["explicit_S"] == -1 and ch["gmres_tol"] == 1e-4 and ch["precision"] == "mixed"
+    assert ch["interface_solver"] == 0
     assert rep["cache_written"] == 0 and rep["best_rho"] <= 0.1
     sol = D.Solver(_spec(p), **{k: v for k, v in ch.items() if k != "autotune_cache"})
     sol.build_transfer()

@@ -122,3 +122,27 @@ def test_direct_solver_needs_explicit_operators():
         sol.solve(dev(p["f"]), dev(p["g"]), u)
     sol.close()
     assert e.value.name == "NOT_IMPLEMENTED"
+
+
+def test_direct_fp64_solves_the_indefinite_case_where_gmres_stalls():
+    """Helmholtz at 512^2, kappa = 100, 63 double slabs of 2w = 16 cells: unrestarted GMRES on
+    (I - K) does not converge there even in the FP64 oracle (relative residual 1e-2 after 1500
+    iterations), while the system itself is well posed.  The FP64 block cyclic reduction solves
+    it to the global solve's accuracy.  In mixed precision the FP32 reduction of this indefinite
+    system is not an approximate inverse (the refinement's corrections grow), which the solve
+    reports as NOT_CONVERGED."""
+    from paper_2510_25991_gb300 import ddst as D
+    p = I.make_problem("helmholtz2d", n=512, w=8, kappa=100.0)
+    A, b = O.assemble(p)
+    uref = O.global_solve(A, b)
+    sol = D.Solver(_spec(p), precision="fp64", interface_solver=1)
+    sol.build_transfer()
+    u = torch.empty((511, 511), dtype=torch.float64, device="cuda")
+    st, info = sol.solve(dev(p["f"]), dev(p["g"]), u)
+    sol.close()
+    assert _relerr(u.cpu().numpy().ravel(), uref) <= 1e-10, info
+    sol = D.Solver(_spec(p), precision="mixed", interface_solver=1, refine_max=6)
+    sol.build_transfer()
+    st, info = sol.solve(dev(p["f"]), dev(p["g"]), u, raise_on_error=False)
+    sol.close()
+    assert D.L.STATUS_NAMES[st] == "NOT_CONVERGED" and info["refine_rho"] > 1.0, info
