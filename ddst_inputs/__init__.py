@@ -175,3 +175,27 @@ def batch_problem(spec: dict) -> dict:
     f = uniform_load(2, n, seed * 10 + 0)
     g = quadratic_boundary(2, n)
     return dict(name=f"batch{seed}", dim=2, n=n, w=w, a=a, b=(0.0, 0.0), c=None, f=f, g=g)
+
+
+def march_problem(dim: int = 2, n: int = 128, w: int = 16, dt: float = 6.94e-3) -> dict:
+    """Inputs of the time-marching workload (the convection-diffusion example of Sec. 6,
+    Example 1, on the unit square or cube with Dirichlet sides): diffusion
+    ``D = D0 (1 + eps (s_y (2y - 1) + s_x cos(2 pi x)))`` with ``D0 = 0.1, eps = 0.3, s_y = 1,
+    s_x = 0.5``, velocity ``v = (-2 y (1 - y), 0[, 0])``, time step ``dt`` (the example's
+    6.94e-3) and a smooth bump as initial state (Gaussian of width 0.1 at the centre, scaled to
+    vanish on the boundary).  Returns the problem dict (``a = D``, ``b = 0``, ``c = 1/dt``, ``f``
+    and ``g`` zero) plus ``vel`` (``dim`` nodal arrays), ``u0`` (interior) and ``dt``."""
+    x = np.linspace(0.0, 1.0, n + 1)
+    grids = np.meshgrid(*([x] * dim), indexing="ij")
+    X, Y = grids[0], grids[1]
+    D = 0.1 * (1.0 + 0.3 * ((2.0 * Y - 1.0) + 0.5 * np.cos(2.0 * np.pi * X)))
+    vel = [-2.0 * Y * (1.0 - Y)] + [np.zeros_like(X) for _ in range(dim - 1)]
+    r2 = sum((G - 0.5) ** 2 for G in grids)
+    cut = np.ones_like(X)
+    for G in grids:
+        cut = cut * (4.0 * G * (1.0 - G))
+    bump = np.exp(-r2 / (2.0 * 0.1 ** 2)) * cut
+    inner = tuple(slice(1, n) for _ in range(dim))
+    return dict(name=f"march{dim}d", dim=dim, n=n, w=w, a=D, b=(0.0,) * dim,
+                c=np.full((n + 1,) * dim, 1.0 / dt), f=np.zeros((n - 1,) * dim),
+                g=np.zeros((n + 1,) * dim), vel=vel, u0=bump[inner].copy(), dt=dt)

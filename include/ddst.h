@@ -235,6 +235,21 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,
                        ddst_info* info);
 
+/* IMEX backward-Euler time marching (Sec. 6, Example 1, Eq. (convdiff)) on a context set up
+ * for the screened operator -div(a grad u) + c u with reaction c = 1/dt (and no convection b):
+ * each of nsteps steps solves it for f = U_n / dt - v . grad_h U_n (central differences at the
+ * interior nodes, U_n = 0 on the boundary) with zero Dirichlet data, so the factors, transfer
+ * operators and (interface_solver = 1) factored equilibrium system are reused by every step.
+ * The refinement of step n + 1 starts from U_n.  Arrays per problem (nprob pointers each):
+ * vel[q] holds dim nodal velocity components, component d at offset d (n+1)^dim; u0[q] the
+ * interior initial state; u[q] receives U_nsteps.  info sums GMRES iterations and refinement
+ * steps over the steps (est_rel_error, rel_residual and refine_rho: the worst step); t_solve is
+ * the whole march.  The paper's example has Neumann and periodic sides; this driver keeps the
+ * library's Dirichlet boundary.  Errors: INVALID_ARG (nsteps < 0, dt <= 0, NULL), STATE,
+ * NOT_CONVERGED (the march stops at the step that missed refine_tol; u holds that step). */
+ddst_status ddst_march(ddst_ctx* ctx, int nsteps, double dt, const double* const* vel,
+                       const double* const* u0, double* const* u, ddst_info* info);
+
 /* Batched form: f, g, u are arrays of nprob pointers (one per problem). */
 ddst_status ddst_solve_batch(ddst_ctx* ctx, const double* const* f, const double* const* g,
                              double* const* u, ddst_info* info);

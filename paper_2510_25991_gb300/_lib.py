@@ -73,6 +73,7 @@ SIGNATURES = {
     "ddst_compress": (C.c_int, [_P, C.c_double]),
     "ddst_solve": (C.c_int, [_P, _P, _P, _P, C.POINTER(ddst_info)]),
     "ddst_solve_batch": (C.c_int, [_P, _PP, _PP, _PP, C.POINTER(ddst_info)]),
+    "ddst_march": (C.c_int, [_P, C.c_int, C.c_double, _PP, _PP, _PP, C.POINTER(ddst_info)]),
     "ddst_solve_adjoint": (C.c_int, [_P, _P, _P, _P, _P, C.POINTER(ddst_info)]),
     "ddst_solve_adjoint_batch": (C.c_int, [_P, _PP, _PP, _PP, _PP, C.POINTER(ddst_info)]),
     "ddst_interface_trace": (C.c_int, [_P, C.c_int, _P]),

@@ -137,6 +137,7 @@ struct ddst_ctx {
   int n_mf_ids = 0;
   void *mf_b = nullptr, *mf_z = nullptr, *mf_z2 = nullptr, *mf_x = nullptr;
   double* if_kx = nullptr;
+  double* d_vel = nullptr;               // marching: nodal velocity components of every problem
   long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
   bool solve_bufs_ready = false;
   // direct interface solver (interface_solver = 1): block cyclic reduction of every problem's
@@ -1210,6 +1211,80 @@ double vec_norm(ddst_ctx* ctx, const double* x, int64_t n, int slot) {
   return std::sqrt(host_scalar(ctx, ctx->scal + slot));
 }
 
+// Result of one forward solve on the device-resident d_f, d_g (solution in d_u).
+struct SolveStats {
+  int total_it = 0, first_it = 0, nref = 0;
+  double est = 0.0, relres = 0.0, rho = 0.0;
+  ddst_status result = DDST_OK;
+};
+
+// The forward solve on the staged data: right-hand side b(f, g), DD solve, FP64 refinement
+// until every problem's error bound is below refine_tol (Alg. 2, Eq. (equilib1), Eq. (modelS)).
+// x0 = 0 (warm = false) or the current d_u (warm = true: the refinement then starts from it).
+template <typename T>
+ddst_status solve_core(ddst_ctx* ctx, bool warm, SolveStats* ss) {
+  cudaStream_t st = ctx->stream;
+  ddst_status s;
+  const int64_t N = ctx->tot_vol;
+  launch_rhs(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_f, ctx->d_g, ctx->d_b, st);
+  if (!warm) CK(cudaMemsetAsync(ctx->d_u, 0, sizeof(double) * N, st));
+  const double bnorm = vec_norm(ctx, ctx->d_b, N, 3);
+  const double tol = ctx->opt.gmres_tol;
+  std::vector<std::vector<double>> dnorm;
+  const int rmax = std::max(0, ctx->opt.refine_max);
+  for (int it = 0; it <= rmax; ++it) {
+    const double* rhs = ctx->d_b;
+    if (it > 0 || warm) {
+      launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
+                      nullptr, 512, st);
+      rhs = ctx->d_r;
+    }
+    int its = 0;
+    double rr = 0.0;
+    s = dd_apply<T>(ctx, rhs, ctx->d_e, &its, &rr, tol);
+    if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+    if (it == 0) ss->first_it = its;
+    ss->total_it += its;
+    ++ss->nref;
+    launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
+    ss->est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_u, dnorm, &ss->rho);
+    if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
+      if (s == DDST_ERR_NOT_CONVERGED) ss->result = s;
+      break;
+    }
+    if (ss->est <= ctx->opt.refine_tol) break;
+    if (it == rmax) ss->result = DDST_ERR_NOT_CONVERGED;
+  }
+  launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
+                  nullptr, 512, st);
+  ss->relres = bnorm > 0.0 ? vec_norm(ctx, ctx->d_r, N, 6) / bnorm : 0.0;
+  return DDST_OK;
+}
+
+void fill_info(ddst_ctx* ctx, const SolveStats& ss, float ms, ddst_info* info) {
+  if (!info) return;
+  info->gmres_iters = ss.total_it;
+  info->gmres_iters_first = ss.first_it;
+  info->refine_iters = ss.nref;
+  info->rel_residual = ss.relres;
+  info->est_rel_error = ss.est;
+  info->refine_rho = ss.rho;
+  info->t_direct = ctx->t_bcr;
+  info->t_factor = ctx->t_factor;
+  info->t_transfer = ctx->t_transfer;
+  info->t_compress = ctx->t_compress;
+  info->t_solve = ms;
+  info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems +
+                                  ctx->fac_big_elems + ctx->pack_elems) * (int64_t)ctx->esz;
+  info->bytes_transfer = ctx->matfree ? 0
+                         : ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
+  info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+  info->fail_slab = -1;
+  info->fail_block = -1;
+  info->factor_chunks = ctx->factor_chunks;
+  info->factor_check = ctx->factor_check;
+}
+
 template <typename T>
 ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* const* g,
                        double* const* u, ddst_info* info) {
@@ -1227,42 +1302,9 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
     CK(stage_in(ctx->d_g + P.node_off, g[q], P.nnode, st));
   }
   Timer tm(st);
-  const int64_t N = ctx->tot_vol;
-  launch_rhs(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_f, ctx->d_g, ctx->d_b, st);
-  CK(cudaMemsetAsync(ctx->d_u, 0, sizeof(double) * N, st));
-  const double bnorm = vec_norm(ctx, ctx->d_b, N, 3);
-  const double tol = ctx->opt.gmres_tol;
-  int total_it = 0, first_it = 0, nref = 0;
-  double est = 0.0, relres = 0.0, rho = 0.0;
-  std::vector<std::vector<double>> dnorm;
-  ddst_status result = DDST_OK;
-  const int rmax = std::max(0, ctx->opt.refine_max);
-  for (int it = 0; it <= rmax; ++it) {
-    const double* rhs = ctx->d_b;
-    if (it > 0) {
-      launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
-                      nullptr, 512, st);
-      rhs = ctx->d_r;
-    }
-    int its = 0;
-    double rr = 0.0;
-    s = dd_apply<T>(ctx, rhs, ctx->d_e, &its, &rr, tol);
-    if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
-    if (it == 0) first_it = its;
-    total_it += its;
-    ++nref;
-    launch_axpy(N, 1.0, ctx->d_e, ctx->d_u, st);
-    est = refine_batch_estimate(ctx, ctx->d_e, ctx->d_u, dnorm, &rho);
-    if (rmax == 0) {  // plain DD solve: its accuracy is the interface GMRES's
-      if (s == DDST_ERR_NOT_CONVERGED) result = s;
-      break;
-    }
-    if (est <= ctx->opt.refine_tol) break;
-    if (it == rmax) result = DDST_ERR_NOT_CONVERGED;
-  }
-  launch_residual(ctx->d_probs, ctx->nprob, ctx->d_a, ctx->d_c, ctx->d_b, ctx->d_u, ctx->d_r, 0,
-                  nullptr, 512, st);
-  relres = bnorm > 0.0 ? vec_norm(ctx, ctx->d_r, N, 6) / bnorm : 0.0;
+  SolveStats ss;
+  s = solve_core<T>(ctx, false, &ss);
+  if (s != DDST_OK) return s;
   const float ms = tm.stop();
   for (int q = 0; q < ctx->nprob; ++q) {
     const ProbDesc& P = ctx->probs[q];
@@ -1272,31 +1314,68 @@ ddst_status solve_impl(ddst_ctx* ctx, const double* const* f, const double* cons
   ddst_status ds = check_status(ctx, info);
   if (ds != DDST_OK) return ds;
   ctx->have_solution = true;
-  if (info) {
-    info->gmres_iters = total_it;
-    info->gmres_iters_first = first_it;
-    info->refine_iters = nref;
-    info->rel_residual = relres;
-    info->est_rel_error = est;
-    info->refine_rho = rho;
-    info->t_direct = ctx->t_bcr;
-    info->t_factor = ctx->t_factor;
-    info->t_transfer = ctx->t_transfer;
-    info->t_compress = ctx->t_compress;
-    info->t_solve = ms + recompute_ms;
-    info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems +
-                                    ctx->fac_big_elems + ctx->pack_elems) * (int64_t)ctx->esz;
-    info->bytes_transfer = ctx->matfree ? 0
-                           : ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
-    info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
-    info->fail_slab = -1;
-    info->fail_block = -1;
-    info->factor_chunks = ctx->factor_chunks;
-    info->factor_check = ctx->factor_check;
-  }
+  fill_info(ctx, ss, ms + recompute_ms, info);
   maybe_release_factors(ctx);
-  if (result != DDST_OK)
-    return fail(ctx, result, "refinement stopped at estimated relative error %.3e", est);
+  if (ss.result != DDST_OK)
+    return fail(ctx, ss.result, "refinement stopped at estimated relative error %.3e", ss.est);
+  return DDST_OK;
+}
+
+// IMEX backward-Euler marching (Sec. 6, Example 1, Eq. (convdiff)): every step solves the
+// context's operator (the caller sets it up with reaction c = 1/dt) for the right-hand side
+// f = U_n / dt - v . grad_h U_n (central differences, U_n = 0 on the boundary) with zero Dirichlet
+// data, reusing the factors, the transfer operators and (interface_solver = 1) the factored
+// equilibrium system.  The refinement of step n + 1 starts from U_n.
+template <typename T>
+ddst_status march_impl(ddst_ctx* ctx, int nsteps, double dt, const double* const* vel,
+                       const double* const* u0, double* const* u, ddst_info* info) {
+  cudaStream_t st = ctx->stream;
+  ddst_status s = ensure_solve_buffers(ctx);
+  if (s != DDST_OK) return s;
+  s = ensure_factors<T>(ctx);
+  if (s != DDST_OK) return s;
+  if (!ctx->d_vel) {  // component-major: component d of every problem's nodes at d tot_nodes
+    cudaError_t e = dalloc(ctx, &ctx->d_vel, sizeof(double) * 3 * ctx->tot_nodes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc velocity");
+  }
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    if (!vel[q] || !u0[q] || !u[q]) return fail(ctx, DDST_ERR_INVALID_ARG, "NULL array for problem %d", q);
+    for (int d = 0; d < P.dim; ++d)
+      CK(stage_in(ctx->d_vel + d * ctx->tot_nodes + P.node_off, vel[q] + (int64_t)d * P.nnode,
+                  P.nnode, st));
+    CK(stage_in(ctx->d_u + P.vol_off, u0[q], P.nint, st));
+  }
+  CK(cudaMemsetAsync(ctx->d_g, 0, sizeof(double) * ctx->tot_nodes, st));
+  Timer tm(st);
+  SolveStats tot;
+  for (int n = 0; n < nsteps; ++n) {
+    launch_imex_rhs(ctx->d_probs, ctx->nprob, ctx->d_u, ctx->d_vel, ctx->tot_nodes, 1.0 / dt,
+                    ctx->d_f, st);
+    SolveStats ss;
+    s = solve_core<T>(ctx, true, &ss);
+    if (s != DDST_OK) return s;
+    tot.total_it += ss.total_it;
+    tot.nref += ss.nref;
+    if (n == 0) tot.first_it = ss.first_it;
+    tot.est = std::max(tot.est, ss.est);
+    tot.rho = std::max(tot.rho, ss.rho);
+    tot.relres = std::max(tot.relres, ss.relres);
+    if (ss.result != DDST_OK) { tot.result = ss.result; break; }
+  }
+  const float ms = tm.stop();
+  for (int q = 0; q < ctx->nprob; ++q) {
+    const ProbDesc& P = ctx->probs[q];
+    CK(stage_out(u[q], ctx->d_u + P.vol_off, P.nint, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  ddst_status ds = check_status(ctx, info);
+  if (ds != DDST_OK) return ds;
+  fill_info(ctx, tot, ms, info);
+  maybe_release_factors(ctx);
+  if (tot.result != DDST_OK)
+    return fail(ctx, tot.result, "a step's refinement stopped at estimated relative error %.3e",
+                tot.est);
   return DDST_OK;
 }
 
@@ -1558,6 +1637,17 @@ ddst_status ddst_solve_batch(ddst_ctx* ctx, const double* const* f, const double
   if (info) { memset(info, 0, sizeof(*info)); info->fail_slab = info->fail_block = -1; }
   return ctx->prec == DDST_FP64 ? solve_impl<double>(ctx, f, g, u, info)
                                 : solve_impl<float>(ctx, f, g, u, info);
+}
+
+ddst_status ddst_march(ddst_ctx* ctx, int nsteps, double dt, const double* const* vel,
+                       const double* const* u0, double* const* u, ddst_info* info) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "transfer operators not built");
+  if (nsteps < 0 || !(dt > 0.0)) return fail(ctx, DDST_ERR_INVALID_ARG, "need nsteps >= 0, dt > 0");
+  if (!vel || !u0 || !u) return fail(ctx, DDST_ERR_INVALID_ARG, "NULL pointer array");
+  if (info) { memset(info, 0, sizeof(*info)); info->fail_slab = info->fail_block = -1; }
+  return ctx->prec == DDST_FP64 ? march_impl<double>(ctx, nsteps, dt, vel, u0, u, info)
+                                : march_impl<float>(ctx, nsteps, dt, vel, u0, u, info);
 }
 
 ddst_status ddst_solve(ddst_ctx* ctx, const double* f, const double* g, double* u,

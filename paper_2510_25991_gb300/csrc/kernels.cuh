@@ -52,6 +52,10 @@ void launch_dot(const double* x, const double* y, int64_t n, double* part, int n
 void launch_prob_sqnorms(const ProbDesc* d_probs, int nprob, const double* x, double* part,
                          int nblk, double* out, cudaStream_t st);
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
+// f = u / dt - v . grad_h u on every problem's interior (u = 0 on the boundary nodes); vel holds
+// component d of the nodal velocity of every problem at vel + d tot_nodes.
+void launch_imex_rhs(const ProbDesc* d_probs, int nprob, const double* u, const double* vel,
+                     int64_t tot_nodes, double inv_dt, double* f, cudaStream_t st);
 
 // One CTA of the pivot sweeps (factor.cu): rows start..last of one slab and direction, inverses
 // stored from `first` on, warm-up inverse of row first-1 (first+1 backward) into check slot chk.

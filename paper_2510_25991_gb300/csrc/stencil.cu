@@ -367,6 +367,39 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
   }
 }
 
+// IMEX right-hand side of one backward-Euler step (Sec. 6, Example 1, Eq. (convdiff)):
+// f = u / dt - v . grad_h u at every interior node, central differences, u = 0 on boundary
+// nodes.  vel: component d of every problem's nodal velocity at vel + d tot_nodes.
+// grid = (chunks, problems).
+__global__ void k_imex_rhs(const ProbDesc* __restrict__ probs, const double* __restrict__ u,
+                           const double* __restrict__ vel, int64_t tot_nodes, double inv_dt,
+                           double* __restrict__ f) {
+  const ProbDesc P = probs[blockIdx.y];
+  const int nb = P.n - 1, nn = P.n + 1;
+  const double inv2h = 0.5 * P.n;
+  const double* U = u + P.vol_off;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.nint;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int c[3] = {0, 0, 0};  // 1-based interior coordinates, x slowest
+    int64_t r = e, node = 0, sint = 1;
+    int64_t s_int[3];
+    for (int d = P.dim - 1; d >= 0; --d) {
+      c[d] = (int)(r % nb) + 1;
+      r /= nb;
+      s_int[d] = sint;
+      sint *= nb;
+    }
+    for (int d = 0; d < P.dim; ++d) node = node * nn + c[d];
+    double val = U[e] * inv_dt;
+    for (int d = 0; d < P.dim; ++d) {
+      const double up = c[d] < nb ? U[e + s_int[d]] : 0.0;
+      const double dn = c[d] > 1 ? U[e - s_int[d]] : 0.0;
+      val -= vel[d * tot_nodes + P.node_off + node] * (up - dn) * inv2h;
+    }
+    f[P.vol_off + e] = val;
+  }
+}
+
 // y = a*x + y  (FP64)
 __global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -467,6 +500,12 @@ void launch_prob_sqnorms(const ProbDesc* d_probs, int nprob, const double* x, do
   k_prob_sqnorm_partial<<<dim3(nblk, nprob), 256, 0, st>>>(d_probs, x, part);
   note_launch();
   k_sum_partials<<<nprob, 256, 0, st>>>(part, nblk, out);
+}
+
+void launch_imex_rhs(const ProbDesc* d_probs, int nprob, const double* u, const double* vel,
+                     int64_t tot_nodes, double inv_dt, double* f, cudaStream_t st) {
+  note_launch();
+  k_imex_rhs<<<dim3(256, nprob), 256, 0, st>>>(d_probs, u, vel, tot_nodes, inv_dt, f);
 }
 
 void launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st) {

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
-           "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch",
+           "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch", "ddst_march",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
            "ddst_time_apply", "ddst_get_options", "ddst_solve_interface",
@@ -162,6 +162,18 @@ def ddst_solve_batch(ctx, fs, gs, us, raise_on_error=True):
     lib = L.load()
     info = L.ddst_info()
     st = lib.ddst_solve_batch(ctx, _parr(fs), _parr(gs), _parr(us), C.byref(info))
+    if raise_on_error:
+        _check(lib, ctx, st)
+    return st, info.as_dict()
+
+
+def ddst_march(ctx, nsteps, dt, vels, u0s, us, raise_on_error=True):
+    """IMEX backward-Euler marching: ``vels[q]`` (dim, (n+1)^dim) nodal velocity, ``u0s[q]`` the
+    interior initial state, ``us[q]`` receives the state after ``nsteps`` steps."""
+    lib = L.load()
+    info = L.ddst_info()
+    st = lib.ddst_march(ctx, int(nsteps), float(dt), _parr(vels), _parr(u0s), _parr(us),
+                        C.byref(info))
     if raise_on_error:
         _check(lib, ctx, st)
     return st, info.as_dict()

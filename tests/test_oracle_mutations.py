@@ -59,6 +59,10 @@ MUTATIONS = [
  ("O2c a_min dropped from the eigenvalue bound", "lam = float(np.min(prob[\"a\"])) * laplacian_lambda_min", "lam = 1.0 * laplacian_lambda_min"),
  ("O3b closed-form multiplier at the slab edge instead of the centre", "s = 1.0 / (2.0 * np.cosh(w * theta))", "s = 1.0 / (2.0 * np.cosh(2 * w * theta))"),
  ("O7 dL/da boundary u_q from 0 instead of g", "u_full = np.array(g, dtype=np.float64).copy()", "u_full = np.zeros_like(np.array(g, dtype=np.float64))"),
+ ("O8 central difference without the 1/2", "U[_shifted(dim, n, d, -1)]) / (2.0 * h)", "U[_shifted(dim, n, d, -1)]) / h"),
+ ("O8 convection term added", "f = f - np.asarray(vel[d])[_interior(dim, n)] * grad", "f = f + np.asarray(vel[d])[_interior(dim, n)] * grad"),
+ ("O8 U_n / dt dropped", "f = U[_interior(dim, n)] / dt", "f = U[_interior(dim, n)] * 1.0"),
+ ("O8 one step fewer", "    for _ in range(nsteps):\n        u = lu.solve(imex_rhs(dim, n, u, vel, dt))", "    for _ in range(nsteps - 1):\n        u = lu.solve(imex_rhs(dim, n, u, vel, dt))"),
 ]
 
 

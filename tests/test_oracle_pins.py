@@ -554,3 +554,57 @@ def test_o3b_poisson_transfer_closed_form_matches_local_solves(dim, n, w):
         for S in (Sp[j], Sn[j]):
             if S is not None:
                 assert np.abs(S @ x - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 16, (2, 3)), (3, 8, (1, 2, 1))])
+def test_o8_eigenmode_decays_by_the_backward_euler_factor(dim, n, k):
+    """O8 with D = 1, no convection and c = 1/dt: a product of sines is an eigenvector of the
+    discrete Laplacian with eigenvalue lam = (4/h^2) sum_d sin^2(pi k_d h / 2), so each backward
+    Euler step divides it by 1 + dt lam exactly (up to rounding)."""
+    dt, nsteps = 2e-3, 5
+    h = 1.0 / n
+    x = np.arange(1, n) * h
+    mode = np.ones((n - 1,) * dim)
+    for d in range(dim):
+        shape = [1] * dim
+        shape[d] = n - 1
+        mode = mode * np.sin(np.pi * k[d] * x).reshape(shape)
+    lam = 4.0 / h ** 2 * sum(np.sin(np.pi * kd * h / 2.0) ** 2 for kd in k)
+    prob = dict(dim=dim, n=n, w=n // 2, a=np.ones((n + 1,) * dim), b=(0.0,) * dim,
+                c=np.full((n + 1,) * dim, 1.0 / dt))
+    vel = [np.zeros((n + 1,) * dim)] * dim
+    u = O.imex_march(prob, mode.ravel(), vel, dt, nsteps)
+    ref = mode.ravel() / (1.0 + dt * lam) ** nsteps
+    assert np.abs(u - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_o8_convection_term_exact_on_quadratics():
+    """Central differences are exact on a function quadratic along each axis, so for
+    U = x(1-x) y(1-y) (zero on the boundary) and arbitrary nodal velocities the right-hand side
+    equals U/dt - v_x dU/dx - v_y dU/dy at every interior node (up to rounding)."""
+    n, dt = 12, 0.05
+    x = np.linspace(0.0, 1.0, n + 1)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    U = X * (1 - X) * Y * (1 - Y)
+    rng = np.random.default_rng(4)
+    vel = [rng.standard_normal((n + 1, n + 1)), rng.standard_normal((n + 1, n + 1))]
+    f = O.imex_rhs(2, n, U[1:n, 1:n].ravel(), vel, dt)
+    Ux = (1 - 2 * X) * Y * (1 - Y)
+    Uy = X * (1 - X) * (1 - 2 * Y)
+    ref = (U / dt - vel[0] * Ux - vel[1] * Uy)[1:n, 1:n].ravel()
+    assert np.abs(f - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_o8_march_is_the_sequence_of_global_solves():
+    """O8 against O1 + O2 step by step on the workload's inputs (a variable D and the shear
+    velocity): every step is the global solve of the screened operator for O8's right-hand
+    side, and the bump is damped and carried along -x."""
+    p = I.march_problem(2, 24, 6)
+    u = p["u0"].ravel()
+    for _ in range(3):
+        q = dict(p, f=O.imex_rhs(2, 24, u, p["vel"], p["dt"]).reshape(23, 23))
+        A, b = O.assemble(q)
+        u = O.global_solve(A, b)
+    um = O.imex_march(p, p["u0"], p["vel"], p["dt"], 3)
+    assert np.abs(um - u).max() <= 1e-12 * np.abs(u).max()
+    assert np.linalg.norm(um) < np.linalg.norm(p["u0"])
