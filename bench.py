@@ -421,20 +421,26 @@ def bench_march(n=1024, w=32, steps=144):
     return out
 
 
-def bench_c5(steps=2, warmup=1):
+def bench_c5(steps=2, warmup=1, rank=0, ws=1):
     """The adjoint batch: 64 independent 2D problems -div(a grad u) = f with grids uneven in
     256^2 .. 1024^2 and 8, 16 or 32 slabs (slab widths 8 .. 128 cells), loss 1/2 ||u - u_obs||^2,
     gradients with respect to a, f and g.  A step is one batched setup (every problem's local
     factors; problems with blocks above 128 on the large-block kernels), transfer operators
     (explicit for the single-CTA classes, matrix-free for the others), the batched forward solve
     and the batched adjoint; the metric is seconds per adjoint gradient (step time / 64).  Inputs
-    resident on the device; the end-to-end leg passes host arrays through the C ABI instead."""
+    resident on the device; the end-to-end leg passes host arrays through the C ABI instead.
+    Under torchrun the 64 problems are sharded over the ranks by ddst_partition (by unknowns; no
+    data-path collective) and the step time is the slowest rank's."""
     import numpy as np
     import torch
 
     import ddst_inputs as I
     from paper_2510_25991_gb300 import ddst as D
     specs = I.batch_specs(64)
+    ntotal = len(specs)
+    if ws > 1:
+        owner, _ = D.ddst_partition([(s_["n"] - 1) ** 2 for s_ in specs], ws)
+        specs = [s_ for s_, r in zip(specs, owner) if r == rank]
     probs = [I.batch_problem(s_) for s_ in specs]
     nprob = len(probs)
     devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -477,6 +483,11 @@ def bench_c5(steps=2, warmup=1):
         if it >= warmup:
             ts.append(e0.elapsed_time(e1))
     ms = statistics.mean(ts)
+    if ws > 1:  # the slowest rank sets the step time
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
     # end to end: pinned host arrays through the C ABI (the library stages them in and out)
     pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
     hb = []
@@ -495,12 +506,13 @@ def bench_c5(steps=2, warmup=1):
     # the median problem, whose oracle gradient the cpu_baseline leg times on the host cores
     order = np.argsort([p["n"] for p in probs], kind="stable")
     pm = probs[order[nprob // 2]]
-    return {"workload": f"adjoint batch: {nprob} problems -div(a grad u) = f, grids 256^2..1024^2 "
+    return {"workload": f"adjoint batch: {ntotal} problems -div(a grad u) = f, grids 256^2..1024^2 "
                         "(n = 64 m, m ~ U{4..16}), 8/16/32 slabs, loss 1/2 ||u - u_obs||^2, "
                         "gradients wrt a, f, g; mixed precision",
-            "dof_total": dof, "problems": nprob,
+            "dof_total": dof, "problems": nprob, "ranks": ws,
+            "sharding": "ddst_partition by unknowns, no data-path collective" if ws > 1 else None,
             "large_block_problems": sum(1 for p in probs if 2 * p["w"] - 1 > 128),
-            "s_per_adjoint_gradient": ms / 1e3 / nprob, "ms_per_step": ms, "steps": steps,
+            "s_per_adjoint_gradient": ms / 1e3 / ntotal, "ms_per_step": ms, "steps": steps,
             "warmup": warmup, "gmres_iters_adjoint": info["gmres_iters"],
             "e2e": {"s_per_adjoint_gradient": e2e_s / nprob, "unit": "s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}}, pm
@@ -757,8 +769,10 @@ def main():
     if rank == 0 and not args.no_c4:
         line["c4"], c4_sol = bench_c4(peaks, src, steps=args.c4_steps, warmup=args.c4_warmup,
                                       n=args.c4_n, w=args.c4_w)
-    if rank == 0 and not args.no_c5:
-        line["c5"], c5_prob = bench_c5()
+    if not args.no_c5:  # every rank runs its shard of the batch under torchrun
+        c5, c5_prob = bench_c5(rank=rank, ws=ws)
+        if rank == 0:
+            line["c5"] = c5
     if rank == 0 and ws == 1 and not args.no_cpu:
         leg = cpu_leg(prob, u_mixed, verify=not args.no_verify, c4=c4_sol, c5_prob=c5_prob,
                       ref_n=args.ref_n or 512)

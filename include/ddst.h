@@ -343,6 +343,14 @@ int64_t ddst_kernel_launches(void);
 ddst_status ddst_solve_interface(ddst_ctx* ctx, int prob, const double* rhs, double* x,
                                  int transpose);
 
+/* Sharding of independent problems over ranks (one process per GPU, no data-path collective):
+ * item i (cost[i] >= 0, e.g. its unknowns) goes to rank owner[i] in [0, world), by longest
+ * processing time first (items by decreasing cost, each to the least-loaded rank; ties by
+ * index and rank), so every rank computes the same assignment without communication.  load
+ * (optional, world values) receives each rank's summed cost.  Host only; no GPU needed.
+ * Errors: INVALID_ARG. */
+ddst_status ddst_partition(int nitems, const double* cost, int world, int* owner, double* load);
+
 /* ---- Autotuner --------------------------------------------------------------------------
  * The method leaves its schedule to the implementation: how the pivot sweeps are split, the
  * tensor-core precision, whether S is formed or applied through local solves, and how the

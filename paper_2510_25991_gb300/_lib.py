@@ -96,6 +96,8 @@ SIGNATURES = {
                                        C.POINTER(C.c_int)]),
     "ddst_autotune_store": (C.c_int, [C.c_char_p, C.c_char_p, C.POINTER(ddst_options)]),
     "ddst_get_options": (C.c_int, [_P, C.POINTER(ddst_options)]),
+    "ddst_partition": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
+                                 C.POINTER(C.c_double)]),
     "ddst_last_error": (C.c_char_p, [_P]),
     "ddst_destroy": (None, [_P]),
 }

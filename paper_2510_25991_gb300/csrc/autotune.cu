@@ -160,6 +160,31 @@ Eval evaluate(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs, cons
 
 extern "C" {
 
+ddst_status ddst_partition(int nitems, const double* cost, int world, int* owner,
+                           double* load) {
+  if (nitems < 0 || world <= 0 || (nitems > 0 && (!cost || !owner)))
+    return arg_error("ddst_partition: bad sizes or NULL argument");
+  for (int i = 0; i < nitems; ++i)
+    if (!(cost[i] >= 0.0)) return arg_error("ddst_partition: costs must be >= 0");
+  // longest processing time first: items by decreasing cost (ties by index), each to the rank
+  // with the least load so far (ties by rank)
+  std::vector<int> order(nitems);
+  for (int i = 0; i < nitems; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<double> ld(world, 0.0);
+  for (int i : order) {
+    int r = 0;
+    for (int k = 1; k < world; ++k)
+      if (ld[k] < ld[r]) r = k;
+    owner[i] = r;
+    ld[r] += cost[i];
+  }
+  if (load)
+    for (int k = 0; k < world; ++k) load[k] = ld[k];
+  return DDST_OK;
+}
+
 ddst_status ddst_autotune_key(int nprob, const ddst_grid* grids, const ddst_coeffs* coeffs,
                               const int* slab_widths, int precision, char* buf, size_t len) {
   if (nprob <= 0 || !grids || !coeffs || !slab_widths || !buf)

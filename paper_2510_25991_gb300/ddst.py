@@ -18,6 +18,7 @@ __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch"
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
            "ddst_time_apply", "ddst_get_options", "ddst_solve_interface",
            "ddst_autotune", "ddst_autotune_key", "ddst_autotune_lookup", "ddst_autotune_store",
+           "ddst_partition",
            "ddst_residual_noalloc",
            "ddst_kernel_launches",
            "ddst_last_error",
@@ -329,6 +330,18 @@ def ddst_autotune_store(path, key, **opts):
     lib = L.load()
     o = ddst_options_default(**opts)
     _check(lib, None, lib.ddst_autotune_store(os.fsencode(path), key.encode(), C.byref(o)))
+
+
+def ddst_partition(costs, world):
+    """(owner per item, load per rank): the library's deterministic sharding of independent
+    items over ``world`` ranks."""
+    lib = L.load()
+    k = len(costs)
+    cost = (C.c_double * max(k, 1))(*[float(c) for c in costs])
+    owner = (C.c_int * max(k, 1))()
+    load = (C.c_double * world)()
+    _check(lib, None, lib.ddst_partition(k, cost, int(world), owner, load))
+    return [owner[i] for i in range(k)], [load[r] for r in range(world)]
 
 
 def ddst_kernel_launches():
