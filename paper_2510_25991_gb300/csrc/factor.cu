@@ -20,34 +20,40 @@
 
 namespace ddst {
 
-// Entry (r, c) of the diagonal block D_k from the stencil pack held in shared memory
-// (cxr/tr, cxc/tc: x offset and z index of row r and column c, precomputed by the caller).
+// X (shared, leading dimension LD) += D_k: the diagonal and the x / z couplings of row r sit in
+// the stencil pack pk at p and 1 entries off the diagonal (x and z neighbours of the node), one
+// thread per row instead of a lookup per entry of the block.
 template <typename T>
-__device__ __forceinline__ T dblock(const T* __restrict__ pk, int M, int m, int r, int c, int cxr,
-                                    int tr, int cxc, int tc) {
-  if (r == c) return pk[PK_DIAG * M + r];
-  if (r >= m || c >= m) return T(0);
-  if (tr == tc) {
-    if (cxc == cxr - 1) return pk[PK_WEST * M + r];
-    if (cxc == cxr + 1) return pk[PK_EAST * M + r];
+__device__ __forceinline__ void add_dblock(T* __restrict__ X, int LD, const T* __restrict__ pk,
+                                           int M, int m, int p) {
+  for (int r = threadIdx.x; r < M; r += blockDim.x) {
+    T* row = X + r * LD;
+    row[r] += pk[PK_DIAG * M + r];
+    if (r >= m) continue;
+    const int cx = r / p, t = r - cx * p;
+    if (cx >= 1) row[r - p] += pk[PK_WEST * M + r];
+    if (r + p < m) row[r + p] += pk[PK_EAST * M + r];
+    if (t >= 1) row[r - 1] += pk[PK_ZLO * M + r];
+    if (t + 1 < p) row[r + 1] += pk[PK_ZHI * M + r];
   }
-  if (cxr == cxc) {
-    if (tc == tr - 1) return pk[PK_ZLO * M + r];
-    if (tc == tr + 1) return pk[PK_ZHI * M + r];
-  }
-  return T(0);
 }
 
-// Writes X (shared, LD) as a row-major M x M block to `dst` and, if dstT, its transpose.
+// Writes X (shared, LD) as a row-major M x M block to `dst` (4 consecutive entries per thread)
+// and, if dstT, its transpose.
 template <typename T, int M>
 __device__ __forceinline__ void store_block(const T* __restrict__ X, T* __restrict__ dst,
                                             T* __restrict__ dstT) {
   constexpr int LD = BGJ<T, M>::LD;
-  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-    const int i = e / M, j = e - i * M;
-    dst[e] = X[i * LD + j];
-    if (dstT) dstT[e] = X[j * LD + i];
+  for (int e = threadIdx.x; e < M * (M / 4); e += blockDim.x) {
+    const int i = e / (M / 4), j = 4 * (e - i * (M / 4));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) dst[i * M + j + u] = X[i * LD + j + u];
   }
+  if (dstT)
+    for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+      const int i = e / M, j = e - i * M;
+      dstT[e] = X[j * LD + i];
+    }
 }
 
 // One chunk of a forward (dir 0) or backward (dir 1) pivot sweep.  Rows are visited from
@@ -130,11 +136,10 @@ __global__ void __launch_bounds__(FactorOcc<T>::threads, FactorOcc<T>::min_block
     // Sigma_k = D_k - diag(ell_k) F_{k-1} diag(ups_{k-1})   (backward: ups_k, B_{k+1}, ell_{k+1})
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
       const int r = e / M, c = e - r * M;
-      const int cxr = r / s.p, tr = r - cxr * s.p, cxc = c / s.p, tc = c - cxc * s.p;
-      T d = dblock<T>(cur, M, s.m, r, c, cxr, tr, cxc, tc);
-      if (step > 0) d -= cur[rowfield * M + r] * X[r * LD + c] * prv[colfield * M + c];
-      X[r * LD + c] = d;
+      X[r * LD + c] = step > 0 ? -(cur[rowfield * M + r] * X[r * LD + c] * prv[colfield * M + c]) : T(0);
     }
+    __syncthreads();
+    add_dblock<T>(X, LD, cur, M, s.m, s.p);
     __syncthreads();
     bgj_invert<T, M>(X, Cp, Rp, thr, st, sid, k);
     if ((k - ch.first) * sgn >= 0) {
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(FactorOcc<T>::threads, FactorOcc<T>::min_block
                                  ? reinterpret_cast<const float*>(pack) + s.pack_off +
                                        (int64_t)(kn - 1) * PK_NFIELDS * M + rowfield * M
                                  : nullptr;
-          store_umma_split_T(reinterpret_cast<const float*>(X), LD, M, scl,
+          store_umma_split_T<M>(reinterpret_cast<const float*>(X), LD, scl,
                              Uhi + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M,
                              Ulo + (dir == 0 ? 0 : umma_half) + s.fac_off + (int64_t)(k - 1) * M * M);
         }
@@ -237,12 +242,13 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
   const T* Bn = B + s.fac_off + (int64_t)k * M * M;        // B_{k+1}
   for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
     const int r = e / M, c = e - r * M;
-    const int cxr = r / s.p, tr = r - cxr * s.p, cxc = c / s.p, tc = c - cxc * s.p;
-    T v = dblock<T>(pk, M, s.m, r, c, cxr, tr, cxc, tc);
+    T v = T(0);
     if (k > 1) v -= pk[PK_SOUTH * M + r] * Fp[e] * up[c];
     if (k < s.nb) v -= pk[PK_NORTH * M + r] * Bn[e] * ln[c];
     X[r * LD + c] = v;
   }
+  __syncthreads();
+  add_dblock<T>(X, LD, pk, M, s.m, s.p);
   __syncthreads();
   bgj_invert<T, M>(X, Cp, Rp, thr, st, sid, k);
   store_block<T, M>(X, Gout + s.fac_off + (int64_t)(k - 1) * M * M, nullptr);

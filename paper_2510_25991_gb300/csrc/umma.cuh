@@ -25,18 +25,27 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Writes the TF32 hi/lo split of (-diag(scale) X)^T in the K-major operand layout: operand row
 // r, K index c holds -scale[c] * X(c, r); X is M x M row-major in shared memory with leading
-// dimension ld, scale a global vector of M values (NULL: the copy is zero).
-__device__ __forceinline__ void store_umma_split_T(const float* __restrict__ X, int ld, int M,
+// dimension ld, scale a global vector of M values (NULL: the copy is zero).  Each thread writes
+// four consecutive K entries of one row (one 16-byte store per part); consecutive threads take
+// consecutive rows, so the shared-memory reads X(c, r) are conflict-free.
+template <int M>
+__device__ __forceinline__ void store_umma_split_T(const float* __restrict__ X, int ld,
                                                    const float* __restrict__ scale,
                                                    float* __restrict__ hi,
                                                    float* __restrict__ lo) {
-  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-    const int r = e / M, c = e - r * M;
-    const float v = scale ? -scale[c] * X[c * ld + r] : 0.f;
-    const float h = tf32_rna(v);
+  for (int e = threadIdx.x; e < M * (M / 4); e += blockDim.x) {
+    const int r = e % M, c = 4 * (e / M);
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = scale ? -scale[c + u] * X[(c + u) * ld + r] : 0.f;
+    float4 h, l;
+    h.x = tf32_rna(v[0]); l.x = tf32_rna(v[0] - h.x);
+    h.y = tf32_rna(v[1]); l.y = tf32_rna(v[1] - h.y);
+    h.z = tf32_rna(v[2]); l.z = tf32_rna(v[2] - h.z);
+    h.w = tf32_rna(v[3]); l.w = tf32_rna(v[3] - h.w);
     const uint32_t o = umma_off(r, c, M) >> 2;
-    hi[o] = h;
-    lo[o] = tf32_rna(v - h);
+    *reinterpret_cast<float4*>(hi + o) = h;
+    *reinterpret_cast<float4*>(lo + o) = l;
   }
 }
 
