@@ -12,14 +12,28 @@ namespace ddst {
 // R = P^{-1} X(q, :), the column panel C = X(:, q) and the trailing update
 // X(i, j) -= C(i, :) R(:, j), X(i, q) = -C(i, :) P^{-1} run on all threads as small GEMMs.
 // Three block barriers per 16 pivots.  X has leading dimension LD = M + 4 (16-byte rows).
-// The trailing update runs over 4 x 4 patches distributed round-robin over the threads.
+// The trailing update runs over 4 x 4 patches distributed round-robin over the threads, with
+// 16-byte shared-memory loads of the column panel (kept transposed) and the row panel.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int M>
 struct BGJ {
   static constexpr int LD = M + 4;
   static constexpr int NB = 16;
-  static constexpr size_t smem_elems = (size_t)M * LD + (size_t)M * (NB + 1) + (size_t)NB * LD;
+  // column panel, stored transposed (NB rows of LD): C(i, t) at Cp[t * LD + i]
+  static constexpr size_t CP = (size_t)NB * LD;
+  static constexpr size_t smem_elems = (size_t)M * LD + CP + (size_t)NB * LD;
 };
+
+// Four consecutive elements from 16-byte-aligned shared memory.
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 
 template <typename T, int M>
 __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp,
@@ -66,10 +80,11 @@ __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp
       for (int e = 0; e < 8; ++e) P[r * LD + 8 * h + e] = v[e];
     }
     __syncthreads();
-    // (b) column panel C = X(:, q) (old values; block rows unused) and row panel R = P^{-1} X(q, :)
+    // (b) column panel C = X(:, q) (old values; block rows unused; stored transposed) and row
+    //     panel R = P^{-1} X(q, :)
     for (int e = tid; e < M * NB; e += blockDim.x) {
       const int i = e / NB, t = e - i * NB;
-      Cp[i * (NB + 1) + t] = X[i * LD + q0 + t];
+      Cp[t * LD + i] = X[i * LD + q0 + t];
     }
     for (int e = tid; e < NB * M; e += blockDim.x) {
       const int t = e / M, j = e - t * M;
@@ -103,11 +118,8 @@ __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
           T cv[4], rv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) cv[a] = Cp[(i0 + a) * (NB + 1) + t];
-          const T* src = in_j ? (X + (q0 + t) * LD + j0) : (Rp + t * LD + j0);
-#pragma unroll
-          for (int b = 0; b < 4; ++b) rv[b] = src[b];
+          ld4(Cp + t * LD + i0, cv);
+          ld4(in_j ? (X + (q0 + t) * LD + j0) : (Rp + t * LD + j0), rv);
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll

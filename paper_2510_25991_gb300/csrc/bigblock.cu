@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(512) k_big_pivot(const SlabDesc* __restrict__ 
     return;
   }
   T* Cp = Xs + BT * LD;
-  T* Rp = Cp + BT * (G::NB + 1);
+  T* Rp = Cp + G::CP;
   T* thr = Rp + G::NB * LD;
   const T* pk = pack + s.pack_off + (int64_t)(k - 1) * PK_NFIELDS * M;
   for (int e = tid; e < BT * BT; e += blockDim.x) {

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(FactorOcc<T>::threads, FactorOcc<T>::min_block
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);
   T* Cp = X + M * LD;
-  T* Rp = Cp + M * (G::NB + 1);
+  T* Rp = Cp + G::CP;
   T* pk = Rp + G::NB * LD;              // [3][PK_NFIELDS * M]: ring (previous, current, next)
   T* thr = pk + 3 * PK_NFIELDS * M;     // [M]
   uint64_t* bar = reinterpret_cast<uint64_t*>(thr + M);  // [3]
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) k_center(const SlabDesc* __restrict__ sla
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);
   T* Cp = X + M * LD;
-  T* Rp = Cp + M * (G::NB + 1);
+  T* Rp = Cp + G::CP;
   T* pk = Rp + G::NB * LD;          // [PK_NFIELDS * M]
   T* thr = pk + PK_NFIELDS * M;     // [M]
   T* up = thr + M;                  // ups_{k-1}
