@@ -86,14 +86,21 @@ __device__ __forceinline__ void bgj_invert(T* __restrict__ X, T* __restrict__ Cp
       const int i = e / NB, t = e - i * NB;
       Cp[t * LD + i] = X[i * LD + q0 + t];
     }
-    for (int e = tid; e < NB * M; e += blockDim.x) {
-      const int t = e / M, j = e - t * M;
-      T acc = T(0);
+    for (int e = tid; e < NB * (M / 4); e += blockDim.x) {  // four columns per thread
+      const int t = e / (M / 4), j = 4 * (e - t * (M / 4));
+      T acc[4] = {T(0), T(0), T(0), T(0)};
       if (j < q0 || j >= q0 + NB) {
 #pragma unroll
-        for (int s2 = 0; s2 < NB; ++s2) acc = fma(X[(q0 + t) * LD + q0 + s2], X[(q0 + s2) * LD + j], acc);
+        for (int s2 = 0; s2 < NB; ++s2) {
+          const T pv = X[(q0 + t) * LD + q0 + s2];
+          T xv[4];
+          ld4(X + (q0 + s2) * LD + j, xv);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = fma(pv, xv[u], acc[u]);
+        }
       }
-      Rp[t * LD + j] = acc;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Rp[t * LD + j + u] = acc[u];
     }
     __syncthreads();
     // (c) trailing update on 4 x 4 patches (patch index -> rows 4*pi.., columns 4*pj..)
