@@ -421,6 +421,21 @@ def bench_march(n=1024, w=32, steps=144):
     return out
 
 
+def bench_autotune(a, f, g, n, w, tol):
+    """The autotuner on the headline workload (untimed, before nothing else depends on it):
+    which knobs it tried and whether any beat the automatic choices by its 2% margin."""
+    from paper_2510_25991_gb300 import ddst as D
+    t0 = time.perf_counter()
+    rep = D.ddst_autotune(dict(dim=2, n=n, w=w, a=a, b=(20.0, 10.0, 0.0)), f, g, compress_tol=tol,
+                          precision="auto", k_max=64, oversample=10)
+    ch = rep["chosen"]
+    return {"wall_s": time.perf_counter() - t0, "candidates": rep["candidates"],
+            "rejected": rep["rejected"], "default_ms": rep["default_ms"], "best_ms": rep["best_ms"],
+            "best_rho": rep["best_rho"],
+            "chosen": {k: ch[k] for k in ("precision", "tensor_cores", "explicit_S", "gmres_tol",
+                                          "check_every", "factor_chunks", "interface_solver")}}
+
+
 def bench_c5(steps=2, warmup=1, rank=0, ws=1):
     """The adjoint batch: 64 independent 2D problems -div(a grad u) = f with grids uneven in
     256^2 .. 1024^2 and 8, 16 or 32 slabs (slab widths 8 .. 128 cells), loss 1/2 ||u - u_obs||^2,
@@ -539,6 +554,7 @@ def main():
     ap.add_argument("--no-direct", action="store_true",
                     help="skip the direct interface solver section")
     ap.add_argument("--no-march", action="store_true", help="skip the time-marching section")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner section")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
     ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
     ap.add_argument("--only-c4", action="store_true",
@@ -761,6 +777,8 @@ def main():
             "rooflines": {"transfer_build": roof_tc, "interface_apply": roof_ap, "factor": roof_fac},
             "clocks": clk,
             "gpu_launches": int(launches), "wall_s": wall}
+    if rank == 0 and not args.no_autotune:
+        line["autotune"] = bench_autotune(a, f, g, n, w, args.tol)
     if rank == 0 and not args.no_direct:
         line["direct"] = bench_direct(a, f, g, n, w, args.tol, peaks, src)
     if rank == 0 and not args.no_march:
