@@ -416,6 +416,8 @@ __global__ void __launch_bounds__(256) k_h_inner(const HBlock* __restrict__ bl, 
                                                  const double* __restrict__ x0,
                                                  double* __restrict__ t, int transpose,
                                                  const int* kdev, int64_t kstride) {
+  // the owner kernel may start now: its dense-leaf part does not read t (programmatic launch)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int wi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (wi >= nblk) return;
   const HBlock& b = bl[wi];
@@ -522,12 +524,6 @@ __global__ void __launch_bounds__(OWN_T) k_h_owner(const HOwn* __restrict__ item
       s_woff[q] = (transpose ? B.v_off : B.u_off) + it->lo - (transpose ? B.col0 : B.row0);
     }
   }
-  for (int e = threadIdx.x; e < NSL * HOWN_TCAP; e += blockDim.x) {
-    const int q = e / HOWN_TCAP, c = e % HOWN_TCAP;
-    const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;
-    const int hb = s < nsrc ? it->hb[s][l] : -1;
-    if (hb >= 0 && c < bl[hb].rank) s_t[e] = static_cast<T>(t[bl[hb].t_off + c]);
-  }
   // dense leaves of both sources over these rows (same tree, so same ld), one pass
   const int ld = nsrc > 0 ? (int)lv[it->leaf[0]].ld : 0;
   const T* M0 = nsrc > 0 ? D + lv[it->leaf[0]].d_off : nullptr;
@@ -596,6 +592,15 @@ __global__ void __launch_bounds__(OWN_T) k_h_owner(const HOwn* __restrict__ item
         if (lane == 0) outv[c] += sm;
       }
     }
+  }
+  // the low-rank part needs t from k_h_inner: when launched as its programmatic dependent, this
+  // kernel ran the dense part concurrently and waits here for the inner kernel's results
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  for (int e = threadIdx.x; e < NSL * HOWN_TCAP; e += blockDim.x) {
+    const int q = e / HOWN_TCAP, c = e % HOWN_TCAP;
+    const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;
+    const int hb = s < nsrc ? it->hb[s][l] : -1;
+    if (hb >= 0 && c < bl[hb].rank) s_t[e] = static_cast<T>(t[bl[hb].t_off + c]);
   }
   __syncthreads();
   // W_out(rows, :) t_b of every low-rank block, one row per thread: the first eight columns of
@@ -934,10 +939,21 @@ void hodlr_apply(HodlrSet& H, const SlabDesc*, const ProbDesc*, int, const doubl
   }
   const int no = transpose ? H.n_own_T : H.n_own;
   if (no > 0) {
+    // programmatic dependent of k_h_inner: the dense leaves stream while the inner products run
     note_launch();
-    k_h_owner<T><<<no, OWN_T, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_leaves,
-                                     (const T*)H.UV, (const T*)H.D, H.t, x, y, transpose, konly,
-                                     kdev, kstride);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(no);
+    cfg.blockDim = dim3(OWN_T);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = H.blocks.empty() ? 0 : 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_h_owner<T>, (const HOwn*)(transpose ? H.d_own_T : H.d_own),
+                       (const HBlock*)H.d_blocks, (const HLeaf*)H.d_leaves, (const T*)H.UV,
+                       (const T*)H.D, (const double*)H.t, x, y, transpose, konly, kdev, kstride);
   }
 }
 
