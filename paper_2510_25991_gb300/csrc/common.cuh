@@ -108,6 +108,15 @@ __device__ __forceinline__ T warp_sum(T v) {
 // mbarrier + bulk-copy (TMA, untiled) helpers.  Every wait is bounded: after ~2 s of
 // clock64 cycles the waiting thread reports ST_TIMEOUT and gives up.
 // ---------------------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start before the kernel ahead of it in the stream has finished; pdl_wait() returns once that
+// kernel has completed and its memory operations are visible (immediately for a plain launch),
+// and pdl_release() lets the kernel behind this one be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(256) k_h_inner(const HBlock* __restrict__ bl, 
                                                  double* __restrict__ t, int transpose,
                                                  const int* kdev, int64_t kstride) {
   // the owner kernel may start now: its dense-leaf part does not read t (programmatic launch)
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_release();
   const int wi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (wi >= nblk) return;
   const HBlock& b = bl[wi];
@@ -595,7 +595,8 @@ __global__ void __launch_bounds__(OWN_T) k_h_owner(const HOwn* __restrict__ item
   }
   // the low-rank part needs t from k_h_inner: when launched as its programmatic dependent, this
   // kernel ran the dense part concurrently and waits here for the inner kernel's results
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  pdl_wait();
+  pdl_release();  // the Arnoldi dots behind this kernel may be scheduled
   for (int e = threadIdx.x; e < NSL * HOWN_TCAP; e += blockDim.x) {
     const int q = e / HOWN_TCAP, c = e % HOWN_TCAP;
     const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;
