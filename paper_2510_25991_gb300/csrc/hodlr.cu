@@ -596,7 +596,6 @@ __global__ void __launch_bounds__(OWN_T) k_h_owner(const HOwn* __restrict__ item
   // the low-rank part needs t from k_h_inner: when launched as its programmatic dependent, this
   // kernel ran the dense part concurrently and waits here for the inner kernel's results
   pdl_wait();
-  pdl_release();  // the Arnoldi dots behind this kernel may be scheduled
   for (int e = threadIdx.x; e < NSL * HOWN_TCAP; e += blockDim.x) {
     const int q = e / HOWN_TCAP, c = e % HOWN_TCAP;
     const int s = q / HOWN_MAXL, l = q % HOWN_MAXL;

@@ -291,8 +291,6 @@ __global__ void __launch_bounds__(ARN_T) k_arn_dots(const double* __restrict__ V
                                                     const int* __restrict__ kdev,
                                                     double* __restrict__ P1, int nchunk) {
   __shared__ double sw[ARN_CHUNK];
-  pdl_wait();  // w from the operator application
-  pdl_release();
   const int k = *kdev;
   const int64_t base = (int64_t)blockIdx.x * ARN_CHUNK;
   double wv[ARN_E];
@@ -344,8 +342,6 @@ __global__ void __launch_bounds__(ARN_T) k_arn_update(const double* __restrict__
                                                       double* __restrict__ Pn, int nchunk,
                                                       int first) {
   __shared__ double sh[1024 + 1];
-  pdl_wait();  // the partial sums (and for the second pass the flag) of the kernel before
-  pdl_release();
   const int k = *kdev;
   if (!first && kdev[1] == 0) {  // no second pass: h2 = 0, Pn already holds |w|^2
     if (blockIdx.x == 0)
@@ -408,7 +404,6 @@ __global__ void __launch_bounds__(ARN_T) k_arn_finish(double* __restrict__ V,
                                                       unsigned* __restrict__ ticket) {
   __shared__ double s_hn2;
   __shared__ bool s_last;
-  pdl_wait();
   const int k = *kdev;
   if (threadIdx.x < 32) {
     double a = 0.0;
@@ -474,26 +469,11 @@ void launch_arnoldi_step(double* V, double* w, int64_t n, int* kdev, double* h1,
   double* P2 = part + (int64_t)(kmax + 1) * nchunk;
   double* Pn = part + 2 * (int64_t)(kmax + 1) * nchunk;
   note_launch(4);
-  // programmatic dependent launches: each kernel waits for the one before it on entry, so the
-  // next kernel's CTAs are scheduled while the previous one finishes
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(nchunk);
-  cfg.blockDim = dim3(ARN_T);
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_arn_dots, (const double*)V, (const double*)w, n, (const int*)kdev,
-                     P1, nchunk);
-  cudaLaunchKernelEx(&cfg, k_arn_update, (const double*)V, w, n, kdev, (const double*)P1, h1, P2,
-                     Pn, nchunk, 1);
-  cudaLaunchKernelEx(&cfg, k_arn_update, (const double*)V, w, n, kdev, (const double*)P2, h2,
-                     (double*)nullptr, Pn, nchunk, 0);
-  cudaLaunchKernelEx(&cfg, k_arn_finish, V, (const double*)w, n, kdev, (const double*)Pn, nchunk,
-                     (const double*)h1, (const double*)h2, H, ldh, cs, sn, gv, beta, resid, kmax,
-                     ticket);
+  k_arn_dots<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, nchunk);
+  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P1, h1, P2, Pn, nchunk, 1);
+  k_arn_update<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, P2, h2, nullptr, Pn, nchunk, 0);
+  k_arn_finish<<<nchunk, ARN_T, 0, st>>>(V, w, n, kdev, Pn, nchunk, h1, h2, H, ldh, cs, sn, gv,
+                                         beta, resid, kmax, ticket);
 }
 
 // ------------------------------------------------------------------------------------------
