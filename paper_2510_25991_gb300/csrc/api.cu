@@ -62,7 +62,9 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
-constexpr int kNormBlocks = 32;  // CTAs per problem in the refinement's per-problem norms
+// CTAs per problem in the refinement's per-problem norms: about 1024 in all (at least 8 and at
+// most 256 per problem), so a single large problem streams its vectors at full bandwidth
+int norm_blocks(int nprob) { return std::max(8, std::min(256, 1024 / std::max(nprob, 1))); }
 
 }  // namespace
 
@@ -835,7 +837,7 @@ ddst_status ensure_solve_buffers(ddst_ctx* ctx) {
   AL(ctx->resid, sizeof(double) * (maxit + 1));
   AL(ctx->part, sizeof(double) * (size_t)(maxit + 1) * std::max(ctx->nchunk, 1024));
   AL(ctx->scal, sizeof(double) * 16);
-  AL(ctx->pn_part, sizeof(double) * 2 * (size_t)ctx->nprob * kNormBlocks);
+  AL(ctx->pn_part, sizeof(double) * 2 * (size_t)ctx->nprob * norm_blocks(ctx->nprob));
   AL(ctx->pn, sizeof(double) * 2 * (size_t)ctx->nprob);
   AL(ctx->ysol, sizeof(double) * (maxit + 1));
   AL(ctx->d_k, sizeof(int) * 4);
@@ -1157,9 +1159,9 @@ double refine_batch_estimate(ddst_ctx* ctx, const double* e, const double* x,
                              std::vector<std::vector<double>>& hist, double* rho) {
   const int np = ctx->nprob;
   cudaStream_t st = ctx->stream;
-  launch_prob_sqnorms(ctx->d_probs, np, e, ctx->pn_part, kNormBlocks, ctx->pn, st);
-  launch_prob_sqnorms(ctx->d_probs, np, x, ctx->pn_part + (size_t)np * kNormBlocks, kNormBlocks,
-                      ctx->pn + np, st);
+  const int nb = norm_blocks(np);
+  launch_prob_sqnorms(ctx->d_probs, np, e, ctx->pn_part, nb, ctx->pn, st);
+  launch_prob_sqnorms(ctx->d_probs, np, x, ctx->pn_part + (size_t)np * nb, nb, ctx->pn + np, st);
   std::vector<double> h(2 * (size_t)np);
   cudaMemcpyAsync(h.data(), ctx->pn, sizeof(double) * 2 * np, cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
