@@ -110,8 +110,15 @@ struct ddst_ctx {
   double factor_check = 0.0;
   bool use_tc = false;            // FP32 transfer build on tcgen05
   cudaStream_t cap_stream = nullptr;     // internal stream for graph capture
-  cudaGraphExec_t arn_graph[2] = {nullptr, nullptr};  // one GMRES step (plain / transposed)
-  int arn_graph_state[2] = {0, 0};       // operator state the graphs were captured for
+  // one GMRES step, captured per (transposed, operator group): index 2 transpose + group
+  cudaGraphExec_t arn_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  int arn_graph_state[4] = {0, 0, 0, 0};  // operator state the graphs were captured for
+  // A context whose problems are partly explicit and partly matrix-free keeps the two operator
+  // groups' interfaces contiguous (explicit problems first) and runs one GMRES per group, so the
+  // explicit problems do not pay a local solve per iteration for as long as the matrix-free ones
+  // iterate (and the other way round).  grp_off / grp_n: interface range of each group.
+  bool grouped = false;
+  int64_t grp_off[2] = {0, 0}, grp_n[2] = {0, 0};
   int* d_k = nullptr;                    // device-resident Krylov basis count
   double* arn_part = nullptr;            // Arnoldi partial sums: 2 (maxit+1) + 1 rows of chunks
   unsigned* arn_ticket = nullptr;        // last-CTA ticket of the Arnoldi finish kernel
@@ -140,7 +147,7 @@ struct ddst_ctx {
   void *mf_b = nullptr, *mf_z = nullptr, *mf_z2 = nullptr, *mf_x = nullptr;
   double* if_kx = nullptr;
   double* d_vel = nullptr;               // marching: nodal velocity components of every problem
-  long long arn_graph_launches[2] = {0, 0};  // kernels per replay of each captured GMRES step
+  long long arn_graph_launches[4] = {0, 0, 0, 0};  // kernels per replay of each captured step
   bool solve_bufs_ready = false;
   // direct interface solver (interface_solver = 1): block cyclic reduction of every problem's
   // equilibrium system, formed from the explicit S at the first solve after build_transfer
@@ -283,7 +290,7 @@ struct Timer {
 };
 
 void drop_graphs(ddst_ctx* ctx) {
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 4; ++q) {
     if (ctx->arn_graph[q]) cudaGraphExecDestroy(ctx->arn_graph[q]);
     ctx->arn_graph[q] = nullptr;
     ctx->arn_graph_state[q] = 0;
@@ -499,6 +506,42 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
   const bool auto_tol = !(ctx->opt.gmres_tol > 0.0);  // picked once the operator kind is known
   int64_t node_off = 0, vol_off = 0, if_off = 0, fac_off = 0, fac_big_off = 0, pack_off = 0,
           loc_off = 0, s_off = 0;
+  // Operator groups: with automatic explicit_S, problems whose blocks exceed the single-CTA
+  // kernels are applied matrix-free and the others explicitly.  Their interfaces are laid out
+  // group by group (explicit first), so that each group's GMRES works on a contiguous range.
+  // (Arguments are checked in the loop below; an invalid problem only gets a placeholder here.)
+  std::vector<int> grp(nprob, 0);
+  std::vector<int64_t> if_len(nprob, 0), if_base(nprob, 0);
+  {
+    bool any_b = false, all_b = true;
+    for (int q = 0; q < nprob; ++q) {
+      const ddst_grid& gr = grids[q];
+      const int w = widths[q];
+      bool big = false;
+      if ((gr.dim == 2 || gr.dim == 3) && w >= 1 && gr.n >= 4 && gr.n <= (1 << 20) &&
+          gr.n % w == 0 && gr.n / w >= 2) {
+        const int64_t pp = gr.dim == 2 ? 1 : gr.n - 1;
+        const int64_t m = (2 * (int64_t)w - 1) * pp;
+        const int M = m <= 8192 ? pad_M((int)m) : -1;
+        big = M < 0 || M > 128 || (ctx->prec == DDST_FP64 && M > 64);
+        if_len[q] = (gr.n / w - 1) * (gr.dim == 2 ? gr.n - 1 : (gr.n - 1) * (gr.n - 1));
+      }
+      grp[q] = big ? 1 : 0;
+      any_b = any_b || big;
+      all_b = all_b && big;
+    }
+    ctx->grouped = ctx->opt.explicit_S < 0 && any_b && !all_b;
+    int64_t o = 0;
+    for (int g = 0; g < 2; ++g) {
+      ctx->grp_off[g] = o;
+      for (int q = 0; q < nprob; ++q)
+        if ((ctx->grouped ? grp[q] : 0) == g) {
+          if_base[q] = o;
+          o += if_len[q];
+        }
+      ctx->grp_n[g] = o - ctx->grp_off[g];
+    }
+  }
   for (int q = 0; q < nprob; ++q) {
     const ddst_grid& gr = grids[q];
     const int w = widths[q];
@@ -533,7 +576,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
     for (int d = 0; d < gr.dim; ++d) { P.nint *= (P.n - 1); P.nnode *= (P.n + 1); }
     P.vol_off = vol_off;
     P.node_off = node_off;
-    P.if_off = if_off;
+    P.if_off = if_base[q];
     P.slab0 = (int)ctx->slabs.size();
     P.has_c = coeffs[q].c != nullptr;
     P.h = 1.0 / P.n;
@@ -550,7 +593,7 @@ ddst_status setup_impl(int nprob, const ddst_grid* grids, const ddst_coeffs* coe
       if (j >= 2 && !isbig) { s.sp_off = s_off; s_off += P.ng * P.ng; }
       if (j <= P.nds - 1 && !isbig) { s.sn_off = s_off; s_off += P.ng * P.ng; }
       s.vol_off = vol_off; s.node_off = node_off;
-      s.if_off = if_off + (int64_t)(j - 1) * P.ng;
+      s.if_off = P.if_off + (int64_t)(j - 1) * P.ng;
       ctx->cls[P.M].push_back((int)ctx->slabs.size());
       ctx->cls_maxnb[P.M] = std::max(ctx->cls_maxnb[P.M], P.nb);
       ctx->slabs.push_back(s);
@@ -900,11 +943,14 @@ void apply_matfree(ddst_ctx* ctx, const double* x, double* y, int mode, cudaStre
                     (mode & 2) ? 1 : 0, st);
 }
 
+// group: -1 every problem; 0 the explicit operators only; 1 the matrix-free ones only (a
+// grouped context's per-group GMRES).  x and y are indexed by absolute interface offsets.
 template <typename T>
 void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
-                       cudaStream_t st = nullptr, const int* kdev = nullptr, int64_t kstride = 0) {
+                       cudaStream_t st = nullptr, const int* kdev = nullptr, int64_t kstride = 0,
+                       int group = -1) {
   if (!st) st = ctx->stream;
-  if (ctx->matfree) {
+  if (ctx->matfree || group == 1) {
     apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
     return;
   }
@@ -916,14 +962,16 @@ void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
   else
     launch_apply_dense<T>(ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), ctx->max_ng,
                           (const T*)ctx->S, x, y, transpose, st, kdev, kstride);
-  if (ctx->mf_any) apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
+  if (ctx->mf_any && group < 0) apply_matfree<T>(ctx, x, y, transpose, st, kdev, kstride);
 }
 
 // One GMRES step (operator application + Arnoldi CGS2 + Givens + normalization) captured as a
 // CUDA graph on the internal stream; replayed on the context stream.
+// group -1 (one GMRES over every problem) or a grouped context's operator group, whose GMRES
+// vectors hold its interface range [grp_off, grp_off + grp_n) only.
 template <typename T>
-ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
-  const int key = transpose ? 1 : 0;
+ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, int group, cudaGraphExec_t* out) {
+  const int key = (transpose ? 2 : 0) + (group > 0 ? 1 : 0);
   if (ctx->arn_graph[key] && ctx->arn_graph_state[key] == ctx->state) {
     *out = ctx->arn_graph[key];
     return DDST_OK;
@@ -933,13 +981,17 @@ ddst_status arnoldi_graph(ddst_ctx* ctx, int transpose, cudaGraphExec_t* out) {
     ctx->arn_graph[key] = nullptr;
   }
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-  const int64_t n = ctx->tot_if;
+  const int64_t n = group < 0 ? ctx->tot_if : ctx->grp_n[group];
+  const int64_t off = group < 0 ? 0 : ctx->grp_off[group];
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
   cudaGraph_t g = nullptr;
   const long long l0 = launch_counter().load();
   CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-  // Arnoldi on K (bit 1 of the mode): same Krylov space as I - K, see launch_arnoldi_step
-  apply_interface_T<T>(ctx, ctx->V, ctx->if_w, transpose | 2, ctx->cap_stream, ctx->d_k, n);
+  // Arnoldi on K (bit 1 of the mode): same Krylov space as I - K, see launch_arnoldi_step.  The
+  // operator kernels index by absolute interface offsets: the basis and w are passed shifted by
+  // the group's offset (entries outside the group are neither read for it nor kept)
+  apply_interface_T<T>(ctx, ctx->V - off, ctx->if_w - off, transpose | 2, ctx->cap_stream,
+                       ctx->d_k, n, group);
   launch_arnoldi_step(ctx->V, ctx->if_w, n, ctx->d_k, ctx->h1, ctx->h2, ctx->arn_part,
                       ctx->arn_ticket, ctx->H, ctx->ldh, ctx->cs, ctx->sn, ctx->gv, ctx->d_beta,
                       ctx->resid, maxit, ctx->cap_stream);
@@ -1067,16 +1119,19 @@ ddst_status direct_interface_solve(ddst_ctx* ctx, const double* rhs, double* x, 
   return DDST_OK;
 }
 
-// GMRES on (I - K) x = rhs (or its transpose), x0 = 0.  Returns iterations; sets *relres.
+// GMRES on (I - K) x = rhs (or its transpose), x0 = 0, over one operator group's interface
+// range (group -1: all of it; rhs and x point at the range's start).  Returns iterations; sets
+// *relres.
 template <typename T>
-ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, int transpose,
-                       int* iters, double* relres) {
+ddst_status gmres_range(ddst_ctx* ctx, const double* rhs, double* x, double tol, int transpose,
+                        int group, int* iters, double* relres) {
   cudaStream_t st = ctx->stream;
-  const int64_t n = ctx->tot_if;
+  const int64_t n = group < 0 ? ctx->tot_if : ctx->grp_n[group];
   const int maxit = std::max(1, ctx->opt.gmres_max_iter);
   // host convergence checks: every iteration when a matrix-free application (local solves on
   // every slab) costs far more than the check's synchronization, else every 8
-  const int check = ctx->opt.check_every > 0 ? ctx->opt.check_every : (ctx->mf_any ? 1 : 8);
+  const bool mf = group < 0 ? ctx->mf_any : group == 1;
+  const int check = ctx->opt.check_every > 0 ? ctx->opt.check_every : (mf ? 1 : 8);
   launch_dot(rhs, rhs, n, ctx->part, 256, ctx->scal, st);
   const double beta = std::sqrt(host_scalar(ctx, ctx->scal));
   *iters = 0;
@@ -1095,14 +1150,14 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   CK(cudaMemsetAsync(ctx->h2, 0, sizeof(double) * (maxit + 1), st));
   CK(cudaMemsetAsync(ctx->scal + 1, 0, sizeof(double), st));
   cudaGraphExec_t graph = nullptr;
-  ddst_status gs = arnoldi_graph<T>(ctx, transpose, &graph);
+  ddst_status gs = arnoldi_graph<T>(ctx, transpose, group, &graph);
   if (gs != DDST_OK) return gs;
   std::vector<double> hres(maxit + 1);
   int kk = -1;
   int k = 0;
   for (k = 1; k <= maxit; ++k) {
     CK(cudaGraphLaunch(graph, st));
-    note_launch((int)ctx->arn_graph_launches[transpose ? 1 : 0]);
+    note_launch((int)ctx->arn_graph_launches[(transpose ? 2 : 0) + (group > 0 ? 1 : 0)]);
     if (k % check == 0 || k == maxit) {
       CK(cudaMemcpyAsync(hres.data(), ctx->resid, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -1121,6 +1176,31 @@ ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, 
   if (hres[kk - 1] > tol && hres[kk - 1] != 0.0)
     return fail(ctx, DDST_ERR_NOT_CONVERGED, "GMRES: relative residual %.3e after %d iterations",
                 hres[kk - 1], kk);
+  return DDST_OK;
+}
+
+// GMRES on the whole interface system: one Krylov space, or one per operator group in a
+// grouped context (the groups never couple).  Iterations and residual: the larger over groups.
+template <typename T>
+ddst_status gmres_impl(ddst_ctx* ctx, const double* rhs, double* x, double tol, int transpose,
+                       int* iters, double* relres) {
+  if (!ctx->grouped) return gmres_range<T>(ctx, rhs, x, tol, transpose, -1, iters, relres);
+  *iters = 0;
+  *relres = 0.0;
+  ddst_status worst = DDST_OK;
+  for (int g = 0; g < 2; ++g) {
+    if (ctx->grp_n[g] == 0) continue;
+    int it = 0;
+    double rr = 0.0;
+    const ddst_status s = gmres_range<T>(ctx, rhs + ctx->grp_off[g], x + ctx->grp_off[g], tol,
+                                         transpose, g, &it, &rr);
+    if (s != DDST_OK && s != DDST_ERR_NOT_CONVERGED) return s;
+    if (s != DDST_OK) worst = s;
+    *iters = std::max(*iters, it);
+    *relres = std::max(*relres, rr);
+  }
+  if (worst != DDST_OK)
+    return fail(ctx, worst, "GMRES: relative residual %.3e after %d iterations", *relres, *iters);
   return DDST_OK;
 }
 

@@ -67,6 +67,34 @@ __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict_
                               : x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
 }
 
+// One column of a column-major block times x over a warp: lanes over the column's contiguous
+// rows, four independent products in flight per lane, the FP32 partial sums flushed into FP64
+// every 32 terms.
+template <typename T>
+__device__ __forceinline__ double warp_col_dot(const T* __restrict__ col,
+                                              const double* __restrict__ xv, int64_t ng,
+                                              int lane) {
+  double acc = 0.0;
+  T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+  int64_t r = lane;
+  int cnt = 0;
+  for (; r + 96 < ng; r += 128) {
+    p0 = fma(col[r], static_cast<T>(xv[r]), p0);
+    p1 = fma(col[r + 32], static_cast<T>(xv[r + 32]), p1);
+    p2 = fma(col[r + 64], static_cast<T>(xv[r + 64]), p2);
+    p3 = fma(col[r + 96], static_cast<T>(xv[r + 96]), p3);
+    if (++cnt == 8) {
+      acc += static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
+             static_cast<double>(p3);
+      p0 = p1 = p2 = p3 = T(0);
+      cnt = 0;
+    }
+  }
+  for (; r < ng; r += 32) p0 = fma(col[r], static_cast<T>(xv[r]), p0);
+  return acc + static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
+         static_cast<double>(p3);
+}
+
 // y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): warp per output
 // point, lanes over the (contiguous) rows of the column-major blocks.  grid = (ceil(ng/8),
 // slabs), 256 threads.
@@ -90,27 +118,11 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
   // blocks (a class applied matrix-free, offset -1) contributes nothing here
   if (s.j <= P.nds - 1 && slabs[sidx + 1].sp_off >= 0) {
     const SlabDesc t = slabs[sidx + 1];
-    const T* col = S + t.sp_off + src * ng;
-    const double* xv = x + t.if_off;
-    T part = T(0);
-    int cnt = 0;
-    for (int64_t r = lane; r < ng; r += 32) {
-      part = fma(col[r], static_cast<T>(xv[r]), part);
-      if (++cnt == 32) { acc += static_cast<double>(part); part = T(0); cnt = 0; }
-    }
-    acc += static_cast<double>(part);
+    acc += warp_col_dot<T>(S + t.sp_off + src * ng, x + t.if_off, ng, lane);
   }
   if (s.j >= 2 && slabs[sidx - 1].sn_off >= 0) {
     const SlabDesc t = slabs[sidx - 1];
-    const T* col = S + t.sn_off + src * ng;
-    const double* xv = x + t.if_off;
-    T part = T(0);
-    int cnt = 0;
-    for (int64_t r = lane; r < ng; r += 32) {
-      part = fma(col[r], static_cast<T>(xv[r]), part);
-      if (++cnt == 32) { acc += static_cast<double>(part); part = T(0); cnt = 0; }
-    }
-    acc += static_cast<double>(part);
+    acc += warp_col_dot<T>(S + t.sn_off + src * ng, x + t.if_off, ng, lane);
   }
   acc = warp_sum(acc);
   if (lane == 0) y[s.if_off + src] = konly ? acc : x[s.if_off + src] - acc;
