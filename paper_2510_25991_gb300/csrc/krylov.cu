@@ -95,9 +95,9 @@ __device__ __forceinline__ double warp_col_dot(const T* __restrict__ col,
          static_cast<double>(p3);
 }
 
-// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): warp per output
-// point, lanes over the (contiguous) rows of the column-major blocks.  grid = (ceil(ng/8),
-// slabs), 256 threads.
+// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): a warp takes four
+// output points, lanes over the (contiguous) rows of the column-major blocks.
+// grid = (ceil(ng/32), slabs), 256 threads.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
                                                        const ProbDesc* __restrict__ probs,
@@ -107,25 +107,26 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
                                                        int64_t kstride, int konly) {
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int sidx = blockIdx.y;
-  const SlabDesc s = slabs[sidx];
-  const ProbDesc P = probs[s.prob];
-  const int64_t ng = s.ng;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t src = (int64_t)blockIdx.x * 8 + warp;
-  if (src >= ng) return;
-  double acc = 0.0;
+  const SlabDesc& s = slabs[sidx];
+  const int64_t ng = s.ng, if_off = s.if_off;
+  const int j = s.j, nds = probs[s.prob].nds;
   // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}; a neighbour without explicit
   // blocks (a class applied matrix-free, offset -1) contributes nothing here
-  if (s.j <= P.nds - 1 && slabs[sidx + 1].sp_off >= 0) {
-    const SlabDesc t = slabs[sidx + 1];
-    acc += warp_col_dot<T>(S + t.sp_off + src * ng, x + t.if_off, ng, lane);
+  const int64_t up_off = j <= nds - 1 ? slabs[sidx + 1].sp_off : -1;
+  const int64_t dn_off = j >= 2 ? slabs[sidx - 1].sn_off : -1;
+  const double* xup = x + if_off + ng;  // Gamma_{j+1}
+  const double* xdn = x + if_off - ng;  // Gamma_{j-1}
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
+    const int64_t src = (int64_t)blockIdx.x * 32 + warp * 4 + q;
+    if (src >= ng) break;
+    double acc = 0.0;
+    if (up_off >= 0) acc += warp_col_dot<T>(S + up_off + src * ng, xup, ng, lane);
+    if (dn_off >= 0) acc += warp_col_dot<T>(S + dn_off + src * ng, xdn, ng, lane);
+    acc = warp_sum(acc);
+    if (lane == 0) y[if_off + src] = konly ? acc : x[if_off + src] - acc;
   }
-  if (s.j >= 2 && slabs[sidx - 1].sn_off >= 0) {
-    const SlabDesc t = slabs[sidx - 1];
-    acc += warp_col_dot<T>(S + t.sn_off + src * ng, x + t.if_off, ng, lane);
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) y[s.if_off + src] = konly ? acc : x[s.if_off + src] - acc;
 }
 
 // GMRES solution from the Krylov basis: x = sum_{i<k} y[i] V[i]
@@ -503,7 +504,7 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
         d_slabs, d_probs, S, x, y, kdev, kstride, konly);
   } else {
     note_launch();
-    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 7) / 8), nslab), 256, 0, st>>>(d_slabs, d_probs,
+    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 31) / 32), nslab), 256, 0, st>>>(d_slabs, d_probs,
                                                                                   S, x, y, kdev, kstride,
                                                                                   konly);
   }
