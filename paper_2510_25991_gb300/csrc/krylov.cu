@@ -67,22 +67,21 @@ __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict_
                               : x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
 }
 
-// One column of a column-major block times x over a warp: lanes over the column's contiguous
-// rows, four independent products in flight per lane, the FP32 partial sums flushed into FP64
-// every 32 terms.
+// One column of a column-major block times x (staged in shared memory) over a warp: lanes over
+// the column's contiguous rows, four independent products in flight per lane, the partial sums
+// in the working precision flushed into FP64 every 32 terms.
 template <typename T>
-__device__ __forceinline__ double warp_col_dot(const T* __restrict__ col,
-                                              const double* __restrict__ xv, int64_t ng,
-                                              int lane) {
+__device__ __forceinline__ double warp_col_dot(const T* __restrict__ col, const T* __restrict__ xs,
+                                              int64_t ng, int lane) {
   double acc = 0.0;
   T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
   int64_t r = lane;
   int cnt = 0;
   for (; r + 96 < ng; r += 128) {
-    p0 = fma(col[r], static_cast<T>(xv[r]), p0);
-    p1 = fma(col[r + 32], static_cast<T>(xv[r + 32]), p1);
-    p2 = fma(col[r + 64], static_cast<T>(xv[r + 64]), p2);
-    p3 = fma(col[r + 96], static_cast<T>(xv[r + 96]), p3);
+    p0 = fma(col[r], xs[r], p0);
+    p1 = fma(col[r + 32], xs[r + 32], p1);
+    p2 = fma(col[r + 64], xs[r + 64], p2);
+    p3 = fma(col[r + 96], xs[r + 96], p3);
     if (++cnt == 8) {
       acc += static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
              static_cast<double>(p3);
@@ -90,14 +89,17 @@ __device__ __forceinline__ double warp_col_dot(const T* __restrict__ col,
       cnt = 0;
     }
   }
-  for (; r < ng; r += 32) p0 = fma(col[r], static_cast<T>(xv[r]), p0);
+  for (; r < ng; r += 32) p0 = fma(col[r], xs[r], p0);
   return acc + static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
          static_cast<double>(p3);
 }
 
-// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): a warp takes four
-// output points, lanes over the (contiguous) rows of the column-major blocks.
-// grid = (ceil(ng/32), slabs), 256 threads.
+// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): the two neighbouring
+// traces are staged once per CTA in shared memory (in the working precision, as in the forward
+// apply), then a warp takes four output points, lanes over the (contiguous) rows of the
+// column-major blocks.  grid = (ceil(ng/32), slabs), 256 threads, 2 max_ng elements of dynamic
+// shared memory.  (With the traces read from global memory per column, the kernel was bound by
+// the L1 request queue at a tenth of the forward apply's bandwidth.)
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
                                                        const ProbDesc* __restrict__ probs,
@@ -105,25 +107,32 @@ __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restric
                                                        const double* __restrict__ x0,
                                                        double* __restrict__ y, const int* kdev,
                                                        int64_t kstride, int konly) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int sidx = blockIdx.y;
   const SlabDesc& s = slabs[sidx];
   const int64_t ng = s.ng, if_off = s.if_off;
+  if ((int64_t)blockIdx.x * 32 >= ng) return;  // uniform over the CTA
   const int j = s.j, nds = probs[s.prob].nds;
   // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}; a neighbour without explicit
   // blocks (a class applied matrix-free, offset -1) contributes nothing here
   const int64_t up_off = j <= nds - 1 ? slabs[sidx + 1].sp_off : -1;
   const int64_t dn_off = j >= 2 ? slabs[sidx - 1].sn_off : -1;
-  const double* xup = x + if_off + ng;  // Gamma_{j+1}
-  const double* xdn = x + if_off - ng;  // Gamma_{j-1}
+  T* xu = reinterpret_cast<T*>(smem_raw);  // Gamma_{j+1}
+  T* xd = xu + ng;                          // Gamma_{j-1}
+  for (int64_t e = threadIdx.x; e < ng; e += blockDim.x) {
+    xu[e] = up_off >= 0 ? static_cast<T>(x[if_off + ng + e]) : T(0);
+    xd[e] = dn_off >= 0 ? static_cast<T>(x[if_off - ng + e]) : T(0);
+  }
+  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
   for (int q = 0; q < 4; ++q) {
     const int64_t src = (int64_t)blockIdx.x * 32 + warp * 4 + q;
     if (src >= ng) break;
     double acc = 0.0;
-    if (up_off >= 0) acc += warp_col_dot<T>(S + up_off + src * ng, xup, ng, lane);
-    if (dn_off >= 0) acc += warp_col_dot<T>(S + dn_off + src * ng, xdn, ng, lane);
+    if (up_off >= 0) acc += warp_col_dot<T>(S + up_off + src * ng, xu, ng, lane);
+    if (dn_off >= 0) acc += warp_col_dot<T>(S + dn_off + src * ng, xd, ng, lane);
     acc = warp_sum(acc);
     if (lane == 0) y[if_off + src] = konly ? acc : x[if_off + src] - acc;
   }
@@ -504,7 +513,9 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
         d_slabs, d_probs, S, x, y, kdev, kstride, konly);
   } else {
     note_launch();
-    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 31) / 32), nslab), 256, 0, st>>>(d_slabs, d_probs,
+    const size_t smT = 2 * (size_t)max_ng * sizeof(T);
+    raise_smem_limit(reinterpret_cast<const void*>(&k_apply_dense_T<T>), smT);
+    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 31) / 32), nslab), 256, smT, st>>>(d_slabs, d_probs,
                                                                                   S, x, y, kdev, kstride,
                                                                                   konly);
   }
