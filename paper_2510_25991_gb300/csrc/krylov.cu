@@ -67,74 +67,77 @@ __global__ void __launch_bounds__(256) k_apply_dense(const SlabDesc* __restrict_
                               : x[s.if_off + row] - (red[threadIdx.x] + red[threadIdx.x + 128]);
 }
 
-// One column of a column-major block times x (staged in shared memory) over a warp: lanes over
-// the column's contiguous rows, four independent products in flight per lane, the partial sums
-// in the working precision flushed into FP64 every 32 terms.
-template <typename T>
-__device__ __forceinline__ double warp_col_dot(const T* __restrict__ col, const T* __restrict__ xs,
-                                              int64_t ng, int lane) {
-  double acc = 0.0;
-  T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
-  int64_t r = lane;
-  int cnt = 0;
-  for (; r + 96 < ng; r += 128) {
-    p0 = fma(col[r], xs[r], p0);
-    p1 = fma(col[r + 32], xs[r + 32], p1);
-    p2 = fma(col[r + 64], xs[r + 64], p2);
-    p3 = fma(col[r + 96], xs[r + 96], p3);
-    if (++cnt == 8) {
-      acc += static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
-             static_cast<double>(p3);
-      p0 = p1 = p2 = p3 = T(0);
-      cnt = 0;
-    }
-  }
-  for (; r < ng; r += 32) p0 = fma(col[r], xs[r], p0);
-  return acc + static_cast<double>(p0) + static_cast<double>(p1) + static_cast<double>(p2) +
-         static_cast<double>(p3);
-}
-
-// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x): the two neighbouring
-// traces are staged once per CTA in shared memory (in the working precision, as in the forward
-// apply), then a warp takes four output points, lanes over the (contiguous) rows of the
-// column-major blocks.  grid = (ceil(ng/32), slabs), 256 threads, 2 max_ng elements of dynamic
-// shared memory.  (With the traces read from global memory per column, the kernel was bound by
-// the L1 request queue at a tenth of the forward apply's bandwidth.)
+// y_j = x_j - S_{j+1,j}^T x_{j+1} - S_{j-1,j}^T x_{j-1} (konly: y = K^T x).  S is stored by
+// columns, so (S^T x)_c is a dot product down column c.  A CTA owns 128 output points (columns)
+// and streams its columns through shared memory in 32-row tiles: warp w loads 16 columns of a
+// tile, one coalesced 32-row segment each (16 independent loads in flight per warp), and the 256
+// threads (128 columns x 2 row halves) then take 16 terms each from the transposed tile, partial
+// sums in the working precision added into FP64 per tile.  The neighbouring traces are staged
+// once in shared memory.  grid = (ceil(ng/128), slabs), 256 threads, dynamic shared memory
+// 2 max_ng + 128 x 33 elements.  (A warp per column reading the traces from global memory was
+// bound by the L1 request queue at a tenth of the forward apply's bandwidth.)
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_dense_T(const SlabDesc* __restrict__ slabs,
                                                        const ProbDesc* __restrict__ probs,
                                                        const T* __restrict__ S,
                                                        const double* __restrict__ x0,
                                                        double* __restrict__ y, const int* kdev,
-                                                       int64_t kstride, int konly) {
+                                                       int64_t kstride, int konly,
+                                                       int64_t max_ng) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const int sidx = blockIdx.y;
   const SlabDesc& s = slabs[sidx];
   const int64_t ng = s.ng, if_off = s.if_off;
-  if ((int64_t)blockIdx.x * 32 >= ng) return;  // uniform over the CTA
+  const int64_t c0 = (int64_t)blockIdx.x * 128;
+  if (c0 >= ng) return;  // uniform over the CTA
   const int j = s.j, nds = probs[s.prob].nds;
   // slab j+1 maps Gamma_j -> Gamma_{j+1} through its S_{j+1,j}; a neighbour without explicit
   // blocks (a class applied matrix-free, offset -1) contributes nothing here
-  const int64_t up_off = j <= nds - 1 ? slabs[sidx + 1].sp_off : -1;
-  const int64_t dn_off = j >= 2 ? slabs[sidx - 1].sn_off : -1;
-  T* xu = reinterpret_cast<T*>(smem_raw);  // Gamma_{j+1}
-  T* xd = xu + ng;                          // Gamma_{j-1}
+  const int64_t offs[2] = {j <= nds - 1 ? slabs[sidx + 1].sp_off : -1,
+                           j >= 2 ? slabs[sidx - 1].sn_off : -1};
+  T* xs0 = reinterpret_cast<T*>(smem_raw);  // Gamma_{j+1}
+  T* xs1 = xs0 + max_ng;                     // Gamma_{j-1}
+  T* tile = xs1 + max_ng;                    // [128][33]: column, row within the tile
   for (int64_t e = threadIdx.x; e < ng; e += blockDim.x) {
-    xu[e] = up_off >= 0 ? static_cast<T>(x[if_off + ng + e]) : T(0);
-    xd[e] = dn_off >= 0 ? static_cast<T>(x[if_off - ng + e]) : T(0);
+    xs0[e] = offs[0] >= 0 ? static_cast<T>(x[if_off + ng + e]) : T(0);
+    xs1[e] = offs[1] >= 0 ? static_cast<T>(x[if_off - ng + e]) : T(0);
+  }
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cl = tid & 127, half = tid >> 7;
+  double acc = 0.0;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int64_t off = offs[side];
+    if (off < 0) continue;  // uniform
+    const T* xs = side == 0 ? xs0 : xs1;
+#pragma unroll 1
+    for (int64_t r0 = 0; r0 < ng; r0 += 32) {
+      __syncthreads();  // the staged traces (first pass) / the previous tile's readers
+      const int64_t r = r0 + lane;
+#pragma unroll
+      for (int cc = 0; cc < 16; ++cc) {
+        const int64_t c = c0 + warp * 16 + cc;
+        tile[(warp * 16 + cc) * 33 + lane] = (c < ng && r < ng) ? S[off + c * ng + r] : T(0);
+      }
+      __syncthreads();
+      T p = T(0);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int rr = half * 16 + i;
+        p = fma(tile[cl * 33 + rr], r0 + rr < ng ? xs[r0 + rr] : T(0), p);
+      }
+      acc += static_cast<double>(p);
+    }
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll 1
-  for (int q = 0; q < 4; ++q) {
-    const int64_t src = (int64_t)blockIdx.x * 32 + warp * 4 + q;
-    if (src >= ng) break;
-    double acc = 0.0;
-    if (up_off >= 0) acc += warp_col_dot<T>(S + up_off + src * ng, xu, ng, lane);
-    if (dn_off >= 0) acc += warp_col_dot<T>(S + dn_off + src * ng, xd, ng, lane);
-    acc = warp_sum(acc);
-    if (lane == 0) y[if_off + src] = konly ? acc : x[if_off + src] - acc;
+  double* red = reinterpret_cast<double*>(tile);  // 256 doubles fit in the tile's space
+  red[tid] = acc;
+  __syncthreads();
+  const int64_t c = c0 + cl;
+  if (half == 0 && c < ng) {
+    const double v = red[tid] + red[tid + 128];
+    y[if_off + c] = konly ? v : x[if_off + c] - v;
   }
 }
 
@@ -513,11 +516,10 @@ void launch_apply_dense(const SlabDesc* d_slabs, const ProbDesc* d_probs, int ns
         d_slabs, d_probs, S, x, y, kdev, kstride, konly);
   } else {
     note_launch();
-    const size_t smT = 2 * (size_t)max_ng * sizeof(T);
+    const size_t smT = (2 * (size_t)max_ng + 128 * 33) * sizeof(T);
     raise_smem_limit(reinterpret_cast<const void*>(&k_apply_dense_T<T>), smT);
-    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 31) / 32), nslab), 256, smT, st>>>(d_slabs, d_probs,
-                                                                                  S, x, y, kdev, kstride,
-                                                                                  konly);
+    k_apply_dense_T<T><<<dim3((unsigned)((max_ng + 127) / 128), nslab), 256, smT, st>>>(
+        d_slabs, d_probs, S, x, y, kdev, kstride, konly, max_ng);
   }
 }
 
