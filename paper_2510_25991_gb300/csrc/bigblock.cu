@@ -630,7 +630,9 @@ __device__ __forceinline__ void load_v(const SolveStep<T>& d, int M, T* v) {
 }
 
 // y = F v (row-major F): a warp takes 4 rows, lanes stride the columns with 16-byte loads.
-// grid = (M / 32, slabs of the class), 256 threads.
+// Only the live m x m part is read: the padding of every F_k is exactly the identity (Sigma_k is
+// the identity there and the Gauss-Jordan panels keep exact zeros off it), so a padded row gives
+// v itself.  grid = (M / 32, slabs of the class), 256 threads.
 template <typename T>
 __global__ void __launch_bounds__(256) k_big_gemv_n(const SlabDesc* __restrict__ slabs,
                                                     const int* __restrict__ ids,
@@ -651,8 +653,18 @@ __global__ void __launch_bounds__(256) k_big_gemv_n(const SlabDesc* __restrict__
   const int r0 = blockIdx.x * 32 + warp * 4;
   constexpr int VW = 16 / sizeof(T);  // elements per 16-byte load
   using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int m = s.m;
+  if (r0 >= m) {  // padded rows: identity
+    if (lane < 4) {
+      const int r = r0 + lane;
+      d.out[r] = (d.R ? d.R[r] : T(0)) + d.os * (d.psi ? d.psi[r] : T(1)) * v[r];
+    }
+    return;
+  }
+  // columns up to m rounded to the load width (covers the diagonal of every row of this warp)
+  const int mc = min(M, (m + VW - 1) / VW * VW);
   T acc[4] = {T(0), T(0), T(0), T(0)};
-  for (int c = lane * VW; c < M; c += 32 * VW) {
+  for (int c = lane * VW; c < mc; c += 32 * VW) {
     T vv[VW];
 #pragma unroll
     for (int e = 0; e < VW; ++e) vv[e] = v[c + e];
@@ -674,8 +686,9 @@ __global__ void __launch_bounds__(256) k_big_gemv_n(const SlabDesc* __restrict__
   }
 }
 
-// y = F^T v: a CTA owns 64 columns (lanes hold two adjacent columns), its 8 warps split the rows
-// and combine their partial sums in shared memory.  grid = (M / 64, slabs of the class).
+// y = F^T v: a CTA owns 64 columns (lanes hold two adjacent columns), its 8 warps split the live
+// rows and combine their partial sums in shared memory; a padded column gives v itself (the
+// padding of F_k is the identity).  grid = (M / 64, slabs of the class).
 template <typename T>
 __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__ slabs,
                                                     const int* __restrict__ ids,
@@ -700,16 +713,17 @@ __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__
   load_v(d, M, v);
   __syncthreads();
   const T* Fk = F + s.fac_off + (int64_t)(d.kf - 1) * M * M;
+  const int m = s.m;
   T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
   int r = warp;
-  for (; r + 8 < M; r += 16) {
+  for (; r + 8 < m; r += 16) {
     const T* p0 = Fk + (int64_t)r * M + c0;
     const T* p1 = Fk + (int64_t)(r + 8) * M + c0;
     const T f00 = p0[0], f01 = p0[1], f10 = p1[0], f11 = p1[1];
     a0 = fma(f00, v[r], a0); a1 = fma(f01, v[r], a1);
     b0 = fma(f10, v[r + 8], b0); b1 = fma(f11, v[r + 8], b1);
   }
-  for (; r < M; r += 8) {
+  for (; r < m; r += 8) {
     const T* p0 = Fk + (int64_t)r * M + c0;
     a0 = fma(p0[0], v[r], a0); a1 = fma(p0[1], v[r], a1);
   }
@@ -721,6 +735,7 @@ __global__ void __launch_bounds__(256) k_big_gemv_t(const SlabDesc* __restrict__
 #pragma unroll
     for (int w = 0; w < 8; ++w) y += red[w * 64 + threadIdx.x];
     const int c = blockIdx.x * 64 + threadIdx.x;
+    if (c >= m) y += v[c];  // the identity on the padding
     d.out[c] = (d.R ? d.R[c] : T(0)) + d.os * (d.psi ? d.psi[c] : T(1)) * y;
   }
 }
