@@ -268,9 +268,9 @@ ddst_status ddst_solve_adjoint_batch(ddst_ctx* ctx, const double* const* dL_du,
                                      double* const* dL_da, ddst_info* info);
 
 /* Interface traces u_Gamma of problem prob from the last solve (N_ds * n_Gamma values, host or
- * device array): the solution of the equilibrium system (I - K) u_Gamma = fhat of Sec. 1,
- * Eq. (modelS) for the last DD solve of the refinement, i.e. the values of u on the interfaces
- * Gamma_j (Sec. 2.2).  Errors: INVALID_ARG (bad prob or NULL), STATE (no solve yet), CUDA. */
+ * device array): the refined solution u on the interfaces Gamma_j (Sec. 2.2), which solves the
+ * equilibrium system (I - K) u_Gamma = fhat of Sec. 1, Eq. (modelS) to the refinement's
+ * accuracy.  Errors: INVALID_ARG (bad prob or NULL), STATE (no solve yet), CUDA. */
 ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG);
 
 /* Copies S_{j,j-1} (side = -1) or S_{j,j+1} (side = +1) of problem prob, slab j (1-based),
