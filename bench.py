@@ -554,6 +554,8 @@ def main():
     ap.add_argument("--no-direct", action="store_true",
                     help="skip the direct interface solver section")
     ap.add_argument("--no-march", action="store_true", help="skip the time-marching section")
+    ap.add_argument("--only-direct", action="store_true",
+                    help="run only the direct-solver section on --n / --w (for profiling smaller cases)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner section")
     ap.add_argument("--no-c4", action="store_true", help="skip the 3D 128^3 workload")
     ap.add_argument("--no-c5", action="store_true", help="skip the 64-problem adjoint batch")
@@ -591,6 +593,12 @@ def main():
         return
     n, w = args.n, args.w
     prob = I.make_problem("convdiff2d", n=n, w=w)
+    if args.only_direct:  # the direct-solver section alone, on the --n / --w workload
+        peaks, src = _peaks()
+        devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        print(json.dumps(bench_direct(devt(prob["a"]), devt(prob["f"]), devt(prob["g"]), n, w,
+                                      args.tol, peaks, src, solves=2)), flush=True)
+        return
     dof = (n - 1) ** 2
     devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
     a, f, g = devt(prob["a"]), devt(prob["f"]), devt(prob["g"])
