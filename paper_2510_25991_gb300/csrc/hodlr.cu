@@ -80,12 +80,12 @@ struct HItem {
 template <typename T>
 __global__ void k_sblk_gemv(const SBlk* __restrict__ sb, const T* __restrict__ S,
                             const double* __restrict__ x, double* __restrict__ y,
-                            int64_t stride, int transpose) {
+                            int64_t stride) {
   const SBlk b = sb[blockIdx.y];
   const double* xv = x + blockIdx.y * stride;
   double* yv = y + blockIdx.y * stride;
   const T* M = S + b.off;
-  if (!transpose) {  // y += S(:, chunk) x(chunk): thread per row, 128 columns per CTA (y zeroed)
+  {  // y += S(:, chunk) x(chunk): thread per row, 128 columns per CTA (y zeroed)
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.z * 128;
     if (row >= b.ng || c0 >= b.ng) return;
@@ -103,26 +103,48 @@ __global__ void k_sblk_gemv(const SBlk* __restrict__ sb, const T* __restrict__ S
       acc += (double)((p[0] + p[1]) + (p[2] + p[3]));
     }
     atomicAdd(&yv[row], acc);
-  } else {  // y = S^T x: warp per column
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t col = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (col >= b.ng || blockIdx.z != 0) return;
-    const T* mc = M + col * b.ng;
-    double acc = 0.0;
-    for (int64_t r0 = 0; r0 < b.ng; r0 += 1024) {  // four independent chains, 32 rows each
-      T p[4] = {T(0), T(0), T(0), T(0)};
-      const int64_t re = min(b.ng, r0 + 1024);
-      int64_t r = r0 + lane;
-      for (; r + 96 < re; r += 128) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] = fma(mc[r + 32 * u], static_cast<T>(xv[r + 32 * u]), p[u]);
-      }
-      for (; r < re; r += 32) p[0] = fma(mc[r], static_cast<T>(xv[r]), p[0]);
-      acc += (double)((p[0] + p[1]) + (p[2] + p[3]));
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) yv[col] = acc;
   }
+}
+
+// y = S^T x for every S block: the columns are streamed through 32-row shared-memory tiles (a
+// CTA owns 128 columns; each warp loads 16 coalesced column segments per tile) and x's 32 tile
+// rows are staged beside them, so the kernel is not bound by per-column reads of x through L1
+// (a warp per column reading x through L1 was).  grid = (ceil(ng/128), blocks), 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sblk_gemv_t(const SBlk* __restrict__ sb,
+                                                     const T* __restrict__ S,
+                                                     const double* __restrict__ x,
+                                                     double* __restrict__ y, int64_t stride) {
+  __shared__ T tile[128 * 33];
+  __shared__ T xs[32];
+  __shared__ double red[256];
+  const SBlk b = sb[blockIdx.y];
+  const int64_t ng = b.ng, c0 = (int64_t)blockIdx.x * 128;
+  if (c0 >= ng) return;  // uniform over the CTA
+  const double* xv = x + blockIdx.y * stride;
+  const T* M = S + b.off;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cl = tid & 127, half = tid >> 7;
+  double acc = 0.0;
+  for (int64_t r0 = 0; r0 < ng; r0 += 32) {
+    const int64_t r = r0 + lane;
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) {
+      const int64_t c = c0 + warp * 16 + cc;
+      tile[(warp * 16 + cc) * 33 + lane] = (c < ng && r < ng) ? M[c * ng + r] : T(0);
+    }
+    if (tid < 32) xs[tid] = r0 + tid < ng ? static_cast<T>(xv[r0 + tid]) : T(0);
+    __syncthreads();
+    T p = T(0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) p = fma(tile[cl * 33 + half * 16 + i], xs[half * 16 + i], p);
+    acc += static_cast<double>(p);
+    __syncthreads();
+  }
+  red[tid] = acc;
+  __syncthreads();
+  const int64_t c = c0 + cl;
+  if (half == 0 && c < ng) y[blockIdx.y * stride + c] = red[tid] + red[tid + 128];
 }
 
 // x_b <- y_b / ||y_b||, nrm[b] = ||y_b||  (one CTA per block)
@@ -801,13 +823,13 @@ int hodlr_build(HodlrSet& H, const HodlrParams& hp, const std::vector<SlabDesc>&
   // threshold, i.e. errs towards higher ranks)
   note_launch();
   k_sblk_init<<<nsb, 256, 0, st>>>(d_sb, d_x, stride, hp.seed ^ 0x9e3779b97f4a7c15ull);
-  const unsigned gr = (unsigned)((max_ng + 255) / 256), gc = (unsigned)((max_ng + 7) / 8);
+  const unsigned gr = (unsigned)((max_ng + 255) / 256);
   const unsigned gz = (unsigned)((max_ng + 127) / 128);
   for (int itp = 0; itp < 2; ++itp) {
     cudaMemsetAsync(d_y, 0, sizeof(double) * stride * nsb, st);
     note_launch(3);
-    k_sblk_gemv<T><<<dim3(gr, nsb, gz), 256, 0, st>>>(d_sb, S, d_x, d_y, stride, 0);
-    k_sblk_gemv<T><<<dim3(gc, nsb, 1), 256, 0, st>>>(d_sb, S, d_y, d_x, stride, 1);
+    k_sblk_gemv<T><<<dim3(gr, nsb, gz), 256, 0, st>>>(d_sb, S, d_x, d_y, stride);
+    k_sblk_gemv_t<T><<<dim3(gz, nsb), 256, 0, st>>>(d_sb, S, d_y, d_x, stride);
     k_sblk_normalize<<<nsb, 256, 0, st>>>(d_sb, d_x, d_x, stride, d_nrm);
   }
   // d_nrm now holds ||S^T S x|| ~ sigma_max^2
