@@ -38,6 +38,11 @@ follows ("the paper" below):
   (Sec. 2.4) on a balanced bisection tree shared by source and target interface, every
   off-diagonal block truncated by SVD at the smallest rank with
   ``sigma_{r+1} <= tol * ||S_{j,j'}||_2``; diagonal leaves kept dense.
+* O9 ``hbs_compress`` / ``hbs_apply``: the nested-basis HBS form of a transfer block computed
+  from random samples ``Y = S Om`` and ``Z = S^T Psi`` alone (Sec. 2.4; Alg. 1 draws
+  ``s = 3k + q`` Gaussian samples): per tree node the bases from the samples projected onto the
+  null space of the node's test rows, the uncaptured diagonal part from pseudo-inverses, and the
+  samples of the reduced matrix passed to the parent; the telescoping apply over the tree.
 * O7 ``adjoint_solve`` / ``gradients``: discrete adjoint of the FD system for a loss on ``u``
   (``lambda = A^{-T} dL/du``) and the gradients with respect to ``f``, ``g`` and nodal ``a``.
 * O8 ``imex_rhs`` / ``imex_march``: backward-Euler IMEX time marching of the convection-diffusion
@@ -73,7 +78,8 @@ __all__ = [
     "transfer_blocks", "poisson_transfer_apply", "equivalent_load", "interface_matrix", "apply_interface",
     "block_thomas", "gmres", "reconstruct", "dd_solve", "hodlr_levels", "hodlr_node",
     "hodlr_compress", "hodlr_dense", "hodlr_apply", "adjoint_solve", "gradients",
-    "loss_and_gradients", "imex_rhs", "imex_march",
+    "loss_and_gradients", "imex_rhs", "imex_march", "hbs_compress", "hbs_dense", "hbs_apply",
+    "hbs_entries",
 ]
 
 
@@ -540,6 +546,118 @@ def hodlr_apply(H, x):
         lo, hi = hodlr_node(ng, L, t)
         y[lo:hi] += D @ x[lo:hi]
     return y
+
+
+# ---------------------------------------------------------------------------------------
+# O9  Nested-basis HBS compression from random samples (Sec. 2.4; Alg. 1)
+# ---------------------------------------------------------------------------------------
+
+def _null_basis(Om):
+    """Orthonormal basis of the null space of ``Om`` (``n x s``, ``n < s``): the trailing
+    ``s - n`` columns of the full orthogonal factor of the Householder QR of ``Om^T``."""
+    Q, _ = sla.qr(Om.T, mode="full")
+    return Q[:, Om.shape[0]:]
+
+
+def _col(X, k: int):
+    """``col(X, k)``: the leading ``k`` columns of the orthogonal factor of the column-pivoted
+    Householder QR of ``X`` (an orthonormal basis of ``k`` columns spanning most of range(X))."""
+    Q, _, _ = sla.qr(X, mode="economic", pivoting=True)
+    return Q[:, :k]
+
+
+def hbs_compress(Y, Z, Om, Psi, k: int, leaf: int):
+    """HBS (nested bases, weak admissibility) of ``S`` from ``Y = S Om`` and ``Z = S^T Psi``.
+
+    ``Om`` and ``Psi`` are ``ng x s`` Gaussian test matrices; the paper draws ``s = 3 k + q``
+    samples (Alg. 1).  The cluster tree is the balanced bisection of ``hodlr_node`` (shared by
+    rows and columns, Sec. 2.4).  Level by level from the leaves, every node ``tau`` with row set
+    of size ``n`` and samples ``(Y_t, Z_t, Om_t, Psi_t)`` (``n x s``) gets
+
+    * ``U = col(Y_t P, k)``, ``P`` an orthonormal basis of null(``Om_t``): ``Y_t P`` samples the
+      off-diagonal block row ``S(tau, tau^c)`` alone, since ``S(tau, tau) Om_t P = 0``;
+      ``V = col(Z_t P', k)`` likewise for the block column;
+    * ``D = (I - U U^T) Y_t Om_t^+ + U U^T ((I - V V^T) Z_t Psi_t^+)^T``, the part of the
+      diagonal block that the bases do not carry (``S_tt - U U^T S_tt V V^T`` when the
+      off-diagonal blocks have rank ``<= k``);
+    * the samples of the reduced matrix ``U^T (S - D) V`` for the next level up:
+      ``V^T Om_t``, ``U^T Psi_t``, ``U^T (Y_t - D Om_t)`` and ``V^T (Z_t - D^T Psi_t)``, a
+      parent's row set being its two children's ``k`` reduced rows, first child first.
+
+    The root keeps the reduced matrix itself, ``D_0 = Y_0 Om_0^+`` (``2k x 2k``; the whole block
+    when the tree has one level).  ``S = U_L (... U_1 D_0 V_1^T + D_1 ...) V_L^T + D_L`` with
+    block-diagonal ``U_l, V_l, D_l``: storage and apply cost are ``O(k N)``.
+    """
+    Y, Z, Om, Psi = (np.asarray(a, dtype=np.float64) for a in (Y, Z, Om, Psi))
+    ng, s = Y.shape
+    L = hodlr_levels(ng, leaf)
+    cur = []
+    for t in range(1 << L):
+        lo, hi = hodlr_node(ng, L, t)
+        cur.append((Y[lo:hi], Z[lo:hi], Om[lo:hi], Psi[lo:hi]))
+    levels = [None] * (L + 1)
+    for lev in range(L, 0, -1):
+        nodes, red = [], []
+        for (Yt, Zt, Ot, Pt) in cur:
+            if Yt.shape[0] + k > s:
+                raise ValueError("HBS: a node's row set plus k exceeds the sample count")
+            U = _col(Yt @ _null_basis(Ot), k)
+            V = _col(Zt @ _null_basis(Pt), k)
+            X1 = Yt @ np.linalg.pinv(Ot)
+            X2 = Zt @ np.linalg.pinv(Pt)
+            D = X1 - U @ (U.T @ X1) + U @ (U.T @ (X2.T - (X2.T @ V) @ V.T))
+            nodes.append((U, V, D))
+            red.append((U.T @ (Yt - D @ Ot), V.T @ (Zt - D.T @ Pt), V.T @ Ot, U.T @ Pt))
+        levels[lev] = nodes
+        cur = [tuple(np.vstack((a, b)) for a, b in zip(red[2 * t], red[2 * t + 1]))
+               for t in range(len(red) // 2)]
+    Y0, _, O0, _ = cur[0]
+    if Y0.shape[0] > s:
+        raise ValueError("HBS: the root's row set exceeds the sample count")
+    levels[0] = Y0 @ np.linalg.pinv(O0)
+    return dict(ng=ng, L=L, k=k, levels=levels)
+
+
+def hbs_dense(H):
+    """Expand an HBS representation: ``A_0 = D_0``, ``A_l = U_l A_{l-1} V_l^T + D_l``."""
+    A = H["levels"][0]
+    for lev in range(1, H["L"] + 1):
+        nodes = H["levels"][lev]
+        A = (sla.block_diag(*[U for U, _, _ in nodes]) @ A
+             @ sla.block_diag(*[V for _, V, _ in nodes]).T
+             + sla.block_diag(*[D for _, _, D in nodes]))
+    return A
+
+
+def hbs_apply(H, x, transpose: bool = False):
+    """``y = S_H x`` (or ``S_H^T x``) by the upward and downward passes over the tree (never
+    forms the dense matrix): ``x_t <- V^T x_t`` from the leaves up, ``y_0 = D_0 x_0`` at the
+    root, then ``y_t = D x_t + U (parent's y, rows of t)`` back down.  The transpose swaps the
+    roles of ``U`` and ``V`` and transposes every ``D``."""
+    ng, L, k, lv = H["ng"], H["L"], H["k"], H["levels"]
+    x = np.asarray(x, dtype=np.float64)
+    xs = [None] * (L + 1)
+    xs[L] = [x[slice(*hodlr_node(ng, L, t))] for t in range(1 << L)]
+    for lev in range(L, 0, -1):
+        red = [(U if transpose else V).T @ xt for (U, V, _), xt in zip(lv[lev], xs[lev])]
+        xs[lev - 1] = [np.concatenate((red[2 * t], red[2 * t + 1])) for t in range(len(red) // 2)]
+    ys = [(lv[0].T if transpose else lv[0]) @ xs[0][0]]
+    for lev in range(1, L + 1):
+        nxt = []
+        for t, ((U, V, D), xt) in enumerate(zip(lv[lev], xs[lev])):
+            slot = ys[t // 2][(t % 2) * k:(t % 2 + 1) * k]
+            nxt.append((D.T if transpose else D) @ xt + (V if transpose else U) @ slot)
+        ys = nxt
+    return np.concatenate(ys)
+
+
+def hbs_entries(H) -> int:
+    """Stored numbers of an HBS representation (leaves: ``n^2 + 2 n k``; inner nodes:
+    ``4 k^2 + 4 k^2``; root: ``4 k^2``)."""
+    tot = H["levels"][0].size
+    for lev in range(1, H["L"] + 1):
+        tot += sum(U.size + V.size + D.size for U, V, D in H["levels"][lev])
+    return int(tot)
 
 
 # ---------------------------------------------------------------------------------------

@@ -62,6 +62,12 @@ MUTATIONS = [
  ("O8 central difference without the 1/2", "U[_shifted(dim, n, d, -1)]) / (2.0 * h)", "U[_shifted(dim, n, d, -1)]) / h"),
  ("O8 convection term added", "f = f - np.asarray(vel[d])[_interior(dim, n)] * grad", "f = f + np.asarray(vel[d])[_interior(dim, n)] * grad"),
  ("O8 U_n / dt dropped", "f = U[_interior(dim, n)] / dt", "f = U[_interior(dim, n)] * 1.0"),
+ ("O9 null basis from the row-space columns", "return Q[:, Om.shape[0]:]", "return Q[:, :Om.shape[0]]"),
+ ("O9 D without the (I - U U^T) projection", "D = X1 - U @ (U.T @ X1) + U", "D = X1 + U"),
+ ("O9 reduced column samples with D instead of D^T", "V.T @ (Zt - D.T @ Pt)", "V.T @ (Zt - D @ Pt)"),
+ ("O9 reduced test matrices swapped", "V.T @ Ot, U.T @ Pt))", "U.T @ Ot, V.T @ Pt))"),
+ ("O9 apply takes the sibling's slot of the parent", "slot = ys[t // 2][(t % 2) * k:(t % 2 + 1) * k]", "slot = ys[t // 2][(1 - t % 2) * k:(2 - t % 2) * k]"),
+ ("O9 transposed apply keeps D untransposed", "nxt.append((D.T if transpose else D) @ xt", "nxt.append(D @ xt"),
  ("O8 one step fewer", "    for _ in range(nsteps):\n        u = lu.solve(imex_rhs(dim, n, u, vel, dt))", "    for _ in range(nsteps - 1):\n        u = lu.solve(imex_rhs(dim, n, u, vel, dt))"),
 ]
 

@@ -608,3 +608,96 @@ def test_o8_march_is_the_sequence_of_global_solves():
     um = O.imex_march(p, p["u0"], p["vel"], p["dt"], 3)
     assert np.abs(um - u).max() <= 1e-12 * np.abs(u).max()
     assert np.linalg.norm(um) < np.linalg.norm(p["u0"])
+
+
+def _random_hbs(ng, k, leaf, rng):
+    """A matrix that is exactly HBS of rank k on the bisection tree, built by the telescoping
+    recursion A_l = U_l A_{l-1} V_l^T + D_l from random orthonormal bases and random blocks."""
+    import scipy.linalg as sla
+    L = O.hodlr_levels(ng, leaf)
+    if L == 0:
+        return rng.standard_normal((ng, ng))
+
+    def orth(n):
+        return np.linalg.qr(rng.standard_normal((n, k)))[0]
+
+    A = rng.standard_normal((2 * k, 2 * k))
+    for lev in range(1, L + 1):
+        if lev == L:
+            sizes = [hi - lo for lo, hi in (O.hodlr_node(ng, L, t) for t in range(1 << L))]
+        else:
+            sizes = [2 * k] * (1 << lev)
+        A = (sla.block_diag(*[orth(n) for n in sizes]) @ A
+             @ sla.block_diag(*[orth(n) for n in sizes]).T
+             + sla.block_diag(*[rng.standard_normal((n, n)) for n in sizes]))
+    return A
+
+
+def _hbs_sigma_ref(S, k, leaf):
+    """max over tree nodes of sigma_{k+1} of the off-diagonal block row and column: no HBS of
+    rank k on this tree can be closer to S (Eckart-Young on each block row / column)."""
+    ng = S.shape[0]
+    L = O.hodlr_levels(ng, leaf)
+    worst = 0.0
+    for lev in range(1, L + 1):
+        for t in range(1 << lev):
+            lo, hi = O.hodlr_node(ng, lev, t)
+            rest = np.r_[0:lo, hi:ng]
+            for B in (S[lo:hi][:, rest], S[rest][:, lo:hi]):
+                sv = np.linalg.svd(B, compute_uv=False)
+                if len(sv) > k:
+                    worst = max(worst, sv[k])
+    return worst
+
+
+@pytest.mark.parametrize("ng,k,leaf", [(200, 6, 12), (137, 4, 8), (64, 8, 16), (9, 3, 12)])
+def test_p10_hbs_recovers_an_exact_hbs_matrix(ng, k, leaf):
+    """P10: from s = 3k + q Gaussian samples of a matrix that is exactly HBS of rank k, the
+    compression reproduces it to rounding (the defining property of sample-based HBS
+    compression, Sec. 2.4); apply and transposed apply equal the dense expansion; storage is
+    the O(kN) count of the format (leaves n^2 + 2nk, inner nodes 8k^2, root 4k^2)."""
+    rng = np.random.default_rng(ng + k)
+    S = _random_hbs(ng, k, leaf, rng)
+    s = 3 * k + 10
+    Om = rng.standard_normal((ng, s))
+    Psi = rng.standard_normal((ng, s))
+    H = O.hbs_compress(S @ Om, S.T @ Psi, Om, Psi, k, leaf)
+    assert np.linalg.norm(O.hbs_dense(H) - S) <= 1e-12 * np.linalg.norm(S)
+    x = rng.standard_normal(ng)
+    assert np.abs(O.hbs_apply(H, x) - S @ x).max() <= 1e-12 * np.abs(S).sum(1).max() * np.abs(x).max()
+    assert np.abs(O.hbs_apply(H, x, transpose=True) - S.T @ x).max() <= \
+        1e-12 * np.abs(S).sum(0).max() * np.abs(x).max()
+    L = H["L"]
+    if L == 0:
+        want = ng * ng
+    else:
+        leaves = [hi - lo for lo, hi in (O.hodlr_node(ng, L, t) for t in range(1 << L))]
+        want = sum(n * n + 2 * n * k for n in leaves) + 8 * k * k * ((1 << L) - 2) + 4 * k * k
+    assert O.hbs_entries(H) == want
+
+
+def test_p10_hbs_error_between_eckart_young_bounds():
+    """P10: on a transfer operator of a 2D double slab the HBS error lies between the best any
+    rank-k HBS on the tree can do (sigma_{k+1} of the worst block row or column) and a small
+    multiple of it, and falls as k grows."""
+    prob = I.make_problem("convdiff2d", n=128, w=16)
+    A, b = O.assemble(prob)
+    geo = O.slab_geometry(2, 128, 16)
+    facs = O.factor_local(A, geo)
+    Sp, Sn = O.transfer_blocks(A, geo, facs, slabs=[2])
+    S = Sn[0]
+    ng = S.shape[0]
+    nS = np.linalg.norm(S, 2)
+    rng = np.random.default_rng(11)
+    errs = []
+    for k in (4, 6, 8, 12):
+        s = 3 * k + 10
+        Om = rng.standard_normal((ng, s))
+        Psi = rng.standard_normal((ng, s))
+        H = O.hbs_compress(S @ Om, S.T @ Psi, Om, Psi, k, 2 * k)
+        err = np.linalg.norm(O.hbs_dense(H) - S, 2)
+        ref = _hbs_sigma_ref(S, k, 2 * k)
+        assert ref <= err * (1 + 1e-12) and err <= 30 * ref, (k, err / nS, ref / nS)
+        errs.append(err / nS)
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+    assert errs[-1] <= 1e-6
