@@ -208,7 +208,7 @@ def cpu_baseline(n=512):
             "sample": f"oracle dd_solve on the {n}x{n} instance of the workload (FP64, {dt:.1f} s)"}
 
 
-def cpu_leg(c2_prob, c2_u, verify=True, c4=None, c5_prob=None, ref_n=512):
+def cpu_leg(c2_prob, c2_u, verify=True, c4=None, c5_prob=None, ref_n=512, u_hbs=None):
     """The cpu_baseline leg: every use of the oracle in the GPU arm, on the host cores, after
     all GPU timing (rank 0, one GPU).
     * the oracle's FP64 DD solve timed on a bounded sample (``cpu_baseline``);
@@ -227,6 +227,9 @@ def cpu_leg(c2_prob, c2_u, verify=True, c4=None, c5_prob=None, ref_n=512):
         ver["rel_error_vs_oracle"] = float(np.linalg.norm(c2_u - ustar) / np.linalg.norm(ustar))
         ver["max_abs_error_vs_oracle"] = float(np.abs(c2_u - ustar).max() / np.abs(ustar).max())
         ver["oracle"] = f"global sparse solve O2 (SuperLU, FP64) of this instance, {time.perf_counter() - t0:.0f} s"
+        if u_hbs is not None:
+            out["hbs_rel_error_vs_oracle"] = float(np.linalg.norm(u_hbs.ravel() - ustar) /
+                                                   np.linalg.norm(ustar))
     out["verify"] = ver
     if c4 is not None:
         prob4, u4 = c4
@@ -383,6 +386,46 @@ def bench_direct(a, f, g, n, w, tol, peaks, src, solves=5):
             "refine_iters": {"direct": res[1][1]["refine_iters"], "gmres": res[0][1]["refine_iters"]},
             "gmres_iters": res[0][1]["gmres_iters"],
             "est_rel_error": {"direct": res[1][1]["est_rel_error"], "gmres": res[0][1]["est_rel_error"]}}
+
+
+def bench_hbs(a, f, g, n, w, peaks, src, ranks=(12, 16), oversample=10, solves=3):
+    """The nested-basis HBS operators (Sec. 2.4, Alg. 1: s = 3k + q samples) on the headline
+    workload in place of HODLR: compression time, stored bytes, the interface apply (time and
+    HBM roofline on its algorithmic bytes: the factors once plus the interface vectors) and the
+    solve (median of `solves` after the first).  Returns the section and the last rank's
+    solution (its error against the oracle is measured in the CPU leg)."""
+    import torch
+
+    from paper_2510_25991_gb300 import ddst as D
+    u = torch.empty((n - 1, n - 1), dtype=torch.float64, device="cuda")
+    nds, ng = n // w - 1, n - 1
+    tot_if = nds * ng
+    out = {"workload": f"convdiff2d n={n} w={w}: {2 * (nds - 1)} transfer operators of {ng} x {ng}, "
+                       f"mixed precision, fixed HBS rank k from 3k + {oversample} device-drawn samples, "
+                       f"leaves of 2k indices", "ranks": {}}
+    for k in ranks:
+        sol = D.Solver(dict(dim=2, n=n, w=w, a=a, b=(20.0, 10.0, 0.0)), precision="mixed")
+        sol.build_transfer()
+        sol.compress_hbs(k, oversample)
+        st, first = sol.solve(f, g, u)
+        ts, info = [], first
+        for _ in range(solves):
+            st, info = sol.solve(f, g, u)
+            ts.append(info["t_solve"])
+        ap_ms = D.ddst_time_apply(sol.ctx, False, 50)
+        sol.close()
+        alg = info["bytes_transfer"] + 24 * tot_if  # factors once; x read twice, y written
+        gbs = alg / (ap_ms / 1e3) / 1e9
+        out["ranks"][str(k)] = {
+            "compress_ms": info["t_compress"], "bytes_transfer": info["bytes_transfer"],
+            "apply_ms": ap_ms,
+            "apply_roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                               "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                               "algorithmic_bytes": alg, "peak_source": src},
+            "solve_ms": statistics.median(ts), "gmres_iters": info["gmres_iters"],
+            "refine_iters": info["refine_iters"], "est_rel_error": info["est_rel_error"]}
+    out["last_rank"] = ranks[-1]
+    return out, u.cpu().numpy()
 
 
 def bench_march(n=1024, w=32, steps=144):
@@ -554,6 +597,7 @@ def main():
     ap.add_argument("--no-direct", action="store_true",
                     help="skip the direct interface solver section")
     ap.add_argument("--no-march", action="store_true", help="skip the time-marching section")
+    ap.add_argument("--no-hbs", action="store_true", help="skip the HBS-operator section")
     ap.add_argument("--only-direct", action="store_true",
                     help="run only the direct-solver section on --n / --w (for profiling smaller cases)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner section")
@@ -789,6 +833,9 @@ def main():
         line["autotune"] = bench_autotune(a, f, g, n, w, args.tol)
     if rank == 0 and not args.no_direct:
         line["direct"] = bench_direct(a, f, g, n, w, args.tol, peaks, src)
+    u_hbs = None
+    if rank == 0 and not args.no_hbs:
+        line["hbs"], u_hbs = bench_hbs(a, f, g, n, w, peaks, src)
     if rank == 0 and not args.no_march:
         line["march"] = bench_march()
     c4_sol = c5_prob = None
@@ -801,11 +848,13 @@ def main():
             line["c5"] = c5
     if rank == 0 and ws == 1 and not args.no_cpu:
         leg = cpu_leg(prob, u_mixed, verify=not args.no_verify, c4=c4_sol, c5_prob=c5_prob,
-                      ref_n=args.ref_n or 512)
+                      ref_n=args.ref_n or 512, u_hbs=u_hbs)
         line["cpu_baseline"] = leg["cpu_baseline"]
         line["verify"] = leg["verify"]
         if "c4_certified_rel_error_bound" in leg:
             line["c4"]["certified_rel_error_bound"] = leg["c4_certified_rel_error_bound"]
+        if "hbs_rel_error_vs_oracle" in leg:
+            line["hbs"]["rel_error_vs_oracle"] = leg["hbs_rel_error_vs_oracle"]
         if "c5_oracle_median_problem" in leg:
             line["c5"]["oracle_median_problem"] = leg["c5_oracle_median_problem"]
     if rank == 0:

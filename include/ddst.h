@@ -224,6 +224,53 @@ ddst_status ddst_build_transfer(ddst_ctx* ctx);
  * matrix-free context: compression samples the explicit operators). */
 ddst_status ddst_compress(ddst_ctx* ctx, double tol);
 
+/* Compresses every S_{j,j'} into nested-basis HBS form (Sec. 2.4: weak admissibility, cluster
+ * tree shared by source and target interface, O(k N) storage and apply) from s = 3 rank +
+ * oversample Gaussian samples Y = S Omega and Z = S^T Psi per operator (Alg. 1), drawn on the
+ * device from options.seed.  Fixed rank `rank` per tree node, leaves of at most 2 rank indices.
+ * Per node: U = the leading `rank` columns of the column-pivoted QR of Y_t P (P an orthonormal
+ * basis of the null space of the node's rows of Omega), V likewise from Z and Psi, the diagonal
+ * remainder D = (I - U U^T) Y_t Omega_t^+ + U U^T ((I - V V^T) Z_t Psi_t^+)^T, and the reduced
+ * samples passed to the parent; the root keeps the reduced 2 rank x 2 rank matrix.  Exact (to
+ * rounding) when every off-diagonal block row and column of the tree has rank <= `rank`.  The
+ * node algebra runs in the working precision (FP32 in DDST_MIXED).  Solves then apply the HBS
+ * operators; ddst_compress (either tol) or ddst_build_transfer drops them.  Requires
+ * ddst_build_transfer.  Errors: STATE, OOM, CUDA, INVALID_ARG (rank outside 1..32, oversample
+ * < 0 or 3 rank + oversample > 96), NOT_IMPLEMENTED (a context that applies any operator
+ * matrix-free). */
+ddst_status ddst_compress_hbs(ddst_ctx* ctx, int rank, int oversample);
+
+/* A dense operator compressed on its own into HBS form (the algorithm of ddst_compress_hbs). */
+typedef struct ddst_hbs ddst_hbs;
+
+/* Compresses the dense ng x ng row-major FP64 host matrix S into HBS form with fixed rank
+ * `rank`, `nsamples` samples (>= 3 rank, <= 96) and leaves of at most `leaf` (<= 64) indices of
+ * the balanced bisection tree (node t of level l covers [t ng / 2^l, (t+1) ng / 2^l)).  omega
+ * and psi: the ng x nsamples row-major FP64 host test matrices, or both NULL to draw them on the
+ * device.  precision: DDST_FP64 or DDST_MIXED (FP32 storage and node algebra).  The caller
+ * keeps its arrays; *out is released with ddst_hbs_destroy.  The paper compresses the transfer
+ * operators only (this entry point exposes the same compression for any dense operator).
+ * Errors: INVALID_ARG (NULL or device pointers, bad sizes, a leaf's size plus rank above
+ * nsamples), OOM, CUDA. */
+ddst_status ddst_hbs_create(const double* S, int64_t ng, int rank, int nsamples, int leaf,
+                            const double* omega, const double* psi, int precision,
+                            ddst_hbs** out);
+
+/* y = S_H x (transpose = 0) or S_H^T x (transpose = 1): the upward pass (V^T x per leaf, then
+ * the inner levels), the root, and the downward pass (D x + U y_parent).  x, y: ng values, host
+ * or device arrays; returns after y is written.  Errors: INVALID_ARG, CUDA. */
+ddst_status ddst_hbs_apply(ddst_hbs* h, const double* x, double* y, int transpose);
+
+/* The dense expansion of S_H, row-major ng x ng into a host array.  Errors: INVALID_ARG, CUDA. */
+ddst_status ddst_hbs_expand(ddst_hbs* h, double* out);
+
+/* Tree depth L (levels below the root) and stored numbers of the representation (leaves
+ * n^2 + 2 n k, inner nodes 8 k^2, root 4 k^2).  Either output may be NULL.  Errors: INVALID_ARG. */
+ddst_status ddst_hbs_stats(const ddst_hbs* h, int* levels, int64_t* entries);
+
+/* Releases a handle from ddst_hbs_create (NULL is ignored). */
+void ddst_hbs_destroy(ddst_hbs* h);
+
 /* Solves for one problem (contexts made by ddst_setup): equivalent loads (Sec. 2.2, Eq.
  * (equilib1)), GMRES on (I - K) u_Gamma = fhat, volume reconstruction, then FP64 residual
  * refinement u += DD(b - A u) until the error bound rho/(1-rho) ||correction|| (rho: observed
@@ -274,13 +321,13 @@ ddst_status ddst_solve_adjoint_batch(ddst_ctx* ctx, const double* const* dL_du,
 ddst_status ddst_interface_trace(ddst_ctx* ctx, int prob, double* uG);
 
 /* Copies S_{j,j-1} (side = -1) or S_{j,j+1} (side = +1) of problem prob, slab j (1-based),
- * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR if compressed) into
+ * as a dense row-major n_Gamma x n_Gamma FP64 matrix (expanded from HODLR or HBS if compressed) into
  * a host or device array.  Errors: INVALID_ARG (bad prob, j or side; no such block at the
  * ends), STATE (transfer operators not built), NOT_IMPLEMENTED (matrix-free context), CUDA. */
 ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* out);
 
 /* y = (I - K) x (transpose = 0) or y = (I - K)^T x (transpose = 1) for problem prob with the
- * current (dense or HODLR) operators (Sec. 2.2, Eq. (modelS)); x and y hold N_ds * n_Gamma
+ * current (dense, HODLR or HBS) operators (Sec. 2.2, Eq. (modelS)); x and y hold N_ds * n_Gamma
  * values, host or device arrays; returns after y is written (synchronizes the context stream).
  * Errors: INVALID_ARG, STATE (transfer operators not built), CUDA. */
 ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, double* y,
@@ -295,7 +342,7 @@ ddst_status ddst_apply_interface(ddst_ctx* ctx, int prob, const double* x, doubl
 ddst_status ddst_time_apply(ddst_ctx* ctx, int transpose, int reps, float* ms);
 
 /* Sizes of problem prob: number of double slabs n_ds, interface length n_gamma, and the
- * largest HODLR rank of the context (0 while dense).  Any output may be NULL.
+ * largest HODLR rank of the context (the HBS rank after ddst_compress_hbs; 0 while dense).  Any output may be NULL.
  * Errors: INVALID_ARG (NULL ctx or bad prob; message via ddst_last_error(NULL), since ctx is
  * const). */
 ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamma,

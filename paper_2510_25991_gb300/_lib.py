@@ -71,6 +71,13 @@ SIGNATURES = {
                                    C.POINTER(_P)]),
     "ddst_build_transfer": (C.c_int, [_P]),
     "ddst_compress": (C.c_int, [_P, C.c_double]),
+    "ddst_compress_hbs": (C.c_int, [_P, C.c_int, C.c_int]),
+    "ddst_hbs_create": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int,
+                                  C.POINTER(_P)]),
+    "ddst_hbs_apply": (C.c_int, [_P, _P, _P, C.c_int]),
+    "ddst_hbs_expand": (C.c_int, [_P, _P]),
+    "ddst_hbs_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "ddst_hbs_destroy": (None, [_P]),
     "ddst_solve": (C.c_int, [_P, _P, _P, _P, C.POINTER(ddst_info)]),
     "ddst_solve_batch": (C.c_int, [_P, _PP, _PP, _PP, C.POINTER(ddst_info)]),
     "ddst_march": (C.c_int, [_P, C.c_int, C.c_double, _PP, _PP, _PP, C.POINTER(ddst_info)]),

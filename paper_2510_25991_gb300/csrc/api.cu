@@ -20,6 +20,7 @@
 
 #include "../../include/ddst.h"
 #include "bcr.cuh"
+#include "hbs.cuh"
 #include "hodlr.cuh"
 #include "kernels.cuh"
 
@@ -68,6 +69,17 @@ int norm_blocks(int nprob) { return std::max(8, std::min(256, 1024 / std::max(np
 
 }  // namespace
 
+// A dense operator compressed on its own into HBS form (the standalone entry points).
+struct ddst_hbs {
+  ddst::HbsSet H;
+  int prec = 0;
+  int64_t ng = 0;
+  cudaStream_t st = nullptr;
+  void* S = nullptr;
+  double* x = nullptr;
+  double* y = nullptr;
+};
+
 struct ddst_ctx {
   int nprob = 0;
   int prec = DDST_MIXED;
@@ -101,7 +113,8 @@ struct ddst_ctx {
   int ldh = 0;
   int nchunk = 0;
   HodlrSet hodlr;  // compressed operators (when compressed)
-  int state = 0;   // 1 factored, 2 transfer formed, 3 compressed
+  HbsSet hbs;      // nested-basis operators (when compressed into HBS form)
+  int state = 0;   // 1 factored, 2 transfer formed, 3 HODLR, 4 HBS
   bool have_solution = false;
   std::vector<void*> owned;
   std::string err;
@@ -782,6 +795,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   if (ctx->matfree) {  // S is applied through the local factors: nothing to form
     ctx->t_transfer = 0.f;
     ctx->hodlr.clear();
+    ctx->hbs.release();
     drop_graphs(ctx);
     ctx->state = 2;
     return DDST_OK;
@@ -841,6 +855,7 @@ ddst_status build_transfer_impl(ddst_ctx* ctx) {
   ddst_status s = check_status(ctx, nullptr);
   if (s != DDST_OK) return s;
   ctx->hodlr.clear();
+  ctx->hbs.release();
   drop_graphs(ctx);
   ctx->state = 2;
   return DDST_OK;
@@ -956,7 +971,9 @@ void apply_interface_T(ddst_ctx* ctx, const double* x, double* y, int transpose,
   }
   // explicit operators (their apply also writes the matrix-free classes' interfaces, as if K
   // were zero there), then the matrix-free classes overwrite their own interfaces
-  if (ctx->state == 3)
+  if (ctx->state == 4)
+    hbs_apply<T>(ctx->hbs, x, y, transpose, st, kdev, kstride);
+  else if (ctx->state == 3)
     hodlr_apply<T>(ctx->hodlr, ctx->d_slabs, ctx->d_probs, (int)ctx->slabs.size(), x, y, transpose,
                    st, kdev, kstride);
   else
@@ -1359,8 +1376,9 @@ void fill_info(ddst_ctx* ctx, const SolveStats& ss, float ms, ddst_info* info) {
   info->bytes_factors = (int64_t)((5 + (ctx->use_tc ? 4 : 0)) * ctx->fac_elems +
                                   ctx->fac_big_elems + ctx->pack_elems) * (int64_t)ctx->esz;
   info->bytes_transfer = ctx->matfree ? 0
-                         : ctx->state == 3 ? ctx->hodlr.bytes : ctx->s_elems * (int64_t)ctx->esz;
-  info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+                         : ctx->state == 3 ? ctx->hodlr.bytes
+                         : ctx->state == 4 ? ctx->hbs.bytes : ctx->s_elems * (int64_t)ctx->esz;
+  info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : ctx->state == 4 ? ctx->hbs.k : 0;
   info->fail_slab = -1;
   info->fail_block = -1;
   info->factor_chunks = ctx->factor_chunks;
@@ -1571,7 +1589,7 @@ ddst_status solve_adjoint_impl(ddst_ctx* ctx, const double* const* dLdu, double*
     info->t_factor = ctx->t_factor;
     info->t_transfer = ctx->t_transfer;
     info->t_compress = ctx->t_compress;
-    info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+    info->max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : ctx->state == 4 ? ctx->hbs.k : 0;
     info->fail_slab = info->fail_block = -1;
   }
   if (info) info->t_solve += recompute_ms;
@@ -1690,6 +1708,7 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
                 "compression samples the explicit transfer operators; this context applies them "
                 "matrix-free (explicit_S = 0, or blocks larger than 128)");
   drop_graphs(ctx);
+  ctx->hbs.release();
   if (!(tol > 0.0)) {
     ctx->hodlr.clear();
     ctx->state = 2;
@@ -1709,6 +1728,153 @@ ddst_status ddst_compress(ddst_ctx* ctx, double tol) {
                 "compress: %s", msg.c_str());
   ctx->state = 3;
   return DDST_OK;
+}
+
+ddst_status ddst_compress_hbs(ddst_ctx* ctx, int rank, int oversample) {
+  if (!ctx) return fail(nullptr, DDST_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->state < 2) return fail(ctx, DDST_ERR_STATE, "ddst_build_transfer has not completed");
+  if (ctx->matfree || ctx->mf_any)
+    return fail(ctx, DDST_ERR_NOT_IMPLEMENTED,
+                "HBS compression samples the explicit transfer operators; this context applies "
+                "some of them matrix-free");
+  if (rank < 1 || rank > 32 || oversample < 0 || 3 * rank + oversample > 96)
+    return fail(ctx, DDST_ERR_INVALID_ARG,
+                "rank %d, oversample %d: need 1 <= rank <= 32 and 3 rank + oversample <= 96", rank,
+                oversample);
+  drop_graphs(ctx);
+  ctx->hodlr.clear();
+  ctx->hbs.release();
+  ctx->state = 2;
+  std::vector<HbsInput> in;
+  for (size_t si = 0; si < ctx->slabs.size(); ++si) {
+    const SlabDesc& s = ctx->slabs[si];
+    const ProbDesc& P = ctx->probs[s.prob];
+    for (int side = -1; side <= 1; side += 2) {
+      const int64_t off = side < 0 ? s.sp_off : s.sn_off;
+      if (off < 0) continue;
+      in.push_back(HbsInput{(const char*)ctx->S + off * (int64_t)ctx->esz, P.ng, nullptr, nullptr,
+                            s.if_off + side * P.ng, s.if_off, (int)si, side});
+    }
+  }
+  std::vector<std::pair<int64_t, int64_t>> bare;  // a single interface: K = 0 there
+  for (int q = 0; q < ctx->nprob; ++q)
+    if (ctx->probs[q].nds == 1) bare.push_back({ctx->probs[q].if_off, ctx->probs[q].ng});
+  Timer tm(ctx->stream);
+  std::string msg;
+  const int s = 3 * rank + oversample;
+  int rc = in.empty() ? 0
+           : ctx->prec == DDST_FP64
+               ? hbs_build<double>(ctx->hbs, in, bare, rank, s, 2 * rank, ctx->opt.seed, ctx->stream, msg)
+               : hbs_build<float>(ctx->hbs, in, bare, rank, s, 2 * rank, ctx->opt.seed, ctx->stream, msg);
+  ctx->t_compress = tm.stop();
+  if (rc != 0)
+    return fail(ctx, rc == 2 ? DDST_ERR_OOM : rc == 3 ? DDST_ERR_INVALID_ARG : DDST_ERR_CUDA,
+                "compress_hbs: %s", msg.c_str());
+  if (in.empty()) return fail(ctx, DDST_ERR_INVALID_ARG, "compress_hbs: no transfer operators");
+  ctx->state = 4;
+  return DDST_OK;
+}
+
+ddst_status ddst_hbs_create(const double* S, int64_t ng, int rank, int nsamples, int leaf,
+                            const double* omega, const double* psi, int precision,
+                            ddst_hbs** out) {
+  if (!out) return fail(nullptr, DDST_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!S || ng < 1) return fail(nullptr, DDST_ERR_INVALID_ARG, "S is NULL or ng < 1");
+  if ((omega == nullptr) != (psi == nullptr))
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "omega and psi are both given or both NULL");
+  if (precision != DDST_FP64 && precision != DDST_MIXED)
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "precision must be DDST_FP64 or DDST_MIXED");
+  if (is_device_ptr(S) || (omega && (is_device_ptr(omega) || is_device_ptr(psi))))
+    return fail(nullptr, DDST_ERR_INVALID_ARG, "S, omega and psi are host arrays");
+  ddst_hbs* h = new ddst_hbs();
+  h->prec = precision;
+  h->ng = ng;
+  const size_t esz = precision == DDST_FP64 ? 8 : 4;
+  const size_t nbytes = esz * (size_t)(ng * ng);
+  cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&h->S, nbytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->x, sizeof(double) * ng);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->y, sizeof(double) * ng);
+  if (e != cudaSuccess) {
+    ddst_hbs_destroy(h);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? DDST_ERR_OOM : DDST_ERR_CUDA, "%s",
+                cudaGetErrorString(e));
+  }
+  // row-major FP64 input -> column-major working precision
+  std::vector<double> cm64;
+  std::vector<float> cm32;
+  if (esz == 8) cm64.resize((size_t)(ng * ng)); else cm32.resize((size_t)(ng * ng));
+  for (int64_t r = 0; r < ng; ++r)
+    for (int64_t c = 0; c < ng; ++c) {
+      const double v = S[r * ng + c];
+      if (esz == 8) cm64[c * ng + r] = v; else cm32[c * ng + r] = (float)v;
+    }
+  e = cudaMemcpyAsync(h->S, esz == 8 ? (const void*)cm64.data() : (const void*)cm32.data(), nbytes,
+                      cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    ddst_hbs_destroy(h);
+    return fail(nullptr, DDST_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  std::vector<HbsInput> in{HbsInput{h->S, ng, omega, psi, 0, 0, 0, 0}};
+  std::string msg;
+  const int rc = esz == 8
+                     ? hbs_build<double>(h->H, in, {}, rank, nsamples, leaf, 1234, h->st, msg)
+                     : hbs_build<float>(h->H, in, {}, rank, nsamples, leaf, 1234, h->st, msg);
+  if (rc != 0) {
+    ddst_hbs_destroy(h);
+    return fail(nullptr, rc == 2 ? DDST_ERR_OOM : rc == 3 ? DDST_ERR_INVALID_ARG : DDST_ERR_CUDA,
+                "hbs_create: %s", msg.c_str());
+  }
+  *out = h;
+  return DDST_OK;
+}
+
+ddst_status ddst_hbs_apply(ddst_hbs* h, const double* x, double* y, int transpose) {
+  if (!h || !x || !y) return fail(nullptr, DDST_ERR_INVALID_ARG, "NULL argument");
+  const size_t nb = sizeof(double) * (size_t)h->ng;
+  const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+  cudaError_t e = cudaMemcpyAsync(h->x, x, nb, dx ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  h->st);
+  if (e != cudaSuccess) return fail(nullptr, DDST_ERR_CUDA, "%s", cudaGetErrorString(e));
+  if (h->prec == DDST_FP64)
+    hbs_apply<double>(h->H, h->x, h->y, (transpose ? 1 : 0) | 2, h->st);
+  else
+    hbs_apply<float>(h->H, h->x, h->y, (transpose ? 1 : 0) | 2, h->st);
+  e = cudaMemcpyAsync(y, h->y, nb, dy ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, DDST_ERR_CUDA, "%s", cudaGetErrorString(e));
+  return DDST_OK;
+}
+
+ddst_status ddst_hbs_expand(ddst_hbs* h, double* out) {
+  if (!h || !out) return fail(nullptr, DDST_ERR_INVALID_ARG, "NULL argument");
+  if (is_device_ptr(out)) return fail(nullptr, DDST_ERR_INVALID_ARG, "out is a host array");
+  const int64_t ng = h->ng;
+  std::vector<double> cm((size_t)(ng * ng));
+  if (hbs_expand(h->H, 0, cm.data(), h->st)) return fail(nullptr, DDST_ERR_CUDA, "expand failed");
+  for (int64_t c = 0; c < ng; ++c)
+    for (int64_t r = 0; r < ng; ++r) out[r * ng + c] = cm[c * ng + r];
+  return DDST_OK;
+}
+
+ddst_status ddst_hbs_stats(const ddst_hbs* h, int* levels, int64_t* entries) {
+  if (!h) return fail(nullptr, DDST_ERR_INVALID_ARG, "NULL handle");
+  if (levels) *levels = h->H.blocks.empty() ? 0 : h->H.blocks[0].L;
+  if (entries) *entries = h->H.f_elems;
+  return DDST_OK;
+}
+
+void ddst_hbs_destroy(ddst_hbs* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  h->H.release();
+  for (void* p : {h->S, (void*)h->x, (void*)h->y})
+    if (p) cudaFree(p);
+  if (h->st) cudaStreamDestroy(h->st);
+  delete h;
 }
 
 ddst_status ddst_solve_batch(ddst_ctx* ctx, const double* const* f, const double* const* g,
@@ -1795,6 +1961,12 @@ ddst_status ddst_get_transfer(ddst_ctx* ctx, int prob, int j, int side, double* 
   if (ctx->state == 3) {
     int rc = hodlr_expand(ctx->hodlr, P.slab0 + j - 1, side, ctx->esz, cm.data(), ctx->stream);
     if (rc) return fail(ctx, DDST_ERR_CUDA, "expand failed");
+  } else if (ctx->state == 4) {
+    int b = -1;
+    for (size_t q = 0; q < ctx->hbs.blk_slab.size(); ++q)
+      if (ctx->hbs.blk_slab[q] == P.slab0 + j - 1 && ctx->hbs.blk_side[q] == side) b = (int)q;
+    if (b < 0 || hbs_expand(ctx->hbs, b, cm.data(), ctx->stream))
+      return fail(ctx, DDST_ERR_CUDA, "expand failed");
   } else if (ctx->esz == 8) {
     CK(cudaMemcpyAsync(cm.data(), (double*)ctx->S + off, sizeof(double) * ng * ng,
                        cudaMemcpyDeviceToHost, ctx->stream));
@@ -1897,7 +2069,8 @@ ddst_status ddst_query(const ddst_ctx* ctx, int prob, int* n_ds, int64_t* n_gamm
   const ProbDesc& P = ctx->probs[prob];
   if (n_ds) *n_ds = P.nds;
   if (n_gamma) *n_gamma = P.ng;
-  if (max_rank) *max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : 0;
+  if (max_rank)
+    *max_rank = ctx->state == 3 ? ctx->hodlr.max_rank : ctx->state == 4 ? ctx->hbs.k : 0;
   return DDST_OK;
 }
 
@@ -1918,6 +2091,7 @@ void ddst_destroy(ddst_ctx* ctx) {
   for (cudaEvent_t ev : ctx->big_ev)
     if (ev) cudaEventDestroy(ev);
   ctx->hodlr.release();
+  ctx->hbs.release();
   for (void* p : ctx->owned) cudaFree(p);
   delete ctx;
 }

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["DDSTError", "ddst_options_default", "ddst_setup", "ddst_setup_batch",
-           "ddst_build_transfer", "ddst_compress", "ddst_solve", "ddst_solve_batch", "ddst_march",
+           "ddst_build_transfer", "ddst_compress", "ddst_compress_hbs", "HBS", "ddst_solve", "ddst_solve_batch", "ddst_march",
            "ddst_solve_adjoint", "ddst_solve_adjoint_batch", "ddst_interface_trace",
            "ddst_get_transfer", "ddst_apply_interface", "ddst_query", "ddst_get_precision",
            "ddst_time_apply", "ddst_get_options", "ddst_solve_interface",
@@ -144,6 +144,71 @@ def ddst_build_transfer(ctx):
 def ddst_compress(ctx, tol):
     lib = L.load()
     _check(lib, ctx, lib.ddst_compress(ctx, float(tol)))
+
+
+def ddst_compress_hbs(ctx, rank, oversample=10):
+    """Nested-basis HBS form of every transfer operator, rank ``rank`` from ``3 rank +
+    oversample`` Gaussian samples (Sec. 2.4, Alg. 1)."""
+    lib = L.load()
+    _check(lib, ctx, lib.ddst_compress_hbs(ctx, int(rank), int(oversample)))
+
+
+class HBS:
+    """A dense operator compressed on its own into HBS form (``ddst_hbs_create``).
+
+    ``S``: ng x ng float64 NumPy array; ``omega``, ``psi``: ng x nsamples float64 NumPy arrays
+    or None (drawn on the device); ``precision``: "fp64" or "mixed"."""
+
+    def __init__(self, S, rank, nsamples=None, leaf=None, omega=None, psi=None, precision="fp64"):
+        lib = L.load()
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        ng = S.shape[0]
+        if S.shape != (ng, ng):
+            raise ValueError("S must be square")
+        nsamples = 3 * rank + 10 if nsamples is None else int(nsamples)
+        leaf = 2 * rank if leaf is None else int(leaf)
+        keep = [S]
+        po = pp = None
+        if omega is not None or psi is not None:
+            omega = np.ascontiguousarray(omega, dtype=np.float64)
+            psi = np.ascontiguousarray(psi, dtype=np.float64)
+            if omega.shape != (ng, nsamples) or psi.shape != (ng, nsamples):
+                raise ValueError("omega and psi must be ng x nsamples")
+            keep += [omega, psi]
+            po, pp = omega.ctypes.data, psi.ctypes.data
+        self.ng = ng
+        self.h = C.c_void_p()
+        st = lib.ddst_hbs_create(S.ctypes.data, ng, int(rank), nsamples, leaf, po, pp,
+                                 _PRECISIONS[precision], C.byref(self.h))
+        _check(lib, None, st)
+
+    def apply(self, x, y, transpose=False):
+        lib = L.load()
+        _check(lib, None, lib.ddst_hbs_apply(self.h, _ptr(x), _ptr(y), int(bool(transpose))))
+
+    def dense(self):
+        lib = L.load()
+        out = np.empty((self.ng, self.ng))
+        _check(lib, None, lib.ddst_hbs_expand(self.h, out.ctypes.data))
+        return out
+
+    def stats(self):
+        """(tree depth L, stored numbers)."""
+        lib = L.load()
+        lv, ne = C.c_int(), C.c_int64()
+        _check(lib, None, lib.ddst_hbs_stats(self.h, C.byref(lv), C.byref(ne)))
+        return lv.value, ne.value
+
+    def close(self):
+        if self.h:
+            L.load().ddst_hbs_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ddst_solve(ctx, f, g, u, raise_on_error=True):
@@ -381,6 +446,10 @@ class Solver:
 
     def compress(self, tol):
         ddst_compress(self.ctx, tol)
+        return self
+
+    def compress_hbs(self, rank, oversample=10):
+        ddst_compress_hbs(self.ctx, rank, oversample)
         return self
 
     def solve(self, f, g, u, **kw):
