@@ -2,7 +2,8 @@
 // telescoping apply (Sec. 2.4; Alg. 1: s = 3k + q Gaussian samples Y = S Omega, Z = S^T Psi).
 //
 // Compression, level by level from the leaves of the bisection tree shared by rows and columns:
-//   k_hbs_gen    : Gaussian test matrices Omega, Psi (counter-based, per block)
+//   k_hbs_gen    : Gaussian test matrices Omega, Psi (counter-based, per block; FP32 arithmetic
+//                  for FP32 samples)
 //   k_hbs_sample : Y = S Omega and Z = S^T Psi (64-row tiles, 32-column chunks in shared memory)
 //   k_hbs_node   : one CTA per tree node.  In shared memory: Householder QR of Omega_t^T applied
 //                  to Y_t^T (its trailing rows are Y_t P with P an orthonormal null-space basis
@@ -12,9 +13,11 @@
 //                  Psi_t^+)^T; the reduced samples V^T Omega_t, U^T Psi_t, U^T (Y_t - D Omega_t)
 //                  and V^T (Z_t - D^T Psi_t) written as the parent's rows.  The root keeps
 //                  D_0 = Y_0 Omega_0^+.
-// Apply (three launches): k_hbs_up_leaf (V^T x per leaf), k_hbs_tree (one CTA per block: the
-// inner levels up, the root, the inner levels down), k_hbs_down_leaf (one CTA per output leaf:
-// D x + U y_parent of both blocks writing there, combined into (I - K) x or K x).
+// Apply (three launches; the tree is cut three levels above the leaves): k_hbs_up (one CTA per
+// subtree below the cut: V^T x of its leaves and inner nodes), k_hbs_top (one CTA per block: the
+// levels above the cut up, the root, and down), k_hbs_down (one CTA per subtree of an output
+// interface: y of its inner nodes, then D x + U g of its leaves for both blocks writing there,
+// combined into (I - K) x or K x).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +49,21 @@ __device__ __forceinline__ double gauss_at(uint64_t seed, int blk, int which, in
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
+// The same in single precision (24-bit uniforms, FP32 logarithm and cosine) for FP32 samples.
+__device__ __forceinline__ float gauss_at_f(uint64_t seed, int blk, int which, int64_t e) {
+  const uint64_t base = mix64(seed ^ mix64(((uint64_t)(uint32_t)blk << 2) | (uint64_t)which));
+  const uint64_t a = mix64(base + 2 * (uint64_t)e), b = mix64(base + 2 * (uint64_t)e + 1);
+  const float u1 = ((float)(a >> 40) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);           // [0, 1)
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+template <typename T>
+__device__ __forceinline__ T gauss_t(uint64_t seed, int blk, int which, int64_t e) {
+  if constexpr (sizeof(T) == 4) return gauss_at_f(seed, blk, which, e);
+  else return static_cast<T>(gauss_at(seed, blk, which, e));
+}
+
 struct SampBlk {     // one block of the sampling step
   const void* S;     // column-major ng x ng
   int64_t ng;
@@ -67,8 +85,8 @@ __global__ void k_hbs_gen(const SampBlk* __restrict__ sb, T* __restrict__ Om, T*
   const int64_t tot = b.ng * s;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
-    Om[b.row0 * s + e] = static_cast<T>(gauss_at(seed, blockIdx.y, 0, e));
-    Ps[b.row0 * s + e] = static_cast<T>(gauss_at(seed, blockIdx.y, 1, e));
+    Om[b.row0 * s + e] = gauss_t<T>(seed, blockIdx.y, 0, e);
+    Ps[b.row0 * s + e] = gauss_t<T>(seed, blockIdx.y, 1, e);
   }
 }
 
@@ -194,25 +212,47 @@ __device__ T house_warp(T* x, int m) {
   return (beta - alpha) / beta;
 }
 
-// Applies H = I - tau [1; v] [1; v]^T (v below the first entry of `v`, length m) to column c.
+// Applies H = I - tau [1; v] [1; v]^T (v below the first entry of `v`, length m) to columns
+// c0 .. ncol-1 of A (leading dimension lda; each column's segment starts at A + c lda, aligned
+// with v).  Four threads per column (a quarter of the rows each, combined by shuffles within the
+// group), every column at once.
 template <typename T>
-__device__ void house_apply_warp(const T* v, T tau, T* c, int m) {
-  const int lane = threadIdx.x & 31;
-  T w = T(0);
-  for (int i = 1 + lane; i < m; i += 32) w += v[i] * c[i];
-  w = warp_sum(w);
-  w = (w + c[0]) * tau;
-  __syncwarp();
-  for (int i = 1 + lane; i < m; i += 32) c[i] -= w * v[i];
-  if (lane == 0) c[0] -= w;
-  __syncwarp();
+__device__ void house_apply_cols(const T* v, T tau, T* A, int64_t lda, int c0, int ncol, int m) {
+  const int sub = threadIdx.x & 3;
+  const unsigned gmask = 0xFu << (threadIdx.x & 28);
+  for (int c = c0 + (threadIdx.x >> 2); c < ncol; c += blockDim.x >> 2) {
+    T* col = A + (int64_t)c * lda;
+    T w = T(0);
+    for (int i = 1 + sub; i < m; i += 4) w += v[i] * col[i];
+    w += __shfl_xor_sync(gmask, w, 1);
+    w += __shfl_xor_sync(gmask, w, 2);
+    w = (w + col[0]) * tau;
+    __syncwarp(gmask);
+    for (int i = 1 + sub; i < m; i += 4) col[i] -= w * v[i];
+    if (sub == 0) col[0] -= w;
+  }
+}
+
+// Squared norms of rows j .. n-1 of columns c0 .. ncol-1 of A (leading dimension lda).
+template <typename T>
+__device__ void col_norms(const T* A, int64_t lda, int j, int n, int c0, int ncol, T* nrm) {
+  const int sub = threadIdx.x & 3;
+  const unsigned gmask = 0xFu << (threadIdx.x & 28);
+  for (int c = c0 + (threadIdx.x >> 2); c < ncol; c += blockDim.x >> 2) {
+    const T* col = A + (int64_t)c * lda;
+    T ss = T(0);
+    for (int i = j + sub; i < n; i += 4) ss += col[i] * col[i];
+    ss += __shfl_xor_sync(gmask, ss, 1);
+    ss += __shfl_xor_sync(gmask, ss, 2);
+    if (sub == 0) nrm[c] = ss;
+  }
 }
 
 // Householder QR of the first n columns of W (s x ncol, ld s), every reflector applied to the
 // other columns as it is formed.  R ends in the upper triangle of the first n columns.
 template <typename T>
 __device__ void qr_front(T* W, int s, int n, int ncol, T* tau) {
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5;
   for (int j = 0; j < n; ++j) {
     if (warp == 0) {
       const T t = house_warp(W + (int64_t)j * s + j, s - j);
@@ -220,9 +260,7 @@ __device__ void qr_front(T* W, int s, int n, int ncol, T* tau) {
     }
     __syncthreads();
     const T t = tau[j];
-    if (t != T(0))
-      for (int c = j + 1 + warp; c < ncol; c += nw)
-        house_apply_warp(W + (int64_t)j * s + j, t, W + (int64_t)c * s + j, s - j);
+    if (t != T(0)) house_apply_cols(W + (int64_t)j * s + j, t, W + j, s, j + 1, ncol, s - j);
     __syncthreads();
   }
 }
@@ -245,15 +283,10 @@ __device__ void pinv_product(const T* W, int s, int n, T* X) {
 // Q (n x k, ld n).  Pivot: the largest remaining partial column norm (first on ties).
 template <typename T>
 __device__ void qrcp_basis(T* G, int n, int r, int k, T* tau, T* nrm, T* Q) {
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ int piv;
   for (int j = 0; j < k; ++j) {
-    for (int c = j + warp; c < r; c += nw) {
-      T ss = T(0);
-      for (int i = j + lane; i < n; i += 32) ss += G[(int64_t)c * n + i] * G[(int64_t)c * n + i];
-      ss = warp_sum(ss);
-      if (lane == 0) nrm[c] = ss;
-    }
+    col_norms(G, n, j, n, j, r, nrm);
     __syncthreads();
     if (threadIdx.x == 0) {
       int p = j;
@@ -276,9 +309,7 @@ __device__ void qrcp_basis(T* G, int n, int r, int k, T* tau, T* nrm, T* Q) {
     }
     __syncthreads();
     const T t = tau[j];
-    if (t != T(0))
-      for (int c = j + 1 + warp; c < r; c += nw)
-        house_apply_warp(G + (int64_t)j * n + j, t, G + (int64_t)c * n + j, n - j);
+    if (t != T(0)) house_apply_cols(G + (int64_t)j * n + j, t, G + j, n, j + 1, r, n - j);
     __syncthreads();
   }
   // Q = H_0 ... H_{k-1} [I_k; 0]
@@ -289,9 +320,7 @@ __device__ void qrcp_basis(T* G, int n, int r, int k, T* tau, T* nrm, T* Q) {
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
     const T t = tau[j];
-    if (t != T(0))
-      for (int c = warp; c < k; c += nw)
-        house_apply_warp(G + (int64_t)j * n + j, t, Q + (int64_t)c * n + j, n - j);
+    if (t != T(0)) house_apply_cols(G + (int64_t)j * n + j, t, Q + j, n, 0, k, n - j);
     __syncthreads();
   }
 }
@@ -424,150 +453,259 @@ __global__ void __launch_bounds__(256) k_hbs_node(const HbsNode* __restrict__ no
 // ---------------------------------------------------------------------------------------------
 // Apply
 // ---------------------------------------------------------------------------------------------
-// x_hat of one leaf: V^T x(leaf) (U^T x transposed).  128 threads; warp per output, lanes over
-// the leaf's rows (at most 64).
+// The tree of a block with L >= 1 levels is cut at level ls = max(1, L - 3): one CTA owns the
+// subtree of each node of level ls (at most 8 leaves, 512 rows, all its inner nodes), so the
+// upward and downward passes inside a subtree run in shared memory; k_hbs_top does the few
+// levels above ls for a whole block.
+__host__ __device__ __forceinline__ int hbs_cut_level(int L) { return L > 3 ? L - 3 : 1; }
+
+// out[p] = W(:, p)^T v for the k columns of W (n x k, column-major, n <= 64) by one warp, in
+// the operators' precision (GB300 runs FP64 arithmetic at a small fraction of FP32); the loads
+// of eight columns are issued before their reductions.  Lane 0 stores the results: out_s in
+// shared memory (working precision), out_g in global memory (FP64).
 template <typename T>
-__global__ void __launch_bounds__(128) k_hbs_up_leaf(const HbsLeafItem* __restrict__ items,
-                                                     const HbsBlock* __restrict__ bl,
-                                                     const HbsNode* __restrict__ nodes,
-                                                     const T* __restrict__ F,
-                                                     const double* __restrict__ x0,
-                                                     double* __restrict__ scratch, int transpose,
-                                                     int k, const int* kdev, int64_t kstride) {
-  __shared__ double xs[64];
+__device__ __forceinline__ void warp_cols_dot(const T* __restrict__ W, int n, int k, const T* v,
+                                              T* out_s, double* out_g) {
+  const int lane = threadIdx.x & 31;
+  for (int p0 = 0; p0 < k; p0 += 8) {
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int p = p0 + u;
+      acc[u] = T(0);
+      if (p < k) {
+        const T* col = W + (int64_t)p * n;
+        if (lane < n) acc[u] = fma(col[lane], v[lane], acc[u]);
+        if (lane + 32 < n) acc[u] = fma(col[lane + 32], v[lane + 32], acc[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T r = warp_sum(acc[u]);
+      const int p = p0 + u;
+      if (lane == 0 && p < k) { out_s[p] = r; out_g[p] = (double)r; }
+    }
+  }
+}
+
+// Upward pass inside one subtree (item: block, subtree root node): x_hat = V^T x of its leaves,
+// then of its inner nodes level by level (U^T transposed), kept in shared memory and written to
+// the block's x_hat scratch.  256 threads, a warp per node.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hbs_up(const HbsLeafItem* __restrict__ items,
+                                                const HbsBlock* __restrict__ bl,
+                                                const HbsNode* __restrict__ nodes,
+                                                const T* __restrict__ F,
+                                                const double* __restrict__ x0,
+                                                double* __restrict__ scratch, int transpose,
+                                                int k, const int* kdev, int64_t kstride) {
+  __shared__ T xs[512];
+  __shared__ T xl[4][8][64];  // [level - ls][node][2k inputs of the next level up]
   const HbsLeafItem it = items[blockIdx.x];
   const HbsBlock b = bl[it.blk];
-  const HbsNode nd = nodes[it.node];
-  const int n = nd.n;
+  const HbsNode rt = nodes[it.node];
+  const int L = b.L, ls = rt.level, m = L - ls, warp = threadIdx.x >> 5;
+  const int64_t hi = ((int64_t)(rt.t + 1) * b.ng) >> ls;
+  const int len = (int)(hi - rt.lo);
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0) +
-                    (transpose ? b.out_if : b.in_if) + nd.lo;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
+                    (transpose ? b.out_if : b.in_if) + rt.lo;
+  for (int r = threadIdx.x; r < len; r += blockDim.x) xs[r] = static_cast<T>(x[r]);
   __syncthreads();
-  const T* W = F + (transpose ? nd.u_off : nd.v_off);
-  double* xh = scratch + b.xh_off + (int64_t)(it.node - b.node0) * k;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int p = warp; p < k; p += 4) {
-    double acc = 0.0;
-    for (int a = lane; a < n; a += 32) acc += (double)W[(int64_t)p * n + a] * xs[a];
-    acc = warp_sum(acc);
-    if (lane == 0) xh[p] = acc;
+  double* xh = scratch + b.xh_off;
+  for (int j = warp; j < (1 << m); j += 8) {  // leaves
+    const int a = (1 << L) - 1 + rt.t * (1 << m) + j;
+    const HbsNode& nd = nodes[b.node0 + a];
+    // x_hat of child j lands in its parent's input vector: rows (j & 1) k of slot j >> 1
+    T* dst = m > 0 ? &xl[m - 1][j >> 1][(j & 1) * k] : &xl[3][0][0];
+    warp_cols_dot(F + (transpose ? nd.u_off : nd.v_off), nd.n, k, xs + (nd.lo - rt.lo), dst,
+                  xh + (int64_t)a * k);
+  }
+  __syncthreads();
+  for (int d = m - 1; d >= 0; --d) {  // inner nodes of the subtree, level ls + d
+    const int lev = ls + d;
+    for (int j = warp; j < (1 << d); j += 8) {
+      const int a = (1 << lev) - 1 + rt.t * (1 << d) + j;
+      const HbsNode& nd = nodes[b.node0 + a];
+      T* dst = d > 0 ? &xl[d - 1][j >> 1][(j & 1) * k] : &xl[3][0][0];
+      warp_cols_dot(F + (transpose ? nd.u_off : nd.v_off), 2 * k, k, xl[d][j], dst,
+                    xh + (int64_t)a * k);
+    }
+    __syncthreads();
   }
 }
 
-// One CTA per block: x_hat of the inner levels (L-1 .. 1), the root's y_0 = D_0 x_0, and the
-// downward vectors of the inner levels (1 .. L-1): y_i = D_i x_i + U_i (parent's y, rows of i).
+// The levels above the cut for one block: x_hat of levels ls-1 .. 1, the root's y_0 = D_0 x_0,
+// and y_a = D_a x_a + U_a g of levels 1 .. ls-1 (transposed: U^T, D^T, V).  Products in the
+// operators' precision from vectors staged in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_hbs_tree(const HbsBlock* __restrict__ bl,
-                                                  const HbsNode* __restrict__ nodes,
-                                                  const T* __restrict__ F,
-                                                  double* __restrict__ scratch, int transpose,
-                                                  int k) {
+__global__ void __launch_bounds__(256) k_hbs_top(const HbsBlock* __restrict__ bl,
+                                                 const HbsNode* __restrict__ nodes,
+                                                 const T* __restrict__ F,
+                                                 double* __restrict__ scratch, int transpose,
+                                                 int k) {
+  __shared__ T vin[1024];  // inputs of up to 1024 / 2k nodes of one level (2k each)
+  __shared__ T gin[512];   // their parents' y at their rows (k each)
   const HbsBlock b = bl[blockIdx.x];
   if (b.L == 0) return;
+  const int ls = hbs_cut_level(b.L), k2 = 2 * k, CH = 1024 / k2;
   double* xh = scratch + b.xh_off;
   double* yh = scratch + b.yh_off;
-  const int k2 = 2 * k;
-  for (int lev = b.L - 1; lev >= 1; --lev) {
+  for (int lev = ls - 1; lev >= 0; --lev) {  // up; level 0 is the root's y_0 = D_0 x_0
     const int first = (1 << lev) - 1, cnt = 1 << lev;
-    for (int e = threadIdx.x; e < cnt * k; e += blockDim.x) {
-      const int i = first + e / k, p = e % k;
-      const HbsNode& nd = nodes[b.node0 + i];
-      const T* W = F + (transpose ? nd.u_off : nd.v_off);
-      const double* xin = xh + (int64_t)(2 * i + 1) * k;  // both children, contiguous
-      double acc = 0.0;
-      for (int a = 0; a < k2; ++a) acc += (double)W[(int64_t)p * k2 + a] * xin[a];
-      xh[(int64_t)i * k + p] = acc;
+    for (int c0 = 0; c0 < cnt; c0 += CH) {
+      const int nc = min(CH, cnt - c0);
+      for (int e = threadIdx.x; e < nc * k2; e += blockDim.x)  // children of the chunk, contiguous
+        vin[e] = static_cast<T>(xh[(int64_t)(2 * (first + c0) + 1) * k + e]);
+      __syncthreads();
+      if (lev > 0) {
+        for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+          const int jn = e / k, p = e % k, i = first + c0 + jn;
+          const HbsNode& nd = nodes[b.node0 + i];
+          const T* W = F + (int64_t)(transpose ? nd.u_off : nd.v_off) + (int64_t)p * k2;
+          T acc = T(0);
+#pragma unroll 8
+          for (int a = 0; a < k2; ++a) acc = fma(W[a], vin[jn * k2 + a], acc);
+          xh[(int64_t)i * k + p] = (double)acc;
+        }
+      } else {
+        const T* D0 = F + nodes[b.node0].d_off;
+        for (int a = threadIdx.x; a < k2; a += blockDim.x) {
+          T acc = T(0);
+#pragma unroll 8
+          for (int c = 0; c < k2; ++c)
+            acc = fma(transpose ? D0[(int64_t)a * k2 + c] : D0[(int64_t)c * k2 + a], vin[c], acc);
+          yh[a] = (double)acc;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  {
-    const T* D0 = F + nodes[b.node0].d_off;
-    const double* xin = xh + k;  // heap nodes 1 and 2
-    for (int a = threadIdx.x; a < k2; a += blockDim.x) {
-      double acc = 0.0;
-      for (int c = 0; c < k2; ++c)
-        acc += (double)(transpose ? D0[(int64_t)a * k2 + c] : D0[(int64_t)c * k2 + a]) * xin[c];
-      yh[a] = acc;
-    }
-    __syncthreads();
-  }
-  for (int lev = 1; lev <= b.L - 1; ++lev) {
+  for (int lev = 1; lev <= ls - 1; ++lev) {  // down
     const int first = (1 << lev) - 1, cnt = 1 << lev;
-    for (int e = threadIdx.x; e < cnt * k2; e += blockDim.x) {
-      const int i = first + e / k2, a = e % k2;
-      const HbsNode& nd = nodes[b.node0 + i];
-      const T* Dm = F + nd.d_off;
-      const T* W2 = F + (transpose ? nd.v_off : nd.u_off);
-      const double* xin = xh + (int64_t)(2 * i + 1) * k;
-      const double* g = yh + (int64_t)((i - 1) / 2) * k2 + ((i - 1) % 2) * k;
-      double acc = 0.0;
-      for (int c = 0; c < k2; ++c)
-        acc += (double)(transpose ? Dm[(int64_t)a * k2 + c] : Dm[(int64_t)c * k2 + a]) * xin[c];
-      for (int p = 0; p < k; ++p) acc += (double)W2[(int64_t)p * k2 + a] * g[p];
-      yh[(int64_t)i * k2 + a] = acc;
+    for (int c0 = 0; c0 < cnt; c0 += CH) {
+      const int nc = min(CH, cnt - c0);
+      for (int e = threadIdx.x; e < nc * k2; e += blockDim.x)
+        vin[e] = static_cast<T>(xh[(int64_t)(2 * (first + c0) + 1) * k + e]);
+      for (int e = threadIdx.x; e < nc * k; e += blockDim.x) {
+        const int i = first + c0 + e / k, p = e % k;
+        gin[e] = static_cast<T>(yh[(int64_t)((i - 1) / 2) * k2 + ((i - 1) & 1) * k + p]);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nc * k2; e += blockDim.x) {
+        const int jn = e / k2, row = e % k2, i = first + c0 + jn;
+        const HbsNode& nd = nodes[b.node0 + i];
+        const T* Dm = F + nd.d_off;
+        const T* W2 = F + (transpose ? nd.v_off : nd.u_off);
+        T acc = T(0);
+#pragma unroll 8
+        for (int c = 0; c < k2; ++c)
+          acc = fma(transpose ? Dm[(int64_t)row * k2 + c] : Dm[(int64_t)c * k2 + row],
+                    vin[jn * k2 + c], acc);
+#pragma unroll 8
+        for (int p = 0; p < k; ++p) acc = fma(W2[(int64_t)p * k2 + row], gin[jn * k + p], acc);
+        yh[(int64_t)i * k2 + row] = (double)acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
-// One CTA per output item (the rows of one leaf of one output interface): for each block
-// writing there, D x(leaf) + U (parent's y, rows of the leaf) (transposed: D^T, V), then
-// y = x - sum (or the sum alone with konly).  256 threads: 64 rows x 4 column groups.
+// Downward pass inside one subtree and the output (item: the rows of one subtree of one output
+// interface; up to two blocks write there, taken one after the other): y_a = D_a x_a + U_a g of
+// the subtree's inner nodes level by level in shared memory (g: the parent's y at the rows of a;
+// for the subtree root from the block's y_hat), then D x + U g of its leaves; y = x - sum (or the
+// sum with konly).  Transposed: D^T and V.  Products in the operators' precision; the sums of
+// the two blocks and the output in FP64.  256 threads.
 template <typename T>
-__global__ void __launch_bounds__(256) k_hbs_down_leaf(const HbsOwn* __restrict__ items,
-                                                       const HbsBlock* __restrict__ bl,
-                                                       const HbsNode* __restrict__ nodes,
-                                                       const T* __restrict__ F,
-                                                       const double* __restrict__ scratch,
-                                                       const double* __restrict__ x0,
-                                                       double* __restrict__ y, int transpose,
-                                                       int konly, int k, const int* kdev,
-                                                       int64_t kstride) {
-  __shared__ double xs[2][64];
-  __shared__ double gs[2][32];
-  __shared__ double part[4][64];
+__global__ void __launch_bounds__(256) k_hbs_down(const HbsOwn* __restrict__ items,
+                                                  const HbsBlock* __restrict__ bl,
+                                                  const HbsNode* __restrict__ nodes,
+                                                  const T* __restrict__ F,
+                                                  const double* __restrict__ scratch,
+                                                  const double* __restrict__ x0,
+                                                  double* __restrict__ y, int transpose, int konly,
+                                                  int k, int lcap, const int* kdev,
+                                                  int64_t kstride) {
+  __shared__ T xs[512];
+  __shared__ double outv[512];
+  __shared__ T xa[4][64];     // inputs x_a of the nodes of one inner level
+  __shared__ T yv[2][4][64];  // y of the nodes of the current and the previous level
+  __shared__ T groot[32];
   const double* x = x0 + (kdev ? (int64_t)(*kdev - 1) * kstride : 0);
   const HbsOwn it = items[blockIdx.x];
-  const int len = it.len;
+  const int len = it.len, k2 = 2 * k;
+  for (int r = threadIdx.x; r < len; r += blockDim.x) outv[r] = 0.0;
   for (int q = 0; q < it.nsrc; ++q) {
     const HbsBlock b = bl[it.blk[q]];
-    const HbsNode& nd = nodes[it.node[q]];
-    const double* xin = x + (transpose ? b.out_if : b.in_if) + nd.lo;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) xs[q][i] = xin[i];
-    if (b.L > 0) {
-      const int il = it.node[q] - b.node0;
-      const double* g = scratch + b.yh_off + (int64_t)((il - 1) / 2) * 2 * k + ((il - 1) % 2) * k;
-      for (int p = threadIdx.x; p < k; p += blockDim.x) gs[q][p] = g[p];
+    const HbsNode rt = nodes[it.node[q]];
+    const int L = b.L, ls = rt.level, m = L - ls;
+    const double* xin = x + (transpose ? b.out_if : b.in_if) + it.lo;
+    __syncthreads();  // the previous source's readers of xs, yv are done
+    for (int r = threadIdx.x; r < len; r += blockDim.x) xs[r] = static_cast<T>(xin[r]);
+    if (L > 0) {
+      const int ir = it.node[q] - b.node0;
+      for (int p = threadIdx.x; p < k; p += blockDim.x)
+        groot[p] = static_cast<T>(
+            scratch[b.yh_off + (int64_t)((ir - 1) / 2) * k2 + ((ir - 1) & 1) * k + p]);
     }
-  }
-  __syncthreads();
-  const int r = threadIdx.x & 63, grp = threadIdx.x >> 6;
-  double acc = 0.0;
-  if (r < len) {
-    for (int q = 0; q < it.nsrc; ++q) {
-      const HbsBlock& b = bl[it.blk[q]];
-      const HbsNode& nd = nodes[it.node[q]];
-      const T* Dm = F + nd.d_off;
-      T part_acc = T(0);
-      if (!transpose) {
-        for (int c = grp; c < len; c += 4) part_acc += Dm[(int64_t)c * len + r] * (T)xs[q][c];
-      } else {
-        for (int c = grp; c < len; c += 4) part_acc += Dm[(int64_t)r * len + c] * (T)xs[q][c];
+    __syncthreads();
+    int cur = 0;
+    for (int d = 0; d < m; ++d) {  // inner nodes of the subtree at level ls + d
+      const int lev = ls + d, nl = 1 << d;
+      for (int e = threadIdx.x; e < nl * k2; e += blockDim.x) {
+        const int j = e / k2, c = e % k2;
+        const int a = (1 << lev) - 1 + rt.t * nl + j;
+        xa[j][c] = static_cast<T>(scratch[b.xh_off + (int64_t)(2 * a + 1) * k + c]);
       }
-      acc += (double)part_acc;
-      if (b.L > 0) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < nl * k2; e += blockDim.x) {
+        const int j = e / k2, row = e % k2;
+        const int a = (1 << lev) - 1 + rt.t * nl + j;
+        const HbsNode& nd = nodes[b.node0 + a];
+        const T* Dm = F + nd.d_off;
         const T* W2 = F + (transpose ? nd.v_off : nd.u_off);
-        for (int p = grp; p < k; p += 4) acc += (double)W2[(int64_t)p * len + r] * gs[q][p];
+        const T* g = d == 0 ? groot : &yv[cur ^ 1][j >> 1][(j & 1) * k];
+        T acc = T(0);
+#pragma unroll 8
+        for (int c = 0; c < k2; ++c)
+          acc = fma(transpose ? Dm[(int64_t)row * k2 + c] : Dm[(int64_t)c * k2 + row], xa[j][c], acc);
+#pragma unroll 8
+        for (int p = 0; p < k; ++p) acc = fma(W2[(int64_t)p * k2 + row], g[p], acc);
+        yv[cur][j][row] = acc;
       }
+      __syncthreads();
+      cur ^= 1;
+    }
+    // leaves (level L): thread per (leaf, row), lcap (the leaf size bound) rows per leaf
+    for (int e = threadIdx.x; e < (1 << m) * lcap; e += blockDim.x) {
+      const int j = e / lcap, rr = e - j * lcap;
+      const int a = (1 << L) - 1 + rt.t * (1 << m) + j;
+      const HbsNode& nd = nodes[b.node0 + a];
+      const int n = nd.n;
+      if (rr >= n) continue;
+      const int off = (int)(nd.lo - it.lo);
+      const T* Dm = F + nd.d_off;
+      T acc = T(0);
+      if (!transpose) {
+#pragma unroll 8
+        for (int c = 0; c < n; ++c) acc = fma(Dm[(int64_t)c * n + rr], xs[off + c], acc);
+      } else {
+#pragma unroll 8
+        for (int c = 0; c < n; ++c) acc = fma(Dm[(int64_t)rr * n + c], xs[off + c], acc);
+      }
+      if (L > 0) {
+        const T* W2 = F + (transpose ? nd.v_off : nd.u_off);
+        const T* g = m == 0 ? groot : &yv[cur ^ 1][j >> 1][(j & 1) * k];
+#pragma unroll 8
+        for (int p = 0; p < k; ++p) acc = fma(W2[(int64_t)p * n + rr], g[p], acc);
+      }
+      outv[off + rr] += (double)acc;
     }
   }
-  part[grp][r] = acc;
   __syncthreads();
-  if (threadIdx.x < len) {
-    const double tot = part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] +
-                       part[3][threadIdx.x];
-    const int64_t o = it.out + it.lo + threadIdx.x;
-    y[o] = konly ? tot : x[o] - tot;
+  for (int r = threadIdx.x; r < len; r += blockDim.x) {
+    const int64_t o = it.out + it.lo + r;
+    y[o] = konly ? outv[r] : x[o] - outv[r];
   }
 }
 
@@ -575,13 +713,14 @@ __global__ void __launch_bounds__(256) k_hbs_down_leaf(const HbsOwn* __restrict_
 // Host side
 // ---------------------------------------------------------------------------------------------
 void HbsSet::release() {
-  for (void* p : {F, (void*)scratch, (void*)d_nodes, (void*)d_blocks, (void*)d_own, (void*)d_own_T,
-                  (void*)d_leaf_items})
+  for (void* p : {F, (void*)scratch, (void*)d_nodes, (void*)d_blocks, (void*)d_own,
+                  (void*)d_own_T, (void*)d_leaf_items})
     if (p) cudaFree(p);
   F = nullptr; scratch = nullptr; d_nodes = nullptr; d_blocks = nullptr; d_own = nullptr;
   d_own_T = nullptr; d_leaf_items = nullptr;
   nodes.clear(); blocks.clear(); blk_slab.clear(); blk_side.clear(); bare.clear();
   n_own = n_own_T = n_leaf_items = 0;
+  max_L = 0;
   f_elems = bytes = 0;
   built = false;
 }
@@ -605,18 +744,18 @@ std::vector<HbsOwn> make_owners(const HbsSet& H, bool transpose) {
     const auto& bs = kv.second;
     for (size_t g = 0; g < bs.size(); g += 2) {  // at most two blocks per item
       const HbsBlock& b0 = H.blocks[bs[g]];
-      const int L = b0.L;
-      for (int t = 0; t < (1 << L); ++t) {
+      const int ls = b0.L == 0 ? 0 : hbs_cut_level(b0.L);
+      for (int t = 0; t < (1 << ls); ++t) {  // one item per subtree below the cut
         HbsOwn o{};
         o.out = kv.first;
         o.nsrc = (g + 1 < bs.size()) ? 2 : 1;
         for (int q = 0; q < o.nsrc; ++q) {
           o.blk[q] = bs[g + q];
-          o.node[q] = H.blocks[bs[g + q]].node0 + (1 << L) - 1 + t;
+          o.node[q] = H.blocks[bs[g + q]].node0 + (1 << ls) - 1 + t;
         }
         const HbsNode& nd = H.nodes[o.node[0]];
         o.lo = nd.lo;
-        o.len = nd.n;
+        o.len = (int)((((int64_t)(t + 1) * b0.ng) >> ls) - nd.lo);
         out.push_back(o);
       }
     }
@@ -723,6 +862,7 @@ int hbs_build(HbsSet& H, const std::vector<HbsInput>& in,
       }
     }
   }
+  H.max_L = Lmax;
   H.f_elems = fo;
   H.bytes = fo * (int64_t)sizeof(T);
   auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
@@ -813,11 +953,12 @@ int hbs_build(HbsSet& H, const std::vector<HbsInput>& in,
     std::swap(Yc, Yn); std::swap(Zc, Zn); std::swap(Oc, On); std::swap(Pc, Pn);
   }
   // apply items
-  std::vector<HbsLeafItem> li;
+  std::vector<HbsLeafItem> li;  // upward-pass items: the subtrees below the cut
   for (int b = 0; b < nb; ++b) {
     const HbsBlock& hb = H.blocks[b];
     if (hb.L == 0) continue;
-    for (int t = 0; t < (1 << hb.L); ++t) li.push_back(HbsLeafItem{b, hb.node0 + (1 << hb.L) - 1 + t});
+    const int ls = hbs_cut_level(hb.L);
+    for (int t = 0; t < (1 << ls); ++t) li.push_back(HbsLeafItem{b, hb.node0 + (1 << ls) - 1 + t});
   }
   const std::vector<HbsOwn> own = make_owners(H, false), ownT = make_owners(H, true);
   ok = al((void**)&H.d_leaf_items, sizeof(HbsLeafItem) * li.size()) &&
@@ -845,20 +986,19 @@ void hbs_apply(HbsSet& H, const double* x, double* y, int transpose, cudaStream_
   const int konly = transpose >> 1;
   transpose &= 1;
   if (H.n_leaf_items > 0) {
-    note_launch();
-    k_hbs_up_leaf<T><<<H.n_leaf_items, 128, 0, st>>>(H.d_leaf_items, H.d_blocks, H.d_nodes,
-                                                     (const T*)H.F, x, H.scratch, transpose, H.k,
-                                                     kdev, kstride);
-    note_launch();
-    k_hbs_tree<T><<<(unsigned)H.blocks.size(), 256, 0, st>>>(H.d_blocks, H.d_nodes, (const T*)H.F,
-                                                             H.scratch, transpose, H.k);
+    note_launch(2);
+    k_hbs_up<T><<<H.n_leaf_items, 256, 0, st>>>(H.d_leaf_items, H.d_blocks, H.d_nodes,
+                                                (const T*)H.F, x, H.scratch, transpose, H.k, kdev,
+                                                kstride);
+    k_hbs_top<T><<<(unsigned)H.blocks.size(), 256, 0, st>>>(H.d_blocks, H.d_nodes, (const T*)H.F,
+                                                            H.scratch, transpose, H.k);
   }
   const int no = transpose ? H.n_own_T : H.n_own;
   if (no > 0) {
     note_launch();
-    k_hbs_down_leaf<T><<<no, 256, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_nodes,
-                                           (const T*)H.F, H.scratch, x, y, transpose, konly, H.k,
-                                           kdev, kstride);
+    k_hbs_down<T><<<no, 256, 0, st>>>(transpose ? H.d_own_T : H.d_own, H.d_blocks, H.d_nodes,
+                                      (const T*)H.F, H.scratch, x, y, transpose, konly, H.k,
+                                      H.leaf, kdev, kstride);
   }
 }
 

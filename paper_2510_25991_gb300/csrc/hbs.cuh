@@ -35,7 +35,8 @@ struct HbsBlock {
   int64_t in_if, out_if;  // interface offsets of the source and target vectors (0 and 0 alone)
 };
 
-// Output item of the apply: the rows of one leaf of one output interface; up to two blocks
+// Output item of the apply: the rows of one subtree of one output interface (node: the
+// subtree's root; the whole block when its tree has one level); up to two blocks
 // write there (S_{j,j-1} and S_{j,j+1} onto Gamma_j; transposed: S_{j+1,j}^T and S_{j-1,j}^T).
 struct HbsOwn {
   int64_t out;      // interface offset of the output rows (+ lo)
@@ -43,18 +44,19 @@ struct HbsOwn {
   int len;
   int nsrc;
   int blk[2];
-  int node[2];      // leaf node (absolute index)
+  int node[2];      // subtree root node (absolute index)
 };
 
-struct HbsLeafItem {  // up-pass item: one leaf of one block
+struct HbsLeafItem {  // up-pass item: one subtree of one block
   int blk;
-  int node;          // absolute node index
+  int node;          // absolute index of the subtree's root node
 };
 
 struct HbsSet {
   bool built = false;
   size_t esz = 4;
   int k = 0, s = 0, leaf = 0;
+  int max_L = 0;                // deepest tree over the blocks
   void* F = nullptr;            // factors (element type of the context)
   double* scratch = nullptr;    // x_hat and y_hat
   HbsNode* d_nodes = nullptr;
