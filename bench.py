@@ -598,6 +598,9 @@ def main():
                     help="skip the direct interface solver section")
     ap.add_argument("--no-march", action="store_true", help="skip the time-marching section")
     ap.add_argument("--no-hbs", action="store_true", help="skip the HBS-operator section")
+    ap.add_argument("--only-hbs", action="store_true",
+                    help="run only the HBS section on --n / --w (for profiling its kernels)")
+    ap.add_argument("--hbs-ranks", default="12,16", help="HBS ranks of that section")
     ap.add_argument("--only-direct", action="store_true",
                     help="run only the direct-solver section on --n / --w (for profiling smaller cases)")
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner section")
@@ -637,6 +640,14 @@ def main():
         return
     n, w = args.n, args.w
     prob = I.make_problem("convdiff2d", n=n, w=w)
+    if args.only_hbs:  # the HBS section alone, on the --n / --w workload
+        peaks, src = _peaks()
+        devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        ranks = tuple(int(r) for r in args.hbs_ranks.split(","))
+        sec, _ = bench_hbs(devt(prob["a"]), devt(prob["f"]), devt(prob["g"]), n, w, peaks, src,
+                           ranks=ranks, solves=1)
+        print(json.dumps(sec), flush=True)
+        return
     if args.only_direct:  # the direct-solver section alone, on the --n / --w workload
         peaks, src = _peaks()
         devt = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -835,7 +846,8 @@ def main():
         line["direct"] = bench_direct(a, f, g, n, w, args.tol, peaks, src)
     u_hbs = None
     if rank == 0 and not args.no_hbs:
-        line["hbs"], u_hbs = bench_hbs(a, f, g, n, w, peaks, src)
+        line["hbs"], u_hbs = bench_hbs(a, f, g, n, w, peaks, src,
+                                       ranks=tuple(int(r) for r in args.hbs_ranks.split(",")))
     if rank == 0 and not args.no_march:
         line["march"] = bench_march()
     c4_sol = c5_prob = None
