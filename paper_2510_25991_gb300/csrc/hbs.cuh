@@ -17,7 +17,7 @@ struct HbsNode {
   int level;
   int n;            // rows of the node's row set (leaves: index count; inner nodes and root: 2k)
   int t;            // index within its level
-  int64_t lo;       // leaves: first index of the node within the block's range
+  int64_t lo;       // first index of the node's range in the bisection tree (t ng >> level)
   int64_t in_row;   // compression: first sample row of the node in the current level buffer
   int64_t out_row;  // compression: first of its k reduced rows in the next level's buffer
   int64_t u_off, v_off, d_off;  // factor offsets (elements); -1 where absent
