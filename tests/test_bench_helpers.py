@@ -61,3 +61,23 @@ def test_reference_sample_size_is_bounded_by_the_step_count():
     assert size(5, 3) == 512 and size(7, 3) == 512     # default run: about two minutes
     assert size(20, 3) == 256                          # longer runs take the smaller sample
     assert size(20, 3, 128) == 128                     # an explicit size wins
+
+
+def test_cpu_leg_reports_errors_of_both_solutions():
+    """The CPU leg measures the timed run's solution and the HBS section's solution against
+    the oracle's global solve of the same instance (exact solutions give zero, a perturbed one
+    its relative size)."""
+    import numpy as np
+
+    import ddst_inputs as I
+    from oracle import ddst_oracle as O
+    prob = I.make_problem("convdiff2d", n=64, w=16)
+    A, b = O.assemble(prob)
+    ustar = O.global_solve(A, b)
+    pert = ustar.reshape(63, 63) * (1.0 + 1e-6)
+    leg = _bench().cpu_leg(prob, ustar.copy(), verify=True, ref_n=64, u_hbs=pert)
+    assert leg["verify"]["rel_error_vs_oracle"] <= 1e-14
+    assert abs(leg["hbs_rel_error_vs_oracle"] - 1e-6) <= 1e-9
+    assert leg["cpu_baseline"]["kind"] == "oracle"
+    leg = _bench().cpu_leg(prob, ustar.copy(), verify=False, ref_n=64, u_hbs=pert)
+    assert "hbs_rel_error_vs_oracle" not in leg
