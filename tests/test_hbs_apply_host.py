@@ -1,0 +1,162 @@
+"""The HBS apply kernels (upward pass, levels above the cut, downward pass with output) compiled
+for the host from `csrc/hbs.cu` itself and run with one OS thread per CUDA thread
+(`tests/hostemu/cuda_host_shim.h`), on HBS factors that the oracle's O9 computes and lays out in
+the library's device format (heap-ordered nodes, U, V and D column-major).  The output must
+equal the oracle's telescoping apply (Sec. 2.4) to rounding, in both directions, on trees of
+depth 0 to 6 with ragged leaves.  CPU only: this checks the kernels' index arithmetic and
+their barriers, including races between threads of a CTA, which a sequential re-statement of
+the same arithmetic would hide."""
+import os
+import re
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import ddst_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+
+MAIN = r'''
+#include <cstdio>
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  auto rd = [&](int64_t* p, int n) { f.read((char*)p, 8 * n); };
+  int64_t h[9]; rd(h, 9);
+  const int ng = (int)h[0], k = (int)h[1], leaf = (int)h[2], tr = (int)h[3];
+  const int nn = (int)h[5], nup = (int)h[6], nown = (int)h[7];
+  const int64_t nf = h[8];
+  int64_t so; rd(&so, 1);
+  std::vector<HbsNode> nodes(nn);
+  for (auto& nd : nodes) {
+    int64_t a[10]; rd(a, 10);
+    nd.blk = (int)a[0]; nd.level = (int)a[1]; nd.n = (int)a[2]; nd.t = (int)a[3]; nd.lo = a[4];
+    nd.in_row = a[5]; nd.out_row = a[6]; nd.u_off = a[7]; nd.v_off = a[8]; nd.d_off = a[9];
+  }
+  int64_t bb[5]; rd(bb, 5);
+  HbsBlock blk{};
+  blk.ng = bb[0]; blk.L = (int)bb[1]; blk.node0 = (int)bb[2]; blk.xh_off = bb[3]; blk.yh_off = bb[4];
+  blk.in_if = 0; blk.out_if = 0;
+  std::vector<HbsLeafItem> up(nup);
+  for (auto& u : up) { int64_t a[2]; rd(a, 2); u.blk = (int)a[0]; u.node = (int)a[1]; }
+  std::vector<HbsOwn> own(nown);
+  for (auto& o : own) {
+    int64_t a[8]; rd(a, 8);
+    o.out = a[0]; o.lo = a[1]; o.len = (int)a[2]; o.nsrc = (int)a[3];
+    o.blk[0] = (int)a[4]; o.blk[1] = (int)a[5]; o.node[0] = (int)a[6]; o.node[1] = (int)a[7];
+  }
+  std::vector<double> F(nf), x(ng), y(ng, 0.0), scratch(so, 0.0);
+  f.read((char*)F.data(), 8 * nf); f.read((char*)x.data(), 8 * ng);
+  if (blk.L > 0) {
+    host_launch(nup, 256, [&] { k_hbs_up<double>(up.data(), &blk, nodes.data(), F.data(), x.data(),
+                                                scratch.data(), tr, k, nullptr, 0); });
+    host_launch(1, 256, [&] { k_hbs_top<double>(&blk, nodes.data(), F.data(), scratch.data(), tr, k); });
+  }
+  host_launch(nown, 256, [&] { k_hbs_down<double>(own.data(), &blk, nodes.data(), F.data(),
+                                                  scratch.data(), x.data(), y.data(), tr, 1, k,
+                                                  leaf, nullptr, 0); });
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)y.data(), 8 * ng);
+  return 0;
+}
+'''
+
+
+def _cut_level():
+    """The tree cut of the apply, read from the kernel source (L > c ? L - c : 1)."""
+    src = open(os.path.join(CSRC, "hbs.cu")).read()
+    m = re.search(r"int hbs_cut_level\(int L\) \{ return L > (\d+) \? L - (\d+) : 1; \}", src)
+    assert m and m.group(1) == m.group(2), "hbs_cut_level not found"
+    c = int(m.group(1))
+    return lambda L: L - c if L > c else 1
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = open(os.path.join(CSRC, "hbs.cu")).read()
+    hdr = open(os.path.join(CSRC, "hbs.cuh")).read()
+    i = src.index("// Apply\n")
+    i = src.rindex("// ----", 0, i)
+    j = src.index("// Host side\n")
+    j = src.rindex("// ----", 0, j)
+    structs = [re.search(r"struct %s \{.*?\n\};" % n, hdr, re.S).group(0)
+               for n in ("HbsNode", "HbsBlock", "HbsOwn", "HbsLeafItem")]
+    d = tmp_path_factory.mktemp("hbs_host")
+    code = ('#include "cuda_host_shim.h"\nnamespace ddst {\n' + "\n".join(structs) + "\n" +
+            src[i:j] + "\n}  // namespace ddst\n" + MAIN)
+    (d / "hbs_apply_host.cpp").write_text(code)
+    exe = d / "hbs_apply_host"
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-I", os.path.join(ROOT, "tests", "hostemu"),
+                        str(d / "hbs_apply_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return d, exe
+
+
+def _case(d, ng, k, leaf, tr, cut):
+    """Oracle HBS factors of a random S in the device layout, the apply's work items, and x."""
+    rng = np.random.default_rng(ng * 7 + k)
+    s = 3 * k + 10
+    S = rng.standard_normal((ng, ng))
+    Om, Ps = rng.standard_normal((ng, s)), rng.standard_normal((ng, s))
+    H = O.hbs_compress(S @ Om, S.T @ Ps, Om, Ps, k, leaf)
+    L, lv = H["L"], H["levels"]
+    F, nodes, fo = [], [], 0
+    for lev in range(L + 1):
+        for t in range(1 << lev):
+            lo = (t * ng) >> lev
+            n = (((t + 1) * ng) >> lev) - lo if lev == L else 2 * k
+            u = v = -1
+            if lev > 0:
+                U, V, D = lv[lev][t]
+                u = fo; F.append(U.T.ravel()); fo += n * k
+                v = fo; F.append(V.T.ravel()); fo += n * k
+            else:
+                D = lv[0]
+                n = D.shape[0]
+            dd = fo; F.append(D.T.ravel()); fo += n * n
+            nodes.append((0, lev, n, t, lo, 0, 0, u, v, dd))
+    F = np.concatenate(F)
+    so = ((2 << L) - 1) * k + max(1, (1 << L) - 1) * 2 * k
+    ls = 0 if L == 0 else cut(L)
+    up = [(0, (1 << ls) - 1 + t) for t in range(1 << ls)] if L > 0 else []
+    own = []
+    for t in range(1 << ls):
+        nd = (1 << ls) - 1 + t
+        lo = nodes[nd][4]
+        own.append((0, lo, (((t + 1) * ng) >> ls) - lo, 1, 0, 0, nd, 0))
+    x = rng.standard_normal(ng)
+    path = d / f"case_{ng}_{k}_{leaf}_{tr}.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("9q", ng, k, leaf, tr, L, len(nodes), len(up), len(own), F.size))
+        f.write(struct.pack("q", so))
+        for nd in nodes:
+            f.write(struct.pack("10q", *nd))
+        f.write(struct.pack("5q", ng, L, 0, 0, ((2 << L) - 1) * k))
+        for it in up:
+            f.write(struct.pack("2q", *it))
+        for o in own:
+            f.write(struct.pack("8q", *o))
+        f.write(F.astype(np.float64).tobytes())
+        f.write(x.tobytes())
+    return path, O.hbs_apply(H, x, transpose=bool(tr)), L
+
+
+@pytest.mark.parametrize("ng,k,leaf", [(200, 6, 12), (137, 4, 8), (64, 8, 16), (9, 3, 12),
+                                       (40, 10, 20), (1000, 8, 16)])
+@pytest.mark.parametrize("tr", [0, 1])
+def test_hbs_apply_kernels_on_the_host_match_the_oracle(harness, ng, k, leaf, tr):
+    d, exe = harness
+    path, want, L = _case(d, ng, k, leaf, tr, _cut_level())
+    out = d / (path.name + ".y")
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    y = np.fromfile(out, dtype=np.float64)
+    assert np.abs(y - want).max() <= 1e-12 * np.abs(want).max(), (L, np.abs(y - want).max())
