@@ -1,9 +1,11 @@
-// Host emulation of the CUDA features used by the HBS apply kernels, for CPU tests of their
-// index arithmetic and synchronisation: one CTA at a time, one OS thread per CUDA thread,
-// std::barrier for __syncthreads and a per-warp exchange buffer for shuffles.  Block-scope
+// Host emulation of the CUDA features used by the HBS kernels, for CPU tests of their index
+// arithmetic and synchronisation: one CTA at a time, one OS thread per CUDA thread,
+// std::barrier for __syncthreads, counter-based warp synchronisation and an exchange buffer for
+// shuffles.  Block-scope
 // __shared__ variables become function statics (shared by the threads of the CTA that runs).
 #pragma once
 #include <algorithm>
+#include <atomic>
 #include <barrier>
 #include <cmath>
 #include <cstdint>
@@ -23,18 +25,27 @@ struct HostDim3 { unsigned x = 0, y = 0, z = 0; };
 inline thread_local HostDim3 threadIdx, blockIdx;
 inline HostDim3 blockDim{256, 1, 1};
 inline std::barrier<>* g_cta_barrier = nullptr;
-inline std::barrier<>* g_warp_barrier[32];
+// Warp-level synchronisation over the lanes of a mask (the whole warp, or a group of lanes
+// that always synchronise together): per-lane arrival counters, one set per mask kind, so that
+// groups that loop a different number of times never wait for one another.
+inline std::atomic<int64_t> g_arrive[2][32][32];
 inline double g_exchange[32][32];
 
 inline void __syncthreads() { g_cta_barrier->arrive_and_wait(); }
-inline void __syncwarp(unsigned = 0xffffffffu) { g_warp_barrier[threadIdx.x >> 5]->arrive_and_wait(); }
+inline void __syncwarp(unsigned mask = 0xffffffffu) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, kind = mask == 0xffffffffu ? 0 : 1;
+  const int64_t my = ++g_arrive[kind][w][l];
+  for (int m = 0; m < 32; ++m)
+    if (mask & (1u << m))
+      while (g_arrive[kind][w][m].load() < my) std::this_thread::yield();
+}
 template <typename T>
-inline T __shfl_xor_sync(unsigned, T v, int lane_mask) {
+inline T __shfl_xor_sync(unsigned mask, T v, int lane_mask) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   g_exchange[w][l] = static_cast<double>(v);
-  g_warp_barrier[w]->arrive_and_wait();
+  __syncwarp(mask);
   const T r = static_cast<T>(g_exchange[w][l ^ lane_mask]);
-  g_warp_barrier[w]->arrive_and_wait();
+  __syncwarp(mask);
   return r;
 }
 template <typename T>
@@ -55,11 +66,12 @@ inline void host_launch(unsigned grid, unsigned threads, const std::function<voi
   for (unsigned b = 0; b < grid; ++b) {
     std::barrier<> cta(threads);
     g_cta_barrier = &cta;
-    for (unsigned w = 0; w < (threads + 31) / 32; ++w) g_warp_barrier[w] = new std::barrier<>(32);
+    for (auto& k : g_arrive)
+      for (auto& w : k)
+        for (auto& c : w) c.store(0);
     std::vector<std::thread> ts;
     for (unsigned t = 0; t < threads; ++t)
       ts.emplace_back([&body, t, b] { threadIdx.x = t; blockIdx.x = b; body(); });
     for (auto& t : ts) t.join();
-    for (unsigned w = 0; w < (threads + 31) / 32; ++w) delete g_warp_barrier[w];
   }
 }

@@ -1,11 +1,14 @@
-"""The HBS apply kernels (upward pass, levels above the cut, downward pass with output) compiled
-for the host from `csrc/hbs.cu` itself and run with one OS thread per CUDA thread
-(`tests/hostemu/cuda_host_shim.h`), on HBS factors that the oracle's O9 computes and lays out in
-the library's device format (heap-ordered nodes, U, V and D column-major).  The output must
-equal the oracle's telescoping apply (Sec. 2.4) to rounding, in both directions, on trees of
-depth 0 to 6 with ragged leaves.  CPU only: this checks the kernels' index arithmetic and
-their barriers, including races between threads of a CTA, which a sequential re-statement of
-the same arithmetic would hide."""
+"""The HBS kernels compiled for the host from `csrc/hbs.cu` itself and run with one OS thread per
+CUDA thread (`tests/hostemu/cuda_host_shim.h`).  CPU only: this checks the kernels' index
+arithmetic and their barriers, including races between threads of a CTA, which a sequential
+re-statement of the same arithmetic would hide.
+
+* The apply kernels (upward pass, levels above the cut, downward pass with output) on HBS
+  factors that the oracle's O9 computes, laid out in the library's device format (heap-ordered
+  nodes, U, V and D column-major): the output equals the oracle's telescoping apply (Sec. 2.4)
+  to rounding, in both directions, on trees of depth 0 to 6 with ragged leaves.
+* The node compression kernel, level by level from the leaves, on the oracle's samples
+  (Alg. 1's Y = S Omega, Z = S^T Psi): the operator its factors define equals the oracle's."""
 import os
 import re
 import shutil
@@ -160,3 +163,162 @@ def test_hbs_apply_kernels_on_the_host_match_the_oracle(harness, ng, k, leaf, tr
     assert r.returncode == 0, r.stderr[-2000:]
     y = np.fromfile(out, dtype=np.float64)
     assert np.abs(y - want).max() <= 1e-12 * np.abs(want).max(), (L, np.abs(y - want).max())
+
+
+# ---------------------------------------------------------------------------------------------
+# The compression kernel (one CTA per tree node, level by level) on the host
+# ---------------------------------------------------------------------------------------------
+NODE_MAIN = r'''
+#include <cstdio>
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  auto rd = [&](int64_t* p, int n) { f.read((char*)p, 8 * n); };
+  int64_t h[7]; rd(h, 7);
+  const int ng = (int)h[0], k = (int)h[1], s = (int)h[2], nn = (int)h[3], nsteps = (int)h[4];
+  const int64_t nf = h[5]; const int nmax = (int)h[6];
+  std::vector<HbsNode> nodes(nn);
+  for (auto& nd : nodes) {
+    int64_t a[10]; rd(a, 10);
+    nd.blk = (int)a[0]; nd.level = (int)a[1]; nd.n = (int)a[2]; nd.t = (int)a[3]; nd.lo = a[4];
+    nd.in_row = a[5]; nd.out_row = a[6]; nd.u_off = a[7]; nd.v_off = a[8]; nd.d_off = a[9];
+  }
+  std::vector<std::vector<int>> steps(nsteps);
+  for (auto& st : steps) {
+    int64_t c; rd(&c, 1);
+    st.resize(c);
+    for (auto& id : st) { int64_t v; rd(&v, 1); id = (int)v; }
+  }
+  const int64_t rows = (int64_t)ng;
+  std::vector<double> arr[8];
+  for (auto& a : arr) a.assign(rows * s + (int64_t)(1 << 12) * s, 0.0);
+  for (int q = 0; q < 4; ++q) f.read((char*)arr[q].data(), 8 * rows * s);  // Y, Z, Omega, Psi
+  std::vector<double> F(nf, 0.0);
+  double *Yc = arr[0].data(), *Zc = arr[1].data(), *Oc = arr[2].data(), *Pc = arr[3].data();
+  double *Yn = arr[4].data(), *Zn = arr[5].data(), *On = arr[6].data(), *Pn = arr[7].data();
+  for (int d = 0; d < nsteps; ++d) {
+    const std::vector<int>& lst = steps[d];
+    host_launch((unsigned)lst.size(), 256, [&] {
+      k_hbs_node<double>(nodes.data(), lst.data(), Yc, Zc, Oc, Pc, Yn, Zn, On, Pn, F.data(), k, s, nmax);
+    });
+    std::swap(Yc, Yn); std::swap(Zc, Zn); std::swap(Oc, On); std::swap(Pc, Pn);
+  }
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)F.data(), 8 * nf);
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def node_harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = open(os.path.join(CSRC, "hbs.cu")).read()
+    hdr = open(os.path.join(CSRC, "hbs.cuh")).read()
+    i = src.rindex("// ----", 0, src.index("// Node compression\n"))
+    j = src.rindex("// ----", 0, src.index("// Apply\n"))
+    body = src[i:j]
+    dyn = "extern __shared__ __align__(16) unsigned char hbs_smem[];"
+    assert body.count(dyn) == 1
+    body = body.replace(dyn, "unsigned char* hbs_smem = host_dynamic_smem;")
+    structs = [re.search(r"struct %s \{.*?\n\};" % n, hdr, re.S).group(0) for n in ("HbsNode",)]
+    d = tmp_path_factory.mktemp("hbs_node_host")
+    code = ('#include "cuda_host_shim.h"\nalignas(16) static unsigned char host_dynamic_smem[256 * 1024];\n'
+            "namespace ddst {\n" + "\n".join(structs) + "\n" + body + "\n}  // namespace ddst\n" + NODE_MAIN)
+    (d / "hbs_node_host.cpp").write_text(code)
+    exe = d / "hbs_node_host"
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-I", os.path.join(ROOT, "tests", "hostemu"),
+                        str(d / "hbs_node_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return d, exe
+
+
+def _node_case(d, S, k, leaf, rng):
+    """Samples of S and the node table of one operator in the library's layout: heap-ordered
+    nodes with U, V, D offsets, and per step from the leaves the nodes with the rows of their
+    samples (in_row) and of their k reduced rows in the next level's arrays (out_row)."""
+    ng = S.shape[0]
+    s = 3 * k + 10
+    Om, Ps = rng.standard_normal((ng, s)), rng.standard_normal((ng, s))
+    Y, Z = S @ Om, S.T @ Ps
+    L = O.hodlr_levels(ng, leaf)
+    nodes, fo = [], 0
+    for lev in range(L + 1):
+        for t in range(1 << lev):
+            lo = (t * ng) >> lev
+            n = (((t + 1) * ng) >> lev) - lo if lev == L else (2 * k if L > 0 else ng)
+            nd = dict(level=lev, t=t, lo=lo, n=n, in_row=0, out_row=0, u=-1, v=-1)
+            if lev > 0:
+                nd["u"] = fo; fo += n * k
+                nd["v"] = fo; fo += n * k
+            nd["d"] = fo; fo += n * n
+            nodes.append(nd)
+    steps = [[(1 << lev) - 1 + t for t in range(1 << lev)] for lev in range(L, -1, -1)]
+    for dd, ids in enumerate(steps):
+        nxt = 0
+        for i in ids:
+            nd = nodes[i]
+            if dd == 0:
+                nd["in_row"] = nd["lo"]
+            if nd["level"] > 0:
+                nd["out_row"] = nxt
+                nxt += k
+                if nd["t"] % 2 == 0:
+                    nodes[(1 << (nd["level"] - 1)) - 1 + nd["t"] // 2]["in_row"] = nd["out_row"]
+    path = d / f"node_{ng}_{k}_{leaf}.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("7q", ng, k, s, len(nodes), len(steps), fo, max(nd["n"] for nd in nodes)))
+        for nd in nodes:
+            f.write(struct.pack("10q", 0, nd["level"], nd["n"], nd["t"], nd["lo"], nd["in_row"],
+                                nd["out_row"], nd["u"], nd["v"], nd["d"]))
+        for ids in steps:
+            f.write(struct.pack("q", len(ids)))
+            f.write(struct.pack("%dq" % len(ids), *ids))
+        for a in (Y, Z, Om, Ps):
+            f.write(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    return path, nodes, L, O.hbs_compress(Y, Z, Om, Ps, k, leaf)
+
+
+def _expand(F, nodes, L, k):
+    """Dense operator of the factors: A_0 = D_0, A_l = U_l A_{l-1} V_l^T + D_l."""
+    import scipy.linalg as sla
+
+    def mat(off, r, c):
+        return F[off:off + r * c].reshape(c, r).T
+
+    A = mat(nodes[0]["d"], nodes[0]["n"], nodes[0]["n"])
+    for lev in range(1, L + 1):
+        lv = nodes[(1 << lev) - 1:(2 << lev) - 1]
+        A = (sla.block_diag(*[mat(nd["u"], nd["n"], k) for nd in lv]) @ A
+             @ sla.block_diag(*[mat(nd["v"], nd["n"], k) for nd in lv]).T
+             + sla.block_diag(*[mat(nd["d"], nd["n"], nd["n"]) for nd in lv]))
+    return A
+
+
+@pytest.mark.parametrize("kind,ng,k,leaf", [("exact", 200, 6, 12), ("exact", 137, 4, 8),
+                                            ("exact", 9, 3, 12), ("exact", 40, 5, 10),
+                                            ("transfer", 127, 8, 16)])
+def test_hbs_node_kernel_on_the_host_matches_the_oracle(node_harness, kind, ng, k, leaf):
+    """Same S, Omega, Psi: the factors the node kernel writes define the oracle's operator."""
+    d, exe = node_harness
+    rng = np.random.default_rng(ng + 3 * k)
+    if kind == "exact":
+        from test_oracle_pins import _random_hbs
+        S = _random_hbs(ng, k, leaf, rng)
+    else:
+        import ddst_inputs as I
+        prob = I.make_problem("convdiff2d", n=128, w=16)
+        A, b = O.assemble(prob)
+        geo = O.slab_geometry(2, 128, 16)
+        S = np.asarray(O.transfer_blocks(A, geo, O.factor_local(A, geo), slabs=[2])[1][0])
+    path, nodes, L, Ho = _node_case(d, S, k, leaf, rng)
+    out = d / (path.name + ".F")
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    F = np.fromfile(out, dtype=np.float64)
+    Do = O.hbs_dense(Ho)
+    err_o = np.linalg.norm(Do - S) / np.linalg.norm(S)
+    assert np.linalg.norm(_expand(F, nodes, L, k) - Do) <= max(1e-10, 2 * err_o) * np.linalg.norm(S)
