@@ -22,6 +22,9 @@ from oracle import ddst_oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer turns every out-of-bounds access of the kernels (shared arrays are statics,
+# device buffers are host vectors) into a failure
+SANITIZE = ["-fsanitize=address", "-fno-omit-frame-pointer"]
 
 MAIN = r'''
 #include <cstdio>
@@ -97,7 +100,7 @@ def harness(tmp_path_factory):
             src[i:j] + "\n}  // namespace ddst\n" + MAIN)
     (d / "hbs_apply_host.cpp").write_text(code)
     exe = d / "hbs_apply_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-I", os.path.join(ROOT, "tests", "hostemu"),
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", *SANITIZE, "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "hbs_apply_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
     return d, exe
@@ -175,9 +178,9 @@ using namespace ddst;
 int main(int argc, char** argv) {
   std::ifstream f(argv[1], std::ios::binary);
   auto rd = [&](int64_t* p, int n) { f.read((char*)p, 8 * n); };
-  int64_t h[7]; rd(h, 7);
+  int64_t h[8]; rd(h, 8);
   const int ng = (int)h[0], k = (int)h[1], s = (int)h[2], nn = (int)h[3], nsteps = (int)h[4];
-  const int64_t nf = h[5]; const int nmax = (int)h[6];
+  const int64_t nf = h[5], rows_max = h[7]; const int nmax = (int)h[6];
   std::vector<HbsNode> nodes(nn);
   for (auto& nd : nodes) {
     int64_t a[10]; rd(a, 10);
@@ -191,10 +194,13 @@ int main(int argc, char** argv) {
     for (auto& id : st) { int64_t v; rd(&v, 1); id = (int)v; }
   }
   const int64_t rows = (int64_t)ng;
-  std::vector<double> arr[8];
-  for (auto& a : arr) a.assign(rows * s + (int64_t)(1 << 12) * s, 0.0);
+  std::vector<double> arr[8];  // the level arrays at the size the library allocates
+  for (auto& a : arr) a.assign(rows_max * s, 0.0);
   for (int q = 0; q < 4; ++q) f.read((char*)arr[q].data(), 8 * rows * s);  // Y, Z, Omega, Psi
   std::vector<double> F(nf, 0.0);
+  // the node workspace of the launch, exactly the size the library requests
+  std::vector<unsigned char> dyn(hbs_node_smem(nmax, s, k, sizeof(double)));
+  host_dynamic_smem = dyn.data();
   double *Yc = arr[0].data(), *Zc = arr[1].data(), *Oc = arr[2].data(), *Pc = arr[3].data();
   double *Yn = arr[4].data(), *Zn = arr[5].data(), *On = arr[6].data(), *Pn = arr[7].data();
   for (int d = 0; d < nsteps; ++d) {
@@ -223,14 +229,14 @@ def node_harness(tmp_path_factory):
     body = src[i:j]
     dyn = "extern __shared__ __align__(16) unsigned char hbs_smem[];"
     assert body.count(dyn) == 1
-    body = body.replace(dyn, "unsigned char* hbs_smem = host_dynamic_smem;")
+    body = body.replace(dyn, "unsigned char* hbs_smem = host_dynamic_smem;")  # sized exactly below
     structs = [re.search(r"struct %s \{.*?\n\};" % n, hdr, re.S).group(0) for n in ("HbsNode",)]
     d = tmp_path_factory.mktemp("hbs_node_host")
-    code = ('#include "cuda_host_shim.h"\nalignas(16) static unsigned char host_dynamic_smem[256 * 1024];\n'
+    code = ('#include "cuda_host_shim.h"\nstatic unsigned char* host_dynamic_smem = nullptr;\n'
             "namespace ddst {\n" + "\n".join(structs) + "\n" + body + "\n}  // namespace ddst\n" + NODE_MAIN)
     (d / "hbs_node_host.cpp").write_text(code)
     exe = d / "hbs_node_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-I", os.path.join(ROOT, "tests", "hostemu"),
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", *SANITIZE, "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "hbs_node_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
     return d, exe
@@ -270,7 +276,8 @@ def _node_case(d, S, k, leaf, rng):
                     nodes[(1 << (nd["level"] - 1)) - 1 + nd["t"] // 2]["in_row"] = nd["out_row"]
     path = d / f"node_{ng}_{k}_{leaf}.bin"
     with open(path, "wb") as f:
-        f.write(struct.pack("7q", ng, k, s, len(nodes), len(steps), fo, max(nd["n"] for nd in nodes)))
+        f.write(struct.pack("8q", ng, k, s, len(nodes), len(steps), fo, max(nd["n"] for nd in nodes),
+                            max(ng, (1 << L) * k)))
         for nd in nodes:
             f.write(struct.pack("10q", 0, nd["level"], nd["n"], nd["t"], nd["lo"], nd["in_row"],
                                 nd["out_row"], nd["u"], nd["v"], nd["d"]))
