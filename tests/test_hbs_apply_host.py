@@ -8,7 +8,10 @@ re-statement of the same arithmetic would hide.
   nodes, U, V and D column-major): the output equals the oracle's telescoping apply (Sec. 2.4)
   to rounding, in both directions, on trees of depth 0 to 6 with ragged leaves.
 * The node compression kernel, level by level from the leaves, on the oracle's samples
-  (Alg. 1's Y = S Omega, Z = S^T Psi): the operator its factors define equals the oracle's."""
+  (Alg. 1's Y = S Omega, Z = S^T Psi): the operator its factors define equals the oracle's.
+* The sampling kernel: Y = S Omega and Z = S^T Psi with ragged tiles equal the plain product.
+
+Every build runs under AddressSanitizer with buffers at the sizes the library allocates."""
 import os
 import re
 import shutil
@@ -329,3 +332,74 @@ def test_hbs_node_kernel_on_the_host_matches_the_oracle(node_harness, kind, ng, 
     Do = O.hbs_dense(Ho)
     err_o = np.linalg.norm(Do - S) / np.linalg.norm(S)
     assert np.linalg.norm(_expand(F, nodes, L, k) - Do) <= max(1e-10, 2 * err_o) * np.linalg.norm(S)
+
+
+# ---------------------------------------------------------------------------------------------
+# The sampling kernel (Y = S Omega, Z = S^T Psi) on the host
+# ---------------------------------------------------------------------------------------------
+SAMPLE_MAIN = r'''
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  int64_t h[3]; f.read((char*)h, 24);
+  const int64_t ng = h[0]; const int s = (int)h[1], trans = (int)h[2];
+  std::vector<double> S(ng * ng), G(ng * s), Y(ng * s, 0.0);
+  f.read((char*)S.data(), 8 * ng * ng); f.read((char*)G.data(), 8 * ng * s);
+  SampBlk sb{S.data(), ng, 0};
+  std::vector<SampItem> items;
+  for (int64_t lo = 0; lo < ng; lo += 64) items.push_back(SampItem{0, lo});
+  auto run = [&](auto kern) {
+    host_launch((unsigned)items.size(), 256, [&] { kern(items.data(), &sb, G.data(), Y.data(), s, trans); });
+  };
+  if (s <= 32) run(k_hbs_sample<double, 2>);
+  else if (s <= 64) run(k_hbs_sample<double, 4>);
+  else run(k_hbs_sample<double, 6>);
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)Y.data(), 8 * ng * s);
+  return 0;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def sample_harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = open(os.path.join(CSRC, "hbs.cu")).read()
+    structs = [re.search(r"struct %s \{.*?\n\};" % n, src, re.S).group(0) for n in ("SampBlk", "SampItem")]
+    i = src.index("// Y = S Omega (trans 0) or Z = S^T Psi (trans 1)")
+    j = src.rindex("// ----", 0, src.index("// Node compression\n"))
+    d = tmp_path_factory.mktemp("hbs_sample_host")
+    code = ('#include "cuda_host_shim.h"\nnamespace ddst {\n' + "\n".join(structs) + "\n" + src[i:j] +
+            "\n}  // namespace ddst\n" + SAMPLE_MAIN)
+    (d / "hbs_sample_host.cpp").write_text(code)
+    exe = d / "hbs_sample_host"
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", *SANITIZE, "-I",
+                        os.path.join(ROOT, "tests", "hostemu"), str(d / "hbs_sample_host.cpp"),
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return d, exe
+
+
+@pytest.mark.parametrize("ng,s", [(200, 28), (77, 58), (130, 94), (31, 19)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_hbs_sample_kernel_on_the_host(sample_harness, ng, s, trans):
+    """Y = S Omega (Z = S^T Psi) over 64-row tiles with ragged row, column and sample tails,
+    S column-major as the library stores it, against the plain product."""
+    d, exe = sample_harness
+    rng = np.random.default_rng(ng + s + trans)
+    S = rng.standard_normal((ng, ng))
+    G = rng.standard_normal((ng, s))
+    path = d / f"sample_{ng}_{s}_{trans}.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("3q", ng, s, trans))
+        f.write(np.ascontiguousarray(S.T).tobytes())  # column-major S
+        f.write(G.tobytes())
+    out = d / (path.name + ".y")
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    Y = np.fromfile(out, dtype=np.float64).reshape(ng, s)
+    want = (S.T if trans else S) @ G
+    assert np.abs(Y - want).max() <= 1e-12 * np.abs(want).max()
