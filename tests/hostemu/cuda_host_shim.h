@@ -60,6 +60,26 @@ inline T warp_sum(T v) {
   return v;
 }
 
+// Runs `body` for every CTA of a (gx, gy) grid of `threads`-thread CTAs.
+inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
+                         const std::function<void()>& body) {
+  blockDim.x = threads;
+  for (unsigned by = 0; by < gy; ++by)
+    for (unsigned bx = 0; bx < gx; ++bx) {
+      std::barrier<> cta(threads);
+      g_cta_barrier = &cta;
+      for (auto& k : g_arrive)
+        for (auto& w : k)
+          for (auto& c : w) c.store(0);
+      std::vector<std::thread> ts;
+      for (unsigned t = 0; t < threads; ++t)
+        ts.emplace_back([&body, t, bx, by] {
+          threadIdx.x = t; blockIdx.x = bx; blockIdx.y = by; body();
+        });
+      for (auto& t : ts) t.join();
+    }
+}
+
 // Runs `body` for every CTA of a one-dimensional grid of `threads`-thread CTAs.
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {
   blockDim.x = threads;
