@@ -80,6 +80,25 @@ inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
     }
 }
 
+// Runs `body` for every CTA of a (gx, gy) grid of (bx, by)-thread CTAs (two-dimensional
+// blocks: threadIdx.x = t % bx, threadIdx.y = t / bx; no warp operations).
+inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
+                          const std::function<void()>& body) {
+  const unsigned threads = bx * by;
+  blockDim.x = bx;
+  for (unsigned gyy = 0; gyy < gy; ++gyy)
+    for (unsigned gxx = 0; gxx < gx; ++gxx) {
+      std::barrier<> cta(threads);
+      g_cta_barrier = &cta;
+      std::vector<std::thread> ts;
+      for (unsigned t = 0; t < threads; ++t)
+        ts.emplace_back([&body, t, bx, gxx, gyy] {
+          threadIdx.x = t % bx; threadIdx.y = t / bx; blockIdx.x = gxx; blockIdx.y = gyy; body();
+        });
+      for (auto& t : ts) t.join();
+    }
+}
+
 // Runs `body` for every CTA of a one-dimensional grid of `threads`-thread CTAs.
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {
   blockDim.x = threads;
