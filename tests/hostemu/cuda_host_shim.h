@@ -23,7 +23,7 @@
 
 struct HostDim3 { unsigned x = 0, y = 0, z = 0; };
 inline thread_local HostDim3 threadIdx, blockIdx;
-inline HostDim3 blockDim{256, 1, 1};
+inline HostDim3 blockDim{256, 1, 1}, gridDim{1, 1, 1};
 inline std::barrier<>* g_cta_barrier = nullptr;
 // Warp-level synchronisation over the lanes of a mask (the whole warp, or a group of lanes
 // that always synchronise together): per-lane arrival counters, one set per mask kind, so that
@@ -50,6 +50,10 @@ inline T __shfl_xor_sync(unsigned mask, T v, int lane_mask) {
 }
 template <typename T>
 inline T __ldcg(const T* p) { return *p; }
+// CTAs run one after another here, so device-scope atomics and fences only need to be atomic
+inline unsigned atomicAdd(unsigned* p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_add(v); }
+inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
+inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 using std::fma;
 using std::max;
 using std::min;
@@ -102,6 +106,7 @@ inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
 // Runs `body` for every CTA of a one-dimensional grid of `threads`-thread CTAs.
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {
   blockDim.x = threads;
+  gridDim.x = grid;
   for (unsigned b = 0; b < grid; ++b) {
     std::barrier<> cta(threads);
     g_cta_barrier = &cta;
