@@ -68,6 +68,8 @@ inline T warp_sum(T v) {
 inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
                          const std::function<void()>& body) {
   blockDim.x = threads;
+  gridDim.x = gx;
+  gridDim.y = gy;
   for (unsigned by = 0; by < gy; ++by)
     for (unsigned bx = 0; bx < gx; ++bx) {
       std::barrier<> cta(threads);
@@ -90,6 +92,9 @@ inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
                           const std::function<void()>& body) {
   const unsigned threads = bx * by;
   blockDim.x = bx;
+  blockDim.y = by;
+  gridDim.x = gx;
+  gridDim.y = gy;
   for (unsigned gyy = 0; gyy < gy; ++gyy)
     for (unsigned gxx = 0; gxx < gx; ++gxx) {
       std::barrier<> cta(threads);
@@ -107,6 +112,7 @@ inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {
   blockDim.x = threads;
   gridDim.x = grid;
+  gridDim.y = 1;
   for (unsigned b = 0; b < grid; ++b) {
     std::barrier<> cta(threads);
     g_cta_barrier = &cta;
