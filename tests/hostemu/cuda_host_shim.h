@@ -53,6 +53,7 @@ inline T __ldcg(const T* p) { return *p; }
 // CTAs run one after another here, so device-scope atomics and fences only need to be atomic
 inline unsigned atomicAdd(unsigned* p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_add(v); }
 inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
+inline double atomicAdd(double* p, double v) { return std::atomic_ref<double>(*p).fetch_add(v); }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 using std::fma;
 using std::max;
