@@ -65,64 +65,47 @@ inline T warp_sum(T v) {
   return v;
 }
 
-// Runs `body` for every CTA of a (gx, gy) grid of `threads`-thread CTAs.
-inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
-                         const std::function<void()>& body) {
-  blockDim.x = threads;
-  gridDim.x = gx;
-  gridDim.y = gy;
-  for (unsigned by = 0; by < gy; ++by)
-    for (unsigned bx = 0; bx < gx; ++bx) {
-      std::barrier<> cta(threads);
-      g_cta_barrier = &cta;
-      for (auto& k : g_arrive)
-        for (auto& w : k)
-          for (auto& c : w) c.store(0);
-      std::vector<std::thread> ts;
-      for (unsigned t = 0; t < threads; ++t)
-        ts.emplace_back([&body, t, bx, by] {
-          threadIdx.x = t; blockIdx.x = bx; blockIdx.y = by; body();
-        });
-      for (auto& t : ts) t.join();
-    }
-}
-
-// Runs `body` for every CTA of a (gx, gy) grid of (bx, by)-thread CTAs (two-dimensional
-// blocks: threadIdx.x = t % bx, threadIdx.y = t / bx; no warp operations).
-inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
+// Runs `body` for every CTA of a (gx, gy) grid of (bx, by)-thread CTAs, one CTA after another:
+// bx * by OS threads (threadIdx.x = t % bx, threadIdx.y = t / bx) walk the CTAs together, with a
+// barrier at the end of each CTA (a kernel's early return only skips to it).
+inline void host_run_grid(unsigned gx, unsigned gy, unsigned bx, unsigned by,
                           const std::function<void()>& body) {
   const unsigned threads = bx * by;
   blockDim.x = bx;
   blockDim.y = by;
   gridDim.x = gx;
   gridDim.y = gy;
-  for (unsigned gyy = 0; gyy < gy; ++gyy)
-    for (unsigned gxx = 0; gxx < gx; ++gxx) {
-      std::barrier<> cta(threads);
-      g_cta_barrier = &cta;
-      std::vector<std::thread> ts;
-      for (unsigned t = 0; t < threads; ++t)
-        ts.emplace_back([&body, t, bx, gxx, gyy] {
-          threadIdx.x = t % bx; threadIdx.y = t / bx; blockIdx.x = gxx; blockIdx.y = gyy; body();
-        });
-      for (auto& t : ts) t.join();
-    }
+  for (auto& k : g_arrive)
+    for (auto& w : k)
+      for (auto& c : w) c.store(0);
+  std::barrier<> cta(threads), end(threads);
+  g_cta_barrier = &cta;
+  std::vector<std::thread> ts;
+  for (unsigned t = 0; t < threads; ++t)
+    ts.emplace_back([&body, &end, t, bx, gx, gy] {
+      threadIdx.x = t % bx;
+      threadIdx.y = t / bx;
+      for (unsigned yy = 0; yy < gy; ++yy)
+        for (unsigned xx = 0; xx < gx; ++xx) {
+          blockIdx.x = xx;
+          blockIdx.y = yy;
+          body();
+          end.arrive_and_wait();
+        }
+    });
+  for (auto& t : ts) t.join();
 }
 
-// Runs `body` for every CTA of a one-dimensional grid of `threads`-thread CTAs.
+inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
+                         const std::function<void()>& body) {
+  host_run_grid(gx, gy, threads, 1, body);
+}
+
+inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
+                          const std::function<void()>& body) {
+  host_run_grid(gx, gy, bx, by, body);
+}
+
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {
-  blockDim.x = threads;
-  gridDim.x = grid;
-  gridDim.y = 1;
-  for (unsigned b = 0; b < grid; ++b) {
-    std::barrier<> cta(threads);
-    g_cta_barrier = &cta;
-    for (auto& k : g_arrive)
-      for (auto& w : k)
-        for (auto& c : w) c.store(0);
-    std::vector<std::thread> ts;
-    for (unsigned t = 0; t < threads; ++t)
-      ts.emplace_back([&body, t, b] { threadIdx.x = t; blockIdx.x = b; body(); });
-    for (auto& t : ts) t.join();
-  }
+  host_run_grid(grid, 1, threads, 1, body);
 }
