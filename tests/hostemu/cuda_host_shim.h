@@ -20,6 +20,10 @@
 #define __launch_bounds__(x)
 #define __restrict__
 #define __shared__ static
+#define __align__(x) __attribute__((aligned(x)))
+
+struct alignas(16) float4 { float x, y, z, w; };
+struct alignas(16) double2 { double x, y; };
 
 struct HostDim3 { unsigned x = 0, y = 0, z = 0; };
 inline thread_local HostDim3 threadIdx, blockIdx;
