@@ -3,7 +3,8 @@ first cancels more than half of ||w||, then the Givens update of the (I - K) Hes
 `k_arn_dots`, `k_arn_update`, `k_arn_finish` of `csrc/krylov.cu`), compiled for the host and run
 with one OS thread per CUDA thread under AddressSanitizer (`tests/hostemu/cuda_host_shim.h`) in
 the order the library launches them, over vectors of several 1024-entry chunks with a ragged
-tail.  The residual estimates and the solution equal those of the oracle's unrestarted GMRES on
+tail, from the normalised start vector (`k_normalize_start`) to the solution (`k_trisolve`,
+`k_combine_basis`).  The residual estimates and the solution equal those of the oracle's unrestarted GMRES on
 I - K (O4; Sec. 5.2: x0 = 0, CGS2, Givens rotations): the Krylov spaces of K and I - K coincide."""
 import os
 import re
@@ -35,11 +36,12 @@ int main(int argc, char** argv) {
       gv(kmax + 1, 0.0), resid(kmax, 0.0), beta(1);
   int kdev[2] = {1, 0};
   unsigned ticket = 0;
-  double bn = 0.0;
-  for (double v : b) bn += v * v;
-  bn = std::sqrt(bn);
-  beta[0] = bn; gv[0] = bn;
-  for (int64_t e = 0; e < n; ++e) V[e] = b[e] / bn;
+  double bn2 = 0.0;
+  for (double v : b) bn2 += v * v;
+  beta[0] = std::sqrt(bn2); gv[0] = beta[0];
+  std::vector<double> dynbuf(kmax + 1);
+  host_dynamic_smem = dynbuf.data();
+  host_launch(4, 256, [&] { k_normalize_start(b.data(), &bn2, V.data(), n); });  // V[0] = b / ||b||
   double* P1 = part.data();
   double* P2 = P1 + (int64_t)(kmax + 1) * nchunk;
   double* Pn = P2 + (int64_t)(kmax + 1) * nchunk;
@@ -56,7 +58,12 @@ int main(int argc, char** argv) {
     host_launch(nchunk, ARN_T, [&] { k_arn_update(V.data(), w.data(), n, kdev, P2, h2.data(), nullptr, Pn, nchunk, 0); });
     host_launch(nchunk, ARN_T, [&] { k_arn_finish(V.data(), w.data(), n, kdev, Pn, nchunk, h1.data(), h2.data(), H.data(), ldh, cs.data(), sn.data(), gv.data(), beta.data(), resid.data(), kmax, &ticket); });
   }
+  // the solution: R y = g by back substitution, then x = V y
+  std::vector<double> y(maxit), x(n);
+  host_launch(1, 256, [&] { k_trisolve(H.data(), ldh, gv.data(), maxit, y.data()); });
+  host_launch(4, 256, [&] { k_combine_basis(V.data(), x.data(), y.data(), maxit, n); });
   std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)x.data(), 8 * n);
   o.write((const char*)resid.data(), 8 * maxit);
   o.write((const char*)gv.data(), 8 * (maxit + 1));
   o.write((const char*)H.data(), 8 * (int64_t)ldh * kmax);
@@ -74,9 +81,16 @@ def harness(tmp_path_factory):
     src = open(os.path.join(CSRC, "krylov.cu")).read()
     i = src.index("constexpr int ARN_T")
     j = src.index("int arnoldi_chunks(int64_t n)")
+    s0 = src.index("// GMRES solution from the Krylov basis")
+    s1 = src.index("// ---- Arnoldi step with device-resident state")
+    sol = src[s0:s1]
+    for dyn in ("extern __shared__ double sh[];", "extern __shared__ double rhs[];"):
+        assert sol.count(dyn) == 1
+        sol = sol.replace(dyn, "double* %s = host_dynamic_smem;" % dyn.split()[-1][:-3])
     d = tmp_path_factory.mktemp("arnoldi_host")
     code = ('#include "cuda_host_shim.h"\nusing std::sqrt; using std::fmax; using std::hypot; using std::fabs;\n'
-            "namespace ddst {\n" + src[i:j] + "\n}  // namespace ddst\n" + MAIN)
+            "static double* host_dynamic_smem = nullptr;\n"
+            "namespace ddst {\n" + sol + "\n" + src[i:j] + "\n}  // namespace ddst\n" + MAIN)
     (d / "arnoldi_host.cpp").write_text(code)
     exe = d / "arnoldi_host"
     r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
@@ -110,6 +124,7 @@ def test_gmres_step_kernels_on_the_host_match_the_oracle(harness, n, rho, shift)
     r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     raw = np.fromfile(out, dtype=np.float64)
+    x_k, raw = raw[:n], raw[n:]
     resid = raw[:maxit]
     gv = raw[maxit:2 * maxit + 1]
     H = raw[2 * maxit + 1:2 * maxit + 1 + (kmax + 1) * kmax].reshape(kmax, kmax + 1).T
@@ -121,3 +136,5 @@ def test_gmres_step_kernels_on_the_host_match_the_oracle(harness, n, rho, shift)
     y = sla.solve_triangular(H[:maxit, :maxit], gv[:maxit])
     x = V[:maxit].T @ y
     assert np.linalg.norm(x - x_o) <= 1e-9 * np.linalg.norm(x_o)
+    # the library's own solution kernels (back substitution, basis combination)
+    assert np.linalg.norm(x_k - x_o) <= 1e-9 * np.linalg.norm(x_o)
