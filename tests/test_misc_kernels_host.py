@@ -1,0 +1,144 @@
+"""Two more kernels compiled for the host and run with one OS thread per CUDA thread under
+AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
+* `k_residual_noalloc` + `k_norms_noalloc` (`csrc/noalloc.cu`): r = b(f, g) - A u with ||r||,
+  ||b|| over 256-unknown partial sums, against the oracle's assembled system (O1), in 2D with
+  convection and reaction and in 3D;
+* `k_gemm_fma` (`csrc/gemm_tc.cu`, the FP64 block products of the direct interface solver):
+  C = alpha A B (+ C) on 128-wide tiles, against the plain product."""
+import os
+import re
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+import ddst_inputs as I
+from oracle import ddst_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+
+NOALLOC_MAIN = r'''
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  int64_t h[4]; double bc[3]; f.read((char*)h, 32); f.read((char*)bc, 24);
+  const int dim = (int)h[0], n = (int)h[1], has_c = (int)h[2]; const int64_t nnode = h[3];
+  int64_t ni = 1; for (int d = 0; d < dim; ++d) ni *= (n - 1);
+  std::vector<double> a(nnode), c(nnode), g(nnode), fv(ni), u(ni), r(ni), part(2 * kNoallocMaxBlocks, 0.0), norms(2);
+  f.read((char*)a.data(), 8 * nnode); f.read((char*)c.data(), 8 * nnode); f.read((char*)g.data(), 8 * nnode);
+  f.read((char*)fv.data(), 8 * ni); f.read((char*)u.data(), 8 * ni);
+  const unsigned nblk = (unsigned)((ni + kNoallocThreads - 1) / kNoallocThreads);
+  host_launch(nblk, kNoallocThreads, [&] { k_residual_noalloc(dim, n, bc[0], bc[1], bc[2], a.data(), has_c ? c.data() : nullptr, fv.data(), g.data(), u.data(), r.data(), part.data(), ni); });
+  host_launch(1, 256, [&] { k_norms_noalloc(part.data(), (int)nblk, norms.data()); });
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)r.data(), 8 * ni); o.write((const char*)norms.data(), 16);
+  return 0;
+}
+'''
+
+GEMM_MAIN = r'''
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  int64_t h[2]; f.read((char*)h, 16);
+  const int nT = (int)h[0], ntasks = (int)h[1]; const int64_t ld = (int64_t)nT * BT;
+  std::vector<std::vector<double>> A(ntasks, std::vector<double>(ld * ld)), B = A, Cm = A;
+  std::vector<GemmTaskT<double>> tasks(ntasks);
+  for (int q = 0; q < ntasks; ++q) {
+    double alpha; int64_t acc; f.read((char*)&alpha, 8); f.read((char*)&acc, 8);
+    f.read((char*)A[q].data(), 8 * ld * ld); f.read((char*)B[q].data(), 8 * ld * ld); f.read((char*)Cm[q].data(), 8 * ld * ld);
+    tasks[q] = GemmTaskT<double>{A[q].data(), B[q].data(), Cm[q].data(), alpha, (int)acc};
+  }
+  host_launch2(nT * nT, ntasks, 256, [&] { k_gemm_fma<double>(tasks.data(), nT); });
+  std::ofstream o(argv[2], std::ios::binary);
+  for (int q = 0; q < ntasks; ++q) o.write((const char*)Cm[q].data(), 8 * ld * ld);
+  return 0;
+}
+'''
+
+
+def _build(d, name, code):
+    cxx = shutil.which("g++")
+    (d / f"{name}.cpp").write_text(code)
+    exe = d / name
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+                        "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
+                        str(d / f"{name}.cpp"), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    return tmp_path_factory.mktemp("misc_host")
+
+
+@pytest.mark.parametrize("name,n,over", [("convdiff2d", 24, {}), ("helmholtz2d", 20, {}),
+                                         ("vardiff3d", 10, {"b": (1.0, -0.5, 2.0)})])
+def test_noalloc_residual_on_the_host(workdir, name, n, over):
+    src = open(os.path.join(CSRC, "noalloc.cu")).read()
+    # The kernels and their constants: from the constants to the host-side helpers, without the
+    # file-scope device array (the host test passes its own partial-sum buffer).
+    body = src[src.index("constexpr int kNoallocThreads"):src.index("namespace {")]
+    body = re.sub(r"static __device__ __align__\(256\) double g_noalloc_partials\[[^\]]*\];", "", body)
+    assert "g_noalloc_partials" not in body and "k_norms_noalloc" in body
+    code = '#include "cuda_host_shim.h"\nnamespace ddst {\n' + body + "\n}  // namespace ddst\n" + NOALLOC_MAIN
+    exe = _build(workdir, "noalloc_host", code)
+    prob = I.make_problem(name, n=n, w=n // 4, **over)
+    dim = prob["dim"]
+    nnode = (n + 1) ** dim
+    has_c = prob.get("c") is not None
+    bb = list(prob["b"]) + [0.0] * (3 - len(prob["b"]))
+    A, b = O.assemble(prob)
+    u = np.random.default_rng(n).standard_normal(b.size)
+    path = workdir / f"noalloc_{name}.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("4q", dim, n, int(has_c), nnode) + struct.pack("3d", *bb))
+        for arr in (prob["a"], prob["c"] if has_c else np.zeros(nnode), prob["g"], prob["f"]):
+            f.write(np.asarray(arr, dtype=np.float64).ravel().tobytes())
+        f.write(u.tobytes())
+    out = workdir / (path.name + ".out")
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = np.fromfile(out, dtype=np.float64)
+    want = b - A @ u
+    assert np.abs(raw[:-2] - want).max() <= 1e-11 * np.abs(want).max()
+    assert abs(raw[-2] - np.linalg.norm(want)) <= 1e-12 * np.linalg.norm(want)
+    assert abs(raw[-1] - np.linalg.norm(b)) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_gemm_fma_on_the_host(workdir):
+    src = open(os.path.join(CSRC, "gemm_tc.cu")).read()
+    kh = open(os.path.join(CSRC, "kernels.cuh")).read()
+    task = re.search(r"template <typename T>\nstruct GemmTaskT \{.*?\n\};", kh, re.S).group(0)
+    i = src.index("template <typename T>\n__global__ void __launch_bounds__(256) k_gemm_fma(")
+    j = src.index("\n}\n", i) + 3
+    code = ('#include "cuda_host_shim.h"\nnamespace ddst {\nconstexpr int BT = 128;\n' + task + "\n" +
+            src[i:j] + "\n}  // namespace ddst\n" + GEMM_MAIN)
+    exe = _build(workdir, "gemm_host", code)
+    nT, rng = 2, np.random.default_rng(3)
+    ld = nT * 128
+    cases = [(1.0, 0), (-0.5, 1), (2.0, 1)]
+    mats = []
+    path = workdir / "gemm.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("2q", nT, len(cases)))
+        for alpha, acc in cases:
+            A, B, C = (rng.standard_normal((ld, ld)) for _ in range(3))
+            mats.append((alpha, acc, A, B, C))
+            f.write(struct.pack("d", alpha) + struct.pack("q", acc))
+            f.write(A.tobytes() + B.tobytes() + C.tobytes())
+    out = workdir / "gemm.out"
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.fromfile(out, dtype=np.float64).reshape(len(cases), ld, ld)
+    for q, (alpha, acc, A, B, C) in enumerate(mats):
+        want = alpha * (A @ B) + (C if acc else 0.0)
+        assert np.abs(got[q] - want).max() <= 1e-11 * np.abs(want).max()
