@@ -59,6 +59,15 @@ inline unsigned atomicAdd(unsigned* p, unsigned v) { return std::atomic_ref<unsi
 inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
 inline double atomicAdd(double* p, double v) { return std::atomic_ref<double>(*p).fetch_add(v); }
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
+// Host stand-ins for the device intrinsics of the random-number generators: the high half of a
+// 32 x 32-bit product and cos / sin of pi x through the C library.
+inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+inline double cospi(double x) { return std::cos(M_PI * x); }
+inline float cospif(float x) { return (float)std::cos(M_PI * (double)x); }
+inline void sincospif(float x, float* s, float* c) {
+  *s = (float)std::sin(M_PI * (double)x);
+  *c = (float)std::cos(M_PI * (double)x);
+}
 using std::fma;
 using std::max;
 using std::min;
