@@ -78,16 +78,17 @@ inline T warp_sum(T v) {
   return v;
 }
 
-// Runs `body` for every CTA of a (gx, gy) grid of (bx, by)-thread CTAs, one CTA after another:
-// bx * by OS threads (threadIdx.x = t % bx, threadIdx.y = t / bx) walk the CTAs together, with a
-// barrier at the end of each CTA (a kernel's early return only skips to it).
+// Runs `body` for every CTA of a (gx, gy, gz) grid of (bx, by)-thread CTAs, one CTA after
+// another: bx * by OS threads (threadIdx.x = t % bx, threadIdx.y = t / bx) walk the CTAs together,
+// with a barrier at the end of each CTA (a kernel's early return only skips to it).
 inline void host_run_grid(unsigned gx, unsigned gy, unsigned bx, unsigned by,
-                          const std::function<void()>& body) {
+                          const std::function<void()>& body, unsigned gz = 1) {
   const unsigned threads = bx * by;
   blockDim.x = bx;
   blockDim.y = by;
   gridDim.x = gx;
   gridDim.y = gy;
+  gridDim.z = gz;
   for (auto& k : g_arrive)
     for (auto& w : k)
       for (auto& c : w) c.store(0);
@@ -95,16 +96,18 @@ inline void host_run_grid(unsigned gx, unsigned gy, unsigned bx, unsigned by,
   g_cta_barrier = &cta;
   std::vector<std::thread> ts;
   for (unsigned t = 0; t < threads; ++t)
-    ts.emplace_back([&body, &end, t, bx, gx, gy] {
+    ts.emplace_back([&body, &end, t, bx, gx, gy, gz] {
       threadIdx.x = t % bx;
       threadIdx.y = t / bx;
-      for (unsigned yy = 0; yy < gy; ++yy)
-        for (unsigned xx = 0; xx < gx; ++xx) {
-          blockIdx.x = xx;
-          blockIdx.y = yy;
-          body();
-          end.arrive_and_wait();
-        }
+      for (unsigned zz = 0; zz < gz; ++zz)
+        for (unsigned yy = 0; yy < gy; ++yy)
+          for (unsigned xx = 0; xx < gx; ++xx) {
+            blockIdx.x = xx;
+            blockIdx.y = yy;
+            blockIdx.z = zz;
+            body();
+            end.arrive_and_wait();
+          }
     });
   for (auto& t : ts) t.join();
 }
@@ -117,6 +120,11 @@ inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
 inline void host_launch2d(unsigned gx, unsigned gy, unsigned bx, unsigned by,
                           const std::function<void()>& body) {
   host_run_grid(gx, gy, bx, by, body);
+}
+
+inline void host_launch3(unsigned gx, unsigned gy, unsigned gz, unsigned threads,
+                         const std::function<void()>& body) {
+  host_run_grid(gx, gy, threads, 1, body, gz);
 }
 
 inline void host_launch(unsigned grid, unsigned threads, const std::function<void()>& body) {

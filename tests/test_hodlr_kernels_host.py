@@ -3,6 +3,9 @@ thread under AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
 * the tiled transposed product of the compression's power iteration (`k_sblk_gemv_t`,
   y_b = S_b^T x_b for every dense transfer block, Sec. 2.4's ||S||_2 estimate), against the
   plain product on blocks with ragged tiles;
+* the whole power iteration (`k_sblk_gemv`, `k_sblk_gemv_t`, `k_sblk_normalize`, two steps in
+  FP64 and FP32) against the same iteration in numpy, and its estimate of ||S||_2^2 bounded
+  above by the largest squared singular value (an underestimate, as the compression assumes);
 * the interface apply (`k_h_inner` + `k_h_owner`: (I - K) x, its transpose, K x, K^T x in FP64
   and FP32) on the oracle's HODLR factors (O6) in the library's layout, against O6's apply."""
 import os
@@ -85,6 +88,111 @@ def test_transposed_block_products_on_the_host(harness, ngs):
     for q, (B, ng) in enumerate(zip(blocks, ngs)):
         want = B.T @ x[q, :ng]
         assert np.abs(y[q, :ng] - want).max() <= 1e-12 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# The power iteration of the compression: ||S||_2^2 ~ ||S^T S x|| after two normalised steps
+# ---------------------------------------------------------------------------------------------
+POWER_MAIN = r"""
+#include <cstring>
+#include <fstream>
+using namespace ddst;
+template <typename T>
+void run(std::ifstream& f, std::ofstream& o, const std::vector<SBlk>& sb, int64_t tot, int64_t stride) {
+  const int nb = (int)sb.size();
+  int64_t maxng = 0;
+  for (auto& b : sb) maxng = std::max(maxng, b.ng);
+  std::vector<double> S64(tot), x(nb * stride), y(nb * stride), nrm(nb, -1.0);
+  f.read((char*)S64.data(), 8 * tot); f.read((char*)x.data(), 8 * nb * stride);
+  std::vector<T> S(S64.begin(), S64.end());
+  const unsigned gr = (unsigned)((maxng + 255) / 256), gz = (unsigned)((maxng + 127) / 128);
+  for (int it = 0; it < 2; ++it) {
+    std::fill(y.begin(), y.end(), 0.0);
+    host_launch3(gr, nb, gz, 256, [&] { k_sblk_gemv<T>(sb.data(), S.data(), x.data(), y.data(), stride); });
+    host_launch2(gz, nb, 256, [&] { k_sblk_gemv_t<T>(sb.data(), S.data(), y.data(), x.data(), stride); });
+    host_launch(nb, 256, [&] { k_sblk_normalize(sb.data(), x.data(), x.data(), stride, nrm.data()); });
+  }
+  o.write((const char*)x.data(), 8 * nb * stride);
+  o.write((const char*)nrm.data(), 8 * nb);
+}
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  int64_t h[3]; f.read((char*)h, 24);
+  const int nb = (int)h[0]; const int64_t stride = h[1], esz = h[2];
+  std::vector<SBlk> sb(nb);
+  int64_t tot = 0;
+  for (auto& b : sb) { int64_t a[2]; f.read((char*)a, 16); b.off = a[0]; b.ng = a[1]; tot = std::max(tot, a[0] + a[1] * a[1]); }
+  std::ofstream o(argv[2], std::ios::binary);
+  if (esz == 8) run<double>(f, o, sb, tot, stride); else run<float>(f, o, sb, tot, stride);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def power_harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = open(os.path.join(CSRC, "hodlr.cu")).read()
+    sblk = re.search(r"struct SBlk \{.*?\n\};", src, re.S).group(0)
+    i = src.index("template <typename T>\n__global__ void k_sblk_gemv(")
+    j = src.index("__global__ void k_sblk_init(")
+    d = tmp_path_factory.mktemp("power_host")
+    code = ('#include "cuda_host_shim.h"\nnamespace ddst {\n' + sblk + "\n" + src[i:j] +
+            "\n}  // namespace ddst\n" + POWER_MAIN)
+    (d / "power_host.cpp").write_text(code)
+    exe = d / "power_host"
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+                        "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
+                        str(d / "power_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return d, exe
+
+
+@pytest.mark.parametrize("esz", [8, 4])
+def test_power_iteration_on_the_host(power_harness, esz):
+    d, exe = power_harness
+    rng = np.random.default_rng(11)
+    ngs = (300, 129, 1, 257)
+    stride = 310
+    blocks, offs, off = [], [], 0
+    for q, ng in enumerate(ngs):
+        if q == 0:   # geometric spectrum, like a transfer operator's
+            U, _ = np.linalg.qr(rng.standard_normal((ng, ng)))
+            V, _ = np.linalg.qr(rng.standard_normal((ng, ng)))
+            B = (U * 0.6 ** np.arange(ng)) @ V.T
+        else:
+            B = rng.standard_normal((ng, ng)) / np.sqrt(ng)
+        blocks.append(B)
+        offs.append(off)
+        off += ng * ng
+    x0 = rng.standard_normal((len(ngs), stride))
+    path = d / f"power_{esz}.bin"
+    with open(path, "wb") as f:
+        f.write(struct.pack("3q", len(ngs), stride, esz))
+        for o, ng in zip(offs, ngs):
+            f.write(struct.pack("2q", o, ng))
+        for B in blocks:
+            f.write(np.ascontiguousarray(B.T).tobytes())
+        f.write(x0.tobytes())
+    out = d / (path.name + ".out")
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = np.fromfile(out, dtype=np.float64)
+    x, nrm = raw[:len(ngs) * stride].reshape(len(ngs), stride), raw[len(ngs) * stride:]
+    tol = 1e-12 if esz == 8 else 2e-5
+    for q, (B, ng) in enumerate(zip(blocks, ngs)):
+        Bw = B if esz == 8 else B.astype(np.float32).astype(np.float64)
+        v = x0[q, :ng].copy()
+        for _ in range(2):
+            v = Bw.T @ (Bw @ v)
+            nv = np.linalg.norm(v)
+            v /= nv
+        assert abs(nrm[q] - nv) <= tol * nv
+        assert np.abs(x[q, :ng] - v).max() <= 10 * tol
+        smax2 = np.linalg.norm(Bw, 2) ** 2
+        assert nrm[q] <= smax2 * (1 + tol)            # a unit vector's ||S^T S x|| <= sigma_max^2
 
 
 # ---------------------------------------------------------------------------------------------
