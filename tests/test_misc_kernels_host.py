@@ -4,7 +4,10 @@ AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
   ||b|| over 256-unknown partial sums, against the oracle's assembled system (O1), in 2D with
   convection and reaction and in 3D;
 * `k_gemm_fma` (`csrc/gemm_tc.cu`, the FP64 block products of the direct interface solver):
-  C = alpha A B (+ C) on 128-wide tiles, against the plain product."""
+  C = alpha A B (+ C) on 128-wide tiles, against the plain product;
+* the FP64 reductions of `csrc/stencil.cu` (`k_dot_partial` + `k_sum_partials`: the inner
+  products of the refinement; `k_prob_sqnorm_partial` + `k_sum_partials`: per-problem squared
+  norms of a batch) and `k_axpy`, on ragged lengths, against numpy."""
 import os
 import re
 import shutil
@@ -142,3 +145,56 @@ def test_gemm_fma_on_the_host(workdir):
     for q, (alpha, acc, A, B, C) in enumerate(mats):
         want = alpha * (A @ B) + (C if acc else 0.0)
         assert np.abs(got[q] - want).max() <= 1e-11 * np.abs(want).max()
+
+
+REDUCE_MAIN = r"""
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  int64_t h[4]; double a; f.read((char*)h, 32); f.read((char*)&a, 8);
+  const int64_t n = h[0], off1 = h[1], n0 = h[2], n1 = h[3];
+  std::vector<double> x(n), y(n), part(64, 0.0), out(4, 0.0);
+  f.read((char*)x.data(), 8 * n); f.read((char*)y.data(), 8 * n);
+  // <x, y> over n with 7 CTAs (grid-stride), then one CTA sums the partials
+  host_launch(7, 256, [&] { k_dot_partial(x.data(), y.data(), n, part.data()); });
+  host_launch(1, 256, [&] { k_sum_partials(part.data(), 7, out.data()); });
+  // per-problem ||x||^2: problem 0 = x[0, n0), problem 1 = x[off1, off1 + n1); 5 CTAs each
+  std::vector<ProbDesc> P(2);
+  P[0].vol_off = 0; P[0].nint = n0; P[1].vol_off = off1; P[1].nint = n1;
+  host_launch2(5, 2, 256, [&] { k_prob_sqnorm_partial(P.data(), x.data(), part.data()); });
+  host_launch(2, 256, [&] { k_sum_partials(part.data(), 5, out.data() + 1); });
+  host_launch(3, 128, [&] { k_axpy(n, a, x.data(), y.data()); });
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)out.data(), 24); o.write((const char*)y.data(), 8 * n);
+  return 0;
+}
+"""
+
+
+def test_reductions_and_axpy_on_the_host(workdir):
+    src = open(os.path.join(CSRC, "stencil.cu")).read()
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    prob = re.search(r"struct ProbDesc \{.*?\n\};", common, re.S).group(0)
+    red = src[src.index("// Partial sums of x.y over n elements"):src.index("// IMEX right-hand side")]
+    axpy = src[src.index("// y = a*x + y  (FP64)"):src.index("// Host launchers")]
+    code = ('#include "cuda_host_shim.h"\nnamespace ddst {\n' + prob + "\n" + red + "\n" + axpy +
+            "\n}  // namespace ddst\n" + REDUCE_MAIN)
+    exe = _build(workdir, "reduce_host", code)
+    rng = np.random.default_rng(5)
+    n, off1, n0, n1, a = 10007, 5000, 4999, 3001, -0.75
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    path = workdir / "reduce.bin"
+    path.write_bytes(struct.pack("4q", n, off1, n0, n1) + struct.pack("d", a) + x.tobytes() +
+                     y.tobytes())
+    out = workdir / "reduce.out"
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = np.fromfile(out, dtype=np.float64)
+    # summation in another order: |error| <= n eps sum |x_i y_i| (Higham, Sec. 3.1)
+    assert abs(raw[0] - x @ y) <= n * 2.2e-16 * np.abs(x * y).sum()
+    assert abs(raw[1] - x[:n0] @ x[:n0]) <= 1e-13 * (x[:n0] @ x[:n0])
+    assert abs(raw[2] - x[off1:off1 + n1] @ x[off1:off1 + n1]) <= 1e-13 * (x[off1:off1 + n1] @ x[off1:off1 + n1])
+    # one rounding, or none where the compiler contracts to a fused multiply-add
+    want = y + a * x
+    assert (np.abs(raw[3:] - want) <= 2.3e-16 * (np.abs(want) + np.abs(a * x))).all()

@@ -8,6 +8,7 @@ J_{j,j'}) and its assembled matrix (O1):
   -A(I_j, J_{j,j-1}) u_{j-1} - A(I_j, J_{j,j+1}) u_{j+1} (from the stencil pack);
 * `k_scatter`: the owned planes of the slabs partition the interior unknowns;
 * `k_gather_T`: adds each unknown once per double slab that contains it (1 or 2);
+* `k_gather_owned`: the gather restricted to the planes each slab owns (adjoint of the scatter);
 * `k_iface_dirichlet_T`, `k_inject_center`: the transposes of the two interface maps
   (dot-product identities), in 2D and 3D."""
 import os
@@ -52,7 +53,7 @@ int main(int argc, char** argv) {
   f.read((char*)uG.data(), 8 * nds * ng); f.read((char*)z.data(), 8 * nloc);
   std::vector<double> pack((int64_t)nds * nb * PK_NFIELDS * M), vol(nint), gmap(nloc, -1.0),
       center(nds * ng, 0.0), dir(nloc, 0.0), ones(nloc, 1.0), scat(nint, 0.0), gT(nint, 0.0),
-      idT(nds * ng, 0.0), inj(nloc, 0.0);
+      idT(nds * ng, 0.0), inj(nloc, 0.0), owned(nloc, -1.0);
   for (int64_t e = 0; e < nint; ++e) vol[e] = (double)e;
   auto L = [&](std::function<void()> fn) { host_launch2(2, nds, 128, fn); };
   host_launch2(nb, nds, 128, [&] { k_stencil_pack<double>(slabs.data(), &P, A.data(), C.data(), pack.data()); });
@@ -63,8 +64,9 @@ int main(int argc, char** argv) {
   L([&] { k_gather_T<double>(slabs.data(), ones.data(), gT.data()); });
   L([&] { k_iface_dirichlet_T<double>(slabs.data(), &P, pack.data(), z.data(), idT.data()); });
   L([&] { k_inject_center<double>(slabs.data(), uG.data(), inj.data()); });
+  L([&] { k_gather_owned<double>(slabs.data(), &P, vol.data(), owned.data()); });
   std::ofstream o(argv[2], std::ios::binary);
-  for (auto* v : {&gmap, &center, &dir, &scat, &gT, &idT, &inj}) o.write((const char*)v->data(), 8 * v->size());
+  for (auto* v : {&gmap, &center, &dir, &scat, &gT, &idT, &inj, &owned}) o.write((const char*)v->data(), 8 * v->size());
   return 0;
 }
 '''
@@ -125,8 +127,8 @@ def test_slab_geometry_kernels_on_the_host(harness, name, n, w):
     r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     raw = np.fromfile(out, dtype=np.float64)
-    sizes = [nloc, nds * ng, nloc, nint, nint, nds * ng, nloc]
-    gmap, center, dirv, scat, gT, idT, inj = np.split(raw, np.cumsum(sizes)[:-1])
+    sizes = [nloc, nds * ng, nloc, nint, nint, nds * ng, nloc, nloc]
+    gmap, center, dirv, scat, gT, idT, inj, owned = np.split(raw, np.cumsum(sizes)[:-1])
     gmap = gmap.reshape(nds, nb, M)
     A = sp.csr_matrix(O.assemble(prob)[0])
     count = np.zeros(nint)
@@ -145,6 +147,15 @@ def test_slab_geometry_kernels_on_the_host(harness, name, n, w):
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
         count[geo.I[j]] += 1
     assert np.all(scat == 1.0)             # owned planes partition the interior
+    # gather restricted to the owned planes (the adjoint of the scatter): slab j owns its first
+    # w x-planes, the last slab all 2w - 1; the rest of the row and the padding are zero
+    owned = owned.reshape(nds, nb, M)
+    for j in range(nds):
+        ncx = 2 * w - 1 if j == nds - 1 else w
+        mask = np.zeros(M, dtype=bool)
+        mask[:ncx * p] = True
+        assert np.array_equal(owned[j][:, mask], gmap[j][:, mask])
+        assert np.all(owned[j][:, ~mask] == 0.0)
     assert np.array_equal(gT, count)       # overlap multiplicity
     # transposes: <dirichlet(uG), z> = <uG, dirichlet_T(z)>, <inject(uG), z> = <uG, extract(z)>
     assert abs(dirv @ z - uG @ idT) <= 1e-11 * max(1.0, abs(dirv @ z))
