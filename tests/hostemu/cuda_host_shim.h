@@ -17,12 +17,13 @@
 #define __device__
 #define __host__
 #define __forceinline__ inline
-#define __launch_bounds__(x)
+#define __launch_bounds__(...)
 #define __restrict__
 #define __shared__ static
 #define __align__(x) __attribute__((aligned(x)))
 
 struct alignas(16) float4 { float x, y, z, w; };
+struct alignas(16) uint4 { unsigned x, y, z, w; };
 struct alignas(16) double2 { double x, y; };
 
 struct HostDim3 { unsigned x = 0, y = 0, z = 0; };
@@ -53,11 +54,24 @@ inline T __shfl_xor_sync(unsigned mask, T v, int lane_mask) {
   return r;
 }
 template <typename T>
+inline T __shfl_sync(unsigned mask, T v, int src_lane) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  g_exchange[w][l] = static_cast<double>(v);
+  __syncwarp(mask);
+  const T r = static_cast<T>(g_exchange[w][src_lane & 31]);
+  __syncwarp(mask);
+  return r;
+}
+template <typename T>
 inline T __ldcg(const T* p) { return *p; }
 // CTAs run one after another here, so device-scope atomics and fences only need to be atomic
 inline unsigned atomicAdd(unsigned* p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_add(v); }
 inline int atomicAdd(int* p, int v) { return std::atomic_ref<int>(*p).fetch_add(v); }
 inline double atomicAdd(double* p, double v) { return std::atomic_ref<double>(*p).fetch_add(v); }
+inline int atomicCAS(int* p, int cmp, int val) {
+  std::atomic_ref<int>(*p).compare_exchange_strong(cmp, val);
+  return cmp;
+}
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 // Host stand-ins for the device intrinsics of the random-number generators: the high half of a
 // 32 x 32-bit product and cos / sin of pi x through the C library.
