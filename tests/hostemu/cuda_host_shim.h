@@ -7,6 +7,8 @@
 #include <algorithm>
 #include <atomic>
 #include <barrier>
+#include <condition_variable>
+#include <mutex>
 #include <cmath>
 #include <cstdint>
 #include <functional>
@@ -92,8 +94,63 @@ inline T warp_sum(T v) {
   return v;
 }
 
+// Worker threads kept across launches (creating a few hundred threads per launch dominated
+// the run time of long launch sequences): run(n, f) calls f(t) on workers 0..n-1 and returns
+// when all of them have finished.
+struct HostThreadPool {
+  std::mutex mu;
+  std::condition_variable wake, done;
+  std::vector<std::thread> workers;
+  std::function<void(unsigned)> job;
+  uint64_t generation = 0;
+  unsigned active = 0, remaining = 0;
+  bool stop = false;
+  void worker(unsigned id) {
+    uint64_t seen = 0;
+    for (;;) {
+      std::function<void(unsigned)> f;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        wake.wait(lk, [&] { return stop || generation != seen; });
+        if (stop) return;
+        seen = generation;
+        if (id >= active) continue;
+        f = job;
+      }
+      f(id);
+      std::lock_guard<std::mutex> lk(mu);
+      if (--remaining == 0) done.notify_all();
+    }
+  }
+  void run(unsigned n, std::function<void(unsigned)> f) {
+    while (workers.size() < n) {
+      const unsigned id = (unsigned)workers.size();
+      workers.emplace_back([this, id] { worker(id); });
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      job = std::move(f);
+      active = n;
+      remaining = n;
+      ++generation;
+    }
+    wake.notify_all();
+    std::unique_lock<std::mutex> lk(mu);
+    done.wait(lk, [&] { return remaining == 0; });
+  }
+  ~HostThreadPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    wake.notify_all();
+    for (auto& t : workers) t.join();
+  }
+};
+inline HostThreadPool g_host_pool;
+
 // Runs `body` for every CTA of a (gx, gy, gz) grid of (bx, by)-thread CTAs, one CTA after
-// another: bx * by OS threads (threadIdx.x = t % bx, threadIdx.y = t / bx) walk the CTAs together,
+// another: bx * by threads (threadIdx.x = t % bx, threadIdx.y = t / bx) walk the CTAs together,
 // with a barrier at the end of each CTA (a kernel's early return only skips to it).
 inline void host_run_grid(unsigned gx, unsigned gy, unsigned bx, unsigned by,
                           const std::function<void()>& body, unsigned gz = 1) {
@@ -108,22 +165,19 @@ inline void host_run_grid(unsigned gx, unsigned gy, unsigned bx, unsigned by,
       for (auto& c : w) c.store(0);
   std::barrier<> cta(threads), end(threads);
   g_cta_barrier = &cta;
-  std::vector<std::thread> ts;
-  for (unsigned t = 0; t < threads; ++t)
-    ts.emplace_back([&body, &end, t, bx, gx, gy, gz] {
-      threadIdx.x = t % bx;
-      threadIdx.y = t / bx;
-      for (unsigned zz = 0; zz < gz; ++zz)
-        for (unsigned yy = 0; yy < gy; ++yy)
-          for (unsigned xx = 0; xx < gx; ++xx) {
-            blockIdx.x = xx;
-            blockIdx.y = yy;
-            blockIdx.z = zz;
-            body();
-            end.arrive_and_wait();
-          }
-    });
-  for (auto& t : ts) t.join();
+  g_host_pool.run(threads, [&body, &end, bx, gx, gy, gz](unsigned t) {
+    threadIdx.x = t % bx;
+    threadIdx.y = t / bx;
+    for (unsigned zz = 0; zz < gz; ++zz)
+      for (unsigned yy = 0; yy < gy; ++yy)
+        for (unsigned xx = 0; xx < gx; ++xx) {
+          blockIdx.x = xx;
+          blockIdx.y = yy;
+          blockIdx.z = zz;
+          body();
+          end.arrive_and_wait();
+        }
+  });
 }
 
 inline void host_launch2(unsigned gx, unsigned gy, unsigned threads,
