@@ -7,7 +7,9 @@ AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
   C = alpha A B (+ C) on 128-wide tiles, against the plain product;
 * the FP64 reductions of `csrc/stencil.cu` (`k_dot_partial` + `k_sum_partials`: the inner
   products of the refinement; `k_prob_sqnorm_partial` + `k_sum_partials`: per-problem squared
-  norms of a batch) and `k_axpy`, on ragged lengths, against numpy."""
+  norms of a batch) and `k_axpy`, on ragged lengths, against numpy;
+* `k_pack_split` (`csrc/gemm_tc.cu`): the TF32 hi/lo operand tiles of the tensor-core product;
+* `k_hbs_cvt` (`csrc/hbs.cu`): caller-given test matrices into the working precision."""
 import os
 import re
 import shutil
@@ -198,3 +200,107 @@ def test_reductions_and_axpy_on_the_host(workdir):
     # one rounding, or none where the compiler contracts to a fused multiply-add
     want = y + a * x
     assert (np.abs(raw[3:] - want) <= 2.3e-16 * (np.abs(want) + np.abs(a * x))).all()
+
+
+PACK_MAIN = r"""
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  const int nT = 2; const int64_t ld = nT * BT;
+  std::vector<float> src(ld * ld), dA(nT * nT * SPLIT_TILE, -1.f), dB(dA.size(), -1.f);
+  f.read((char*)src.data(), 4 * ld * ld);
+  std::vector<PackTask> tasks = {PackTask{src.data(), dA.data(), 0}, PackTask{src.data(), dB.data(), 1}};
+  std::vector<float> smem(PACK_SMEM / sizeof(float));
+  host_dynamic_smem = smem.data();
+  host_launch2(nT * nT, 2, 256, [&] { k_pack_split(tasks.data(), nT); });
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)dA.data(), 4 * dA.size()); o.write((const char*)dB.data(), 4 * dB.size());
+  return 0;
+}
+"""
+
+
+def test_split_packing_on_the_host(workdir):
+    """`k_pack_split` (`csrc/gemm_tc.cu`): 128 x 128 tiles of an A operand (tile (I, kt) holds
+    src(128 I + r, 128 kt + k)) and of a B operand packed as B^T (tile (J, kt) holds
+    src(128 kt + k, 128 J + r)), as TF32 hi/lo parts in 16-wide K chunks of the K-major
+    core-matrix layout; hi + lo equals the FP32 value to 2^-21."""
+    src = open(os.path.join(CSRC, "gemm_tc.cu")).read()
+    kern = open(os.path.join(CSRC, "kernels.cuh")).read()
+    umma = open(os.path.join(CSRC, "umma.cuh")).read()
+    split = open(os.path.join(CSRC, "splittile.cuh")).read()
+    task = re.search(r"struct PackTask \{.*?\n\};", kern, re.S).group(0)
+    off = re.search(r"__host__ __device__ __forceinline__ uint32_t umma_off\(.*?\n\}", umma, re.S).group(0)
+    sp_ = split[split.index("constexpr int BT = 128;"):split.index("}  // namespace ddst")]
+    body = src[src.index("constexpr int PK_LS = BT + 1;"):src.index("// -----", src.index("k_pack_split("))]
+    body = body.replace("extern __shared__ float S[];", "float* S = host_dynamic_smem;")
+    rna = ("inline float tf32_rna(float x) {  // 10-bit significand, nearest, ties away\n"
+           "  uint32_t u; std::memcpy(&u, &x, 4); u = (u + 0x1000u) & ~0x1fffu;\n"
+           "  float r; std::memcpy(&r, &u, 4); return r;\n}\n")
+    code = ('#include "cuda_host_shim.h"\n#include <cstring>\nstatic float* host_dynamic_smem = nullptr;\n'
+            "namespace ddst {\n" + task + "\n" + rna + off + "\n" + sp_ + "\n" + body +
+            "\n}  // namespace ddst\n" + PACK_MAIN)
+    exe = _build(workdir, "pack_host", code)
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((256, 256)).astype(np.float32)
+    path = workdir / "pack.bin"
+    path.write_bytes(A.tobytes())
+    out = workdir / "pack.out"
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = np.fromfile(out, dtype=np.float32)
+    st = 2 * 128 * 128
+    dA, dB = raw[:4 * st], raw[4 * st:]
+    rr, kk = np.meshgrid(np.arange(128), np.arange(128), indexing="ij")
+    c = kk % 16
+    idx = (kk // 16) * 2048 + (rr >> 3) * 128 + (c >> 2) * 32 + (rr & 7) * 4 + (c & 3)
+    A64 = A.astype(np.float64)
+    for I_ in range(2):
+        for kt in range(2):
+            for dst, want in ((dA, A64[128 * I_:128 * I_ + 128, 128 * kt:128 * kt + 128]),
+                              (dB, A64[128 * kt:128 * kt + 128, 128 * I_:128 * I_ + 128].T)):
+                tile = dst[(I_ * 2 + kt) * st:(I_ * 2 + kt + 1) * st]
+                hi, lo = tile[:128 * 128][idx], tile[128 * 128:][idx]
+                assert np.all(hi.view(np.uint32) & 0x1FFF == 0) and np.all(lo.view(np.uint32) & 0x1FFF == 0)
+                got = hi.astype(np.float64) + lo.astype(np.float64)
+                assert np.all(np.abs(got - want) <= 2.0 ** -21 * np.abs(want))
+
+
+CVT_MAIN = r"""
+#include <fstream>
+using namespace ddst;
+int main(int argc, char** argv) {
+  std::ifstream f(argv[1], std::ios::binary);
+  const int64_t n = 1000;
+  std::vector<double> x(n); f.read((char*)x.data(), 8 * n);
+  std::vector<float> y(n + 3, -7.f);
+  std::vector<double> z(n + 3, -7.0);
+  host_launch(3, 64, [&] { k_hbs_cvt<float>(x.data(), y.data(), n); });
+  host_launch(2, 96, [&] { k_hbs_cvt<double>(x.data(), z.data(), n); });
+  std::ofstream o(argv[2], std::ios::binary);
+  o.write((const char*)y.data(), 4 * y.size()); o.write((const char*)z.data(), 8 * z.size());
+  return 0;
+}
+"""
+
+
+def test_sample_conversion_on_the_host(workdir):
+    """`k_hbs_cvt` (`csrc/hbs.cu`): caller-given FP64 test matrices into the working precision,
+    every element once (grid-stride), round to nearest, nothing written past the end."""
+    src = open(os.path.join(CSRC, "hbs.cu")).read()
+    i = src.index("template <typename T>\n__global__ void k_hbs_cvt(")
+    body = src[i:src.index("\n}\n", i) + 3]
+    exe = _build(workdir, "cvt_host", '#include "cuda_host_shim.h"\nnamespace ddst {\n' + body +
+                 "\n}  // namespace ddst\n" + CVT_MAIN)
+    x = np.random.default_rng(4).standard_normal(1000) * 10.0 ** np.linspace(-30, 30, 1000)
+    path = workdir / "cvt.bin"
+    path.write_bytes(x.tobytes())
+    out = workdir / "cvt.out"
+    r = subprocess.run([str(exe), str(path), str(out)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    raw = out.read_bytes()
+    y = np.frombuffer(raw[:4 * 1003], dtype=np.float32)
+    z = np.frombuffer(raw[4 * 1003:], dtype=np.float64)
+    assert np.array_equal(y[:1000], x.astype(np.float32)) and np.all(y[1000:] == -7.0)
+    assert np.array_equal(z[:1000], x) and np.all(z[1000:] == -7.0)
