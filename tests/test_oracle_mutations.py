@@ -13,6 +13,7 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -72,20 +73,35 @@ MUTATIONS = [
 ]
 
 
-@pytest.mark.slow
-@pytest.mark.timeout(600)
-@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_oracle_mistake_fails_a_pin(tmp_path, name, old, new):
+def _run_planted(d, old, new):
+    """Runs the pins against a copy of the oracle with `old` replaced by `new`, in folder d."""
     src = open(ORACLE).read()
-    assert src.count(old) == 1, f"mutation site not found: {name}"
-    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests")
-    shutil.copytree(os.path.join(ROOT, "ddst_inputs"), tmp_path / "ddst_inputs",
+    shutil.copytree(os.path.join(ROOT, "tests"), d / "tests",
                     ignore=shutil.ignore_patterns("__pycache__"))
-    (tmp_path / "oracle").mkdir()
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), tmp_path / "oracle" / "__init__.py")
-    (tmp_path / "oracle" / "ddst_oracle.py").write_text(src.replace(old, new))
-    env = dict(os.environ, OMP_NUM_THREADS="4", OPENBLAS_NUM_THREADS="4", MKL_NUM_THREADS="4")
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
-                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True,
-                       timeout=600, env=env)
+    shutil.copytree(os.path.join(ROOT, "ddst_inputs"), d / "ddst_inputs",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    (d / "oracle").mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), d / "oracle" / "__init__.py")
+    (d / "oracle" / "ddst_oracle.py").write_text(src.replace(old, new))
+    env = dict(os.environ, OMP_NUM_THREADS="2", OPENBLAS_NUM_THREADS="2", MKL_NUM_THREADS="2")
+    return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+                           "-p", "no:cacheprovider"], cwd=d, capture_output=True, text=True,
+                          timeout=600, env=env)
+
+
+@pytest.fixture(scope="module")
+def planted_runs(tmp_path_factory):
+    """All planted variants, four pin runs at a time (each is its own Python process)."""
+    dirs = [tmp_path_factory.mktemp("planted") for _ in MUTATIONS]
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        runs = list(ex.map(lambda a: _run_planted(a[0], a[1][1], a[1][2]), zip(dirs, MUTATIONS)))
+    return {m[0]: r for m, r in zip(MUTATIONS, runs)}
+
+
+@pytest.mark.slow
+@pytest.mark.timeout(1200)
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_oracle_mistake_fails_a_pin(planted_runs, name, old, new):
+    assert open(ORACLE).read().count(old) == 1, f"mutation site not found: {name}"
+    r = planted_runs[name]
     assert r.returncode == 1, f"{name}: no pin failed\n{r.stdout[-2000:]}"
