@@ -64,6 +64,16 @@ inline T __shfl_sync(unsigned mask, T v, int src_lane) {
   __syncwarp(mask);
   return r;
 }
+inline int __all_sync(unsigned mask, int pred) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  g_exchange[w][l] = pred ? 1.0 : 0.0;
+  __syncwarp(mask);
+  int all = 1;
+  for (int m = 0; m < 32; ++m)
+    if ((mask & (1u << m)) && g_exchange[w][m] == 0.0) all = 0;
+  __syncwarp(mask);
+  return all;
+}
 template <typename T>
 inline T __ldcg(const T* p) { return *p; }
 // CTAs run one after another here, so device-scope atomics and fences only need to be atomic

@@ -1,6 +1,7 @@
 // Host model of the shared-memory mbarrier and the bulk (TMA, untiled) global -> shared copy,
 // as the library's kernels use them: one arrival per phase (mbarrier.init with count 1), made
-// by the thread that issues the phase's copies with the expected byte count.  The 64-bit
+// by the thread that issues the phase's copies with the expected byte count, or by a plain
+// arrival (a tensor-core commit).  The 64-bit
 // barrier word holds the number of completed phases (bits 0..31), the transaction bytes still
 // outstanding (bits 32..62) and whether the phase's arrival has happened (bit 63).  A copy is a
 // memcpy that then counts its bytes off; the phase completes when none are outstanding.  The
@@ -42,6 +43,16 @@ inline void host_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* 
   }
   v = pend == bytes ? (v & 0xffffffffull) + 1 : (v & ~(0x7fffffffull << 32)) | ((pend - bytes) << 32);
   a.store(v, std::memory_order_release);
+}
+
+// A plain arrival (mbarrier.arrive, or a tensor-core commit): completes the phase unless copies
+// announced by an expect-tx are still outstanding.
+inline void host_mbar_arrive(uint64_t* bar) {
+  std::atomic_ref<uint64_t> a(*bar);
+  const uint64_t v = a.load();
+  if (v >> 63) { std::fprintf(stderr, "mbarrier model: second arrival in one phase\n"); std::abort(); }
+  const uint64_t pend = (v >> 32) & 0x7fffffffull;
+  a.store(pend == 0 ? (v & 0xffffffffull) + 1 : v | (1ull << 63), std::memory_order_release);
 }
 
 // True once the phase of the given parity has completed.
