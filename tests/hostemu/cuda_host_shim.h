@@ -74,6 +74,16 @@ inline int __all_sync(unsigned mask, int pred) {
   __syncwarp(mask);
   return all;
 }
+inline int __any_sync(unsigned mask, int pred) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  g_exchange[w][l] = pred ? 1.0 : 0.0;
+  __syncwarp(mask);
+  int any = 0;
+  for (int m = 0; m < 32; ++m)
+    if ((mask & (1u << m)) && g_exchange[w][m] != 0.0) any = 1;
+  __syncwarp(mask);
+  return any;
+}
 template <typename T>
 inline T __ldcg(const T* p) { return *p; }
 // CTAs run one after another here, so device-scope atomics and fences only need to be atomic

@@ -18,7 +18,10 @@ definitions:
   check, and too short a warm-up makes the check report a large difference;
 * the FP32 factorization's tensor-core operand copies hold the TF32 hi/lo split of
   -diag(ell_{k+1}) F_k (forward) and -diag(ups_{k-1}) B_k (backward), transposed, in the K-major
-  operand layout.
+  operand layout;
+* the tensor-core transfer build (`csrc/sweep_tc.cu`, on the tcgen05 model of
+  `tests/hostemu/tcgen05_host.h`) from those copies gives O3's operators, every entry written,
+  in 3xTF32 and in TF32.
 In FP64 and FP32, for block sizes 32 and 64, in 2D with convection and in 3D.
 """
 import os
@@ -33,12 +36,13 @@ import scipy.sparse as sp
 
 import ddst_inputs as I
 from oracle import ddst_oracle as O
+from test_tc_kernels_host import _host_tmem_calls
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
 
-# Host stand-ins for the inline-PTX helpers: the mbarrier / bulk-copy model and TF32 rounding
-# (cvt.rna.tf32.f32: round the FP32 significand to 10 bits, nearest, ties away from zero).
+# Host stand-ins for the inline-PTX helpers on the mbarrier / bulk-copy model (TF32 rounding and
+# the tensor-core instructions come from the tcgen05 model).
 HOST_HELPERS = r'''
 inline void mbar_init(uint64_t* bar, uint32_t count) { host_mbar_init(bar, count); }
 inline void fence_mbar_init() {}
@@ -50,13 +54,17 @@ inline bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, int slab, i
   set_status(st, ST_TIMEOUT, slab, block);
   return false;
 }
-inline float tf32_rna(float x) {
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  u = (u + 0x1000u) & ~0x1fffu;
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
+inline bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort, DevStatus* st,
+                         int slab, int block, long long budget = 0) {
+  (void)budget;
+  for (long it = 0; it < 20000000L; ++it) {
+    if (host_mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    std::this_thread::yield();
+  }
+  set_status(st, ST_TIMEOUT, slab, block);
+  *abort = 1;
+  return false;
 }
 '''
 
@@ -195,6 +203,33 @@ int run(std::ifstream& f, std::ofstream& o, const int64_t* h, const double* dd) 
     });
   }
   put(o, S);
+  if constexpr (sizeof(T) == 4) {
+    // the same operators on the tensor cores, from the factor kernel's TF32 operand copies
+    using Ct = TcCfg<M>;
+    const int Rt = Ct::NT * Ct::TILE;
+    std::vector<TileDesc> tt;
+    for (int sid = 0; sid < nds; ++sid)
+      for (int64_t q0 = 0; q0 < ng; q0 += Rt) {
+        const int nq = (int)std::min<int64_t>(Rt, ng - q0);
+        TileDesc up{sid, (int)q0, nq, 0, (int)((q0 + nq - 1) / p) + 1, 0};
+        up.len = up.kstart;
+        TileDesc dn{sid, (int)q0, nq, 1, (int)(q0 / p) + 1, 0};
+        dn.len = nb - dn.kstart + 1;
+        tt.push_back(up);
+        tt.push_back(dn);
+      }
+    unsigned char* sm = static_cast<unsigned char*>(std::aligned_alloc(1024, (Ct::SMEM + 1023) / 1024 * 1024));
+    host_smem_base = sm;
+    for (int three = 1; three >= 0; --three) {
+      std::vector<float> Stc(s_off, std::numeric_limits<float>::quiet_NaN());
+      host_launch((unsigned)tt.size(), Ct::THREADS, [&] {
+        k_sbuild_tc<M>(slabs.data(), tt.data(), Uhi.data(), Ulo.data(), Uhi.data() + nfac,
+                       Ulo.data() + nfac, G.data(), pack.data(), Stc.data(), &stt, 4000000000LL, three);
+      });
+      put(o, Stc);
+    }
+    std::free(sm);
+  }
   const double code = stt.code;
   o.write((const char*)&code, 8);
   return 0;
@@ -241,6 +276,9 @@ def harness(tmp_path_factory):
         grab(r"__host__ __device__ __forceinline__ uint32_t umma_off\(.*?\n\}", umma),
         _between(umma, "template <int M>\n__device__ __forceinline__ void store_umma_split_T(",
                  "// -----"),
+        grab(r"__device__ __forceinline__ uint64_t umma_desc\(.*?\n\}", umma),
+        grab(r"__host__ __device__ constexpr uint32_t idesc_tf32\(.*?\n\}", umma),
+        grab(r"__device__ __forceinline__ void tf32_split\(.*?\n\}", umma),
         _between(bgj, "template <typename T, int M>\nstruct BGJ {", "}  // namespace ddst"),
         _between(st, "__device__ __forceinline__ int64_t node_index(",
                  "// b = f + (Dirichlet neighbour terms)"),
@@ -251,11 +289,16 @@ def harness(tmp_path_factory):
         _between(swp, "template <typename T, int N>\n__device__ __forceinline__ void lds(",
                  "template <typename T, int M, int R, int NST>\nstatic void run_sbuild("),
     ]
+    tc = _between(rd("sweep_tc.cu"), "template <int MB>\nstruct TcCfg {",
+                  "template <int MB>\nstatic void run_tc(")
+    tc = tc.replace("extern __shared__ __align__(1024) unsigned char smem_raw[];",
+                    "unsigned char* smem_raw = host_smem_base;")
+    parts.append(_host_tmem_calls(tc))
     body = "\n".join(parts)
     dyn = "extern __shared__ __align__(128) unsigned char smem_raw[];"
     assert body.count(dyn) == 4
     body = body.replace(dyn, "unsigned char* smem_raw = host_dynamic_smem;")
-    code = ('#include "cuda_host_shim.h"\n#include "mbarrier_host.h"\n#include <cstring>\n'
+    code = ('#include "cuda_host_shim.h"\n#include "mbarrier_host.h"\n#include "tcgen05_host.h"\n#include <cstring>\n'
             "static unsigned char* host_dynamic_smem = nullptr;\nnamespace ddst {\n" + body +
             "\n}  // namespace ddst\n" + MAIN)
     d = tmp_path_factory.mktemp("factor_host")
@@ -335,6 +378,8 @@ def _run(harness, name, n, w, esz, chunks, full, over=None, tag=""):
     if full:
         sizes += [("G", nfac), ("x", nloc), ("xT", nloc), ("iface", nds * ng),
                   ("S", 2 * (nds - 1) * ng * ng)]
+        if esz == 4:
+            sizes += [("S_tc3", 2 * (nds - 1) * ng * ng), ("S_tc1", 2 * (nds - 1) * ng * ng)]
     for key, cnt in sizes:
         res[key] = raw[pos:pos + cnt]
         pos += cnt
@@ -453,9 +498,17 @@ def test_factor_solve_and_transfer_build_on_the_host(harness, name, n, w, esz, o
             if Sref is None:
                 continue
             blk = S[s_off:s_off + ng * ng].reshape(ng, ng).T
-            s_off += ng * ng
             assert np.abs(blk - Sref).max() <= tol * np.abs(Sref).max()
+            if esz == 4:
+                # the tensor-core build from the TF32 operand copies: 3xTF32 to FP32 accuracy;
+                # one TF32 product per step rounds an operand to 11 bits once per block row
+                for key, tl in (("S_tc3", tol), ("S_tc1", nb * 2.0 ** -11)):
+                    bt = res[key][s_off:s_off + ng * ng].reshape(ng, ng).T
+                    assert np.abs(bt - Sref).max() <= tl * np.abs(Sref).max(), key
+            s_off += ng * ng
     assert s_off == S.size
+    if esz == 4:
+        assert not np.isnan(res["S_tc3"]).any() and not np.isnan(res["S_tc1"]).any()
 
 
 @pytest.mark.parametrize("W", [20, 4])

@@ -38,7 +38,7 @@ inline bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st, int slab, i
 inline bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort, DevStatus* st,
                          int slab, int block, long long budget = 0) {
   (void)budget;
-  for (long it = 0; it < 200000000L; ++it) {
+  for (long it = 0; it < 20000000L; ++it) {
     if (host_mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
     std::this_thread::yield();
@@ -58,11 +58,11 @@ def _between(src, start, end):
 def _host_tmem_calls(body):
     """The in-kernel tcgen05.alloc / relinquish / dealloc statements as calls of the model."""
     body, n1 = re.subn(r'asm volatile\("tcgen05\.alloc\.[^"]*"\s*::"r"\(\s*smem_u32\(&(\w+)\)\),\s*'
-                       r'"r"\(([^)]*)\)\s*:\s*"memory"\);', r"host_tmem_alloc(&\1, \2);", body)
+                       r'"r"\((.*?)\)\s*:\s*"memory"\);', r"host_tmem_alloc(&\1, \2);", body, flags=re.S)
     body, n2 = re.subn(r'asm volatile\("tcgen05\.relinquish_alloc_permit[^"]*"\s*:::\s*"memory"\);',
                        "host_tmem_relinquish();", body)
-    body, n3 = re.subn(r'asm volatile\("tcgen05\.dealloc\.[^"]*"\s*::"r"\((\w+)\),\s*"r"\(([^)]*)\)'
-                       r'\s*:\s*"memory"\);', r"host_tmem_dealloc(\1, \2);", body)
+    body, n3 = re.subn(r'asm volatile\("tcgen05\.dealloc\.[^"]*"\s*::"r"\((\w+)\),\s*"r"\((.*?)\)'
+                       r'\s*:\s*"memory"\);', r"host_tmem_dealloc(\1, \2);", body, flags=re.S)
     assert n1 == n2 == n3 >= 1 and "asm" not in body
     return body
 
