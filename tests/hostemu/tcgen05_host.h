@@ -1,7 +1,6 @@
 // Host model of the tcgen05 tensor-core instructions that the library's kernels use, written
 // from the public PTX ISA description, for CPU tests of those kernels' index arithmetic, operand
-// layouts and synchronisation (include after cuda_host_shim.h and mbarrier_host.h, inside the
-// library's namespace, where DevStatus, set_status and ST_TIMEOUT are defined):
+// layouts and synchronisation (include after cuda_host_shim.h and mbarrier_host.h):
 // * tensor memory: 128 lanes x 512 columns of 32-bit words for the CTA that runs; an address is
 //   lane << 16 | column; alloc returns column 0 and accesses outside the allocation abort;
 // * shared-memory matrix descriptors: start address >> 4 in bits 0..13, leading byte offset
@@ -84,11 +83,17 @@ template <typename GetA>
 inline void host_mma(uint32_t tmem_d, GetA a, uint64_t b, uint32_t idesc, uint32_t accum) {
   const int N = (int)((idesc >> 17) & 0x3fu) << 3, M = (int)((idesc >> 24) & 0x1fu) << 4;
   if (M != 128 || N < 8 || N > 256) host_tc_fail("shape");
+  float As[128][8], Bs[256][8];
+  for (int m = 0; m < M; ++m)
+    for (int k = 0; k < 8; ++k) As[m][k] = host_tf32(a(m, k));
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < 8; ++k) Bs[n][k] = host_tf32(host_desc_elem(b, n, k));
   for (int m = 0; m < M; ++m)
     for (int n = 0; n < N; ++n) {
-      float acc = accum ? __uint_as_float(host_tmem_at(tmem_d, m, n)) : 0.f;
-      for (int k = 0; k < 8; ++k) acc += host_tf32(a(m, k)) * host_tf32(host_desc_elem(b, n, k));
-      host_tmem_at(tmem_d, m, n) = __float_as_uint(acc);
+      uint32_t& d = host_tmem_at(tmem_d, m, n);
+      float acc = accum ? __uint_as_float(d) : 0.f;
+      for (int k = 0; k < 8; ++k) acc += As[m][k] * Bs[n][k];
+      d = __float_as_uint(acc);
     }
 }
 

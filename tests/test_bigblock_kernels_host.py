@@ -1,5 +1,5 @@
 """The large-block factorization and local solves of `csrc/bigblock.cu` (double slabs with
-m > 128 unknowns per block row), FMA path, compiled for the host and run with one OS thread per
+m > 128 unknowns per block row), compiled for the host and run with one OS thread per
 CUDA thread under AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
 * `k_big_sigma`, `k_big_pivot`, `k_big_gemm_fma` (row and update steps of the 128-wide panel
   Gauss-Jordan inversion, with the look-ahead split of the update): F_k = Sigma_k^{-1} of the
@@ -12,7 +12,9 @@ CUDA thread under AddressSanitizer (`tests/hostemu/cuda_host_shim.h`):
 * `k_big_gemv_n`, `k_big_gemv_t`, `k_big_extract`: A_j^{-1} b, A_j^{-T} b and the central rows,
   against a sparse direct solve;
 * the tensor-core operand copies of the first pivot step (`k_big_pivot` with split tiles, FP32):
-  TF32 hi/lo parts of X(B, Q), X(Q, B)^T, P, P^{-1} and P^{-T} in the chunked K-major layout.
+  TF32 hi/lo parts of X(B, Q), X(Q, B)^T, P, P^{-1} and P^{-T} in the chunked K-major layout;
+* the FP32 factorization with the panel products on the tensor cores (`k_big_gemm_tc` on the
+  tcgen05 model of `tests/hostemu/tcgen05_host.h`), 3xTF32 and TF32.
 In FP64 and FP32.
 """
 import os
@@ -28,20 +30,10 @@ import scipy.sparse.linalg as spla
 
 import ddst_inputs as I
 from oracle import ddst_oracle as O
+from test_tc_kernels_host import MBAR_HELPERS, _host_tmem_calls
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
-
-HOST_HELPERS = r'''
-inline float tf32_rna(float x) {  // cvt.rna.tf32.f32: 10-bit significand, nearest, ties away
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  u = (u + 0x1000u) & ~0x1fffu;
-  float r;
-  std::memcpy(&r, &u, 4);
-  return r;
-}
-'''
 
 MAIN = r'''
 #include <fstream>
@@ -109,7 +101,7 @@ int run(std::ifstream& f, std::ofstream& o, const int64_t* h, const double* dd) 
   const size_t gj = BGJ<T, BT>::smem_elems * sizeof(T) + BT * sizeof(T) + 16;
   const size_t stage = (size_t)BT * (BT + 1) * sizeof(T);
   std::vector<unsigned char> pdyn(gj > stage ? gj : stage);
-  auto pivot = [&](int k, int q) {
+  std::function<void(int, int)> pivot = [&](int k, int q) {
     const int e = q & 1;
     host_dynamic_smem = pdyn.data();
     host_launch2(nP, nids, 512, [&] {
@@ -117,16 +109,62 @@ int run(std::ifstream& f, std::ofstream& o, const int64_t* h, const double* dd) 
                             RT[e].data(), Pinv[e].data(), &stt);
     });
   };
-  auto row = [&](int k, int q) {
+  std::function<void(int, int)> row = [&](int k, int q) {
     const int e = q & 1;
     gemm<T, GJ_ROW>(nP, nids, sl, id, F.data(), k, q, Cb[e].data(), XqT[e].data(), RT[e].data(), Pinv[e].data(), GJ_ALL);
   };
-  auto update = [&](int k, int q, int tset) {
+  std::function<void(int, int, int)> update = [&](int k, int q, int tset) {
     const int e = q & 1;
     const int cnt = gj_count(tset, nP);
     if (cnt == 0) return;
     gemm<T, GJ_UPDATE>(cnt, nids, sl, id, F.data(), k, q, Cb[e].data(), XqT[e].data(), RT[e].data(), Pinv[e].data(), tset);
   };
+  // tensor-core path (FP32): split-tile work buffers; from the second panel on, the pivot copies
+  // come from the previous panel's update and row steps
+  const int tc = (int)h[9], three = tc == 1 ? 1 : 0;
+  std::vector<float> Cs2[2], Xs2[2], Rs2[2], Ps2[2];
+  unsigned char* tsm = nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {
+      for (int e = 0; e < 2; ++e) {
+        Cs2[e].assign((int64_t)nids * nP * SPLIT_TILE, 0.f); Xs2[e] = Cs2[e]; Rs2[e] = Cs2[e];
+        Ps2[e].assign((int64_t)nids * SPLIT_TILE, 0.f);
+      }
+      tsm = static_cast<unsigned char*>(std::aligned_alloc(1024, (GjTc::SMEM + 1023) / 1024 * 1024));
+      const size_t stage2 = 2 * (size_t)BT * (BT + 1) * 4;
+      if (pdyn.size() < stage2) pdyn.resize(stage2);
+      pivot = [&](int k, int q) {
+        const int e = q & 1;
+        host_dynamic_smem = pdyn.data();
+        host_launch2(q == 0 ? nP : 1, nids, 512, [&] {
+          k_big_pivot<float, true>(sl, id, pack.data(), F.data(), k, q, Cs2[e].data(), Xs2[e].data(),
+                                   Rs2[e].data(), Ps2[e].data(), &stt);
+        });
+      };
+      row = [&](int k, int q) {
+        const int e = q & 1;
+        const bool nx = q + 1 < nP;
+        host_smem_base = tsm;
+        host_launch3(nP, 1, nids, GjTc::THREADS, [&] {
+          k_big_gemm_tc<GJ_ROW>(sl, id, F.data(), k, q, Cs2[e].data(), Xs2[e].data(), Rs2[e].data(),
+                                Ps2[e].data(), &stt, GJ_ALL, nx ? Cs2[e ^ 1].data() : nullptr,
+                                nx ? Xs2[e ^ 1].data() : nullptr, three);
+        });
+      };
+      update = [&](int k, int q, int tset) {
+        const int e = q & 1;
+        const int cnt = gj_count(tset, nP);
+        if (cnt == 0) return;
+        const bool nx = tset == GJ_NEXT;
+        host_smem_base = tsm;
+        host_launch3(cnt, 1, nids, GjTc::THREADS, [&] {
+          k_big_gemm_tc<GJ_UPDATE>(sl, id, F.data(), k, q, Cs2[e].data(), Xs2[e].data(), Rs2[e].data(),
+                                   Ps2[e].data(), &stt, tset, nx ? Cs2[e ^ 1].data() : nullptr,
+                                   nx ? Xs2[e ^ 1].data() : nullptr, three);
+        });
+      };
+    }
+  }
   for (int k = 1; k <= nb; ++k) {
     host_launch2(4, nids, 256, [&] { k_big_sigma<T>(sl, id, pack.data(), F.data(), k); });
     pivot(k, 0);
@@ -144,6 +182,7 @@ int run(std::ifstream& f, std::ofstream& o, const int64_t* h, const double* dd) 
     }
   }
   put(o, F);
+  if (tsm) std::free(tsm);
 
   // local solves of the listed slabs
   std::vector<T> z(nloc, T(0)), x(nloc, T(0)), xT(nloc, T(0));
@@ -198,24 +237,30 @@ def harness(tmp_path_factory):
         grab(r"__device__ __forceinline__ void set_status\(.*?\n\}", common),
         _between(common, "template <typename T> struct Eps;", "// -----"),
         grab(r"__device__ __forceinline__ int64_t vol_index\(.*?\n\}", common),
-        HOST_HELPERS,
+        MBAR_HELPERS,
         grab(r"__host__ __device__ __forceinline__ uint32_t umma_off\(.*?\n\}", umma),
+        grab(r"__device__ __forceinline__ uint64_t umma_desc\(.*?\n\}", umma),
+        grab(r"__host__ __device__ constexpr uint32_t idesc_tf32\(.*?\n\}", umma),
         _between(split, "constexpr int BT = 128;", "}  // namespace ddst"),
         _between(bgj, "template <typename T, int M>\nstruct BGJ {", "}  // namespace ddst"),
         _between(st, "__device__ __forceinline__ int64_t node_index(",
                  "// b = f + (Dirichlet neighbour terms)"),
         _between(big, "template <typename T>\n__global__ void __launch_bounds__(256) k_big_sigma(",
                  "struct GjTc {"),
+        _between(big, "struct GjTc {", "// Local solves through the stored inverses"),
         _between(big, "enum { SV_NFWD = 0", "// Host launchers"),
         _between(big, "// Central rows of slab-local vectors",
                  "template <typename T>\nvoid launch_big_extract("),
     ]
     body = "\n".join(parts)
+    body = _host_tmem_calls(body.replace("extern __shared__ __align__(1024) unsigned char smem_raw[];",
+                                         "unsigned char* smem_raw = host_smem_base;"))
     for dyn in ("extern __shared__ __align__(128) unsigned char smem_raw[];",
                 "extern __shared__ __align__(16) unsigned char smem_raw[];"):
         assert dyn in body
         body = body.replace(dyn, "unsigned char* smem_raw = host_dynamic_smem;")
-    code = ('#include "cuda_host_shim.h"\n#include <cstring>\n#include <type_traits>\n'
+    code = ('#include "cuda_host_shim.h"\n#include "mbarrier_host.h"\n#include "tcgen05_host.h"\n'
+            '#include <cstring>\n#include <type_traits>\n'
             "static unsigned char* host_dynamic_smem = nullptr;\nnamespace ddst {\n" + body +
             "\n}  // namespace ddst\n" + MAIN)
     d = tmp_path_factory.mktemp("bigblock_host")
@@ -235,7 +280,7 @@ CFG64 = (21, 7, (0, 1))
 CFG32 = (20, 5, (0, 2))
 
 
-def _run(harness, esz, sched, cfg):
+def _run(harness, esz, sched, cfg, tc=0):
     d, exe = harness
     N, W, IDS = cfg
     prob = I.make_problem("vardiff3d", n=N, w=W, b=(1.0, -0.5, 0.75))
@@ -247,10 +292,10 @@ def _run(harness, esz, sched, cfg):
     rng = np.random.default_rng(17)
     b = np.zeros((nds, nb, M))
     b[:, :, :m] = rng.standard_normal((nds, nb, m))
-    path = d / f"big_{esz}_{sched}.bin"
+    path = d / f"big_{esz}_{sched}_{tc}.bin"
     with open(path, "wb") as f:
         has_c = prob.get("c") is not None
-        f.write(struct.pack("10q", 3, N, W, M, int(has_c), nnode, esz, len(IDS), sched, 0))
+        f.write(struct.pack("10q", 3, N, W, M, int(has_c), nnode, esz, len(IDS), sched, tc))
         f.write(struct.pack("4d", 1.0 / N, *prob["b"]))
         f.write(np.asarray(prob["a"], dtype=np.float64).ravel().tobytes())
         f.write((np.asarray(prob["c"], dtype=np.float64).ravel() if has_c else np.zeros(nnode)).tobytes())
@@ -385,3 +430,35 @@ def _check_split_pivot(res, ctx):
                 assert close(Xt, X[:128, 128 * bb:128 * (bb + 1)].T)
         assert close(_decode(res["Ps"][y * st:(y + 1) * st]), Pinv)
         assert close(_decode(res["Rs"][y * nP * st:(y * nP + 1) * st]), Pinv.T)
+
+
+@pytest.mark.parametrize("tc", [1, 2])
+def test_large_block_tensor_core_factor_on_the_host(harness, tc):
+    """The FP32 factorization with the row and update products on the tensor cores
+    (`k_big_gemm_tc` on the tcgen05 model of `tests/hostemu/tcgen05_host.h`; 1: 3xTF32, 2: one
+    TF32 product), its split-tile pivot copies and the next panel's operand tiles written by the
+    update and row steps: F_k against the one-sided block LU, the padding exactly the identity,
+    and (3xTF32) the solves against a sparse direct solve."""
+    res, ctx = _run(harness, 4, 0, CFG32, tc)
+    assert res["code"] == 0.0
+    m, M, nb, nP = ctx["m"], ctx["M"], ctx["nb"], ctx["nP"]
+    # 3xTF32: FP32 accuracy; TF32: one 11-bit operand rounding per panel product
+    tol = 256 * 2.0 ** -24 if tc == 1 else 4 * nP * 2.0 ** -11
+    pad = np.diag(np.r_[np.zeros(m), np.ones(M - m)])
+    for j in ctx["ids"]:
+        Aj = _local(ctx, j)
+        Fr = _one_sided_lu(Aj, nb, m)
+        for k in range(nb):
+            got = res["F"][j, k]
+            assert np.abs(got[:m, :m] - Fr[k]).max() <= tol * np.abs(Fr[k]).max()
+            rest = got.copy()
+            rest[:m, :m] = 0.0
+            assert np.array_equal(rest, pad)
+        if tc == 1:
+            bj = ctx["b"][j, :, :m].ravel()
+            lu = spla.splu(sp.csc_matrix(Aj))
+            inv = spla.LinearOperator(Aj.shape, matvec=lu.solve,
+                                      rmatvec=lambda v: lu.solve(v, trans="T"), dtype=np.float64)
+            cond = spla.onenormest(sp.csc_matrix(Aj)) * spla.onenormest(inv)
+            want = lu.solve(bj)
+            assert np.abs(res["x"][j][:, :m].ravel() - want).max() <= 8 * cond * 2.0 ** -24 * np.abs(want).max()
