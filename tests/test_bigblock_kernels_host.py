@@ -462,3 +462,18 @@ def test_large_block_tensor_core_factor_on_the_host(harness, tc):
             cond = spla.onenormest(sp.csc_matrix(Aj)) * spla.onenormest(inv)
             want = lu.solve(bj)
             assert np.abs(res["x"][j][:, :m].ravel() - want).max() <= 8 * cond * 2.0 ** -24 * np.abs(want).max()
+
+
+def test_tensor_core_lookahead_orders_give_the_same_factors(harness):
+    """Three panels (M = 384) on the tensor-core model, 3xTF32: the next panel's operand tiles
+    are written by the update of its row and column blocks and by the row step, into the other
+    parity's buffers, while the rest of the current panel's update still reads this parity's.
+    Both legal orders give the same factors bit for bit, and they are the block LU's."""
+    cfg = (CFG64[0], CFG64[1], (1,))
+    (r0, ctx), (r1, _) = (_run(harness, 4, sched, cfg, 1) for sched in (0, 1))
+    assert r0["code"] == 0.0 and r1["code"] == 0.0 and ctx["nP"] == 3
+    assert np.array_equal(r0["F"], r1["F"])
+    m, nb = ctx["m"], ctx["nb"]
+    Fr = _one_sided_lu(_local(ctx, 1), nb, m)
+    for k in range(nb):
+        assert np.abs(r0["F"][1, k, :m, :m] - Fr[k]).max() <= 256 * 2.0 ** -24 * np.abs(Fr[k]).max()
