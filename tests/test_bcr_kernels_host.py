@@ -17,6 +17,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 
 MAIN = r'''
 #include <fstream>
@@ -83,7 +86,7 @@ def harness(tmp_path_factory):
             bmv + "\n" + body + "\n}  // namespace ddst\n" + MAIN)
     (d / "bcr_host.cpp").write_text(code)
     exe = d / "bcr_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "bcr_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]

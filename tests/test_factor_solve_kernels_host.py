@@ -40,6 +40,9 @@ from test_tc_kernels_host import _host_tmem_calls
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 
 # Host stand-ins for the inline-PTX helpers on the mbarrier / bulk-copy model (TF32 rounding and
 # the tensor-core instructions come from the tcgen05 model).
@@ -304,7 +307,7 @@ def harness(tmp_path_factory):
     d = tmp_path_factory.mktemp("factor_host")
     (d / "factor_host.cpp").write_text(code)
     exe = d / "factor_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "factor_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-4000:]

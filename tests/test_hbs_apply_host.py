@@ -25,9 +25,12 @@ from oracle import ddst_oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 # AddressSanitizer turns every out-of-bounds access of the kernels (shared arrays are statics,
 # device buffers are host vectors) into a failure
-SANITIZE = ["-fsanitize=address", "-fno-omit-frame-pointer"]
+SANITIZE = [SANITIZE, "-fno-omit-frame-pointer"]
 
 MAIN = r'''
 #include <cstdio>

@@ -19,6 +19,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 
 MAIN = r'''
 #include <fstream>
@@ -55,7 +58,7 @@ def harness(tmp_path_factory):
             "\n}  // namespace ddst\n" + MAIN)
     (d / "sblk_host.cpp").write_text(code)
     exe = d / "sblk_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "sblk_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
@@ -143,7 +146,7 @@ def power_harness(tmp_path_factory):
             "\n}  // namespace ddst\n" + POWER_MAIN)
     (d / "power_host.cpp").write_text(code)
     exe = d / "power_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "power_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
@@ -257,7 +260,7 @@ def apply_harness(tmp_path_factory):
             "\n".join(structs) + "\n" + consts + "\n" + src[i:j] + "\n}  // namespace ddst\n" + APPLY_MAIN)
     (d / "hodlr_apply_host.cpp").write_text(code)
     exe = d / "hodlr_apply_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "hodlr_apply_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]

@@ -21,6 +21,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 
 # Known-answer vectors of Philox4x32-10: (counter, key) -> output, as published with the
 # generator's reference implementation (Random123).
@@ -114,7 +117,7 @@ def run(tmp_path_factory):
             "\n}  // namespace ddst\n" + MAIN)
     (d / "rng.cpp").write_text(code)
     exe = d / "rng"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "rng.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]

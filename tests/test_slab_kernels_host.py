@@ -26,6 +26,9 @@ from oracle import ddst_oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 
 MAIN = r'''
 #include <fstream>
@@ -92,7 +95,7 @@ def harness(tmp_path_factory):
             "\n" + vidx + "\n" + src[i:j] + "\n" + src[k0:k1] + "\n}  // namespace ddst\n" + MAIN)
     (d / "slab_host.cpp").write_text(code)
     exe = d / "slab_host"
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", os.path.join(ROOT, "tests", "hostemu"),
                         str(d / "slab_host.cpp"), "-o", str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]

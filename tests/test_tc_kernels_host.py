@@ -19,6 +19,9 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2510_25991_gb300", "csrc")
+# AddressSanitizer by default; DDST_HOST_SANITIZER=thread runs the same tests under
+# ThreadSanitizer, which reports accesses of two threads that no barrier orders
+SANITIZE = "-fsanitize=" + os.environ.get("DDST_HOST_SANITIZER", "address")
 HOSTEMU = os.path.join(ROOT, "tests", "hostemu")
 
 # mbarrier helpers of common.cuh / umma.cuh on the host model (inside the library namespace,
@@ -98,7 +101,7 @@ def _compile(d, name, body, main):
             "#include <cstring>\nnamespace ddst {\n" + body + "\n}  // namespace ddst\n" + main)
     (d / f"{name}.cpp").write_text(code)
     exe = d / name
-    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", "-fsanitize=address",
+    r = subprocess.run([cxx, "-std=c++20", "-O1", "-pthread", SANITIZE,
                         "-fno-omit-frame-pointer", "-I", HOSTEMU, str(d / f"{name}.cpp"), "-o",
                         str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-4000:]
