@@ -22,6 +22,7 @@ import re
 import shutil
 import struct
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -278,8 +279,9 @@ def harness(tmp_path_factory):
 
 # 3D problems: (n, w, listed slabs).  n = 21, w = 7: m = 13 * 20 = 260 unknowns per block row,
 # M = 384 (three 128-wide panels: the look-ahead has a rest of the update to run beside the next
-# panel); n = 20, w = 5: m = 171, M = 256 (two panels), the first and last of three slabs.
-CFG64 = (21, 7, (0, 1))
+# panel), the second of two slabs; n = 20, w = 5: m = 171, M = 256 (two panels), the first and
+# last of three slabs (per-slab work buffers, a gap in the slab list).
+CFG64 = (21, 7, (1,))
 CFG32 = (20, 5, (0, 2))
 
 
@@ -350,7 +352,8 @@ def _one_sided_lu(Aj, nb, m):
 
 @pytest.fixture(scope="module")
 def fp64_runs(harness):
-    return [_run(harness, 8, sched, CFG64) for sched in (0, 1)]
+    with ThreadPoolExecutor(max_workers=2) as ex:   # two host processes side by side
+        return list(ex.map(lambda sched: _run(harness, 8, sched, CFG64), (0, 1)))
 
 
 def test_lookahead_orders_give_the_same_factors(fp64_runs):
@@ -472,8 +475,8 @@ def test_tensor_core_lookahead_orders_give_the_same_factors(harness):
     are written by the update of its row and column blocks and by the row step, into the other
     parity's buffers, while the rest of the current panel's update still reads this parity's.
     Both legal orders give the same factors bit for bit, and they are the block LU's."""
-    cfg = (CFG64[0], CFG64[1], (1,))
-    (r0, ctx), (r1, _) = (_run(harness, 4, sched, cfg, 1) for sched in (0, 1))
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        (r0, ctx), (r1, _) = ex.map(lambda sched: _run(harness, 4, sched, CFG64, 1), (0, 1))
     assert r0["code"] == 0.0 and r1["code"] == 0.0 and ctx["nP"] == 3
     assert np.array_equal(r0["F"], r1["F"])
     m, nb = ctx["m"], ctx["nb"]
